@@ -1,0 +1,233 @@
+"""Seeded synthetic NMPC instances (inputs only; none of the method's arithmetic).
+
+This module is the one piece shared by the CUDA path, its tests, the bench
+and the oracle's callers.  It draws numbers and lays out instance
+descriptions; it never evaluates the model, the KKT map or any solver step.
+
+Random numbers come from SplitMix64 (Steele, Lea, Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014): state += 0x9E3779B97F4A7C15,
+then two xor-shift-multiply rounds.  Doubles in [0, 1) take the top 53 bits;
+normals use the Box-Muller transform.
+
+Workload shapes follow the heat-transfer problems the method is evaluated on
+(Sec. 5 of the paper uses a 2D plate; the instances here are 1D/2D nonlinear
+heat equations with point heat-source actuators):
+
+* ``heat1d_single``  1D, M=32, dt=1e-4, N=20, actuators at x=0.25, 0.75
+* ``heat2d_single``  2D 64x64, dt=2e-5, N=50, 8 actuators on a 2x4 grid
+* ``heat1d_ragged_batch``  1024 1D instances with M, N, n_u, R drawn per seed
+* ``heat2d_large_batch``   64 2D 256x256 instances, N=100, 16 actuators
+
+Grid convention: interior cells only (Dirichlet-zero ring outside), cell
+(iy, ix) at coordinates ((ix+1)/(mx+1), (iy+1)/(my+1)), stored row-major,
+flat index iy*mx + ix.  A "point actuator at p" acts on the interior cell
+nearest to p (ties to the lower index) as a heat source: that cell's
+temperature equation gains ``act_gain * u_a``.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, n: int) -> np.ndarray:
+    """First ``n`` outputs of SplitMix64 started from state ``seed``."""
+    with np.errstate(over="ignore"):
+        k = np.arange(1, n + 1, dtype=np.uint64)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + k * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed: int, n: int) -> np.ndarray:
+    """``n`` doubles in [0, 1) from the top 53 bits of SplitMix64(seed)."""
+    return (splitmix64(seed, n) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def normal(seed: int, n: int) -> np.ndarray:
+    """``n`` standard normals by Box-Muller on consecutive uniform pairs."""
+    m = (n + 1) // 2
+    u = uniform01(seed, 2 * m)
+    u1 = 1.0 - u[0::2]  # (0, 1]
+    u2 = u[1::2]
+    r = np.sqrt(-2.0 * np.log(u1))
+    z = np.empty(2 * m)
+    z[0::2] = r * np.cos(2.0 * np.pi * u2)
+    z[1::2] = r * np.sin(2.0 * np.pi * u2)
+    return z[:n]
+
+
+@dataclasses.dataclass
+class Instance:
+    """One NMPC instance: grid, horizon, actuators, weights, x0 and reference.
+
+    ``x0`` and ``ref`` are flat (my*mx,) float64 arrays on the interior grid.
+    ``act`` holds flat cell indices of the actuator (heat source) cells and
+    ``act_gain`` the heating rate of such a cell per unit input.
+    Diffusivity k(w) = k0 * (1 + k1 * w).  Weights: stage cost
+    h/2 (q |x - ref|^2 + r |u|^2), terminal cost h/2 qf |x_N - ref|^2.
+    """
+
+    dim: int
+    mx: int
+    my: int
+    horizon: int
+    h: float
+    act: np.ndarray
+    q: float
+    r: float
+    qf: float
+    gamma: float
+    k0: float
+    k1: float
+    x0: np.ndarray
+    ref: np.ndarray
+    act_gain: float = 32.0
+    name: str = ""
+
+    @property
+    def ng(self) -> int:
+        return self.mx * self.my
+
+    @property
+    def n_u(self) -> int:
+        return int(len(self.act))
+
+
+def nearest_cell(p: float, m: int) -> int:
+    """0-based interior cell nearest to coordinate p on m cells of [0,1]."""
+    # cell j (0-based) sits at (j+1)/(m+1); ties go to the lower index
+    t = p * (m + 1) - 1.0
+    j = int(math.floor(t))
+    if t - j > 0.5:
+        j += 1
+    return min(max(j, 0), m - 1)
+
+
+def _coords_1d(m: int) -> np.ndarray:
+    return np.arange(1, m + 1, dtype=np.float64) / (m + 1)
+
+
+def _sine_field(mx: int, my: int, seed: int, modes: int = 4, std: float = 0.1) -> np.ndarray:
+    a = normal(seed, modes * modes).reshape(modes, modes) * std
+    xs, ys = _coords_1d(mx), _coords_1d(my)
+    f = np.zeros((my, mx))
+    for p in range(1, modes + 1):
+        sx = np.sin(p * np.pi * xs)
+        for q in range(1, modes + 1):
+            f += a[p - 1, q - 1] * np.outer(np.sin(q * np.pi * ys), sx)
+    return f.reshape(-1)
+
+
+def _gauss_bump(mx: int, my: int, cx: float = 0.5, cy: float = 0.5,
+                amp: float = 1.0, width: float = 0.15) -> np.ndarray:
+    xs, ys = _coords_1d(mx), _coords_1d(my)
+    d2 = (xs[None, :] - cx) ** 2 + (ys[:, None] - cy) ** 2
+    return (amp * np.exp(-d2 / (2.0 * width * width))).reshape(-1)
+
+
+def _act_grid(mx: int, my: int, nx_act: int, ny_act: int) -> np.ndarray:
+    cells = []
+    for r in range(ny_act):
+        iy = nearest_cell((r + 0.5) / ny_act, my)
+        for c in range(nx_act):
+            ix = nearest_cell((c + 0.5) / nx_act, mx)
+            cells.append(iy * mx + ix)
+    return np.asarray(cells, dtype=np.int32)
+
+
+def default_gamma(h: float, r: float) -> float:
+    """Regularization weight used when a workload does not fix one: gamma = h R,
+    the ratio of the paper's experiment (gamma = 0.5 with h = 5 s, R = 0.1)."""
+    return h * r
+
+
+def heat1d(m: int, horizon: int, n_u: int, r: float, seed: int, h: float = 1e-4,
+           act_pos: Optional[List[float]] = None, gamma: Optional[float] = None,
+           k1: float = 0.5, name: str = "") -> Instance:
+    """1D instance: x0 ~ U[0,1] per cell (SplitMix64(seed)), ref 0.8 sin(pi x)."""
+    if act_pos is None:
+        act_pos = [(a + 0.5) / n_u for a in range(n_u)]
+    act = np.asarray([nearest_cell(p, m) for p in act_pos], dtype=np.int32)
+    x0 = uniform01(seed, m)
+    ref = 0.8 * np.sin(np.pi * _coords_1d(m))
+    return Instance(dim=1, mx=m, my=1, horizon=horizon, h=h, act=act, q=1.0, r=r,
+                    qf=10.0, gamma=default_gamma(h, r) if gamma is None else gamma,
+                    k0=0.1, k1=k1, x0=x0, ref=ref, name=name)
+
+
+def heat2d(mx: int, my: int, horizon: int, nx_act: int, ny_act: int, seed: int,
+           h: float = 2e-5, r: float = 0.01, gamma: Optional[float] = None,
+           ref_center=(0.5, 0.5), ref_amp: float = 1.0, k1: float = 0.5,
+           name: str = "") -> Instance:
+    """2D instance: 16-mode sine initial field (a_pq ~ N(0, 0.1^2), seed),
+    Gaussian-bump reference (sigma 0.15), actuators on a regular grid."""
+    act = _act_grid(mx, my, nx_act, ny_act)
+    x0 = _sine_field(mx, my, seed)
+    ref = _gauss_bump(mx, my, ref_center[0], ref_center[1], ref_amp)
+    return Instance(dim=2, mx=mx, my=my, horizon=horizon, h=h, act=act, q=1.0, r=r,
+                    qf=10.0, gamma=default_gamma(h, r) if gamma is None else gamma,
+                    k0=0.1, k1=k1, x0=x0, ref=ref, name=name)
+
+
+def heat1d_single() -> Instance:
+    """1D, M=32, dt=1e-4, N=20, actuators at x=0.25 and 0.75, x0 ~ U[0,1] seed 0."""
+    return heat1d(32, 20, 2, 0.01, seed=0, act_pos=[0.25, 0.75], name="heat1d_M32_N20")
+
+
+def heat2d_single(seed: int = 1) -> Instance:
+    """2D 64x64, dt=2e-5, N=50, 8 actuators (2 rows x 4 columns), seed 1."""
+    return heat2d(64, 64, 50, 4, 2, seed=seed, name="heat2d_64x64_N50")
+
+
+def heat1d_ragged_batch(n: int = 1024, base_seed: int = 3000) -> List[Instance]:
+    """Ragged 1D batch: instance b uses seed base_seed+b to draw
+    M ~ U{32..256}, N ~ U{10..60}, n_u ~ U{1..4}, R = 10^U[-3,-1];
+    its x0 comes from seed (base_seed+b) << 20."""
+    out = []
+    for b in range(n):
+        s = base_seed + b
+        d = uniform01(s, 4)
+        m = 32 + int(d[0] * 225)
+        horizon = 10 + int(d[1] * 51)
+        n_u = 1 + int(d[2] * 4)
+        r = 10.0 ** (-3.0 + 2.0 * d[3])
+        out.append(heat1d(m, horizon, n_u, r, seed=s << 20, name=f"heat1d_b{b}"))
+    return out
+
+
+def heat2d_large_batch(n: int = 64, base_seed: int = 5000, m: int = 256,
+                       horizon: int = 100) -> List[Instance]:
+    """Large 2D batch: 256x256, N=100, 16 actuators (4x4), dt=2e-5; instance b
+    has sine initial field seed base_seed+b and a bump reference whose centre
+    ~ U[0.3,0.7]^2 and amplitude ~ U[0.5,1.5] come from seed base_seed+b+10^6."""
+    out = []
+    for b in range(n):
+        d = uniform01(base_seed + b + 1_000_000, 3)
+        out.append(heat2d(m, m, horizon, 4, 4, seed=base_seed + b,
+                          ref_center=(0.3 + 0.4 * d[0], 0.3 + 0.4 * d[1]),
+                          ref_amp=0.5 + d[2], name=f"heat2d_{m}_b{b}"))
+    return out
+
+
+def tiny1d(m: int = 8, horizon: int = 4, n_u: int = 1, seed: int = 7, h: float = 1e-3,
+           k1: float = 0.5, gamma: Optional[float] = None) -> Instance:
+    """Small 1D instance for dense cross-checks (Newton, full KKT LU, Riccati)."""
+    return heat1d(m, horizon, n_u, 0.01, seed=seed, h=h, k1=k1, gamma=gamma,
+                  name=f"tiny1d_M{m}_N{horizon}")
+
+
+def tiny2d(mx: int = 6, my: int = 6, horizon: int = 3, seed: int = 11, h: float = 1e-3,
+           k1: float = 0.5, gamma: Optional[float] = None) -> Instance:
+    """Small 2D instance (2x2 actuators) for dense cross-checks."""
+    return heat2d(mx, my, horizon, 2, 2, seed=seed, h=h, k1=k1, gamma=gamma,
+                  name=f"tiny2d_{mx}x{my}_N{horizon}")
