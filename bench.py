@@ -1,0 +1,290 @@
+"""Benchmark: solves/s of the double-layer Jacobi NMPC method on one GB300.
+
+A step is one complete solve, from the cold start S^0, of the 2D nonlinear
+heat workload (64x64 grid, N = 50 stages, 8 actuators, dt = 2e-5) to
+||K||_inf <= 1e-6, with a fresh seeded initial field every step, on the
+MIXED path (float32 lower layer, float64 KKT residual / norms / update).
+Inputs are resident in HBM when a step starts; the L2 cache is flushed
+(256 MiB write) between steps, outside the per-step CUDA events.
+
+Under torchrun (N > 1) every rank solves its own replicas (the instances are
+independent; there is no data-path collective): value = solves of all ranks
+/ max-over-ranks time.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores for the same
+workload and metric (bounded sample: a fixed number of oracle iterations per
+step, converted to solves/s with the oracle's own iteration count).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Solves/s to KKT res≤1e-6, batched+learned vs plain; HBM GB/s vs peak"
+WORKLOAD = ("heat2d_64x64_N50: 2D nonlinear heat eq. k(w)=0.1(1+0.5w), 64x64 grid, dt=2e-5, "
+            "N=50, 8 actuators (2x4), Gaussian-bump reference, 16-mode sine initial field; "
+            "plain double-layer Jacobi, cold start, tol ||K||_inf<=1e-6")
+TOL = 1e-6
+BYTES_PER_POINT_STAGE = 32  # algorithmic bytes per cell-stage per iteration
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--ref-iters", type=int, default=8, help="oracle iterations per reference step")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def step_instance(step: int, rank: int):
+    from paper_2004_02484_gb300 import workloads as wl
+    # step 0 is the canonical seed-1 field; later steps draw fresh seeded fields
+    seed = 1 if (step == 0 and rank == 0) else 100_000 + 1000 * rank + step
+    return wl.heat2d_single(seed=seed)
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx = float(r[1])
+                for n, v in zip(names, r[4:8]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def run_oracle_sample(iters: int):
+    """Bounded oracle sample on the host: `iters` upper-layer iterations of the
+    workload, and the oracle's own iteration count to the tolerance."""
+    from oracle import nmpc as O
+    inst = step_instance(0, 0)
+    p = O.Problem(inst)
+    X, U, L = p.cold_start()
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        X, U, L, _ = O.jacobi_iteration(p, X, U, L)
+    return time.perf_counter() - t0
+
+
+def oracle_iters_to_tol():
+    from oracle import nmpc as O
+    p = O.Problem(step_instance(0, 0))
+    _, info = O.solve_jacobi(p, tol=TOL)
+    return info["iters"]
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    n_it = oracle_iters_to_tol()  # part of warm-up: the oracle's own iteration count
+    for _ in range(args.warmup):
+        run_oracle_sample(1)
+    t = 0.0
+    for _ in range(args.steps):
+        t += run_oracle_sample(args.ref_iters)
+    sec_per_iter = t / (args.steps * args.ref_iters)
+    value = 1.0 / (sec_per_iter * n_it)
+    cb = {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+          "sample": f"{args.ref_iters} FP64 numpy oracle iterations per step x {args.steps} steps; "
+                    f"solves/s = 1 / (s per iteration x {n_it} oracle iterations to 1e-6)"}
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+                      "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": 1e3 * sec_per_iter * n_it, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic", "config": {"workload": WORKLOAD, "tol": TOL},
+                      "cpu_baseline": cb,
+                      "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    rank, world, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2004_02484_gb300 import build as b
+    b.build()
+    from paper_2004_02484_gb300 import nmpc as G
+
+    prec = G.NMPC_MIXED if args.precision == "mixed" else G.NMPC_FP64
+    insts = [step_instance(s, rank) for s in range(args.warmup + args.steps)]
+    solver = G.Solver([insts[0]], tol=TOL, precision=prec, max_iter=5000, check_every=16)
+    dev = solver.u.device
+    x0s = [torch.from_numpy(G.pack_fields([i], "x0")).to(dev) for i in insts]
+    refs = [torch.from_numpy(G.pack_fields([i], "ref")).to(dev) for i in insts]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def one(step):
+        return G.nmpc_solve(solver.h, x0s[step], refs[step], solver.u, 1, stream=stream)
+
+    for s in range(args.warmup):
+        rc, st = one(s)
+        assert rc == G.NMPC_OK, rc
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    iters, launches0 = [], G.nmpc_launch_count(solver.h)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            rc, st = one(args.warmup + k)
+            ev[k][1].record(stream)
+            assert rc == G.NMPC_OK and st[0].res_inf <= TOL, (rc, st[0].res_inf)
+            iters.append(st[0].iters)
+        torch.cuda.synchronize()
+    launches = G.nmpc_launch_count(solver.h) - launches0
+    t_ms = sum(a.elapsed_time(b_) for a, b_ in ev)
+    if world > 1:
+        tt = torch.tensor([t_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(tt.item())
+        torch.distributed.barrier()
+    value = world * args.steps / (t_ms / 1e3)
+
+    # end to end through the host-pointer entry point (pinned host buffers)
+    x0h = [torch.from_numpy(G.pack_fields([i], "x0")).pin_memory().numpy() for i in insts]
+    refh = [torch.from_numpy(G.pack_fields([i], "ref")).pin_memory().numpy() for i in insts]
+    uh = torch.zeros(solver.n_u, dtype=torch.float64).pin_memory().numpy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        rc, st = G.nmpc_solve_host(solver.h, x0h[args.warmup + k], refh[args.warmup + k], uh, 1)
+        assert rc == G.NMPC_OK
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+
+    # roofline of the dominant kernel (the fused iteration kernel): average
+    # duration per iteration launch over the timed region (includes the graph
+    # gaps and host polls, so it is an upper bound on the kernel duration)
+    ins = insts[0]
+    cells = ins.horizon * ins.mx * ins.my
+    iter_launches = sum(i + 1 for i in iters)
+    avg_launch_ms = t_ms / max(1, launches)
+    peaks, which = measured_peaks()
+    achieved = BYTES_PER_POINT_STAGE * cells / (avg_launch_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "peak_source": which,
+            "kernel": "k_iterate<float,SOLVE> (fused residual + lower layer + update)",
+            "algorithmic_bytes_per_launch": BYTES_PER_POINT_STAGE * cells,
+            "avg_launch_ms": avg_launch_ms}
+    cpu = None
+    if rank == 0:
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        n_it = oracle_iters_to_tol()
+        t_or = run_oracle_sample(args.ref_iters)
+        sec_per_iter = t_or / args.ref_iters
+        cpu = {"value": 1.0 / (sec_per_iter * n_it), "unit": "solves/s", "cores": 1,
+               "kind": "oracle",
+               "sample": f"{args.ref_iters} FP64 numpy oracle iterations of the seed-1 field; "
+                         f"solves/s = 1 / (s per iteration x {n_it} oracle iterations to 1e-6)"}
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f32+f64" if prec == G.NMPC_MIXED else "f64", "data": "synthetic",
+               "config": {"workload": WORKLOAD, "precision": args.precision, "tol": TOL,
+                          "instances_per_rank": 1,
+                          "l2": "flushed between steps (256 MiB write) outside the per-step events",
+                          "iterations_per_solve": {"min": min(iters), "max": max(iters),
+                                                   "mean": sum(iters) / len(iters)}},
+               "e2e": {"value": world * args.steps / e2e_s, "unit": "solves/s",
+                       "h2d_bytes_per_step": 2 * 8 * ins.mx * ins.my,
+                       "d2h_bytes_per_step": 8 * ins.horizon * len(ins.act)},
+               "gpu_launches": launches,
+               "roofline": roof,
+               "cpu_baseline": cpu,
+               "clocks": clk.summary()}
+        print(json.dumps(out), flush=True)
+    solver.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * nmpc.h -- C ABI of the GB300 double-layer Jacobi NMPC solver.
+ *
+ * Method: H. Deng, T. Ohtsuka, "A Double-Layer Jacobi Method for
+ * PDE-Constrained Nonlinear Model Predictive Control".
+ *
+ * Problem solved for each instance (Sec. 2-3 of the paper):
+ *   model   w_t = div(k(w) grad w) + sum_a act_gain * u_a * [cell act_cell[a]]
+ *           k(w) = k0 (1 + k1 w), interior grid of mx*my cells on [0,1]^dim
+ *           with a Dirichlet-zero ring, 3-point (1D) / 5-point (2D)
+ *           finite differences of the Kirchhoff form (Sec. 2, eq. 4);
+ *   NLP     backward Euler x_i = x_{i-1} + h f(u_i, x_i), i = 1..N (eq. 6),
+ *           cost sum_i h/2 (q|x_i - ref|^2 + r|u_i|^2) + h/2 qf|x_N - ref|^2,
+ *           regularization gamma/2 |u_i - u_i^k|^2 (eq. 7, Remark 1);
+ *   solve   K(S) = 0 for the KKT map of eq. 9 by the upper-layer Jacobi
+ *           iteration S <- S - alpha D^{-1} K (eq. 15, all stages at once)
+ *           with the lower-layer structured solve of each stage block
+ *           (Sec. 4.3, eqs. 21-24; u fixed-point iteration of Sec. 5.2).
+ *
+ * Array layout ("packed"), for instances b = 0..n-1 in setup order, each
+ * grid stored row-major (flat cell index iy*mx + ix), all float64:
+ *   x0, ref   [sum_b ng_b]              ng_b = mx_b * my_b
+ *   x, lam    [sum_b N_b * ng_b]        stage-major: stage i (1..N) at (i-1)*ng_b
+ *   u         [sum_b N_b * n_u_b]       stage-major
+ * Device pointers are plain CUDA device addresses (e.g. torch data_ptr()).
+ * The caller owns every buffer it passes; the handle owns its workspace,
+ * allocated in nmpc_setup and freed in nmpc_destroy.  Solves allocate
+ * nothing.  All calls are asynchronous on `stream` (a cudaStream_t, NULL =
+ * legacy default stream) except where stated.  Functions return NMPC_OK or a
+ * negative NMPC_ERR_* code; no C++ exception crosses this interface.
+ */
+#ifndef NMPC_GB300_H
+#define NMPC_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NMPC_OK 0
+#define NMPC_ERR_BAD_ARG (-1)       /* invalid argument or descriptor          */
+#define NMPC_ERR_CUDA (-2)          /* a CUDA runtime call failed              */
+#define NMPC_ERR_NOT_CONVERGED (-3) /* max_iter reached above tol              */
+#define NMPC_ERR_DIVERGED (-4)      /* residual became NaN/Inf or exploded     */
+#define NMPC_ERR_NO_DEVICE (-5)     /* no usable CUDA device                   */
+#define NMPC_ERR_UNSUPPORTED (-6)   /* size beyond what the kernels support    */
+
+#define NMPC_FP64 0  /* all arithmetic in float64                              */
+#define NMPC_MIXED 1 /* lower layer (Sec. 4.3) in float32; KKT residual, norms,
+                        convergence test and the update of S in float64       */
+
+#define NMPC_INIT_COLD 0 /* S^0: x_i = x0, u_i = 0, lambda_i = 0              */
+#define NMPC_INIT_WARM 1 /* S^0 = the handle's current state (last solution or
+                            a state set by nmpc_set_state)                     */
+
+/* Per-instance status in nmpc_stats.status */
+#define NMPC_STATUS_CONVERGED 1
+#define NMPC_STATUS_DIVERGED 2
+#define NMPC_STATUS_MAX_ITER 3
+
+/* One NMPC instance.  act_cell is a host pointer read during nmpc_setup only. */
+typedef struct {
+  int dim;             /* 1 or 2                                              */
+  int mx, my;          /* interior cells per axis (my = 1 when dim == 1)      */
+  int horizon;         /* N >= 1 stages                                       */
+  int n_u;             /* actuators, 1..NMPC_MAX_NU                           */
+  const int* act_cell; /* [n_u] flat cell indices, 0 <= c < mx*my             */
+  double h;            /* stage length T/N                                    */
+  double q, r, qf;     /* Q = q I, R = r I, terminal Qf = qf I                */
+  double gamma;        /* regularization weight (> 0 in practice, Thm 2)      */
+  double k0, k1;       /* k(w) = k0 (1 + k1 w)                                */
+  double act_gain;     /* heating rate of an actuator cell per unit input     */
+} nmpc_desc;
+
+#define NMPC_MAX_NU 64
+#define NMPC_MAX_NG (1 << 20)
+
+/* Iteration options; nmpc_default_opts fills the paper's settings
+   (two lower-layer Jacobi sweeps and two u-iterations, Table 2 / Sec. 5.2). */
+typedef struct {
+  double tol;      /* stop once ||K(S^k)||_inf <= tol (float64 norm)          */
+  int max_iter;    /* upper-layer iterations before NMPC_STATUS_MAX_ITER      */
+  int n_lo;        /* pointwise Jacobi sweeps per F_x and F_x^T solve (>= 1)  */
+  int n_u_it;      /* fixed-point iterations for Delta u (>= 1)               */
+  int precision;   /* NMPC_FP64 or NMPC_MIXED                                 */
+  int check_every; /* iterations between host polls of the convergence count  */
+  double alpha;    /* step length in (0, 1]                                   */
+  double div_limit;/* residual above div_limit * ||K(S^0)||_inf => diverged   */
+  int threads;     /* threads per CTA (multiple of 32, <= 512); 0 = auto      */
+  int use_graph;   /* capture the iteration chunk in a CUDA graph (1) or not  */
+} nmpc_opts;
+
+typedef struct {
+  int iters;      /* index k of the returned iterate S^k                       */
+  int status;     /* NMPC_STATUS_*                                            */
+  double res_inf; /* ||K(S^k)||_inf (float64)                                 */
+  double res_2;   /* ||K(S^k)||_2                                             */
+} nmpc_stats;
+
+typedef struct nmpc_handle nmpc_handle;
+
+/* Fill *o with defaults: tol 1e-6, max_iter 2000, n_lo 2, n_u_it 2, FP64,
+   check_every 16, alpha 1, div_limit 1e8, threads auto, graph on. */
+void nmpc_default_opts(nmpc_opts* o);
+
+/* Validate the descriptors, build the device instance table and allocate the
+   workspace on the current CUDA device.  On success *out owns everything;
+   release it with nmpc_destroy.  Errors: BAD_ARG (a descriptor field out of
+   range, NULL pointers), UNSUPPORTED (n_u > NMPC_MAX_NU, ng > NMPC_MAX_NG),
+   NO_DEVICE, CUDA.  Synchronous. */
+int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
+               nmpc_handle** out);
+
+/* Solve every instance from x0 (packed [sum ng], device) tracking ref
+   (packed [sum ng], device).  horizon: 0 = each instance's own N; only 0 or a
+   value equal to every instance's N is accepted (BAD_ARG otherwise).
+   weights: NULL, or device [n_instances][3] = (q, r, qf) overriding the
+   descriptors for this and later solves.  init: NMPC_INIT_COLD / _WARM.
+   u_out: device packed u of the returned iterates.  stats: host
+   [n_instances], written before return (the call synchronizes on stream).
+   Returns NMPC_OK when every instance converged, else the first of
+   NOT_CONVERGED / DIVERGED met; stats are filled in either case. */
+int nmpc_solve(nmpc_handle* h, const double* x0, const double* ref, int horizon,
+               const double* weights, int init, double* u_out, nmpc_stats* stats,
+               void* stream);
+
+/* As nmpc_solve, but x0, ref, weights and u_out are HOST pointers; the
+   host-device copies run on `stream` inside the call. */
+int nmpc_solve_host(nmpc_handle* h, const double* x0, const double* ref, int horizon,
+                    const double* weights, int init, double* u_out, nmpc_stats* stats,
+                    void* stream);
+
+/* Float64 KKT residual (eq. 9, u~ = u) of the state (x, u, lam) (packed,
+   device) for initial states x0 and references ref (device).  out: host
+   [n_instances][2] = (||K_b||_inf, ||K_b||_2).  Synchronizes on stream. */
+int nmpc_residual(nmpc_handle* h, const double* x0, const double* ref, const double* x,
+                  const double* u, const double* lam, double* out, void* stream);
+
+/* n_iter >= 1 plain upper-layer iterations (eq. 15) from (x_in, u_in,
+   lam_in) to (x_out, u_out, lam_out), all packed device arrays, with no
+   convergence test (the handle's ping-pong buffers hold the intermediate
+   iterates, so in and out may alias).  out_res: NULL or host
+   [n_instances][2], the norms of K at the last input iterate S^{n_iter-1}.
+   Synchronizes on stream when out_res is given. */
+int nmpc_iterate(nmpc_handle* h, const double* x0, const double* ref, const double* x_in,
+                 const double* u_in, const double* lam_in, double* x_out, double* u_out,
+                 double* lam_out, int n_iter, double* out_res, void* stream);
+
+/* Copy the handle's current state (after a solve: the returned iterates) to
+   packed device arrays x, u, lam; any pointer may be NULL to skip it. */
+int nmpc_get_state(nmpc_handle* h, double* x, double* u, double* lam, void* stream);
+
+/* Replace the handle's current state (the NMPC_INIT_WARM start). */
+int nmpc_set_state(nmpc_handle* h, const double* x, const double* u, const double* lam,
+                   void* stream);
+
+/* Sizes of the packed arrays: out[0] = sum ng, out[1] = sum N*ng,
+   out[2] = sum N*n_u. */
+int nmpc_sizes(const nmpc_handle* h, int64_t* out);
+
+/* Number of kernel launches issued by this handle since setup (all entry
+   points), for launch accounting. */
+int64_t nmpc_launch_count(const nmpc_handle* h);
+
+/* Free the workspace and the handle (NULL is a no-op).  Synchronizes. */
+void nmpc_destroy(nmpc_handle* h);
+
+/* Static string for an NMPC_* code. */
+const char* nmpc_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NMPC_GB300_H */

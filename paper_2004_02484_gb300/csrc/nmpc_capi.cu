@@ -1,0 +1,638 @@
+// Host side of the C ABI declared in include/nmpc.h: descriptor validation,
+// device instance table, workspace ownership, launch configuration, the
+// graph-replayed iteration loop and the result gathering.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/nmpc.h"
+#include "nmpc_kernels.cuh"
+
+using nmpc_dev::InstDev;
+using nmpc_dev::IterArgs;
+using nmpc_dev::FinalArgs;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct nmpc_handle {
+  int n_inst = 0;
+  nmpc_opts opts{};
+  int device = 0;
+  int num_sms = 0;
+  std::vector<InstDev> inst_h;
+  long long n_g = 0, n_s = 0, n_u = 0;  // packed sizes: sum ng, sum N*ng, sum N*nu
+  int ng_max = 0, nu_max = 0, n_work = 0, n_max_horizon = 0;
+  // device data
+  InstDev* inst_d = nullptr;
+  int2* work_d = nullptr;
+  int* act_d = nullptr;
+  double* x0_d = nullptr;
+  double* ref_d = nullptr;
+  double* uo_d = nullptr;  // staging for the host-pointer solve
+  double* w_d = nullptr;   // staging for host weights
+  double* xb[3] = {nullptr, nullptr, nullptr};  // A, B, current
+  double* ub[3] = {nullptr, nullptr, nullptr};
+  double* lb[3] = {nullptr, nullptr, nullptr};
+  // control
+  int* ictl = nullptr;  // iter_k, block_done, n_active
+  unsigned long long* res_inf = nullptr;
+  double* res_sq = nullptr;
+  unsigned long long* res_first = nullptr;
+  int* status = nullptr;
+  int* iters = nullptr;
+  int* final_buf = nullptr;
+  double* fin_inf = nullptr;
+  double* fin_2 = nullptr;
+  char* scratch = nullptr;
+  long long scratch_stride = 0;
+  // pinned host mirrors
+  int* h_active = nullptr;
+  int* h_status = nullptr;
+  int* h_iters = nullptr;
+  double* h_fin = nullptr;  // [2][n]
+  double* h_res = nullptr;  // [2][n] for residual readback
+  unsigned long long* h_resinf = nullptr;
+  // launch configuration
+  int threads = 0;
+  int grid = 0;
+  size_t smem = 0;
+  bool smem_mode = true;
+  bool mixed = false;
+  // graph of one chunk of iterations
+  cudaGraphExec_t graph_exec = nullptr;
+  int graph_chunk = 0;
+  long long launches = 0;
+  bool has_state = false;
+};
+
+namespace {
+
+template <typename T>
+size_t small_shared_bytes() {
+  return (sizeof(nmpc_dev::SmallShared<T>) + 15) & ~size_t(15);
+}
+
+#define CK(call)                                                   \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) {                                       \
+      fprintf(stderr, "nmpc: %s failed: %s (%s:%d)\n", #call,      \
+              cudaGetErrorString(e_), __FILE__, __LINE__);         \
+      return NMPC_ERR_CUDA;                                        \
+    }                                                              \
+  } while (0)
+
+template <typename P>
+cudaError_t dev_alloc(P** p, size_t count) {
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)p, count * sizeof(P));
+}
+
+void free_all(nmpc_handle* h) {
+  if (!h) return;
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  void* ptrs[] = {h->inst_d, h->work_d, h->act_d, h->x0_d, h->ref_d, h->uo_d, h->w_d,
+                  h->xb[0], h->xb[1], h->xb[2], h->ub[0], h->ub[1], h->ub[2],
+                  h->lb[0], h->lb[1], h->lb[2], h->ictl, h->res_inf, h->res_sq,
+                  h->res_first, h->status, h->iters, h->final_buf, h->fin_inf,
+                  h->fin_2, h->scratch};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  void* hp[] = {h->h_active, h->h_status, h->h_iters, h->h_fin, h->h_res, h->h_resinf};
+  for (void* p : hp)
+    if (p) cudaFreeHost(p);
+}
+
+IterArgs make_args(nmpc_handle* h) {
+  IterArgs A{};
+  A.inst = h->inst_d;
+  A.work = h->work_d;
+  A.n_work = h->n_work;
+  A.n_inst = h->n_inst;
+  A.act = h->act_d;
+  A.x0 = h->x0_d;
+  A.ref = h->ref_d;
+  for (int q = 0; q < 2; ++q) {
+    A.xin[q] = h->xb[q];
+    A.uin[q] = h->ub[q];
+    A.lin[q] = h->lb[q];
+    A.xout[q] = h->xb[q];
+    A.uout[q] = h->ub[q];
+    A.lout[q] = h->lb[q];
+  }
+  A.iter_k = h->ictl + 0;
+  A.block_done = h->ictl + 1;
+  A.n_active = h->ictl + 2;
+  A.res_inf = h->res_inf;
+  A.res_sq = h->res_sq;
+  A.res_first = h->res_first;
+  A.status = h->status;
+  A.iters = h->iters;
+  A.final_buf = h->final_buf;
+  A.fin_inf = h->fin_inf;
+  A.fin_2 = h->fin_2;
+  A.tol = h->opts.tol;
+  A.div_limit = h->opts.div_limit;
+  A.alpha = h->opts.alpha;
+  A.max_iter = h->opts.max_iter;
+  A.n_lo = h->opts.n_lo;
+  A.n_u_it = h->opts.n_u_it;
+  A.resid_only = 0;
+  A.scratch = h->smem_mode ? nullptr : h->scratch;
+  A.scratch_stride = h->scratch_stride;
+  A.ng_max = h->ng_max;
+  return A;
+}
+
+template <int MODE>
+cudaError_t launch_iterate(nmpc_handle* h, const IterArgs& A, cudaStream_t st) {
+  h->launches++;
+  if (h->mixed)
+    nmpc_dev::k_iterate<float, MODE><<<h->grid, h->threads, h->smem, st>>>(A);
+  else
+    nmpc_dev::k_iterate<double, MODE><<<h->grid, h->threads, h->smem, st>>>(A);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t configure_kernels(size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(nmpc_dev::k_iterate<T, nmpc_dev::MODE_SOLVE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(nmpc_dev::k_iterate<T, nmpc_dev::MODE_ONESHOT>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+int validate(const nmpc_desc* d) {
+  if (!d) return NMPC_ERR_BAD_ARG;
+  if (d->dim != 1 && d->dim != 2) return NMPC_ERR_BAD_ARG;
+  if (d->mx < 1 || d->my < 1 || (d->dim == 1 && d->my != 1)) return NMPC_ERR_BAD_ARG;
+  if (d->horizon < 1 || d->n_u < 1 || !d->act_cell) return NMPC_ERR_BAD_ARG;
+  if (d->n_u > NMPC_MAX_NU) return NMPC_ERR_UNSUPPORTED;
+  if ((long long)d->mx * d->my > NMPC_MAX_NG) return NMPC_ERR_UNSUPPORTED;
+  const long long ng = (long long)d->mx * d->my;
+  for (int a = 0; a < d->n_u; ++a)
+    if (d->act_cell[a] < 0 || d->act_cell[a] >= ng) return NMPC_ERR_BAD_ARG;
+  if (!(d->h > 0) || !(d->q >= 0) || !(d->r > 0) || !(d->qf >= 0) || !(d->gamma >= 0))
+    return NMPC_ERR_BAD_ARG;
+  if (!(d->k0 > 0) || !std::isfinite(d->k1) || !std::isfinite(d->act_gain))
+    return NMPC_ERR_BAD_ARG;
+  return NMPC_OK;
+}
+
+int run_chunk(nmpc_handle* h, const IterArgs& A, cudaStream_t st, int chunk) {
+  if (h->opts.use_graph) {
+    if (!h->graph_exec || h->graph_chunk != chunk) {
+      if (h->graph_exec) {
+        cudaGraphExecDestroy(h->graph_exec);
+        h->graph_exec = nullptr;
+      }
+      cudaStream_t cap;
+      CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+      cudaGraph_t g;
+      CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+      for (int i = 0; i < chunk; ++i) {
+        cudaError_t e = launch_iterate<nmpc_dev::MODE_SOLVE>(h, A, cap);
+        if (e != cudaSuccess) {
+          cudaStreamEndCapture(cap, &g);
+          cudaStreamDestroy(cap);
+          return NMPC_ERR_CUDA;
+        }
+      }
+      h->launches -= chunk;  // capture is not execution
+      CK(cudaStreamEndCapture(cap, &g));
+      CK(cudaGraphInstantiate(&h->graph_exec, g, 0));
+      cudaGraphDestroy(g);
+      cudaStreamDestroy(cap);
+      h->graph_chunk = chunk;
+    }
+    CK(cudaGraphLaunch(h->graph_exec, st));
+    h->launches += chunk;
+  } else {
+    for (int i = 0; i < chunk; ++i) CK(launch_iterate<nmpc_dev::MODE_SOLVE>(h, A, st));
+  }
+  return NMPC_OK;
+}
+
+FinalArgs make_final(nmpc_handle* h, double* u_out) {
+  FinalArgs F{};
+  F.inst = h->inst_d;
+  F.n_inst = h->n_inst;
+  for (int q = 0; q < 2; ++q) {
+    F.xs[q] = h->xb[q];
+    F.us[q] = h->ub[q];
+    F.ls[q] = h->lb[q];
+  }
+  F.xc = h->xb[2];
+  F.uc = h->ub[2];
+  F.lc = h->lb[2];
+  F.u_out = u_out;
+  F.status = h->status;
+  F.iters = h->iters;
+  F.final_buf = h->final_buf;
+  F.fin_inf = h->fin_inf;
+  F.fin_2 = h->fin_2;
+  F.res_inf = h->res_inf;
+  F.res_sq = h->res_sq;
+  F.tol = h->opts.tol;
+  F.max_iter = h->opts.max_iter;
+  return F;
+}
+
+dim3 per_instance_grid(const nmpc_handle* h) {
+  return dim3(64, (unsigned)h->n_inst);
+}
+
+// The solve proper, on device buffers owned by the handle (x0_d, ref_d).
+int solve_core(nmpc_handle* h, int horizon, const double* weights, int init, double* u_out,
+               nmpc_stats* stats, cudaStream_t st) {
+  if (horizon != 0) {
+    for (const InstDev& I : h->inst_h)
+      if (I.N != horizon) return NMPC_ERR_BAD_ARG;
+  }
+  if (init != NMPC_INIT_COLD && init != NMPC_INIT_WARM) return NMPC_ERR_BAD_ARG;
+  if (init == NMPC_INIT_WARM && !h->has_state) return NMPC_ERR_BAD_ARG;
+  if (weights) {
+    nmpc_dev::k_set_weights<<<(h->n_inst + 127) / 128, 128, 0, st>>>(h->inst_d, h->n_inst,
+                                                                    weights);
+    h->launches++;
+    CK(cudaGetLastError());
+  }
+  IterArgs A = make_args(h);
+  if (init == NMPC_INIT_WARM) {
+    CK(cudaMemcpyAsync(h->xb[0], h->xb[2], h->n_s * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(h->lb[0], h->lb[2], h->n_s * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(h->ub[0], h->ub[2], h->n_u * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
+  nmpc_dev::k_init_control<<<per_instance_grid(h), 256, 0, st>>>(A, init == NMPC_INIT_COLD);
+  h->launches++;
+  CK(cudaGetLastError());
+
+  const int chunk = std::max(1, h->opts.check_every);
+  long long launched = 0;
+  while (launched <= h->opts.max_iter) {
+    int rc = run_chunk(h, A, st, chunk);
+    if (rc != NMPC_OK) return rc;
+    launched += chunk;
+    CK(cudaMemcpyAsync(h->h_active, h->ictl + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (*h->h_active == 0) break;
+  }
+  FinalArgs F = make_final(h, u_out);
+  nmpc_dev::k_finalize_status<<<(h->n_inst + 127) / 128, 128, 0, st>>>(F);
+  nmpc_dev::k_gather_final<<<per_instance_grid(h), 256, 0, st>>>(F);
+  h->launches += 2;
+  CK(cudaGetLastError());
+  h->has_state = true;
+  const int n = h->n_inst;
+  CK(cudaMemcpyAsync(h->h_status, h->status, n * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h->h_iters, h->iters, n * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h->h_fin, h->fin_inf, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h->h_fin + n, h->fin_2, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  int rc = NMPC_OK;
+  for (int b = 0; b < n; ++b) {
+    if (stats) {
+      stats[b].status = h->h_status[b];
+      stats[b].iters = h->h_iters[b];
+      stats[b].res_inf = h->h_fin[b];
+      stats[b].res_2 = h->h_fin[n + b];
+    }
+    if (rc == NMPC_OK) {
+      if (h->h_status[b] == nmpc_dev::ST_DIVERGED) rc = NMPC_ERR_DIVERGED;
+      else if (h->h_status[b] != nmpc_dev::ST_CONVERGED) rc = NMPC_ERR_NOT_CONVERGED;
+    }
+  }
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+void nmpc_default_opts(nmpc_opts* o) {
+  if (!o) return;
+  o->tol = 1e-6;
+  o->max_iter = 2000;
+  o->n_lo = 2;
+  o->n_u_it = 2;
+  o->precision = NMPC_FP64;
+  o->check_every = 16;
+  o->alpha = 1.0;
+  o->div_limit = 1e8;
+  o->threads = 0;
+  o->use_graph = 1;
+}
+
+int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
+               nmpc_handle** out) {
+  if (!out || !descs || n_instances < 1 || n_instances > 65535) return NMPC_ERR_BAD_ARG;
+  *out = nullptr;
+  nmpc_opts o;
+  nmpc_default_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.tol >= 0) || o.max_iter < 0 || o.n_lo < 1 || o.n_u_it < 1 || o.check_every < 1 ||
+      !(o.alpha > 0 && o.alpha <= 1) || !(o.div_limit > 0) ||
+      (o.precision != NMPC_FP64 && o.precision != NMPC_MIXED) || o.threads < 0 ||
+      o.threads > 512 || (o.threads % 32) != 0)
+    return NMPC_ERR_BAD_ARG;
+  for (int b = 0; b < n_instances; ++b) {
+    int rc = validate(&descs[b]);
+    if (rc != NMPC_OK) return rc;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return NMPC_ERR_NO_DEVICE;
+
+  nmpc_handle* h = new (std::nothrow) nmpc_handle();
+  if (!h) return NMPC_ERR_CUDA;
+  h->n_inst = n_instances;
+  h->opts = o;
+  h->mixed = (o.precision == NMPC_MIXED);
+  cudaGetDevice(&h->device);
+  cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+
+  std::vector<int> act_all;
+  std::vector<int2> work;
+  for (int b = 0; b < n_instances; ++b) {
+    const nmpc_desc& d = descs[b];
+    InstDev I{};
+    I.dim = d.dim;
+    I.mx = d.mx;
+    I.my = d.my;
+    I.ng = d.mx * d.my;
+    I.N = d.horizon;
+    I.nu = d.n_u;
+    I.act_off = (int)act_all.size();
+    I.s_off = h->n_s;
+    I.u_off = h->n_u;
+    I.g_off = h->n_g;
+    I.h = d.h;
+    I.q = d.q;
+    I.r = d.r;
+    I.qf = d.qf;
+    I.gamma = d.gamma;
+    I.k0 = d.k0;
+    I.k1 = d.k1;
+    I.b0 = d.act_gain;
+    const double dx = 1.0 / (d.mx + 1), dy = 1.0 / (d.my + 1);
+    I.cx = 1.0 / (dx * dx);
+    I.cy = (d.dim == 2) ? 1.0 / (dy * dy) : 0.0;
+    for (int a = 0; a < d.n_u; ++a) act_all.push_back(d.act_cell[a]);
+    for (int s = 0; s < d.horizon; ++s) work.push_back(make_int2(b, s));
+    h->n_s += (long long)I.N * I.ng;
+    h->n_u += (long long)I.N * I.nu;
+    h->n_g += I.ng;
+    h->ng_max = std::max(h->ng_max, I.ng);
+    h->nu_max = std::max(h->nu_max, I.nu);
+    h->n_max_horizon = std::max(h->n_max_horizon, I.N);
+    h->inst_h.push_back(I);
+  }
+  h->n_work = (int)work.size();
+
+  // launch configuration
+  int threads = o.threads;
+  if (threads == 0) {
+    threads = ((h->ng_max / 8 + 31) / 32) * 32;
+    threads = std::min(512, std::max(64, threads));
+  }
+  h->threads = threads;
+  const size_t elem = h->mixed ? sizeof(float) : sizeof(double);
+  const size_t small = h->mixed ? small_shared_bytes<float>() : small_shared_bytes<double>();
+  const size_t work_bytes = (size_t)nmpc_dev::NUM_WORK_ARRAYS * h->ng_max * elem;
+  int max_optin = 0;
+  cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+  h->smem_mode = (small + work_bytes) <= (size_t)max_optin;
+  h->smem = h->smem_mode ? small + work_bytes : small;
+  cudaError_t ce = h->mixed ? configure_kernels<float>(h->smem) : configure_kernels<double>(h->smem);
+  if (ce != cudaSuccess) {
+    fprintf(stderr, "nmpc: kernel attribute: %s\n", cudaGetErrorString(ce));
+    delete h;
+    return NMPC_ERR_CUDA;
+  }
+  int per_sm = 1;
+  if (h->mixed)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, nmpc_dev::k_iterate<float, nmpc_dev::MODE_SOLVE>, threads, h->smem);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, nmpc_dev::k_iterate<double, nmpc_dev::MODE_SOLVE>, threads, h->smem);
+  per_sm = std::max(1, per_sm);
+  const int resident = per_sm * std::max(1, h->num_sms);
+  h->grid = h->smem_mode ? h->n_work : std::min(h->n_work, resident);
+
+  bool ok = true;
+  auto A = [&](cudaError_t e) { ok = ok && (e == cudaSuccess); };
+  A(dev_alloc(&h->inst_d, n_instances));
+  A(dev_alloc(&h->work_d, h->n_work));
+  A(dev_alloc(&h->act_d, act_all.size()));
+  A(dev_alloc(&h->x0_d, h->n_g));
+  A(dev_alloc(&h->ref_d, h->n_g));
+  A(dev_alloc(&h->uo_d, h->n_u));
+  A(dev_alloc(&h->w_d, 3 * (size_t)n_instances));
+  for (int q = 0; q < 3; ++q) {
+    A(dev_alloc(&h->xb[q], h->n_s));
+    A(dev_alloc(&h->lb[q], h->n_s));
+    A(dev_alloc(&h->ub[q], h->n_u));
+  }
+  A(dev_alloc(&h->ictl, 4));
+  A(dev_alloc(&h->res_inf, 3 * (size_t)n_instances));
+  A(dev_alloc(&h->res_sq, 3 * (size_t)n_instances));
+  A(dev_alloc(&h->res_first, n_instances));
+  A(dev_alloc(&h->status, n_instances));
+  A(dev_alloc(&h->iters, n_instances));
+  A(dev_alloc(&h->final_buf, n_instances));
+  A(dev_alloc(&h->fin_inf, n_instances));
+  A(dev_alloc(&h->fin_2, n_instances));
+  if (!h->smem_mode) {
+    h->scratch_stride = (long long)((work_bytes + 255) & ~size_t(255));
+    A(cudaMalloc((void**)&h->scratch, (size_t)h->scratch_stride * h->grid));
+  }
+  A(cudaMallocHost((void**)&h->h_active, sizeof(int)));
+  A(cudaMallocHost((void**)&h->h_status, n_instances * sizeof(int)));
+  A(cudaMallocHost((void**)&h->h_iters, n_instances * sizeof(int)));
+  A(cudaMallocHost((void**)&h->h_fin, 2 * n_instances * sizeof(double)));
+  A(cudaMallocHost((void**)&h->h_res, 2 * n_instances * sizeof(double)));
+  A(cudaMallocHost((void**)&h->h_resinf, n_instances * sizeof(unsigned long long)));
+  if (ok) {
+    A(cudaMemcpy(h->inst_d, h->inst_h.data(), n_instances * sizeof(InstDev), cudaMemcpyHostToDevice));
+    A(cudaMemcpy(h->work_d, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    A(cudaMemcpy(h->act_d, act_all.data(), act_all.size() * sizeof(int), cudaMemcpyHostToDevice));
+    A(cudaMemset(h->ictl, 0, 4 * sizeof(int)));
+    A(cudaDeviceSynchronize());
+  }
+  if (!ok) {
+    fprintf(stderr, "nmpc: setup allocation failed: %s\n", cudaGetErrorString(cudaGetLastError()));
+    free_all(h);
+    delete h;
+    return NMPC_ERR_CUDA;
+  }
+  *out = h;
+  return NMPC_OK;
+}
+
+int nmpc_solve(nmpc_handle* h, const double* x0, const double* ref, int horizon,
+               const double* weights, int init, double* u_out, nmpc_stats* stats,
+               void* stream) {
+  if (!h || !x0 || !ref) return NMPC_ERR_BAD_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(h->x0_d, x0, h->n_g * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(h->ref_d, ref, h->n_g * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return solve_core(h, horizon, weights, init, u_out, stats, st);
+}
+
+int nmpc_solve_host(nmpc_handle* h, const double* x0, const double* ref, int horizon,
+                    const double* weights, int init, double* u_out, nmpc_stats* stats,
+                    void* stream) {
+  if (!h || !x0 || !ref) return NMPC_ERR_BAD_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(h->x0_d, x0, h->n_g * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(h->ref_d, ref, h->n_g * sizeof(double), cudaMemcpyHostToDevice, st));
+  const double* wd = nullptr;
+  if (weights) {
+    CK(cudaMemcpyAsync(h->w_d, weights, 3 * h->n_inst * sizeof(double), cudaMemcpyHostToDevice, st));
+    wd = h->w_d;
+  }
+  int rc = solve_core(h, horizon, wd, init, h->uo_d, stats, st);
+  if (rc == NMPC_ERR_BAD_ARG || rc == NMPC_ERR_CUDA) return rc;
+  if (u_out) {
+    CK(cudaMemcpyAsync(u_out, h->uo_d, h->n_u * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  return rc;
+}
+
+static int oneshot(nmpc_handle* h, const double* xi, const double* ui, const double* li,
+                   double* xo, double* uo, double* lo, int resid_only, double* out_res,
+                   cudaStream_t st) {
+  IterArgs A = make_args(h);
+  A.xin[0] = xi;
+  A.uin[0] = ui;
+  A.lin[0] = li;
+  A.xout[1] = xo;
+  A.uout[1] = uo;
+  A.lout[1] = lo;
+  A.res_first = nullptr;
+  A.resid_only = resid_only;
+  if (out_res) {
+    CK(cudaMemsetAsync(h->res_inf, 0, h->n_inst * sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(h->res_sq, 0, h->n_inst * sizeof(double), st));
+  }
+  CK(launch_iterate<nmpc_dev::MODE_ONESHOT>(h, A, st));
+  if (out_res) {
+    CK(cudaMemcpyAsync(h->h_resinf, h->res_inf, h->n_inst * sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h->h_res, h->res_sq, h->n_inst * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int b = 0; b < h->n_inst; ++b) {
+      double r;
+      std::memcpy(&r, &h->h_resinf[b], sizeof(double));
+      out_res[2 * b] = r;
+      out_res[2 * b + 1] = std::sqrt(h->h_res[b]);
+    }
+  }
+  return NMPC_OK;
+}
+
+int nmpc_residual(nmpc_handle* h, const double* x0, const double* ref, const double* x,
+                  const double* u, const double* lam, double* out, void* stream) {
+  if (!h || !x0 || !ref || !x || !u || !lam || !out) return NMPC_ERR_BAD_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(h->x0_d, x0, h->n_g * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(h->ref_d, ref, h->n_g * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return oneshot(h, x, u, lam, nullptr, nullptr, nullptr, 1, out, st);
+}
+
+int nmpc_iterate(nmpc_handle* h, const double* x0, const double* ref, const double* x_in,
+                 const double* u_in, const double* lam_in, double* x_out, double* u_out,
+                 double* lam_out, int n_iter, double* out_res, void* stream) {
+  if (!h || !x0 || !ref || !x_in || !u_in || !lam_in || !x_out || !u_out || !lam_out ||
+      n_iter < 1)
+    return NMPC_ERR_BAD_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(h->x0_d, x0, h->n_g * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(h->ref_d, ref, h->n_g * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  // ping-pong through the handle's A/B buffers, then copy out (so in and out
+  // may alias)
+  const double* xi = x_in;
+  const double* ui = u_in;
+  const double* li = lam_in;
+  for (int it = 0; it < n_iter; ++it) {
+    const bool lastit = (it == n_iter - 1);
+    double* xo = h->xb[it & 1];
+    double* uo = h->ub[it & 1];
+    double* lo = h->lb[it & 1];
+    int rc = oneshot(h, xi, ui, li, xo, uo, lo, 0, lastit ? out_res : nullptr, st);
+    if (rc != NMPC_OK) return rc;
+    xi = xo;
+    ui = uo;
+    li = lo;
+  }
+  CK(cudaMemcpyAsync(x_out, xi, h->n_s * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(lam_out, li, h->n_s * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(u_out, ui, h->n_u * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return NMPC_OK;
+}
+
+int nmpc_get_state(nmpc_handle* h, double* x, double* u, double* lam, void* stream) {
+  if (!h) return NMPC_ERR_BAD_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (x) CK(cudaMemcpyAsync(x, h->xb[2], h->n_s * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (lam) CK(cudaMemcpyAsync(lam, h->lb[2], h->n_s * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (u) CK(cudaMemcpyAsync(u, h->ub[2], h->n_u * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return NMPC_OK;
+}
+
+int nmpc_set_state(nmpc_handle* h, const double* x, const double* u, const double* lam,
+                   void* stream) {
+  if (!h || !x || !u || !lam) return NMPC_ERR_BAD_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(h->xb[2], x, h->n_s * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(h->lb[2], lam, h->n_s * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(h->ub[2], u, h->n_u * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  h->has_state = true;
+  return NMPC_OK;
+}
+
+int nmpc_sizes(const nmpc_handle* h, int64_t* out) {
+  if (!h || !out) return NMPC_ERR_BAD_ARG;
+  out[0] = h->n_g;
+  out[1] = h->n_s;
+  out[2] = h->n_u;
+  return NMPC_OK;
+}
+
+int64_t nmpc_launch_count(const nmpc_handle* h) { return h ? h->launches : 0; }
+
+void nmpc_destroy(nmpc_handle* h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  free_all(h);
+  delete h;
+}
+
+const char* nmpc_strerror(int code) {
+  switch (code) {
+    case NMPC_OK: return "ok";
+    case NMPC_ERR_BAD_ARG: return "invalid argument";
+    case NMPC_ERR_CUDA: return "CUDA runtime error";
+    case NMPC_ERR_NOT_CONVERGED: return "not converged within max_iter";
+    case NMPC_ERR_DIVERGED: return "diverged (residual NaN/Inf or exploded)";
+    case NMPC_ERR_NO_DEVICE: return "no CUDA device";
+    case NMPC_ERR_UNSUPPORTED: return "size not supported";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,68 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+declared in include/nmpc.h (no compute calls; runs without a GPU)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "nmpc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(nmpc_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2004_02484_gb300 import build as b
+    return b.build()
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    declared = _declared()
+    assert len(declared) >= 10
+    lib = ctypes.CDLL(lib_path)
+    for name in declared:
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\b(nmpc_[a-z_]+)\b", out))
+    assert set(declared) <= exported
+
+
+def test_binding_covers_the_header(lib_path):
+    from paper_2004_02484_gb300 import nmpc as G
+    assert sorted(G.EXPORTED) == _declared()
+
+
+def test_strerror_and_defaults(lib_path):
+    from paper_2004_02484_gb300 import nmpc as G
+    o = G.nmpc_default_opts()
+    assert o.n_lo == 2 and o.n_u_it == 2 and o.tol == 1e-6 and o.precision == G.NMPC_FP64
+    assert G.LIB.nmpc_strerror(G.NMPC_ERR_DIVERGED).decode().startswith("diverged")
+
+
+def test_setup_rejects_bad_descriptors_before_touching_the_device(lib_path):
+    """Descriptor validation happens on the host before any CUDA call."""
+    from paper_2004_02484_gb300 import nmpc as G
+    from paper_2004_02484_gb300 import workloads as wl
+    bad = []
+    i = wl.heat1d_single(); i.horizon = 0; bad.append((i, G.NMPC_ERR_BAD_ARG))
+    i = wl.heat1d_single(); i.act = [0, 32]; bad.append((i, G.NMPC_ERR_BAD_ARG))
+    i = wl.heat1d_single(); i.my = 2; bad.append((i, G.NMPC_ERR_BAD_ARG))
+    i = wl.heat1d_single(); i.act = list(range(65)); bad.append((i, G.NMPC_ERR_UNSUPPORTED))
+    i = wl.heat1d_single(); i.r = 0.0; bad.append((i, G.NMPC_ERR_BAD_ARG))
+    for inst, code in bad:
+        descs, keep = G.make_descs([inst])
+        h = ctypes.c_void_p()
+        rc = G.LIB.nmpc_setup(descs, 1, None, ctypes.byref(h))
+        assert rc == code, (rc, code)
+    o = G.nmpc_default_opts()
+    o.n_lo = 0
+    descs, keep = G.make_descs([wl.heat1d_single()])
+    h = ctypes.c_void_p()
+    assert G.LIB.nmpc_setup(descs, 1, ctypes.byref(o), ctypes.byref(h)) == G.NMPC_ERR_BAD_ARG

@@ -1,0 +1,268 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances, derived from the arithmetic:
+* FP64 path, one or a few iterations from the same iterate: the kernel and
+  the oracle evaluate the same formulas in a different order (stencil sums,
+  fused multiply-adds), so results agree to a few ulps of the largest term;
+  relative 1e-11 on states (scaled by the field's max) leaves 100x margin.
+* MIXED path: the lower layer runs in float32 (unit roundoff 6e-8), so one
+  update Delta s carries a relative error of about 1e-6 after ~20 dependent
+  operations; the float64 master state then differs by <= 1e-5 * |Delta s|.
+* Solves to a tolerance: the FP64 path follows the oracle's iterate sequence
+  exactly, so the iteration count is equal and controls agree to 1e-9
+  relative; the MIXED path reaches the same root (the fixed point depends
+  only on the float64 residual) and its controls agree to 1e-3 relative at
+  ||K||_inf <= 1e-6 and to 1e-5 relative when both are driven to 1e-10.
+"""
+import numpy as np
+import pytest
+
+from oracle import nmpc as O
+from paper_2004_02484_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2004_02484_gb300 import build as b
+    b.build()
+    from paper_2004_02484_gb300 import nmpc as G
+    import torch
+    torch.cuda.set_device(0)
+    return G
+
+
+def _t(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def _rand_state(insts, seed, sx=0.05, su=0.5, sl=1e-4):
+    """A perturbed cold start per instance, packed (x, u, lam) + per-instance lists."""
+    rng = np.random.default_rng(seed)
+    Xs, Us, Ls = [], [], []
+    for inst in insts:
+        p = O.Problem(inst)
+        X, U, L = p.cold_start()
+        Xs.append(X + sx * rng.standard_normal(X.shape))
+        Us.append(U + su * rng.standard_normal(U.shape))
+        Ls.append(L + sl * rng.standard_normal(L.shape))
+    pk = lambda A: np.concatenate([a.reshape(-1) for a in A])
+    return (pk(Xs), pk(Us), pk(Ls)), (Xs, Us, Ls)
+
+
+def _unpack(G, insts, x, u, lam):
+    return (G.split_stages(insts, x, "ng"), G.split_stages(insts, u, "nu"),
+            G.split_stages(insts, lam, "ng"))
+
+
+def _iterate_gpu(G, insts, state, n_iter, **opts):
+    import torch
+    h = G.nmpc_setup(insts, **opts)
+    x0 = _t(G.pack_fields(insts, "x0"))
+    ref = _t(G.pack_fields(insts, "ref"))
+    xi, ui, li = (_t(a) for a in state)
+    xo, uo, lo = torch.empty_like(xi), torch.empty_like(ui), torch.empty_like(li)
+    res = G.nmpc_iterate(h, x0, ref, xi, ui, li, xo, uo, lo, n_iter, len(insts))
+    torch.cuda.synchronize()
+    G.nmpc_destroy(h)
+    return (xo.cpu().numpy(), uo.cpu().numpy(), lo.cpu().numpy()), res
+
+
+def _oracle_iterate(insts, lists, n_iter):
+    out = []
+    norms = []
+    for b, inst in enumerate(insts):
+        p = O.Problem(inst)
+        X, U, L = lists[0][b], lists[1][b], lists[2][b]
+        for _ in range(n_iter):
+            X, U, L, nm = O.jacobi_iteration(p, X, U, L)
+        out.append((X.reshape(p.N, -1), U, L.reshape(p.N, -1)))
+        norms.append(nm)
+    return out, norms
+
+
+def _cmp_iterates(G, insts, gpu, ora, rtol):
+    gx, gu, gl = _unpack(G, insts, *gpu)
+    for b in range(len(insts)):
+        X, U, L = ora[b]
+        for g, o in ((gx[b], X), (gl[b], L), (gu[b], U)):
+            scale = max(np.abs(o).max(), 1e-300)
+            err = np.abs(g - o).max() / scale
+            assert err <= rtol, (b, err)
+
+
+CASES = {
+    "heat1d_M32_N20": lambda: [wl.heat1d_single()],
+    "heat2d_16x12_N7": lambda: [wl.heat2d(16, 12, 7, 3, 2, seed=4)],
+    "heat2d_64x64_N50": lambda: [wl.heat2d_single()],
+    "ragged1d_x24": lambda: wl.heat1d_ragged_batch(24),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_one_iteration_fp64_matches_oracle(G, case):
+    insts = CASES[case]()
+    state, lists = _rand_state(insts, 1)
+    gpu, res = _iterate_gpu(G, insts, state, 1, precision=G.NMPC_FP64)
+    ora, norms = _oracle_iterate(insts, lists, 1)
+    _cmp_iterates(G, insts, gpu, ora, 1e-11)
+    for b in range(len(insts)):
+        assert abs(res[b, 0] - norms[b][0]) <= 1e-12 * norms[b][0]
+        assert abs(res[b, 1] - norms[b][1]) <= 1e-10 * norms[b][1]
+
+
+@pytest.mark.parametrize("case", ["heat1d_M32_N20", "heat2d_16x12_N7", "ragged1d_x24"])
+def test_several_iterations_fp64_match_oracle(G, case):
+    insts = CASES[case]()
+    state, lists = _rand_state(insts, 2)
+    gpu, _ = _iterate_gpu(G, insts, state, 12, precision=G.NMPC_FP64)
+    ora, _ = _oracle_iterate(insts, lists, 12)
+    _cmp_iterates(G, insts, gpu, ora, 1e-10)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_one_iteration_mixed_matches_oracle(G, case):
+    """Float32 lower layer: compare the update Delta s relative to its size."""
+    insts = CASES[case]()
+    state, lists = _rand_state(insts, 3)
+    gpu, res = _iterate_gpu(G, insts, state, 1, precision=G.NMPC_MIXED)
+    ora, norms = _oracle_iterate(insts, lists, 1)
+    gx, gu, gl = _unpack(G, insts, *gpu)
+    for b in range(len(insts)):
+        X, U, L = ora[b]
+        x_in, u_in, l_in = (lists[q][b].reshape(X.shape if q != 1 else U.shape) for q in range(3))
+        for g, o, i in ((gx[b], X, x_in), (gl[b], L, l_in), (gu[b], U, u_in)):
+            d_or = o - i
+            err = np.abs((g - i) - d_or).max() / max(np.abs(d_or).max(), 1e-300)
+            assert err <= 1e-4, (b, err)
+        # the residual norm is float64 in both modes
+        assert abs(res[b, 0] - norms[b][0]) <= 1e-12 * norms[b][0]
+
+
+def _solve_gpu(G, insts, **opts):
+    import torch
+    s = G.Solver(insts, **opts)
+    rc, stats = s.solve()
+    torch.cuda.synchronize()
+    u = s.u.cpu().numpy()
+    x, uu, lam = (t.cpu().numpy() for t in s.state())
+    st = [(stats[b].status, stats[b].iters, stats[b].res_inf) for b in range(len(insts))]
+    s.close()
+    return rc, st, u, (x, uu, lam)
+
+
+@pytest.mark.parametrize("case", ["heat1d_M32_N20", "heat2d_16x12_N7"])
+def test_solve_fp64_follows_the_oracle_iterates(G, case):
+    insts = CASES[case]()
+    rc, st, u, _ = _solve_gpu(G, insts, tol=1e-8, precision=G.NMPC_FP64)
+    assert rc == G.NMPC_OK
+    ug = G.split_stages(insts, u, "nu")
+    for b, inst in enumerate(insts):
+        p = O.Problem(inst)
+        (X, U, L), info = O.solve_jacobi(p, tol=1e-8)
+        assert st[b][0] == G.NMPC_STATUS_CONVERGED
+        assert st[b][1] == info["iters"]
+        assert abs(st[b][2] - info["res_inf"]) <= 1e-9 * info["res_inf"] + 1e-20
+        assert st[b][2] <= 1e-8
+        err = np.abs(ug[b] - U).max() / np.abs(U).max()
+        assert err <= 1e-9, err
+
+
+def test_solve_heat2d_64x64_fp64_and_mixed_reach_the_oracle_root(G):
+    """The 2D 64x64, N=50 workload: both paths reach ||K||_inf <= 1e-6 and
+    their controls match the oracle at the same tolerance; driven to 1e-10
+    the mixed path matches the oracle's tight root to 1e-5."""
+    insts = [wl.heat2d_single()]
+    p = O.Problem(insts[0])
+    (X6, U6, L6), info6 = O.solve_jacobi(p, tol=1e-6)
+    rc, st, u, _ = _solve_gpu(G, insts, tol=1e-6, precision=G.NMPC_FP64)
+    assert rc == G.NMPC_OK and st[0][1] == info6["iters"] and st[0][2] <= 1e-6
+    ug = u.reshape(p.N, -1)
+    assert np.abs(ug - U6).max() / np.abs(U6).max() <= 1e-9
+    rc, st, u, _ = _solve_gpu(G, insts, tol=1e-6, precision=G.NMPC_MIXED)
+    assert rc == G.NMPC_OK and st[0][2] <= 1e-6
+    ug = u.reshape(p.N, -1)
+    assert np.abs(ug - U6).max() / np.abs(U6).max() <= 1e-3
+    (Xt, Ut, Lt), infot = O.solve_jacobi(p, tol=1e-10)
+    rc, st, u, _ = _solve_gpu(G, insts, tol=1e-10, precision=G.NMPC_MIXED)
+    assert rc == G.NMPC_OK and st[0][2] <= 1e-10
+    ug = u.reshape(p.N, -1)
+    assert np.abs(ug - Ut).max() / np.abs(Ut).max() <= 1e-5
+
+
+def test_ragged_batch_solve_matches_each_instance_alone(G):
+    insts = wl.heat1d_ragged_batch(40)
+    rc, st, u, _ = _solve_gpu(G, insts, tol=1e-7, precision=G.NMPC_FP64)
+    assert rc == G.NMPC_OK
+    ug = G.split_stages(insts, u, "nu")
+    for b in (0, 7, 19, 39):
+        p = O.Problem(insts[b])
+        (X, U, L), info = O.solve_jacobi(p, tol=1e-7)
+        assert st[b][1] == info["iters"], (b, st[b], info["iters"])
+        assert np.abs(ug[b] - U).max() / np.abs(U).max() <= 1e-9
+        rc1, st1, u1, _ = _solve_gpu(G, [insts[b]], tol=1e-7, precision=G.NMPC_FP64)
+        assert st1[0][1] == st[b][1]
+        np.testing.assert_allclose(u1.reshape(ug[b].shape), ug[b], rtol=0, atol=1e-13 * np.abs(U).max())
+
+
+def test_edge_cases_single_stage_tiny_grid_repeated_actuator(G):
+    insts = [wl.heat1d(1, 1, 1, 0.01, seed=5),                       # M=1, N=1
+             wl.heat1d(3, 2, 2, 0.05, seed=6, act_pos=[0.5, 0.5]),    # repeated actuator cell
+             wl.heat2d(1, 5, 3, 1, 1, seed=7),                         # 2D with mx=1
+             wl.heat1d(256, 60, 4, 1e-3, seed=8)]                      # largest ragged member
+    state, lists = _rand_state(insts, 9)
+    gpu, res = _iterate_gpu(G, insts, state, 2, precision=G.NMPC_FP64)
+    ora, _ = _oracle_iterate(insts, lists, 2)
+    _cmp_iterates(G, insts, gpu, ora, 1e-11)
+
+
+def test_max_iter_and_divergence_are_reported_not_faulted(G):
+    import torch
+    insts = [wl.heat1d_single(), wl.heat1d_single()]
+    insts[1].x0 = insts[1].x0.copy()
+    insts[1].x0[3] = np.nan
+    s = G.Solver(insts, tol=1e-12, max_iter=5, precision=G.NMPC_FP64)
+    rc, stats = s.solve()
+    torch.cuda.synchronize()
+    assert rc in (G.NMPC_ERR_NOT_CONVERGED, G.NMPC_ERR_DIVERGED)
+    assert stats[0].status == G.NMPC_STATUS_MAX_ITER and stats[0].iters == 5
+    assert stats[1].status == G.NMPC_STATUS_DIVERGED
+    # the handle stays usable
+    s2 = G.Solver([wl.heat1d_single()], tol=1e-6)
+    rc2, st2 = s2.solve()
+    assert rc2 == G.NMPC_OK
+    s.close()
+    s2.close()
+
+
+def test_host_pointer_solve_equals_device_solve(G):
+    import torch
+    insts = [wl.heat2d(20, 20, 10, 2, 2, seed=12)]
+    s = G.Solver(insts, tol=1e-8, precision=G.NMPC_MIXED)
+    rc, st = s.solve()
+    ud = s.u.cpu().numpy()
+    uh = np.zeros_like(ud)
+    rc2, st2 = G.nmpc_solve_host(s.h, G.pack_fields(insts, "x0"), G.pack_fields(insts, "ref"),
+                                 uh, len(insts))
+    assert rc == rc2 == G.NMPC_OK and st[0].iters == st2[0].iters
+    np.testing.assert_array_equal(ud, uh)
+    # warm start from the solution converges at once
+    rc3, st3 = s.solve(init=G.NMPC_INIT_WARM)
+    assert rc3 == G.NMPC_OK and st3[0].iters == 0
+    s.close()
+
+
+def test_residual_entry_point_matches_oracle(G):
+    insts = [wl.heat2d(24, 16, 9, 2, 2, seed=13), wl.heat1d(50, 12, 3, 0.02, seed=14)]
+    state, lists = _rand_state(insts, 15)
+    h = G.nmpc_setup(insts)
+    out = G.nmpc_residual(h, _t(G.pack_fields(insts, "x0")), _t(G.pack_fields(insts, "ref")),
+                          *(_t(a) for a in state), len(insts))
+    G.nmpc_destroy(h)
+    for b, inst in enumerate(insts):
+        p = O.Problem(inst)
+        r = O.kkt_norms(*O.kkt(p, lists[0][b], lists[1][b], lists[2][b]))
+        assert abs(out[b, 0] - r[0]) <= 1e-12 * r[0]
+        assert abs(out[b, 1] - r[1]) <= 1e-10 * r[1]
