@@ -415,7 +415,11 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
   cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
   h->smem_mode = (small + work_bytes) <= (size_t)max_optin;
   h->smem = h->smem_mode ? small + work_bytes : small;
-  cudaError_t ce = h->mixed ? configure_kernels<float>(h->smem) : configure_kernels<double>(h->smem);
+  // the attribute is per kernel and process-wide: raise it to the device
+  // limit so that a later setup with smaller stages cannot lower it under a
+  // live handle's launch size
+  cudaError_t ce = h->mixed ? configure_kernels<float>((size_t)max_optin)
+                            : configure_kernels<double>((size_t)max_optin);
   if (ce != cudaSuccess) {
     fprintf(stderr, "nmpc: kernel attribute: %s\n", cudaGetErrorString(ce));
     delete h;
