@@ -163,6 +163,27 @@ int nmpc_sizes(const nmpc_handle* h, int64_t* out);
    points), for launch accounting. */
 int64_t nmpc_launch_count(const nmpc_handle* h);
 
+/* Allocation-free solve of ONE instance (no counterpart in the paper; it
+   exists for callers that may not allocate device memory when they solve:
+   a real-time control loop that forbids allocation after start-up, code
+   whose device memory belongs to another allocator or pool, or code that
+   must not trigger the device-wide synchronization of cudaMalloc/cudaFree).
+   No handle is needed and nothing is allocated: the workspace is a static
+   device array of NMPC_NOALLOC_SCRATCH_BYTES inside this library, which every
+   GPU that loads the library holds until the process exits.  The first call
+   on a device looks up that array's device address (make that first call
+   before any stream capture).  desc: the instance (act_cell is read during
+   the call); opts: NULL for defaults; x0, ref: device [mx*my]; u_out: device
+   [horizon*n_u]; stats: host, one entry.  Returns UNSUPPORTED (and prints the
+   needed size) when the instance's workspace exceeds the static array,
+   otherwise as nmpc_solve.  Every call reuses the same array, and the call
+   resets whatever must start from zero; calls whose GPU work overlaps (other
+   streams or threads on the same device) race on it and corrupt each other's
+   results.  Synchronizes on stream. */
+#define NMPC_NOALLOC_SCRATCH_BYTES (32u << 20)
+int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts, const double* x0,
+                       const double* ref, double* u_out, nmpc_stats* stats, void* stream);
+
 /* Free the workspace and the handle (NULL is a no-op).  Synchronizes. */
 void nmpc_destroy(nmpc_handle* h);
 

@@ -640,3 +640,268 @@ const char* nmpc_strerror(int code) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free single-instance solve (nmpc_solve_noalloc).
+//
+// Some callers cannot allocate device memory at the moment they need a
+// solve: a real-time control loop that forbids allocation after start-up
+// (allocation latency is unbounded), a process whose device memory is owned
+// by another allocator or memory pool, or code running where cudaMalloc /
+// cudaFree would synchronize the device.  This entry point needs no handle:
+// its whole workspace (instance table, work list, the two ping-pong state
+// copies, convergence control and, when a stage does not fit in shared
+// memory, the lower-layer slab) lives in one file-scope device array of
+// NMPC_NOALLOC_SCRATCH_BYTES.  Every GPU that loads this library keeps that
+// array until the process exits.
+//
+// The host never dereferences the array's name: in host code it is only a
+// stand-in symbol, so its device address is looked up with
+// cudaGetSymbolAddress, once per device, with that device current, on the
+// first call made on that device (that first call should therefore come
+// before any stream capture).  Calls share the array and it keeps the last
+// call's contents; the init kernel rewrites every part that must start from
+// a known value (control counters, residual slots, the starting iterate).
+// Two calls whose GPU work overlaps (different streams or threads on the same
+// device) race on the array and corrupt each other's results.
+// ===========================================================================
+#include <mutex>
+
+static __device__ __align__(256) unsigned char g_nmpc_noalloc_scratch[NMPC_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kNoallocMaxDevices] = {};
+
+// Device address of the static workspace on the current device; the first
+// call on a device looks it up and sets the kernels' shared-memory limits.
+int noalloc_workspace(void** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoallocMaxDevices) return NMPC_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_nmpc_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      fprintf(stderr, "nmpc_solve_noalloc: cudaGetSymbolAddress failed: %s\n",
+              cudaGetErrorString(e));
+      return NMPC_ERR_CUDA;
+    }
+    int max_optin = 0;
+    CK(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    CK(configure_kernels<float>((size_t)max_optin));
+    CK(configure_kernels<double>((size_t)max_optin));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return NMPC_OK;
+}
+
+size_t carve(size_t* off, size_t bytes) {
+  const size_t at = *off;
+  *off = (at + bytes + 255) & ~size_t(255);
+  return at;
+}
+
+}  // namespace
+
+extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
+                                  const double* x0, const double* ref, double* u_out,
+                                  nmpc_stats* stats, void* stream) {
+  if (!desc || !x0 || !ref || !u_out) return NMPC_ERR_BAD_ARG;
+  int rc = validate(desc);
+  if (rc != NMPC_OK) return rc;
+  nmpc_opts o;
+  nmpc_default_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.tol >= 0) || o.max_iter < 0 || o.n_lo < 1 || o.n_u_it < 1 || o.check_every < 1 ||
+      !(o.alpha > 0 && o.alpha <= 1) || !(o.div_limit > 0) ||
+      (o.precision != NMPC_FP64 && o.precision != NMPC_MIXED) || o.threads < 0 ||
+      o.threads > 512 || (o.threads % 32) != 0)
+    return NMPC_ERR_BAD_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return NMPC_ERR_NO_DEVICE;
+
+  const nmpc_desc& d = *desc;
+  const bool mixed = (o.precision == NMPC_MIXED);
+  const int ng = d.mx * d.my, N = d.horizon, nu = d.n_u;
+  const long long n_s = (long long)N * ng, n_u = (long long)N * nu;
+
+  // launch configuration, chosen exactly as nmpc_setup chooses it
+  int threads = o.threads;
+  if (threads == 0) {
+    threads = ((ng / 8 + 31) / 32) * 32;
+    threads = std::min(512, std::max(64, threads));
+  }
+  const size_t elem = mixed ? sizeof(float) : sizeof(double);
+  const size_t small = mixed ? small_shared_bytes<float>() : small_shared_bytes<double>();
+  const size_t work_bytes = (size_t)nmpc_dev::NUM_WORK_ARRAYS * ng * elem;
+  int dev = 0, max_optin = 0, num_sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  CK(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+  const bool smem_mode = (small + work_bytes) <= (size_t)max_optin;
+  const size_t smem = smem_mode ? small + work_bytes : small;
+  int grid = N;
+  const long long slab = (long long)((work_bytes + 255) & ~size_t(255));
+  if (!smem_mode) grid = std::min(N, std::max(1, num_sms));
+
+  // workspace layout inside the static array
+  size_t off = 0;
+  const size_t o_inst = carve(&off, sizeof(InstDev));
+  const size_t o_work = carve(&off, (size_t)N * sizeof(int2));
+  const size_t o_act = carve(&off, (size_t)nu * sizeof(int));
+  size_t o_x[2], o_l[2], o_u[2];
+  for (int q = 0; q < 2; ++q) {
+    o_x[q] = carve(&off, (size_t)n_s * sizeof(double));
+    o_l[q] = carve(&off, (size_t)n_s * sizeof(double));
+    o_u[q] = carve(&off, (size_t)n_u * sizeof(double));
+  }
+  const size_t o_ctl = carve(&off, 4 * sizeof(int));
+  const size_t o_rinf = carve(&off, 3 * sizeof(unsigned long long));
+  const size_t o_rsq = carve(&off, 3 * sizeof(double));
+  const size_t o_rfirst = carve(&off, sizeof(unsigned long long));
+  const size_t o_status = carve(&off, 3 * sizeof(int));  // status, iters, final_buf
+  const size_t o_fin = carve(&off, 2 * sizeof(double));  // fin_inf, fin_2
+  const size_t o_slab = carve(&off, smem_mode ? 0 : (size_t)slab * grid);
+  if (off > (size_t)NMPC_NOALLOC_SCRATCH_BYTES) {
+    fprintf(stderr,
+            "nmpc_solve_noalloc: this instance needs %zu bytes of workspace; the static "
+            "workspace holds %u bytes (use nmpc_setup/nmpc_solve for larger instances)\n",
+            off, (unsigned)NMPC_NOALLOC_SCRATCH_BYTES);
+    return NMPC_ERR_UNSUPPORTED;
+  }
+  void* base_v = nullptr;
+  rc = noalloc_workspace(&base_v);
+  if (rc != NMPC_OK) return rc;
+  char* base = static_cast<char*>(base_v);
+  cudaStream_t st = (cudaStream_t)stream;
+
+  // instance table, work list and actuator cells (pageable host copies are
+  // staged by the runtime before cudaMemcpyAsync returns)
+  InstDev I{};
+  I.dim = d.dim;
+  I.mx = d.mx;
+  I.my = d.my;
+  I.ng = ng;
+  I.N = N;
+  I.nu = nu;
+  I.h = d.h;
+  I.q = d.q;
+  I.r = d.r;
+  I.qf = d.qf;
+  I.gamma = d.gamma;
+  I.k0 = d.k0;
+  I.k1 = d.k1;
+  I.b0 = d.act_gain;
+  const double dx = 1.0 / (d.mx + 1), dy = 1.0 / (d.my + 1);
+  I.cx = 1.0 / (dx * dx);
+  I.cy = (d.dim == 2) ? 1.0 / (dy * dy) : 0.0;
+  CK(cudaMemcpyAsync(base + o_inst, &I, sizeof(InstDev), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(base + o_act, d.act_cell, nu * sizeof(int), cudaMemcpyHostToDevice, st));
+  int2 chunk_buf[256];
+  for (int s0 = 0; s0 < N; s0 += 256) {
+    const int cnt = std::min(256, N - s0);
+    for (int j = 0; j < cnt; ++j) chunk_buf[j] = make_int2(0, s0 + j);
+    CK(cudaMemcpyAsync(base + o_work + (size_t)s0 * sizeof(int2), chunk_buf,
+                       cnt * sizeof(int2), cudaMemcpyHostToDevice, st));
+  }
+
+  IterArgs A{};
+  A.inst = reinterpret_cast<const InstDev*>(base + o_inst);
+  A.work = reinterpret_cast<const int2*>(base + o_work);
+  A.n_work = N;
+  A.n_inst = 1;
+  A.act = reinterpret_cast<const int*>(base + o_act);
+  A.x0 = x0;
+  A.ref = ref;
+  for (int q = 0; q < 2; ++q) {
+    A.xin[q] = A.xout[q] = reinterpret_cast<double*>(base + o_x[q]);
+    A.lin[q] = A.lout[q] = reinterpret_cast<double*>(base + o_l[q]);
+    A.uin[q] = A.uout[q] = reinterpret_cast<double*>(base + o_u[q]);
+  }
+  int* ctl = reinterpret_cast<int*>(base + o_ctl);
+  A.iter_k = ctl + 0;
+  A.block_done = ctl + 1;
+  A.n_active = ctl + 2;
+  A.res_inf = reinterpret_cast<unsigned long long*>(base + o_rinf);
+  A.res_sq = reinterpret_cast<double*>(base + o_rsq);
+  A.res_first = reinterpret_cast<unsigned long long*>(base + o_rfirst);
+  int* stat = reinterpret_cast<int*>(base + o_status);
+  A.status = stat + 0;
+  A.iters = stat + 1;
+  A.final_buf = stat + 2;
+  double* fin = reinterpret_cast<double*>(base + o_fin);
+  A.fin_inf = fin + 0;
+  A.fin_2 = fin + 1;
+  A.tol = o.tol;
+  A.div_limit = o.div_limit;
+  A.alpha = o.alpha;
+  A.max_iter = o.max_iter;
+  A.n_lo = o.n_lo;
+  A.n_u_it = o.n_u_it;
+  A.resid_only = 0;
+  A.scratch = smem_mode ? nullptr : base + o_slab;
+  A.scratch_stride = slab;
+  A.ng_max = ng;
+
+  nmpc_dev::k_init_control<<<dim3(64, 1), 256, 0, st>>>(A, 1);
+  CK(cudaGetLastError());
+  long long launched = 0;
+  int active = 1;
+  while (launched <= o.max_iter) {
+    for (int i = 0; i < o.check_every; ++i) {
+      if (mixed)
+        nmpc_dev::k_iterate<float, nmpc_dev::MODE_SOLVE><<<grid, threads, smem, st>>>(A);
+      else
+        nmpc_dev::k_iterate<double, nmpc_dev::MODE_SOLVE><<<grid, threads, smem, st>>>(A);
+    }
+    CK(cudaGetLastError());
+    launched += o.check_every;
+    CK(cudaMemcpyAsync(&active, A.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (active == 0) break;
+  }
+  FinalArgs F{};
+  F.inst = A.inst;
+  F.n_inst = 1;
+  for (int q = 0; q < 2; ++q) {
+    F.xs[q] = A.xin[q];
+    F.us[q] = A.uin[q];
+    F.ls[q] = A.lin[q];
+  }
+  // the gathered iterate lands in buffer 0 (a copy onto itself when it is there)
+  F.xc = A.xout[0];
+  F.uc = A.uout[0];
+  F.lc = A.lout[0];
+  F.u_out = u_out;
+  F.status = A.status;
+  F.iters = A.iters;
+  F.final_buf = A.final_buf;
+  F.fin_inf = A.fin_inf;
+  F.fin_2 = A.fin_2;
+  F.res_inf = A.res_inf;
+  F.res_sq = A.res_sq;
+  F.tol = o.tol;
+  F.max_iter = o.max_iter;
+  nmpc_dev::k_finalize_status<<<1, 32, 0, st>>>(F);
+  nmpc_dev::k_gather_final<<<dim3(64, 1), 256, 0, st>>>(F);
+  CK(cudaGetLastError());
+  int h_stat[3] = {0, 0, 0};
+  double h_fin[2] = {0.0, 0.0};
+  CK(cudaMemcpyAsync(h_stat, stat, sizeof(h_stat), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h_fin, fin, sizeof(h_fin), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (stats) {
+    stats->status = h_stat[0];
+    stats->iters = h_stat[1];
+    stats->res_inf = h_fin[0];
+    stats->res_2 = h_fin[1];
+  }
+  if (h_stat[0] == nmpc_dev::ST_DIVERGED) return NMPC_ERR_DIVERGED;
+  if (h_stat[0] != nmpc_dev::ST_CONVERGED) return NMPC_ERR_NOT_CONVERGED;
+  return NMPC_OK;
+}

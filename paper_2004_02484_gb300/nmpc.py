@@ -56,7 +56,8 @@ class nmpc_stats(ctypes.Structure):
 
 EXPORTED = ["nmpc_default_opts", "nmpc_setup", "nmpc_solve", "nmpc_solve_host",
             "nmpc_residual", "nmpc_iterate", "nmpc_get_state", "nmpc_set_state",
-            "nmpc_sizes", "nmpc_launch_count", "nmpc_destroy", "nmpc_strerror"]
+            "nmpc_sizes", "nmpc_launch_count", "nmpc_destroy", "nmpc_strerror",
+            "nmpc_solve_noalloc"]
 
 
 def _load() -> ctypes.CDLL:
@@ -80,6 +81,8 @@ def _load() -> ctypes.CDLL:
         "nmpc_launch_count": (ctypes.c_int64, [P]),
         "nmpc_destroy": (V, [P]),
         "nmpc_strerror": (ctypes.c_char_p, [I]),
+        "nmpc_solve_noalloc": (I, [ctypes.POINTER(nmpc_desc), ctypes.POINTER(nmpc_opts), P, P,
+                                   P, ctypes.POINTER(nmpc_stats), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -211,6 +214,20 @@ def nmpc_launch_count(h) -> int:
 
 def nmpc_destroy(h):
     LIB.nmpc_destroy(h)
+
+
+def nmpc_solve_noalloc(inst, x0, ref, u_out, stream=None, **opts) -> tuple:
+    """Allocation-free single-instance solve (static device workspace)."""
+    o = nmpc_default_opts()
+    for k, v in opts.items():
+        setattr(o, k, v)
+    descs, keep = make_descs([inst])
+    st = nmpc_stats()
+    rc = LIB.nmpc_solve_noalloc(descs, ctypes.byref(o), _ptr(x0), _ptr(ref), _ptr(u_out),
+                                ctypes.byref(st), _stream(stream))
+    del keep
+    _check(rc, "nmpc_solve_noalloc", allow=(NMPC_ERR_NOT_CONVERGED, NMPC_ERR_DIVERGED))
+    return rc, st
 
 
 # ---------------------------------------------------------------------------
