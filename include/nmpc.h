@@ -89,6 +89,13 @@ typedef struct {
   double div_limit;/* residual above div_limit * ||K(S^0)||_inf => diverged   */
   int threads;     /* threads per CTA (multiple of 32, <= 512); 0 = auto      */
   int use_graph;   /* capture the iteration chunk in a CUDA graph (1) or not  */
+  int cluster;     /* CTAs per stage (1..8 or 16, a thread-block cluster that
+                      splits the stage grid); 0 = auto                        */
+  double split_min;/* NMPC_MIXED: iterations whose previous residual is above
+                      max(tol, split_min) evaluate K with float64 differences
+                      and float32 O(h) terms; from the first one below, every
+                      iteration uses the float64 residual (convergence is only
+                      ever declared on a float64 residual)                    */
 } nmpc_opts;
 
 typedef struct {
@@ -101,7 +108,8 @@ typedef struct {
 typedef struct nmpc_handle nmpc_handle;
 
 /* Fill *o with defaults: tol 1e-6, max_iter 2000, n_lo 2, n_u_it 2, FP64,
-   check_every 16, alpha 1, div_limit 1e8, threads auto, graph on. */
+   check_every 16, alpha 1, div_limit 1e8, threads auto, graph on, cluster
+   auto, split_min 1e-7. */
 void nmpc_default_opts(nmpc_opts* o);
 
 /* Validate the descriptors, build the device instance table and allocate the

@@ -55,6 +55,8 @@ struct nmpc_handle {
   int* final_buf = nullptr;
   double* fin_inf = nullptr;
   double* fin_2 = nullptr;
+  int* full_from = nullptr;
+  int* full0 = nullptr;
   char* scratch = nullptr;
   long long scratch_stride = 0;
   // pinned host mirrors
@@ -67,6 +69,8 @@ struct nmpc_handle {
   // launch configuration
   int threads = 0;
   int grid = 0;
+  int csize = 1;
+  int slab_max = 0;
   size_t smem = 0;
   bool smem_mode = true;
   bool mixed = false;
@@ -107,7 +111,7 @@ void free_all(nmpc_handle* h) {
                   h->xb[0], h->xb[1], h->xb[2], h->ub[0], h->ub[1], h->ub[2],
                   h->lb[0], h->lb[1], h->lb[2], h->ictl, h->res_inf, h->res_sq,
                   h->res_first, h->status, h->iters, h->final_buf, h->fin_inf,
-                  h->fin_2, h->scratch};
+                  h->fin_2, h->full_from, h->full0, h->scratch};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   void* hp[] = {h->h_active, h->h_status, h->h_iters, h->h_fin, h->h_res, h->h_resinf};
@@ -146,33 +150,130 @@ IterArgs make_args(nmpc_handle* h) {
   A.tol = h->opts.tol;
   A.div_limit = h->opts.div_limit;
   A.alpha = h->opts.alpha;
+  A.split_min = h->opts.split_min;
   A.max_iter = h->opts.max_iter;
   A.n_lo = h->opts.n_lo;
   A.n_u_it = h->opts.n_u_it;
   A.resid_only = 0;
+  A.full_from = h->full_from;
+  A.full0 = h->full0;
+  A.full_all = h->mixed ? 0 : 1;
+  A.csize = h->csize;
+  A.slab_max = h->slab_max;
   A.scratch = h->smem_mode ? nullptr : h->scratch;
   A.scratch_stride = h->scratch_stride;
-  A.ng_max = h->ng_max;
   return A;
+}
+
+// Launch shape of the iteration kernel: CTAs per stage (cluster size), slab
+// length, threads, dynamic shared memory, grid.
+struct LaunchPlan {
+  int threads = 0, csize = 1, slab_max = 0, grid = 0;
+  size_t smem = 0;
+  bool smem_mode = true;
+};
+
+int slab_cells(const InstDev& I, int C) {
+  const int unit = (I.dim == 2) ? I.mx : 1;
+  const int nun = (I.dim == 2) ? I.my : I.mx;
+  return ((nun + C - 1) / C) * unit;
+}
+
+template <typename T>
+size_t small_shared_bytes_t() {
+  return (sizeof(nmpc_dev::SmallShared<T>) + 15) & ~size_t(15);
+}
+
+// Cluster size: the smallest that fits a stage slab in shared memory, then
+// grown (up to 8) while the whole batch still fits in one wave of CTAs and
+// slabs keep at least 512 cells; cluster sizes above 8 are 16 only.  A stage
+// that does not fit even at 16 runs one CTA per stage on a global slab.
+LaunchPlan plan_launch(const InstDev* insts, int n_inst, int n_work, const nmpc_opts& o,
+                       bool mixed, int num_sms, int max_optin) {
+  LaunchPlan P;
+  const size_t elem = mixed ? sizeof(float) : sizeof(double);
+  const size_t small = mixed ? small_shared_bytes_t<float>() : small_shared_bytes_t<double>();
+  auto slab = [&](int C) {
+    int m = 0;
+    for (int b = 0; b < n_inst; ++b) m = std::max(m, slab_cells(insts[b], C));
+    return m;
+  };
+  auto bytes = [&](int C) { return small + (size_t)nmpc_dev::NUM_WORK_ARRAYS * slab(C) * elem; };
+  auto next_c = [](int C) { return C < 8 ? C + 1 : 16; };
+  int C = 1;
+  if (o.cluster > 0) {
+    C = o.cluster;
+  } else {
+    while (C < 16 && bytes(C) > (size_t)max_optin) C = next_c(C);
+    if (bytes(C) <= (size_t)max_optin) {
+      while (C < 8) {
+        const int C2 = C + 1;
+        if ((long long)n_work * C2 > num_sms || slab(C2) < 512) break;
+        C = C2;
+      }
+    }
+  }
+  P.smem_mode = bytes(C) <= (size_t)max_optin;
+  if (!P.smem_mode) C = 1;
+  P.csize = C;
+  P.slab_max = slab(C);
+  int threads = o.threads;
+  if (threads == 0) {
+    threads = ((P.slab_max / 8 + 31) / 32) * 32;
+    threads = std::min(512, std::max(64, threads));
+  }
+  P.threads = threads;
+  P.smem = P.smem_mode ? bytes(C) : small;
+  P.grid = n_work * C;
+  return P;
+}
+
+template <typename T, int MODE>
+cudaError_t launch_k(const LaunchPlan& P, const IterArgs& A, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)P.grid);
+  cfg.blockDim = dim3((unsigned)P.threads);
+  cfg.dynamicSmemBytes = P.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)P.csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, nmpc_dev::k_iterate<T, MODE>, A);
+}
+
+LaunchPlan plan_of(const nmpc_handle* h) {
+  LaunchPlan P;
+  P.threads = h->threads;
+  P.csize = h->csize;
+  P.slab_max = h->slab_max;
+  P.grid = h->grid;
+  P.smem = h->smem;
+  P.smem_mode = h->smem_mode;
+  return P;
 }
 
 template <int MODE>
 cudaError_t launch_iterate(nmpc_handle* h, const IterArgs& A, cudaStream_t st) {
   h->launches++;
-  if (h->mixed)
-    nmpc_dev::k_iterate<float, MODE><<<h->grid, h->threads, h->smem, st>>>(A);
-  else
-    nmpc_dev::k_iterate<double, MODE><<<h->grid, h->threads, h->smem, st>>>(A);
-  return cudaGetLastError();
+  const LaunchPlan P = plan_of(h);
+  return h->mixed ? launch_k<float, MODE>(P, A, st) : launch_k<double, MODE>(P, A, st);
 }
 
 template <typename T>
 cudaError_t configure_kernels(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(nmpc_dev::k_iterate<T, nmpc_dev::MODE_SOLVE>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(nmpc_dev::k_iterate<T, nmpc_dev::MODE_ONESHOT>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  void (*fns[2])(IterArgs) = {nmpc_dev::k_iterate<T, nmpc_dev::MODE_SOLVE>,
+                              nmpc_dev::k_iterate<T, nmpc_dev::MODE_ONESHOT>};
+  for (auto fn : fns) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 int validate(const nmpc_desc* d) {
@@ -334,6 +435,8 @@ void nmpc_default_opts(nmpc_opts* o) {
   o->div_limit = 1e8;
   o->threads = 0;
   o->use_graph = 1;
+  o->cluster = 0;
+  o->split_min = 1e-7;
 }
 
 int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
@@ -346,7 +449,8 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
   if (!(o.tol >= 0) || o.max_iter < 0 || o.n_lo < 1 || o.n_u_it < 1 || o.check_every < 1 ||
       !(o.alpha > 0 && o.alpha <= 1) || !(o.div_limit > 0) ||
       (o.precision != NMPC_FP64 && o.precision != NMPC_MIXED) || o.threads < 0 ||
-      o.threads > 512 || (o.threads % 32) != 0)
+      o.threads > 512 || (o.threads % 32) != 0 || o.cluster < 0 || o.cluster > 16 ||
+      (o.cluster > 8 && o.cluster != 16) || !(o.split_min >= 0))
     return NMPC_ERR_BAD_ARG;
   for (int b = 0; b < n_instances; ++b) {
     int rc = validate(&descs[b]);
@@ -402,22 +506,8 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
   h->n_work = (int)work.size();
 
   // launch configuration
-  int threads = o.threads;
-  if (threads == 0) {
-    threads = ((h->ng_max / 8 + 31) / 32) * 32;
-    threads = std::min(512, std::max(64, threads));
-  }
-  h->threads = threads;
-  const size_t elem = h->mixed ? sizeof(float) : sizeof(double);
-  const size_t small = h->mixed ? small_shared_bytes<float>() : small_shared_bytes<double>();
-  const size_t work_bytes = (size_t)nmpc_dev::NUM_WORK_ARRAYS * h->ng_max * elem;
   int max_optin = 0;
   cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-  h->smem_mode = (small + work_bytes) <= (size_t)max_optin;
-  h->smem = h->smem_mode ? small + work_bytes : small;
-  // the attribute is per kernel and process-wide: raise it to the device
-  // limit so that a later setup with smaller stages cannot lower it under a
-  // live handle's launch size
   cudaError_t ce = h->mixed ? configure_kernels<float>((size_t)max_optin)
                             : configure_kernels<double>((size_t)max_optin);
   if (ce != cudaSuccess) {
@@ -425,16 +515,26 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
     delete h;
     return NMPC_ERR_CUDA;
   }
-  int per_sm = 1;
-  if (h->mixed)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, nmpc_dev::k_iterate<float, nmpc_dev::MODE_SOLVE>, threads, h->smem);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, nmpc_dev::k_iterate<double, nmpc_dev::MODE_SOLVE>, threads, h->smem);
-  per_sm = std::max(1, per_sm);
-  const int resident = per_sm * std::max(1, h->num_sms);
-  h->grid = h->smem_mode ? h->n_work : std::min(h->n_work, resident);
+  LaunchPlan P = plan_launch(h->inst_h.data(), n_instances, h->n_work, o, h->mixed,
+                             std::max(1, h->num_sms), max_optin);
+  if (!P.smem_mode) {
+    int per_sm = 1;
+    if (h->mixed)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &per_sm, nmpc_dev::k_iterate<float, nmpc_dev::MODE_SOLVE>, P.threads, P.smem);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &per_sm, nmpc_dev::k_iterate<double, nmpc_dev::MODE_SOLVE>, P.threads, P.smem);
+    P.grid = std::min(h->n_work, std::max(1, per_sm) * std::max(1, h->num_sms));
+  }
+  h->threads = P.threads;
+  h->csize = P.csize;
+  h->slab_max = P.slab_max;
+  h->smem = P.smem;
+  h->smem_mode = P.smem_mode;
+  h->grid = P.grid;
+  const size_t elem = h->mixed ? sizeof(float) : sizeof(double);
+  const size_t work_bytes = (size_t)nmpc_dev::NUM_WORK_ARRAYS * h->slab_max * elem;
 
   bool ok = true;
   auto A = [&](cudaError_t e) { ok = ok && (e == cudaSuccess); };
@@ -451,8 +551,10 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
     A(dev_alloc(&h->ub[q], h->n_u));
   }
   A(dev_alloc(&h->ictl, 4));
-  A(dev_alloc(&h->res_inf, 3 * (size_t)n_instances));
-  A(dev_alloc(&h->res_sq, 3 * (size_t)n_instances));
+  A(dev_alloc(&h->res_inf, (size_t)nmpc_dev::RES_SLOTS * n_instances));
+  A(dev_alloc(&h->res_sq, (size_t)nmpc_dev::RES_SLOTS * n_instances));
+  A(dev_alloc(&h->full_from, n_instances));
+  A(dev_alloc(&h->full0, n_instances));
   A(dev_alloc(&h->res_first, n_instances));
   A(dev_alloc(&h->status, n_instances));
   A(dev_alloc(&h->iters, n_instances));
@@ -720,7 +822,8 @@ extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
   if (!(o.tol >= 0) || o.max_iter < 0 || o.n_lo < 1 || o.n_u_it < 1 || o.check_every < 1 ||
       !(o.alpha > 0 && o.alpha <= 1) || !(o.div_limit > 0) ||
       (o.precision != NMPC_FP64 && o.precision != NMPC_MIXED) || o.threads < 0 ||
-      o.threads > 512 || (o.threads % 32) != 0)
+      o.threads > 512 || (o.threads % 32) != 0 || o.cluster < 0 || o.cluster > 16 ||
+      (o.cluster > 8 && o.cluster != 16) || !(o.split_min >= 0))
     return NMPC_ERR_BAD_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return NMPC_ERR_NO_DEVICE;
@@ -731,57 +834,10 @@ extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
   const long long n_s = (long long)N * ng, n_u = (long long)N * nu;
 
   // launch configuration, chosen exactly as nmpc_setup chooses it
-  int threads = o.threads;
-  if (threads == 0) {
-    threads = ((ng / 8 + 31) / 32) * 32;
-    threads = std::min(512, std::max(64, threads));
-  }
-  const size_t elem = mixed ? sizeof(float) : sizeof(double);
-  const size_t small = mixed ? small_shared_bytes<float>() : small_shared_bytes<double>();
-  const size_t work_bytes = (size_t)nmpc_dev::NUM_WORK_ARRAYS * ng * elem;
   int dev = 0, max_optin = 0, num_sms = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   CK(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
-  const bool smem_mode = (small + work_bytes) <= (size_t)max_optin;
-  const size_t smem = smem_mode ? small + work_bytes : small;
-  int grid = N;
-  const long long slab = (long long)((work_bytes + 255) & ~size_t(255));
-  if (!smem_mode) grid = std::min(N, std::max(1, num_sms));
-
-  // workspace layout inside the static array
-  size_t off = 0;
-  const size_t o_inst = carve(&off, sizeof(InstDev));
-  const size_t o_work = carve(&off, (size_t)N * sizeof(int2));
-  const size_t o_act = carve(&off, (size_t)nu * sizeof(int));
-  size_t o_x[2], o_l[2], o_u[2];
-  for (int q = 0; q < 2; ++q) {
-    o_x[q] = carve(&off, (size_t)n_s * sizeof(double));
-    o_l[q] = carve(&off, (size_t)n_s * sizeof(double));
-    o_u[q] = carve(&off, (size_t)n_u * sizeof(double));
-  }
-  const size_t o_ctl = carve(&off, 4 * sizeof(int));
-  const size_t o_rinf = carve(&off, 3 * sizeof(unsigned long long));
-  const size_t o_rsq = carve(&off, 3 * sizeof(double));
-  const size_t o_rfirst = carve(&off, sizeof(unsigned long long));
-  const size_t o_status = carve(&off, 3 * sizeof(int));  // status, iters, final_buf
-  const size_t o_fin = carve(&off, 2 * sizeof(double));  // fin_inf, fin_2
-  const size_t o_slab = carve(&off, smem_mode ? 0 : (size_t)slab * grid);
-  if (off > (size_t)NMPC_NOALLOC_SCRATCH_BYTES) {
-    fprintf(stderr,
-            "nmpc_solve_noalloc: this instance needs %zu bytes of workspace; the static "
-            "workspace holds %u bytes (use nmpc_setup/nmpc_solve for larger instances)\n",
-            off, (unsigned)NMPC_NOALLOC_SCRATCH_BYTES);
-    return NMPC_ERR_UNSUPPORTED;
-  }
-  void* base_v = nullptr;
-  rc = noalloc_workspace(&base_v);
-  if (rc != NMPC_OK) return rc;
-  char* base = static_cast<char*>(base_v);
-  cudaStream_t st = (cudaStream_t)stream;
-
-  // instance table, work list and actuator cells (pageable host copies are
-  // staged by the runtime before cudaMemcpyAsync returns)
   InstDev I{};
   I.dim = d.dim;
   I.mx = d.mx;
@@ -800,6 +856,47 @@ extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
   const double dx = 1.0 / (d.mx + 1), dy = 1.0 / (d.my + 1);
   I.cx = 1.0 / (dx * dx);
   I.cy = (d.dim == 2) ? 1.0 / (dy * dy) : 0.0;
+  LaunchPlan P = plan_launch(&I, 1, N, o, mixed, std::max(1, num_sms), max_optin);
+  const bool smem_mode = P.smem_mode;
+  if (!smem_mode) P.grid = std::min(N, std::max(1, num_sms));
+  const size_t elem = mixed ? sizeof(float) : sizeof(double);
+  const long long slab =
+      (long long)(((size_t)nmpc_dev::NUM_WORK_ARRAYS * P.slab_max * elem + 255) & ~size_t(255));
+
+  // workspace layout inside the static array
+  size_t off = 0;
+  const size_t o_inst = carve(&off, sizeof(InstDev));
+  const size_t o_work = carve(&off, (size_t)N * sizeof(int2));
+  const size_t o_act = carve(&off, (size_t)nu * sizeof(int));
+  size_t o_x[2], o_l[2], o_u[2];
+  for (int q = 0; q < 2; ++q) {
+    o_x[q] = carve(&off, (size_t)n_s * sizeof(double));
+    o_l[q] = carve(&off, (size_t)n_s * sizeof(double));
+    o_u[q] = carve(&off, (size_t)n_u * sizeof(double));
+  }
+  const size_t o_ctl = carve(&off, 4 * sizeof(int));
+  const size_t o_rinf = carve(&off, nmpc_dev::RES_SLOTS * sizeof(unsigned long long));
+  const size_t o_rsq = carve(&off, nmpc_dev::RES_SLOTS * sizeof(double));
+  const size_t o_ffrom = carve(&off, 2 * sizeof(int));  // full_from, full0
+  const size_t o_rfirst = carve(&off, sizeof(unsigned long long));
+  const size_t o_status = carve(&off, 3 * sizeof(int));  // status, iters, final_buf
+  const size_t o_fin = carve(&off, 2 * sizeof(double));  // fin_inf, fin_2
+  const size_t o_slab = carve(&off, smem_mode ? 0 : (size_t)slab * P.grid);
+  if (off > (size_t)NMPC_NOALLOC_SCRATCH_BYTES) {
+    fprintf(stderr,
+            "nmpc_solve_noalloc: this instance needs %zu bytes of workspace; the static "
+            "workspace holds %u bytes (use nmpc_setup/nmpc_solve for larger instances)\n",
+            off, (unsigned)NMPC_NOALLOC_SCRATCH_BYTES);
+    return NMPC_ERR_UNSUPPORTED;
+  }
+  void* base_v = nullptr;
+  rc = noalloc_workspace(&base_v);
+  if (rc != NMPC_OK) return rc;
+  char* base = static_cast<char*>(base_v);
+  cudaStream_t st = (cudaStream_t)stream;
+
+  // instance table, work list and actuator cells (pageable host copies are
+  // staged by the runtime before cudaMemcpyAsync returns)
   CK(cudaMemcpyAsync(base + o_inst, &I, sizeof(InstDev), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(base + o_act, d.act_cell, nu * sizeof(int), cudaMemcpyHostToDevice, st));
   int2 chunk_buf[256];
@@ -840,13 +937,18 @@ extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
   A.tol = o.tol;
   A.div_limit = o.div_limit;
   A.alpha = o.alpha;
+  A.split_min = o.split_min;
   A.max_iter = o.max_iter;
   A.n_lo = o.n_lo;
   A.n_u_it = o.n_u_it;
   A.resid_only = 0;
+  A.full_from = reinterpret_cast<int*>(base + o_ffrom);
+  A.full0 = A.full_from + 1;
+  A.full_all = mixed ? 0 : 1;
+  A.csize = P.csize;
+  A.slab_max = P.slab_max;
   A.scratch = smem_mode ? nullptr : base + o_slab;
   A.scratch_stride = slab;
-  A.ng_max = ng;
 
   nmpc_dev::k_init_control<<<dim3(64, 1), 256, 0, st>>>(A, 1);
   CK(cudaGetLastError());
@@ -855,11 +957,10 @@ extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
   while (launched <= o.max_iter) {
     for (int i = 0; i < o.check_every; ++i) {
       if (mixed)
-        nmpc_dev::k_iterate<float, nmpc_dev::MODE_SOLVE><<<grid, threads, smem, st>>>(A);
+        CK((launch_k<float, nmpc_dev::MODE_SOLVE>(P, A, st)));
       else
-        nmpc_dev::k_iterate<double, nmpc_dev::MODE_SOLVE><<<grid, threads, smem, st>>>(A);
+        CK((launch_k<double, nmpc_dev::MODE_SOLVE>(P, A, st)));
     }
-    CK(cudaGetLastError());
     launched += o.check_every;
     CK(cudaMemcpyAsync(&active, A.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));

@@ -1,26 +1,39 @@
 // Device code of the double-layer Jacobi NMPC solver (sm_103a).
 //
-// One CTA processes one (instance, stage) work item of one upper-layer
-// iteration (eq. 15): every stage of every instance is updated at once from
-// iterate k, so the whole grid is one iteration.  Inside a work item:
-//   phase A (float64): the stage's KKT rows K_i (eq. 9) from x_{i-1}, s_i,
-//     lambda_{i+1}; the coefficient fields Phi'(x) and A_xx of the reordered
-//     stage block (eq. 21); the residual norms (max |K|, sum K^2);
-//   phase B (T = float or double): the lower layer (Sec. 4.3, eqs. 22-24 and
-//     the u fixed-point iteration of Sec. 5.2) by pointwise Jacobi sweeps over
-//     the stage grid held in shared memory (or a global scratch slab when the
-//     stage does not fit);
-//   phase C (float64): S_i <- S_i - alpha Delta s_i into the other buffer.
-// Convergence bookkeeping (per-instance status, iteration counter, norms) is
-// kept on the device so that a chunk of iterations can be replayed as a CUDA
-// graph without host involvement.
+// One thread-block cluster of C CTAs processes one (instance, stage) work
+// item of one upper-layer iteration (eq. 15); every stage of every instance
+// is updated at once from iterate k, so one launch is one iteration.  The
+// stage grid is split into C slabs (rows in 2D, segments in 1D); stencil
+// neighbours in another CTA's slab are read from its shared memory through
+// the cluster's distributed shared memory.  Inside a work item:
+//   P1/P2 residual: the stage's KKT rows K_i (eq. 9) from x_{i-1}, s_i,
+//     lambda_{i+1}, the coefficient fields Phi'(x), A_xx and 1/diag(F_x) of
+//     the reordered stage block (eq. 21), and the residual norms.  Two forms:
+//       full  - everything in float64 (the certifying residual);
+//       split - the O(1) differences x_{i-1} - x_i and lambda_{i+1} -
+//               lambda_i in float64, the O(h) stencil terms in float32.
+//   P3 lower layer (T = float or double): Sec. 4.3 (eqs. 22-24) with the u
+//     fixed-point iteration of Sec. 5.2, by pointwise Jacobi sweeps over the
+//     slab; the first sweep from zero is D^{-1} c and is folded into the
+//     second sweep's neighbour reads.
+//   P4 update: S_i <- S_i - alpha Delta s_i in float64 into the other buffer.
+// Convergence bookkeeping (per-instance status, residual history, the switch
+// from split to full residuals, the iteration counter) stays on the device so
+// that chunks of iterations replay as a CUDA graph with no host arguments.
 #pragma once
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math_constants.h>
 #include <stdint.h>
 
 namespace nmpc_dev {
+
+namespace cg = cooperative_groups;
+
+constexpr int RES_SLOTS = 16;    // rolling residual history per instance
+constexpr int NUM_WORK_ARRAYS = 11;
+constexpr int MAX_NU = 64;
 
 struct InstDev {
   int dim, mx, my, ng;
@@ -33,7 +46,6 @@ struct InstDev {
 
 enum { MODE_SOLVE = 0, MODE_ONESHOT = 1 };
 enum { ST_RUNNING = 0, ST_CONVERGED = 1, ST_DIVERGED = 2, ST_MAX_ITER = 3 };
-enum { NUM_WORK_ARRAYS = 8 };
 
 struct IterArgs {
   const InstDev* inst;
@@ -54,53 +66,121 @@ struct IterArgs {
   // control (solve mode)
   int* iter_k;
   int* block_done;
-  unsigned long long* res_inf;  // [3][n_inst] bit patterns of non-negative doubles
-  double* res_sq;               // [3][n_inst]
-  unsigned long long* res_first;// [n_inst] ||K(S^0)||_inf
+  unsigned long long* res_inf;   // [RES_SLOTS][n_inst], bits of non-negative doubles
+  double* res_sq;                // [RES_SLOTS][n_inst]
+  unsigned long long* res_first; // [n_inst] ||K(S^0)||_inf
   int* status;
   int* iters;
   int* final_buf;
   double* fin_inf;
   double* fin_2;
+  int* full_from;  // [n_inst] first iteration evaluated with the float64 residual
+  int* full0;      // [n_inst] 1: iteration 0 also uses it (warm starts)
   int* n_active;
   double tol, div_limit, alpha;
+  double split_min;  // below max(tol, split_min) iterations use the float64 residual
   int max_iter, n_lo, n_u_it;
-  int resid_only;  // one-shot: residual norms only
+  int resid_only;  // one-shot: residual norms only (float64)
+  int full_all;    // every residual in float64 (FP64 precision)
+  int csize;       // CTAs per work item (cluster size)
+  int slab_max;    // cells per CTA slab (length of each shared work array)
   // lower-layer work arrays: shared memory (scratch == nullptr) or a global
   // slab of scratch_stride bytes per CTA
   char* scratch;
   long long scratch_stride;
-  int ng_max;
 };
 
-__device__ __forceinline__ double phi_k(double w, double k0, double k1) {
+struct Cl {
+  int C, rank;
+  __device__ __forceinline__ void sync() const {
+    if (C > 1) cg::this_cluster().sync();
+    else __syncthreads();
+  }
+  template <typename T>
+  __device__ __forceinline__ const T* map(const T* p, int r) const {
+    return cg::this_cluster().map_shared_rank(const_cast<T*>(p), r);
+  }
+};
+
+// Cells [lo, hi) of the instance grid owned by cluster rank `rank`; slabs are
+// whole rows in 2D and segments in 1D, per_cells cells per rank.
+struct Slab {
+  int lo, hi, per_cells;
+};
+
+__device__ __forceinline__ Slab slab_of(const InstDev& I, int C, int rank) {
+  const int unit = (I.dim == 2) ? I.mx : 1;
+  const int nun = (I.dim == 2) ? I.my : I.mx;
+  const int per = (nun + C - 1) / C;
+  Slab s;
+  s.per_cells = per * unit;
+  s.lo = min(rank * per, nun) * unit;
+  s.hi = min(rank * per + per, nun) * unit;
+  return s;
+}
+
+// Value of slab array `a` at grid cell m, local or in another rank's slab.
+template <typename T>
+__device__ __forceinline__ T ldn(const T* a, int m, const Slab& sl, const Cl& cl) {
+  if (m >= sl.lo && m < sl.hi) return a[m - sl.lo];
+  const int r = m / sl.per_cells;
+  return cl.map(a, r)[m - r * sl.per_cells];
+}
+
+__device__ __forceinline__ double phi_d(double w, double k0, double k1) {
   return k0 * (w + 0.5 * k1 * w * w);
 }
 
-__device__ __forceinline__ double sanitize_abs(double v) {
-  double a = fabs(v);
+__device__ __forceinline__ double abs_or_inf(double v) {
+  const double a = fabs(v);
   return (a <= 1.79e308) ? a : CUDART_INF;  // NaN and Inf count as +Inf
 }
 
-// Sum of the four (or two) stencil neighbours, each weighted by its axis
+__device__ __forceinline__ float abs_or_inf_f(float v) {
+  const float a = fabsf(v);
+  return (a <= 3.4e38f) ? a : CUDART_INF_F;
+}
+
+// float64 <-> float32 by IEEE-754 bit manipulation on the integer ALUs (the
+// float64 pipe issues 2 lanes per clock per SM on this part).  d2f truncates
+// toward zero (relative error < 2^-23); zero/subnormal doubles become +-0 and
+// out-of-range or NaN doubles become +-Inf.  f2d is exact for normal floats;
+// subnormal floats become +-0.
+__device__ __forceinline__ float d2f(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d);
+  const unsigned lo = (unsigned)__double2loint(d);
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 896;  // rebias 1023 -> 127
+  const unsigned man = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  unsigned bits = sign | ((unsigned)e << 23) | man;
+  bits = (e <= 0) ? sign : bits;
+  bits = (e >= 255) ? (sign | 0x7f800000u) : bits;
+  return __uint_as_float(bits);
+}
+
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned sign = b & 0x80000000u;
+  const unsigned e = (b >> 23) & 0xffu;
+  const unsigned man = b & 0x7fffffu;
+  unsigned hi = sign | ((e + 896u) << 20) | (man >> 3);
+  unsigned lo = man << 29;
+  hi = (e == 0u) ? sign : hi;
+  lo = (e == 0u) ? 0u : lo;
+  hi = (e == 255u) ? (sign | 0x7ff00000u | (man >> 3)) : hi;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// Sum of the stencil neighbours' values, each weighted by its axis
 // coefficient; cells outside the interior grid are zero (Dirichlet ring).
-template <typename V, typename Getter>
-__device__ __forceinline__ V nbr_sum(int c, int ix, int iy, int mx, int my, V cx, V cy,
-                                     Getter g) {
+template <typename V, typename G>
+__device__ __forceinline__ V nbr_sum(int c, int ix, int iy, int mx, int my, V cx, V cy, G g) {
   V sx = V(0), sy = V(0);
   if (ix > 0) sx += g(c - 1);
   if (ix < mx - 1) sx += g(c + 1);
   if (iy > 0) sy += g(c - mx);
   if (iy < my - 1) sy += g(c + mx);
   return cx * sx + cy * sy;
-}
-
-template <typename T>
-__device__ __forceinline__ T act_sum(int c, int nu, const int* act_s, const T* v) {
-  T s = T(0);
-  for (int a = 0; a < nu; ++a)
-    if (act_s[a] == c) s += v[a];
-  return s;
 }
 
 struct BlockRed {
@@ -114,7 +194,7 @@ __device__ __forceinline__ void block_reduce_store(double vmax, double vsq, Bloc
     vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
     vsq += __shfl_xor_sync(0xffffffffu, vsq, o);
   }
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
     red->mx[wid] = vmax;
     red->sq[wid] = vsq;
@@ -122,7 +202,7 @@ __device__ __forceinline__ void block_reduce_store(double vmax, double vsq, Bloc
   __syncthreads();
   if (threadIdx.x == 0) {
     double m = 0.0, s = 0.0;
-    int nw = (blockDim.x + 31) >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
     for (int w = 0; w < nw; ++w) {
       m = fmax(m, red->mx[w]);
       s += red->sq[w];
@@ -132,24 +212,29 @@ __device__ __forceinline__ void block_reduce_store(double vmax, double vsq, Bloc
   }
 }
 
-// Shared-memory layout of one work item: small per-stage arrays first, then
-// (in shared-memory mode) the NUM_WORK_ARRAYS work arrays of ng_max T each.
+// Per-work-item shared scalars (the NUM_WORK_ARRAYS slab arrays follow).
 template <typename T>
 struct SmallShared {
   BlockRed red;
   double red_out[2];
-  double u[64];
-  T b3[64];
-  T v3[64];
-  int act[64];
+  double u[MAX_NU];
+  T b3[MAX_NU];
+  T v3[MAX_NU];
+  T b1a[MAX_NU];  // state-equation row K1 at each actuator cell (owner rank only)
+  int act[MAX_NU];
   int skip;
+  int full;
 };
 
+__device__ __forceinline__ double to_double(float v) { return f2d(v); }
+__device__ __forceinline__ double to_double(double v) { return v; }
+
 template <typename T>
-__device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, bool resid_only,
-                             SmallShared<T>& sm, T* wk) {
+__device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, bool full,
+                             bool resid_only, SmallShared<T>& sm, T* wk, const Cl& cl) {
   const InstDev I = A.inst[b];
-  const int ng = I.ng, mx = I.mx, my = I.my, nu = I.nu, N = I.N;
+  const Slab sl = slab_of(I, cl.C, cl.rank);
+  const int mx = I.mx, my = I.my, nu = I.nu, N = I.N, ng = I.ng;
   const long long so = I.s_off + (long long)s * ng;
   const double* __restrict__ X = A.xin[rd];
   const double* __restrict__ L = A.lin[rd];
@@ -159,146 +244,242 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
   const double h = I.h, cx = I.cx, cy = I.cy, k0 = I.k0, k1 = I.k1, b0 = I.b0;
   const double dcoef = 2.0 * (cx + cy);
   const bool last = (s == N - 1);
+  const int SM = A.slab_max;
 
-  T* b1 = wk;
-  T* b2 = wk + ng;
-  T* dp = wk + 2 * ng;
-  T* ax = wk + 3 * ng;
-  T* va = wk + 4 * ng;
-  T* vb = wk + 5 * ng;
-  T* wa = wk + 6 * ng;
-  T* wb = wk + 7 * ng;
+  T* b2 = wk;               // costate row K3
+  T* dp = wk + 1 * SM;      // Phi'(x)
+  T* ax = wk + 2 * SM;      // A_xx
+  T* rg = wk + 3 * SM;      // 1 / diag(F_x)
+  T* v1 = wk + 4 * SM;      // first F_x sweep  D^{-1} c4,  c4 = F_u v3 - K1
+  T* p1 = wk + 5 * SM;      // Phi' * v1 (its neighbour product)
+  T* y5 = wk + 6 * SM;      // x-part of Y(v3)
+  T* w1 = wk + 7 * SM;      // first F_x^T sweep
+  T* y4 = wk + 8 * SM;      // lambda-part of Y(v3)
+  T* e1 = wk + 9 * SM;      // ping-pong spares for n_lo > 2
+  T* e2 = wk + 10 * SM;
+  // split-residual float copies of x, lambda and Phi(x), alive in P1-P2 only
+  float* xf = reinterpret_cast<float*>(y5);
+  float* lf = reinterpret_cast<float*>(w1);
+  float* pf = reinterpret_cast<float*>(y4);
 
   for (int a = threadIdx.x; a < nu; a += blockDim.x) {
     sm.act[a] = A.act[I.act_off + a];
     sm.u[a] = Uin[I.u_off + (long long)s * nu + a];
+    sm.v3[a] = T(0);
   }
   __syncthreads();
 
-  // ---- phase A: K_i (eq. 9) in float64, coefficient fields, norms ----
+  // ---- P1 (split residual): float copies for the stencils ----
+  if (!full) {
+    const float k0f = (float)k0, k1h = (float)(0.5 * k1);
+    for (int c = sl.lo + threadIdx.x; c < sl.hi; c += blockDim.x) {
+      const float xv = d2f(X[so + c]);
+      xf[c - sl.lo] = xv;
+      lf[c - sl.lo] = d2f(L[so + c]);
+      pf[c - sl.lo] = k0f * (xv + k1h * xv * xv);
+    }
+    cl.sync();
+  }
+
+  // ---- P2: K_i (eq. 9), coefficient fields, norms ----
   double vmax = 0.0, vsq = 0.0;
-  for (int c = threadIdx.x; c < ng; c += blockDim.x) {
+  float fmax_ = 0.0f, fsq = 0.0f;
+  const T th = (T)h, tdc = (T)dcoef;
+  const float cxf = (float)cx, cyf = (float)cy, dcf = (float)dcoef, hf = (float)h;
+  const float k0f_ = (float)k0, k1f_ = (float)k1, qf_ = (float)I.q, b0f = (float)b0;
+  const float k01f = (float)(k0 * k1), hqff = last ? (float)(h * I.qf) : 0.0f;
+  const double hqf = h * I.qf;
+  for (int c = sl.lo + threadIdx.x; c < sl.hi; c += blockDim.x) {
     const int ix = c % mx, iy = c / mx;
+    const int cl_ = c - sl.lo;
     const double x = X[so + c];
     const double lam = L[so + c];
     const double xp = (s == 0) ? x0[c] : X[so - ng + c];
-    const double ln = last ? h * I.qf * (x - ref[c]) : L[so + ng + c];
-    const double* Xs = X + so;
-    const double* Ls = L + so;
-    const double nphi = nbr_sum<double>(c, ix, iy, mx, my, cx, cy,
-                                        [&](int m) { return phi_k(Xs[m], k0, k1); });
-    const double lphi = nphi - dcoef * phi_k(x, k0, k1);
-    const double nlam = nbr_sum<double>(c, ix, iy, mx, my, cx, cy, [&](int m) { return Ls[m]; });
-    const double mu = nlam - dcoef * lam;  // (Lap lambda)_c
-    const double src = b0 * act_sum<double>(c, nu, sm.act, sm.u);
-    const double dphi = k0 * (1.0 + k1 * x);
-    const double K1 = xp - x + h * (lphi + src);
-    const double K3 = ln - lam + h * (I.q * (x - ref[c]) + dphi * mu);
-    double a1 = sanitize_abs(K1), a3 = sanitize_abs(K3);
-    vmax = fmax(vmax, fmax(a1, a3));
-    vsq += K1 * K1 + K3 * K3;
+    T K1t, K3t, dpt, axt;
+    if (full) {
+      const double ln = last ? hqf * (x - ref[c]) : L[so + ng + c];
+      double srcd = 0.0;
+      for (int a = 0; a < nu; ++a)
+        if (sm.act[a] == c) srcd += sm.u[a];
+      srcd *= b0;
+      const double* Xs = X + so;
+      const double* Ls = L + so;
+      const double nphi = nbr_sum<double>(c, ix, iy, mx, my, cx, cy,
+                                          [&](int m) { return phi_d(Xs[m], k0, k1); });
+      const double lphi = nphi - dcoef * phi_d(x, k0, k1);
+      const double mu = nbr_sum<double>(c, ix, iy, mx, my, cx, cy,
+                                        [&](int m) { return Ls[m]; }) - dcoef * lam;
+      const double dphi = k0 * (1.0 + k1 * x);
+      const double K1 = xp - x + h * (lphi + srcd);
+      const double K3 = ln - lam + h * (I.q * (x - ref[c]) + dphi * mu);
+      vmax = fmax(vmax, fmax(abs_or_inf(K1), abs_or_inf(K3)));
+      vsq += K1 * K1 + K3 * K3;
+      K1t = (T)K1;
+      K3t = (T)K3;
+      dpt = (T)dphi;
+      axt = (T)(h * (I.q + k0 * k1 * mu) + (last ? h * I.qf : 0.0));
+    } else {
+      const float nphi = nbr_sum<float>(c, ix, iy, mx, my, cxf, cyf,
+                                        [&](int m) { return ldn(pf, m, sl, cl); });
+      const float lphi = nphi - dcf * pf[cl_];
+      const float mu = nbr_sum<float>(c, ix, iy, mx, my, cxf, cyf,
+                                      [&](int m) { return ldn(lf, m, sl, cl); }) - dcf * lf[cl_];
+      const float xv = xf[cl_];
+      const float rv = d2f(ref[c]);
+      float srcf = 0.0f;
+      for (int a = 0; a < nu; ++a)
+        if (sm.act[a] == c) srcf += (float)sm.u[a];
+      const float dphi = k0f_ * (1.0f + k1f_ * xv);
+      const float t1 = hf * (lphi + b0f * srcf);
+      const float t3 = hf * (qf_ * (xv - rv) + dphi * mu);
+      // the O(1) differences in float64; at the last stage lambda_{N+1} is
+      // h qf (x_N - ref), an O(h) term
+      const double d3 = last ? -lam : L[so + ng + c] - lam;
+      const float K1 = d2f(xp - x) + t1;
+      const float K3 = d2f(d3) + t3 + (last ? hqff * (xv - rv) : 0.0f);
+      fmax_ = fmaxf(fmax_, fmaxf(abs_or_inf_f(K1), abs_or_inf_f(K3)));
+      fsq += K1 * K1 + K3 * K3;
+      K1t = (T)K1;
+      K3t = (T)K3;
+      dpt = (T)dphi;
+      axt = (T)(hf * (qf_ + k01f * mu) + hqff);
+    }
     if (!resid_only) {
-      b1[c] = (T)K1;
-      b2[c] = (T)K3;
-      dp[c] = (T)dphi;
-      ax[c] = (T)(h * (I.q + k0 * k1 * mu) + (last ? h * I.qf : 0.0));
+      const T r = T(1) / (-T(1) - th * tdc * dpt);
+      b2[cl_] = K3t;
+      dp[cl_] = dpt;
+      ax[cl_] = axt;
+      rg[cl_] = r;
+      const T v = -K1t * r;  // first sweep of F_x v5 = -K1 (v3 = 0)
+      v1[cl_] = v;
+      p1[cl_] = dpt * v;
+      for (int a = 0; a < nu; ++a)
+        if (sm.act[a] == c) sm.b1a[a] = K1t;
     }
   }
+  vmax = fmax(vmax, (double)fmax_);
+  vsq += (double)fsq;
   for (int a = threadIdx.x; a < nu; a += blockDim.x) {
     const double K2 = h * (I.r * sm.u[a] + b0 * L[so + sm.act[a]]);
-    vmax = fmax(vmax, sanitize_abs(K2));
-    vsq += K2 * K2;
+    if (cl.rank == 0) {
+      vmax = fmax(vmax, abs_or_inf(K2));
+      vsq += K2 * K2;
+    }
     sm.b3[a] = (T)K2;
-    sm.v3[a] = T(0);
   }
   block_reduce_store(vmax, vsq, &sm.red, &sm.red_out[0], &sm.red_out[1]);
   if (threadIdx.x == 0) {
-    const int slot = (k % 3) * A.n_inst + b;
+    const int slot = (k % RES_SLOTS) * A.n_inst + b;
     atomicMax(&A.res_inf[slot], (unsigned long long)__double_as_longlong(sm.red_out[0]));
     atomicAdd(&A.res_sq[slot], sm.red_out[1]);
     if (k == 0 && A.res_first)
       atomicMax(&A.res_first[b], (unsigned long long)__double_as_longlong(sm.red_out[0]));
   }
-  if (resid_only) {
-    __syncthreads();
-    return;
-  }
-  __syncthreads();
+  cl.sync();
+  if (resid_only) return;
 
-  // ---- phase B: lower layer in T ----
-  const T th = (T)h, tcx = (T)cx, tcy = (T)cy, tb0 = (T)b0;
-  const T tdc = (T)dcoef;
+  // ---- P3: lower layer in T ----
+  const T tcx = (T)cx, tcy = (T)cy, tb0 = (T)b0;
   const T auu = (T)(h * I.r + I.gamma);
   const int n_lo = A.n_lo;
-  T* y5 = va;  // final buffers of the two Jacobi solves (set below)
-  T* y4 = wa;
+  T* y5c = y5;
+  T* y4c = y4;
   for (int it = 0; it <= A.n_u_it; ++it) {
-    // Y(v3) = P^{-1}(F_u v3 - b1, -b2): F_x v5 = c4 by n_lo sweeps from zero
-    T* cur = va;
-    T* nxt = vb;
-    for (int c = threadIdx.x; c < ng; c += blockDim.x) {
-      const T c4 = -b1[c] + th * tb0 * act_sum<T>(c, nu, sm.act, sm.v3);
-      const T d = -T(1) - th * tdc * dp[c];
-      cur[c] = c4 / d;
+    if (it > 0) {
+      // c4 = F_u v3 - K1 changes only on actuator cells: refresh v1, p1 there
+      for (int a = threadIdx.x; a < nu; a += blockDim.x) {
+        const int c = sm.act[a];
+        bool first = (c >= sl.lo && c < sl.hi);
+        for (int a2 = 0; a2 < a && first; ++a2)
+          if (sm.act[a2] == c) first = false;
+        if (first) {
+          T inj = T(0);
+          for (int a2 = 0; a2 < nu; ++a2)
+            if (sm.act[a2] == c) inj += sm.v3[a2];
+          const T v = (th * tb0 * inj - sm.b1a[a]) * rg[c - sl.lo];
+          v1[c - sl.lo] = v;
+          p1[c - sl.lo] = dp[c - sl.lo] * v;
+        }
+      }
+      cl.sync();
     }
-    __syncthreads();
-    for (int sw = 1; sw < n_lo; ++sw) {
-      for (int c = threadIdx.x; c < ng; c += blockDim.x) {
-        const int ix = c % mx, iy = c / mx;
-        const T c4 = -b1[c] + th * tb0 * act_sum<T>(c, nu, sm.act, sm.v3);
-        const T d = -T(1) - th * tdc * dp[c];
+    // F_x v5 = c4 by n_lo pointwise Jacobi sweeps from zero: sweep 1 is v1;
+    // sweep s+1 = v1 - D^{-1} (offdiag F_x) sweep s, reading neighbours
+    T* cur = v1;
+    if (n_lo >= 2) {
+      cur = y5;
+      for (int c = sl.lo + threadIdx.x; c < sl.hi; c += blockDim.x) {
+        const int ix = c % mx, iy = c / mx, q = c - sl.lo;
         const T off = th * nbr_sum<T>(c, ix, iy, mx, my, tcx, tcy,
-                                      [&](int m) { return dp[m] * cur[m]; });
-        nxt[c] = (c4 - off) / d;
+                                      [&](int m) { return ldn(p1, m, sl, cl); });
+        cur[q] = v1[q] - rg[q] * off;
       }
-      __syncthreads();
-      T* t = cur; cur = nxt; nxt = t;
-    }
-    y5 = cur;
-    // F_x^T v4 = -b2 - A_xx v5 by n_lo sweeps from zero
-    T* wc = (y5 == va) ? wa : wa;  // wa/wb are free
-    T* wn = wb;
-    for (int c = threadIdx.x; c < ng; c += blockDim.x) {
-      const T e = -b2[c] - ax[c] * y5[c];
-      const T d = -T(1) - th * tdc * dp[c];
-      wc[c] = e / d;
-    }
-    __syncthreads();
-    for (int sw = 1; sw < n_lo; ++sw) {
-      for (int c = threadIdx.x; c < ng; c += blockDim.x) {
-        const int ix = c % mx, iy = c / mx;
-        const T e = -b2[c] - ax[c] * y5[c];
-        const T d = -T(1) - th * tdc * dp[c];
-        const T off = th * dp[c] * nbr_sum<T>(c, ix, iy, mx, my, tcx, tcy,
-                                              [&](int m) { return wc[m]; });
-        wn[c] = (e - off) / d;
+      T* nxt = e1;
+      for (int sw = 2; sw < n_lo; ++sw) {
+        cl.sync();
+        for (int c = sl.lo + threadIdx.x; c < sl.hi; c += blockDim.x) {
+          const int ix = c % mx, iy = c / mx, q = c - sl.lo;
+          const T off = th * nbr_sum<T>(c, ix, iy, mx, my, tcx, tcy, [&](int m) {
+            return ldn(dp, m, sl, cl) * ldn(cur, m, sl, cl);
+          });
+          nxt[q] = v1[q] - rg[q] * off;
+        }
+        T* t = cur; cur = nxt; nxt = t;
       }
-      __syncthreads();
-      T* t = wc; wc = wn; wn = t;
     }
-    y4 = wc;
+    y5c = cur;
+    // sweep 1 of F_x^T v4 = -K3 - A_xx v5 (own cells only)
+    for (int c = sl.lo + threadIdx.x; c < sl.hi; c += blockDim.x) {
+      const int q = c - sl.lo;
+      w1[q] = (-b2[q] - ax[q] * y5c[q]) * rg[q];
+    }
+    cur = w1;
+    if (n_lo >= 2) {
+      cl.sync();
+      cur = y4;
+      for (int c = sl.lo + threadIdx.x; c < sl.hi; c += blockDim.x) {
+        const int ix = c % mx, iy = c / mx, q = c - sl.lo;
+        const T off = th * dp[q] * nbr_sum<T>(c, ix, iy, mx, my, tcx, tcy,
+                                              [&](int m) { return ldn(w1, m, sl, cl); });
+        cur[q] = w1[q] - rg[q] * off;
+      }
+      T* nxt = (y5c == e1) ? e2 : e1;  // the spare that does not hold v5
+      for (int sw = 2; sw < n_lo; ++sw) {
+        cl.sync();
+        for (int c = sl.lo + threadIdx.x; c < sl.hi; c += blockDim.x) {
+          const int ix = c % mx, iy = c / mx, q = c - sl.lo;
+          const T off = th * dp[q] * nbr_sum<T>(c, ix, iy, mx, my, tcx, tcy,
+                                                [&](int m) { return ldn(cur, m, sl, cl); });
+          nxt[q] = w1[q] - rg[q] * off;
+        }
+        T* t = cur; cur = nxt; nxt = t;
+      }
+    }
+    y4c = cur;
+    cl.sync();
     if (it < A.n_u_it) {
-      // A_uu v3 = b3 + F_u^T y_lambda (A_ux = 0)
-      __syncthreads();
+      // A_uu v3 = K2 + F_u^T y_lambda (A_ux = 0); every rank keeps all of v3
       for (int a = threadIdx.x; a < nu; a += blockDim.x)
-        sm.v3[a] = (sm.b3[a] + th * tb0 * y4[sm.act[a]]) / auu;
+        sm.v3[a] = (sm.b3[a] + th * tb0 * ldn(y4c, sm.act[a], sl, cl)) / auu;
       __syncthreads();
     }
   }
-  // back-solve (eq. 23b): (v1, v2) = P^{-1}(b1 - F_u v3, b2) = -Y(v3)
+  // back-solve (eq. 23b): (v1, v2) = P^{-1}(K1 - F_u v3, K3) = -Y(v3)
 
-  // ---- phase C: S_i <- S_i - alpha Delta s_i (float64) ----
+  // ---- P4: S_i <- S_i - alpha Delta s_i (float64) ----
   const double alpha = A.alpha;
   double* Xo = A.xout[rd ^ 1];
   double* Lo = A.lout[rd ^ 1];
   double* Uo = A.uout[rd ^ 1];
-  for (int c = threadIdx.x; c < ng; c += blockDim.x) {
-    Xo[so + c] = X[so + c] + alpha * (double)y5[c];
-    Lo[so + c] = L[so + c] + alpha * (double)y4[c];
+  for (int c = sl.lo + threadIdx.x; c < sl.hi; c += blockDim.x) {
+    const int q = c - sl.lo;
+    Xo[so + c] = fma(alpha, to_double(y5c[q]), X[so + c]);
+    Lo[so + c] = fma(alpha, to_double(y4c[q]), L[so + c]);
   }
-  for (int a = threadIdx.x; a < nu; a += blockDim.x)
-    Uo[I.u_off + (long long)s * nu + a] = sm.u[a] - alpha * (double)sm.v3[a];
-  __syncthreads();
+  if (cl.rank == 0)
+    for (int a = threadIdx.x; a < nu; a += blockDim.x)
+      Uo[I.u_off + (long long)s * nu + a] = sm.u[a] - alpha * (double)sm.v3[a];
+  cl.sync();
 }
 
 template <typename T, int MODE>
@@ -307,32 +488,49 @@ __global__ void __launch_bounds__(512) k_iterate(IterArgs A) {
   SmallShared<T>& sm = *reinterpret_cast<SmallShared<T>*>(smem_raw);
   T* wk;
   if (A.scratch == nullptr) {
-    size_t off = (sizeof(SmallShared<T>) + 15) & ~size_t(15);
+    const size_t off = (sizeof(SmallShared<T>) + 15) & ~size_t(15);
     wk = reinterpret_cast<T*>(smem_raw + off);
   } else {
     wk = reinterpret_cast<T*>(A.scratch + (long long)blockIdx.x * A.scratch_stride);
   }
+  Cl cl;
+  cl.C = A.csize;
+  cl.rank = (A.csize > 1) ? (int)cg::this_cluster().block_rank() : 0;
   const int k = (MODE == MODE_SOLVE) ? *(volatile int*)A.iter_k : 0;
+  const int n_clusters = gridDim.x / A.csize;
 
-  for (int w = blockIdx.x; w < A.n_work; w += gridDim.x) {
+  for (int w = blockIdx.x / A.csize; w < A.n_work; w += n_clusters) {
     const int2 item = A.work[w];
     const int b = item.x, s = item.y;
-    bool resid_only = (MODE == MODE_ONESHOT) ? (A.resid_only != 0) : false;
-    if (MODE == MODE_SOLVE) {
+    bool resid_only = false;
+    bool full = true;
+    if (MODE == MODE_ONESHOT) {
+      resid_only = (A.resid_only != 0);
+      full = resid_only || (A.full_all != 0);
+    } else {
       if (threadIdx.x == 0) {
-        int skip = 0;
+        int skip = 0, fl = 1;
         if (k > A.max_iter || A.status[b] != ST_RUNNING) {
           skip = 1;
-        } else if (k > 0) {
-          const int pslot = ((k - 1) % 3) * A.n_inst + b;
-          const double r = __longlong_as_double((long long)A.res_inf[pslot]);
-          const double r0 = __longlong_as_double((long long)A.res_first[b]);
+        } else {
+          const int ffrom = A.full_from[b];
+          const int f0 = A.full0[b];
           int st = ST_RUNNING;
-          if (r <= A.tol) st = ST_CONVERGED;
-          else if (!(r <= 1.79e308) || r > A.div_limit * fmax(r0, 1e-300)) st = ST_DIVERGED;
+          bool switch_now = false;
+          double r = 0.0;
+          int pslot = 0;
+          if (k > 0) {
+            pslot = ((k - 1) % RES_SLOTS) * A.n_inst + b;
+            r = __longlong_as_double((long long)A.res_inf[pslot]);
+            const double r0 = __longlong_as_double((long long)A.res_first[b]);
+            const bool prev_full = (k - 1 >= ffrom) || (k == 1 && f0);
+            if (!(r <= 1.79e308) || r > A.div_limit * fmax(r0, 1e-300)) st = ST_DIVERGED;
+            else if (prev_full && r <= A.tol) st = ST_CONVERGED;
+            else if (!prev_full && r <= fmax(A.tol, A.split_min)) switch_now = true;
+          }
           if (st != ST_RUNNING) {
             skip = 1;
-            if (s == 0) {
+            if (s == 0 && cl.rank == 0) {
               A.status[b] = st;
               A.iters[b] = k - 1;
               A.final_buf[b] = (k - 1) & 1;
@@ -340,23 +538,29 @@ __global__ void __launch_bounds__(512) k_iterate(IterArgs A) {
               A.fin_2[b] = sqrt(A.res_sq[pslot]);
               atomicSub(A.n_active, 1);
             }
+          } else {
+            fl = (A.full_all || k >= ffrom || switch_now || k == A.max_iter || (k == 0 && f0))
+                     ? 1 : 0;
+            if (s == 0 && cl.rank == 0) {
+              if (fl && ffrom > k) A.full_from[b] = k;
+              const int nslot = ((k + 1) % RES_SLOTS) * A.n_inst + b;
+              A.res_inf[nslot] = 0ull;
+              A.res_sq[nslot] = 0.0;
+            }
           }
         }
-        if (!skip && s == 0) {
-          const int nslot = ((k + 1) % 3) * A.n_inst + b;
-          A.res_inf[nslot] = 0ull;
-          A.res_sq[nslot] = 0.0;
-        }
         sm.skip = skip;
+        sm.full = fl;
       }
       __syncthreads();
-      if (sm.skip) {
-        __syncthreads();
-        continue;
-      }
+      const bool sk = sm.skip != 0;
+      full = sm.full != 0;
+      __syncthreads();
+      if (sk) continue;  // uniform across the cluster: every rank read the same slots
       resid_only = (k == A.max_iter);
     }
-    process_item<T>(A, b, s, k, (MODE == MODE_SOLVE) ? (k & 1) : 0, resid_only, sm, wk);
+    process_item<T>(A, b, s, k, (MODE == MODE_SOLVE) ? (k & 1) : 0, full, resid_only, sm, wk,
+                    cl);
   }
 
   if (MODE == MODE_SOLVE) {
@@ -379,7 +583,7 @@ __global__ void k_init_control(IterArgs A, int cold) {
   if (b >= A.n_inst) return;
   const InstDev I = A.inst[b];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    for (int q = 0; q < 3; ++q) {
+    for (int q = 0; q < RES_SLOTS; ++q) {
       A.res_inf[q * A.n_inst + b] = 0ull;
       A.res_sq[q * A.n_inst + b] = 0.0;
     }
@@ -389,6 +593,8 @@ __global__ void k_init_control(IterArgs A, int cold) {
     A.final_buf[b] = 0;
     A.fin_inf[b] = 0.0;
     A.fin_2[b] = 0.0;
+    A.full_from[b] = A.full_all ? 0 : 0x7fffffff;
+    A.full0[b] = cold ? 0 : 1;  // a warm start may already be converged
     if (b == 0) {
       *A.n_active = A.n_inst;
       *A.iter_k = 0;
@@ -413,7 +619,7 @@ __global__ void k_init_control(IterArgs A, int cold) {
 
 // After the iteration chunks: settle instances still running at max_iter,
 // gather every instance's returned iterate into the "current" buffers and
-// u_out.  src[0]/src[1] are the ping-pong buffers.
+// u_out.  xs/us/ls[0..1] are the ping-pong buffers.
 struct FinalArgs {
   const InstDev* inst;
   int n_inst;
@@ -439,7 +645,8 @@ __global__ void k_finalize_status(FinalArgs F) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= F.n_inst) return;
   if (F.status[b] == ST_RUNNING) {
-    const int slot = (F.max_iter % 3) * F.n_inst + b;
+    // iteration max_iter always evaluates the float64 residual
+    const int slot = (F.max_iter % RES_SLOTS) * F.n_inst + b;
     const double r = __longlong_as_double((long long)F.res_inf[slot]);
     F.status[b] = (r <= F.tol) ? ST_CONVERGED : ((r <= 1.79e308) ? ST_MAX_ITER : ST_DIVERGED);
     F.iters[b] = F.max_iter;

@@ -46,7 +46,8 @@ class nmpc_opts(ctypes.Structure):
                 ("n_u_it", ctypes.c_int), ("precision", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("alpha", ctypes.c_double),
                 ("div_limit", ctypes.c_double), ("threads", ctypes.c_int),
-                ("use_graph", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("cluster", ctypes.c_int),
+                ("split_min", ctypes.c_double)]
 
 
 class nmpc_stats(ctypes.Structure):

@@ -137,8 +137,9 @@ def test_one_iteration_mixed_matches_oracle(G, case):
             d_or = o - i
             err = np.abs((g - i) - d_or).max() / max(np.abs(d_or).max(), 1e-300)
             assert err <= 1e-4, (b, err)
-        # the residual norm is float64 in both modes
-        assert abs(res[b, 0] - norms[b][0]) <= 1e-12 * norms[b][0]
+        # the mixed path's iterations use the split residual: float64
+        # differences, float32 O(h) terms and a float32 max-norm
+        assert abs(res[b, 0] - norms[b][0]) <= 1e-5 * norms[b][0]
 
 
 def _solve_gpu(G, insts, **opts):
@@ -266,3 +267,60 @@ def test_residual_entry_point_matches_oracle(G):
         r = O.kkt_norms(*O.kkt(p, lists[0][b], lists[1][b], lists[2][b]))
         assert abs(out[b, 0] - r[0]) <= 1e-12 * r[0]
         assert abs(out[b, 1] - r[1]) <= 1e-10 * r[1]
+
+
+CLUSTER_CASES = {
+    "heat2d_16x12_N7": lambda: [wl.heat2d(16, 12, 7, 3, 2, seed=4)],
+    "heat1d_M50_N6": lambda: [wl.heat1d(50, 6, 3, 0.02, seed=21)],
+    "mixed_2d_1d": lambda: [wl.heat2d(10, 9, 4, 2, 2, seed=22), wl.heat1d(40, 5, 2, 0.01, seed=23)],
+}
+
+
+@pytest.mark.parametrize("cluster", [2, 3, 5, 8, 16])
+@pytest.mark.parametrize("case", list(CLUSTER_CASES))
+def test_cluster_split_stage_matches_oracle(G, case, cluster):
+    """A stage split over a thread-block cluster (slab halos read through
+    distributed shared memory) gives the oracle's iterate."""
+    insts = CLUSTER_CASES[case]()
+    state, lists = _rand_state(insts, 30)
+    gpu, res = _iterate_gpu(G, insts, state, 3, precision=G.NMPC_FP64, cluster=cluster)
+    ora, norms = _oracle_iterate(insts, lists, 3)
+    _cmp_iterates(G, insts, gpu, ora, 1e-10)
+
+
+@pytest.mark.parametrize("n_lo,n_u_it", [(1, 1), (1, 2), (3, 2), (4, 3), (2, 1), (2, 3)])
+@pytest.mark.parametrize("cluster", [1, 3])
+def test_inner_iteration_counts_match_oracle(G, n_lo, n_u_it, cluster):
+    insts = [wl.heat2d(12, 14, 5, 2, 2, seed=31), wl.heat1d(33, 4, 3, 0.05, seed=32)]
+    state, lists = _rand_state(insts, 33)
+    gpu, _ = _iterate_gpu(G, insts, state, 2, precision=G.NMPC_FP64, n_lo=n_lo,
+                          n_u_it=n_u_it, cluster=cluster)
+    out = []
+    for b, inst in enumerate(insts):
+        p = O.Problem(inst)
+        X, U, L = lists[0][b], lists[1][b], lists[2][b]
+        for _ in range(2):
+            X, U, L, _n = O.jacobi_iteration(p, X, U, L, n_lo=n_lo, n_u_it=n_u_it)
+        out.append((X.reshape(p.N, -1), U, L.reshape(p.N, -1)))
+    _cmp_iterates(G, insts, gpu, out, 1e-10)
+
+
+@pytest.mark.parametrize("cluster", [1, 2, 3])
+def test_mixed_solve_certifies_with_a_float64_residual(G, cluster):
+    """The mixed path iterates on the split residual and stops only on a
+    float64 residual: the returned state's residual, recomputed by the FP64
+    residual entry point and by the oracle, is below tol."""
+    import torch
+    insts = [wl.heat2d(32, 32, 20, 4, 2, seed=40)]
+    s = G.Solver(insts, tol=1e-7, precision=G.NMPC_MIXED, cluster=cluster)
+    rc, st = s.solve()
+    assert rc == G.NMPC_OK and st[0].res_inf <= 1e-7
+    x, u, lam = s.state()
+    out = G.nmpc_residual(s.h, s.x0, s.ref, x, u, lam, 1)
+    assert out[0, 0] <= 1e-7 and abs(out[0, 0] - st[0].res_inf) <= 1e-12 * st[0].res_inf + 1e-20
+    p = O.Problem(insts[0])
+    X = x.cpu().numpy().reshape((p.N,) + p.shape)
+    L = lam.cpu().numpy().reshape((p.N,) + p.shape)
+    U = u.cpu().numpy().reshape(p.N, -1)
+    assert O.kkt_norms(*O.kkt(p, X, U, L))[0] <= 1e-7
+    s.close()
