@@ -1,8 +1,9 @@
 """Build the sm_103a shared library ``_lib/libnmpc_gb300.so`` with nvcc.
 
-One translation unit (the C ABI plus the kernels it launches), compiled
-in-tree; the output is git-ignored.  ``build()`` rebuilds only when a source
-is newer than the library.
+Two translation units (the solver's C ABI with its kernels, and the learned
+warm start's network), compiled in parallel in-tree and linked into one
+library; the outputs are git-ignored.  ``build()`` rebuilds only when a
+source is newer than the library.
 """
 from __future__ import annotations
 
@@ -14,9 +15,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libnmpc_gb300.so")
-SOURCES = [os.path.join(HERE, "csrc", "nmpc_capi.cu")]
+SOURCES = [os.path.join(HERE, "csrc", "nmpc_capi.cu"), os.path.join(HERE, "csrc", "mlp_capi.cu")]
 DEPS = SOURCES + [os.path.join(HERE, "csrc", "nmpc_kernels.cuh"),
-                  os.path.join(ROOT, "include", "nmpc.h")]
+                  os.path.join(HERE, "csrc", "mlp_kernels.cuh"),
+                  os.path.join(ROOT, "include", "nmpc.h"),
+                  os.path.join(ROOT, "include", "nmpc_mlp.h")]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -38,13 +41,23 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB_PATH
     os.makedirs(LIB_DIR, exist_ok=True)
-    tmp = LIB_PATH + ".tmp"
-    cmd = [nvcc_path(), "-O3", "-std=c++17", ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
-           "-shared", "-o", tmp] + SOURCES
+    nvcc = nvcc_path()
+    flags = ["-O3", "-std=c++17", ARCH, "-lineinfo", "-Xcompiler", "-fPIC"]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-        print(" ".join(cmd), file=sys.stderr)
-    subprocess.run(cmd, check=True)
+        flags.append("-Xptxas=-v")
+    objs, procs = [], []
+    for src in SOURCES:
+        obj = os.path.join(LIB_DIR, os.path.basename(src) + ".o")
+        objs.append(obj)
+        cmd = [nvcc] + flags + ["-c", "-o", obj, src]
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        procs.append((cmd, subprocess.Popen(cmd)))
+    for cmd, p in procs:
+        if p.wait() != 0:
+            raise subprocess.CalledProcessError(p.returncode, cmd)
+    tmp = LIB_PATH + ".tmp"
+    subprocess.run([nvcc, ARCH, "-shared", "-o", tmp] + objs, check=True)
     os.replace(tmp, LIB_PATH)
     return LIB_PATH
 

@@ -1,0 +1,351 @@
+// Host side of the learned-warm-start network (include/nmpc_mlp.h): a
+// fully connected network with GELU hidden layers, BF16 tensor-core GEMMs with
+// FP32 accumulation, MSE loss, backward pass and Adam on FP32 master weights.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/nmpc_mlp.h"
+#include "mlp_kernels.cuh"
+
+namespace {
+
+#define MCK(call)                                                  \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) {                                       \
+      fprintf(stderr, "nmpc_mlp: %s failed: %s (%s:%d)\n", #call,  \
+              cudaGetErrorString(e_), __FILE__, __LINE__);         \
+      return NMPC_MLP_ERR_CUDA;                                    \
+    }                                                              \
+  } while (0)
+
+int grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  return (int)std::min<long long>(std::max<long long>(b, 1), 4096);
+}
+
+cudaError_t gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bias, float* C,
+                 __nv_bfloat16* Cb, int M, int N, int K, int lda, int ldb, int ldc, int epi,
+                 cudaStream_t st) {
+  mlp_dev::GemmArgs g{A, B, bias, C, Cb, M, N, K, lda, ldb, ldc, epi};
+  dim3 grid((N + mlp_dev::BN - 1) / mlp_dev::BN, (M + mlp_dev::BM - 1) / mlp_dev::BM);
+  mlp_dev::k_gemm_bf16<<<grid, mlp_dev::GEMM_THREADS, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+cudaError_t transpose(const __nv_bfloat16* in, __nv_bfloat16* out, int rows, int cols,
+                      cudaStream_t st) {
+  dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+  mlp_dev::k_transpose_bf16<<<grid, dim3(32, 8), 0, st>>>(in, out, rows, cols);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+struct nmpc_mlp {
+  int L = 0;                    // layers
+  std::vector<int> w;           // widths, L + 1
+  int max_batch = 0;
+  long long n_params = 0;
+  // per layer device buffers
+  std::vector<float*> W, b, gW, gb, mW, vW, mb, vb;   // fp32
+  std::vector<__nv_bfloat16*> Wb, WTb;                  // bf16 [out,in] and [in,out]
+  std::vector<float*> z;         // pre-activation [B, out] fp32
+  std::vector<__nv_bfloat16*> a;  // activations [B, width] bf16, a[0] = input
+  std::vector<__nv_bfloat16*> aT; // transposes for the weight gradient
+  float* da = nullptr;            // [B, max width] fp32
+  float* dz = nullptr;
+  __nv_bfloat16* dz16 = nullptr;
+  __nv_bfloat16* dzT = nullptr;
+  float* y = nullptr;             // [B, out]
+  float* loss = nullptr;
+  float* h_loss = nullptr;
+  int step = 0;
+  long long launches = 0;
+};
+
+extern "C" {
+
+int nmpc_gemm_bf16(const void* A, const void* B, const float* bias, float* C, void* Cb, int M,
+                   int N, int K, int lda, int ldb, int ldc, int gelu, void* stream) {
+  if (!A || !B || (!C && !Cb) || M < 1 || N < 1 || K < 1 || (K % 8) != 0 || lda < K || ldb < K ||
+      ldc < N || (lda % 8) || (ldb % 8))
+    return NMPC_MLP_ERR_BAD_ARG;
+  if (((uintptr_t)A | (uintptr_t)B) & 15) return NMPC_MLP_ERR_BAD_ARG;
+  MCK(gemm((const __nv_bfloat16*)A, (const __nv_bfloat16*)B, bias, C, (__nv_bfloat16*)Cb, M, N, K,
+           lda, ldb, ldc, gelu ? mlp_dev::EPI_GELU : mlp_dev::EPI_NONE, (cudaStream_t)stream));
+  return NMPC_MLP_OK;
+}
+
+int nmpc_cast_f32_bf16(const float* in, void* out, int64_t n, void* stream) {
+  if (!in || !out || n < 0) return NMPC_MLP_ERR_BAD_ARG;
+  if (n == 0) return NMPC_MLP_OK;
+  mlp_dev::k_cast_bf16<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(
+      in, (__nv_bfloat16*)out, n);
+  MCK(cudaGetLastError());
+  return NMPC_MLP_OK;
+}
+
+int nmpc_transpose_bf16(const void* in, void* out, int rows, int cols, void* stream) {
+  if (!in || !out || rows < 1 || cols < 1) return NMPC_MLP_ERR_BAD_ARG;
+  MCK(transpose((const __nv_bfloat16*)in, (__nv_bfloat16*)out, rows, cols, (cudaStream_t)stream));
+  return NMPC_MLP_OK;
+}
+
+int nmpc_cast_f32_f64(const float* in, double* out, int64_t n, void* stream) {
+  if (!in || !out || n < 0) return NMPC_MLP_ERR_BAD_ARG;
+  if (n == 0) return NMPC_MLP_OK;
+  mlp_dev::k_cast_f64<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(in, out, n);
+  MCK(cudaGetLastError());
+  return NMPC_MLP_OK;
+}
+
+int nmpc_cast_f64_f32(const double* in, float* out, int64_t n, void* stream) {
+  if (!in || !out || n < 0) return NMPC_MLP_ERR_BAD_ARG;
+  if (n == 0) return NMPC_MLP_OK;
+  mlp_dev::k_cast_f64_f32<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(in, out, n);
+  MCK(cudaGetLastError());
+  return NMPC_MLP_OK;
+}
+
+int nmpc_mlp_create(int n_layers, const int* widths, int max_batch, uint64_t seed,
+                    nmpc_mlp** out) {
+  if (!out || !widths || n_layers < 1 || n_layers > 16 || max_batch < 1) return NMPC_MLP_ERR_BAD_ARG;
+  for (int l = 0; l <= n_layers; ++l)
+    if (widths[l] < 1 || (widths[l] % 8) != 0) return NMPC_MLP_ERR_BAD_ARG;
+  *out = nullptr;
+  nmpc_mlp* m = new (std::nothrow) nmpc_mlp();
+  if (!m) return NMPC_MLP_ERR_CUDA;
+  m->L = n_layers;
+  m->w.assign(widths, widths + n_layers + 1);
+  m->max_batch = max_batch;
+  const int B = max_batch;
+  int wmax = 0;
+  for (int v : m->w) wmax = std::max(wmax, v);
+  bool ok = true;
+  auto A = [&](cudaError_t e) { ok = ok && (e == cudaSuccess); };
+  auto fal = [&](float** p, size_t n) { *p = nullptr; A(cudaMalloc((void**)p, std::max<size_t>(n, 1) * 4)); };
+  auto bal = [&](__nv_bfloat16** p, size_t n) { *p = nullptr; A(cudaMalloc((void**)p, std::max<size_t>(n, 1) * 2)); };
+  m->W.resize(n_layers); m->b.resize(n_layers); m->gW.resize(n_layers); m->gb.resize(n_layers);
+  m->mW.resize(n_layers); m->vW.resize(n_layers); m->mb.resize(n_layers); m->vb.resize(n_layers);
+  m->Wb.resize(n_layers); m->WTb.resize(n_layers); m->z.resize(n_layers);
+  m->a.resize(n_layers + 1); m->aT.resize(n_layers + 1);
+  for (int l = 0; l < n_layers; ++l) {
+    const size_t nin = m->w[l], nout = m->w[l + 1];
+    fal(&m->W[l], nin * nout); fal(&m->gW[l], nin * nout); fal(&m->mW[l], nin * nout);
+    fal(&m->vW[l], nin * nout); fal(&m->b[l], nout); fal(&m->gb[l], nout);
+    fal(&m->mb[l], nout); fal(&m->vb[l], nout);
+    bal(&m->Wb[l], nin * nout); bal(&m->WTb[l], nin * nout);
+    fal(&m->z[l], (size_t)B * nout);
+    m->n_params += (long long)nin * nout + nout;
+  }
+  for (int l = 0; l <= n_layers; ++l) {
+    bal(&m->a[l], (size_t)B * m->w[l]);
+    bal(&m->aT[l], (size_t)B * m->w[l]);
+  }
+  fal(&m->da, (size_t)B * wmax);
+  fal(&m->dz, (size_t)B * wmax);
+  bal(&m->dz16, (size_t)B * wmax);
+  bal(&m->dzT, (size_t)B * wmax);
+  fal(&m->y, (size_t)B * m->w[n_layers]);
+  fal(&m->loss, 1);
+  A(cudaMallocHost((void**)&m->h_loss, sizeof(float)));
+  if (!ok) {
+    nmpc_mlp_destroy(m);
+    return NMPC_MLP_ERR_CUDA;
+  }
+  // initial weights: U(-1/sqrt(in), 1/sqrt(in)) from SplitMix64(seed), biases 0
+  std::vector<float> host((size_t)m->n_params);
+  uint64_t state = seed;
+  size_t o = 0;
+  for (int l = 0; l < n_layers; ++l) {
+    const int nin = m->w[l], nout = m->w[l + 1];
+    const float bound = 1.0f / std::sqrt((float)nin);
+    for (long long e = 0; e < (long long)nin * nout; ++e) {
+      state += 0x9E3779B97F4A7C15ull;
+      uint64_t z = state;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+      host[o++] = (float)((2.0 * u - 1.0) * bound);
+    }
+    for (int e = 0; e < nout; ++e) host[o++] = 0.0f;
+  }
+  int rc = nmpc_mlp_set_params(m, host.data());
+  if (rc != NMPC_MLP_OK) {
+    nmpc_mlp_destroy(m);
+    return rc;
+  }
+  *out = m;
+  return NMPC_MLP_OK;
+}
+
+int64_t nmpc_mlp_num_params(const nmpc_mlp* m) { return m ? m->n_params : 0; }
+
+int nmpc_mlp_set_params(nmpc_mlp* m, const float* host) {
+  if (!m || !host) return NMPC_MLP_ERR_BAD_ARG;
+  size_t o = 0;
+  for (int l = 0; l < m->L; ++l) {
+    const size_t nin = m->w[l], nout = m->w[l + 1];
+    MCK(cudaMemcpy(m->W[l], host + o, nin * nout * 4, cudaMemcpyHostToDevice));
+    o += nin * nout;
+    MCK(cudaMemcpy(m->b[l], host + o, nout * 4, cudaMemcpyHostToDevice));
+    o += nout;
+    MCK(cudaMemset(m->mW[l], 0, nin * nout * 4));
+    MCK(cudaMemset(m->vW[l], 0, nin * nout * 4));
+    MCK(cudaMemset(m->mb[l], 0, nout * 4));
+    MCK(cudaMemset(m->vb[l], 0, nout * 4));
+    mlp_dev::k_cast_bf16<<<grid_for(nin * nout, 256), 256>>>(m->W[l], m->Wb[l], nin * nout);
+    MCK(cudaGetLastError());
+    MCK(transpose(m->Wb[l], m->WTb[l], (int)nout, (int)nin, 0));
+  }
+  m->step = 0;
+  MCK(cudaDeviceSynchronize());
+  return NMPC_MLP_OK;
+}
+
+static int copy_out(nmpc_mlp* m, float* host, bool grads) {
+  size_t o = 0;
+  MCK(cudaDeviceSynchronize());
+  for (int l = 0; l < m->L; ++l) {
+    const size_t nin = m->w[l], nout = m->w[l + 1];
+    MCK(cudaMemcpy(host + o, grads ? m->gW[l] : m->W[l], nin * nout * 4, cudaMemcpyDeviceToHost));
+    o += nin * nout;
+    MCK(cudaMemcpy(host + o, grads ? m->gb[l] : m->b[l], nout * 4, cudaMemcpyDeviceToHost));
+    o += nout;
+  }
+  return NMPC_MLP_OK;
+}
+
+int nmpc_mlp_get_params(nmpc_mlp* m, float* host) {
+  if (!m || !host) return NMPC_MLP_ERR_BAD_ARG;
+  return copy_out(m, host, false);
+}
+
+int nmpc_mlp_get_grads(nmpc_mlp* m, float* host) {
+  if (!m || !host) return NMPC_MLP_ERR_BAD_ARG;
+  return copy_out(m, host, true);
+}
+
+static int forward_impl(nmpc_mlp* m, const float* x, int B, float* y, cudaStream_t st) {
+  const int n_in = m->w[0];
+  mlp_dev::k_cast_bf16<<<grid_for((long long)B * n_in, 256), 256, 0, st>>>(x, m->a[0],
+                                                                        (long long)B * n_in);
+  MCK(cudaGetLastError());
+  m->launches++;
+  for (int l = 0; l < m->L; ++l) {
+    const int nin = m->w[l], nout = m->w[l + 1];
+    const bool last = (l == m->L - 1);
+    // z = a W^T + b (fp32 kept for the backward pass); hidden layers store GELU(z) as bf16
+    MCK(gemm(m->a[l], m->Wb[l], m->b[l], m->z[l], nullptr, B, nout, nin, nin, nin, nout,
+             mlp_dev::EPI_NONE, st));
+    m->launches++;
+    if (!last) {
+      MCK(gemm(m->a[l], m->Wb[l], m->b[l], nullptr, m->a[l + 1], B, nout, nin, nin, nin, nout,
+               mlp_dev::EPI_GELU, st));
+      m->launches++;
+    }
+  }
+  const int nout = m->w[m->L];
+  MCK(cudaMemcpyAsync(y, m->z[m->L - 1], (size_t)B * nout * 4, cudaMemcpyDeviceToDevice, st));
+  return NMPC_MLP_OK;
+}
+
+int nmpc_mlp_forward(nmpc_mlp* m, const float* x, int B, float* y, void* stream) {
+  if (!m || !x || !y || B < 1 || B > m->max_batch) return NMPC_MLP_ERR_BAD_ARG;
+  return forward_impl(m, x, B, y, (cudaStream_t)stream);
+}
+
+int nmpc_mlp_backward(nmpc_mlp* m, const float* x, const float* target, int B, float* loss_host,
+                      void* stream) {
+  if (!m || !x || !target || B < 1 || B > m->max_batch || (B % 8) != 0) return NMPC_MLP_ERR_BAD_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = forward_impl(m, x, B, m->y, st);
+  if (rc != NMPC_MLP_OK) return rc;
+  const int nout_all = m->w[m->L];
+  MCK(cudaMemsetAsync(m->loss, 0, sizeof(float), st));
+  const long long ny = (long long)B * nout_all;
+  mlp_dev::k_mse<<<grid_for(ny, 256), 256, 0, st>>>(m->y, target, ny, m->dz, m->dz16, m->loss);
+  MCK(cudaGetLastError());
+  m->launches++;
+  for (int l = m->L - 1; l >= 0; --l) {
+    const int nin = m->w[l], nout = m->w[l + 1];
+    // dz (fp32 in m->dz, bf16 in m->dz16) holds dL/dz_l, [B, nout]
+    mlp_dev::k_bias_grad<<<(nout + 127) / 128, 128, 0, st>>>(m->dz, m->gb[l], B, nout);
+    MCK(cudaGetLastError());
+    // gW[o, i] = sum_b dz[b, o] a_l[b, i]: A = dz^T [nout, B], B-operand = a_l^T [nin, B]
+    MCK(transpose(m->dz16, m->dzT, B, nout, st));
+    MCK(transpose(m->a[l], m->aT[l], B, nin, st));
+    MCK(gemm(m->dzT, m->aT[l], nullptr, m->gW[l], nullptr, nout, nin, B, B, B, nin,
+             mlp_dev::EPI_NONE, st));
+    m->launches += 4;
+    if (l > 0) {
+      // da[b, i] = sum_o dz[b, o] W[o, i]: A = dz [B, nout], B-operand = W^T [nin, nout]
+      MCK(gemm(m->dz16, m->WTb[l], nullptr, m->da, nullptr, B, nin, nout, nout, nout, nin,
+               mlp_dev::EPI_NONE, st));
+      const long long n = (long long)B * nin;
+      mlp_dev::k_gelu_backward<<<grid_for(n, 256), 256, 0, st>>>(m->da, m->z[l - 1], m->dz,
+                                                                m->dz16, n);
+      MCK(cudaGetLastError());
+      m->launches += 2;
+    }
+  }
+  if (loss_host) {
+    MCK(cudaMemcpyAsync(m->h_loss, m->loss, sizeof(float), cudaMemcpyDeviceToHost, st));
+    MCK(cudaStreamSynchronize(st));
+    *loss_host = *m->h_loss;
+  }
+  return NMPC_MLP_OK;
+}
+
+int nmpc_mlp_adam_step(nmpc_mlp* m, float lr, void* stream) {
+  if (!m || !(lr > 0)) return NMPC_MLP_ERR_BAD_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  m->step++;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const float c1 = 1.0f - std::pow(b1, (float)m->step), c2 = 1.0f - std::pow(b2, (float)m->step);
+  for (int l = 0; l < m->L; ++l) {
+    const long long nw = (long long)m->w[l] * m->w[l + 1];
+    mlp_dev::k_adam<<<grid_for(nw, 256), 256, 0, st>>>(m->W[l], m->gW[l], m->mW[l], m->vW[l],
+                                                       m->Wb[l], nw, lr, b1, b2, eps, c1, c2);
+    mlp_dev::k_adam<<<grid_for(m->w[l + 1], 256), 256, 0, st>>>(
+        m->b[l], m->gb[l], m->mb[l], m->vb[l], nullptr, m->w[l + 1], lr, b1, b2, eps, c1, c2);
+    MCK(cudaGetLastError());
+    MCK(transpose(m->Wb[l], m->WTb[l], m->w[l + 1], m->w[l], st));
+    m->launches += 3;
+  }
+  return NMPC_MLP_OK;
+}
+
+int nmpc_mlp_train_step(nmpc_mlp* m, const float* x, const float* target, int B, float lr,
+                        float* loss_host, void* stream) {
+  int rc = nmpc_mlp_backward(m, x, target, B, loss_host, stream);
+  if (rc != NMPC_MLP_OK) return rc;
+  return nmpc_mlp_adam_step(m, lr, stream);
+}
+
+int64_t nmpc_mlp_launch_count(const nmpc_mlp* m) { return m ? m->launches : 0; }
+
+void nmpc_mlp_destroy(nmpc_mlp* m) {
+  if (!m) return;
+  cudaDeviceSynchronize();
+  auto F = [](void* p) { if (p) cudaFree(p); };
+  for (int l = 0; l < (int)m->W.size(); ++l) {
+    F(m->W[l]); F(m->b[l]); F(m->gW[l]); F(m->gb[l]); F(m->mW[l]); F(m->vW[l]);
+    F(m->mb[l]); F(m->vb[l]); F(m->Wb[l]); F(m->WTb[l]); F(m->z[l]);
+  }
+  for (size_t l = 0; l < m->a.size(); ++l) { F(m->a[l]); F(m->aT[l]); }
+  F(m->da); F(m->dz); F(m->dz16); F(m->dzT); F(m->y); F(m->loss);
+  if (m->h_loss) cudaFreeHost(m->h_loss);
+  delete m;
+}
+
+}  // extern "C"

@@ -231,3 +231,13 @@ def tiny2d(mx: int = 6, my: int = 6, horizon: int = 3, seed: int = 11, h: float 
     """Small 2D instance (2x2 actuators) for dense cross-checks."""
     return heat2d(mx, my, horizon, 2, 2, seed=seed, h=h, k1=k1, gamma=gamma,
                   name=f"tiny2d_{mx}x{my}_N{horizon}")
+
+
+def heat2d_learning_instance(seed: int) -> Instance:
+    """The 2D 64x64, N=50 problem with a seeded smooth initial field (seed) and
+    a Gaussian-bump reference whose centre ~ U[0.3, 0.7]^2 and amplitude ~
+    U[0.5, 1.5] come from seed + 77_777_777 (training and test sets of the
+    learned warm start use disjoint seed ranges)."""
+    d = uniform01(seed + 77_777_777, 3)
+    return heat2d(64, 64, 50, 4, 2, seed=seed, ref_center=(0.3 + 0.4 * d[0], 0.3 + 0.4 * d[1]),
+                  ref_amp=0.5 + d[2], name=f"heat2d_learn_{seed}")

@@ -10,10 +10,15 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared():
-    src = open(os.path.join(ROOT, "include", "nmpc.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(nmpc_[a-z_]+)\s*\(", src)))
+def _declared(header=None):
+    names = set()
+    for h in ([header] if header else sorted(os.listdir(os.path.join(ROOT, "include")))):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(nmpc_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -30,13 +35,15 @@ def test_library_exports_every_declared_symbol(lib_path):
         assert hasattr(lib, name), name
     out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True,
                          text=True, check=True).stdout
-    exported = set(re.findall(r"\b(nmpc_[a-z_]+)\b", out))
+    exported = set(re.findall(r"\b(nmpc_[a-z0-9_]+)\b", out))
     assert set(declared) <= exported
 
 
-def test_binding_covers_the_header(lib_path):
+def test_binding_covers_the_headers(lib_path):
     from paper_2004_02484_gb300 import nmpc as G
-    assert sorted(G.EXPORTED) == _declared()
+    from paper_2004_02484_gb300 import mlp as GM
+    assert sorted(G.EXPORTED) == _declared("nmpc.h")
+    assert sorted(GM.EXPORTED) == _declared("nmpc_mlp.h")
 
 
 def test_strerror_and_defaults(lib_path):
