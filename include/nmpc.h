@@ -52,7 +52,13 @@ extern "C" {
 
 #define NMPC_INIT_COLD 0 /* S^0: x_i = x0, u_i = 0, lambda_i = 0              */
 #define NMPC_INIT_WARM 1 /* S^0 = the handle's current state (last solution or
-                            a state set by nmpc_set_state)                     */
+                            a state set by nmpc_set_state); in NMPC_MIXED the
+                            first iteration evaluates the float64 residual, so
+                            an already converged state returns at once        */
+#define NMPC_INIT_GUESS 2 /* as WARM, for a state that is only a guess (e.g.
+                            the learned warm start): no float64 first residual */
+#define NMPC_INIT_SHIFT 3 /* receding horizon: the current state shifted by one
+                            stage, (s_2, ..., s_N, s_N)                        */
 
 /* Per-instance status in nmpc_stats.status */
 #define NMPC_STATUS_CONVERGED 1
@@ -96,6 +102,12 @@ typedef struct {
                       and float32 O(h) terms; from the first one below, every
                       iteration uses the float64 residual (convergence is only
                       ever declared on a float64 residual)                    */
+  int u_local;     /* 1: the u-iteration uses the actuators' local responses
+                      (P^{-1} is a fixed linear map, so Y(v3) = Y(0) + sum_b
+                      v3_b Z(e_b) with Z(e_b) zero outside 2(n_lo-1) cells of
+                      actuator b; one full-field P^{-1} per iteration) when
+                      n_lo <= 4 and the boxes fit; 0: n_u_it + 1 full-field
+                      P^{-1} applications in the paper's literal order        */
 } nmpc_opts;
 
 typedef struct {
@@ -109,7 +121,7 @@ typedef struct nmpc_handle nmpc_handle;
 
 /* Fill *o with defaults: tol 1e-6, max_iter 2000, n_lo 2, n_u_it 2, FP64,
    check_every 16, alpha 1, div_limit 1e8, threads auto, graph on, cluster
-   auto, split_min 1e-7. */
+   auto, split_min 1e-7, u_local 1. */
 void nmpc_default_opts(nmpc_opts* o);
 
 /* Validate the descriptors, build the device instance table and allocate the
@@ -124,7 +136,7 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
    (packed [sum ng], device).  horizon: 0 = each instance's own N; only 0 or a
    value equal to every instance's N is accepted (BAD_ARG otherwise).
    weights: NULL, or device [n_instances][3] = (q, r, qf) overriding the
-   descriptors for this and later solves.  init: NMPC_INIT_COLD / _WARM.
+   descriptors for this and later solves.  init: NMPC_INIT_COLD / _WARM / _GUESS.
    u_out: device packed u of the returned iterates.  stats: host
    [n_instances], written before return (the call synchronizes on stream).
    Returns NMPC_OK when every instance converged, else the first of
@@ -154,6 +166,27 @@ int nmpc_residual(nmpc_handle* h, const double* x0, const double* ref, const dou
 int nmpc_iterate(nmpc_handle* h, const double* x0, const double* ref, const double* x_in,
                  const double* u_in, const double* lam_in, double* x_out, double* u_out,
                  double* lam_out, int n_iter, double* out_res, void* stream);
+
+/* Plant simulator for the closed loop: advance the true system w (device
+   [sum ng], in place) by dt (dt = 0: each instance's own stage length h)
+   under the first-stage controls u_1 of the current solution, with n_sub
+   explicit-Euler sub-steps of the same finite-difference model,
+   w += (dt/n_sub) (Lap Phi(w) + act_gain B u_1).  Explicit Euler is
+   stable for (dt/n_sub) k_max 2 (1/dx^2 + 1/dy^2) <= 1.  u_rec: NULL or device
+   [sum n_u], receives u_1.  Requires a solved state. */
+int nmpc_plant_step(nmpc_handle* h, double* w, double dt, int n_sub, double* u_rec,
+                    void* stream);
+
+/* Receding-horizon closed loop (the paper's Sec. 5.3 use): for each of
+   `steps` sampling periods, solve with x0 = w (the first from the cold start
+   unless the handle holds a state, then from the shifted previous solution,
+   NMPC_INIT_SHIFT), apply u_1 to the plant for one stage length h
+   (nmpc_plant_step with n_sub sub-steps).  w: device [sum ng] plant state,
+   in/out; ref: device [sum ng]; u_hist: NULL or device [steps][sum n_u];
+   iters_hist, res_hist: NULL or host [steps][n_instances].  Returns the first
+   non-OK solve status met (the loop continues through it). */
+int nmpc_closed_loop(nmpc_handle* h, double* w, const double* ref, int steps, int n_sub,
+                     double* u_hist, int* iters_hist, double* res_hist, void* stream);
 
 /* Copy the handle's current state (after a solve: the returned iterates) to
    packed device arrays x, u, lam; any pointer may be NULL to skip it. */

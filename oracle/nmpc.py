@@ -487,3 +487,35 @@ def lagrangian(p: Problem, X, U, Lam):
         val += np.sum(Lam[i] * (xprev - X[i] + p.h * p.f(X[i], U[i])))
         xprev = X[i]
     return val + p.h * 0.5 * p.qf * np.sum((X[-1] - xr) ** 2)
+
+
+# ---------------------------------------------------------------------------
+# Closed loop (Sec. 5.3): receding horizon with an explicit-Euler plant
+# ---------------------------------------------------------------------------
+def plant_step(p: Problem, w, u1, dt, n_sub):
+    """Advance the true system by dt with n_sub explicit-Euler sub-steps of the
+    same finite-difference model under the first-stage controls u1."""
+    w = np.array(w, dtype=np.float64, copy=True).reshape(p.shape)
+    for _ in range(n_sub):
+        w = w + (dt / n_sub) * p.f(w, np.asarray(u1, dtype=np.float64))
+    return w
+
+
+def closed_loop(inst, steps, n_sub, tol=1e-10, max_iter=20000):
+    """Each step: solve the NMPC problem from the measured plant state (cold
+    start, so the result does not depend on warm-start choices), apply u_1 for
+    one stage length h, advance the plant.  Returns (U1 [steps, nu],
+    W [steps + 1, ng], iterations per step)."""
+    import copy
+    cur = copy.copy(inst)
+    w = np.asarray(inst.x0, dtype=np.float64).copy()
+    U1, W, its = [], [w.copy()], []
+    for _ in range(steps):
+        cur.x0 = w.copy()
+        p = Problem(cur)
+        (X, U, L), info = solve_jacobi(p, tol=tol, max_iter=max_iter)
+        U1.append(U[0].copy())
+        its.append(info["iters"])
+        w = plant_step(p, w, U[0], p.h, n_sub).ravel()
+        W.append(w.copy())
+    return np.array(U1), np.array(W), its

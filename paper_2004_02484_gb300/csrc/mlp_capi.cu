@@ -35,6 +35,10 @@ cudaError_t gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bi
                  __nv_bfloat16* Cb, int M, int N, int K, int lda, int ldb, int ldc, int epi,
                  cudaStream_t st) {
   mlp_dev::GemmArgs g{A, B, bias, C, Cb, M, N, K, lda, ldb, ldc, epi};
+  if (M <= mlp_dev::GEMV_MAX_M) {
+    mlp_dev::k_gemv_bf16<<<(N + 7) / 8, 256, 0, st>>>(g);
+    return cudaGetLastError();
+  }
   dim3 grid((N + mlp_dev::BN - 1) / mlp_dev::BN, (M + mlp_dev::BM - 1) / mlp_dev::BM);
   mlp_dev::k_gemm_bf16<<<grid, mlp_dev::GEMM_THREADS, 0, st>>>(g);
   return cudaGetLastError();

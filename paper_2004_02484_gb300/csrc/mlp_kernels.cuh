@@ -170,6 +170,56 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_gemm_bf16(GemmArgs g) {
       }
 }
 
+// The same product for few rows (M <= 8, e.g. single-instance inference):
+// one warp per output column n, 16-byte loads of B's row and of the M rows of
+// A (shared by all warps through L1), FP32 accumulation, warp-shuffle sums.
+constexpr int GEMV_MAX_M = 8;
+
+__global__ void __launch_bounds__(256) k_gemv_bf16(GemmArgs g) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n = blockIdx.x * 8 + warp;
+  if (n >= g.N) return;
+  float acc[GEMV_MAX_M];
+#pragma unroll
+  for (int m = 0; m < GEMV_MAX_M; ++m) acc[m] = 0.0f;
+  const __nv_bfloat16* brow = g.B + (long long)n * g.ldb;
+  for (int k = lane * 8; k < g.K; k += 256) {
+    const uint4 bv = *reinterpret_cast<const uint4*>(brow + k);
+    const __nv_bfloat162* b2 = reinterpret_cast<const __nv_bfloat162*>(&bv);
+    float bf[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float2 f = __bfloat1622float2(b2[q]);
+      bf[2 * q] = f.x;
+      bf[2 * q + 1] = f.y;
+    }
+#pragma unroll
+    for (int m = 0; m < GEMV_MAX_M; ++m) {
+      if (m < g.M) {
+        const uint4 av = *reinterpret_cast<const uint4*>(g.A + (long long)m * g.lda + k);
+        const __nv_bfloat162* a2 = reinterpret_cast<const __nv_bfloat162*>(&av);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float2 f = __bfloat1622float2(a2[q]);
+          acc[m] = fmaf(f.x, bf[2 * q], acc[m]);
+          acc[m] = fmaf(f.y, bf[2 * q + 1], acc[m]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < GEMV_MAX_M; ++m) {
+    float v = acc[m];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0 && m < g.M) {
+      if (g.bias) v += g.bias[n];
+      if (g.epi == EPI_GELU) v = gelu(v);
+      if (g.C) g.C[(long long)m * g.ldc + n] = v;
+      if (g.Cb) g.Cb[(long long)m * g.ldc + n] = __float2bfloat16_rn(v);
+    }
+  }
+}
+
 // out[c, r] = in[r, c] (bf16), 32 x 32 tiles through shared memory
 __global__ void k_transpose_bf16(const __nv_bfloat16* in, __nv_bfloat16* out, int rows, int cols) {
   __shared__ __nv_bfloat16 t[32][33];

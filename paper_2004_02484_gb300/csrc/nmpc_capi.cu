@@ -34,6 +34,7 @@ struct nmpc_handle {
   std::vector<InstDev> inst_h;
   long long n_g = 0, n_s = 0, n_u = 0;  // packed sizes: sum ng, sum N*ng, sum N*nu
   int ng_max = 0, nu_max = 0, n_work = 0, n_max_horizon = 0;
+  long long nu_tot = 0;  // sum of n_u (first-stage control vector length)
   // device data
   InstDev* inst_d = nullptr;
   int2* work_d = nullptr;
@@ -73,6 +74,10 @@ struct nmpc_handle {
   int slab_max = 0;
   size_t smem = 0;
   bool smem_mode = true;
+  bool stage = true;
+  bool local_u = false;
+  int box_r = 0;
+  size_t box_bytes = 0;
   bool mixed = false;
   // graph of one chunk of iterations
   cudaGraphExec_t graph_exec = nullptr;
@@ -160,6 +165,9 @@ IterArgs make_args(nmpc_handle* h) {
   A.full_all = h->mixed ? 0 : 1;
   A.csize = h->csize;
   A.slab_max = h->slab_max;
+  A.stage = h->stage ? 1 : 0;
+  A.local_u = h->local_u ? 1 : 0;
+  A.box_r = h->box_r;
   A.scratch = h->smem_mode ? nullptr : h->scratch;
   A.scratch_stride = h->scratch_stride;
   return A;
@@ -171,6 +179,10 @@ struct LaunchPlan {
   int threads = 0, csize = 1, slab_max = 0, grid = 0;
   size_t smem = 0;
   bool smem_mode = true;
+  bool stage = true;  // float64 slab inputs staged in shared memory
+  bool local_u = false;  // u-iteration through the actuators' local responses
+  int box_r = 0;
+  size_t box_bytes = 0;
 };
 
 int slab_cells(const InstDev& I, int C) {
@@ -184,45 +196,104 @@ size_t small_shared_bytes_t() {
   return (sizeof(nmpc_dev::SmallShared<T>) + 15) & ~size_t(15);
 }
 
-// Cluster size: the smallest that fits a stage slab in shared memory, then
-// grown (up to 8) while the whole batch still fits in one wave of CTAs and
-// slabs keep at least 512 cells; cluster sizes above 8 are 16 only.  A stage
-// that does not fit even at 16 runs one CTA per stage on a global slab.
+int auto_threads(int slab) {
+  int t = ((slab / 4 + 31) / 32) * 32;  // about four cells per thread
+  return std::min(512, std::max(128, t));
+}
+
+// Clusters of C CTAs (auto threads, `smem` bytes) the device keeps resident at
+// once for the iteration kernel.
+int clusters_resident(int C, int slab, size_t smem, bool mixed) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(C * 256));
+  cfg.blockDim = dim3((unsigned)auto_threads(slab));
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  cudaError_t e = mixed ? cudaOccupancyMaxActiveClusters(
+                              &n, nmpc_dev::k_iterate<float, nmpc_dev::MODE_SOLVE>, &cfg)
+                        : cudaOccupancyMaxActiveClusters(
+                              &n, nmpc_dev::k_iterate<double, nmpc_dev::MODE_SOLVE>, &cfg);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+// Cluster size: the smallest that fits a stage slab (with the float64 inputs
+// staged in shared memory if possible) in shared memory, then grown up to 8
+// while every cluster of the batch stays resident in one wave; cluster sizes
+// above 8 are 16 only.  A stage that does not fit even at 16 runs one CTA per
+// stage on a global slab.
 LaunchPlan plan_launch(const InstDev* insts, int n_inst, int n_work, const nmpc_opts& o,
                        bool mixed, int num_sms, int max_optin) {
   LaunchPlan P;
   const size_t elem = mixed ? sizeof(float) : sizeof(double);
   const size_t small = mixed ? small_shared_bytes_t<float>() : small_shared_bytes_t<double>();
+  // local-response boxes: 4 arrays of (2R+1)^dim cells per actuator, R = 2 (n_lo - 1)
+  int nu_max = 0, dim_max = 1;
+  for (int b = 0; b < n_inst; ++b) {
+    nu_max = std::max(nu_max, insts[b].nu);
+    dim_max = std::max(dim_max, insts[b].dim);
+  }
+  P.box_r = 2 * (o.n_lo - 1);
+  const size_t side = (size_t)(2 * P.box_r + 1);
+  const size_t box_bytes = (size_t)nu_max * 4 * (dim_max == 2 ? side * side : side) * elem;
+  P.local_u = o.u_local && (o.n_lo <= 4) && box_bytes <= 32768;
+  P.box_bytes = P.local_u ? ((box_bytes + 15) & ~size_t(15)) : 0;
   auto slab = [&](int C) {
     int m = 0;
     for (int b = 0; b < n_inst; ++b) m = std::max(m, slab_cells(insts[b], C));
     return m;
   };
-  auto bytes = [&](int C) { return small + (size_t)nmpc_dev::NUM_WORK_ARRAYS * slab(C) * elem; };
+  bool stage = true;
+  auto bytes = [&](int C) {
+    return small + P.box_bytes +
+           (size_t)slab(C) * (nmpc_dev::NUM_WORK_ARRAYS * elem +
+                              (stage ? nmpc_dev::NUM_STAGE_ARRAYS * sizeof(double) : 0));
+  };
   auto next_c = [](int C) { return C < 8 ? C + 1 : 16; };
+  auto fits = [&](int C) { return bytes(C) <= (size_t)max_optin; };
   int C = 1;
   if (o.cluster > 0) {
     C = o.cluster;
+    if (!fits(C)) stage = false;
   } else {
-    while (C < 16 && bytes(C) > (size_t)max_optin) C = next_c(C);
-    if (bytes(C) <= (size_t)max_optin) {
+    // the smallest cluster that fits with staging, else without staging
+    while (C < 16 && !fits(C)) C = next_c(C);
+    if (!fits(C)) {
+      stage = false;
+      C = 1;
+      while (C < 16 && !fits(C)) C = next_c(C);
+    }
+    if (fits(C)) {
+      // grow while every cluster of the batch is still resident in one wave
+      // (clusters are packed per GPC, so this is a cluster-occupancy query,
+      // not a CTA count) and slabs keep at least 512 cells
       while (C < 8) {
         const int C2 = C + 1;
-        if ((long long)n_work * C2 > num_sms || slab(C2) < 512) break;
+        if (!fits(C2) || slab(C2) < 512) break;
+        if (clusters_resident(C2, slab(C2), bytes(C2), mixed) < n_work) break;
         C = C2;
       }
     }
   }
-  P.smem_mode = bytes(C) <= (size_t)max_optin;
-  if (!P.smem_mode) C = 1;
+  P.smem_mode = fits(C);
+  if (!P.smem_mode) {
+    C = 1;
+    stage = false;
+  }
+  P.stage = stage;
   P.csize = C;
   P.slab_max = slab(C);
-  int threads = o.threads;
-  if (threads == 0) {
-    threads = ((P.slab_max / 8 + 31) / 32) * 32;
-    threads = std::min(512, std::max(64, threads));
-  }
-  P.threads = threads;
+  P.threads = o.threads ? o.threads : auto_threads(P.slab_max);
   P.smem = P.smem_mode ? bytes(C) : small;
   P.grid = n_work * C;
   return P;
@@ -249,6 +320,10 @@ LaunchPlan plan_of(const nmpc_handle* h) {
   LaunchPlan P;
   P.threads = h->threads;
   P.csize = h->csize;
+  P.stage = h->stage;
+  P.local_u = h->local_u;
+  P.box_r = h->box_r;
+  P.box_bytes = h->box_bytes;
   P.slab_max = h->slab_max;
   P.grid = h->grid;
   P.smem = h->smem;
@@ -274,6 +349,13 @@ cudaError_t configure_kernels(size_t smem) {
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// Rounding level of the split residual: its O(h) stencil terms are float32
+// sums of magnitude ~ h 4 (cx + cy) k(w) |w| with |w| ~ 1 (8 ulps of margin).
+double split_floor_of(const InstDev& I) {
+  const double eps32 = 5.960464477539063e-08;
+  return 8.0 * eps32 * I.h * 4.0 * (I.cx + I.cy) * I.k0 * (1.0 + std::fabs(I.k1));
 }
 
 int validate(const nmpc_desc* d) {
@@ -363,8 +445,10 @@ int solve_core(nmpc_handle* h, int horizon, const double* weights, int init, dou
     for (const InstDev& I : h->inst_h)
       if (I.N != horizon) return NMPC_ERR_BAD_ARG;
   }
-  if (init != NMPC_INIT_COLD && init != NMPC_INIT_WARM) return NMPC_ERR_BAD_ARG;
-  if (init == NMPC_INIT_WARM && !h->has_state) return NMPC_ERR_BAD_ARG;
+  if (init != NMPC_INIT_COLD && init != NMPC_INIT_WARM && init != NMPC_INIT_GUESS &&
+      init != NMPC_INIT_SHIFT)
+    return NMPC_ERR_BAD_ARG;
+  if (init != NMPC_INIT_COLD && !h->has_state) return NMPC_ERR_BAD_ARG;
   if (weights) {
     nmpc_dev::k_set_weights<<<(h->n_inst + 127) / 128, 128, 0, st>>>(h->inst_d, h->n_inst,
                                                                     weights);
@@ -372,12 +456,14 @@ int solve_core(nmpc_handle* h, int horizon, const double* weights, int init, dou
     CK(cudaGetLastError());
   }
   IterArgs A = make_args(h);
-  if (init == NMPC_INIT_WARM) {
+  if (init == NMPC_INIT_WARM || init == NMPC_INIT_GUESS) {
     CK(cudaMemcpyAsync(h->xb[0], h->xb[2], h->n_s * sizeof(double), cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(h->lb[0], h->lb[2], h->n_s * sizeof(double), cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(h->ub[0], h->ub[2], h->n_u * sizeof(double), cudaMemcpyDeviceToDevice, st));
   }
-  nmpc_dev::k_init_control<<<per_instance_grid(h), 256, 0, st>>>(A, init == NMPC_INIT_COLD);
+  const int mode = (init == NMPC_INIT_COLD) ? 0 : (init == NMPC_INIT_SHIFT ? 2 : 1);
+  nmpc_dev::k_init_control<<<per_instance_grid(h), 256, 0, st>>>(
+      A, mode, init == NMPC_INIT_WARM, h->xb[2], h->ub[2], h->lb[2]);
   h->launches++;
   CK(cudaGetLastError());
 
@@ -437,6 +523,7 @@ void nmpc_default_opts(nmpc_opts* o) {
   o->use_graph = 1;
   o->cluster = 0;
   o->split_min = 1e-7;
+  o->u_local = 1;
 }
 
 int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
@@ -493,7 +580,9 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
     const double dx = 1.0 / (d.mx + 1), dy = 1.0 / (d.my + 1);
     I.cx = 1.0 / (dx * dx);
     I.cy = (d.dim == 2) ? 1.0 / (dy * dy) : 0.0;
+    I.split_floor = split_floor_of(I);
     for (int a = 0; a < d.n_u; ++a) act_all.push_back(d.act_cell[a]);
+    h->nu_tot += d.n_u;
     for (int s = 0; s < d.horizon; ++s) work.push_back(make_int2(b, s));
     h->n_s += (long long)I.N * I.ng;
     h->n_u += (long long)I.N * I.nu;
@@ -532,9 +621,13 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
   h->slab_max = P.slab_max;
   h->smem = P.smem;
   h->smem_mode = P.smem_mode;
+  h->stage = P.stage;
+  h->local_u = P.local_u;
+  h->box_r = P.box_r;
+  h->box_bytes = P.box_bytes;
   h->grid = P.grid;
   const size_t elem = h->mixed ? sizeof(float) : sizeof(double);
-  const size_t work_bytes = (size_t)nmpc_dev::NUM_WORK_ARRAYS * h->slab_max * elem;
+  const size_t work_bytes = (size_t)nmpc_dev::NUM_WORK_ARRAYS * h->slab_max * elem + h->box_bytes;
 
   bool ok = true;
   auto A = [&](cudaError_t e) { ok = ok && (e == cudaSuccess); };
@@ -689,6 +782,53 @@ int nmpc_iterate(nmpc_handle* h, const double* x0, const double* ref, const doub
   CK(cudaMemcpyAsync(lam_out, li, h->n_s * sizeof(double), cudaMemcpyDeviceToDevice, st));
   CK(cudaMemcpyAsync(u_out, ui, h->n_u * sizeof(double), cudaMemcpyDeviceToDevice, st));
   return NMPC_OK;
+}
+
+int nmpc_plant_step(nmpc_handle* h, double* w, double dt, int n_sub, double* u_rec,
+                    void* stream) {
+  if (!h || !w || !(dt >= 0) || n_sub < 1 || !h->has_state) return NMPC_ERR_BAD_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  // ping-pong through the handle's x0 staging buffer
+  for (int k = 0; k < n_sub; ++k) {
+    const bool even = (k % 2) == 0;
+    const double* win = even ? w : h->x0_d;
+    double* wout = even ? h->x0_d : w;
+    nmpc_dev::k_plant_substep<<<dim3(32, h->n_inst), 256, 0, st>>>(
+        h->inst_d, h->n_inst, h->act_d, win, wout, h->ub[2], (k == 0) ? u_rec : nullptr, dt,
+        n_sub);
+    h->launches++;
+    CK(cudaGetLastError());
+  }
+  if (n_sub % 2 == 1)
+    CK(cudaMemcpyAsync(w, h->x0_d, h->n_g * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return NMPC_OK;
+}
+
+int nmpc_closed_loop(nmpc_handle* h, double* w, const double* ref, int steps, int n_sub,
+                     double* u_hist, int* iters_hist, double* res_hist, void* stream) {
+  if (!h || !w || !ref || steps < 1 || n_sub < 1) return NMPC_ERR_BAD_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = h->n_inst;
+  std::vector<nmpc_stats> stats(n);
+  int rc_all = NMPC_OK;
+  for (int t = 0; t < steps; ++t) {
+    // the measured plant state is the next problem's x0
+    CK(cudaMemcpyAsync(h->x0_d, w, h->n_g * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(h->ref_d, ref, h->n_g * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    int rc = solve_core(h, 0, nullptr, (t == 0 && !h->has_state) ? NMPC_INIT_COLD : NMPC_INIT_SHIFT,
+                        nullptr, stats.data(), st);
+    if (rc == NMPC_ERR_BAD_ARG || rc == NMPC_ERR_CUDA) return rc;
+    if (rc != NMPC_OK && rc_all == NMPC_OK) rc_all = rc;
+    for (int b = 0; b < n; ++b) {
+      if (iters_hist) iters_hist[(size_t)t * n + b] = stats[b].iters;
+      if (res_hist) res_hist[(size_t)t * n + b] = stats[b].res_inf;
+    }
+    // the plant moves one sampling period h under the first-stage controls
+    int prc = nmpc_plant_step(h, w, 0.0, n_sub,
+                              u_hist ? u_hist + (size_t)t * h->nu_tot : nullptr, stream);
+    if (prc != NMPC_OK) return prc;
+  }
+  return rc_all;
 }
 
 int nmpc_get_state(nmpc_handle* h, double* x, double* u, double* lam, void* stream) {
@@ -856,12 +996,13 @@ extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
   const double dx = 1.0 / (d.mx + 1), dy = 1.0 / (d.my + 1);
   I.cx = 1.0 / (dx * dx);
   I.cy = (d.dim == 2) ? 1.0 / (dy * dy) : 0.0;
+  I.split_floor = split_floor_of(I);
   LaunchPlan P = plan_launch(&I, 1, N, o, mixed, std::max(1, num_sms), max_optin);
   const bool smem_mode = P.smem_mode;
   if (!smem_mode) P.grid = std::min(N, std::max(1, num_sms));
   const size_t elem = mixed ? sizeof(float) : sizeof(double);
-  const long long slab =
-      (long long)(((size_t)nmpc_dev::NUM_WORK_ARRAYS * P.slab_max * elem + 255) & ~size_t(255));
+  const long long slab = (long long)(((size_t)nmpc_dev::NUM_WORK_ARRAYS * P.slab_max * elem +
+                                      P.box_bytes + 255) & ~size_t(255));
 
   // workspace layout inside the static array
   size_t off = 0;
@@ -947,10 +1088,13 @@ extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
   A.full_all = mixed ? 0 : 1;
   A.csize = P.csize;
   A.slab_max = P.slab_max;
+  A.stage = P.stage ? 1 : 0;
+  A.local_u = P.local_u ? 1 : 0;
+  A.box_r = P.box_r;
   A.scratch = smem_mode ? nullptr : base + o_slab;
   A.scratch_stride = slab;
 
-  nmpc_dev::k_init_control<<<dim3(64, 1), 256, 0, st>>>(A, 1);
+  nmpc_dev::k_init_control<<<dim3(64, 1), 256, 0, st>>>(A, 0, 0, nullptr, nullptr, nullptr);
   CK(cudaGetLastError());
   long long launched = 0;
   int active = 1;

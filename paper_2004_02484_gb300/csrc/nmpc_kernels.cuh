@@ -32,7 +32,9 @@ namespace nmpc_dev {
 namespace cg = cooperative_groups;
 
 constexpr int RES_SLOTS = 16;    // rolling residual history per instance
+constexpr int STALL_WINDOW = 12; // < RES_SLOTS - 3: slot k-1-W is neither zeroed nor reused yet
 constexpr int NUM_WORK_ARRAYS = 11;
+constexpr int NUM_STAGE_ARRAYS = 5;  // float64 staging of x_i, lambda_i, x_{i-1}, lambda_{i+1}, ref
 constexpr int MAX_NU = 64;
 
 struct InstDev {
@@ -42,6 +44,7 @@ struct InstDev {
   long long u_off;  // offset in packed u
   long long g_off;  // offset in packed x0 / ref
   double h, q, r, qf, gamma, k0, k1, b0, cx, cy;
+  double split_floor;  // float32 rounding level of the split residual's O(h) terms
 };
 
 enum { MODE_SOLVE = 0, MODE_ONESHOT = 1 };
@@ -83,6 +86,9 @@ struct IterArgs {
   int resid_only;  // one-shot: residual norms only (float64)
   int full_all;    // every residual in float64 (FP64 precision)
   int csize;       // CTAs per work item (cluster size)
+  int stage;       // float64 slab inputs staged in shared memory (1) or read in place
+  int local_u;     // u-iteration through the actuators' local responses (1) or full sweeps
+  int box_r;       // half-width of a local-response box, 2 (n_lo - 1)
   int slab_max;    // cells per CTA slab (length of each shared work array)
   // lower-layer work arrays: shared memory (scratch == nullptr) or a global
   // slab of scratch_stride bytes per CTA
@@ -221,6 +227,8 @@ struct SmallShared {
   T b3[MAX_NU];
   T v3[MAX_NU];
   T b1a[MAX_NU];  // state-equation row K1 at each actuator cell (owner rank only)
+  T y4a[MAX_NU];  // lambda-part of Y(0) at each actuator cell
+  T v3n[MAX_NU];
   int act[MAX_NU];
   int skip;
   int full;
@@ -229,9 +237,17 @@ struct SmallShared {
 __device__ __forceinline__ double to_double(float v) { return f2d(v); }
 __device__ __forceinline__ double to_double(double v) { return v; }
 
+__device__ __forceinline__ void cp_async8(void* dst_smem, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
+}
+
+// gstage: NUM_STAGE_ARRAYS float64 slab arrays in shared memory, or nullptr
+// (global-slab mode: the stage is read from global memory in place).
 template <typename T>
 __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, bool full,
-                             bool resid_only, SmallShared<T>& sm, T* wk, const Cl& cl) {
+                             bool resid_only, SmallShared<T>& sm, T* wk, const Cl& cl,
+                             double* gstage) {
   const InstDev I = A.inst[b];
   const Slab sl = slab_of(I, cl.C, cl.rank);
   const int mx = I.mx, my = I.my, nu = I.nu, N = I.N, ng = I.ng;
@@ -267,15 +283,44 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
     sm.u[a] = Uin[I.u_off + (long long)s * nu + a];
     sm.v3[a] = T(0);
   }
-  __syncthreads();
+  // float64 inputs of this slab: x_i, lambda_i, x_{i-1} (x0 at the first stage),
+  // lambda_{i+1} (unused at the last stage) and ref, staged into shared memory by
+  // asynchronous copies that are all in flight at once; indexed by c - lo
+  const double *gx, *gl, *gxp, *gln, *grf;
+  if (gstage) {
+    const int SMd = A.slab_max;
+    double* sx = gstage;
+    double* sl_ = gstage + SMd;
+    double* sxp = gstage + 2 * SMd;
+    double* sln = gstage + 3 * SMd;
+    double* srf = gstage + 4 * SMd;
+    for (int c = sl.lo + threadIdx.x; c < sl.hi; c += blockDim.x) {
+      const int q = c - sl.lo;
+      cp_async8(sx + q, X + so + c);
+      cp_async8(sl_ + q, L + so + c);
+      cp_async8(sxp + q, (s == 0) ? x0 + c : X + so - ng + c);
+      if (!last) cp_async8(sln + q, L + so + ng + c);
+      cp_async8(srf + q, ref + c);
+    }
+    asm volatile("cp.async.wait_all;\n" ::);
+    gx = sx; gl = sl_; gxp = sxp; gln = sln; grf = srf;
+  } else {
+    gx = X + so + sl.lo;
+    gl = L + so + sl.lo;
+    gxp = ((s == 0) ? x0 : X + so - ng) + sl.lo;
+    gln = L + so + ng + sl.lo;
+    grf = ref + sl.lo;
+  }
+  if (full) cl.sync();  // neighbours' staged x, lambda are read below
+  else __syncthreads();
 
   // ---- P1 (split residual): float copies for the stencils ----
   if (!full) {
     const float k0f = (float)k0, k1h = (float)(0.5 * k1);
     for (int c = sl.lo + threadIdx.x; c < sl.hi; c += blockDim.x) {
-      const float xv = d2f(X[so + c]);
+      const float xv = d2f(gx[c - sl.lo]);
       xf[c - sl.lo] = xv;
-      lf[c - sl.lo] = d2f(L[so + c]);
+      lf[c - sl.lo] = d2f(gl[c - sl.lo]);
       pf[c - sl.lo] = k0f * (xv + k1h * xv * xv);
     }
     cl.sync();
@@ -292,26 +337,29 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
   for (int c = sl.lo + threadIdx.x; c < sl.hi; c += blockDim.x) {
     const int ix = c % mx, iy = c / mx;
     const int cl_ = c - sl.lo;
-    const double x = X[so + c];
-    const double lam = L[so + c];
-    const double xp = (s == 0) ? x0[c] : X[so - ng + c];
+    const double x = gx[cl_];
+    const double lam = gl[cl_];
+    const double xp = gxp[cl_];
+    const double rc_ = grf[cl_];
     T K1t, K3t, dpt, axt;
     if (full) {
-      const double ln = last ? hqf * (x - ref[c]) : L[so + ng + c];
+      const double ln = last ? hqf * (x - rc_) : gln[cl_];
       double srcd = 0.0;
       for (int a = 0; a < nu; ++a)
         if (sm.act[a] == c) srcd += sm.u[a];
       srcd *= b0;
-      const double* Xs = X + so;
-      const double* Ls = L + so;
-      const double nphi = nbr_sum<double>(c, ix, iy, mx, my, cx, cy,
-                                          [&](int m) { return phi_d(Xs[m], k0, k1); });
+      // staged slabs: neighbours from shared memory (other ranks through the
+      // cluster); in place: gx, gl address the global stage directly
+      auto nx = [&](int m) { return gstage ? ldn(gx, m, sl, cl) : gx[m - sl.lo]; };
+      auto nl = [&](int m) { return gstage ? ldn(gl, m, sl, cl) : gl[m - sl.lo]; };
+      const double nphi = nbr_sum<double>(
+          c, ix, iy, mx, my, cx, cy, [&](int m) { return phi_d(nx(m), k0, k1); });
       const double lphi = nphi - dcoef * phi_d(x, k0, k1);
       const double mu = nbr_sum<double>(c, ix, iy, mx, my, cx, cy,
-                                        [&](int m) { return Ls[m]; }) - dcoef * lam;
+                                        [&](int m) { return nl(m); }) - dcoef * lam;
       const double dphi = k0 * (1.0 + k1 * x);
       const double K1 = xp - x + h * (lphi + srcd);
-      const double K3 = ln - lam + h * (I.q * (x - ref[c]) + dphi * mu);
+      const double K3 = ln - lam + h * (I.q * (x - rc_) + dphi * mu);
       vmax = fmax(vmax, fmax(abs_or_inf(K1), abs_or_inf(K3)));
       vsq += K1 * K1 + K3 * K3;
       K1t = (T)K1;
@@ -325,7 +373,7 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
       const float mu = nbr_sum<float>(c, ix, iy, mx, my, cxf, cyf,
                                       [&](int m) { return ldn(lf, m, sl, cl); }) - dcf * lf[cl_];
       const float xv = xf[cl_];
-      const float rv = d2f(ref[c]);
+      const float rv = d2f(rc_);
       float srcf = 0.0f;
       for (int a = 0; a < nu; ++a)
         if (sm.act[a] == c) srcf += (float)sm.u[a];
@@ -334,7 +382,7 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
       const float t3 = hf * (qf_ * (xv - rv) + dphi * mu);
       // the O(1) differences in float64; at the last stage lambda_{N+1} is
       // h qf (x_N - ref), an O(h) term
-      const double d3 = last ? -lam : L[so + ng + c] - lam;
+      const double d3 = last ? -lam : gln[cl_] - lam;
       const float K1 = d2f(xp - x) + t1;
       const float K3 = d2f(d3) + t3 + (last ? hqff * (xv - rv) : 0.0f);
       fmax_ = fmaxf(fmax_, fmaxf(abs_or_inf_f(K1), abs_or_inf_f(K3)));
@@ -384,7 +432,8 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
   const int n_lo = A.n_lo;
   T* y5c = y5;
   T* y4c = y4;
-  for (int it = 0; it <= A.n_u_it; ++it) {
+  const int n_full = A.local_u ? 1 : A.n_u_it + 1;  // full-field Y applications
+  for (int it = 0; it < n_full; ++it) {
     if (it > 0) {
       // c4 = F_u v3 - K1 changes only on actuator cells: refresh v1, p1 there
       for (int a = threadIdx.x; a < nu; a += blockDim.x) {
@@ -457,12 +506,122 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
     }
     y4c = cur;
     cl.sync();
-    if (it < A.n_u_it) {
+    if (!A.local_u && it < A.n_u_it) {
       // A_uu v3 = K2 + F_u^T y_lambda (A_ux = 0); every rank keeps all of v3
       for (int a = threadIdx.x; a < nu; a += blockDim.x)
         sm.v3[a] = (sm.b3[a] + th * tb0 * ldn(y4c, sm.act[a], sl, cl)) / auu;
       __syncthreads();
     }
+  }
+  if (A.local_u) {
+    // Y(v3) = Y(0) + sum_b v3_b Z(e_b), Z(e_b) = P^{-1}(F_u e_b, 0): the fixed
+    // sweeps are linear and Z(e_b) vanishes outside a box of half-width
+    // R = 2 (n_lo - 1) around actuator b (each sweep reaches one cell further).
+    // The u-iteration then needs Y(0) at the actuator cells and the boxes.
+    for (int a = threadIdx.x; a < nu; a += blockDim.x) sm.y4a[a] = ldn(y4c, sm.act[a], sl, cl);
+    const int R = A.box_r;
+    const int Sx = 2 * R + 1, Sy = (I.dim == 2) ? 2 * R + 1 : 1, Ry = (I.dim == 2) ? R : 0;
+    const int S2 = Sx * Sy;
+    T* boxes = wk + (size_t)NUM_WORK_ARRAYS * SM;
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int bb = threadIdx.x >> 5; bb < nu; bb += nw) {
+      T* z5 = boxes + (size_t)bb * 4 * S2;
+      T* z4 = z5 + S2;
+      T* t0 = z5 + 2 * S2;
+      T* t1 = z5 + 3 * S2;
+      const int ca = sm.act[bb], ixb = ca % mx, iyb = ca / mx;
+      auto cell = [&](int j, int i, int& c) {
+        const int gy = iyb + j - Ry, gx = ixb + i - R;
+        c = gy * mx + gx;
+        return gx >= 0 && gx < mx && gy >= 0 && gy < my;
+      };
+      // off-diagonal stencil of a box field v at box cell (j, i), weight on the neighbour
+      auto boxnbr = [&](const T* v, int j, int i, bool with_dp) {
+        T sx = T(0), sy = T(0);
+        int c;
+        if (i > 0 && cell(j, i - 1, c)) sx += (with_dp ? ldn(dp, c, sl, cl) : T(1)) * v[j * Sx + i - 1];
+        if (i < Sx - 1 && cell(j, i + 1, c)) sx += (with_dp ? ldn(dp, c, sl, cl) : T(1)) * v[j * Sx + i + 1];
+        if (j > 0 && cell(j - 1, i, c)) sy += (with_dp ? ldn(dp, c, sl, cl) : T(1)) * v[(j - 1) * Sx + i];
+        if (j < Sy - 1 && cell(j + 1, i, c)) sy += (with_dp ? ldn(dp, c, sl, cl) : T(1)) * v[(j + 1) * Sx + i];
+        return tcx * sx + tcy * sy;
+      };
+      const T v1c = th * tb0 * ldn(rg, ca, sl, cl);  // first F_x sweep: D^{-1} h b0 e_b
+      for (int q = lane; q < S2; q += 32) t0[q] = (q == Ry * Sx + R) ? v1c : T(0);
+      __syncwarp();
+      T* cur = t0;
+      T* nxt = t1;
+      for (int sw = 1; sw < n_lo; ++sw) {
+        for (int q = lane; q < S2; q += 32) {
+          const int j = q / Sx, i = q % Sx;
+          int c;
+          T v = T(0);
+          if (cell(j, i, c)) v = ((q == Ry * Sx + R) ? v1c : T(0)) - ldn(rg, c, sl, cl) * th * boxnbr(cur, j, i, true);
+          nxt[q] = v;
+        }
+        __syncwarp();
+        T* t = cur; cur = nxt; nxt = t;
+      }
+      for (int q = lane; q < S2; q += 32) z5[q] = cur[q];
+      __syncwarp();
+      // F_x^T sweeps with right-hand side -A_xx z5: w^1 stays in t0; the
+      // n_lo - 1 later sweeps alternate between t1 and z4, the last one in z4
+      for (int q = lane; q < S2; q += 32) {
+        const int j = q / Sx, i = q % Sx;
+        int c;
+        t0[q] = cell(j, i, c) ? -ldn(ax, c, sl, cl) * z5[q] * ldn(rg, c, sl, cl) : T(0);
+      }
+      __syncwarp();
+      if (n_lo == 1) {
+        for (int q = lane; q < S2; q += 32) z4[q] = t0[q];
+      } else {
+        const T* src = t0;
+        for (int sw = 1; sw < n_lo; ++sw) {
+          T* dst = (((n_lo - 1 - sw) & 1) == 0) ? z4 : t1;
+          for (int q = lane; q < S2; q += 32) {
+            const int j = q / Sx, i = q % Sx;
+            int c;
+            T v = T(0);
+            if (cell(j, i, c))
+              v = t0[q] - ldn(rg, c, sl, cl) * th * ldn(dp, c, sl, cl) * boxnbr(src, j, i, false);
+            dst[q] = v;
+          }
+          __syncwarp();
+          src = dst;
+        }
+      }
+      __syncwarp();
+    }
+    cl.sync();  // boxes ready; every rank has read Y(0) at the actuator cells
+    // u fixed-point iteration on n_u numbers: y_lambda(act_a) = Y(0) + sum_b G_ab v3_b
+    for (int it = 0; it < A.n_u_it; ++it) {
+      for (int a = threadIdx.x; a < nu; a += blockDim.x) {
+        T y = sm.y4a[a];
+        const int ca = sm.act[a], ixa = ca % mx, iya = ca / mx;
+        for (int bb = 0; bb < nu; ++bb) {
+          const int cb = sm.act[bb];
+          const int di = ixa - cb % mx + R, dj = iya - cb / mx + Ry;
+          if (di >= 0 && di < Sx && dj >= 0 && dj < Sy)
+            y += sm.v3[bb] * boxes[(size_t)bb * 4 * S2 + S2 + dj * Sx + di];
+        }
+        sm.v3n[a] = (sm.b3[a] + th * tb0 * y) / auu;
+      }
+      __syncthreads();
+      for (int a = threadIdx.x; a < nu; a += blockDim.x) sm.v3[a] = sm.v3n[a];
+      __syncthreads();
+    }
+    // Y(v3) = Y(0) + sum_b v3_b Z(e_b) on this rank's cells
+    for (int e = threadIdx.x; e < nu * S2; e += blockDim.x) {
+      const int bb = e / S2, q = e % S2;
+      const int cb = sm.act[bb];
+      const int gy = cb / mx + q / Sx - Ry, gx = cb % mx + q % Sx - R;
+      if (gx < 0 || gx >= mx || gy < 0 || gy >= my) continue;
+      const int c = gy * mx + gx;
+      if (c < sl.lo || c >= sl.hi) continue;
+      const T* z5 = boxes + (size_t)bb * 4 * S2;
+      atomicAdd(&y5c[c - sl.lo], sm.v3[bb] * z5[q]);
+      atomicAdd(&y4c[c - sl.lo], sm.v3[bb] * z5[S2 + q]);
+    }
+    __syncthreads();
   }
   // back-solve (eq. 23b): (v1, v2) = P^{-1}(K1 - F_u v3, K3) = -Y(v3)
 
@@ -473,8 +632,8 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
   double* Uo = A.uout[rd ^ 1];
   for (int c = sl.lo + threadIdx.x; c < sl.hi; c += blockDim.x) {
     const int q = c - sl.lo;
-    Xo[so + c] = fma(alpha, to_double(y5c[q]), X[so + c]);
-    Lo[so + c] = fma(alpha, to_double(y4c[q]), L[so + c]);
+    Xo[so + c] = fma(alpha, to_double(y5c[q]), gx[q]);
+    Lo[so + c] = fma(alpha, to_double(y4c[q]), gl[q]);
   }
   if (cl.rank == 0)
     for (int a = threadIdx.x; a < nu; a += blockDim.x)
@@ -482,14 +641,21 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
   cl.sync();
 }
 
+__device__ __forceinline__ double I_split_floor(const IterArgs& A, int b) {
+  return A.inst[b].split_floor;
+}
+
 template <typename T, int MODE>
 __global__ void __launch_bounds__(512) k_iterate(IterArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmallShared<T>& sm = *reinterpret_cast<SmallShared<T>*>(smem_raw);
   T* wk;
+  double* gstage = nullptr;
   if (A.scratch == nullptr) {
     const size_t off = (sizeof(SmallShared<T>) + 15) & ~size_t(15);
-    wk = reinterpret_cast<T*>(smem_raw + off);
+    gstage = A.stage ? reinterpret_cast<double*>(smem_raw + off) : nullptr;
+    wk = reinterpret_cast<T*>(
+        smem_raw + off + (A.stage ? (size_t)NUM_STAGE_ARRAYS * A.slab_max * sizeof(double) : 0));
   } else {
     wk = reinterpret_cast<T*>(A.scratch + (long long)blockIdx.x * A.scratch_stride);
   }
@@ -526,7 +692,19 @@ __global__ void __launch_bounds__(512) k_iterate(IterArgs A) {
             const bool prev_full = (k - 1 >= ffrom) || (k == 1 && f0);
             if (!(r <= 1.79e308) || r > A.div_limit * fmax(r0, 1e-300)) st = ST_DIVERGED;
             else if (prev_full && r <= A.tol) st = ST_CONVERGED;
-            else if (!prev_full && r <= fmax(A.tol, A.split_min)) switch_now = true;
+            else if (!prev_full) {
+              // leave the split residual once it is near its float32 floor:
+              // below the threshold, or stalled (no 2x progress over the window)
+              // within 100x of it (the early transient is far above)
+              const double thr = fmax(fmax(A.tol, A.split_min), I_split_floor(A, b));
+              if (r <= thr) {
+                switch_now = true;
+              } else if (k - 1 >= STALL_WINDOW && r <= 100.0 * thr) {
+                const int oslot = ((k - 1 - STALL_WINDOW) % RES_SLOTS) * A.n_inst + b;
+                const double ro = __longlong_as_double((long long)A.res_inf[oslot]);
+                if (r > 0.5 * ro) switch_now = true;
+              }
+            }
           }
           if (st != ST_RUNNING) {
             skip = 1;
@@ -560,7 +738,7 @@ __global__ void __launch_bounds__(512) k_iterate(IterArgs A) {
       resid_only = (k == A.max_iter);
     }
     process_item<T>(A, b, s, k, (MODE == MODE_SOLVE) ? (k & 1) : 0, full, resid_only, sm, wk,
-                    cl);
+                    cl, gstage);
   }
 
   if (MODE == MODE_SOLVE) {
@@ -577,8 +755,13 @@ __global__ void __launch_bounds__(512) k_iterate(IterArgs A) {
   }
 }
 
-// Reset the per-instance control and write S^0 (cold start) into buffer 0.
-__global__ void k_init_control(IterArgs A, int cold) {
+// Reset the per-instance control and write S^0 into buffer 0: the cold start
+// (mode 0), nothing (mode 1: buffer 0 already holds S^0) or the current state
+// shifted by one stage with the last stage repeated (mode 2; receding
+// horizon, the paper's closed loop).  first_full: iteration 0 evaluates the
+// float64 residual (warm starts that may already be converged).
+__global__ void k_init_control(IterArgs A, int mode, int first_full, const double* xc,
+                               const double* uc, const double* lc) {
   const int b = blockIdx.y;
   if (b >= A.n_inst) return;
   const InstDev I = A.inst[b];
@@ -594,27 +777,73 @@ __global__ void k_init_control(IterArgs A, int cold) {
     A.fin_inf[b] = 0.0;
     A.fin_2[b] = 0.0;
     A.full_from[b] = A.full_all ? 0 : 0x7fffffff;
-    A.full0[b] = cold ? 0 : 1;  // a warm start may already be converged
+    A.full0[b] = first_full;
     if (b == 0) {
       *A.n_active = A.n_inst;
       *A.iter_k = 0;
       *A.block_done = 0;
     }
   }
-  if (!cold) return;
+  if (mode == 1) return;
   const long long n = (long long)I.N * I.ng;
   double* X = A.xout[0];
   double* L = A.lout[0];
   double* U = A.uout[0];
+  const long long nu_all = (long long)I.N * I.nu;
+  if (mode == 0) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+      X[I.s_off + e] = A.x0[I.g_off + (e % I.ng)];
+      L[I.s_off + e] = 0.0;
+    }
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nu_all;
+         e += (long long)gridDim.x * blockDim.x)
+      U[I.u_off + e] = 0.0;
+    return;
+  }
+  // shift: stage i takes stage i+1 of the current state; the last is repeated
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x) {
-    X[I.s_off + e] = A.x0[I.g_off + (e % I.ng)];
-    L[I.s_off + e] = 0.0;
+    const long long i = e / I.ng;
+    const long long src = (i + 1 < I.N) ? e + I.ng : e;
+    X[I.s_off + e] = xc[I.s_off + src];
+    L[I.s_off + e] = lc[I.s_off + src];
   }
-  const long long nu_all = (long long)I.N * I.nu;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nu_all;
-       e += (long long)gridDim.x * blockDim.x)
-    U[I.u_off + e] = 0.0;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / I.nu;
+    U[I.u_off + e] = uc[I.u_off + ((i + 1 < I.N) ? e + I.nu : e)];
+  }
+}
+
+// One explicit-Euler sub-step of the plant for every instance:
+//   w_out = w_in + (dt / n_sub) (Lap Phi(w_in) + b0 B u_1),
+// u_1 the first-stage controls of the current solution (u_cur).  Optionally
+// records u_1 into u_rec (packed [sum n_u]).
+__global__ void k_plant_substep(const InstDev* inst, int n_inst, const int* act,
+                                const double* w_in, double* w_out, const double* u_cur,
+                                double* u_rec, double dt_all, int n_sub) {
+  const int b = blockIdx.y;
+  if (b >= n_inst) return;
+  const InstDev I = inst[b];
+  // each instance's sampling period is its own stage length unless dt_all > 0
+  const double dt = ((dt_all > 0.0) ? dt_all : I.h) / n_sub;
+  const double* wi = w_in + I.g_off;
+  const double cx = I.cx, cy = I.cy, k0 = I.k0, k1 = I.k1;
+  const double dc = 2.0 * (cx + cy);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < I.ng; c += gridDim.x * blockDim.x) {
+    const int ix = c % I.mx, iy = c / I.mx;
+    double src = 0.0;
+    for (int a = 0; a < I.nu; ++a)
+      if (act[I.act_off + a] == c) src += u_cur[I.u_off + a];
+    const double lphi = nbr_sum<double>(c, ix, iy, I.mx, I.my, cx, cy,
+                                        [&](int m) { return phi_d(wi[m], k0, k1); }) -
+                        dc * phi_d(wi[c], k0, k1);
+    w_out[I.g_off + c] = wi[c] + dt * (lphi + I.b0 * src);
+  }
+  if (u_rec && blockIdx.x == 0)
+    for (int a = threadIdx.x; a < I.nu; a += blockDim.x)
+      u_rec[I.act_off + a] = u_cur[I.u_off + a];
 }
 
 // After the iteration chunks: settle instances still running at max_iter,

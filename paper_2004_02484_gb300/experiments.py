@@ -1,0 +1,110 @@
+"""Measurements of the batched and closed-loop workloads (GPU).
+
+    python -m paper_2004_02484_gb300.experiments batch1d   [--n 1024]
+    python -m paper_2004_02484_gb300.experiments closedloop [--n 64 --steps 200 --grid 256]
+
+batch1d:    the ragged 1D batch (M ~ U{32..256}, N ~ U{10..60}, n_u ~ U{1..4},
+            R = 10^U[-3,-1]) solved in one handle, mixed precision, to
+            ||K||_inf <= 1e-6; reports solves/s and iterations.
+closedloop: the 2D 256x256, N = 100, 16-actuator batch in a receding-horizon
+            loop (shifted warm starts, explicit-Euler plant), mixed precision;
+            reports solves/s (instances x steps / time), iterations per step,
+            the iteration kernel's algorithmic HBM bandwidth and, with
+            --check, the float64 residual of sampled returned states.
+Prints one JSON line per experiment.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import nmpc as G
+from . import workloads as wl
+
+BYTES_PER_CELL_STAGE = 32  # read x, lambda; write x, lambda (float64)
+
+
+def batch1d(n: int, tol: float = 1e-6, reps: int = 3):
+    import torch
+    insts = wl.heat1d_ragged_batch(n)
+    s = G.Solver(insts, tol=tol, precision=G.NMPC_MIXED, max_iter=20000)
+    rc, st = s.solve()
+    assert rc == G.NMPC_OK, rc
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        rc, st = s.solve()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / reps
+    its = np.array([st[b].iters for b in range(n)])
+    cells = sum(i.mx * i.horizon for i in insts)
+    out = {"experiment": "batch1d", "instances": n, "s_per_batch": dt, "solves_per_s": n / dt,
+           "iters_mean": float(its.mean()), "iters_max": int(its.max()),
+           "cell_stages": cells, "launches": G.nmpc_launch_count(s.h)}
+    s.close()
+    return out
+
+
+def closedloop(n: int, steps: int, grid: int, horizon: int, n_sub: int, check: int,
+               **opts):
+    import torch
+    insts = wl.heat2d_large_batch(n=n, m=grid, horizon=horizon)
+    s = G.Solver(insts, tol=1e-6, precision=G.NMPC_MIXED, max_iter=4000, **opts)
+    w = s.x0.clone()
+    nu_tot = sum(len(i.act) for i in insts)
+    u_hist = torch.zeros(steps * nu_tot, dtype=torch.float64, device="cuda")
+    l0 = G.nmpc_launch_count(s.h)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, iters, res = G.nmpc_closed_loop(s.h, w, s.ref, steps, n_sub, n, u_hist)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    launches = G.nmpc_launch_count(s.h) - l0
+    iter_launches = int(iters.max(axis=1).sum() + steps)  # kernels that did work (approx.)
+    cells = n * horizon * grid * grid
+    out = {"experiment": "closedloop", "instances": n, "steps": steps, "grid": grid,
+           "horizon": horizon, "rc": rc, "s_total": dt, "solves_per_s": n * steps / dt,
+           "iters_first_step_mean": float(iters[0].mean()),
+           "iters_later_mean": float(iters[1:].mean()) if steps > 1 else None,
+           "res_max": float(res.max()), "launches": launches,
+           "hbm_gbs_algorithmic": BYTES_PER_CELL_STAGE * cells * iter_launches / dt / 1e9}
+    if check:
+        # one more solve from the final plant state, then its float64 residual
+        rc2, st = G.nmpc_solve(s.h, w, s.ref, s.u, n, init=G.NMPC_INIT_SHIFT)
+        x, u, lam = s.state()
+        r = G.nmpc_residual(s.h, w, s.ref, x, u, lam, n)
+        out["float64_residual_max_recomputed"] = float(r[:, 0].max())
+    s.close()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("which", choices=["batch1d", "closedloop"])
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--grid", type=int, default=256)
+    ap.add_argument("--horizon", type=int, default=100)
+    ap.add_argument("--n-sub", type=int, default=2)
+    ap.add_argument("--check", type=int, default=1)
+    ap.add_argument("--cluster", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0)
+    a = ap.parse_args()
+    import torch
+    torch.cuda.set_device(0)
+    from . import build
+    build.build()
+    if a.which == "batch1d":
+        print(json.dumps(batch1d(a.n or 1024)), flush=True)
+    else:
+        res = closedloop(a.n or 64, a.steps, a.grid, a.horizon, a.n_sub, a.check,
+                         cluster=a.cluster, threads=a.threads)
+        res.update({"cluster": a.cluster, "threads": a.threads})
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -27,6 +27,8 @@ NMPC_FP64 = 0
 NMPC_MIXED = 1
 NMPC_INIT_COLD = 0
 NMPC_INIT_WARM = 1
+NMPC_INIT_GUESS = 2
+NMPC_INIT_SHIFT = 3
 NMPC_STATUS_CONVERGED = 1
 NMPC_STATUS_DIVERGED = 2
 NMPC_STATUS_MAX_ITER = 3
@@ -47,7 +49,7 @@ class nmpc_opts(ctypes.Structure):
                 ("check_every", ctypes.c_int), ("alpha", ctypes.c_double),
                 ("div_limit", ctypes.c_double), ("threads", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("cluster", ctypes.c_int),
-                ("split_min", ctypes.c_double)]
+                ("split_min", ctypes.c_double), ("u_local", ctypes.c_int)]
 
 
 class nmpc_stats(ctypes.Structure):
@@ -58,7 +60,7 @@ class nmpc_stats(ctypes.Structure):
 EXPORTED = ["nmpc_default_opts", "nmpc_setup", "nmpc_solve", "nmpc_solve_host",
             "nmpc_residual", "nmpc_iterate", "nmpc_get_state", "nmpc_set_state",
             "nmpc_sizes", "nmpc_launch_count", "nmpc_destroy", "nmpc_strerror",
-            "nmpc_solve_noalloc"]
+            "nmpc_solve_noalloc", "nmpc_plant_step", "nmpc_closed_loop"]
 
 
 def _load() -> ctypes.CDLL:
@@ -84,6 +86,8 @@ def _load() -> ctypes.CDLL:
         "nmpc_strerror": (ctypes.c_char_p, [I]),
         "nmpc_solve_noalloc": (I, [ctypes.POINTER(nmpc_desc), ctypes.POINTER(nmpc_opts), P, P,
                                    P, ctypes.POINTER(nmpc_stats), P]),
+        "nmpc_plant_step": (I, [P, P, D, I, P, P]),
+        "nmpc_closed_loop": (I, [P, P, P, I, I, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -207,6 +211,22 @@ def nmpc_get_state(h, x, u, lam, stream=None):
 
 def nmpc_set_state(h, x, u, lam, stream=None):
     _check(LIB.nmpc_set_state(h, _ptr(x), _ptr(u), _ptr(lam), _stream(stream)), "nmpc_set_state")
+
+
+def nmpc_plant_step(h, w, dt: float, n_sub: int, u_rec=None, stream=None):
+    _check(LIB.nmpc_plant_step(h, _ptr(w), dt, n_sub, _ptr(u_rec), _stream(stream)),
+           "nmpc_plant_step")
+
+
+def nmpc_closed_loop(h, w, ref, steps: int, n_sub: int, n_inst: int, u_hist=None,
+                     stream=None):
+    """Returns (rc, iters [steps, n], res [steps, n])."""
+    iters = np.zeros((steps, n_inst), dtype=np.int32)
+    res = np.zeros((steps, n_inst), dtype=np.float64)
+    rc = LIB.nmpc_closed_loop(h, _ptr(w), _ptr(ref), steps, n_sub, _ptr(u_hist),
+                              iters.ctypes.data, res.ctypes.data, _stream(stream))
+    _check(rc, "nmpc_closed_loop", allow=(NMPC_ERR_NOT_CONVERGED, NMPC_ERR_DIVERGED))
+    return rc, iters, res
 
 
 def nmpc_launch_count(h) -> int:

@@ -36,8 +36,9 @@ def _f(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
 
 
-@pytest.mark.parametrize("M_,N_,K_", [(1, 8, 8), (37, 130, 72), (128, 128, 32), (256, 512, 8192),
-                                      (300, 6800, 512), (512, 64, 4096)])
+@pytest.mark.parametrize("M_,N_,K_", [(1, 8, 8), (1, 512, 8192), (5, 6800, 512), (8, 13, 24),
+                                      (9, 130, 72), (37, 130, 72), (128, 128, 32),
+                                      (256, 512, 8192), (300, 6800, 512), (512, 64, 4096)])
 @pytest.mark.parametrize("gelu", [False, True])
 def test_gemm_matches_oracle(GM, M_, N_, K_, gelu):
     import torch

@@ -276,6 +276,24 @@ CLUSTER_CASES = {
 }
 
 
+def test_large_stage_without_staging_matches_oracle(G):
+    """A 256x256 stage (16-CTA cluster, slab inputs read in place, not staged)
+    and a one-CTA global-slab stage in FP64: one iteration each vs the oracle."""
+    for prec in (G.NMPC_MIXED, G.NMPC_FP64):
+        insts = [wl.heat2d(256, 256, 3, 4, 4, seed=61)]
+        state, lists = _rand_state(insts, 62)
+        gpu, res = _iterate_gpu(G, insts, state, 1, precision=prec)
+        ora, norms = _oracle_iterate(insts, lists, 1)
+        if prec == G.NMPC_FP64:
+            _cmp_iterates(G, insts, gpu, ora, 1e-10)
+        else:
+            gx, gu, gl = _unpack(G, insts, *gpu)
+            X, U, L = ora[0]
+            d_or = X - lists[0][0].reshape(X.shape)
+            assert np.abs((gx[0] - lists[0][0].reshape(X.shape)) - d_or).max() <= \
+                1e-4 * np.abs(d_or).max()
+
+
 @pytest.mark.parametrize("cluster", [2, 3, 5, 8, 16])
 @pytest.mark.parametrize("case", list(CLUSTER_CASES))
 def test_cluster_split_stage_matches_oracle(G, case, cluster):
@@ -288,13 +306,18 @@ def test_cluster_split_stage_matches_oracle(G, case, cluster):
     _cmp_iterates(G, insts, gpu, ora, 1e-10)
 
 
-@pytest.mark.parametrize("n_lo,n_u_it", [(1, 1), (1, 2), (3, 2), (4, 3), (2, 1), (2, 3)])
+@pytest.mark.parametrize("n_lo,n_u_it", [(1, 1), (1, 2), (3, 2), (4, 3), (2, 1), (2, 3), (5, 2)])
 @pytest.mark.parametrize("cluster", [1, 3])
-def test_inner_iteration_counts_match_oracle(G, n_lo, n_u_it, cluster):
-    insts = [wl.heat2d(12, 14, 5, 2, 2, seed=31), wl.heat1d(33, 4, 3, 0.05, seed=32)]
+@pytest.mark.parametrize("u_local", [1, 0])
+def test_inner_iteration_counts_match_oracle(G, n_lo, n_u_it, cluster, u_local):
+    """Both lower-layer orders (local actuator responses, literal full sweeps)
+    give the oracle's iterate; actuators 2 cells apart make the responses
+    overlap."""
+    insts = [wl.heat2d(12, 14, 5, 2, 2, seed=31), wl.heat1d(33, 4, 3, 0.05, seed=32),
+             wl.heat1d(20, 3, 2, 0.02, seed=34, act_pos=[0.45, 0.55])]
     state, lists = _rand_state(insts, 33)
     gpu, _ = _iterate_gpu(G, insts, state, 2, precision=G.NMPC_FP64, n_lo=n_lo,
-                          n_u_it=n_u_it, cluster=cluster)
+                          n_u_it=n_u_it, cluster=cluster, u_local=u_local)
     out = []
     for b, inst in enumerate(insts):
         p = O.Problem(inst)
@@ -324,3 +347,17 @@ def test_mixed_solve_certifies_with_a_float64_residual(G, cluster):
     U = u.cpu().numpy().reshape(p.N, -1)
     assert O.kkt_norms(*O.kkt(p, X, U, L))[0] <= 1e-7
     s.close()
+
+
+def test_mixed_reaches_tight_tolerance_above_the_split_floor(G):
+    """1D M=256, h=1e-4: the split residual's float32 floor (~1e-7) is above
+    tol = 1e-8; the solve must switch to the float64 residual and converge to
+    the oracle's root."""
+    insts = [wl.heat1d(256, 20, 4, 1e-3, seed=71), wl.heat1d(200, 12, 2, 0.05, seed=72)]
+    rc, st, u, _ = _solve_gpu(G, insts, tol=1e-8, precision=G.NMPC_MIXED, max_iter=20000)
+    assert rc == G.NMPC_OK and all(s_[2] <= 1e-8 for s_ in st)
+    ug = G.split_stages(insts, u, "nu")
+    for b, inst in enumerate(insts):
+        p = O.Problem(inst)
+        (X, U, L), info = O.solve_jacobi(p, tol=1e-10, max_iter=50000)
+        assert np.abs(ug[b] - U).max() <= 1e-4 * np.abs(U).max()

@@ -1,0 +1,74 @@
+"""Learned warm start (GPU): POD basis, training on solver-generated data, and
+the gain in upper-layer iterations over the cold start at equal residual."""
+import numpy as np
+import pytest
+
+from oracle import nmpc as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def WS():
+    from paper_2004_02484_gb300 import build as b
+    b.build()
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2004_02484_gb300 import warmstart as WS
+    return WS
+
+
+def test_pod_basis_recovers_a_low_dimensional_subspace(WS):
+    rng = np.random.default_rng(0)
+    basis, _ = np.linalg.qr(rng.standard_normal((4096, 8)))
+    snaps = rng.standard_normal((600, 8)) @ basis.T
+    V = WS.pod_basis(snaps, 8)
+    np.testing.assert_allclose(V.T @ V, np.eye(8), atol=1e-5)
+    # the span is recovered to BF16 accuracy (operands rounded to 8 bits)
+    resid = snaps - (snaps @ V) @ V.T
+    assert np.linalg.norm(resid) / np.linalg.norm(snaps) < 2e-2
+
+
+@pytest.fixture(scope="module")
+def trained(WS):
+    from paper_2004_02484_gb300 import workloads as wl
+    data = WS.generate(list(range(1_000_000, 1_001_024)), batch=128)
+    ws = WS.LearnedWarmStart(wl.heat2d_learning_instance(1_000_000), rank=64)
+    losses = ws.fit(data, steps=800, lr=1e-3)
+    return ws, losses
+
+
+def test_training_loss_falls(trained):
+    ws, losses = trained
+    assert losses[-1] < 0.1 * losses[0]
+
+
+def test_learned_start_cuts_iterations_at_equal_residual(WS, trained):
+    import torch
+    from paper_2004_02484_gb300 import nmpc as G
+    from paper_2004_02484_gb300 import workloads as wl
+    ws, _ = trained
+    its_c, its_l = [], []
+    for s in range(2_000_000, 2_000_012):
+        inst = wl.heat2d_learning_instance(s)
+        sol = G.Solver([inst], tol=1e-6, precision=G.NMPC_MIXED)
+        rc, st = sol.solve(init=G.NMPC_INIT_COLD)
+        uc = sol.u.cpu().numpy().copy()
+        rc2, st2, used = ws.solve(sol, check_residual=True)
+        ul = sol.u.cpu().numpy()
+        assert rc == G.NMPC_OK and rc2 == G.NMPC_OK
+        assert st[0].res_inf <= 1e-6 and st2[0].res_inf <= 1e-6 and used == "learned"
+        # both are roots to the same tolerance: controls agree at the FP32-path bar
+        assert np.abs(ul - uc).max() <= 1e-3 * np.abs(uc).max()
+        # the float64 residual of the returned state, recomputed by the oracle
+        if s == 2_000_000:
+            x, u, lam = sol.state()
+            p = O.Problem(inst)
+            X = x.cpu().numpy().reshape((p.N,) + p.shape)
+            L = lam.cpu().numpy().reshape((p.N,) + p.shape)
+            U = u.cpu().numpy().reshape(p.N, -1)
+            assert O.kkt_norms(*O.kkt(p, X, U, L))[0] <= 1e-6
+        its_c.append(st[0].iters)
+        its_l.append(st2[0].iters)
+        sol.close()
+    assert np.mean(its_l) <= 0.85 * np.mean(its_c), (its_c, its_l)
