@@ -97,17 +97,22 @@ typedef struct {
   int use_graph;   /* capture the iteration chunk in a CUDA graph (1) or not  */
   int cluster;     /* CTAs per stage (1..8 or 16, a thread-block cluster that
                       splits the stage grid); 0 = auto                        */
-  double split_min;/* NMPC_MIXED: iterations whose previous residual is above
-                      max(tol, split_min) evaluate K with float64 differences
-                      and float32 O(h) terms; from the first one below, every
-                      iteration uses the float64 residual (convergence is only
-                      ever declared on a float64 residual)                    */
+  double split_min;/* NMPC_MIXED: iterations evaluate K with float64
+                      differences and float32 O(h) terms (the split residual,
+                      with a computed bound e on its rounding error) while the
+                      previous split residual r has r - e > max(tol,
+                      split_min); from then on every iteration uses the
+                      float64 residual (convergence is only ever declared on
+                      a float64 residual)                                     */
   int u_local;     /* 1: the u-iteration uses the actuators' local responses
                       (P^{-1} is a fixed linear map, so Y(v3) = Y(0) + sum_b
                       v3_b Z(e_b) with Z(e_b) zero outside 2(n_lo-1) cells of
                       actuator b; one full-field P^{-1} per iteration) when
                       n_lo <= 4 and the boxes fit; 0: n_u_it + 1 full-field
                       P^{-1} applications in the paper's literal order        */
+  int cells;       /* cells each thread carries through a pass at once, as
+                      independent dependency chains: 2 (CTAs of up to 512
+                      threads) or 4 (up to 384 threads); 0 = auto (2)        */
 } nmpc_opts;
 
 typedef struct {
@@ -121,7 +126,7 @@ typedef struct nmpc_handle nmpc_handle;
 
 /* Fill *o with defaults: tol 1e-6, max_iter 2000, n_lo 2, n_u_it 2, FP64,
    check_every 16, alpha 1, div_limit 1e8, threads auto, graph on, cluster
-   auto, split_min 1e-7, u_local 1. */
+   auto, split_min 1e-7, u_local 1, cells auto. */
 void nmpc_default_opts(nmpc_opts* o);
 
 /* Validate the descriptors, build the device instance table and allocate the

@@ -6,7 +6,9 @@ converges: CTAs per stage (thread-block cluster size), threads per CTA,
 iterations per host poll (graph chunk length), lower-layer sweeps n_lo and
 u-iterations n_u_it.  The KKT root does not depend on these (the lower layer
 is a fixed linear approximation of D_i^{-1} and the iteration's fixed point
-is K(S) = 0), only the iteration count and the time per iteration do.
+is K(S) = 0), only the iteration count and the time per iteration do.  The
+u-iteration's form (through the actuators' local responses or full-field
+sweeps) is a candidate as well.
 
 Results are cached in a JSON file keyed by a bucketed signature of the batch
 (dimension, grid size, horizon, actuators, batch size, precision).
@@ -41,12 +43,16 @@ def signature(instances: Sequence, precision: int) -> str:
 
 def candidates(instances: Sequence, quick: bool = True) -> List[Dict]:
     ngmax = max(i.mx * i.my for i in instances)
-    clusters = [0, 1] if ngmax < 1024 else [0, 1, 2, 4]
-    threads = [0, 128, 256] if quick else [0, 64, 128, 256, 512]
-    inner = [(2, 2), (2, 1), (1, 2), (3, 2)] if not quick else [(2, 2), (2, 1)]
+    clusters = [0, 1] if ngmax < 1024 else [0, 2, 4, 8]
+    threads = [0, 256] if quick else [0, 64, 128, 256, 512]
+    inner = [(2, 2), (2, 1), (2, 3), (1, 2), (3, 2)] if not quick else [(2, 2), (2, 1)]
     out = []
-    for c, t, (nlo, nut), ce in itertools.product(clusters, threads, inner, (16, 32)):
-        out.append({"cluster": c, "threads": t, "n_lo": nlo, "n_u_it": nut, "check_every": ce})
+    cells = (0,) if quick else (0, 4)
+    for c, t, (nlo, nut), ul, ce in itertools.product(clusters, threads, inner, (1, 0), cells):
+        if ce == 4 and t > 384:
+            continue
+        out.append({"cluster": c, "threads": t, "n_lo": nlo, "n_u_it": nut, "u_local": ul,
+                    "cells": ce, "check_every": 16})
     return out
 
 
@@ -111,4 +117,4 @@ def tune(instances: Sequence, precision: int, tol: float = 1e-6, cache_path: str
 def solver_opts(result: Dict) -> Dict:
     """The nmpc_opts fields of a tuning result."""
     return {k: v for k, v in result.items() if k in ("cluster", "threads", "n_lo", "n_u_it",
-                                                     "check_every")}
+                                                     "u_local", "cells", "check_every")}

@@ -49,6 +49,7 @@ struct nmpc_handle {
   // control
   int* ictl = nullptr;  // iter_k, block_done, n_active
   unsigned long long* res_inf = nullptr;
+  unsigned long long* res_err = nullptr;
   double* res_sq = nullptr;
   unsigned long long* res_first = nullptr;
   int* status = nullptr;
@@ -69,6 +70,7 @@ struct nmpc_handle {
   unsigned long long* h_resinf = nullptr;
   // launch configuration
   int threads = 0;
+  int cpt = 2;
   int grid = 0;
   int csize = 1;
   int slab_max = 0;
@@ -114,7 +116,7 @@ void free_all(nmpc_handle* h) {
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
   void* ptrs[] = {h->inst_d, h->work_d, h->act_d, h->x0_d, h->ref_d, h->uo_d, h->w_d,
                   h->xb[0], h->xb[1], h->xb[2], h->ub[0], h->ub[1], h->ub[2],
-                  h->lb[0], h->lb[1], h->lb[2], h->ictl, h->res_inf, h->res_sq,
+                  h->lb[0], h->lb[1], h->lb[2], h->ictl, h->res_inf, h->res_err, h->res_sq,
                   h->res_first, h->status, h->iters, h->final_buf, h->fin_inf,
                   h->fin_2, h->full_from, h->full0, h->scratch};
   for (void* p : ptrs)
@@ -145,6 +147,7 @@ IterArgs make_args(nmpc_handle* h) {
   A.block_done = h->ictl + 1;
   A.n_active = h->ictl + 2;
   A.res_inf = h->res_inf;
+  A.res_err = h->res_err;
   A.res_sq = h->res_sq;
   A.res_first = h->res_first;
   A.status = h->status;
@@ -177,6 +180,7 @@ IterArgs make_args(nmpc_handle* h) {
 // length, threads, dynamic shared memory, grid.
 struct LaunchPlan {
   int threads = 0, csize = 1, slab_max = 0, grid = 0;
+  int cpt = 2;  // cells per thread per pass round (kernel variant)
   size_t smem = 0;
   bool smem_mode = true;
   bool stage = true;  // float64 slab inputs staged in shared memory
@@ -185,10 +189,20 @@ struct LaunchPlan {
   size_t box_bytes = 0;
 };
 
+// Interior cells of the largest rank slab of a stage split over C CTAs.
 int slab_cells(const InstDev& I, int C) {
   const int unit = (I.dim == 2) ? I.mx : 1;
   const int nun = (I.dim == 2) ? I.my : I.mx;
   return ((nun + C - 1) / C) * unit;
+}
+
+// Length of a padded slab array: (rows + 2) (mx + 2) in 2D, cells + 2 in 1D
+// (halo rows or cells and zero pads around the slab), rounded up to 4 elements.
+int slab_stride(const InstDev& I, int C) {
+  const int nun = (I.dim == 2) ? I.my : I.mx;
+  const int per = (nun + C - 1) / C;
+  const int len = (I.dim == 2) ? (per + 2) * (I.mx + 2) : per + 2;
+  return (len + 3) & ~3;
 }
 
 template <typename T>
@@ -196,17 +210,38 @@ size_t small_shared_bytes_t() {
   return (sizeof(nmpc_dev::SmallShared<T>) + 15) & ~size_t(15);
 }
 
-int auto_threads(int slab) {
-  int t = ((slab / 4 + 31) / 32) * 32;  // about four cells per thread
-  return std::min(512, std::max(128, t));
+using IterKernel = void (*)(IterArgs);
+
+template <typename T, int MODE>
+IterKernel iter_kernel(int cpt) {
+  return cpt == 4 ? nmpc_dev::k_iterate<T, MODE, 4> : nmpc_dev::k_iterate<T, MODE, 2>;
 }
 
-// Clusters of C CTAs (auto threads, `smem` bytes) the device keeps resident at
-// once for the iteration kernel.
-int clusters_resident(int C, int slab, size_t smem, bool mixed) {
+IterKernel iter_kernel_of(bool mixed, int mode, int cpt) {
+  if (mixed)
+    return mode == nmpc_dev::MODE_SOLVE ? iter_kernel<float, nmpc_dev::MODE_SOLVE>(cpt)
+                                        : iter_kernel<float, nmpc_dev::MODE_ONESHOT>(cpt);
+  return mode == nmpc_dev::MODE_SOLVE ? iter_kernel<double, nmpc_dev::MODE_SOLVE>(cpt)
+                                      : iter_kernel<double, nmpc_dev::MODE_ONESHOT>(cpt);
+}
+
+// Threads per CTA and cells per thread per pass round for a slab of `slab`
+// interior cells: about four cells per thread, at least 128 threads; two
+// cells per round unless asked for four (that kernel has the larger register
+// budget and at most 384 threads; measured slower on the workloads so far).
+void thread_shape(int slab, const nmpc_opts& o, int* threads, int* cpt) {
+  const int natural = std::max(128, ((slab / 4 + 31) / 32) * 32);
+  const int c = o.cells ? o.cells : 2;
+  *cpt = c;
+  *threads = o.threads ? o.threads : std::min(c == 4 ? 384 : 512, natural);
+}
+
+// Clusters of C CTAs (`threads` threads, `smem` bytes) the device keeps
+// resident at once for the iteration kernel.
+int clusters_resident(int C, int threads, int cpt, size_t smem, bool mixed) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(C * 256));
-  cfg.blockDim = dim3((unsigned)auto_threads(slab));
+  cfg.blockDim = dim3((unsigned)threads);
   cfg.dynamicSmemBytes = smem;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -216,10 +251,8 @@ int clusters_resident(int C, int slab, size_t smem, bool mixed) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int n = 0;
-  cudaError_t e = mixed ? cudaOccupancyMaxActiveClusters(
-                              &n, nmpc_dev::k_iterate<float, nmpc_dev::MODE_SOLVE>, &cfg)
-                        : cudaOccupancyMaxActiveClusters(
-                              &n, nmpc_dev::k_iterate<double, nmpc_dev::MODE_SOLVE>, &cfg);
+  cudaError_t e = cudaOccupancyMaxActiveClusters(
+      &n, (const void*)iter_kernel_of(mixed, nmpc_dev::MODE_SOLVE, cpt), &cfg);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -248,15 +281,20 @@ LaunchPlan plan_launch(const InstDev* insts, int n_inst, int n_work, const nmpc_
   const size_t box_bytes = (size_t)nu_max * 4 * (dim_max == 2 ? side * side : side) * elem;
   P.local_u = o.u_local && (o.n_lo <= 4) && box_bytes <= 32768;
   P.box_bytes = P.local_u ? ((box_bytes + 15) & ~size_t(15)) : 0;
-  auto slab = [&](int C) {
+  auto slab = [&](int C) {  // interior cells
     int m = 0;
     for (int b = 0; b < n_inst; ++b) m = std::max(m, slab_cells(insts[b], C));
+    return m;
+  };
+  auto stride = [&](int C) {  // padded array length
+    int m = 0;
+    for (int b = 0; b < n_inst; ++b) m = std::max(m, slab_stride(insts[b], C));
     return m;
   };
   bool stage = true;
   auto bytes = [&](int C) {
     return small + P.box_bytes +
-           (size_t)slab(C) * (nmpc_dev::NUM_WORK_ARRAYS * elem +
+           (size_t)stride(C) * (nmpc_dev::NUM_WORK_ARRAYS * elem +
                               (stage ? nmpc_dev::NUM_STAGE_ARRAYS * sizeof(double) : 0));
   };
   auto next_c = [](int C) { return C < 8 ? C + 1 : 16; };
@@ -280,7 +318,9 @@ LaunchPlan plan_launch(const InstDev* insts, int n_inst, int n_work, const nmpc_
       while (C < 8) {
         const int C2 = C + 1;
         if (!fits(C2) || slab(C2) < 512) break;
-        if (clusters_resident(C2, slab(C2), bytes(C2), mixed) < n_work) break;
+        int t2, c2;
+        thread_shape(slab(C2), o, &t2, &c2);
+        if (clusters_resident(C2, t2, c2, bytes(C2), mixed) < n_work) break;
         C = C2;
       }
     }
@@ -292,8 +332,8 @@ LaunchPlan plan_launch(const InstDev* insts, int n_inst, int n_work, const nmpc_
   }
   P.stage = stage;
   P.csize = C;
-  P.slab_max = slab(C);
-  P.threads = o.threads ? o.threads : auto_threads(P.slab_max);
+  P.slab_max = stride(C);
+  thread_shape(slab(C), o, &P.threads, &P.cpt);
   P.smem = P.smem_mode ? bytes(C) : small;
   P.grid = n_work * C;
   return P;
@@ -313,12 +353,13 @@ cudaError_t launch_k(const LaunchPlan& P, const IterArgs& A, cudaStream_t st) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, nmpc_dev::k_iterate<T, MODE>, A);
+  return cudaLaunchKernelEx(&cfg, iter_kernel<T, MODE>(P.cpt), A);
 }
 
 LaunchPlan plan_of(const nmpc_handle* h) {
   LaunchPlan P;
   P.threads = h->threads;
+  P.cpt = h->cpt;
   P.csize = h->csize;
   P.stage = h->stage;
   P.local_u = h->local_u;
@@ -340,8 +381,10 @@ cudaError_t launch_iterate(nmpc_handle* h, const IterArgs& A, cudaStream_t st) {
 
 template <typename T>
 cudaError_t configure_kernels(size_t smem) {
-  void (*fns[2])(IterArgs) = {nmpc_dev::k_iterate<T, nmpc_dev::MODE_SOLVE>,
-                              nmpc_dev::k_iterate<T, nmpc_dev::MODE_ONESHOT>};
+  IterKernel fns[4] = {nmpc_dev::k_iterate<T, nmpc_dev::MODE_SOLVE, 2>,
+                       nmpc_dev::k_iterate<T, nmpc_dev::MODE_ONESHOT, 2>,
+                       nmpc_dev::k_iterate<T, nmpc_dev::MODE_SOLVE, 4>,
+                       nmpc_dev::k_iterate<T, nmpc_dev::MODE_ONESHOT, 4>};
   for (auto fn : fns) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -351,11 +394,13 @@ cudaError_t configure_kernels(size_t smem) {
   return cudaSuccess;
 }
 
-// Rounding level of the split residual: its O(h) stencil terms are float32
-// sums of magnitude ~ h 4 (cx + cy) k(w) |w| with |w| ~ 1 (8 ulps of margin).
-double split_floor_of(const InstDev& I) {
-  const double eps32 = 5.960464477539063e-08;
-  return 8.0 * eps32 * I.h * 4.0 * (I.cx + I.cy) * I.k0 * (1.0 + std::fabs(I.k1));
+bool opts_ok(const nmpc_opts& o) {
+  return (o.tol >= 0) && o.max_iter >= 0 && o.n_lo >= 1 && o.n_u_it >= 1 && o.check_every >= 1 &&
+         (o.alpha > 0 && o.alpha <= 1) && (o.div_limit > 0) &&
+         (o.precision == NMPC_FP64 || o.precision == NMPC_MIXED) && o.threads >= 0 &&
+         o.threads <= 512 && (o.threads % 32) == 0 && o.cluster >= 0 && o.cluster <= 16 &&
+         (o.cluster <= 8 || o.cluster == 16) && (o.split_min >= 0) &&
+         (o.cells == 0 || o.cells == 2 || o.cells == 4) && !(o.cells == 4 && o.threads > 384);
 }
 
 int validate(const nmpc_desc* d) {
@@ -524,6 +569,7 @@ void nmpc_default_opts(nmpc_opts* o) {
   o->cluster = 0;
   o->split_min = 1e-7;
   o->u_local = 1;
+  o->cells = 0;
 }
 
 int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
@@ -533,12 +579,7 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
   nmpc_opts o;
   nmpc_default_opts(&o);
   if (opts) o = *opts;
-  if (!(o.tol >= 0) || o.max_iter < 0 || o.n_lo < 1 || o.n_u_it < 1 || o.check_every < 1 ||
-      !(o.alpha > 0 && o.alpha <= 1) || !(o.div_limit > 0) ||
-      (o.precision != NMPC_FP64 && o.precision != NMPC_MIXED) || o.threads < 0 ||
-      o.threads > 512 || (o.threads % 32) != 0 || o.cluster < 0 || o.cluster > 16 ||
-      (o.cluster > 8 && o.cluster != 16) || !(o.split_min >= 0))
-    return NMPC_ERR_BAD_ARG;
+  if (!opts_ok(o)) return NMPC_ERR_BAD_ARG;
   for (int b = 0; b < n_instances; ++b) {
     int rc = validate(&descs[b]);
     if (rc != NMPC_OK) return rc;
@@ -580,7 +621,6 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
     const double dx = 1.0 / (d.mx + 1), dy = 1.0 / (d.my + 1);
     I.cx = 1.0 / (dx * dx);
     I.cy = (d.dim == 2) ? 1.0 / (dy * dy) : 0.0;
-    I.split_floor = split_floor_of(I);
     for (int a = 0; a < d.n_u; ++a) act_all.push_back(d.act_cell[a]);
     h->nu_tot += d.n_u;
     for (int s = 0; s < d.horizon; ++s) work.push_back(make_int2(b, s));
@@ -608,15 +648,12 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
                              std::max(1, h->num_sms), max_optin);
   if (!P.smem_mode) {
     int per_sm = 1;
-    if (h->mixed)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &per_sm, nmpc_dev::k_iterate<float, nmpc_dev::MODE_SOLVE>, P.threads, P.smem);
-    else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &per_sm, nmpc_dev::k_iterate<double, nmpc_dev::MODE_SOLVE>, P.threads, P.smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, iter_kernel_of(h->mixed, nmpc_dev::MODE_SOLVE, P.cpt), P.threads, P.smem);
     P.grid = std::min(h->n_work, std::max(1, per_sm) * std::max(1, h->num_sms));
   }
   h->threads = P.threads;
+  h->cpt = P.cpt;
   h->csize = P.csize;
   h->slab_max = P.slab_max;
   h->smem = P.smem;
@@ -645,6 +682,7 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
   }
   A(dev_alloc(&h->ictl, 4));
   A(dev_alloc(&h->res_inf, (size_t)nmpc_dev::RES_SLOTS * n_instances));
+  A(dev_alloc(&h->res_err, (size_t)nmpc_dev::RES_SLOTS * n_instances));
   A(dev_alloc(&h->res_sq, (size_t)nmpc_dev::RES_SLOTS * n_instances));
   A(dev_alloc(&h->full_from, n_instances));
   A(dev_alloc(&h->full0, n_instances));
@@ -959,12 +997,7 @@ extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
   nmpc_opts o;
   nmpc_default_opts(&o);
   if (opts) o = *opts;
-  if (!(o.tol >= 0) || o.max_iter < 0 || o.n_lo < 1 || o.n_u_it < 1 || o.check_every < 1 ||
-      !(o.alpha > 0 && o.alpha <= 1) || !(o.div_limit > 0) ||
-      (o.precision != NMPC_FP64 && o.precision != NMPC_MIXED) || o.threads < 0 ||
-      o.threads > 512 || (o.threads % 32) != 0 || o.cluster < 0 || o.cluster > 16 ||
-      (o.cluster > 8 && o.cluster != 16) || !(o.split_min >= 0))
-    return NMPC_ERR_BAD_ARG;
+  if (!opts_ok(o)) return NMPC_ERR_BAD_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return NMPC_ERR_NO_DEVICE;
 
@@ -996,7 +1029,6 @@ extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
   const double dx = 1.0 / (d.mx + 1), dy = 1.0 / (d.my + 1);
   I.cx = 1.0 / (dx * dx);
   I.cy = (d.dim == 2) ? 1.0 / (dy * dy) : 0.0;
-  I.split_floor = split_floor_of(I);
   LaunchPlan P = plan_launch(&I, 1, N, o, mixed, std::max(1, num_sms), max_optin);
   const bool smem_mode = P.smem_mode;
   if (!smem_mode) P.grid = std::min(N, std::max(1, num_sms));
@@ -1017,6 +1049,7 @@ extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
   }
   const size_t o_ctl = carve(&off, 4 * sizeof(int));
   const size_t o_rinf = carve(&off, nmpc_dev::RES_SLOTS * sizeof(unsigned long long));
+  const size_t o_rerr = carve(&off, nmpc_dev::RES_SLOTS * sizeof(unsigned long long));
   const size_t o_rsq = carve(&off, nmpc_dev::RES_SLOTS * sizeof(double));
   const size_t o_ffrom = carve(&off, 2 * sizeof(int));  // full_from, full0
   const size_t o_rfirst = carve(&off, sizeof(unsigned long long));
@@ -1066,6 +1099,7 @@ extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
   A.block_done = ctl + 1;
   A.n_active = ctl + 2;
   A.res_inf = reinterpret_cast<unsigned long long*>(base + o_rinf);
+  A.res_err = reinterpret_cast<unsigned long long*>(base + o_rerr);
   A.res_sq = reinterpret_cast<double*>(base + o_rsq);
   A.res_first = reinterpret_cast<unsigned long long*>(base + o_rfirst);
   int* stat = reinterpret_cast<int*>(base + o_status);

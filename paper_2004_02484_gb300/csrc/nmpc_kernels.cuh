@@ -32,7 +32,6 @@ namespace nmpc_dev {
 namespace cg = cooperative_groups;
 
 constexpr int RES_SLOTS = 16;    // rolling residual history per instance
-constexpr int STALL_WINDOW = 12; // < RES_SLOTS - 3: slot k-1-W is neither zeroed nor reused yet
 constexpr int NUM_WORK_ARRAYS = 11;
 constexpr int NUM_STAGE_ARRAYS = 5;  // float64 staging of x_i, lambda_i, x_{i-1}, lambda_{i+1}, ref
 constexpr int MAX_NU = 64;
@@ -44,7 +43,6 @@ struct InstDev {
   long long u_off;  // offset in packed u
   long long g_off;  // offset in packed x0 / ref
   double h, q, r, qf, gamma, k0, k1, b0, cx, cy;
-  double split_floor;  // float32 rounding level of the split residual's O(h) terms
 };
 
 enum { MODE_SOLVE = 0, MODE_ONESHOT = 1 };
@@ -70,6 +68,7 @@ struct IterArgs {
   int* iter_k;
   int* block_done;
   unsigned long long* res_inf;   // [RES_SLOTS][n_inst], bits of non-negative doubles
+  unsigned long long* res_err;   // [RES_SLOTS][n_inst] bound on a split residual's rounding error
   double* res_sq;                // [RES_SLOTS][n_inst]
   unsigned long long* res_first; // [n_inst] ||K(S^0)||_inf
   int* status;
@@ -89,7 +88,7 @@ struct IterArgs {
   int stage;       // float64 slab inputs staged in shared memory (1) or read in place
   int local_u;     // u-iteration through the actuators' local responses (1) or full sweeps
   int box_r;       // half-width of a local-response box, 2 (n_lo - 1)
-  int slab_max;    // cells per CTA slab (length of each shared work array)
+  int slab_max;    // length of each padded slab array (halo rows and pads included)
   // lower-layer work arrays: shared memory (scratch == nullptr) or a global
   // slab of scratch_stride bytes per CTA
   char* scratch;
@@ -103,34 +102,167 @@ struct Cl {
     else __syncthreads();
   }
   template <typename T>
-  __device__ __forceinline__ const T* map(const T* p, int r) const {
-    return cg::this_cluster().map_shared_rank(const_cast<T*>(p), r);
+  __device__ __forceinline__ T* map(T* p, int r) const {
+    return cg::this_cluster().map_shared_rank(p, r);
   }
 };
 
-// Cells [lo, hi) of the instance grid owned by cluster rank `rank`; slabs are
-// whole rows in 2D and segments in 1D, per_cells cells per rank.
-struct Slab {
-  int lo, hi, per_cells;
-};
-
-__device__ __forceinline__ Slab slab_of(const InstDev& I, int C, int rank) {
-  const int unit = (I.dim == 2) ? I.mx : 1;
-  const int nun = (I.dim == 2) ? I.my : I.mx;
-  const int per = (nun + C - 1) / C;
-  Slab s;
-  s.per_cells = per * unit;
-  s.lo = min(rank * per, nun) * unit;
-  s.hi = min(rank * per + per, nun) * unit;
-  return s;
+// Quotient q / d for 0 <= q < 2^22, d >= 1, inv = 1.0f / d: the float
+// estimate is off by at most one and is corrected.
+__device__ __forceinline__ int fdiv(int q, int d, float inv) {
+  const int j = __float2int_rz(__int2float_rz(q) * inv);
+  const int r = q - j * d;
+  return j + (r >= d ? 1 : 0) - (r < 0 ? 1 : 0);
 }
 
-// Value of slab array `a` at grid cell m, local or in another rank's slab.
+// A cluster rank's slab in the padded layout of its shared work arrays.  The
+// stage grid is split into whole rows (2D) or segments (1D), `per` rows or
+// cells per rank (the last non-empty rank may hold fewer, later ranks none).
+// 2D: slab cell (row j, column i) sits at p = (j + 1) W + i + 1, W = mx + 2;
+// padded rows 0 and rows + 1 hold the neighbouring ranks' boundary rows (the
+// halo) or zeros at the grid's Dirichlet ring, padded columns 0 and mx + 1
+// are zero.  1D: cell q sits at p = q + 1; positions 0 and n + 1 are halo or
+// zero.  Stencils then read their neighbours with no bounds tests, and a rank
+// that writes a boundary value also stores it into the neighbour's halo.
+struct Geo {
+  int dim;
+  int mx, per;   // grid row length; rows (2D) / cells (1D) per rank
+  int cols;      // 2D: mx; 1D: n
+  int n;         // cells of this rank
+  int rows;      // 2D: rows of this rank; 1D: 1
+  int W;         // 2D: padded row stride mx + 2; 1D: 0
+  int lo;        // first grid cell of the slab
+  int r0;        // first grid row (2D) / cell (1D) of the slab
+  int edge;      // cells of the first (last) row: 2D mx, 1D 1
+  int up_off;    // shift into rank - 1's layout: its bottom halo row
+  int dn_off;    // shift back into rank + 1's layout: its top halo row
+  int plen;      // padded positions in use
+  bool up, dn;   // rank - 1 / rank + 1 hold cells (halo exchange partners)
+  float inv_cols, inv_W;
+  __device__ __forceinline__ int pidx(int q) const {
+    return (dim == 2) ? W + 1 + q + 2 * fdiv(q, cols, inv_cols) : q + 1;
+  }
+};
+
+__device__ __forceinline__ Geo geo_of(const InstDev& I, int C, int rank) {
+  Geo g;
+  const bool d2 = (I.dim == 2);
+  g.dim = I.dim;
+  g.mx = I.mx;
+  const int nun = d2 ? I.my : I.mx;
+  g.per = (nun + C - 1) / C;
+  const int a = min(rank * g.per, nun), b = min(a + g.per, nun);
+  g.r0 = a;
+  g.rows = d2 ? b - a : 1;
+  g.n = d2 ? (b - a) * I.mx : b - a;
+  g.cols = d2 ? I.mx : g.n;
+  g.W = d2 ? I.mx + 2 : 0;
+  g.lo = d2 ? a * I.mx : a;
+  g.edge = d2 ? I.mx : 1;
+  g.up_off = d2 ? g.per * g.W : g.per;
+  g.dn_off = d2 ? (b - a) * g.W : (b - a);
+  g.plen = d2 ? (b - a + 2) * g.W : (b - a) + 2;
+  g.up = (rank > 0) && (b > a);
+  g.dn = (b < nun) && (b > a);
+  g.inv_cols = 1.0f / (float)max(g.cols, 1);
+  g.inv_W = 1.0f / (float)max(g.W, 1);
+  return g;
+}
+
+// Padded position of grid cell c in the slab of the rank that owns it.
+__device__ __forceinline__ int owner_of(int c, const Geo& g, int& p) {
+  if (g.dim == 2) {
+    const int row = c / g.mx, col = c - row * g.mx;
+    const int r = row / g.per;
+    p = (row - r * g.per + 1) * (g.mx + 2) + col + 1;
+    return r;
+  }
+  const int r = c / g.per;
+  p = c - r * g.per + 1;
+  return r;
+}
+
+// Element of slab array `a` at grid cell c, in this rank's or another rank's
+// shared memory.
 template <typename T>
-__device__ __forceinline__ T ldn(const T* a, int m, const Slab& sl, const Cl& cl) {
-  if (m >= sl.lo && m < sl.hi) return a[m - sl.lo];
-  const int r = m / sl.per_cells;
-  return cl.map(a, r)[m - r * sl.per_cells];
+__device__ __forceinline__ T* at(T* a, int c, const Geo& g, const Cl& cl) {
+  int p;
+  const int r = owner_of(c, g, p);
+  return (r == cl.rank) ? a + p : cl.map(a, r) + p;
+}
+
+// The neighbours' copies of a slab array (their halo rows receive this rank's
+// boundary values).
+template <typename T>
+struct Halo {
+  T* up;
+  T* dn;
+};
+
+template <typename T>
+__device__ __forceinline__ Halo<T> halo_of(T* a, const Geo& g, const Cl& cl) {
+  Halo<T> hl;
+  hl.up = g.up ? cl.map(a, cl.rank - 1) : nullptr;
+  hl.dn = g.dn ? cl.map(a, cl.rank + 1) : nullptr;
+  return hl;
+}
+
+// Store v at own cell q (padded position p) and, on a boundary row, into the
+// neighbours' halo.
+template <typename T>
+__device__ __forceinline__ void put(T* a, const Halo<T>& hl, const Geo& g, int q, int p, T v) {
+  a[p] = v;
+  if (g.up && q < g.edge) hl.up[p + g.up_off] = v;
+  if (g.dn && q >= g.n - g.edge) hl.dn[p - g.dn_off] = v;
+}
+
+// Zero the padded positions of `a` that no rank writes in a work item: the
+// column pads and the halo rows at the grid boundary (the Dirichlet ring).
+template <typename V>
+__device__ __forceinline__ void zero_ring(V* a, const Geo& g) {
+  if (g.n == 0) return;
+  if (g.dim == 2) {
+    for (int jj = threadIdx.x; jj < g.rows + 2; jj += blockDim.x) {
+      a[jj * g.W] = V(0);
+      a[jj * g.W + g.W - 1] = V(0);
+    }
+    if (!g.up)
+      for (int i = threadIdx.x; i < g.W; i += blockDim.x) a[i] = V(0);
+    if (!g.dn)
+      for (int i = threadIdx.x; i < g.W; i += blockDim.x) a[(g.rows + 1) * g.W + i] = V(0);
+  } else if (threadIdx.x == 0) {
+    if (!g.up) a[0] = V(0);
+    if (!g.dn) a[g.n + 1] = V(0);
+  }
+}
+
+// Weighted sum of the four (2D) or two (1D) stencil neighbours of padded
+// position p.
+template <typename V, typename F>
+__device__ __forceinline__ V stencil(const Geo& g, int p, V cx, V cy, F a) {
+  const V sx = a(p - 1) + a(p + 1);
+  if (g.dim == 2) return cx * sx + cy * (a(p - g.W) + a(p + g.W));
+  return cx * sx;
+}
+
+// One pass over the rank's n cells, CPT cells per thread per round: every
+// cell's loads and arithmetic (ld) come before any of the round's stores
+// (st), so the CPT cells form independent dependency chains.
+template <int CPT, typename V, typename LD, typename ST>
+__device__ __forceinline__ void pass(int n, LD ld, ST st) {
+  for (int base = threadIdx.x; base < n; base += CPT * blockDim.x) {
+    V v[CPT];
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+      const int q = base + k * blockDim.x;
+      if (q < n) v[k] = ld(q);
+    }
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+      const int q = base + k * blockDim.x;
+      if (q < n) st(q, v[k]);
+    }
+  }
 }
 
 __device__ __forceinline__ double phi_d(double w, double k0, double k1) {
@@ -192,6 +324,7 @@ __device__ __forceinline__ V nbr_sum(int c, int ix, int iy, int mx, int my, V cx
 struct BlockRed {
   double mx[32];
   double sq[32];
+  float4 mg[32];
 };
 
 __device__ __forceinline__ void block_reduce_store(double vmax, double vsq, BlockRed* red,
@@ -218,9 +351,52 @@ __device__ __forceinline__ void block_reduce_store(double vmax, double vsq, Bloc
   }
 }
 
+// Split residual: float32 partial norms (max, sum of squares) and the four
+// magnitude maxima of its rounding bound, block-reduced; thread 0 receives the
+// norms in float64 and the maxima in mags[4].
+__device__ __forceinline__ void block_reduce_store_f(float vmax, float vsq, float4 mg,
+                                                     BlockRed* red, double* out_max,
+                                                     double* out_sq, float* mags) {
+  for (int o = 16; o > 0; o >>= 1) {
+    vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    vsq += __shfl_xor_sync(0xffffffffu, vsq, o);
+    mg.x = fmaxf(mg.x, __shfl_xor_sync(0xffffffffu, mg.x, o));
+    mg.y = fmaxf(mg.y, __shfl_xor_sync(0xffffffffu, mg.y, o));
+    mg.z = fmaxf(mg.z, __shfl_xor_sync(0xffffffffu, mg.z, o));
+    mg.w = fmaxf(mg.w, __shfl_xor_sync(0xffffffffu, mg.w, o));
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red->mx[wid] = f2d(vmax);
+    red->sq[wid] = f2d(vsq);
+    red->mg[wid] = mg;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0, s = 0.0;
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int w = 0; w < nw; ++w) {
+      m = fmax(m, red->mx[w]);
+      s += red->sq[w];
+      g.x = fmaxf(g.x, red->mg[w].x);
+      g.y = fmaxf(g.y, red->mg[w].y);
+      g.z = fmaxf(g.z, red->mg[w].z);
+      g.w = fmaxf(g.w, red->mg[w].w);
+    }
+    *out_max = m;
+    *out_sq = s;
+    mags[0] = g.x;
+    mags[1] = g.y;
+    mags[2] = g.z;
+    mags[3] = g.w;
+  }
+}
+
 // Per-work-item shared scalars (the NUM_WORK_ARRAYS slab arrays follow).
 template <typename T>
 struct SmallShared {
+  unsigned long long amask[512];  // per thread: which of its cells carry an actuator
   BlockRed red;
   double red_out[2];
   double u[MAX_NU];
@@ -237,20 +413,34 @@ struct SmallShared {
 __device__ __forceinline__ double to_double(float v) { return f2d(v); }
 __device__ __forceinline__ double to_double(double v) { return v; }
 
+// float64 -> T off the float64 pipe (truncating for float)
+template <typename T>
+__device__ __forceinline__ T to_T(double v);
+template <>
+__device__ __forceinline__ float to_T<float>(double v) { return d2f(v); }
+template <>
+__device__ __forceinline__ double to_T<double>(double v) { return v; }
+
+// 1 / v rounded to nearest (the same value as the IEEE division)
+__device__ __forceinline__ float rcp_T(float v) { return __frcp_rn(v); }
+__device__ __forceinline__ double rcp_T(double v) { return __drcp_rn(v); }
+
 __device__ __forceinline__ void cp_async8(void* dst_smem, const void* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
 }
 
-// gstage: NUM_STAGE_ARRAYS float64 slab arrays in shared memory, or nullptr
-// (global-slab mode: the stage is read from global memory in place).
-template <typename T>
+// gstage: NUM_STAGE_ARRAYS float64 arrays in shared memory in the padded
+// layout (x_i and lambda_i with their halo rows; x_{i-1}, lambda_{i+1}, ref at
+// the own cells), or nullptr (the stage is read from global memory in place).
+template <typename T, int CPT>
 __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, bool full,
                              bool resid_only, SmallShared<T>& sm, T* wk, const Cl& cl,
                              double* gstage) {
   const InstDev I = A.inst[b];
-  const Slab sl = slab_of(I, cl.C, cl.rank);
-  const int mx = I.mx, my = I.my, nu = I.nu, N = I.N, ng = I.ng;
+  const Geo g = geo_of(I, cl.C, cl.rank);
+  const int nu = I.nu, N = I.N, ng = I.ng, n = g.n;
+  const int tid = threadIdx.x, bd = blockDim.x;
   const long long so = I.s_off + (long long)s * ng;
   const double* __restrict__ X = A.xin[rd];
   const double* __restrict__ L = A.lin[rd];
@@ -261,6 +451,12 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
   const double dcoef = 2.0 * (cx + cy);
   const bool last = (s == N - 1);
   const int SM = A.slab_max;
+  const int n_lo = A.n_lo;
+  const bool wide = n_lo > 2;  // sweeps 3.. read dp and the previous sweep at neighbours
+  // the residual pass keeps many values live per cell: fewer cells per round
+  // (float64 form: one)
+  constexpr int RES_CPT = (CPT > 2) ? CPT / 2 : CPT;
+  constexpr int FULL_CPT = 1;
 
   T* b2 = wk;               // costate row K3
   T* dp = wk + 1 * SM;      // Phi'(x)
@@ -273,58 +469,115 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
   T* y4 = wk + 8 * SM;      // lambda-part of Y(v3)
   T* e1 = wk + 9 * SM;      // ping-pong spares for n_lo > 2
   T* e2 = wk + 10 * SM;
-  // split-residual float copies of x, lambda and Phi(x), alive in P1-P2 only
+  // residual inputs, alive in P1-P2 only: float copies of x, lambda and Phi(x)
+  // (split residual), or Phi(x) in float64 (full residual, staged slab)
   float* xf = reinterpret_cast<float*>(y5);
   float* lf = reinterpret_cast<float*>(w1);
   float* pf = reinterpret_cast<float*>(y4);
+  double* phid = reinterpret_cast<double*>(y5);
 
-  for (int a = threadIdx.x; a < nu; a += blockDim.x) {
-    sm.act[a] = A.act[I.act_off + a];
+  // actuators: controls of this stage, and per thread a bit mask of which of
+  // its cells carry one (cell q is bit q / blockDim of thread q % blockDim)
+  for (int a = tid; a < nu; a += bd) {
+    const int c = A.act[I.act_off + a];
+    sm.act[a] = c;
     sm.u[a] = Uin[I.u_off + (long long)s * nu + a];
     sm.v3[a] = T(0);
+    const int q = c - g.lo;
+    if (q >= 0 && q < n && q / bd < 64) atomicOr(&sm.amask[q % bd], 1ull << (q / bd));
   }
-  // float64 inputs of this slab: x_i, lambda_i, x_{i-1} (x0 at the first stage),
-  // lambda_{i+1} (unused at the last stage) and ref, staged into shared memory by
-  // asynchronous copies that are all in flight at once; indexed by c - lo
-  const double *gx, *gl, *gxp, *gln, *grf;
+  double* sx = gstage;
+  double* sl_ = gstage + SM;
+  double* sxp = gstage + 2 * SM;
+  double* sln = gstage + 3 * SM;
+  double* srf = gstage + 4 * SM;
   if (gstage) {
-    const int SMd = A.slab_max;
-    double* sx = gstage;
-    double* sl_ = gstage + SMd;
-    double* sxp = gstage + 2 * SMd;
-    double* sln = gstage + 3 * SMd;
-    double* srf = gstage + 4 * SMd;
-    for (int c = sl.lo + threadIdx.x; c < sl.hi; c += blockDim.x) {
-      const int q = c - sl.lo;
-      cp_async8(sx + q, X + so + c);
-      cp_async8(sl_ + q, L + so + c);
-      cp_async8(sxp + q, (s == 0) ? x0 + c : X + so - ng + c);
-      if (!last) cp_async8(sln + q, L + so + ng + c);
-      cp_async8(srf + q, ref + c);
+    // asynchronous copies, all in flight at once; outside the grid: zero
+    for (int pp = tid; pp < g.plen; pp += bd) {
+      int row, col;
+      bool own;
+      if (g.dim == 2) {
+        const int jj = fdiv(pp, g.W, g.inv_W);
+        row = g.r0 - 1 + jj;
+        col = pp - jj * g.W - 1;
+        own = jj >= 1 && jj <= g.rows;
+      } else {
+        row = 0;
+        col = g.r0 - 1 + pp;
+        own = pp >= 1 && pp <= n;
+      }
+      if (col >= 0 && col < I.mx && row >= 0 && row < I.my) {
+        const int c = row * I.mx + col;
+        cp_async8(sx + pp, X + so + c);
+        cp_async8(sl_ + pp, L + so + c);
+        if (own) {
+          cp_async8(sxp + pp, (s == 0) ? x0 + c : X + so - ng + c);
+          if (!last) cp_async8(sln + pp, L + so + ng + c);
+          cp_async8(srf + pp, ref + c);
+        }
+      } else {
+        sx[pp] = 0.0;
+        sl_[pp] = 0.0;
+      }
     }
-    asm volatile("cp.async.wait_all;\n" ::);
-    gx = sx; gl = sl_; gxp = sxp; gln = sln; grf = srf;
-  } else {
-    gx = X + so + sl.lo;
-    gl = L + so + sl.lo;
-    gxp = ((s == 0) ? x0 : X + so - ng) + sl.lo;
-    gln = L + so + ng + sl.lo;
-    grf = ref + sl.lo;
   }
-  if (full) cl.sync();  // neighbours' staged x, lambda are read below
-  else __syncthreads();
+  zero_ring(p1, g);
+  if (wide) {
+    zero_ring(dp, g);
+    zero_ring(e1, g);
+    zero_ring(e2, g);
+  }
+  if (gstage) asm volatile("cp.async.wait_all;\n" ::);
+  __syncthreads();
+  // own-cell float64 inputs at cell q (padded position p)
+  auto OX = [&](int q, int p) { return gstage ? sx[p] : X[so + g.lo + q]; };
+  auto OL = [&](int q, int p) { return gstage ? sl_[p] : L[so + g.lo + q]; };
+  auto OXP = [&](int q, int p) {
+    return gstage ? sxp[p] : ((s == 0) ? x0[g.lo + q] : X[so - ng + g.lo + q]);
+  };
+  auto OLN = [&](int q, int p) { return gstage ? sln[p] : L[so + ng + g.lo + q]; };
+  auto ORF = [&](int q, int p) { return gstage ? srf[p] : ref[g.lo + q]; };
+  // float64 x or lambda at padded position pp read in place (zero outside the grid)
+  auto gpad = [&](const double* base, int pp) {
+    int row, col;
+    if (g.dim == 2) {
+      const int jj = fdiv(pp, g.W, g.inv_W);
+      row = g.r0 - 1 + jj;
+      col = pp - jj * g.W - 1;
+    } else {
+      row = 0;
+      col = g.r0 - 1 + pp;
+    }
+    return (col >= 0 && col < I.mx && row >= 0 && row < I.my) ? base[so + row * I.mx + col] : 0.0;
+  };
 
-  // ---- P1 (split residual): float copies for the stencils ----
+  // ---- P1: residual inputs on the padded slab, halo rows included ----
+  const float k0f = (float)k0, k1h = (float)(0.5 * k1);
+  struct F3 { float x, l, p; };
+  // magnitudes for the split residual's rounding bound: max |x|, |lambda| over
+  // the padded slab, max |float64 difference|, |ref| over the own cells
+  float4 mg = make_float4(0.f, 0.f, 0.f, 0.f);
   if (!full) {
-    const float k0f = (float)k0, k1h = (float)(0.5 * k1);
-    for (int c = sl.lo + threadIdx.x; c < sl.hi; c += blockDim.x) {
-      const float xv = d2f(gx[c - sl.lo]);
-      xf[c - sl.lo] = xv;
-      lf[c - sl.lo] = d2f(gl[c - sl.lo]);
-      pf[c - sl.lo] = k0f * (xv + k1h * xv * xv);
-    }
-    cl.sync();
+    pass<CPT, F3>(g.plen,
+        [&](int pp) {
+          F3 o;
+          o.x = d2f(gstage ? sx[pp] : gpad(X, pp));
+          o.l = d2f(gstage ? sl_[pp] : gpad(L, pp));
+          o.p = k0f * (o.x + k1h * o.x * o.x);
+          mg.x = fmaxf(mg.x, fabsf(o.x));
+          mg.y = fmaxf(mg.y, fabsf(o.l));
+          return o;
+        },
+        [&](int pp, F3 o) {
+          xf[pp] = o.x;
+          lf[pp] = o.l;
+          pf[pp] = o.p;
+        });
+  } else if (gstage) {
+    pass<CPT, double>(g.plen, [&](int pp) { return phi_d(sx[pp], k0, k1); },
+                      [&](int pp, double v) { phid[pp] = v; });
   }
+  __syncthreads();
 
   // ---- P2: K_i (eq. 9), coefficient fields, norms ----
   double vmax = 0.0, vsq = 0.0;
@@ -334,90 +587,168 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
   const float k0f_ = (float)k0, k1f_ = (float)k1, qf_ = (float)I.q, b0f = (float)b0;
   const float k01f = (float)(k0 * k1), hqff = last ? (float)(h * I.qf) : 0.0f;
   const double hqf = h * I.qf;
-  for (int c = sl.lo + threadIdx.x; c < sl.hi; c += blockDim.x) {
-    const int ix = c % mx, iy = c / mx;
-    const int cl_ = c - sl.lo;
-    const double x = gx[cl_];
-    const double lam = gl[cl_];
-    const double xp = gxp[cl_];
-    const double rc_ = grf[cl_];
-    T K1t, K3t, dpt, axt;
-    if (full) {
-      const double ln = last ? hqf * (x - rc_) : gln[cl_];
-      double srcd = 0.0;
+  const unsigned long long amask = sm.amask[tid];
+  sm.amask[tid] = 0ull;  // ready for the next work item
+  struct P2Out {
+    int p;
+    bool act;
+    T K1, K3, dp, ax;
+  };
+  const Halo<T> hdp = halo_of(dp, g, cl);
+  const Halo<T> hp1 = halo_of(p1, g, cl);
+  auto p2_store = [&](int q, P2Out o) {
+    if (resid_only) return;
+    const int p = o.p;
+    const T r = rcp_T(-T(1) - th * tdc * o.dp);
+    b2[p] = o.K3;
+    ax[p] = o.ax;
+    rg[p] = r;
+    const T v = -o.K1 * r;  // first sweep of F_x v5 = -K1 (v3 = 0)
+    v1[p] = v;
+    if (wide) put(dp, hdp, g, q, p, o.dp);
+    else dp[p] = o.dp;
+    put(p1, hp1, g, q, p, o.dp * v);
+    if (o.act) {
+      const int c = g.lo + q;
       for (int a = 0; a < nu; ++a)
-        if (sm.act[a] == c) srcd += sm.u[a];
-      srcd *= b0;
-      // staged slabs: neighbours from shared memory (other ranks through the
-      // cluster); in place: gx, gl address the global stage directly
-      auto nx = [&](int m) { return gstage ? ldn(gx, m, sl, cl) : gx[m - sl.lo]; };
-      auto nl = [&](int m) { return gstage ? ldn(gl, m, sl, cl) : gl[m - sl.lo]; };
-      const double nphi = nbr_sum<double>(
-          c, ix, iy, mx, my, cx, cy, [&](int m) { return phi_d(nx(m), k0, k1); });
-      const double lphi = nphi - dcoef * phi_d(x, k0, k1);
-      const double mu = nbr_sum<double>(c, ix, iy, mx, my, cx, cy,
-                                        [&](int m) { return nl(m); }) - dcoef * lam;
-      const double dphi = k0 * (1.0 + k1 * x);
-      const double K1 = xp - x + h * (lphi + srcd);
-      const double K3 = ln - lam + h * (I.q * (x - rc_) + dphi * mu);
-      vmax = fmax(vmax, fmax(abs_or_inf(K1), abs_or_inf(K3)));
-      vsq += K1 * K1 + K3 * K3;
-      K1t = (T)K1;
-      K3t = (T)K3;
-      dpt = (T)dphi;
-      axt = (T)(h * (I.q + k0 * k1 * mu) + (last ? h * I.qf : 0.0));
-    } else {
-      const float nphi = nbr_sum<float>(c, ix, iy, mx, my, cxf, cyf,
-                                        [&](int m) { return ldn(pf, m, sl, cl); });
-      const float lphi = nphi - dcf * pf[cl_];
-      const float mu = nbr_sum<float>(c, ix, iy, mx, my, cxf, cyf,
-                                      [&](int m) { return ldn(lf, m, sl, cl); }) - dcf * lf[cl_];
-      const float xv = xf[cl_];
-      const float rv = d2f(rc_);
-      float srcf = 0.0f;
-      for (int a = 0; a < nu; ++a)
-        if (sm.act[a] == c) srcf += (float)sm.u[a];
-      const float dphi = k0f_ * (1.0f + k1f_ * xv);
-      const float t1 = hf * (lphi + b0f * srcf);
-      const float t3 = hf * (qf_ * (xv - rv) + dphi * mu);
-      // the O(1) differences in float64; at the last stage lambda_{N+1} is
-      // h qf (x_N - ref), an O(h) term
-      const double d3 = last ? -lam : gln[cl_] - lam;
-      const float K1 = d2f(xp - x) + t1;
-      const float K3 = d2f(d3) + t3 + (last ? hqff * (xv - rv) : 0.0f);
-      fmax_ = fmaxf(fmax_, fmaxf(abs_or_inf_f(K1), abs_or_inf_f(K3)));
-      fsq += K1 * K1 + K3 * K3;
-      K1t = (T)K1;
-      K3t = (T)K3;
-      dpt = (T)dphi;
-      axt = (T)(hf * (qf_ + k01f * mu) + hqff);
+        if (sm.act[a] == c) sm.b1a[a] = o.K1;
     }
-    if (!resid_only) {
-      const T r = T(1) / (-T(1) - th * tdc * dpt);
-      b2[cl_] = K3t;
-      dp[cl_] = dpt;
-      ax[cl_] = axt;
-      rg[cl_] = r;
-      const T v = -K1t * r;  // first sweep of F_x v5 = -K1 (v3 = 0)
-      v1[cl_] = v;
-      p1[cl_] = dpt * v;
-      for (int a = 0; a < nu; ++a)
-        if (sm.act[a] == c) sm.b1a[a] = K1t;
-    }
+  };
+  if (full) {
+    pass<FULL_CPT, P2Out>(n,
+        [&](int q) {
+          P2Out o;
+          const int p = g.pidx(q);
+          const int c = g.lo + q;
+          const int slot = q / bd;  // this cell's bit in the thread's mask
+          bool isact = (slot < 64) ? ((amask >> slot) & 1ull) != 0ull : false;
+          if (slot >= 64)
+            for (int a = 0; a < nu; ++a) isact |= (sm.act[a] == c);
+          o.p = p;
+          o.act = isact;
+          const double x = OX(q, p);
+          const double lam = OL(q, p);
+          const double xp = OXP(q, p);
+          const double rc_ = ORF(q, p);
+          const double ln = last ? hqf * (x - rc_) : OLN(q, p);
+          double srcd = 0.0;
+          if (isact) {
+            for (int a = 0; a < nu; ++a)
+              if (sm.act[a] == c) srcd += sm.u[a];
+            srcd *= b0;
+          }
+          double lphi, mu;
+          if (gstage) {
+            lphi = stencil<double>(g, p, cx, cy, [&](int m) { return phid[m]; }) - dcoef * phid[p];
+            mu = stencil<double>(g, p, cx, cy, [&](int m) { return sl_[m]; }) - dcoef * lam;
+          } else {
+            const int iy = (g.dim == 2) ? g.r0 + fdiv(q, g.cols, g.inv_cols) : 0;
+            const int ix = c - iy * I.mx;
+            const double* Xs = X + so;
+            const double* Ls = L + so;
+            lphi = nbr_sum<double>(c, ix, iy, I.mx, I.my, cx, cy,
+                                   [&](int m) { return phi_d(Xs[m], k0, k1); }) -
+                   dcoef * phi_d(x, k0, k1);
+            mu = nbr_sum<double>(c, ix, iy, I.mx, I.my, cx, cy, [&](int m) { return Ls[m]; }) -
+                 dcoef * lam;
+          }
+          const double dphi = k0 * (1.0 + k1 * x);
+          const double K1 = xp - x + h * (lphi + srcd);
+          const double K3 = ln - lam + h * (I.q * (x - rc_) + dphi * mu);
+          vmax = fmax(vmax, fmax(abs_or_inf(K1), abs_or_inf(K3)));
+          vsq += K1 * K1 + K3 * K3;
+          o.K1 = to_T<T>(K1);
+          o.K3 = to_T<T>(K3);
+          o.dp = to_T<T>(dphi);
+          o.ax = to_T<T>(h * (I.q + k0 * k1 * mu) + (last ? hqf : 0.0));
+          return o;
+        },
+        p2_store);
+  } else {
+    pass<RES_CPT, P2Out>(n,
+        [&](int q) {
+          P2Out o;
+          const int p = g.pidx(q);
+          const int c = g.lo + q;
+          const int slot = q / bd;  // this cell's bit in the thread's mask
+          bool isact = (slot < 64) ? ((amask >> slot) & 1ull) != 0ull : false;
+          if (slot >= 64)
+            for (int a = 0; a < nu; ++a) isact |= (sm.act[a] == c);
+          o.p = p;
+          o.act = isact;
+          const double x = OX(q, p);
+          const double lam = OL(q, p);
+          const double xp = OXP(q, p);
+          const double rc_ = ORF(q, p);
+          const float lphi = stencil<float>(g, p, cxf, cyf, [&](int m) { return pf[m]; }) - dcf * pf[p];
+          const float mu = stencil<float>(g, p, cxf, cyf, [&](int m) { return lf[m]; }) - dcf * lf[p];
+          const float xv = xf[p];
+          const float rv = d2f(rc_);
+          float srcf = 0.0f;
+          if (isact)
+            for (int a = 0; a < nu; ++a)
+              if (sm.act[a] == c) srcf += d2f(sm.u[a]);
+          const float dphi = k0f_ * (1.0f + k1f_ * xv);
+          const float t1 = hf * (lphi + b0f * srcf);
+          const float t3 = hf * (qf_ * (xv - rv) + dphi * mu);
+          // the O(1) differences in float64; at the last stage lambda_{N+1} is
+          // h qf (x_N - ref), an O(h) term
+          const double d3 = last ? -lam : OLN(q, p) - lam;
+          const float dx = d2f(xp - x), dl = d2f(d3);
+          mg.z = fmaxf(mg.z, fmaxf(fabsf(dx), fabsf(dl)));
+          mg.w = fmaxf(mg.w, fabsf(rv));
+          const float K1 = dx + t1;
+          const float K3 = dl + t3 + (last ? hqff * (xv - rv) : 0.0f);
+          fmax_ = fmaxf(fmax_, fmaxf(abs_or_inf_f(K1), abs_or_inf_f(K3)));
+          fsq += K1 * K1 + K3 * K3;
+          o.K1 = (T)K1;
+          o.K3 = (T)K3;
+          o.dp = (T)dphi;
+          o.ax = (T)(hf * (qf_ + k01f * mu) + hqff);
+          return o;
+        },
+        p2_store);
   }
-  vmax = fmax(vmax, (double)fmax_);
-  vsq += (double)fsq;
-  for (int a = threadIdx.x; a < nu; a += blockDim.x) {
+  for (int a = tid; a < nu; a += bd) {
     const double K2 = h * (I.r * sm.u[a] + b0 * L[so + sm.act[a]]);
     if (cl.rank == 0) {
-      vmax = fmax(vmax, abs_or_inf(K2));
-      vsq += K2 * K2;
+      if (full) {
+        vmax = fmax(vmax, abs_or_inf(K2));
+        vsq += K2 * K2;
+      } else {
+        const float K2f = d2f(K2);
+        fmax_ = fmaxf(fmax_, abs_or_inf_f(K2f));
+        fsq += K2f * K2f;
+        mg.z = fmaxf(mg.z, fabsf(K2f));
+      }
     }
     sm.b3[a] = (T)K2;
   }
-  block_reduce_store(vmax, vsq, &sm.red, &sm.red_out[0], &sm.red_out[1]);
-  if (threadIdx.x == 0) {
+  float mags[4];
+  if (full) block_reduce_store(vmax, vsq, &sm.red, &sm.red_out[0], &sm.red_out[1]);
+  else block_reduce_store_f(fmax_, fsq, mg, &sm.red, &sm.red_out[0], &sm.red_out[1], mags);
+  if (tid == 0) {
     const int slot = (k % RES_SLOTS) * A.n_inst + b;
+    if (!full) {
+      // Rounding bound of the split residual on this slab (unit roundoff
+      // u = 2^-24).  x and lambda are truncated to float32 (2u), Phi, Phi' and
+      // the five-point sums are evaluated in float32 (a few u each): with
+      // X, Lm the maxima of |x|, |lambda| over the padded slab, every O(h) term
+      // is off by at most 16 u h S, S = 4 (cx + cy) (Phi_max + Phi'_max Lm) +
+      // b0 sum|u| + (q + qf [last stage]) (X + max|ref|); the float64
+      // differences and the stage-gradient rows are truncated once (2u) and
+      // summed (u).  Every cell's |K_split - K| is below the bound.
+      const double u32 = 5.9604644775390625e-08;
+      const double Xm = f2d(mags[0]), Lm = f2d(mags[1]), Dm = f2d(mags[2]), Rm = f2d(mags[3]);
+      double usum = 0.0;
+      for (int a = 0; a < nu; ++a) usum += fabs(sm.u[a]);
+      const double pmax = fabs(k0) * (Xm + 0.5 * fabs(k1) * Xm * Xm);
+      const double dpmax = fabs(k0) * (1.0 + fabs(k1) * Xm);
+      const double S = 4.0 * (cx + cy) * (pmax + dpmax * Lm) + fabs(b0) * usum +
+                       (I.q + (last ? I.qf : 0.0)) * (Xm + Rm);
+      const double e = u32 * (3.0 * Dm + 16.0 * h * S);
+      atomicMax(&A.res_err[slot], (unsigned long long)__double_as_longlong(e));
+    }
     atomicMax(&A.res_inf[slot], (unsigned long long)__double_as_longlong(sm.red_out[0]));
     atomicAdd(&A.res_sq[slot], sm.red_out[1]);
     if (k == 0 && A.res_first)
@@ -427,90 +758,130 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
   if (resid_only) return;
 
   // ---- P3: lower layer in T ----
+  // the residual inputs are dead: restore the zero ring of the arrays they used
+  zero_ring(y5, g);
+  zero_ring(w1, g);
+  zero_ring(y4, g);
   const T tcx = (T)cx, tcy = (T)cy, tb0 = (T)b0;
   const T auu = (T)(h * I.r + I.gamma);
-  const int n_lo = A.n_lo;
   T* y5c = y5;
   T* y4c = y4;
+  const Halo<T> hw1 = halo_of(w1, g, cl);
+  struct PV {
+    int p;
+    T v;
+  };
+  struct PV2 {
+    int p;
+    T v, w;
+  };
   const int n_full = A.local_u ? 1 : A.n_u_it + 1;  // full-field Y applications
   for (int it = 0; it < n_full; ++it) {
     if (it > 0) {
       // c4 = F_u v3 - K1 changes only on actuator cells: refresh v1, p1 there
-      for (int a = threadIdx.x; a < nu; a += blockDim.x) {
+      for (int a = tid; a < nu; a += bd) {
         const int c = sm.act[a];
-        bool first = (c >= sl.lo && c < sl.hi);
+        const int q = c - g.lo;
+        bool first = (q >= 0 && q < n);
         for (int a2 = 0; a2 < a && first; ++a2)
           if (sm.act[a2] == c) first = false;
         if (first) {
           T inj = T(0);
           for (int a2 = 0; a2 < nu; ++a2)
             if (sm.act[a2] == c) inj += sm.v3[a2];
-          const T v = (th * tb0 * inj - sm.b1a[a]) * rg[c - sl.lo];
-          v1[c - sl.lo] = v;
-          p1[c - sl.lo] = dp[c - sl.lo] * v;
+          const int p = g.pidx(q);
+          const T v = (th * tb0 * inj - sm.b1a[a]) * rg[p];
+          v1[p] = v;
+          put(p1, hp1, g, q, p, dp[p] * v);
         }
       }
       cl.sync();
     }
     // F_x v5 = c4 by n_lo pointwise Jacobi sweeps from zero: sweep 1 is v1;
-    // sweep s+1 = v1 - D^{-1} (offdiag F_x) sweep s, reading neighbours
+    // sweep s+1 = v1 - D^{-1} (offdiag F_x) sweep s, reading neighbours.  The
+    // last sweep also forms sweep 1 of F_x^T v4 = -K3 - A_xx v5 (own cells).
     T* cur = v1;
-    if (n_lo >= 2) {
+    if (n_lo == 1) {
+      pass<CPT, PV>(n,
+          [&](int q) {
+            const int p = g.pidx(q);
+            return PV{p, (-b2[p] - ax[p] * v1[p]) * rg[p]};
+          },
+          [&](int q, PV o) { put(w1, hw1, g, q, o.p, o.v); });
+    } else {
       cur = y5;
-      for (int c = sl.lo + threadIdx.x; c < sl.hi; c += blockDim.x) {
-        const int ix = c % mx, iy = c / mx, q = c - sl.lo;
-        const T off = th * nbr_sum<T>(c, ix, iy, mx, my, tcx, tcy,
-                                      [&](int m) { return ldn(p1, m, sl, cl); });
-        cur[q] = v1[q] - rg[q] * off;
-      }
+      const Halo<T> hc = halo_of(cur, g, cl);
+      const bool lastsw = (n_lo == 2);
+      pass<CPT, PV2>(n,
+          [&](int q) {
+            const int p = g.pidx(q);
+            const T off = th * stencil<T>(g, p, tcx, tcy, [&](int m) { return p1[m]; });
+            const T v = v1[p] - rg[p] * off;
+            return PV2{p, v, (-b2[p] - ax[p] * v) * rg[p]};
+          },
+          [&](int q, PV2 o) {
+            if (wide) put(cur, hc, g, q, o.p, o.v);
+            else cur[o.p] = o.v;
+            if (lastsw) put(w1, hw1, g, q, o.p, o.w);
+          });
       T* nxt = e1;
       for (int sw = 2; sw < n_lo; ++sw) {
         cl.sync();
-        for (int c = sl.lo + threadIdx.x; c < sl.hi; c += blockDim.x) {
-          const int ix = c % mx, iy = c / mx, q = c - sl.lo;
-          const T off = th * nbr_sum<T>(c, ix, iy, mx, my, tcx, tcy, [&](int m) {
-            return ldn(dp, m, sl, cl) * ldn(cur, m, sl, cl);
-          });
-          nxt[q] = v1[q] - rg[q] * off;
-        }
+        const Halo<T> hn = halo_of(nxt, g, cl);
+        const bool fin = (sw == n_lo - 1);
+        pass<CPT, PV2>(n,
+            [&](int q) {
+              const int p = g.pidx(q);
+              const T off = th * stencil<T>(g, p, tcx, tcy, [&](int m) { return dp[m] * cur[m]; });
+              const T v = v1[p] - rg[p] * off;
+              return PV2{p, v, (-b2[p] - ax[p] * v) * rg[p]};
+            },
+            [&](int q, PV2 o) {
+              put(nxt, hn, g, q, o.p, o.v);
+              if (fin) put(w1, hw1, g, q, o.p, o.w);
+            });
         T* t = cur; cur = nxt; nxt = t;
       }
     }
     y5c = cur;
-    // sweep 1 of F_x^T v4 = -K3 - A_xx v5 (own cells only)
-    for (int c = sl.lo + threadIdx.x; c < sl.hi; c += blockDim.x) {
-      const int q = c - sl.lo;
-      w1[q] = (-b2[q] - ax[q] * y5c[q]) * rg[q];
-    }
     cur = w1;
     if (n_lo >= 2) {
       cl.sync();
       cur = y4;
-      for (int c = sl.lo + threadIdx.x; c < sl.hi; c += blockDim.x) {
-        const int ix = c % mx, iy = c / mx, q = c - sl.lo;
-        const T off = th * dp[q] * nbr_sum<T>(c, ix, iy, mx, my, tcx, tcy,
-                                              [&](int m) { return ldn(w1, m, sl, cl); });
-        cur[q] = w1[q] - rg[q] * off;
-      }
+      const Halo<T> hc = halo_of(cur, g, cl);
+      pass<CPT, PV>(n,
+          [&](int q) {
+            const int p = g.pidx(q);
+            const T off = th * dp[p] * stencil<T>(g, p, tcx, tcy, [&](int m) { return w1[m]; });
+            return PV{p, w1[p] - rg[p] * off};
+          },
+          [&](int q, PV o) {
+            if (wide) put(cur, hc, g, q, o.p, o.v);
+            else cur[o.p] = o.v;
+          });
       T* nxt = (y5c == e1) ? e2 : e1;  // the spare that does not hold v5
       for (int sw = 2; sw < n_lo; ++sw) {
         cl.sync();
-        for (int c = sl.lo + threadIdx.x; c < sl.hi; c += blockDim.x) {
-          const int ix = c % mx, iy = c / mx, q = c - sl.lo;
-          const T off = th * dp[q] * nbr_sum<T>(c, ix, iy, mx, my, tcx, tcy,
-                                                [&](int m) { return ldn(cur, m, sl, cl); });
-          nxt[q] = w1[q] - rg[q] * off;
-        }
+        const Halo<T> hn = halo_of(nxt, g, cl);
+        pass<CPT, PV>(n,
+            [&](int q) {
+              const int p = g.pidx(q);
+              const T off = th * dp[p] * stencil<T>(g, p, tcx, tcy, [&](int m) { return cur[m]; });
+              return PV{p, w1[p] - rg[p] * off};
+            },
+            [&](int q, PV o) { put(nxt, hn, g, q, o.p, o.v); });
         T* t = cur; cur = nxt; nxt = t;
       }
     }
     y4c = cur;
-    cl.sync();
-    if (!A.local_u && it < A.n_u_it) {
-      // A_uu v3 = K2 + F_u^T y_lambda (A_ux = 0); every rank keeps all of v3
-      for (int a = threadIdx.x; a < nu; a += blockDim.x)
-        sm.v3[a] = (sm.b3[a] + th * tb0 * ldn(y4c, sm.act[a], sl, cl)) / auu;
-      __syncthreads();
+    if (A.local_u || it < A.n_u_it) {
+      cl.sync();  // Y(.) at the actuator cells is read across ranks below
+      if (!A.local_u) {
+        // A_uu v3 = K2 + F_u^T y_lambda (A_ux = 0); every rank keeps all of v3
+        for (int a = tid; a < nu; a += bd)
+          sm.v3[a] = (sm.b3[a] + th * tb0 * *at(y4c, sm.act[a], g, cl)) / auu;
+        __syncthreads();
+      }
     }
   }
   if (A.local_u) {
@@ -518,13 +889,14 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
     // sweeps are linear and Z(e_b) vanishes outside a box of half-width
     // R = 2 (n_lo - 1) around actuator b (each sweep reaches one cell further).
     // The u-iteration then needs Y(0) at the actuator cells and the boxes.
-    for (int a = threadIdx.x; a < nu; a += blockDim.x) sm.y4a[a] = ldn(y4c, sm.act[a], sl, cl);
+    for (int a = tid; a < nu; a += bd) sm.y4a[a] = *at(y4c, sm.act[a], g, cl);
     const int R = A.box_r;
+    const int mx = I.mx, my = I.my;
     const int Sx = 2 * R + 1, Sy = (I.dim == 2) ? 2 * R + 1 : 1, Ry = (I.dim == 2) ? R : 0;
     const int S2 = Sx * Sy;
     T* boxes = wk + (size_t)NUM_WORK_ARRAYS * SM;
-    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int bb = threadIdx.x >> 5; bb < nu; bb += nw) {
+    const int lane = tid & 31, nw = bd >> 5;
+    for (int bb = tid >> 5; bb < nu; bb += nw) {
       T* z5 = boxes + (size_t)bb * 4 * S2;
       T* z4 = z5 + S2;
       T* t0 = z5 + 2 * S2;
@@ -539,13 +911,13 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
       auto boxnbr = [&](const T* v, int j, int i, bool with_dp) {
         T sx = T(0), sy = T(0);
         int c;
-        if (i > 0 && cell(j, i - 1, c)) sx += (with_dp ? ldn(dp, c, sl, cl) : T(1)) * v[j * Sx + i - 1];
-        if (i < Sx - 1 && cell(j, i + 1, c)) sx += (with_dp ? ldn(dp, c, sl, cl) : T(1)) * v[j * Sx + i + 1];
-        if (j > 0 && cell(j - 1, i, c)) sy += (with_dp ? ldn(dp, c, sl, cl) : T(1)) * v[(j - 1) * Sx + i];
-        if (j < Sy - 1 && cell(j + 1, i, c)) sy += (with_dp ? ldn(dp, c, sl, cl) : T(1)) * v[(j + 1) * Sx + i];
+        if (i > 0 && cell(j, i - 1, c)) sx += (with_dp ? *at(dp, c, g, cl) : T(1)) * v[j * Sx + i - 1];
+        if (i < Sx - 1 && cell(j, i + 1, c)) sx += (with_dp ? *at(dp, c, g, cl) : T(1)) * v[j * Sx + i + 1];
+        if (j > 0 && cell(j - 1, i, c)) sy += (with_dp ? *at(dp, c, g, cl) : T(1)) * v[(j - 1) * Sx + i];
+        if (j < Sy - 1 && cell(j + 1, i, c)) sy += (with_dp ? *at(dp, c, g, cl) : T(1)) * v[(j + 1) * Sx + i];
         return tcx * sx + tcy * sy;
       };
-      const T v1c = th * tb0 * ldn(rg, ca, sl, cl);  // first F_x sweep: D^{-1} h b0 e_b
+      const T v1c = th * tb0 * *at(rg, ca, g, cl);  // first F_x sweep: D^{-1} h b0 e_b
       for (int q = lane; q < S2; q += 32) t0[q] = (q == Ry * Sx + R) ? v1c : T(0);
       __syncwarp();
       T* cur = t0;
@@ -555,7 +927,8 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
           const int j = q / Sx, i = q % Sx;
           int c;
           T v = T(0);
-          if (cell(j, i, c)) v = ((q == Ry * Sx + R) ? v1c : T(0)) - ldn(rg, c, sl, cl) * th * boxnbr(cur, j, i, true);
+          if (cell(j, i, c))
+            v = ((q == Ry * Sx + R) ? v1c : T(0)) - *at(rg, c, g, cl) * th * boxnbr(cur, j, i, true);
           nxt[q] = v;
         }
         __syncwarp();
@@ -568,7 +941,7 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
       for (int q = lane; q < S2; q += 32) {
         const int j = q / Sx, i = q % Sx;
         int c;
-        t0[q] = cell(j, i, c) ? -ldn(ax, c, sl, cl) * z5[q] * ldn(rg, c, sl, cl) : T(0);
+        t0[q] = cell(j, i, c) ? -*at(ax, c, g, cl) * z5[q] * *at(rg, c, g, cl) : T(0);
       }
       __syncwarp();
       if (n_lo == 1) {
@@ -582,7 +955,7 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
             int c;
             T v = T(0);
             if (cell(j, i, c))
-              v = t0[q] - ldn(rg, c, sl, cl) * th * ldn(dp, c, sl, cl) * boxnbr(src, j, i, false);
+              v = t0[q] - *at(rg, c, g, cl) * th * *at(dp, c, g, cl) * boxnbr(src, j, i, false);
             dst[q] = v;
           }
           __syncwarp();
@@ -594,7 +967,7 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
     cl.sync();  // boxes ready; every rank has read Y(0) at the actuator cells
     // u fixed-point iteration on n_u numbers: y_lambda(act_a) = Y(0) + sum_b G_ab v3_b
     for (int it = 0; it < A.n_u_it; ++it) {
-      for (int a = threadIdx.x; a < nu; a += blockDim.x) {
+      for (int a = tid; a < nu; a += bd) {
         T y = sm.y4a[a];
         const int ca = sm.act[a], ixa = ca % mx, iya = ca / mx;
         for (int bb = 0; bb < nu; ++bb) {
@@ -606,20 +979,22 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
         sm.v3n[a] = (sm.b3[a] + th * tb0 * y) / auu;
       }
       __syncthreads();
-      for (int a = threadIdx.x; a < nu; a += blockDim.x) sm.v3[a] = sm.v3n[a];
+      for (int a = tid; a < nu; a += bd) sm.v3[a] = sm.v3n[a];
       __syncthreads();
     }
     // Y(v3) = Y(0) + sum_b v3_b Z(e_b) on this rank's cells
-    for (int e = threadIdx.x; e < nu * S2; e += blockDim.x) {
+    for (int e = tid; e < nu * S2; e += bd) {
       const int bb = e / S2, q = e % S2;
       const int cb = sm.act[bb];
       const int gy = cb / mx + q / Sx - Ry, gx = cb % mx + q % Sx - R;
       if (gx < 0 || gx >= mx || gy < 0 || gy >= my) continue;
       const int c = gy * mx + gx;
-      if (c < sl.lo || c >= sl.hi) continue;
+      const int qc = c - g.lo;
+      if (qc < 0 || qc >= n) continue;
+      const int p = g.pidx(qc);
       const T* z5 = boxes + (size_t)bb * 4 * S2;
-      atomicAdd(&y5c[c - sl.lo], sm.v3[bb] * z5[q]);
-      atomicAdd(&y4c[c - sl.lo], sm.v3[bb] * z5[S2 + q]);
+      atomicAdd(&y5c[p], sm.v3[bb] * z5[q]);
+      atomicAdd(&y4c[p], sm.v3[bb] * z5[S2 + q]);
     }
     __syncthreads();
   }
@@ -627,26 +1002,31 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
 
   // ---- P4: S_i <- S_i - alpha Delta s_i (float64) ----
   const double alpha = A.alpha;
-  double* Xo = A.xout[rd ^ 1];
-  double* Lo = A.lout[rd ^ 1];
+  double* Xo = A.xout[rd ^ 1] + so + g.lo;
+  double* Lo = A.lout[rd ^ 1] + so + g.lo;
   double* Uo = A.uout[rd ^ 1];
-  for (int c = sl.lo + threadIdx.x; c < sl.hi; c += blockDim.x) {
-    const int q = c - sl.lo;
-    Xo[so + c] = fma(alpha, to_double(y5c[q]), gx[q]);
-    Lo[so + c] = fma(alpha, to_double(y4c[q]), gl[q]);
-  }
+  struct D2 {
+    double x, l;
+  };
+  pass<CPT, D2>(n,
+      [&](int q) {
+        const int p = g.pidx(q);
+        return D2{fma(alpha, to_double(y5c[p]), OX(q, p)), fma(alpha, to_double(y4c[p]), OL(q, p))};
+      },
+      [&](int q, D2 o) {
+        Xo[q] = o.x;
+        Lo[q] = o.l;
+      });
   if (cl.rank == 0)
-    for (int a = threadIdx.x; a < nu; a += blockDim.x)
+    for (int a = tid; a < nu; a += bd)
       Uo[I.u_off + (long long)s * nu + a] = sm.u[a] - alpha * (double)sm.v3[a];
   cl.sync();
 }
 
-__device__ __forceinline__ double I_split_floor(const IterArgs& A, int b) {
-  return A.inst[b].split_floor;
-}
-
-template <typename T, int MODE>
-__global__ void __launch_bounds__(512) k_iterate(IterArgs A) {
+// CPT: cells per thread per pass round (2 or 4); with 4 the register budget
+// of a thread grows and the CTA is limited to 384 threads.
+template <typename T, int MODE, int CPT>
+__global__ void __launch_bounds__(CPT >= 4 ? 384 : 512) k_iterate(IterArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmallShared<T>& sm = *reinterpret_cast<SmallShared<T>*>(smem_raw);
   T* wk;
@@ -662,6 +1042,8 @@ __global__ void __launch_bounds__(512) k_iterate(IterArgs A) {
   Cl cl;
   cl.C = A.csize;
   cl.rank = (A.csize > 1) ? (int)cg::this_cluster().block_rank() : 0;
+  sm.amask[threadIdx.x] = 0ull;
+  if (MODE == MODE_ONESHOT) __syncthreads();  // solve mode: the prologue's barrier
   const int k = (MODE == MODE_SOLVE) ? *(volatile int*)A.iter_k : 0;
   const int n_clusters = gridDim.x / A.csize;
 
@@ -693,17 +1075,11 @@ __global__ void __launch_bounds__(512) k_iterate(IterArgs A) {
             if (!(r <= 1.79e308) || r > A.div_limit * fmax(r0, 1e-300)) st = ST_DIVERGED;
             else if (prev_full && r <= A.tol) st = ST_CONVERGED;
             else if (!prev_full) {
-              // leave the split residual once it is near its float32 floor:
-              // below the threshold, or stalled (no 2x progress over the window)
-              // within 100x of it (the early transient is far above)
-              const double thr = fmax(fmax(A.tol, A.split_min), I_split_floor(A, b));
-              if (r <= thr) {
-                switch_now = true;
-              } else if (k - 1 >= STALL_WINDOW && r <= 100.0 * thr) {
-                const int oslot = ((k - 1 - STALL_WINDOW) % RES_SLOTS) * A.n_inst + b;
-                const double ro = __longlong_as_double((long long)A.res_inf[oslot]);
-                if (r > 0.5 * ro) switch_now = true;
-              }
+              // leave the split residual once it can no longer show that the
+              // float64 residual is above the threshold: r minus its rounding
+              // bound at or below max(tol, split_min)
+              const double e = __longlong_as_double((long long)A.res_err[pslot]);
+              if (r - e <= fmax(A.tol, A.split_min)) switch_now = true;
             }
           }
           if (st != ST_RUNNING) {
@@ -723,6 +1099,7 @@ __global__ void __launch_bounds__(512) k_iterate(IterArgs A) {
               if (fl && ffrom > k) A.full_from[b] = k;
               const int nslot = ((k + 1) % RES_SLOTS) * A.n_inst + b;
               A.res_inf[nslot] = 0ull;
+              A.res_err[nslot] = 0ull;
               A.res_sq[nslot] = 0.0;
             }
           }
@@ -737,7 +1114,7 @@ __global__ void __launch_bounds__(512) k_iterate(IterArgs A) {
       if (sk) continue;  // uniform across the cluster: every rank read the same slots
       resid_only = (k == A.max_iter);
     }
-    process_item<T>(A, b, s, k, (MODE == MODE_SOLVE) ? (k & 1) : 0, full, resid_only, sm, wk,
+    process_item<T, CPT>(A, b, s, k, (MODE == MODE_SOLVE) ? (k & 1) : 0, full, resid_only, sm, wk,
                     cl, gstage);
   }
 
@@ -768,6 +1145,7 @@ __global__ void k_init_control(IterArgs A, int mode, int first_full, const doubl
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     for (int q = 0; q < RES_SLOTS; ++q) {
       A.res_inf[q * A.n_inst + b] = 0ull;
+      A.res_err[q * A.n_inst + b] = 0ull;
       A.res_sq[q * A.n_inst + b] = 0.0;
     }
     A.res_first[b] = 0ull;

@@ -49,7 +49,8 @@ class nmpc_opts(ctypes.Structure):
                 ("check_every", ctypes.c_int), ("alpha", ctypes.c_double),
                 ("div_limit", ctypes.c_double), ("threads", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("cluster", ctypes.c_int),
-                ("split_min", ctypes.c_double), ("u_local", ctypes.c_int)]
+                ("split_min", ctypes.c_double), ("u_local", ctypes.c_int),
+                ("cells", ctypes.c_int)]
 
 
 class nmpc_stats(ctypes.Structure):
