@@ -110,9 +110,10 @@ typedef struct {
                       actuator b; one full-field P^{-1} per iteration) when
                       n_lo <= 4 and the boxes fit; 0: n_u_it + 1 full-field
                       P^{-1} applications in the paper's literal order        */
-  int cells;       /* cells each thread carries through a pass at once, as
-                      independent dependency chains: 2 (CTAs of up to 512
-                      threads) or 4 (up to 384 threads); 0 = auto (2)        */
+  int cells;       /* target cells per thread (1..8) when threads is auto:
+                      each thread carries its cells through every pass of a
+                      work item as independent dependency chains; 0 = auto
+                      (4)                                                     */
 } nmpc_opts;
 
 typedef struct {

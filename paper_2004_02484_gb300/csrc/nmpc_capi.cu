@@ -70,7 +70,7 @@ struct nmpc_handle {
   unsigned long long* h_resinf = nullptr;
   // launch configuration
   int threads = 0;
-  int cpt = 2;
+  int cpt = 4;
   int grid = 0;
   int csize = 1;
   int slab_max = 0;
@@ -180,7 +180,7 @@ IterArgs make_args(nmpc_handle* h) {
 // length, threads, dynamic shared memory, grid.
 struct LaunchPlan {
   int threads = 0, csize = 1, slab_max = 0, grid = 0;
-  int cpt = 2;  // cells per thread per pass round (kernel variant)
+  int cpt = 4;  // cells per thread (kernel variant)
   size_t smem = 0;
   bool smem_mode = true;
   bool stage = true;  // float64 slab inputs staged in shared memory
@@ -196,49 +196,67 @@ int slab_cells(const InstDev& I, int C) {
   return ((nun + C - 1) / C) * unit;
 }
 
-// Length of a padded slab array: (rows + 2) (mx + 2) in 2D, cells + 2 in 1D
-// (halo rows or cells and zero pads around the slab), rounded up to 4 elements.
+// Records of a padded rank slab: (rows + 2) (mx + 2) in 2D, cells + 2 in 1D
+// (halo rows or cells and zero pads around the slab), even.
 int slab_stride(const InstDev& I, int C) {
   const int nun = (I.dim == 2) ? I.my : I.mx;
   const int per = (nun + C - 1) / C;
   const int len = (I.dim == 2) ? (per + 2) * (I.mx + 2) : per + 2;
-  return (len + 3) & ~3;
+  return (len + 1) & ~1;
 }
+
+// Largest cells per thread of the shared-memory kernels, and of a CTA.
+constexpr int MAX_NC = 8;
+constexpr int MAX_THREADS = 512;
+// Cells per thread of the global-slab kernel per round.
+constexpr int GLOBAL_NC = 4;
 
 template <typename T>
 size_t small_shared_bytes_t() {
   return (sizeof(nmpc_dev::SmallShared<T>) + 15) & ~size_t(15);
 }
 
-using IterKernel = void (*)(IterArgs);
+using IterKernel = void (*)(IterArgs, int);
 
-template <typename T, int MODE>
-IterKernel iter_kernel(int cpt) {
-  return cpt == 4 ? nmpc_dev::k_iterate<T, MODE, 4> : nmpc_dev::k_iterate<T, MODE, 2>;
+// Kernel variants: NC cells per thread (1, 2, 4, 8) with the slab in shared
+// memory, or the global-slab kernel.
+template <typename T>
+IterKernel iter_kernel(int nc, bool smem) {
+  if (!smem) return nmpc_dev::k_iterate<T, GLOBAL_NC, false>;
+  switch (nc) {
+    case 1: return nmpc_dev::k_iterate<T, 1, true>;
+    case 2: return nmpc_dev::k_iterate<T, 2, true>;
+    case 4: return nmpc_dev::k_iterate<T, 4, true>;
+    default: return nmpc_dev::k_iterate<T, 8, true>;
+  }
 }
 
-IterKernel iter_kernel_of(bool mixed, int mode, int cpt) {
-  if (mixed)
-    return mode == nmpc_dev::MODE_SOLVE ? iter_kernel<float, nmpc_dev::MODE_SOLVE>(cpt)
-                                        : iter_kernel<float, nmpc_dev::MODE_ONESHOT>(cpt);
-  return mode == nmpc_dev::MODE_SOLVE ? iter_kernel<double, nmpc_dev::MODE_SOLVE>(cpt)
-                                      : iter_kernel<double, nmpc_dev::MODE_ONESHOT>(cpt);
+IterKernel iter_kernel_of(bool mixed, int nc, bool smem) {
+  return mixed ? iter_kernel<float>(nc, smem) : iter_kernel<double>(nc, smem);
 }
 
-// Threads per CTA and cells per thread per pass round for a slab of `slab`
-// interior cells: about four cells per thread, at least 128 threads; two
-// cells per round unless asked for four (that kernel has the larger register
-// budget and at most 384 threads; measured slower on the workloads so far).
-void thread_shape(int slab, const nmpc_opts& o, int* threads, int* cpt) {
-  const int natural = std::max(128, ((slab / 4 + 31) / 32) * 32);
-  const int c = o.cells ? o.cells : 2;
-  *cpt = c;
-  *threads = o.threads ? o.threads : std::min(c == 4 ? 384 : 512, natural);
+// Threads per CTA and cells per thread for a shared-memory slab of `slab`
+// interior cells: opts.cells (default 4) cells per thread, at least 128
+// threads, at most 512; the kernel variant's cells per thread is the power of
+// two that covers the slab.  Returns false if no variant covers it.
+bool thread_shape(int slab, const nmpc_opts& o, int* threads, int* nc) {
+  const int target = o.cells ? o.cells : 4;
+  int t = o.threads;
+  if (!t) {
+    t = ((slab + target - 1) / target + 31) / 32 * 32;
+    t = std::min(MAX_THREADS, std::max(128, t));
+    while ((long long)MAX_NC * t < slab && t < MAX_THREADS) t += 32;
+  }
+  int c = 1;
+  while ((long long)c * t < slab && c < MAX_NC) c *= 2;
+  *threads = t;
+  *nc = c;
+  return (long long)c * t >= slab;
 }
 
 // Clusters of C CTAs (`threads` threads, `smem` bytes) the device keeps
 // resident at once for the iteration kernel.
-int clusters_resident(int C, int threads, int cpt, size_t smem, bool mixed) {
+int clusters_resident(int C, int threads, int nc, size_t smem, bool mixed) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(C * 256));
   cfg.blockDim = dim3((unsigned)threads);
@@ -252,7 +270,7 @@ int clusters_resident(int C, int threads, int cpt, size_t smem, bool mixed) {
   cfg.numAttrs = 1;
   int n = 0;
   cudaError_t e = cudaOccupancyMaxActiveClusters(
-      &n, (const void*)iter_kernel_of(mixed, nmpc_dev::MODE_SOLVE, cpt), &cfg);
+      &n, (const void*)iter_kernel_of(mixed, nc, true), &cfg);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -261,10 +279,11 @@ int clusters_resident(int C, int threads, int cpt, size_t smem, bool mixed) {
 }
 
 // Cluster size: the smallest that fits a stage slab (with the float64 inputs
-// staged in shared memory if possible) in shared memory, then grown up to 8
-// while every cluster of the batch stays resident in one wave; cluster sizes
-// above 8 are 16 only.  A stage that does not fit even at 16 runs one CTA per
-// stage on a global slab.
+// staged in shared memory if possible) in shared memory and in the threads
+// of a CTA (at most MAX_NC cells each), then grown up to 8 while every
+// cluster of the batch stays resident in one wave; cluster sizes above 8 are
+// 16 only.  A stage that does not fit even at 16 runs one CTA per stage on a
+// global slab.
 LaunchPlan plan_launch(const InstDev* insts, int n_inst, int n_work, const nmpc_opts& o,
                        bool mixed, int num_sms, int max_optin) {
   LaunchPlan P;
@@ -286,7 +305,7 @@ LaunchPlan plan_launch(const InstDev* insts, int n_inst, int n_work, const nmpc_
     for (int b = 0; b < n_inst; ++b) m = std::max(m, slab_cells(insts[b], C));
     return m;
   };
-  auto stride = [&](int C) {  // padded array length
+  auto stride = [&](int C) {  // records per slab
     int m = 0;
     for (int b = 0; b < n_inst; ++b) m = std::max(m, slab_stride(insts[b], C));
     return m;
@@ -294,11 +313,14 @@ LaunchPlan plan_launch(const InstDev* insts, int n_inst, int n_work, const nmpc_
   bool stage = true;
   auto bytes = [&](int C) {
     return small + P.box_bytes +
-           (size_t)stride(C) * (nmpc_dev::NUM_WORK_ARRAYS * elem +
-                              (stage ? nmpc_dev::NUM_STAGE_ARRAYS * sizeof(double) : 0));
+           (size_t)stride(C) * (nmpc_dev::NUM_FIELDS * elem +
+                                (stage ? nmpc_dev::NUM_SFIELDS * sizeof(double) : 0));
   };
   auto next_c = [](int C) { return C < 8 ? C + 1 : 16; };
-  auto fits = [&](int C) { return bytes(C) <= (size_t)max_optin; };
+  auto fits = [&](int C) {
+    int t, c;
+    return bytes(C) <= (size_t)max_optin && thread_shape(slab(C), o, &t, &c);
+  };
   int C = 1;
   if (o.cluster > 0) {
     C = o.cluster;
@@ -333,14 +355,19 @@ LaunchPlan plan_launch(const InstDev* insts, int n_inst, int n_work, const nmpc_
   P.stage = stage;
   P.csize = C;
   P.slab_max = stride(C);
-  thread_shape(slab(C), o, &P.threads, &P.cpt);
+  if (P.smem_mode) {
+    thread_shape(slab(C), o, &P.threads, &P.cpt);
+  } else {
+    P.threads = o.threads ? o.threads : MAX_THREADS;
+    P.cpt = GLOBAL_NC;
+  }
   P.smem = P.smem_mode ? bytes(C) : small;
   P.grid = n_work * C;
   return P;
 }
 
-template <typename T, int MODE>
-cudaError_t launch_k(const LaunchPlan& P, const IterArgs& A, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_k(const LaunchPlan& P, const IterArgs& A, cudaStream_t st, int mode) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)P.grid);
   cfg.blockDim = dim3((unsigned)P.threads);
@@ -353,7 +380,7 @@ cudaError_t launch_k(const LaunchPlan& P, const IterArgs& A, cudaStream_t st) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, iter_kernel<T, MODE>(P.cpt), A);
+  return cudaLaunchKernelEx(&cfg, iter_kernel<T>(P.cpt, P.smem_mode), A, mode);
 }
 
 LaunchPlan plan_of(const nmpc_handle* h) {
@@ -376,15 +403,14 @@ template <int MODE>
 cudaError_t launch_iterate(nmpc_handle* h, const IterArgs& A, cudaStream_t st) {
   h->launches++;
   const LaunchPlan P = plan_of(h);
-  return h->mixed ? launch_k<float, MODE>(P, A, st) : launch_k<double, MODE>(P, A, st);
+  return h->mixed ? launch_k<float>(P, A, st, MODE) : launch_k<double>(P, A, st, MODE);
 }
 
 template <typename T>
 cudaError_t configure_kernels(size_t smem) {
-  IterKernel fns[4] = {nmpc_dev::k_iterate<T, nmpc_dev::MODE_SOLVE, 2>,
-                       nmpc_dev::k_iterate<T, nmpc_dev::MODE_ONESHOT, 2>,
-                       nmpc_dev::k_iterate<T, nmpc_dev::MODE_SOLVE, 4>,
-                       nmpc_dev::k_iterate<T, nmpc_dev::MODE_ONESHOT, 4>};
+  IterKernel fns[5] = {nmpc_dev::k_iterate<T, 1, true>, nmpc_dev::k_iterate<T, 2, true>,
+                       nmpc_dev::k_iterate<T, 4, true>, nmpc_dev::k_iterate<T, 8, true>,
+                       nmpc_dev::k_iterate<T, GLOBAL_NC, false>};
   for (auto fn : fns) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -400,7 +426,7 @@ bool opts_ok(const nmpc_opts& o) {
          (o.precision == NMPC_FP64 || o.precision == NMPC_MIXED) && o.threads >= 0 &&
          o.threads <= 512 && (o.threads % 32) == 0 && o.cluster >= 0 && o.cluster <= 16 &&
          (o.cluster <= 8 || o.cluster == 16) && (o.split_min >= 0) &&
-         (o.cells == 0 || o.cells == 2 || o.cells == 4) && !(o.cells == 4 && o.threads > 384);
+         (o.cells >= 0 && o.cells <= 8);
 }
 
 int validate(const nmpc_desc* d) {
@@ -649,7 +675,7 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
   if (!P.smem_mode) {
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, iter_kernel_of(h->mixed, nmpc_dev::MODE_SOLVE, P.cpt), P.threads, P.smem);
+        &per_sm, iter_kernel_of(h->mixed, GLOBAL_NC, false), P.threads, P.smem);
     P.grid = std::min(h->n_work, std::max(1, per_sm) * std::max(1, h->num_sms));
   }
   h->threads = P.threads;
@@ -664,7 +690,7 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
   h->box_bytes = P.box_bytes;
   h->grid = P.grid;
   const size_t elem = h->mixed ? sizeof(float) : sizeof(double);
-  const size_t work_bytes = (size_t)nmpc_dev::NUM_WORK_ARRAYS * h->slab_max * elem + h->box_bytes;
+  const size_t work_bytes = (size_t)nmpc_dev::NUM_FIELDS * h->slab_max * elem + h->box_bytes;
 
   bool ok = true;
   auto A = [&](cudaError_t e) { ok = ok && (e == cudaSuccess); };
@@ -1033,7 +1059,7 @@ extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
   const bool smem_mode = P.smem_mode;
   if (!smem_mode) P.grid = std::min(N, std::max(1, num_sms));
   const size_t elem = mixed ? sizeof(float) : sizeof(double);
-  const long long slab = (long long)(((size_t)nmpc_dev::NUM_WORK_ARRAYS * P.slab_max * elem +
+  const long long slab = (long long)(((size_t)nmpc_dev::NUM_FIELDS * P.slab_max * elem +
                                       P.box_bytes + 255) & ~size_t(255));
 
   // workspace layout inside the static array
@@ -1135,9 +1161,9 @@ extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
   while (launched <= o.max_iter) {
     for (int i = 0; i < o.check_every; ++i) {
       if (mixed)
-        CK((launch_k<float, nmpc_dev::MODE_SOLVE>(P, A, st)));
+        CK((launch_k<float>(P, A, st, nmpc_dev::MODE_SOLVE)));
       else
-        CK((launch_k<double, nmpc_dev::MODE_SOLVE>(P, A, st)));
+        CK((launch_k<double>(P, A, st, nmpc_dev::MODE_SOLVE)));
     }
     launched += o.check_every;
     CK(cudaMemcpyAsync(&active, A.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));

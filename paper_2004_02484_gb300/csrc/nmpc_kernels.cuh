@@ -3,9 +3,10 @@
 // One thread-block cluster of C CTAs processes one (instance, stage) work
 // item of one upper-layer iteration (eq. 15); every stage of every instance
 // is updated at once from iterate k, so one launch is one iteration.  The
-// stage grid is split into C slabs (rows in 2D, segments in 1D); stencil
-// neighbours in another CTA's slab are read from its shared memory through
-// the cluster's distributed shared memory.  Inside a work item:
+// stage grid is split into C slabs (rows in 2D, segments in 1D) held as
+// padded records in shared memory; a CTA also stores its boundary values into
+// the neighbouring CTAs' halo records through the cluster's distributed shared
+// memory, so every stencil read is local.  Inside a work item:
 //   P1/P2 residual: the stage's KKT rows K_i (eq. 9) from x_{i-1}, s_i,
 //     lambda_{i+1}, the coefficient fields Phi'(x), A_xx and 1/diag(F_x) of
 //     the reordered stage block (eq. 21), and the residual norms.  Two forms:
@@ -32,8 +33,6 @@ namespace nmpc_dev {
 namespace cg = cooperative_groups;
 
 constexpr int RES_SLOTS = 16;    // rolling residual history per instance
-constexpr int NUM_WORK_ARRAYS = 11;
-constexpr int NUM_STAGE_ARRAYS = 5;  // float64 staging of x_i, lambda_i, x_{i-1}, lambda_{i+1}, ref
 constexpr int MAX_NU = 64;
 
 struct InstDev {
@@ -88,7 +87,7 @@ struct IterArgs {
   int stage;       // float64 slab inputs staged in shared memory (1) or read in place
   int local_u;     // u-iteration through the actuators' local responses (1) or full sweeps
   int box_r;       // half-width of a local-response box, 2 (n_lo - 1)
-  int slab_max;    // length of each padded slab array (halo rows and pads included)
+  int slab_max;    // records per slab (padded positions, halo rows and pads included)
   // lower-layer work arrays: shared memory (scratch == nullptr) or a global
   // slab of scratch_stride bytes per CTA
   char* scratch;
@@ -115,154 +114,179 @@ __device__ __forceinline__ int fdiv(int q, int d, float inv) {
   return j + (r >= d ? 1 : 0) - (r < 0 ? 1 : 0);
 }
 
-// A cluster rank's slab in the padded layout of its shared work arrays.  The
-// stage grid is split into whole rows (2D) or segments (1D), `per` rows or
-// cells per rank (the last non-empty rank may hold fewer, later ranks none).
-// 2D: slab cell (row j, column i) sits at p = (j + 1) W + i + 1, W = mx + 2;
-// padded rows 0 and rows + 1 hold the neighbouring ranks' boundary rows (the
-// halo) or zeros at the grid's Dirichlet ring, padded columns 0 and mx + 1
-// are zero.  1D: cell q sits at p = q + 1; positions 0 and n + 1 are halo or
-// zero.  Stencils then read their neighbours with no bounds tests, and a rank
-// that writes a boundary value also stores it into the neighbour's halo.
+// ---------------------------------------------------------------------------
+// Work-item slab in shared memory (or a global scratch slab).
+//
+// The stage grid is split across the C cluster ranks in whole rows (2D) or
+// segments (1D), `per` rows or cells per rank (the last non-empty rank may
+// hold fewer, later ranks none).  2D: a rank's slab is a padded layout of
+// (rows + 2) x W positions, W = mx + 2, interior cell (row j, column i) at
+// p = (j + 1) W + i + 1; padded rows 0 and rows + 1 hold the neighbouring
+// ranks' boundary rows (the halo) or zeros at the grid's Dirichlet ring,
+// columns 0 and W - 1 are zero.  1D: one padded row, cell q at p = q + 1,
+// positions 0 and n + 1 the halo or zero.  The five-point stencil reads
+// p +- 1 and p +- Wv with Wv = W in 2D and Wv = 0 in 1D (the cell itself,
+// under the zero vertical weight).  Each position holds one record of
+// NUM_FIELDS values of T (work record) and, when the float64 inputs are
+// staged, one record of NUM_SFIELDS doubles: a field access is one
+// shared-memory access at a fixed offset from the record.  A rank that writes
+// a boundary value also stores it into the neighbour's halo record.
+enum WField { F_B2 = 0, F_DP, F_AX, F_RG, F_V1, F_P1, F_Y5, F_W1, F_Y4, F_E1, F_E2, NUM_FIELDS };
+// NUM_FIELDS is odd: consecutive records start in distinct banks.
+// Split residual: float copies of x, lambda and Phi(x) in the F_Y5, F_W1 and
+// F_Y4 fields (dead before those are written).
+enum SField { S_X = 0, S_L, S_XP, S_LN, S_RF, S_PH };
+constexpr int NUM_SFIELDS = 7;  // 14 words per record: 16 consecutive records hit distinct bank pairs
+
 struct Geo {
-  int dim;
-  int mx, per;   // grid row length; rows (2D) / cells (1D) per rank
-  int cols;      // 2D: mx; 1D: n
-  int n;         // cells of this rank
-  int rows;      // 2D: rows of this rank; 1D: 1
-  int W;         // 2D: padded row stride mx + 2; 1D: 0
-  int lo;        // first grid cell of the slab
-  int r0;        // first grid row (2D) / cell (1D) of the slab
-  int edge;      // cells of the first (last) row: 2D mx, 1D 1
-  int up_off;    // shift into rank - 1's layout: its bottom halo row
-  int dn_off;    // shift back into rank + 1's layout: its top halo row
-  int plen;      // padded positions in use
-  bool up, dn;   // rank - 1 / rank + 1 hold cells (halo exchange partners)
-  float inv_cols, inv_W;
-  __device__ __forceinline__ int pidx(int q) const {
-    return (dim == 2) ? W + 1 + q + 2 * fdiv(q, cols, inv_cols) : q + 1;
-  }
+  int n;       // cells of this rank
+  int cols;    // cells per interior row: 2D mx, 1D n
+  int rows;    // interior rows: 2D slab rows, 1D 1
+  int W;       // padded row length
+  int Wv;      // position distance of the vertical stencil neighbours: 2D W, 1D 0
+  int p0;      // position of the first cell: 2D W + 1, 1D 1
+  int plen;    // padded positions: 2D (rows + 2) W, 1D n + 2
+  int lo;      // first grid cell of the slab
+  int r0;      // first grid row (2D) / cell (1D) of the slab
+  int per;     // rows (2D) / cells (1D) per rank
+  int edge;    // cells of the first (last) row: 2D mx, 1D 1
+  int up_off;  // position shift into rank - 1's layout (its bottom / right halo)
+  int dn_off;  // position shift back into rank + 1's layout (its top / left halo)
+  bool d2;     // 2D grid
+  bool up, dn; // rank - 1 / rank + 1 hold cells and exchange halos with this rank
 };
 
 __device__ __forceinline__ Geo geo_of(const InstDev& I, int C, int rank) {
   Geo g;
-  const bool d2 = (I.dim == 2);
-  g.dim = I.dim;
-  g.mx = I.mx;
-  const int nun = d2 ? I.my : I.mx;
+  g.d2 = (I.dim == 2);
+  const int nun = g.d2 ? I.my : I.mx;
   g.per = (nun + C - 1) / C;
   const int a = min(rank * g.per, nun), b = min(a + g.per, nun);
   g.r0 = a;
-  g.rows = d2 ? b - a : 1;
-  g.n = d2 ? (b - a) * I.mx : b - a;
-  g.cols = d2 ? I.mx : g.n;
-  g.W = d2 ? I.mx + 2 : 0;
-  g.lo = d2 ? a * I.mx : a;
-  g.edge = d2 ? I.mx : 1;
-  g.up_off = d2 ? g.per * g.W : g.per;
-  g.dn_off = d2 ? (b - a) * g.W : (b - a);
-  g.plen = d2 ? (b - a + 2) * g.W : (b - a) + 2;
+  g.n = g.d2 ? (b - a) * I.mx : b - a;
+  g.cols = g.d2 ? I.mx : b - a;
+  g.rows = g.d2 ? b - a : 1;
+  g.W = g.d2 ? I.mx + 2 : g.per + 2;
+  g.Wv = g.d2 ? g.W : 0;
+  g.p0 = g.d2 ? g.W + 1 : 1;
+  g.plen = g.d2 ? (g.rows + 2) * g.W : g.n + 2;
+  g.lo = g.d2 ? a * I.mx : a;
+  g.edge = g.d2 ? I.mx : 1;
+  g.up_off = g.d2 ? g.per * g.W : g.per;
+  g.dn_off = g.d2 ? (b - a) * g.W : (b - a);
   g.up = (rank > 0) && (b > a);
   g.dn = (b < nun) && (b > a);
-  g.inv_cols = 1.0f / (float)max(g.cols, 1);
-  g.inv_W = 1.0f / (float)max(g.W, 1);
   return g;
 }
 
-// Padded position of grid cell c in the slab of the rank that owns it.
-__device__ __forceinline__ int owner_of(int c, const Geo& g, int& p) {
-  if (g.dim == 2) {
-    const int row = c / g.mx, col = c - row * g.mx;
+// The NC cells a thread carries through a pass: positions, and bit masks of
+// the slots that hold a cell and of those whose value also goes to
+// rank - 1's / rank + 1's halo.  Slot k holds cell q = first + k blockDim.  A
+// slot past the slab gets position p0, whose stencil neighbours lie inside
+// every rank's records: its loads are harmless, its stores are skipped.
+template <int NC>
+struct Cells {
+  int p[NC];
+  unsigned valid, pu, pd;
+};
+
+template <int NC>
+__device__ __forceinline__ Cells<NC> cells_of(const Geo& g, int first) {
+  Cells<NC> cs;
+  cs.valid = 0u;
+  cs.pu = 0u;
+  cs.pd = 0u;
+  const int bd = blockDim.x;
+  const int cols = max(g.cols, 1);
+  int j = first / cols, i = first - j * cols;
+  const int dj = bd / cols, di = bd - dj * cols;
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    const int q = first + k * bd;
+    const bool v = q < g.n;
+    cs.p[k] = v ? g.p0 + j * g.W + i : g.p0;
+    cs.valid |= (v ? 1u : 0u) << k;
+    cs.pu |= ((v && g.up && q < g.edge) ? 1u : 0u) << k;
+    cs.pd |= ((v && g.dn && q >= g.n - g.edge) ? 1u : 0u) << k;
+    i += di;
+    j += dj;
+    if (i >= cols) {
+      i -= cols;
+      ++j;
+    }
+  }
+  return cs;
+}
+
+// Slot of a pass: mask bit (round * NC + k), slot k, cell q, position p, and
+// whether it holds a cell.
+struct Slot {
+  int kk, k, q, p;
+  bool v;
+};
+
+// One pass over the rank's cells.  Rounds of NC cells per thread (one round
+// for shared-memory slabs, whose cells the host sizes to fit; several for
+// global slabs); within a round, groups of G slots: every slot's loads and
+// arithmetic (ld) come before the group's stores (st), so a group forms G
+// independent dependency chains.
+template <int NC, int G, bool MULTI, typename V, typename LD, typename ST>
+__device__ __forceinline__ void pass(const Geo& g, const Cells<NC>& c0, LD ld, ST st) {
+  static_assert(NC % G == 0, "group size must divide the cells per thread");
+  const int rounds = MULTI ? (g.n + NC * (int)blockDim.x - 1) / (NC * (int)blockDim.x) : 1;
+  for (int r = 0; r < rounds; ++r) {
+    Cells<NC> cs = c0;
+    if (MULTI && r > 0) cs = cells_of<NC>(g, threadIdx.x + r * NC * blockDim.x);
+#pragma unroll
+    for (int k0 = 0; k0 < NC; k0 += G) {
+      V v[G];
+#pragma unroll
+      for (int k = 0; k < G; ++k) {
+        const Slot sl{r * NC + k0 + k, k0 + k, (int)threadIdx.x + (r * NC + k0 + k) * (int)blockDim.x,
+                      cs.p[k0 + k], ((cs.valid >> (k0 + k)) & 1u) != 0u};
+        v[k] = ld(sl, cs);
+      }
+#pragma unroll
+      for (int k = 0; k < G; ++k) {
+        const Slot sl{r * NC + k0 + k, k0 + k, (int)threadIdx.x + (r * NC + k0 + k) * (int)blockDim.x,
+                      cs.p[k0 + k], ((cs.valid >> (k0 + k)) & 1u) != 0u};
+        st(sl, cs, v[k]);
+      }
+    }
+  }
+}
+
+// Shared-memory address of a generic pointer into this CTA's shared memory,
+// and the same location in cluster rank r's shared memory.
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned map_rank(unsigned a, int r) {
+  unsigned out;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(a), "r"(r));
+  return out;
+}
+// Store v to a cluster shared-memory address when flag != 0 (predicated, no branch).
+__device__ __forceinline__ void push_if(unsigned addr, float v, unsigned flag) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %2, 0;\n @q st.shared::cluster.f32 [%0], %1;\n}"
+               :: "r"(addr), "f"(v), "r"(flag) : "memory");
+}
+__device__ __forceinline__ void push_if(unsigned addr, double v, unsigned flag) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %2, 0;\n @q st.shared::cluster.f64 [%0], %1;\n}"
+               :: "r"(addr), "d"(v), "r"(flag) : "memory");
+}
+
+// Rank owning grid cell c and its padded position there.
+__device__ __forceinline__ int owner_of(int c, const Geo& g, int mx, int& p) {
+  if (g.d2) {
+    const int row = c / mx, col = c - row * mx;
     const int r = row / g.per;
-    p = (row - r * g.per + 1) * (g.mx + 2) + col + 1;
+    p = (row - r * g.per + 1) * g.W + col + 1;
     return r;
   }
   const int r = c / g.per;
   p = c - r * g.per + 1;
   return r;
-}
-
-// Element of slab array `a` at grid cell c, in this rank's or another rank's
-// shared memory.
-template <typename T>
-__device__ __forceinline__ T* at(T* a, int c, const Geo& g, const Cl& cl) {
-  int p;
-  const int r = owner_of(c, g, p);
-  return (r == cl.rank) ? a + p : cl.map(a, r) + p;
-}
-
-// The neighbours' copies of a slab array (their halo rows receive this rank's
-// boundary values).
-template <typename T>
-struct Halo {
-  T* up;
-  T* dn;
-};
-
-template <typename T>
-__device__ __forceinline__ Halo<T> halo_of(T* a, const Geo& g, const Cl& cl) {
-  Halo<T> hl;
-  hl.up = g.up ? cl.map(a, cl.rank - 1) : nullptr;
-  hl.dn = g.dn ? cl.map(a, cl.rank + 1) : nullptr;
-  return hl;
-}
-
-// Store v at own cell q (padded position p) and, on a boundary row, into the
-// neighbours' halo.
-template <typename T>
-__device__ __forceinline__ void put(T* a, const Halo<T>& hl, const Geo& g, int q, int p, T v) {
-  a[p] = v;
-  if (g.up && q < g.edge) hl.up[p + g.up_off] = v;
-  if (g.dn && q >= g.n - g.edge) hl.dn[p - g.dn_off] = v;
-}
-
-// Zero the padded positions of `a` that no rank writes in a work item: the
-// column pads and the halo rows at the grid boundary (the Dirichlet ring).
-template <typename V>
-__device__ __forceinline__ void zero_ring(V* a, const Geo& g) {
-  if (g.n == 0) return;
-  if (g.dim == 2) {
-    for (int jj = threadIdx.x; jj < g.rows + 2; jj += blockDim.x) {
-      a[jj * g.W] = V(0);
-      a[jj * g.W + g.W - 1] = V(0);
-    }
-    if (!g.up)
-      for (int i = threadIdx.x; i < g.W; i += blockDim.x) a[i] = V(0);
-    if (!g.dn)
-      for (int i = threadIdx.x; i < g.W; i += blockDim.x) a[(g.rows + 1) * g.W + i] = V(0);
-  } else if (threadIdx.x == 0) {
-    if (!g.up) a[0] = V(0);
-    if (!g.dn) a[g.n + 1] = V(0);
-  }
-}
-
-// Weighted sum of the four (2D) or two (1D) stencil neighbours of padded
-// position p.
-template <typename V, typename F>
-__device__ __forceinline__ V stencil(const Geo& g, int p, V cx, V cy, F a) {
-  const V sx = a(p - 1) + a(p + 1);
-  if (g.dim == 2) return cx * sx + cy * (a(p - g.W) + a(p + g.W));
-  return cx * sx;
-}
-
-// One pass over the rank's n cells, CPT cells per thread per round: every
-// cell's loads and arithmetic (ld) come before any of the round's stores
-// (st), so the CPT cells form independent dependency chains.
-template <int CPT, typename V, typename LD, typename ST>
-__device__ __forceinline__ void pass(int n, LD ld, ST st) {
-  for (int base = threadIdx.x; base < n; base += CPT * blockDim.x) {
-    V v[CPT];
-#pragma unroll
-    for (int k = 0; k < CPT; ++k) {
-      const int q = base + k * blockDim.x;
-      if (q < n) v[k] = ld(q);
-    }
-#pragma unroll
-    for (int k = 0; k < CPT; ++k) {
-      const int q = base + k * blockDim.x;
-      if (q < n) st(q, v[k]);
-    }
-  }
 }
 
 __device__ __forceinline__ double phi_d(double w, double k0, double k1) {
@@ -393,7 +417,7 @@ __device__ __forceinline__ void block_reduce_store_f(float vmax, float vsq, floa
   }
 }
 
-// Per-work-item shared scalars (the NUM_WORK_ARRAYS slab arrays follow).
+// Per-work-item shared scalars (the slab records follow).
 template <typename T>
 struct SmallShared {
   unsigned long long amask[512];  // per thread: which of its cells carry an actuator
@@ -430,16 +454,21 @@ __device__ __forceinline__ void cp_async8(void* dst_smem, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
 }
 
-// gstage: NUM_STAGE_ARRAYS float64 arrays in shared memory in the padded
-// layout (x_i and lambda_i with their halo rows; x_{i-1}, lambda_{i+1}, ref at
-// the own cells), or nullptr (the stage is read from global memory in place).
-template <typename T, int CPT>
+// One (instance, stage) work item of an upper-layer iteration on this rank's
+// slab.  B: base of the slab region (shared memory when SMEM), work records at
+// byte offset wk_off, staged float64 records at st_off (when `staged`).
+template <typename T, int NC, bool SMEM>
 __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, bool full,
-                             bool resid_only, SmallShared<T>& sm, T* wk, const Cl& cl,
-                             double* gstage) {
+                             bool resid_only, SmallShared<T>& sm, char* B, int wk_off, int st_off,
+                             bool staged, const Cl& cl) {
+  constexpr int TS = (int)sizeof(T);
+  constexpr int RB = NUM_FIELDS * TS;  // bytes per work record
+  constexpr int SB = NUM_SFIELDS * 8;  // bytes per staged record
+  constexpr bool MULTI = !SMEM;        // global slabs: several rounds of cells per thread
+  constexpr int G2 = (NC >= 2) ? 2 : 1;  // residual pass: two cells per group (register budget)
   const InstDev I = A.inst[b];
   const Geo g = geo_of(I, cl.C, cl.rank);
-  const int nu = I.nu, N = I.N, ng = I.ng, n = g.n;
+  const int nu = I.nu, N = I.N, ng = I.ng;
   const int tid = threadIdx.x, bd = blockDim.x;
   const long long so = I.s_off + (long long)s * ng;
   const double* __restrict__ X = A.xin[rd];
@@ -450,31 +479,45 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
   const double h = I.h, cx = I.cx, cy = I.cy, k0 = I.k0, k1 = I.k1, b0 = I.b0;
   const double dcoef = 2.0 * (cx + cy);
   const bool last = (s == N - 1);
-  const int SM = A.slab_max;
   const int n_lo = A.n_lo;
   const bool wide = n_lo > 2;  // sweeps 3.. read dp and the previous sweep at neighbours
-  // the residual pass keeps many values live per cell: fewer cells per round
-  // (float64 form: one)
-  constexpr int RES_CPT = (CPT > 2) ? CPT / 2 : CPT;
-  constexpr int FULL_CPT = 1;
+  const int WRB = g.Wv * RB, WSB = g.Wv * SB;
+  const Cells<NC> c0 = cells_of<NC>(g, tid);
 
-  T* b2 = wk;               // costate row K3
-  T* dp = wk + 1 * SM;      // Phi'(x)
-  T* ax = wk + 2 * SM;      // A_xx
-  T* rg = wk + 3 * SM;      // 1 / diag(F_x)
-  T* v1 = wk + 4 * SM;      // first F_x sweep  D^{-1} c4,  c4 = F_u v3 - K1
-  T* p1 = wk + 5 * SM;      // Phi' * v1 (its neighbour product)
-  T* y5 = wk + 6 * SM;      // x-part of Y(v3)
-  T* w1 = wk + 7 * SM;      // first F_x^T sweep
-  T* y4 = wk + 8 * SM;      // lambda-part of Y(v3)
-  T* e1 = wk + 9 * SM;      // ping-pong spares for n_lo > 2
-  T* e2 = wk + 10 * SM;
-  // residual inputs, alive in P1-P2 only: float copies of x, lambda and Phi(x)
-  // (split residual), or Phi(x) in float64 (full residual, staged slab)
-  float* xf = reinterpret_cast<float*>(y5);
-  float* lf = reinterpret_cast<float*>(w1);
-  float* pf = reinterpret_cast<float*>(y4);
-  double* phid = reinterpret_cast<double*>(y5);
+  // field f of the work record at byte offset pb (relative to B); float view
+  // for the split residual's copies; staged field f of record sb
+  auto WV = [&](int pb, int f) -> T& { return *reinterpret_cast<T*>(B + pb + f * TS); };
+  auto WF = [&](int pb, int f) -> float& { return *reinterpret_cast<float*>(B + pb + f * TS); };
+  auto SV = [&](int sb, int f) -> double& { return *reinterpret_cast<double*>(B + sb + f * 8); };
+  auto wpos = [&](int p) { return wk_off + p * RB; };
+  auto spos = [&](int p) { return st_off + p * SB; };
+  // this CTA's work records in the neighbours' shared memory (halo stores)
+  // (mapa is given this CTA's record base, a valid local address; the
+  // position shifts are applied to the mapped address, and every store lands
+  // inside the neighbour's records)
+  unsigned up_base = 0u, dn_base = 0u;
+  if constexpr (SMEM) {
+    const unsigned mine = smem_u32(B) + (unsigned)wk_off;
+    if (g.up) up_base = map_rank(mine, cl.rank - 1) + (unsigned)(g.up_off * RB);
+    if (g.dn) dn_base = map_rank(mine, cl.rank + 1) - (unsigned)(g.dn_off * RB);
+  }
+  // store v into field f of own position p and of the neighbours' halo copies
+  // (slots past the slab store nothing)
+  auto put = [&](const Cells<NC>& cs, const Slot& sl, int f, T v) {
+    if (sl.v) WV(wpos(sl.p), f) = v;
+    if constexpr (SMEM) {
+      const unsigned rel = (unsigned)(sl.p * RB + f * TS);
+      push_if(up_base + rel, v, (cs.pu >> sl.k) & 1u);
+      push_if(dn_base + rel, v, (cs.pd >> sl.k) & 1u);
+    }
+  };
+  // generic pointer to field f at grid cell c (this rank's or another rank's record)
+  auto at = [&](int c, int f) -> T* {
+    int p;
+    const int r = owner_of(c, g, I.mx, p);
+    T* a = reinterpret_cast<T*>(B + wpos(p) + f * TS);
+    return (r == cl.rank) ? a : cl.map(a, r);
+  };
 
   // actuators: controls of this stage, and per thread a bit mask of which of
   // its cells carry one (cell q is bit q / blockDim of thread q % blockDim)
@@ -484,98 +527,126 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
     sm.u[a] = Uin[I.u_off + (long long)s * nu + a];
     sm.v3[a] = T(0);
     const int q = c - g.lo;
-    if (q >= 0 && q < n && q / bd < 64) atomicOr(&sm.amask[q % bd], 1ull << (q / bd));
+    if (q >= 0 && q < g.n && q / bd < 64) atomicOr(&sm.amask[q % bd], 1ull << (q / bd));
   }
-  double* sx = gstage;
-  double* sl_ = gstage + SM;
-  double* sxp = gstage + 2 * SM;
-  double* sln = gstage + 3 * SM;
-  double* srf = gstage + 4 * SM;
-  if (gstage) {
-    // asynchronous copies, all in flight at once; outside the grid: zero
+  // padded position pp -> grid cell (or -1 outside the grid), own flag
+  const float invW = 1.0f / (float)g.W;
+  auto grid_cell = [&](int pp, bool& own) {
+    if (g.d2) {
+      const int jj = fdiv(pp, g.W, invW), ii = pp - jj * g.W;
+      own = jj >= 1 && jj <= g.rows && ii >= 1 && ii <= g.cols;
+      const int gr = g.r0 - 1 + jj, gc = ii - 1;
+      return (gr >= 0 && gr < I.my && gc >= 0 && gc < I.mx) ? gr * I.mx + gc : -1;
+    }
+    own = pp >= 1 && pp <= g.n;
+    const int gc = g.r0 - 1 + pp;
+    return (gc >= 0 && gc < I.mx) ? gc : -1;
+  };
+  if (staged) {
+    // float64 inputs by asynchronous copies, all in flight at once; zero
+    // outside the grid
     for (int pp = tid; pp < g.plen; pp += bd) {
-      int row, col;
       bool own;
-      if (g.dim == 2) {
-        const int jj = fdiv(pp, g.W, g.inv_W);
-        row = g.r0 - 1 + jj;
-        col = pp - jj * g.W - 1;
-        own = jj >= 1 && jj <= g.rows;
-      } else {
-        row = 0;
-        col = g.r0 - 1 + pp;
-        own = pp >= 1 && pp <= n;
-      }
-      if (col >= 0 && col < I.mx && row >= 0 && row < I.my) {
-        const int c = row * I.mx + col;
-        cp_async8(sx + pp, X + so + c);
-        cp_async8(sl_ + pp, L + so + c);
+      const int c = grid_cell(pp, own);
+      const int sb = spos(pp);
+      if (c >= 0) {
+        cp_async8(&SV(sb, S_X), X + so + c);
+        cp_async8(&SV(sb, S_L), L + so + c);
         if (own) {
-          cp_async8(sxp + pp, (s == 0) ? x0 + c : X + so - ng + c);
-          if (!last) cp_async8(sln + pp, L + so + ng + c);
-          cp_async8(srf + pp, ref + c);
+          cp_async8(&SV(sb, S_XP), (s == 0) ? x0 + c : X + so - ng + c);
+          if (!last) cp_async8(&SV(sb, S_LN), L + so + ng + c);
+          cp_async8(&SV(sb, S_RF), ref + c);
         }
       } else {
-        sx[pp] = 0.0;
-        sl_[pp] = 0.0;
+        SV(sb, S_X) = 0.0;
+        SV(sb, S_L) = 0.0;
       }
     }
   }
-  zero_ring(p1, g);
-  if (wide) {
-    zero_ring(dp, g);
-    zero_ring(e1, g);
-    zero_ring(e2, g);
-  }
-  if (gstage) asm volatile("cp.async.wait_all;\n" ::);
-  __syncthreads();
-  // own-cell float64 inputs at cell q (padded position p)
-  auto OX = [&](int q, int p) { return gstage ? sx[p] : X[so + g.lo + q]; };
-  auto OL = [&](int q, int p) { return gstage ? sl_[p] : L[so + g.lo + q]; };
-  auto OXP = [&](int q, int p) {
-    return gstage ? sxp[p] : ((s == 0) ? x0[g.lo + q] : X[so - ng + g.lo + q]);
-  };
-  auto OLN = [&](int q, int p) { return gstage ? sln[p] : L[so + ng + g.lo + q]; };
-  auto ORF = [&](int q, int p) { return gstage ? srf[p] : ref[g.lo + q]; };
-  // float64 x or lambda at padded position pp read in place (zero outside the grid)
-  auto gpad = [&](const double* base, int pp) {
-    int row, col;
-    if (g.dim == 2) {
-      const int jj = fdiv(pp, g.W, g.inv_W);
-      row = g.r0 - 1 + jj;
-      col = pp - jj * g.W - 1;
-    } else {
-      row = 0;
-      col = g.r0 - 1 + pp;
+  // zero the work records that no rank writes in this item: the column pads
+  // and the halo rows at the grid boundary (2D), the halo cells at the grid
+  // boundary (1D)
+  if (g.n > 0) {
+    auto zrec = [&](int p) {
+#pragma unroll
+      for (int f = 0; f < NUM_FIELDS; ++f) WV(wpos(p), f) = T(0);
+    };
+    if (g.d2) {
+      for (int jj = tid; jj < g.rows + 2; jj += bd) {
+        zrec(jj * g.W);
+        zrec(jj * g.W + g.W - 1);
+      }
+      if (!g.up)
+        for (int i = tid; i < g.W; i += bd) zrec(i);
+      if (!g.dn)
+        for (int i = tid; i < g.W; i += bd) zrec((g.rows + 1) * g.W + i);
+    } else if (tid == 0) {
+      if (!g.up) zrec(0);
+      if (!g.dn) zrec(g.n + 1);
     }
-    return (col >= 0 && col < I.mx && row >= 0 && row < I.my) ? base[so + row * I.mx + col] : 0.0;
+  }
+  if (staged) asm volatile("cp.async.wait_all;\n" ::);
+  __syncthreads();
+  // own-cell float64 inputs of slot sl (staged record, or global memory for
+  // slots that hold a cell; zero otherwise)
+  auto OX = [&](const Slot& sl) {
+    return staged ? SV(spos(sl.p), S_X) : (sl.v ? X[so + g.lo + sl.q] : 0.0);
   };
+  auto OL = [&](const Slot& sl) {
+    return staged ? SV(spos(sl.p), S_L) : (sl.v ? L[so + g.lo + sl.q] : 0.0);
+  };
+  auto OXP = [&](const Slot& sl) {
+    return staged ? SV(spos(sl.p), S_XP)
+                  : (sl.v ? ((s == 0) ? x0[g.lo + sl.q] : X[so - ng + g.lo + sl.q]) : 0.0);
+  };
+  auto OLN = [&](const Slot& sl) {
+    return staged ? SV(spos(sl.p), S_LN) : (sl.v ? L[so + ng + g.lo + sl.q] : 0.0);
+  };
+  auto ORF = [&](const Slot& sl) { return staged ? SV(spos(sl.p), S_RF) : (sl.v ? ref[g.lo + sl.q] : 0.0); };
 
   // ---- P1: residual inputs on the padded slab, halo rows included ----
   const float k0f = (float)k0, k1h = (float)(0.5 * k1);
-  struct F3 { float x, l, p; };
   // magnitudes for the split residual's rounding bound: max |x|, |lambda| over
   // the padded slab, max |float64 difference|, |ref| over the own cells
   float4 mg = make_float4(0.f, 0.f, 0.f, 0.f);
   if (!full) {
-    pass<CPT, F3>(g.plen,
-        [&](int pp) {
-          F3 o;
-          o.x = d2f(gstage ? sx[pp] : gpad(X, pp));
-          o.l = d2f(gstage ? sl_[pp] : gpad(L, pp));
-          o.p = k0f * (o.x + k1h * o.x * o.x);
-          mg.x = fmaxf(mg.x, fabsf(o.x));
-          mg.y = fmaxf(mg.y, fabsf(o.l));
-          return o;
-        },
-        [&](int pp, F3 o) {
-          xf[pp] = o.x;
-          lf[pp] = o.l;
-          pf[pp] = o.p;
-        });
-  } else if (gstage) {
-    pass<CPT, double>(g.plen, [&](int pp) { return phi_d(sx[pp], k0, k1); },
-                      [&](int pp, double v) { phid[pp] = v; });
+    for (int p0 = tid; p0 < g.plen; p0 += 4 * bd) {
+      float xv[4], lv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int pp = p0 + u * bd;
+        double xd = 0.0, ld = 0.0;
+        if (pp < g.plen) {
+          if (staged) {
+            xd = SV(spos(pp), S_X);
+            ld = SV(spos(pp), S_L);
+          } else {
+            bool own;
+            const int c = grid_cell(pp, own);
+            if (c >= 0) {
+              xd = X[so + c];
+              ld = L[so + c];
+            }
+          }
+        }
+        xv[u] = d2f(xd);
+        lv[u] = d2f(ld);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int pp = p0 + u * bd;
+        if (pp < g.plen) {
+          const int pb = wpos(pp);
+          WF(pb, F_Y5) = xv[u];
+          WF(pb, F_W1) = lv[u];
+          WF(pb, F_Y4) = k0f * (xv[u] + k1h * xv[u] * xv[u]);
+          mg.x = fmaxf(mg.x, fabsf(xv[u]));
+          mg.y = fmaxf(mg.y, fabsf(lv[u]));
+        }
+      }
+    }
+  } else if (staged) {
+    for (int pp = tid; pp < g.plen; pp += bd) SV(spos(pp), S_PH) = phi_d(SV(spos(pp), S_X), k0, k1);
   }
   __syncthreads();
 
@@ -583,67 +654,61 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
   double vmax = 0.0, vsq = 0.0;
   float fmax_ = 0.0f, fsq = 0.0f;
   const T th = (T)h, tdc = (T)dcoef;
-  const float cxf = (float)cx, cyf = (float)cy, dcf = (float)dcoef, hf = (float)h;
-  const float k0f_ = (float)k0, k1f_ = (float)k1, qf_ = (float)I.q, b0f = (float)b0;
-  const float k01f = (float)(k0 * k1), hqff = last ? (float)(h * I.qf) : 0.0f;
-  const double hqf = h * I.qf;
   const unsigned long long amask = sm.amask[tid];
   sm.amask[tid] = 0ull;  // ready for the next work item
   struct P2Out {
-    int p;
-    bool act;
     T K1, K3, dp, ax;
+    bool act;
   };
-  const Halo<T> hdp = halo_of(dp, g, cl);
-  const Halo<T> hp1 = halo_of(p1, g, cl);
-  auto p2_store = [&](int q, P2Out o) {
-    if (resid_only) return;
-    const int p = o.p;
+  auto is_act = [&](const Slot& sl) {
+    if (sl.kk < 64) return ((amask >> sl.kk) & 1ull) != 0ull;
+    bool a_ = false;
+    for (int a = 0; a < nu; ++a) a_ |= (sm.act[a] == g.lo + sl.q);
+    return a_;
+  };
+  auto p2_store = [&](const Slot& sl, const Cells<NC>& cs, P2Out o) {
+    if (resid_only || !sl.v) return;
+    const int pb = wpos(sl.p);
     const T r = rcp_T(-T(1) - th * tdc * o.dp);
-    b2[p] = o.K3;
-    ax[p] = o.ax;
-    rg[p] = r;
+    WV(pb, F_B2) = o.K3;
+    WV(pb, F_AX) = o.ax;
+    WV(pb, F_RG) = r;
     const T v = -o.K1 * r;  // first sweep of F_x v5 = -K1 (v3 = 0)
-    v1[p] = v;
-    if (wide) put(dp, hdp, g, q, p, o.dp);
-    else dp[p] = o.dp;
-    put(p1, hp1, g, q, p, o.dp * v);
+    WV(pb, F_V1) = v;
+    if (wide) put(cs, sl, F_DP, o.dp);
+    else WV(pb, F_DP) = o.dp;
+    put(cs, sl, F_P1, o.dp * v);
     if (o.act) {
-      const int c = g.lo + q;
+      const int c = g.lo + sl.q;
       for (int a = 0; a < nu; ++a)
         if (sm.act[a] == c) sm.b1a[a] = o.K1;
     }
   };
   if (full) {
-    pass<FULL_CPT, P2Out>(n,
-        [&](int q) {
-          P2Out o;
-          const int p = g.pidx(q);
-          const int c = g.lo + q;
-          const int slot = q / bd;  // this cell's bit in the thread's mask
-          bool isact = (slot < 64) ? ((amask >> slot) & 1ull) != 0ull : false;
-          if (slot >= 64)
-            for (int a = 0; a < nu; ++a) isact |= (sm.act[a] == c);
-          o.p = p;
-          o.act = isact;
-          const double x = OX(q, p);
-          const double lam = OL(q, p);
-          const double xp = OXP(q, p);
-          const double rc_ = ORF(q, p);
-          const double ln = last ? hqf * (x - rc_) : OLN(q, p);
+    pass<NC, 1, MULTI, P2Out>(g, c0,
+        [&](const Slot& sl, const Cells<NC>&) {
+          P2Out o{T(0), T(0), T(0), T(0), false};
+          if (!sl.v) return o;
+          const bool valid = true;
+          const int c = g.lo + sl.q;
+          o.act = is_act(sl);
+          const double x = OX(sl), lam = OL(sl), xp = OXP(sl), rc_ = ORF(sl);
+          const double ln = last ? h * I.qf * (x - rc_) : OLN(sl);
           double srcd = 0.0;
-          if (isact) {
+          if (o.act) {
             for (int a = 0; a < nu; ++a)
               if (sm.act[a] == c) srcd += sm.u[a];
             srcd *= b0;
           }
           double lphi, mu;
-          if (gstage) {
-            lphi = stencil<double>(g, p, cx, cy, [&](int m) { return phid[m]; }) - dcoef * phid[p];
-            mu = stencil<double>(g, p, cx, cy, [&](int m) { return sl_[m]; }) - dcoef * lam;
+          if (staged) {
+            const int sb = spos(sl.p);
+            lphi = cx * (SV(sb - SB, S_PH) + SV(sb + SB, S_PH)) +
+                   cy * (SV(sb - WSB, S_PH) + SV(sb + WSB, S_PH)) - dcoef * SV(sb, S_PH);
+            mu = cx * (SV(sb - SB, S_L) + SV(sb + SB, S_L)) +
+                 cy * (SV(sb - WSB, S_L) + SV(sb + WSB, S_L)) - dcoef * lam;
           } else {
-            const int iy = (g.dim == 2) ? g.r0 + fdiv(q, g.cols, g.inv_cols) : 0;
-            const int ix = c - iy * I.mx;
+            const int iy = g.d2 ? c / I.mx : 0, ix = c - iy * I.mx;
             const double* Xs = X + so;
             const double* Ls = L + so;
             lphi = nbr_sum<double>(c, ix, iy, I.mx, I.my, cx, cy,
@@ -655,52 +720,55 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
           const double dphi = k0 * (1.0 + k1 * x);
           const double K1 = xp - x + h * (lphi + srcd);
           const double K3 = ln - lam + h * (I.q * (x - rc_) + dphi * mu);
-          vmax = fmax(vmax, fmax(abs_or_inf(K1), abs_or_inf(K3)));
-          vsq += K1 * K1 + K3 * K3;
+          if (valid) {
+            vmax = fmax(vmax, fmax(abs_or_inf(K1), abs_or_inf(K3)));
+            vsq += K1 * K1 + K3 * K3;
+          }
           o.K1 = to_T<T>(K1);
           o.K3 = to_T<T>(K3);
           o.dp = to_T<T>(dphi);
-          o.ax = to_T<T>(h * (I.q + k0 * k1 * mu) + (last ? hqf : 0.0));
+          o.ax = to_T<T>(h * (I.q + k0 * k1 * mu) + (last ? h * I.qf : 0.0));
           return o;
         },
         p2_store);
   } else {
-    pass<RES_CPT, P2Out>(n,
-        [&](int q) {
+    const float cxf = (float)cx, cyf = (float)cy, dcf = (float)dcoef, hf = (float)h;
+    const float k0f_ = (float)k0, k1f_ = (float)k1, qf_ = (float)I.q, b0f = (float)b0;
+    const float k01f = (float)(k0 * k1), hqff = last ? (float)(h * I.qf) : 0.0f;
+    pass<NC, G2, MULTI, P2Out>(g, c0,
+        [&](const Slot& sl, const Cells<NC>&) {
           P2Out o;
-          const int p = g.pidx(q);
-          const int c = g.lo + q;
-          const int slot = q / bd;  // this cell's bit in the thread's mask
-          bool isact = (slot < 64) ? ((amask >> slot) & 1ull) != 0ull : false;
-          if (slot >= 64)
-            for (int a = 0; a < nu; ++a) isact |= (sm.act[a] == c);
-          o.p = p;
-          o.act = isact;
-          const double x = OX(q, p);
-          const double lam = OL(q, p);
-          const double xp = OXP(q, p);
-          const double rc_ = ORF(q, p);
-          const float lphi = stencil<float>(g, p, cxf, cyf, [&](int m) { return pf[m]; }) - dcf * pf[p];
-          const float mu = stencil<float>(g, p, cxf, cyf, [&](int m) { return lf[m]; }) - dcf * lf[p];
-          const float xv = xf[p];
+          const bool valid = sl.v;
+          const int pb = wpos(sl.p);
+          o.act = valid && is_act(sl);
+          const float lphi = cxf * (WF(pb - RB, F_Y4) + WF(pb + RB, F_Y4)) +
+                             cyf * (WF(pb - WRB, F_Y4) + WF(pb + WRB, F_Y4)) - dcf * WF(pb, F_Y4);
+          const float mu = cxf * (WF(pb - RB, F_W1) + WF(pb + RB, F_W1)) +
+                           cyf * (WF(pb - WRB, F_W1) + WF(pb + WRB, F_W1)) - dcf * WF(pb, F_W1);
+          const float xv = WF(pb, F_Y5);
+          const double x = OX(sl), lam = OL(sl), xp = OXP(sl), rc_ = ORF(sl);
           const float rv = d2f(rc_);
           float srcf = 0.0f;
-          if (isact)
+          if (o.act) {
+            const int c = g.lo + sl.q;
             for (int a = 0; a < nu; ++a)
               if (sm.act[a] == c) srcf += d2f(sm.u[a]);
+          }
           const float dphi = k0f_ * (1.0f + k1f_ * xv);
           const float t1 = hf * (lphi + b0f * srcf);
           const float t3 = hf * (qf_ * (xv - rv) + dphi * mu);
           // the O(1) differences in float64; at the last stage lambda_{N+1} is
           // h qf (x_N - ref), an O(h) term
-          const double d3 = last ? -lam : OLN(q, p) - lam;
+          const double d3 = last ? -lam : OLN(sl) - lam;
           const float dx = d2f(xp - x), dl = d2f(d3);
-          mg.z = fmaxf(mg.z, fmaxf(fabsf(dx), fabsf(dl)));
-          mg.w = fmaxf(mg.w, fabsf(rv));
           const float K1 = dx + t1;
           const float K3 = dl + t3 + (last ? hqff * (xv - rv) : 0.0f);
-          fmax_ = fmaxf(fmax_, fmaxf(abs_or_inf_f(K1), abs_or_inf_f(K3)));
-          fsq += K1 * K1 + K3 * K3;
+          if (valid) {
+            mg.z = fmaxf(mg.z, fmaxf(fabsf(dx), fabsf(dl)));
+            mg.w = fmaxf(mg.w, fabsf(rv));
+            fmax_ = fmaxf(fmax_, fmaxf(abs_or_inf_f(K1), abs_or_inf_f(K3)));
+            fsq += K1 * K1 + K3 * K3;
+          }
           o.K1 = (T)K1;
           o.K3 = (T)K3;
           o.dp = (T)dphi;
@@ -758,41 +826,36 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
   if (resid_only) return;
 
   // ---- P3: lower layer in T ----
-  // the residual inputs are dead: restore the zero ring of the arrays they used
-  zero_ring(y5, g);
-  zero_ring(w1, g);
-  zero_ring(y4, g);
   const T tcx = (T)cx, tcy = (T)cy, tb0 = (T)b0;
   const T auu = (T)(h * I.r + I.gamma);
-  T* y5c = y5;
-  T* y4c = y4;
-  const Halo<T> hw1 = halo_of(w1, g, cl);
-  struct PV {
-    int p;
-    T v;
-  };
-  struct PV2 {
-    int p;
+  int y5f = F_Y5, y4f = F_Y4;  // fields holding Y(v3) = (v5, v4)
+  const int n_full = A.local_u ? 1 : A.n_u_it + 1;  // full-field Y applications
+  struct V2 {
     T v, w;
   };
-  const int n_full = A.local_u ? 1 : A.n_u_it + 1;  // full-field Y applications
   for (int it = 0; it < n_full; ++it) {
     if (it > 0) {
       // c4 = F_u v3 - K1 changes only on actuator cells: refresh v1, p1 there
       for (int a = tid; a < nu; a += bd) {
         const int c = sm.act[a];
         const int q = c - g.lo;
-        bool first = (q >= 0 && q < n);
+        bool first = (q >= 0 && q < g.n);
         for (int a2 = 0; a2 < a && first; ++a2)
           if (sm.act[a2] == c) first = false;
         if (first) {
           T inj = T(0);
           for (int a2 = 0; a2 < nu; ++a2)
             if (sm.act[a2] == c) inj += sm.v3[a2];
-          const int p = g.pidx(q);
-          const T v = (th * tb0 * inj - sm.b1a[a]) * rg[p];
-          v1[p] = v;
-          put(p1, hp1, g, q, p, dp[p] * v);
+          int p;
+          owner_of(c, g, I.mx, p);
+          const int pb = wpos(p);
+          const T v = (th * tb0 * inj - sm.b1a[a]) * WV(pb, F_RG);
+          WV(pb, F_V1) = v;
+          // halo copies of p1 for a boundary-row actuator cell
+          Cells<NC> one{};
+          one.pu = (g.up && q < g.edge) ? 1u : 0u;
+          one.pd = (g.dn && q >= g.n - g.edge) ? 1u : 0u;
+          put(one, Slot{0, 0, q, p, true}, F_P1, WV(pb, F_DP) * v);
         }
       }
       cl.sync();
@@ -800,86 +863,92 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
     // F_x v5 = c4 by n_lo pointwise Jacobi sweeps from zero: sweep 1 is v1;
     // sweep s+1 = v1 - D^{-1} (offdiag F_x) sweep s, reading neighbours.  The
     // last sweep also forms sweep 1 of F_x^T v4 = -K3 - A_xx v5 (own cells).
-    T* cur = v1;
+    int cur = F_V1;
     if (n_lo == 1) {
-      pass<CPT, PV>(n,
-          [&](int q) {
-            const int p = g.pidx(q);
-            return PV{p, (-b2[p] - ax[p] * v1[p]) * rg[p]};
+      pass<NC, NC, MULTI, T>(g, c0,
+          [&](const Slot& sl, const Cells<NC>&) {
+            const int pb = wpos(sl.p);
+            return (-WV(pb, F_B2) - WV(pb, F_AX) * WV(pb, F_V1)) * WV(pb, F_RG);
           },
-          [&](int q, PV o) { put(w1, hw1, g, q, o.p, o.v); });
+          [&](const Slot& sl, const Cells<NC>& cs, T w) { put(cs, sl, F_W1, w); });
     } else {
-      cur = y5;
-      const Halo<T> hc = halo_of(cur, g, cl);
+      cur = F_Y5;
       const bool lastsw = (n_lo == 2);
-      pass<CPT, PV2>(n,
-          [&](int q) {
-            const int p = g.pidx(q);
-            const T off = th * stencil<T>(g, p, tcx, tcy, [&](int m) { return p1[m]; });
-            const T v = v1[p] - rg[p] * off;
-            return PV2{p, v, (-b2[p] - ax[p] * v) * rg[p]};
+      pass<NC, NC, MULTI, V2>(g, c0,
+          [&](const Slot& sl, const Cells<NC>&) {
+            const int pb = wpos(sl.p);
+            const T off = th * (tcx * (WV(pb - RB, F_P1) + WV(pb + RB, F_P1)) +
+                                tcy * (WV(pb - WRB, F_P1) + WV(pb + WRB, F_P1)));
+            const T v = WV(pb, F_V1) - WV(pb, F_RG) * off;
+            return V2{v, (-WV(pb, F_B2) - WV(pb, F_AX) * v) * WV(pb, F_RG)};
           },
-          [&](int q, PV2 o) {
-            if (wide) put(cur, hc, g, q, o.p, o.v);
-            else cur[o.p] = o.v;
-            if (lastsw) put(w1, hw1, g, q, o.p, o.w);
+          [&](const Slot& sl, const Cells<NC>& cs, V2 o) {
+            if (wide) put(cs, sl, F_Y5, o.v);
+            else if (sl.v) WV(wpos(sl.p), F_Y5) = o.v;
+            if (lastsw) put(cs, sl, F_W1, o.w);
           });
-      T* nxt = e1;
+      int nxt = F_E1;
       for (int sw = 2; sw < n_lo; ++sw) {
         cl.sync();
-        const Halo<T> hn = halo_of(nxt, g, cl);
         const bool fin = (sw == n_lo - 1);
-        pass<CPT, PV2>(n,
-            [&](int q) {
-              const int p = g.pidx(q);
-              const T off = th * stencil<T>(g, p, tcx, tcy, [&](int m) { return dp[m] * cur[m]; });
-              const T v = v1[p] - rg[p] * off;
-              return PV2{p, v, (-b2[p] - ax[p] * v) * rg[p]};
+        const int cf = cur, nf = nxt;
+        pass<NC, NC, MULTI, V2>(g, c0,
+            [&](const Slot& sl, const Cells<NC>&) {
+              const int pb = wpos(sl.p);
+              const T off = th * (tcx * (WV(pb - RB, F_DP) * WV(pb - RB, cf) +
+                                         WV(pb + RB, F_DP) * WV(pb + RB, cf)) +
+                                  tcy * (WV(pb - WRB, F_DP) * WV(pb - WRB, cf) +
+                                         WV(pb + WRB, F_DP) * WV(pb + WRB, cf)));
+              const T v = WV(pb, F_V1) - WV(pb, F_RG) * off;
+              return V2{v, (-WV(pb, F_B2) - WV(pb, F_AX) * v) * WV(pb, F_RG)};
             },
-            [&](int q, PV2 o) {
-              put(nxt, hn, g, q, o.p, o.v);
-              if (fin) put(w1, hw1, g, q, o.p, o.w);
+            [&](const Slot& sl, const Cells<NC>& cs, V2 o) {
+              put(cs, sl, nf, o.v);
+              if (fin) put(cs, sl, F_W1, o.w);
             });
-        T* t = cur; cur = nxt; nxt = t;
+        const int t = cur; cur = nxt; nxt = t;
       }
     }
-    y5c = cur;
-    cur = w1;
+    y5f = cur;
+    cur = F_W1;
     if (n_lo >= 2) {
       cl.sync();
-      cur = y4;
-      const Halo<T> hc = halo_of(cur, g, cl);
-      pass<CPT, PV>(n,
-          [&](int q) {
-            const int p = g.pidx(q);
-            const T off = th * dp[p] * stencil<T>(g, p, tcx, tcy, [&](int m) { return w1[m]; });
-            return PV{p, w1[p] - rg[p] * off};
+      cur = F_Y4;
+      pass<NC, NC, MULTI, T>(g, c0,
+          [&](const Slot& sl, const Cells<NC>&) {
+            const int pb = wpos(sl.p);
+            const T off = th * WV(pb, F_DP) *
+                          (tcx * (WV(pb - RB, F_W1) + WV(pb + RB, F_W1)) +
+                           tcy * (WV(pb - WRB, F_W1) + WV(pb + WRB, F_W1)));
+            return WV(pb, F_W1) - WV(pb, F_RG) * off;
           },
-          [&](int q, PV o) {
-            if (wide) put(cur, hc, g, q, o.p, o.v);
-            else cur[o.p] = o.v;
+          [&](const Slot& sl, const Cells<NC>& cs, T v) {
+            if (wide) put(cs, sl, F_Y4, v);
+            else if (sl.v) WV(wpos(sl.p), F_Y4) = v;
           });
-      T* nxt = (y5c == e1) ? e2 : e1;  // the spare that does not hold v5
+      int nxt = (y5f == F_E1) ? F_E2 : F_E1;  // the spare that does not hold v5
       for (int sw = 2; sw < n_lo; ++sw) {
         cl.sync();
-        const Halo<T> hn = halo_of(nxt, g, cl);
-        pass<CPT, PV>(n,
-            [&](int q) {
-              const int p = g.pidx(q);
-              const T off = th * dp[p] * stencil<T>(g, p, tcx, tcy, [&](int m) { return cur[m]; });
-              return PV{p, w1[p] - rg[p] * off};
+        const int cf = cur, nf = nxt;
+        pass<NC, NC, MULTI, T>(g, c0,
+            [&](const Slot& sl, const Cells<NC>&) {
+              const int pb = wpos(sl.p);
+              const T off = th * WV(pb, F_DP) *
+                            (tcx * (WV(pb - RB, cf) + WV(pb + RB, cf)) +
+                             tcy * (WV(pb - WRB, cf) + WV(pb + WRB, cf)));
+              return WV(pb, F_W1) - WV(pb, F_RG) * off;
             },
-            [&](int q, PV o) { put(nxt, hn, g, q, o.p, o.v); });
-        T* t = cur; cur = nxt; nxt = t;
+            [&](const Slot& sl, const Cells<NC>& cs, T v) { put(cs, sl, nf, v); });
+        const int t = cur; cur = nxt; nxt = t;
       }
     }
-    y4c = cur;
+    y4f = cur;
     if (A.local_u || it < A.n_u_it) {
       cl.sync();  // Y(.) at the actuator cells is read across ranks below
       if (!A.local_u) {
         // A_uu v3 = K2 + F_u^T y_lambda (A_ux = 0); every rank keeps all of v3
         for (int a = tid; a < nu; a += bd)
-          sm.v3[a] = (sm.b3[a] + th * tb0 * *at(y4c, sm.act[a], g, cl)) / auu;
+          sm.v3[a] = (sm.b3[a] + th * tb0 * *at(sm.act[a], y4f)) / auu;
         __syncthreads();
       }
     }
@@ -889,12 +958,12 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
     // sweeps are linear and Z(e_b) vanishes outside a box of half-width
     // R = 2 (n_lo - 1) around actuator b (each sweep reaches one cell further).
     // The u-iteration then needs Y(0) at the actuator cells and the boxes.
-    for (int a = tid; a < nu; a += bd) sm.y4a[a] = *at(y4c, sm.act[a], g, cl);
+    for (int a = tid; a < nu; a += bd) sm.y4a[a] = *at(sm.act[a], y4f);
     const int R = A.box_r;
     const int mx = I.mx, my = I.my;
-    const int Sx = 2 * R + 1, Sy = (I.dim == 2) ? 2 * R + 1 : 1, Ry = (I.dim == 2) ? R : 0;
+    const int Sx = 2 * R + 1, Sy = g.d2 ? 2 * R + 1 : 1, Ry = g.d2 ? R : 0;
     const int S2 = Sx * Sy;
-    T* boxes = wk + (size_t)NUM_WORK_ARRAYS * SM;
+    T* boxes = reinterpret_cast<T*>(B + wpos(A.slab_max));  // after the work records
     const int lane = tid & 31, nw = bd >> 5;
     for (int bb = tid >> 5; bb < nu; bb += nw) {
       T* z5 = boxes + (size_t)bb * 4 * S2;
@@ -911,37 +980,37 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
       auto boxnbr = [&](const T* v, int j, int i, bool with_dp) {
         T sx = T(0), sy = T(0);
         int c;
-        if (i > 0 && cell(j, i - 1, c)) sx += (with_dp ? *at(dp, c, g, cl) : T(1)) * v[j * Sx + i - 1];
-        if (i < Sx - 1 && cell(j, i + 1, c)) sx += (with_dp ? *at(dp, c, g, cl) : T(1)) * v[j * Sx + i + 1];
-        if (j > 0 && cell(j - 1, i, c)) sy += (with_dp ? *at(dp, c, g, cl) : T(1)) * v[(j - 1) * Sx + i];
-        if (j < Sy - 1 && cell(j + 1, i, c)) sy += (with_dp ? *at(dp, c, g, cl) : T(1)) * v[(j + 1) * Sx + i];
+        if (i > 0 && cell(j, i - 1, c)) sx += (with_dp ? *at(c, F_DP) : T(1)) * v[j * Sx + i - 1];
+        if (i < Sx - 1 && cell(j, i + 1, c)) sx += (with_dp ? *at(c, F_DP) : T(1)) * v[j * Sx + i + 1];
+        if (j > 0 && cell(j - 1, i, c)) sy += (with_dp ? *at(c, F_DP) : T(1)) * v[(j - 1) * Sx + i];
+        if (j < Sy - 1 && cell(j + 1, i, c)) sy += (with_dp ? *at(c, F_DP) : T(1)) * v[(j + 1) * Sx + i];
         return tcx * sx + tcy * sy;
       };
-      const T v1c = th * tb0 * *at(rg, ca, g, cl);  // first F_x sweep: D^{-1} h b0 e_b
+      const T v1c = th * tb0 * *at(ca, F_RG);  // first F_x sweep: D^{-1} h b0 e_b
       for (int q = lane; q < S2; q += 32) t0[q] = (q == Ry * Sx + R) ? v1c : T(0);
       __syncwarp();
-      T* cur = t0;
-      T* nxt = t1;
+      T* cb = t0;
+      T* nb = t1;
       for (int sw = 1; sw < n_lo; ++sw) {
         for (int q = lane; q < S2; q += 32) {
           const int j = q / Sx, i = q % Sx;
           int c;
           T v = T(0);
           if (cell(j, i, c))
-            v = ((q == Ry * Sx + R) ? v1c : T(0)) - *at(rg, c, g, cl) * th * boxnbr(cur, j, i, true);
-          nxt[q] = v;
+            v = ((q == Ry * Sx + R) ? v1c : T(0)) - *at(c, F_RG) * th * boxnbr(cb, j, i, true);
+          nb[q] = v;
         }
         __syncwarp();
-        T* t = cur; cur = nxt; nxt = t;
+        T* t = cb; cb = nb; nb = t;
       }
-      for (int q = lane; q < S2; q += 32) z5[q] = cur[q];
+      for (int q = lane; q < S2; q += 32) z5[q] = cb[q];
       __syncwarp();
       // F_x^T sweeps with right-hand side -A_xx z5: w^1 stays in t0; the
       // n_lo - 1 later sweeps alternate between t1 and z4, the last one in z4
       for (int q = lane; q < S2; q += 32) {
         const int j = q / Sx, i = q % Sx;
         int c;
-        t0[q] = cell(j, i, c) ? -*at(ax, c, g, cl) * z5[q] * *at(rg, c, g, cl) : T(0);
+        t0[q] = cell(j, i, c) ? -*at(c, F_AX) * z5[q] * *at(c, F_RG) : T(0);
       }
       __syncwarp();
       if (n_lo == 1) {
@@ -955,7 +1024,7 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
             int c;
             T v = T(0);
             if (cell(j, i, c))
-              v = t0[q] - *at(rg, c, g, cl) * th * *at(dp, c, g, cl) * boxnbr(src, j, i, false);
+              v = t0[q] - *at(c, F_RG) * th * *at(c, F_DP) * boxnbr(src, j, i, false);
             dst[q] = v;
           }
           __syncwarp();
@@ -971,8 +1040,8 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
         T y = sm.y4a[a];
         const int ca = sm.act[a], ixa = ca % mx, iya = ca / mx;
         for (int bb = 0; bb < nu; ++bb) {
-          const int cb = sm.act[bb];
-          const int di = ixa - cb % mx + R, dj = iya - cb / mx + Ry;
+          const int cb2 = sm.act[bb];
+          const int di = ixa - cb2 % mx + R, dj = iya - cb2 / mx + Ry;
           if (di >= 0 && di < Sx && dj >= 0 && dj < Sy)
             y += sm.v3[bb] * boxes[(size_t)bb * 4 * S2 + S2 + dj * Sx + di];
         }
@@ -985,16 +1054,17 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
     // Y(v3) = Y(0) + sum_b v3_b Z(e_b) on this rank's cells
     for (int e = tid; e < nu * S2; e += bd) {
       const int bb = e / S2, q = e % S2;
-      const int cb = sm.act[bb];
-      const int gy = cb / mx + q / Sx - Ry, gx = cb % mx + q % Sx - R;
+      const int cb2 = sm.act[bb];
+      const int gy = cb2 / mx + q / Sx - Ry, gx = cb2 % mx + q % Sx - R;
       if (gx < 0 || gx >= mx || gy < 0 || gy >= my) continue;
       const int c = gy * mx + gx;
       const int qc = c - g.lo;
-      if (qc < 0 || qc >= n) continue;
-      const int p = g.pidx(qc);
+      if (qc < 0 || qc >= g.n) continue;
+      int p;
+      owner_of(c, g, mx, p);
       const T* z5 = boxes + (size_t)bb * 4 * S2;
-      atomicAdd(&y5c[p], sm.v3[bb] * z5[q]);
-      atomicAdd(&y4c[p], sm.v3[bb] * z5[S2 + q]);
+      atomicAdd(&WV(wpos(p), y5f), sm.v3[bb] * z5[q]);
+      atomicAdd(&WV(wpos(p), y4f), sm.v3[bb] * z5[S2 + q]);
     }
     __syncthreads();
   }
@@ -1008,14 +1078,17 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
   struct D2 {
     double x, l;
   };
-  pass<CPT, D2>(n,
-      [&](int q) {
-        const int p = g.pidx(q);
-        return D2{fma(alpha, to_double(y5c[p]), OX(q, p)), fma(alpha, to_double(y4c[p]), OL(q, p))};
+  const int f5 = y5f, f4 = y4f;
+  pass<NC, NC, MULTI, D2>(g, c0,
+      [&](const Slot& sl, const Cells<NC>&) {
+        const int pb = wpos(sl.p);
+        return D2{fma(alpha, to_double(WV(pb, f5)), OX(sl)), fma(alpha, to_double(WV(pb, f4)), OL(sl))};
       },
-      [&](int q, D2 o) {
-        Xo[q] = o.x;
-        Lo[q] = o.l;
+      [&](const Slot& sl, const Cells<NC>&, D2 o) {
+        if (sl.v) {
+          Xo[sl.q] = o.x;
+          Lo[sl.q] = o.l;
+        }
       });
   if (cl.rank == 0)
     for (int a = tid; a < nu; a += bd)
@@ -1023,21 +1096,26 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
   cl.sync();
 }
 
-// CPT: cells per thread per pass round (2 or 4); with 4 the register budget
-// of a thread grows and the CTA is limited to 384 threads.
-template <typename T, int MODE, int CPT>
-__global__ void __launch_bounds__(CPT >= 4 ? 384 : 512) k_iterate(IterArgs A) {
+// One upper-layer iteration (MODE_SOLVE: iteration iter_k of a running solve
+// with its convergence bookkeeping; MODE_ONESHOT: one residual or iteration
+// from the given buffers).  NC: cells per thread per pass round.  SMEM: the
+// slab records live in shared memory (a compile-time fact, so every record
+// access is a shared-memory access; one round of cells per thread) or in a
+// global scratch slab per CTA (several rounds).
+template <typename T, int NC, bool SMEM>
+__global__ void __launch_bounds__(512) k_iterate(IterArgs A, int MODE) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmallShared<T>& sm = *reinterpret_cast<SmallShared<T>*>(smem_raw);
-  T* wk;
-  double* gstage = nullptr;
-  if (A.scratch == nullptr) {
-    const size_t off = (sizeof(SmallShared<T>) + 15) & ~size_t(15);
-    gstage = A.stage ? reinterpret_cast<double*>(smem_raw + off) : nullptr;
-    wk = reinterpret_cast<T*>(
-        smem_raw + off + (A.stage ? (size_t)NUM_STAGE_ARRAYS * A.slab_max * sizeof(double) : 0));
+  char* B;
+  int wk_off = 0, st_off = 0;
+  bool staged = false;
+  if constexpr (SMEM) {
+    B = reinterpret_cast<char*>(smem_raw);
+    st_off = (int)((sizeof(SmallShared<T>) + 15) & ~size_t(15));
+    staged = (A.stage != 0);
+    wk_off = st_off + (staged ? A.slab_max * NUM_SFIELDS * 8 : 0);
   } else {
-    wk = reinterpret_cast<T*>(A.scratch + (long long)blockIdx.x * A.scratch_stride);
+    B = A.scratch + (long long)blockIdx.x * A.scratch_stride;
   }
   Cl cl;
   cl.C = A.csize;
@@ -1114,8 +1192,8 @@ __global__ void __launch_bounds__(CPT >= 4 ? 384 : 512) k_iterate(IterArgs A) {
       if (sk) continue;  // uniform across the cluster: every rank read the same slots
       resid_only = (k == A.max_iter);
     }
-    process_item<T, CPT>(A, b, s, k, (MODE == MODE_SOLVE) ? (k & 1) : 0, full, resid_only, sm, wk,
-                    cl, gstage);
+    process_item<T, NC, SMEM>(A, b, s, k, (MODE == MODE_SOLVE) ? (k & 1) : 0, full, resid_only, sm,
+                              B, wk_off, st_off, staged, cl);
   }
 
   if (MODE == MODE_SOLVE) {
