@@ -47,7 +47,7 @@ struct nmpc_handle {
   double* ub[3] = {nullptr, nullptr, nullptr};
   double* lb[3] = {nullptr, nullptr, nullptr};
   // control
-  int* ictl = nullptr;  // iter_k, block_done, n_active
+  int* ictl = nullptr;  // iter_k, (unused), n_active
   unsigned long long* res_inf = nullptr;
   unsigned long long* res_err = nullptr;
   double* res_sq = nullptr;
@@ -144,7 +144,6 @@ IterArgs make_args(nmpc_handle* h) {
     A.lout[q] = h->lb[q];
   }
   A.iter_k = h->ictl + 0;
-  A.block_done = h->ictl + 1;
   A.n_active = h->ictl + 2;
   A.res_inf = h->res_inf;
   A.res_err = h->res_err;
@@ -216,7 +215,7 @@ size_t small_shared_bytes_t() {
   return (sizeof(nmpc_dev::SmallShared<T>) + 15) & ~size_t(15);
 }
 
-using IterKernel = void (*)(IterArgs, int);
+using IterKernel = void (*)(IterArgs, int, int);
 
 // Kernel variants: NC cells per thread (1, 2, 4, 8) with the slab in shared
 // memory, or the global-slab kernel.
@@ -367,7 +366,7 @@ LaunchPlan plan_launch(const InstDev* insts, int n_inst, int n_work, const nmpc_
 }
 
 template <typename T>
-cudaError_t launch_k(const LaunchPlan& P, const IterArgs& A, cudaStream_t st, int mode) {
+cudaError_t launch_k(const LaunchPlan& P, const IterArgs& A, cudaStream_t st, int mode, int j) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)P.grid);
   cfg.blockDim = dim3((unsigned)P.threads);
@@ -380,7 +379,7 @@ cudaError_t launch_k(const LaunchPlan& P, const IterArgs& A, cudaStream_t st, in
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, iter_kernel<T>(P.cpt, P.smem_mode), A, mode);
+  return cudaLaunchKernelEx(&cfg, iter_kernel<T>(P.cpt, P.smem_mode), A, mode, j);
 }
 
 LaunchPlan plan_of(const nmpc_handle* h) {
@@ -400,10 +399,22 @@ LaunchPlan plan_of(const nmpc_handle* h) {
 }
 
 template <int MODE>
-cudaError_t launch_iterate(nmpc_handle* h, const IterArgs& A, cudaStream_t st) {
+cudaError_t launch_iterate(nmpc_handle* h, const IterArgs& A, cudaStream_t st, int j = 0) {
   h->launches++;
   const LaunchPlan P = plan_of(h);
-  return h->mixed ? launch_k<float>(P, A, st, MODE) : launch_k<double>(P, A, st, MODE);
+  return h->mixed ? launch_k<float>(P, A, st, MODE, j) : launch_k<double>(P, A, st, MODE, j);
+}
+
+// One chunk of solve iterations on stream st: launches j = 0 .. chunk - 1
+// (iterations *iter_k + j), then the counter advance.
+cudaError_t enqueue_chunk(nmpc_handle* h, const IterArgs& A, cudaStream_t st, int chunk) {
+  for (int i = 0; i < chunk; ++i) {
+    cudaError_t e = launch_iterate<nmpc_dev::MODE_SOLVE>(h, A, st, i);
+    if (e != cudaSuccess) return e;
+  }
+  nmpc_dev::k_advance<<<1, 32, 0, st>>>(A.iter_k, chunk);
+  h->launches++;
+  return cudaGetLastError();
 }
 
 template <typename T>
@@ -457,15 +468,14 @@ int run_chunk(nmpc_handle* h, const IterArgs& A, cudaStream_t st, int chunk) {
       CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
       cudaGraph_t g;
       CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-      for (int i = 0; i < chunk; ++i) {
-        cudaError_t e = launch_iterate<nmpc_dev::MODE_SOLVE>(h, A, cap);
-        if (e != cudaSuccess) {
-          cudaStreamEndCapture(cap, &g);
-          cudaStreamDestroy(cap);
-          return NMPC_ERR_CUDA;
-        }
+      const long long l0 = h->launches;
+      cudaError_t e = enqueue_chunk(h, A, cap, chunk);
+      h->launches = l0;  // capture is not execution
+      if (e != cudaSuccess) {
+        cudaStreamEndCapture(cap, &g);
+        cudaStreamDestroy(cap);
+        return NMPC_ERR_CUDA;
       }
-      h->launches -= chunk;  // capture is not execution
       CK(cudaStreamEndCapture(cap, &g));
       CK(cudaGraphInstantiate(&h->graph_exec, g, 0));
       cudaGraphDestroy(g);
@@ -473,9 +483,9 @@ int run_chunk(nmpc_handle* h, const IterArgs& A, cudaStream_t st, int chunk) {
       h->graph_chunk = chunk;
     }
     CK(cudaGraphLaunch(h->graph_exec, st));
-    h->launches += chunk;
+    h->launches += chunk + 1;
   } else {
-    for (int i = 0; i < chunk; ++i) CK(launch_iterate<nmpc_dev::MODE_SOLVE>(h, A, st));
+    CK(enqueue_chunk(h, A, st, chunk));
   }
   return NMPC_OK;
 }
@@ -647,6 +657,7 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
     const double dx = 1.0 / (d.mx + 1), dy = 1.0 / (d.my + 1);
     I.cx = 1.0 / (dx * dx);
     I.cy = (d.dim == 2) ? 1.0 / (dy * dy) : 0.0;
+    nmpc_dev::derive(I);
     for (int a = 0; a < d.n_u; ++a) act_all.push_back(d.act_cell[a]);
     h->nu_tot += d.n_u;
     for (int s = 0; s < d.horizon; ++s) work.push_back(make_int2(b, s));
@@ -1055,6 +1066,7 @@ extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
   const double dx = 1.0 / (d.mx + 1), dy = 1.0 / (d.my + 1);
   I.cx = 1.0 / (dx * dx);
   I.cy = (d.dim == 2) ? 1.0 / (dy * dy) : 0.0;
+  nmpc_dev::derive(I);
   LaunchPlan P = plan_launch(&I, 1, N, o, mixed, std::max(1, num_sms), max_optin);
   const bool smem_mode = P.smem_mode;
   if (!smem_mode) P.grid = std::min(N, std::max(1, num_sms));
@@ -1122,7 +1134,6 @@ extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
   }
   int* ctl = reinterpret_cast<int*>(base + o_ctl);
   A.iter_k = ctl + 0;
-  A.block_done = ctl + 1;
   A.n_active = ctl + 2;
   A.res_inf = reinterpret_cast<unsigned long long*>(base + o_rinf);
   A.res_err = reinterpret_cast<unsigned long long*>(base + o_rerr);
@@ -1161,10 +1172,12 @@ extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
   while (launched <= o.max_iter) {
     for (int i = 0; i < o.check_every; ++i) {
       if (mixed)
-        CK((launch_k<float>(P, A, st, nmpc_dev::MODE_SOLVE)));
+        CK((launch_k<float>(P, A, st, nmpc_dev::MODE_SOLVE, i)));
       else
-        CK((launch_k<double>(P, A, st, nmpc_dev::MODE_SOLVE)));
+        CK((launch_k<double>(P, A, st, nmpc_dev::MODE_SOLVE, i)));
     }
+    nmpc_dev::k_advance<<<1, 32, 0, st>>>(A.iter_k, o.check_every);
+    CK(cudaGetLastError());
     launched += o.check_every;
     CK(cudaMemcpyAsync(&active, A.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));

@@ -42,7 +42,29 @@ struct InstDev {
   long long u_off;  // offset in packed u
   long long g_off;  // offset in packed x0 / ref
   double h, q, r, qf, gamma, k0, k1, b0, cx, cy;
+  // derived (derive()): float64 2 (cx + cy), h qf, h r + gamma; float32 copies
+  double dcoef, hqf, auu;
+  float fh, fcx, fcy, fdc, fk0, fk1, fk1h, fk01, fq, fb0, fhqf, fauu;
 };
+
+// Fill the derived fields of an instance from its parameters.
+__host__ __device__ inline void derive(InstDev& I) {
+  I.dcoef = 2.0 * (I.cx + I.cy);
+  I.hqf = I.h * I.qf;
+  I.auu = I.h * I.r + I.gamma;
+  I.fh = (float)I.h;
+  I.fcx = (float)I.cx;
+  I.fcy = (float)I.cy;
+  I.fdc = (float)I.dcoef;
+  I.fk0 = (float)I.k0;
+  I.fk1 = (float)I.k1;
+  I.fk1h = (float)(0.5 * I.k1);
+  I.fk01 = (float)(I.k0 * I.k1);
+  I.fq = (float)I.q;
+  I.fb0 = (float)I.b0;
+  I.fhqf = (float)I.hqf;
+  I.fauu = (float)I.auu;
+}
 
 enum { MODE_SOLVE = 0, MODE_ONESHOT = 1 };
 enum { ST_RUNNING = 0, ST_CONVERGED = 1, ST_DIVERGED = 2, ST_MAX_ITER = 3 };
@@ -65,7 +87,6 @@ struct IterArgs {
   double* lout[2];
   // control (solve mode)
   int* iter_k;
-  int* block_done;
   unsigned long long* res_inf;   // [RES_SLOTS][n_inst], bits of non-negative doubles
   unsigned long long* res_err;   // [RES_SLOTS][n_inst] bound on a split residual's rounding error
   double* res_sq;                // [RES_SLOTS][n_inst]
@@ -298,9 +319,14 @@ __device__ __forceinline__ double abs_or_inf(double v) {
   return (a <= 1.79e308) ? a : CUDART_INF;  // NaN and Inf count as +Inf
 }
 
-__device__ __forceinline__ float abs_or_inf_f(float v) {
-  const float a = fabsf(v);
-  return (a <= 3.4e38f) ? a : CUDART_INF_F;
+// max(a, b) that returns NaN when either is NaN (one instruction)
+__device__ __forceinline__ float fmax_nan(float a, float b) {
+  float d;
+  asm("max.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+  return d;
+}
+__device__ __forceinline__ double dmax_nan(double a, double b) {
+  return (a != a) ? a : ((b != b || b > a) ? b : a);
 }
 
 // float64 <-> float32 by IEEE-754 bit manipulation on the integer ALUs (the
@@ -311,26 +337,23 @@ __device__ __forceinline__ float abs_or_inf_f(float v) {
 __device__ __forceinline__ float d2f(double d) {
   const unsigned hi = (unsigned)__double2hiint(d);
   const unsigned lo = (unsigned)__double2loint(d);
-  const unsigned sign = hi & 0x80000000u;
-  const int e = (int)((hi >> 20) & 0x7ffu) - 896;  // rebias 1023 -> 127
-  const unsigned man = ((hi & 0xfffffu) << 3) | (lo >> 29);
-  unsigned bits = sign | ((unsigned)e << 23) | man;
-  bits = (e <= 0) ? sign : bits;
-  bits = (e >= 255) ? (sign | 0x7f800000u) : bits;
-  return __uint_as_float(bits);
+  const unsigned a = hi & 0x7fffffffu;
+  // exponent rebiased (1023 -> 127) and the top 23 mantissa bits, in one funnel shift
+  unsigned bits = __funnelshift_l(lo, a - 0x38000000u, 3);
+  bits = (a < 0x38100000u) ? 0u : bits;           // below the float32 normal range
+  bits = (a >= 0x47f00000u) ? 0x7f800000u : bits;  // beyond it, Inf or NaN
+  return __uint_as_float(bits | (hi & 0x80000000u));
 }
 
 __device__ __forceinline__ double f2d(float f) {
   const unsigned b = __float_as_uint(f);
-  const unsigned sign = b & 0x80000000u;
-  const unsigned e = (b >> 23) & 0xffu;
-  const unsigned man = b & 0x7fffffu;
-  unsigned hi = sign | ((e + 896u) << 20) | (man >> 3);
-  unsigned lo = man << 29;
-  hi = (e == 0u) ? sign : hi;
-  lo = (e == 0u) ? 0u : lo;
-  hi = (e == 255u) ? (sign | 0x7ff00000u | (man >> 3)) : hi;
-  return __hiloint2double((int)hi, (int)lo);
+  const unsigned a = b & 0x7fffffffu;
+  unsigned hi = (a >> 3) + 0x38000000u;  // exponent rebiased (127 -> 1023)
+  unsigned lo = a << 29;
+  hi = (a < 0x00800000u) ? 0u : hi;  // zero or subnormal
+  lo = (a < 0x00800000u) ? 0u : lo;
+  hi = (a >= 0x7f800000u) ? (0x7ff00000u | (a >> 3)) : hi;  // Inf, NaN
+  return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)lo);
 }
 
 // Sum of the stencil neighbours' values, each weighted by its axis
@@ -382,7 +405,7 @@ __device__ __forceinline__ void block_reduce_store_f(float vmax, float vsq, floa
                                                      BlockRed* red, double* out_max,
                                                      double* out_sq, float* mags) {
   for (int o = 16; o > 0; o >>= 1) {
-    vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    vmax = fmax_nan(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
     vsq += __shfl_xor_sync(0xffffffffu, vsq, o);
     mg.x = fmaxf(mg.x, __shfl_xor_sync(0xffffffffu, mg.x, o));
     mg.y = fmaxf(mg.y, __shfl_xor_sync(0xffffffffu, mg.y, o));
@@ -401,7 +424,7 @@ __device__ __forceinline__ void block_reduce_store_f(float vmax, float vsq, floa
     float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
     const int nw = (blockDim.x + 31) >> 5;
     for (int w = 0; w < nw; ++w) {
-      m = fmax(m, red->mx[w]);
+      m = dmax_nan(m, red->mx[w]);
       s += red->sq[w];
       g.x = fmaxf(g.x, red->mg[w].x);
       g.y = fmaxf(g.y, red->mg[w].y);
@@ -430,6 +453,7 @@ struct SmallShared {
   T y4a[MAX_NU];  // lambda-part of Y(0) at each actuator cell
   T v3n[MAX_NU];
   int act[MAX_NU];
+  double lact[MAX_NU];  // lambda at the actuator cells
   int skip;
   int full;
 };
@@ -445,6 +469,14 @@ __device__ __forceinline__ float to_T<float>(double v) { return d2f(v); }
 template <>
 __device__ __forceinline__ double to_T<double>(double v) { return v; }
 
+// The float64 or the float32 copy of a constant, for arithmetic in T.
+template <typename T>
+__device__ __forceinline__ T pick(double d, float f);
+template <>
+__device__ __forceinline__ float pick<float>(double, float f) { return f; }
+template <>
+__device__ __forceinline__ double pick<double>(double d, float) { return d; }
+
 // 1 / v rounded to nearest (the same value as the IEEE division)
 __device__ __forceinline__ float rcp_T(float v) { return __frcp_rn(v); }
 __device__ __forceinline__ double rcp_T(double v) { return __drcp_rn(v); }
@@ -452,6 +484,17 @@ __device__ __forceinline__ double rcp_T(double v) { return __drcp_rn(v); }
 __device__ __forceinline__ void cp_async8(void* dst_smem, const void* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
+}
+
+// Residual norms of a work item (max, sum of squares) and, for the split
+// residual, its rounding bound, into iteration k's slot of instance b.
+__device__ __forceinline__ void publish_residual(const IterArgs& A, int slot, int b, int k,
+                                                 double rmax, double rsq, double e, bool full) {
+  if (!full) atomicMax(&A.res_err[slot], (unsigned long long)__double_as_longlong(e));
+  atomicMax(&A.res_inf[slot], (unsigned long long)__double_as_longlong(rmax));
+  atomicAdd(&A.res_sq[slot], rsq);
+  if (k == 0 && A.res_first)
+    atomicMax(&A.res_first[b], (unsigned long long)__double_as_longlong(rmax));
 }
 
 // One (instance, stage) work item of an upper-layer iteration on this rank's
@@ -477,7 +520,7 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
   const double* __restrict__ x0 = A.x0 + I.g_off;
   const double* __restrict__ ref = A.ref + I.g_off;
   const double h = I.h, cx = I.cx, cy = I.cy, k0 = I.k0, k1 = I.k1, b0 = I.b0;
-  const double dcoef = 2.0 * (cx + cy);
+  const double dcoef = I.dcoef;
   const bool last = (s == N - 1);
   const int n_lo = A.n_lo;
   const bool wide = n_lo > 2;  // sweeps 3.. read dp and the previous sweep at neighbours
@@ -525,6 +568,7 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
     const int c = A.act[I.act_off + a];
     sm.act[a] = c;
     sm.u[a] = Uin[I.u_off + (long long)s * nu + a];
+    sm.lact[a] = L[so + c];  // lambda at the actuator cell, for the stage-gradient row K2
     sm.v3[a] = T(0);
     const int q = c - g.lo;
     if (q >= 0 && q < g.n && q / bd < 64) atomicOr(&sm.amask[q % bd], 1ull << (q / bd));
@@ -605,7 +649,7 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
   auto ORF = [&](const Slot& sl) { return staged ? SV(spos(sl.p), S_RF) : (sl.v ? ref[g.lo + sl.q] : 0.0); };
 
   // ---- P1: residual inputs on the padded slab, halo rows included ----
-  const float k0f = (float)k0, k1h = (float)(0.5 * k1);
+  const float k0f = I.fk0, k1h = I.fk1h;
   // magnitudes for the split residual's rounding bound: max |x|, |lambda| over
   // the padded slab, max |float64 difference|, |ref| over the own cells
   float4 mg = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -653,7 +697,7 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
   // ---- P2: K_i (eq. 9), coefficient fields, norms ----
   double vmax = 0.0, vsq = 0.0;
   float fmax_ = 0.0f, fsq = 0.0f;
-  const T th = (T)h, tdc = (T)dcoef;
+  const T th = pick<T>(h, I.fh), tdc = pick<T>(dcoef, I.fdc);
   const unsigned long long amask = sm.amask[tid];
   sm.amask[tid] = 0ull;  // ready for the next work item
   struct P2Out {
@@ -661,22 +705,24 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
     bool act;
   };
   auto is_act = [&](const Slot& sl) {
-    if (sl.kk < 64) return ((amask >> sl.kk) & 1ull) != 0ull;
+    if (!MULTI || sl.kk < 64) return ((amask >> sl.kk) & 1ull) != 0ull;
     bool a_ = false;
     for (int a = 0; a < nu; ++a) a_ |= (sm.act[a] == g.lo + sl.q);
     return a_;
   };
   auto p2_store = [&](const Slot& sl, const Cells<NC>& cs, P2Out o) {
-    if (resid_only || !sl.v) return;
+    if (resid_only) return;
     const int pb = wpos(sl.p);
     const T r = rcp_T(-T(1) - th * tdc * o.dp);
-    WV(pb, F_B2) = o.K3;
-    WV(pb, F_AX) = o.ax;
-    WV(pb, F_RG) = r;
     const T v = -o.K1 * r;  // first sweep of F_x v5 = -K1 (v3 = 0)
-    WV(pb, F_V1) = v;
+    if (sl.v) {
+      WV(pb, F_B2) = o.K3;
+      WV(pb, F_AX) = o.ax;
+      WV(pb, F_RG) = r;
+      WV(pb, F_V1) = v;
+    }
     if (wide) put(cs, sl, F_DP, o.dp);
-    else WV(pb, F_DP) = o.dp;
+    else if (sl.v) WV(pb, F_DP) = o.dp;
     put(cs, sl, F_P1, o.dp * v);
     if (o.act) {
       const int c = g.lo + sl.q;
@@ -693,7 +739,7 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
           const int c = g.lo + sl.q;
           o.act = is_act(sl);
           const double x = OX(sl), lam = OL(sl), xp = OXP(sl), rc_ = ORF(sl);
-          const double ln = last ? h * I.qf * (x - rc_) : OLN(sl);
+          const double ln = last ? I.hqf * (x - rc_) : OLN(sl);
           double srcd = 0.0;
           if (o.act) {
             for (int a = 0; a < nu; ++a)
@@ -727,14 +773,14 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
           o.K1 = to_T<T>(K1);
           o.K3 = to_T<T>(K3);
           o.dp = to_T<T>(dphi);
-          o.ax = to_T<T>(h * (I.q + k0 * k1 * mu) + (last ? h * I.qf : 0.0));
+          o.ax = to_T<T>(h * (I.q + k0 * k1 * mu) + (last ? I.hqf : 0.0));
           return o;
         },
         p2_store);
   } else {
-    const float cxf = (float)cx, cyf = (float)cy, dcf = (float)dcoef, hf = (float)h;
-    const float k0f_ = (float)k0, k1f_ = (float)k1, qf_ = (float)I.q, b0f = (float)b0;
-    const float k01f = (float)(k0 * k1), hqff = last ? (float)(h * I.qf) : 0.0f;
+    const float cxf = I.fcx, cyf = I.fcy, dcf = I.fdc, hf = I.fh;
+    const float k0f_ = I.fk0, k1f_ = I.fk1, qf_ = I.fq, b0f = I.fb0;
+    const float k01f = I.fk01, hqff = last ? I.fhqf : 0.0f;
     pass<NC, G2, MULTI, P2Out>(g, c0,
         [&](const Slot& sl, const Cells<NC>&) {
           P2Out o;
@@ -763,12 +809,12 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
           const float dx = d2f(xp - x), dl = d2f(d3);
           const float K1 = dx + t1;
           const float K3 = dl + t3 + (last ? hqff * (xv - rv) : 0.0f);
-          if (valid) {
-            mg.z = fmaxf(mg.z, fmaxf(fabsf(dx), fabsf(dl)));
-            mg.w = fmaxf(mg.w, fabsf(rv));
-            fmax_ = fmaxf(fmax_, fmaxf(abs_or_inf_f(K1), abs_or_inf_f(K3)));
-            fsq += K1 * K1 + K3 * K3;
-          }
+          // slots past the slab contribute nothing (selects, no branch)
+          const float K1v = valid ? K1 : 0.0f, K3v = valid ? K3 : 0.0f;
+          mg.z = fmaxf(mg.z, valid ? fmaxf(fabsf(dx), fabsf(dl)) : 0.0f);
+          mg.w = fmaxf(mg.w, valid ? fabsf(rv) : 0.0f);
+          fmax_ = fmax_nan(fmax_, fmax_nan(fabsf(K1v), fabsf(K3v)));
+          fsq += K1v * K1v + K3v * K3v;
           o.K1 = (T)K1;
           o.K3 = (T)K3;
           o.dp = (T)dphi;
@@ -778,14 +824,14 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
         p2_store);
   }
   for (int a = tid; a < nu; a += bd) {
-    const double K2 = h * (I.r * sm.u[a] + b0 * L[so + sm.act[a]]);
+    const double K2 = h * (I.r * sm.u[a] + b0 * sm.lact[a]);
     if (cl.rank == 0) {
       if (full) {
         vmax = fmax(vmax, abs_or_inf(K2));
         vsq += K2 * K2;
       } else {
         const float K2f = d2f(K2);
-        fmax_ = fmaxf(fmax_, abs_or_inf_f(K2f));
+        fmax_ = fmax_nan(fmax_, fabsf(K2f));
         fsq += K2f * K2f;
         mg.z = fmaxf(mg.z, fabsf(K2f));
       }
@@ -797,6 +843,7 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
   else block_reduce_store_f(fmax_, fsq, mg, &sm.red, &sm.red_out[0], &sm.red_out[1], mags);
   if (tid == 0) {
     const int slot = (k % RES_SLOTS) * A.n_inst + b;
+    double e = 0.0;
     if (!full) {
       // Rounding bound of the split residual on this slab (unit roundoff
       // u = 2^-24).  x and lambda are truncated to float32 (2u), Phi, Phi' and
@@ -805,29 +852,29 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
       // is off by at most 16 u h S, S = 4 (cx + cy) (Phi_max + Phi'_max Lm) +
       // b0 sum|u| + (q + qf [last stage]) (X + max|ref|); the float64
       // differences and the stage-gradient rows are truncated once (2u) and
-      // summed (u).  Every cell's |K_split - K| is below the bound.
-      const double u32 = 5.9604644775390625e-08;
-      const double Xm = f2d(mags[0]), Lm = f2d(mags[1]), Dm = f2d(mags[2]), Rm = f2d(mags[3]);
-      double usum = 0.0;
-      for (int a = 0; a < nu; ++a) usum += fabs(sm.u[a]);
-      const double pmax = fabs(k0) * (Xm + 0.5 * fabs(k1) * Xm * Xm);
-      const double dpmax = fabs(k0) * (1.0 + fabs(k1) * Xm);
-      const double S = 4.0 * (cx + cy) * (pmax + dpmax * Lm) + fabs(b0) * usum +
-                       (I.q + (last ? I.qf : 0.0)) * (Xm + Rm);
-      const double e = u32 * (3.0 * Dm + 16.0 * h * S);
-      atomicMax(&A.res_err[slot], (unsigned long long)__double_as_longlong(e));
+      // summed (u).  Every cell's |K_split - K| is below the bound.  It is
+      // evaluated in float32 (its own rounding, a few u relative, is far
+      // inside the factor 16) and rounded up by 1%.
+      const float u32 = 5.9604645e-08f;
+      const float Xm = mags[0], Lm = mags[1], Dm = mags[2], Rm = mags[3];
+      float usum = 0.0f;
+      for (int a = 0; a < nu; ++a) usum += fabsf(d2f(sm.u[a]));
+      const float ak0 = fabsf(I.fk0), ak1 = fabsf(I.fk1);
+      const float pmax = ak0 * (Xm + 0.5f * ak1 * Xm * Xm);
+      const float dpmax = ak0 * (1.0f + ak1 * Xm);
+      const float S = 2.0f * I.fdc * (pmax + dpmax * Lm) + fabsf(I.fb0) * usum +
+                      (I.fq + (last ? I.fhqf / I.fh : 0.0f)) * (Xm + Rm);
+      e = f2d(1.01f * u32 * (3.0f * Dm + 16.0f * I.fh * S));
     }
-    atomicMax(&A.res_inf[slot], (unsigned long long)__double_as_longlong(sm.red_out[0]));
-    atomicAdd(&A.res_sq[slot], sm.red_out[1]);
-    if (k == 0 && A.res_first)
-      atomicMax(&A.res_first[b], (unsigned long long)__double_as_longlong(sm.red_out[0]));
+    // each CTA's own atomics, issued before the barrier (they do not block)
+    publish_residual(A, slot, b, k, sm.red_out[0], sm.red_out[1], e, full);
   }
   cl.sync();
   if (resid_only) return;
 
   // ---- P3: lower layer in T ----
-  const T tcx = (T)cx, tcy = (T)cy, tb0 = (T)b0;
-  const T auu = (T)(h * I.r + I.gamma);
+  const T tcx = pick<T>(cx, I.fcx), tcy = pick<T>(cy, I.fcy), tb0 = pick<T>(b0, I.fb0);
+  const T auu = pick<T>(I.auu, I.fauu);
   int y5f = F_Y5, y4f = F_Y4;  // fields holding Y(v3) = (v5, v4)
   const int n_full = A.local_u ? 1 : A.n_u_it + 1;  // full-field Y applications
   struct V2 {
@@ -1096,14 +1143,15 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
   cl.sync();
 }
 
-// One upper-layer iteration (MODE_SOLVE: iteration iter_k of a running solve
-// with its convergence bookkeeping; MODE_ONESHOT: one residual or iteration
-// from the given buffers).  NC: cells per thread per pass round.  SMEM: the
+// One upper-layer iteration (MODE_SOLVE: iteration *iter_k + j of a running
+// solve with its convergence bookkeeping, j the launch's index in its chunk
+// (k_advance moves *iter_k on after each chunk); MODE_ONESHOT: one residual or
+// iteration from the given buffers).  NC: cells per thread per pass round.  SMEM: the
 // slab records live in shared memory (a compile-time fact, so every record
 // access is a shared-memory access; one round of cells per thread) or in a
 // global scratch slab per CTA (several rounds).
 template <typename T, int NC, bool SMEM>
-__global__ void __launch_bounds__(512) k_iterate(IterArgs A, int MODE) {
+__global__ void __launch_bounds__(512) k_iterate(IterArgs A, int MODE, int j) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SmallShared<T>& sm = *reinterpret_cast<SmallShared<T>*>(smem_raw);
   char* B;
@@ -1122,7 +1170,7 @@ __global__ void __launch_bounds__(512) k_iterate(IterArgs A, int MODE) {
   cl.rank = (A.csize > 1) ? (int)cg::this_cluster().block_rank() : 0;
   sm.amask[threadIdx.x] = 0ull;
   if (MODE == MODE_ONESHOT) __syncthreads();  // solve mode: the prologue's barrier
-  const int k = (MODE == MODE_SOLVE) ? *(volatile int*)A.iter_k : 0;
+  const int k = (MODE == MODE_SOLVE) ? *(volatile int*)A.iter_k + j : 0;
   const int n_clusters = gridDim.x / A.csize;
 
   for (int w = blockIdx.x / A.csize; w < A.n_work; w += n_clusters) {
@@ -1136,19 +1184,23 @@ __global__ void __launch_bounds__(512) k_iterate(IterArgs A, int MODE) {
     } else {
       if (threadIdx.x == 0) {
         int skip = 0, fl = 1;
-        if (k > A.max_iter || A.status[b] != ST_RUNNING) {
+        // every control word this decision reads, loaded at once
+        const int pslot = (k > 0) ? ((k - 1) % RES_SLOTS) * A.n_inst + b : 0;
+        const int status_b = A.status[b];
+        const int ffrom = A.full_from[b];
+        const int f0 = A.full0[b];
+        const unsigned long long r_bits = A.res_inf[pslot];
+        const unsigned long long r0_bits = A.res_first[b];
+        const unsigned long long e_bits = A.res_err[pslot];
+        if (k > A.max_iter || status_b != ST_RUNNING) {
           skip = 1;
         } else {
-          const int ffrom = A.full_from[b];
-          const int f0 = A.full0[b];
           int st = ST_RUNNING;
           bool switch_now = false;
           double r = 0.0;
-          int pslot = 0;
           if (k > 0) {
-            pslot = ((k - 1) % RES_SLOTS) * A.n_inst + b;
-            r = __longlong_as_double((long long)A.res_inf[pslot]);
-            const double r0 = __longlong_as_double((long long)A.res_first[b]);
+            r = __longlong_as_double((long long)r_bits);
+            const double r0 = __longlong_as_double((long long)r0_bits);
             const bool prev_full = (k - 1 >= ffrom) || (k == 1 && f0);
             if (!(r <= 1.79e308) || r > A.div_limit * fmax(r0, 1e-300)) st = ST_DIVERGED;
             else if (prev_full && r <= A.tol) st = ST_CONVERGED;
@@ -1156,7 +1208,7 @@ __global__ void __launch_bounds__(512) k_iterate(IterArgs A, int MODE) {
               // leave the split residual once it can no longer show that the
               // float64 residual is above the threshold: r minus its rounding
               // bound at or below max(tol, split_min)
-              const double e = __longlong_as_double((long long)A.res_err[pslot]);
+              const double e = __longlong_as_double((long long)e_bits);
               if (r - e <= fmax(A.tol, A.split_min)) switch_now = true;
             }
           }
@@ -1196,18 +1248,12 @@ __global__ void __launch_bounds__(512) k_iterate(IterArgs A, int MODE) {
                               B, wk_off, st_off, staged, cl);
   }
 
-  if (MODE == MODE_SOLVE) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      const int d = atomicAdd(A.block_done, 1);
-      if (d == (int)gridDim.x - 1) {
-        *A.block_done = 0;
-        *A.iter_k = k + 1;
-        __threadfence();
-      }
-    }
-  }
+}
+
+// After a chunk of n iteration launches: the next chunk starts at iteration
+// *iter_k + n.
+__global__ void k_advance(int* iter_k, int n) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *iter_k += n;
 }
 
 // Reset the per-instance control and write S^0 into buffer 0: the cold start
@@ -1237,7 +1283,6 @@ __global__ void k_init_control(IterArgs A, int mode, int first_full, const doubl
     if (b == 0) {
       *A.n_active = A.n_inst;
       *A.iter_k = 0;
-      *A.block_done = 0;
     }
   }
   if (mode == 1) return;
@@ -1368,6 +1413,7 @@ __global__ void k_set_weights(InstDev* inst, int n_inst, const double* w) {
   inst[b].q = w[3 * b + 0];
   inst[b].r = w[3 * b + 1];
   inst[b].qf = w[3 * b + 2];
+  derive(inst[b]);
 }
 
 }  // namespace nmpc_dev
