@@ -34,7 +34,20 @@ WORKLOAD = ("heat2d_64x64_N50: 2D nonlinear heat eq. k(w)=0.1(1+0.5w), 64x64 gri
             "N=50, 8 actuators (2x4), Gaussian-bump reference, 16-mode sine initial field; "
             "plain double-layer Jacobi, cold start, tol ||K||_inf<=1e-6")
 TOL = 1e-6
-BYTES_PER_POINT_STAGE = 32  # algorithmic bytes per cell-stage per iteration
+# algorithmic bytes per cell-stage per iteration: read x_i, lambda_i and write
+# them back in float64 (the neighbour-stage reads are the same arrays)
+BYTES_PER_POINT_STAGE = 32
+# algorithmic float32 flops per cell-stage per iteration of the mixed path with
+# two P^-1 applications (n_u_it = 1): split residual ~30, two applications of
+# 2 x 2 sweeps x ~10 flops + 2, coefficients ~10
+FP32_FLOPS_PER_POINT_STAGE = 124
+# float32 FMA peak: 128 lanes x 2 flops x 152 SMs x 2.07 GHz (unit counts and
+# maximum SM clock of the part)
+FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.07e9 / 1e12
+# dram__bytes_read.sum + dram__bytes_write.sum of one iteration launch of this
+# workload from the committed ncu capture of the iteration kernel (cold
+# caches); None once the kernel changes after that capture
+TRAFFIC_BYTES_PER_LAUNCH = 3.48e6
 
 
 def parse():
@@ -208,6 +221,7 @@ def main():
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     iters, launches0 = [], G.nmpc_launch_count(solver.h)
+    it_launches0 = G.nmpc_launch_plan(solver.h)["iteration_launches"]
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         for k in range(args.steps):
@@ -219,6 +233,7 @@ def main():
             iters.append(st[0].iters)
         torch.cuda.synchronize()
     launches = G.nmpc_launch_count(solver.h) - launches0
+    it_launches = G.nmpc_launch_plan(solver.h)["iteration_launches"] - it_launches0
     t_ms = sum(a.elapsed_time(b_) for a, b_ in ev)
     if world > 1:
         tt = torch.tensor([t_ms], device=dev)
@@ -242,21 +257,30 @@ def main():
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         e2e_s = float(tt.item())
 
-    # roofline of the dominant kernel (the fused iteration kernel): average
-    # duration per iteration launch over the timed region (includes the graph
-    # gaps and host polls, so it is an upper bound on the kernel duration)
+    # roofline of the dominant kernel (the fused iteration kernel, one launch
+    # per iteration): the timed region divided by its launches (the region
+    # also holds the launch gaps, the host polls between chunks of launches
+    # and the small control kernels, so this over-estimates the kernel's
+    # duration)
     ins = insts[0]
     cells = ins.horizon * ins.mx * ins.my
-    iter_launches = sum(i + 1 for i in iters)
-    avg_launch_ms = t_ms / max(1, launches)
+    avg_launch_ms = t_ms / max(1, it_launches)
     peaks, which = measured_peaks()
     achieved = BYTES_PER_POINT_STAGE * cells / (avg_launch_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "frac": achieved / peaks["hbm_gbs"], "traffic": TRAFFIC_BYTES_PER_LAUNCH,
             "peak_source": which,
             "kernel": "k_iterate<float,SOLVE> (fused residual + lower layer + update)",
             "algorithmic_bytes_per_launch": BYTES_PER_POINT_STAGE * cells,
-            "avg_launch_ms": avg_launch_ms}
+            "avg_launch_ms": avg_launch_ms, "iteration_launches": it_launches,
+            "plan": {k: v for k, v in G.nmpc_launch_plan(solver.h).items()
+                     if k in ("threads", "cluster", "cells", "staged", "persistent")}}
+    # the same launches against the float32 ALU ceiling (the 64x64 stage slabs
+    # live in shared memory; the kernel is latency-bound)
+    ach_alu = FP32_FLOPS_PER_POINT_STAGE * cells / (avg_launch_ms / 1e3) / 1e12
+    roof_alu = {"bound": "alu", "achieved": ach_alu, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach_alu / FP32_PEAK_TFLOPS, "peak_source": "derived (unit counts x clock)",
+                "flops_per_cell_stage": FP32_FLOPS_PER_POINT_STAGE}
     cpu = None
     if rank == 0:
         os.environ.setdefault("OMP_NUM_THREADS", "1")
@@ -282,6 +306,7 @@ def main():
                        "d2h_bytes_per_step": 8 * ins.horizon * len(ins.act)},
                "gpu_launches": launches,
                "roofline": roof,
+               "roofline_alu": roof_alu,
                "cpu_baseline": cpu,
                "clocks": clk.summary()}
         print(json.dumps(out), flush=True)

@@ -114,6 +114,12 @@ typedef struct {
                       each thread carries its cells through every pass of a
                       work item as independent dependency chains; 0 = auto
                       (4)                                                     */
+  int persistent;  /* 1: when one cluster per stage fits on the device at
+                      once (staged slabs), one launch runs the whole solve
+                      with device-wide barriers between iterations (bounded
+                      waits; a wait that runs out restarts the solve with
+                      one launch per iteration); the iterates are identical
+                      to those of 0: one launch per iteration (default)     */
 } nmpc_opts;
 
 typedef struct {
@@ -127,7 +133,7 @@ typedef struct nmpc_handle nmpc_handle;
 
 /* Fill *o with defaults: tol 1e-6, max_iter 2000, n_lo 2, n_u_it 2, FP64,
    check_every 16, alpha 1, div_limit 1e8, threads auto, graph on, cluster
-   auto, split_min 1e-7, u_local 1, cells auto. */
+   auto, split_min 1e-7, u_local 0, cells auto, persistent 0. */
 void nmpc_default_opts(nmpc_opts* o);
 
 /* Validate the descriptors, build the device instance table and allocate the
@@ -209,6 +215,18 @@ int nmpc_sizes(const nmpc_handle* h, int64_t* out);
 /* Number of kernel launches issued by this handle since setup (all entry
    points), for launch accounting. */
 int64_t nmpc_launch_count(const nmpc_handle* h);
+
+/* The launch plan the handle chose (no counterpart in the paper; for tuning
+   and diagnostics): out[0] threads per CTA, out[1] CTAs per stage (cluster
+   size), out[2] cells per thread, out[3] 1 if the float64 inputs are staged
+   in shared memory, out[4] 1 if one persistent launch runs each solve,
+   out[5] dynamic shared memory bytes per CTA, out[6] CTAs per iteration
+   launch, out[7] 1 if the u-iteration uses local responses, out[8] clusters
+   of this shape the device keeps resident at once for the persistent
+   launch, out[9] work items (instance stages), out[10] launches of the
+   iteration kernel (one per iteration; one per solve when persistent) since
+   setup.  Returns NMPC_ERR_BAD_ARG for a null handle or array. */
+int nmpc_launch_plan(const nmpc_handle* h, int64_t* out);
 
 /* Allocation-free solve of ONE instance (no counterpart in the paper; it
    exists for callers that may not allocate device memory when they solve:

@@ -47,7 +47,7 @@ struct nmpc_handle {
   double* ub[3] = {nullptr, nullptr, nullptr};
   double* lb[3] = {nullptr, nullptr, nullptr};
   // control
-  int* ictl = nullptr;  // iter_k, (unused), n_active
+  int* ictl = nullptr;  // iter_k, (unused), n_active, (unused), grid barrier words [4]
   unsigned long long* res_inf = nullptr;
   unsigned long long* res_err = nullptr;
   double* res_sq = nullptr;
@@ -71,6 +71,8 @@ struct nmpc_handle {
   // launch configuration
   int threads = 0;
   int cpt = 4;
+  bool persistent = false;
+  int resident_clusters = 0;
   int grid = 0;
   int csize = 1;
   int slab_max = 0;
@@ -85,6 +87,7 @@ struct nmpc_handle {
   cudaGraphExec_t graph_exec = nullptr;
   int graph_chunk = 0;
   long long launches = 0;
+  long long iter_launches = 0;  // of the iteration kernel
   bool has_state = false;
 };
 
@@ -145,6 +148,7 @@ IterArgs make_args(nmpc_handle* h) {
   }
   A.iter_k = h->ictl + 0;
   A.n_active = h->ictl + 2;
+  A.gsync = reinterpret_cast<unsigned*>(h->ictl + 4);
   A.res_inf = h->res_inf;
   A.res_err = h->res_err;
   A.res_sq = h->res_sq;
@@ -180,6 +184,8 @@ IterArgs make_args(nmpc_handle* h) {
 struct LaunchPlan {
   int threads = 0, csize = 1, slab_max = 0, grid = 0;
   int cpt = 4;  // cells per thread (kernel variant)
+  bool persistent = false;  // one launch runs the whole solve (k_solve)
+  int resident_clusters = 0;  // clusters resident at once for k_solve
   size_t smem = 0;
   bool smem_mode = true;
   bool stage = true;  // float64 slab inputs staged in shared memory
@@ -234,6 +240,22 @@ IterKernel iter_kernel_of(bool mixed, int nc, bool smem) {
   return mixed ? iter_kernel<float>(nc, smem) : iter_kernel<double>(nc, smem);
 }
 
+using SolveKernel = void (*)(IterArgs);
+
+template <typename T>
+SolveKernel solve_kernel(int nc) {
+  switch (nc) {
+    case 1: return nmpc_dev::k_solve<T, 1>;
+    case 2: return nmpc_dev::k_solve<T, 2>;
+    case 4: return nmpc_dev::k_solve<T, 4>;
+    default: return nmpc_dev::k_solve<T, 8>;
+  }
+}
+
+SolveKernel solve_kernel_of(bool mixed, int nc) {
+  return mixed ? solve_kernel<float>(nc) : solve_kernel<double>(nc);
+}
+
 // Threads per CTA and cells per thread for a shared-memory slab of `slab`
 // interior cells: opts.cells (default 4) cells per thread, at least 128
 // threads, at most 512; the kernel variant's cells per thread is the power of
@@ -254,8 +276,9 @@ bool thread_shape(int slab, const nmpc_opts& o, int* threads, int* nc) {
 }
 
 // Clusters of C CTAs (`threads` threads, `smem` bytes) the device keeps
-// resident at once for the iteration kernel.
-int clusters_resident(int C, int threads, int nc, size_t smem, bool mixed) {
+// resident at once for the iteration kernel (or, with `solve`, the
+// persistent kernel).
+int clusters_resident(int C, int threads, int nc, size_t smem, bool mixed, bool solve = false) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(C * 256));
   cfg.blockDim = dim3((unsigned)threads);
@@ -268,8 +291,9 @@ int clusters_resident(int C, int threads, int nc, size_t smem, bool mixed) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int n = 0;
-  cudaError_t e = cudaOccupancyMaxActiveClusters(
-      &n, (const void*)iter_kernel_of(mixed, nc, true), &cfg);
+  const void* fn = solve ? (const void*)solve_kernel_of(mixed, nc)
+                         : (const void*)iter_kernel_of(mixed, nc, true);
+  cudaError_t e = cudaOccupancyMaxActiveClusters(&n, fn, &cfg);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -362,6 +386,10 @@ LaunchPlan plan_launch(const InstDev* insts, int n_inst, int n_work, const nmpc_
   }
   P.smem = P.smem_mode ? bytes(C) : small;
   P.grid = n_work * C;
+  // one cluster per work item for the whole solve, if all fit at once
+  P.resident_clusters =
+      P.smem_mode ? clusters_resident(C, P.threads, P.cpt, P.smem, mixed, true) : 0;
+  P.persistent = o.persistent && P.smem_mode && P.stage && P.resident_clusters >= n_work;
   return P;
 }
 
@@ -382,10 +410,40 @@ cudaError_t launch_k(const LaunchPlan& P, const IterArgs& A, cudaStream_t st, in
   return cudaLaunchKernelEx(&cfg, iter_kernel<T>(P.cpt, P.smem_mode), A, mode, j);
 }
 
+// The persistent solve launch: one cluster per work item, launched as a
+// cooperative launch where the runtime accepts one with clusters (co-resident
+// by construction), else as a plain cluster launch (the host has checked that
+// all clusters fit at once; the kernel's waits are bounded either way).
+template <typename T>
+cudaError_t launch_solve(const LaunchPlan& P, const IterArgs& A, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)P.grid);
+  cfg.blockDim = dim3((unsigned)P.threads);
+  cfg.dynamicSmemBytes = P.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)P.csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeCooperative;
+  attr[1].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, solve_kernel<T>(P.cpt), A);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, solve_kernel<T>(P.cpt), A);
+  }
+  return e;
+}
+
 LaunchPlan plan_of(const nmpc_handle* h) {
   LaunchPlan P;
   P.threads = h->threads;
   P.cpt = h->cpt;
+  P.persistent = h->persistent;
   P.csize = h->csize;
   P.stage = h->stage;
   P.local_u = h->local_u;
@@ -401,6 +459,7 @@ LaunchPlan plan_of(const nmpc_handle* h) {
 template <int MODE>
 cudaError_t launch_iterate(nmpc_handle* h, const IterArgs& A, cudaStream_t st, int j = 0) {
   h->launches++;
+  h->iter_launches++;
   const LaunchPlan P = plan_of(h);
   return h->mixed ? launch_k<float>(P, A, st, MODE, j) : launch_k<double>(P, A, st, MODE, j);
 }
@@ -423,6 +482,14 @@ cudaError_t configure_kernels(size_t smem) {
                        nmpc_dev::k_iterate<T, 4, true>, nmpc_dev::k_iterate<T, 8, true>,
                        nmpc_dev::k_iterate<T, GLOBAL_NC, false>};
   for (auto fn : fns) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  SolveKernel sfns[4] = {nmpc_dev::k_solve<T, 1>, nmpc_dev::k_solve<T, 2>, nmpc_dev::k_solve<T, 4>,
+                         nmpc_dev::k_solve<T, 8>};
+  for (auto fn : sfns) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -468,9 +535,10 @@ int run_chunk(nmpc_handle* h, const IterArgs& A, cudaStream_t st, int chunk) {
       CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
       cudaGraph_t g;
       CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-      const long long l0 = h->launches;
+      const long long l0 = h->launches, i0 = h->iter_launches;
       cudaError_t e = enqueue_chunk(h, A, cap, chunk);
       h->launches = l0;  // capture is not execution
+      h->iter_launches = i0;
       if (e != cudaSuccess) {
         cudaStreamEndCapture(cap, &g);
         cudaStreamDestroy(cap);
@@ -484,6 +552,7 @@ int run_chunk(nmpc_handle* h, const IterArgs& A, cudaStream_t st, int chunk) {
     }
     CK(cudaGraphLaunch(h->graph_exec, st));
     h->launches += chunk + 1;
+    h->iter_launches += chunk;
   } else {
     CK(enqueue_chunk(h, A, st, chunk));
   }
@@ -537,20 +606,46 @@ int solve_core(nmpc_handle* h, int horizon, const double* weights, int init, dou
     CK(cudaGetLastError());
   }
   IterArgs A = make_args(h);
-  if (init == NMPC_INIT_WARM || init == NMPC_INIT_GUESS) {
-    CK(cudaMemcpyAsync(h->xb[0], h->xb[2], h->n_s * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(h->lb[0], h->lb[2], h->n_s * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(h->ub[0], h->ub[2], h->n_u * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  }
-  const int mode = (init == NMPC_INIT_COLD) ? 0 : (init == NMPC_INIT_SHIFT ? 2 : 1);
-  nmpc_dev::k_init_control<<<per_instance_grid(h), 256, 0, st>>>(
-      A, mode, init == NMPC_INIT_WARM, h->xb[2], h->ub[2], h->lb[2]);
-  h->launches++;
-  CK(cudaGetLastError());
+  // S^0 and the control words (again after a persistent launch that could not
+  // finish: the state it left is discarded)
+  auto start = [&]() -> int {
+    if (init == NMPC_INIT_WARM || init == NMPC_INIT_GUESS) {
+      CK(cudaMemcpyAsync(h->xb[0], h->xb[2], h->n_s * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(h->lb[0], h->lb[2], h->n_s * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(h->ub[0], h->ub[2], h->n_u * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+    const int mode = (init == NMPC_INIT_COLD) ? 0 : (init == NMPC_INIT_SHIFT ? 2 : 1);
+    nmpc_dev::k_init_control<<<per_instance_grid(h), 256, 0, st>>>(
+        A, mode, init == NMPC_INIT_WARM, h->xb[2], h->ub[2], h->lb[2]);
+    h->launches++;
+    CK(cudaGetLastError());
+    return NMPC_OK;
+  };
+  int rc0 = start();
+  if (rc0 != NMPC_OK) return rc0;
 
+  bool done = false;
+  if (h->persistent) {
+    const LaunchPlan P = plan_of(h);
+    CK(h->mixed ? launch_solve<float>(P, A, st) : launch_solve<double>(P, A, st));
+    h->launches++;
+    h->iter_launches++;
+    CK(cudaMemcpyAsync(h->h_active, h->ictl, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h->h_active[7] == 0) {
+      done = true;
+    } else {
+      // a barrier wait ran out (the clusters were not all resident): from now
+      // on this handle iterates with one launch per iteration
+      fprintf(stderr, "nmpc: persistent launch not co-resident; using per-iteration launches\n");
+      h->persistent = false;
+      rc0 = start();
+      if (rc0 != NMPC_OK) return rc0;
+    }
+  }
   const int chunk = std::max(1, h->opts.check_every);
   long long launched = 0;
-  while (launched <= h->opts.max_iter) {
+  while (!done && launched <= h->opts.max_iter) {
     int rc = run_chunk(h, A, st, chunk);
     if (rc != NMPC_OK) return rc;
     launched += chunk;
@@ -604,8 +699,9 @@ void nmpc_default_opts(nmpc_opts* o) {
   o->use_graph = 1;
   o->cluster = 0;
   o->split_min = 1e-7;
-  o->u_local = 1;
+  o->u_local = 0;
   o->cells = 0;
+  o->persistent = 0;
 }
 
 int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
@@ -691,6 +787,8 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
   }
   h->threads = P.threads;
   h->cpt = P.cpt;
+  h->persistent = P.persistent;
+  h->resident_clusters = P.resident_clusters;
   h->csize = P.csize;
   h->slab_max = P.slab_max;
   h->smem = P.smem;
@@ -717,7 +815,7 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
     A(dev_alloc(&h->lb[q], h->n_s));
     A(dev_alloc(&h->ub[q], h->n_u));
   }
-  A(dev_alloc(&h->ictl, 4));
+  A(dev_alloc(&h->ictl, 8));
   A(dev_alloc(&h->res_inf, (size_t)nmpc_dev::RES_SLOTS * n_instances));
   A(dev_alloc(&h->res_err, (size_t)nmpc_dev::RES_SLOTS * n_instances));
   A(dev_alloc(&h->res_sq, (size_t)nmpc_dev::RES_SLOTS * n_instances));
@@ -733,7 +831,7 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
     h->scratch_stride = (long long)((work_bytes + 255) & ~size_t(255));
     A(cudaMalloc((void**)&h->scratch, (size_t)h->scratch_stride * h->grid));
   }
-  A(cudaMallocHost((void**)&h->h_active, sizeof(int)));
+  A(cudaMallocHost((void**)&h->h_active, 8 * sizeof(int)));
   A(cudaMallocHost((void**)&h->h_status, n_instances * sizeof(int)));
   A(cudaMallocHost((void**)&h->h_iters, n_instances * sizeof(int)));
   A(cudaMallocHost((void**)&h->h_fin, 2 * n_instances * sizeof(double)));
@@ -743,7 +841,7 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
     A(cudaMemcpy(h->inst_d, h->inst_h.data(), n_instances * sizeof(InstDev), cudaMemcpyHostToDevice));
     A(cudaMemcpy(h->work_d, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice));
     A(cudaMemcpy(h->act_d, act_all.data(), act_all.size() * sizeof(int), cudaMemcpyHostToDevice));
-    A(cudaMemset(h->ictl, 0, 4 * sizeof(int)));
+    A(cudaMemset(h->ictl, 0, 8 * sizeof(int)));
     A(cudaDeviceSynchronize());
   }
   if (!ok) {
@@ -936,6 +1034,22 @@ int nmpc_sizes(const nmpc_handle* h, int64_t* out) {
 
 int64_t nmpc_launch_count(const nmpc_handle* h) { return h ? h->launches : 0; }
 
+int nmpc_launch_plan(const nmpc_handle* h, int64_t* out) {
+  if (!h || !out) return NMPC_ERR_BAD_ARG;
+  out[0] = h->threads;
+  out[1] = h->csize;
+  out[2] = h->cpt;
+  out[3] = h->stage ? 1 : 0;
+  out[4] = h->persistent ? 1 : 0;
+  out[5] = (int64_t)h->smem;
+  out[6] = h->grid;
+  out[7] = h->local_u ? 1 : 0;
+  out[8] = h->resident_clusters;
+  out[9] = h->n_work;
+  out[10] = h->iter_launches;
+  return NMPC_OK;
+}
+
 void nmpc_destroy(nmpc_handle* h) {
   if (!h) return;
   cudaDeviceSynchronize();
@@ -1085,7 +1199,7 @@ extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
     o_l[q] = carve(&off, (size_t)n_s * sizeof(double));
     o_u[q] = carve(&off, (size_t)n_u * sizeof(double));
   }
-  const size_t o_ctl = carve(&off, 4 * sizeof(int));
+  const size_t o_ctl = carve(&off, 8 * sizeof(int));
   const size_t o_rinf = carve(&off, nmpc_dev::RES_SLOTS * sizeof(unsigned long long));
   const size_t o_rerr = carve(&off, nmpc_dev::RES_SLOTS * sizeof(unsigned long long));
   const size_t o_rsq = carve(&off, nmpc_dev::RES_SLOTS * sizeof(double));
@@ -1135,6 +1249,7 @@ extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
   int* ctl = reinterpret_cast<int*>(base + o_ctl);
   A.iter_k = ctl + 0;
   A.n_active = ctl + 2;
+  A.gsync = reinterpret_cast<unsigned*>(ctl + 4);
   A.res_inf = reinterpret_cast<unsigned long long*>(base + o_rinf);
   A.res_err = reinterpret_cast<unsigned long long*>(base + o_rerr);
   A.res_sq = reinterpret_cast<double*>(base + o_rsq);

@@ -99,6 +99,9 @@ struct IterArgs {
   int* full_from;  // [n_inst] first iteration evaluated with the float64 residual
   int* full0;      // [n_inst] 1: iteration 0 also uses it (warm starts)
   int* n_active;
+  // persistent launch: [0] barrier arrivals, [1] barrier generation, [2] stop
+  // (no instance running), [3] a wait ran out of time
+  unsigned* gsync;
   double tol, div_limit, alpha;
   double split_min;  // below max(tol, split_min) iterations use the float64 residual
   int max_iter, n_lo, n_u_it;
@@ -454,6 +457,7 @@ struct SmallShared {
   T v3n[MAX_NU];
   int act[MAX_NU];
   double lact[MAX_NU];  // lambda at the actuator cells
+  int bar_code;         // persistent launch: the grid barrier's stop / error bits
   int skip;
   int full;
 };
@@ -486,6 +490,69 @@ __device__ __forceinline__ void cp_async8(void* dst_smem, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
 }
 
+// Iteration k's decision for work item (b, s), taken by one thread from the
+// instance's residual history (iteration k - 1): skip (instance finished, or
+// k past max_iter) and whether the residual is evaluated in float64.  The CTA
+// of stage 0, cluster rank 0 records a finished instance (status, returned
+// iterate k - 1) and clears the residual slot of iteration k + 1.  Control
+// words are read around L1 (other CTAs write them within a persistent
+// launch).
+__device__ __noinline__ void control_decision(const IterArgs& A, int b, int s, int k, const Cl& cl,
+                                              int& skip_out, int& full_out) {
+  int skip = 0, fl = 1;
+  // every control word this decision reads, loaded at once
+  const int pslot = (k > 0) ? ((k - 1) % RES_SLOTS) * A.n_inst + b : 0;
+  const int status_b = __ldcg(A.status + b);
+  const int ffrom = __ldcg(A.full_from + b);
+  const int f0 = __ldcg(A.full0 + b);
+  const unsigned long long r_bits = __ldcg(A.res_inf + pslot);
+  const unsigned long long r0_bits = __ldcg(A.res_first + b);
+  const unsigned long long e_bits = __ldcg(A.res_err + pslot);
+  if (k > A.max_iter || status_b != ST_RUNNING) {
+    skip = 1;
+  } else {
+    int st = ST_RUNNING;
+    bool switch_now = false;
+    double r = 0.0;
+    if (k > 0) {
+      r = __longlong_as_double((long long)r_bits);
+      const double r0 = __longlong_as_double((long long)r0_bits);
+      const bool prev_full = (k - 1 >= ffrom) || (k == 1 && f0);
+      if (!(r <= 1.79e308) || r > A.div_limit * fmax(r0, 1e-300)) st = ST_DIVERGED;
+      else if (prev_full && r <= A.tol) st = ST_CONVERGED;
+      else if (!prev_full) {
+        // leave the split residual once it can no longer show that the
+        // float64 residual is above the threshold: r minus its rounding
+        // bound at or below max(tol, split_min)
+        const double e = __longlong_as_double((long long)e_bits);
+        if (r - e <= fmax(A.tol, A.split_min)) switch_now = true;
+      }
+    }
+    if (st != ST_RUNNING) {
+      skip = 1;
+      if (s == 0 && cl.rank == 0) {
+        A.status[b] = st;
+        A.iters[b] = k - 1;
+        A.final_buf[b] = (k - 1) & 1;
+        A.fin_inf[b] = r;
+        A.fin_2[b] = sqrt(__ldcg(A.res_sq + pslot));
+        atomicSub(A.n_active, 1);
+      }
+    } else {
+      fl = (A.full_all || k >= ffrom || switch_now || k == A.max_iter || (k == 0 && f0)) ? 1 : 0;
+      if (s == 0 && cl.rank == 0) {
+        if (fl && ffrom > k) A.full_from[b] = k;
+        const int nslot = ((k + 1) % RES_SLOTS) * A.n_inst + b;
+        A.res_inf[nslot] = 0ull;
+        A.res_err[nslot] = 0ull;
+        A.res_sq[nslot] = 0.0;
+      }
+    }
+  }
+  skip_out = skip;
+  full_out = fl;
+}
+
 // Residual norms of a work item (max, sum of squares) and, for the split
 // residual, its rounding bound, into iteration k's slot of instance b.
 __device__ __forceinline__ void publish_residual(const IterArgs& A, int slot, int b, int k,
@@ -500,10 +567,15 @@ __device__ __forceinline__ void publish_residual(const IterArgs& A, int slot, in
 // One (instance, stage) work item of an upper-layer iteration on this rank's
 // slab.  B: base of the slab region (shared memory when SMEM), work records at
 // byte offset wk_off, staged float64 records at st_off (when `staged`).
+// resident: the staged records, the zeroed ring, the actuator cells and the
+// controls u still hold this item's state from the previous iteration of a
+// persistent launch (only x_{i-1} and lambda_{i+1} are loaded).  keep: the
+// update also goes into the staged records (own cells and the neighbours'
+// halo copies) and into every rank's u, for the next resident iteration.
 template <typename T, int NC, bool SMEM>
 __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, bool full,
                              bool resid_only, SmallShared<T>& sm, char* B, int wk_off, int st_off,
-                             bool staged, const Cl& cl) {
+                             bool staged, const Cl& cl, bool resident = false, bool keep = false) {
   constexpr int TS = (int)sizeof(T);
   constexpr int RB = NUM_FIELDS * TS;  // bytes per work record
   constexpr int SB = NUM_SFIELDS * 8;  // bytes per staged record
@@ -538,11 +610,16 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
   // (mapa is given this CTA's record base, a valid local address; the
   // position shifts are applied to the mapped address, and every store lands
   // inside the neighbour's records)
-  unsigned up_base = 0u, dn_base = 0u;
+  unsigned up_base = 0u, dn_base = 0u, sup_base = 0u, sdn_base = 0u;
   if constexpr (SMEM) {
     const unsigned mine = smem_u32(B) + (unsigned)wk_off;
     if (g.up) up_base = map_rank(mine, cl.rank - 1) + (unsigned)(g.up_off * RB);
     if (g.dn) dn_base = map_rank(mine, cl.rank + 1) - (unsigned)(g.dn_off * RB);
+    if (keep) {
+      const unsigned smine = smem_u32(B) + (unsigned)st_off;
+      if (g.up) sup_base = map_rank(smine, cl.rank - 1) + (unsigned)(g.up_off * SB);
+      if (g.dn) sdn_base = map_rank(smine, cl.rank + 1) - (unsigned)(g.dn_off * SB);
+    }
   }
   // store v into field f of own position p and of the neighbours' halo copies
   // (slots past the slab store nothing)
@@ -565,10 +642,12 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
   // actuators: controls of this stage, and per thread a bit mask of which of
   // its cells carry one (cell q is bit q / blockDim of thread q % blockDim)
   for (int a = tid; a < nu; a += bd) {
-    const int c = A.act[I.act_off + a];
-    sm.act[a] = c;
-    sm.u[a] = Uin[I.u_off + (long long)s * nu + a];
-    sm.lact[a] = L[so + c];  // lambda at the actuator cell, for the stage-gradient row K2
+    if (!resident) {
+      sm.act[a] = A.act[I.act_off + a];
+      sm.u[a] = Uin[I.u_off + (long long)s * nu + a];
+    }
+    const int c = sm.act[a];
+    sm.lact[a] = __ldcg(L + so + c);  // lambda at the actuator cell, for the stage-gradient row K2
     sm.v3[a] = T(0);
     const int q = c - g.lo;
     if (q >= 0 && q < g.n && q / bd < 64) atomicOr(&sm.amask[q % bd], 1ull << (q / bd));
@@ -586,7 +665,25 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
     const int gc = g.r0 - 1 + pp;
     return (gc >= 0 && gc < I.mx) ? gc : -1;
   };
-  if (staged) {
+  if (resident) {
+    // x_{i-1} (x0 is resident) and lambda_{i+1} of the own cells, around L1
+    // (other CTAs wrote them in this launch)
+    double xp_[NC], ln_[NC];
+#pragma unroll
+    for (int kq = 0; kq < NC; ++kq) {
+      const bool v = (c0.valid >> kq) & 1u;
+      const int c = g.lo + tid + kq * bd;
+      xp_[kq] = (v && s > 0) ? __ldcg(X + so - ng + c) : 0.0;
+      ln_[kq] = (v && !last) ? __ldcg(L + so + ng + c) : 0.0;
+    }
+#pragma unroll
+    for (int kq = 0; kq < NC; ++kq) {
+      if ((c0.valid >> kq) & 1u) {
+        if (s > 0) SV(spos(c0.p[kq]), S_XP) = xp_[kq];
+        SV(spos(c0.p[kq]), S_LN) = ln_[kq];
+      }
+    }
+  } else if (staged) {
     // float64 inputs by asynchronous copies, all in flight at once; zero
     // outside the grid
     for (int pp = tid; pp < g.plen; pp += bd) {
@@ -610,7 +707,7 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
   // zero the work records that no rank writes in this item: the column pads
   // and the halo rows at the grid boundary (2D), the halo cells at the grid
   // boundary (1D)
-  if (g.n > 0) {
+  if (g.n > 0 && !resident) {
     auto zrec = [&](int p) {
 #pragma unroll
       for (int f = 0; f < NUM_FIELDS; ++f) WV(wpos(p), f) = T(0);
@@ -629,7 +726,7 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
       if (!g.dn) zrec(g.n + 1);
     }
   }
-  if (staged) asm volatile("cp.async.wait_all;\n" ::);
+  if (staged && !resident) asm volatile("cp.async.wait_all;\n" ::);
   __syncthreads();
   // own-cell float64 inputs of slot sl (staged record, or global memory for
   // slots that hold a cell; zero otherwise)
@@ -1131,15 +1228,33 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
         const int pb = wpos(sl.p);
         return D2{fma(alpha, to_double(WV(pb, f5)), OX(sl)), fma(alpha, to_double(WV(pb, f4)), OL(sl))};
       },
-      [&](const Slot& sl, const Cells<NC>&, D2 o) {
+      [&](const Slot& sl, const Cells<NC>& cs, D2 o) {
         if (sl.v) {
           Xo[sl.q] = o.x;
           Lo[sl.q] = o.l;
         }
+        if constexpr (SMEM) {
+          if (keep) {
+            // the next iteration's staged x, lambda: own record and the
+            // neighbours' halo copies
+            const int sb = spos(sl.p);
+            if (sl.v) {
+              SV(sb, S_X) = o.x;
+              SV(sb, S_L) = o.l;
+            }
+            const unsigned rel = (unsigned)(sl.p * SB);
+            push_if(sup_base + rel + S_X * 8, o.x, (cs.pu >> sl.k) & 1u);
+            push_if(sup_base + rel + S_L * 8, o.l, (cs.pu >> sl.k) & 1u);
+            push_if(sdn_base + rel + S_X * 8, o.x, (cs.pd >> sl.k) & 1u);
+            push_if(sdn_base + rel + S_L * 8, o.l, (cs.pd >> sl.k) & 1u);
+          }
+        }
       });
-  if (cl.rank == 0)
-    for (int a = tid; a < nu; a += bd)
-      Uo[I.u_off + (long long)s * nu + a] = sm.u[a] - alpha * (double)sm.v3[a];
+  for (int a = tid; a < nu; a += bd) {
+    const double un = sm.u[a] - alpha * (double)sm.v3[a];
+    if (cl.rank == 0) Uo[I.u_off + (long long)s * nu + a] = un;
+    if (keep) sm.u[a] = un;  // every rank computes the same value
+  }
   cl.sync();
 }
 
@@ -1182,61 +1297,7 @@ __global__ void __launch_bounds__(512) k_iterate(IterArgs A, int MODE, int j) {
       resid_only = (A.resid_only != 0);
       full = resid_only || (A.full_all != 0);
     } else {
-      if (threadIdx.x == 0) {
-        int skip = 0, fl = 1;
-        // every control word this decision reads, loaded at once
-        const int pslot = (k > 0) ? ((k - 1) % RES_SLOTS) * A.n_inst + b : 0;
-        const int status_b = A.status[b];
-        const int ffrom = A.full_from[b];
-        const int f0 = A.full0[b];
-        const unsigned long long r_bits = A.res_inf[pslot];
-        const unsigned long long r0_bits = A.res_first[b];
-        const unsigned long long e_bits = A.res_err[pslot];
-        if (k > A.max_iter || status_b != ST_RUNNING) {
-          skip = 1;
-        } else {
-          int st = ST_RUNNING;
-          bool switch_now = false;
-          double r = 0.0;
-          if (k > 0) {
-            r = __longlong_as_double((long long)r_bits);
-            const double r0 = __longlong_as_double((long long)r0_bits);
-            const bool prev_full = (k - 1 >= ffrom) || (k == 1 && f0);
-            if (!(r <= 1.79e308) || r > A.div_limit * fmax(r0, 1e-300)) st = ST_DIVERGED;
-            else if (prev_full && r <= A.tol) st = ST_CONVERGED;
-            else if (!prev_full) {
-              // leave the split residual once it can no longer show that the
-              // float64 residual is above the threshold: r minus its rounding
-              // bound at or below max(tol, split_min)
-              const double e = __longlong_as_double((long long)e_bits);
-              if (r - e <= fmax(A.tol, A.split_min)) switch_now = true;
-            }
-          }
-          if (st != ST_RUNNING) {
-            skip = 1;
-            if (s == 0 && cl.rank == 0) {
-              A.status[b] = st;
-              A.iters[b] = k - 1;
-              A.final_buf[b] = (k - 1) & 1;
-              A.fin_inf[b] = r;
-              A.fin_2[b] = sqrt(A.res_sq[pslot]);
-              atomicSub(A.n_active, 1);
-            }
-          } else {
-            fl = (A.full_all || k >= ffrom || switch_now || k == A.max_iter || (k == 0 && f0))
-                     ? 1 : 0;
-            if (s == 0 && cl.rank == 0) {
-              if (fl && ffrom > k) A.full_from[b] = k;
-              const int nslot = ((k + 1) % RES_SLOTS) * A.n_inst + b;
-              A.res_inf[nslot] = 0ull;
-              A.res_err[nslot] = 0ull;
-              A.res_sq[nslot] = 0.0;
-            }
-          }
-        }
-        sm.skip = skip;
-        sm.full = fl;
-      }
+      if (threadIdx.x == 0) control_decision(A, b, s, k, cl, sm.skip, sm.full);
       __syncthreads();
       const bool sk = sm.skip != 0;
       full = sm.full != 0;
@@ -1248,6 +1309,97 @@ __global__ void __launch_bounds__(512) k_iterate(IterArgs A, int MODE, int j) {
                               B, wk_off, st_off, staged, cl);
   }
 
+}
+
+// Spin budget of one grid-barrier wait (SM clock cycles, about two seconds).
+constexpr long long GRID_WAIT_CYCLES = 4000000000LL;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier of a persistent launch with n_clusters clusters: the
+// cluster's CTAs meet (after publishing their global writes), rank 0 arrives
+// on the counter, the last arrival decides whether to stop (no instance
+// running) and opens the next generation; the others wait for it, for at most
+// GRID_WAIT_CYCLES, and on timeout raise the error word.  Returns
+// stop | error << 1 to every thread of the cluster.
+template <typename T>
+__device__ int grid_barrier(const IterArgs& A, int n_clusters, unsigned& gen, const Cl& cl,
+                            SmallShared<T>& sm) {
+  __syncthreads();
+  if (threadIdx.x == 0) __threadfence();
+  cl.sync();
+  if (cl.rank == 0 && threadIdx.x == 0) {
+    unsigned* gs = A.gsync;
+    const unsigned target = gen + 1u;
+    if (atomicAdd(&gs[0], 1u) == (unsigned)n_clusters - 1u) {
+      gs[0] = 0u;
+      if (atomicOr(A.n_active, 0) == 0) gs[2] = 1u;
+      __threadfence();
+      atomicExch(&gs[1], target);
+    } else {
+      const long long t0 = clock64();
+      while (ld_acquire_u32(&gs[1]) != target) {
+        if (ld_acquire_u32(&gs[3]) != 0u) break;
+        if (clock64() - t0 > GRID_WAIT_CYCLES) {
+          atomicExch(&gs[3], 1u);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    const int code = (int)(ld_acquire_u32(&gs[2]) | (ld_acquire_u32(&gs[3]) << 1));
+    gen = target;
+    if (cl.C == 1) sm.bar_code = code;
+    else
+      for (int r = 0; r < cl.C; ++r) *cl.map(&sm.bar_code, r) = code;
+  }
+  cl.sync();
+  return sm.bar_code;
+}
+
+// Persistent solve: cluster w owns work item w for the whole launch (the
+// host launches one cluster per item and only when all are resident at once)
+// and runs iterations k = *iter_k .. max_iter, with a grid barrier between
+// iterations, until no instance is running.  The item's staged inputs stay
+// in shared memory between iterations (only x_{i-1} and lambda_{i+1} are
+// reloaded), so the launch needs staged slabs.  A barrier wait that runs out
+// ends the launch with gsync[3] set; the host then restarts the solve with
+// one launch per iteration.
+template <typename T, int NC>
+__global__ void __launch_bounds__(512) k_solve(IterArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SmallShared<T>& sm = *reinterpret_cast<SmallShared<T>*>(smem_raw);
+  char* B = reinterpret_cast<char*>(smem_raw);
+  const int st_off = (int)((sizeof(SmallShared<T>) + 15) & ~size_t(15));
+  const int wk_off = st_off + A.slab_max * NUM_SFIELDS * 8;
+  Cl cl;
+  cl.C = A.csize;
+  cl.rank = (A.csize > 1) ? (int)cg::this_cluster().block_rank() : 0;
+  sm.amask[threadIdx.x] = 0ull;
+  const int n_clusters = gridDim.x / A.csize;
+  const int2 item = A.work[blockIdx.x / A.csize];
+  const int b = item.x, s = item.y;
+  unsigned gen = 0u;
+  if (cl.rank == 0 && threadIdx.x == 0) gen = ld_acquire_u32(&A.gsync[1]);
+  bool resident = false;
+  for (int k = *(volatile int*)A.iter_k; k <= A.max_iter; ++k) {
+    if (threadIdx.x == 0) control_decision(A, b, s, k, cl, sm.skip, sm.full);
+    __syncthreads();
+    const bool sk = sm.skip != 0;
+    const bool full = sm.full != 0;
+    __syncthreads();
+    if (!sk) {
+      process_item<T, NC, true>(A, b, s, k, k & 1, full, k == A.max_iter, sm, B, wk_off, st_off,
+                                true, cl, resident, true);
+      resident = true;
+    }
+    if (grid_barrier(A, n_clusters, gen, cl, sm) != 0) break;
+  }
 }
 
 // After a chunk of n iteration launches: the next chunk starts at iteration
@@ -1283,6 +1435,9 @@ __global__ void k_init_control(IterArgs A, int mode, int first_full, const doubl
     if (b == 0) {
       *A.n_active = A.n_inst;
       *A.iter_k = 0;
+      A.gsync[0] = 0u;  // the barrier generation (gsync[1]) carries on
+      A.gsync[2] = 0u;
+      A.gsync[3] = 0u;
     }
   }
   if (mode == 1) return;

@@ -50,7 +50,7 @@ class nmpc_opts(ctypes.Structure):
                 ("div_limit", ctypes.c_double), ("threads", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("cluster", ctypes.c_int),
                 ("split_min", ctypes.c_double), ("u_local", ctypes.c_int),
-                ("cells", ctypes.c_int)]
+                ("cells", ctypes.c_int), ("persistent", ctypes.c_int)]
 
 
 class nmpc_stats(ctypes.Structure):
@@ -60,7 +60,7 @@ class nmpc_stats(ctypes.Structure):
 
 EXPORTED = ["nmpc_default_opts", "nmpc_setup", "nmpc_solve", "nmpc_solve_host",
             "nmpc_residual", "nmpc_iterate", "nmpc_get_state", "nmpc_set_state",
-            "nmpc_sizes", "nmpc_launch_count", "nmpc_destroy", "nmpc_strerror",
+            "nmpc_sizes", "nmpc_launch_count", "nmpc_launch_plan", "nmpc_destroy", "nmpc_strerror",
             "nmpc_solve_noalloc", "nmpc_plant_step", "nmpc_closed_loop"]
 
 
@@ -82,6 +82,7 @@ def _load() -> ctypes.CDLL:
         "nmpc_get_state": (I, [P, P, P, P, P]),
         "nmpc_set_state": (I, [P, P, P, P, P]),
         "nmpc_sizes": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
+        "nmpc_launch_plan": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
         "nmpc_launch_count": (ctypes.c_int64, [P]),
         "nmpc_destroy": (V, [P]),
         "nmpc_strerror": (ctypes.c_char_p, [I]),
@@ -159,6 +160,16 @@ def nmpc_setup(instances: Sequence, **opts) -> ctypes.c_void_p:
     _check(LIB.nmpc_setup(descs, len(instances), ctypes.byref(o), ctypes.byref(h)), "nmpc_setup")
     del keep
     return h
+
+
+def nmpc_launch_plan(h) -> dict:
+    """The launch plan of a handle (threads, cluster, cells, staged, persistent,
+    smem, grid, local_u, resident_clusters, work_items, iteration_launches)."""
+    out = (ctypes.c_int64 * 11)()
+    _check(LIB.nmpc_launch_plan(h, out), "nmpc_launch_plan")
+    keys = ("threads", "cluster", "cells", "staged", "persistent", "smem", "grid", "local_u",
+            "resident_clusters", "work_items", "iteration_launches")
+    return {k: int(v) for k, v in zip(keys, out)}
 
 
 def nmpc_sizes(h) -> tuple:

@@ -361,3 +361,34 @@ def test_mixed_reaches_tight_tolerance_above_the_split_floor(G):
         p = O.Problem(inst)
         (X, U, L), info = O.solve_jacobi(p, tol=1e-10, max_iter=50000)
         assert np.abs(ug[b] - U).max() <= 1e-4 * np.abs(U).max()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("case", ["c2", "ragged3", "heat1d_split"])
+def test_persistent_solve_is_bit_identical_to_per_iteration_launches(G, precision, case):
+    """One launch for the whole solve (grid barriers between iterations, the
+    stage state resident in shared memory) performs exactly the arithmetic of
+    one launch per iteration: same iteration counts, same iterates."""
+    import torch
+    if case == "c2":
+        insts, kw = [wl.heat2d_single()], dict(cluster=8)
+    elif case == "ragged3":
+        insts, kw = wl.heat1d_ragged_batch(3), {}
+    else:
+        insts, kw = [wl.heat1d(40, 9, 3, 0.02, seed=11)], dict(cluster=3)
+    out = []
+    for persistent in (1, 0):
+        s = G.Solver(insts, tol=1e-6, precision=precision, max_iter=4000, persistent=persistent,
+                     **kw)
+        rc, st = s.solve()
+        x, u, lam = s.state()
+        torch.cuda.synchronize()
+        out.append(([st[i].iters for i in range(len(insts))], [st[i].res_inf for i in range(len(insts))],
+                    x.cpu().numpy(), u.cpu().numpy(), lam.cpu().numpy(), rc))
+        s.close()
+    a, b = out
+    assert a[5] == b[5] == G.NMPC_OK
+    assert a[0] == b[0]
+    assert a[1] == b[1]
+    for i in (2, 3, 4):
+        assert np.array_equal(a[i], b[i])
