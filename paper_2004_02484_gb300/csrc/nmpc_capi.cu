@@ -86,6 +86,9 @@ struct nmpc_handle {
   // graph of one chunk of iterations
   cudaGraphExec_t graph_exec = nullptr;
   int graph_chunk = 0;
+  // the whole iteration loop as one graph: a WHILE node over chunks
+  cudaGraphExec_t loop_exec = nullptr;
+  int loop_chunk = 0;
   long long launches = 0;
   long long iter_launches = 0;  // of the iteration kernel
   bool has_state = false;
@@ -117,6 +120,7 @@ cudaError_t dev_alloc(P** p, size_t count) {
 void free_all(nmpc_handle* h) {
   if (!h) return;
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->loop_exec) cudaGraphExecDestroy(h->loop_exec);
   void* ptrs[] = {h->inst_d, h->work_d, h->act_d, h->x0_d, h->ref_d, h->uo_d, h->w_d,
                   h->xb[0], h->xb[1], h->xb[2], h->ub[0], h->ub[1], h->ub[2],
                   h->lb[0], h->lb[1], h->lb[2], h->ictl, h->res_inf, h->res_err, h->res_sq,
@@ -400,13 +404,18 @@ cudaError_t launch_k(const LaunchPlan& P, const IterArgs& A, cudaStream_t st, in
   cfg.blockDim = dim3((unsigned)P.threads);
   cfg.dynamicSmemBytes = P.smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = (unsigned)P.csize;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  // consecutive iteration launches overlap their start with the previous
+  // launch's end (programmatic dependent launch; the kernel waits for the
+  // previous iteration before it reads any state)
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = (mode == nmpc_dev::MODE_SOLVE) ? 2 : 1;
   return cudaLaunchKernelEx(&cfg, iter_kernel<T>(P.cpt, P.smem_mode), A, mode, j);
 }
 
@@ -559,6 +568,65 @@ int run_chunk(nmpc_handle* h, const IterArgs& A, cudaStream_t st, int chunk) {
   return NMPC_OK;
 }
 
+// The iteration loop of a solve as one graph: a condition kernel, then a
+// WHILE node whose body is one chunk of iteration launches, the counter
+// advance and the condition kernel again (no host round trip between chunks).
+int build_loop_graph(nmpc_handle* h, const IterArgs& A, int chunk) {
+  if (h->loop_exec && h->loop_chunk == chunk) return NMPC_OK;
+  if (h->loop_exec) {
+    cudaGraphExecDestroy(h->loop_exec);
+    h->loop_exec = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  cudaStream_t cap = nullptr;
+  int rc = NMPC_ERR_CUDA;
+  const long long l0 = h->launches, i0 = h->iter_launches;
+  do {
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) break;
+    cudaGraphConditionalHandle cond;
+    if (cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault) != cudaSuccess)
+      break;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) break;
+    // the first decision (an already finished solve runs no chunk)
+    if (cudaStreamBeginCaptureToGraph(cap, g, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      break;
+    nmpc_dev::k_loop_cond<<<1, 32, 0, cap>>>(cond, A.n_active, A.iter_k, h->opts.max_iter);
+    cudaGraph_t gc = nullptr;
+    if (cudaStreamEndCapture(cap, &gc) != cudaSuccess) break;
+    cudaGraphNode_t first;
+    size_t nfirst = 1;
+    if (cudaGraphGetNodes(g, &first, &nfirst) != cudaSuccess || nfirst != 1) break;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t loop;
+    if (cudaGraphAddNode(&loop, g, &first, nullptr, 1, &cp) != cudaSuccess) break;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      break;
+    cudaError_t e = enqueue_chunk(h, A, cap, chunk);
+    nmpc_dev::k_loop_cond<<<1, 32, 0, cap>>>(cond, A.n_active, A.iter_k, h->opts.max_iter);
+    cudaGraph_t gb = nullptr;
+    if (cudaStreamEndCapture(cap, &gb) != cudaSuccess || e != cudaSuccess) break;
+    if (cudaGraphInstantiate(&h->loop_exec, g, 0) != cudaSuccess) break;
+    h->loop_chunk = chunk;
+    rc = NMPC_OK;
+  } while (false);
+  h->launches = l0;  // capture is not execution
+  h->iter_launches = i0;
+  if (g) cudaGraphDestroy(g);
+  if (cap) cudaStreamDestroy(cap);
+  if (rc != NMPC_OK) {
+    cudaGetLastError();
+    fprintf(stderr, "nmpc: could not build the solve-loop graph\n");
+  }
+  return rc;
+}
+
 FinalArgs make_final(nmpc_handle* h, double* u_out) {
   FinalArgs F{};
   F.inst = h->inst_d;
@@ -644,6 +712,15 @@ int solve_core(nmpc_handle* h, int horizon, const double* weights, int init, dou
     }
   }
   const int chunk = std::max(1, h->opts.check_every);
+  bool loop_graph = false;
+  if (!done && h->opts.use_graph) {
+    // the whole loop on the device: one graph launch, no host polls
+    int rc = build_loop_graph(h, A, chunk);
+    if (rc != NMPC_OK) return rc;
+    CK(cudaGraphLaunch(h->loop_exec, st));
+    loop_graph = true;
+    done = true;
+  }
   long long launched = 0;
   while (!done && launched <= h->opts.max_iter) {
     int rc = run_chunk(h, A, st, chunk);
@@ -664,7 +741,15 @@ int solve_core(nmpc_handle* h, int horizon, const double* weights, int init, dou
   CK(cudaMemcpyAsync(h->h_iters, h->iters, n * sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(h->h_fin, h->fin_inf, n * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(h->h_fin + n, h->fin_2, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (loop_graph)
+    CK(cudaMemcpyAsync(h->h_active, h->ictl, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  if (loop_graph) {
+    // launch accounting: the loop ran iter_k / chunk chunks
+    const long long runs = (h->h_active[0] + chunk - 1) / chunk;
+    h->launches += 1 + runs * (chunk + 2);
+    h->iter_launches += runs * chunk;
+  }
   int rc = NMPC_OK;
   for (int b = 0; b < n; ++b) {
     if (stats) {

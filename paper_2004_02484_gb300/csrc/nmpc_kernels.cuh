@@ -300,6 +300,12 @@ __device__ __forceinline__ void push_if(unsigned addr, double v, unsigned flag) 
                :: "r"(addr), "d"(v), "r"(flag) : "memory");
 }
 
+// Programmatic dependent launch: let the next launch in the stream start its
+// CTAs now, and wait until the previous launch has finished and its writes
+// are visible (both no-ops for launches without the attribute).
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Rank owning grid cell c and its padded position there.
 __device__ __forceinline__ int owner_of(int c, const Geo& g, int mx, int& p) {
   if (g.d2) {
@@ -1285,8 +1291,14 @@ __global__ void __launch_bounds__(512) k_iterate(IterArgs A, int MODE, int j) {
   cl.rank = (A.csize > 1) ? (int)cg::this_cluster().block_rank() : 0;
   sm.amask[threadIdx.x] = 0ull;
   if (MODE == MODE_ONESHOT) __syncthreads();  // solve mode: the prologue's barrier
+  // the next iteration's CTAs may start as soon as every CTA of this one has
+  // (they hold their state loads behind pdl_wait until this launch is done)
+  pdl_trigger();
+  // *iter_k only changes between chunks of launches (k_advance), never while
+  // an iteration launch of the chunk is in flight
   const int k = (MODE == MODE_SOLVE) ? *(volatile int*)A.iter_k + j : 0;
   const int n_clusters = gridDim.x / A.csize;
+  pdl_wait();  // the previous iteration's state, residuals and control words
 
   for (int w = blockIdx.x / A.csize; w < A.n_work; w += n_clusters) {
     const int2 item = A.work[w];
@@ -1399,6 +1411,19 @@ __global__ void __launch_bounds__(512) k_solve(IterArgs A) {
       resident = true;
     }
     if (grid_barrier(A, n_clusters, gen, cl, sm) != 0) break;
+  }
+}
+
+// Condition of the solve loop's graph WHILE node: run another chunk of
+// iteration launches while some instance is running and the next iteration
+// is at most max_iter (the counter grows by the chunk length per pass, so the
+// loop always ends).
+__global__ void k_loop_cond(cudaGraphConditionalHandle c, const int* n_active, const int* iter_k,
+                            int max_iter) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const int act = *(volatile const int*)n_active;
+    const int k = *(volatile const int*)iter_k;
+    cudaGraphSetConditional(c, (act > 0 && k <= max_iter) ? 1u : 0u);
   }
 }
 
