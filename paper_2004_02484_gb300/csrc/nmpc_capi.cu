@@ -768,6 +768,172 @@ int solve_core(nmpc_handle* h, int horizon, const double* weights, int init, dou
 
 }  // namespace
 
+namespace {
+
+// Capture what fn enqueues on `cap` into graph g after the nodes deps[0..nd);
+// *last receives the capture's terminal node (the captured work is a chain).
+template <typename F>
+cudaError_t capture_after(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd, cudaStream_t cap,
+                          F fn, cudaGraphNode_t* last) {
+  cudaError_t e = cudaStreamBeginCaptureToGraph(cap, g, deps, nullptr, nd,
+                                                cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t ef = fn();
+  cudaStreamCaptureStatus status;
+  const cudaGraphNode_t* term = nullptr;
+  size_t nterm = 0;
+  cudaError_t ei = cudaStreamGetCaptureInfo(cap, &status, nullptr, nullptr, &term, nullptr, &nterm);
+  if (ei == cudaSuccess && nterm == 1) *last = term[0];
+  else if (ei == cudaSuccess) ei = cudaErrorInvalidValue;
+  cudaGraph_t gg = nullptr;
+  e = cudaStreamEndCapture(cap, &gg);
+  if (ef != cudaSuccess) return ef;
+  if (ei != cudaSuccess) return ei;
+  return e;
+}
+
+// Add a WHILE node to g after `dep`; returns the node and its body graph.
+cudaError_t add_while(cudaGraph_t g, cudaGraphNode_t dep, cudaGraphConditionalHandle c,
+                      cudaGraphNode_t* node, cudaGraph_t* body) {
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = c;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaError_t e = cudaGraphAddNode(node, g, &dep, nullptr, 1, &cp);
+  if (e == cudaSuccess) *body = cp.conditional.phGraph_out[0];
+  return e;
+}
+
+// The closed loop as one graph: a WHILE node over the steps whose body copies
+// the plant state into x0, starts the solve (cold or from the handle's state
+// at step 0, shifted afterwards), runs the solve loop (a nested WHILE node
+// over chunks of iteration launches), settles the instances, records the
+// step's status / iterations / residual, and moves the plant.
+int closed_loop_graph(nmpc_handle* h, double* w, int steps, int n_sub, double* u_hist,
+                      int* iters_hist, double* res_hist, cudaStream_t st) {
+  const int n = h->n_inst;
+  const int chunk = std::max(1, h->opts.check_every);
+  IterArgs A = make_args(h);
+  FinalArgs F = make_final(h, nullptr);
+  int* step = h->ictl + 1;
+  const int first_mode = h->has_state ? 2 : 0;
+  int* st_hist = nullptr;
+  int* it_hist = nullptr;
+  double* rs_hist = nullptr;
+  CK(dev_alloc(&st_hist, (size_t)steps * n));
+  CK(dev_alloc(&it_hist, (size_t)steps * n));
+  CK(dev_alloc(&rs_hist, (size_t)steps * n));
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  cudaStream_t cap = nullptr;
+  const long long l0 = h->launches, i0 = h->iter_launches;
+  int rc = NMPC_ERR_CUDA;
+  do {
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) break;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) break;
+    cudaGraphConditionalHandle outer, inner;
+    if (cudaGraphConditionalHandleCreate(&outer, g, 0, cudaGraphCondAssignDefault) != cudaSuccess)
+      break;
+    cudaGraphNode_t n0, nloop, n1, ninner, n2;
+    cudaGraph_t body_o = nullptr, body_i = nullptr;
+    if (capture_after(g, nullptr, 0, cap, [&]() {
+          nmpc_dev::k_cl_start<<<1, 32, 0, cap>>>(step, steps, outer);
+          return cudaGetLastError();
+        }, &n0) != cudaSuccess)
+      break;
+    if (add_while(g, n0, outer, &nloop, &body_o) != cudaSuccess) break;
+    if (cudaGraphConditionalHandleCreate(&inner, body_o, 0, cudaGraphCondAssignDefault) !=
+        cudaSuccess)
+      break;
+    // step: x0 <- w, start, first loop decision
+    if (capture_after(body_o, nullptr, 0, cap, [&]() {
+          nmpc_dev::k_copy_f64<<<256, 256, 0, cap>>>(h->x0_d, w, h->n_g);
+          nmpc_dev::k_init_control<<<per_instance_grid(h), 256, 0, cap>>>(
+              A, first_mode, 0, h->xb[2], h->ub[2], h->lb[2], step);
+          nmpc_dev::k_loop_cond<<<1, 32, 0, cap>>>(inner, A.n_active, A.iter_k, h->opts.max_iter);
+          return cudaGetLastError();
+        }, &n1) != cudaSuccess)
+      break;
+    if (add_while(body_o, n1, inner, &ninner, &body_i) != cudaSuccess) break;
+    if (capture_after(body_i, nullptr, 0, cap, [&]() {
+          cudaError_t e = enqueue_chunk(h, A, cap, chunk);
+          nmpc_dev::k_loop_cond<<<1, 32, 0, cap>>>(inner, A.n_active, A.iter_k, h->opts.max_iter);
+          return e != cudaSuccess ? e : cudaGetLastError();
+        }, &n2) != cudaSuccess)
+      break;
+    // step: settle, record, plant, next
+    if (capture_after(body_o, &ninner, 1, cap, [&]() {
+          nmpc_dev::k_finalize_status<<<(n + 127) / 128, 128, 0, cap>>>(F);
+          nmpc_dev::k_gather_final<<<per_instance_grid(h), 256, 0, cap>>>(F);
+          nmpc_dev::k_cl_record<<<(n + 127) / 128, 128, 0, cap>>>(step, n, h->status, h->iters,
+                                                                  h->fin_inf, st_hist, it_hist,
+                                                                  rs_hist);
+          for (int k = 0; k < n_sub; ++k) {
+            const bool even = (k % 2) == 0;
+            nmpc_dev::k_plant_substep<<<dim3(32, n), 256, 0, cap>>>(
+                h->inst_d, n, h->act_d, even ? w : h->x0_d, even ? h->x0_d : w, h->ub[2],
+                (k == 0) ? u_hist : nullptr, 0.0, n_sub, step, (long long)h->nu_tot);
+          }
+          if (n_sub % 2 == 1) nmpc_dev::k_copy_f64<<<256, 256, 0, cap>>>(w, h->x0_d, h->n_g);
+          nmpc_dev::k_cl_next<<<1, 32, 0, cap>>>(step, steps, outer);
+          return cudaGetLastError();
+        }, &n2) != cudaSuccess)
+      break;
+    if (cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) break;
+    rc = NMPC_OK;
+  } while (false);
+  h->launches = l0;  // capture is not execution
+  h->iter_launches = i0;
+  if (rc == NMPC_OK && cudaGraphLaunch(ge, st) != cudaSuccess) rc = NMPC_ERR_CUDA;
+  std::vector<int> sth((size_t)steps * n), ith((size_t)steps * n);
+  std::vector<double> rsh((size_t)steps * n);
+  if (rc == NMPC_OK) {
+    if (cudaMemcpyAsync(sth.data(), st_hist, sth.size() * sizeof(int), cudaMemcpyDeviceToHost,
+                        st) != cudaSuccess ||
+        cudaMemcpyAsync(ith.data(), it_hist, ith.size() * sizeof(int), cudaMemcpyDeviceToHost,
+                        st) != cudaSuccess ||
+        cudaMemcpyAsync(rsh.data(), rs_hist, rsh.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                        st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      rc = NMPC_ERR_CUDA;
+  }
+  if (ge) cudaGraphExecDestroy(ge);
+  if (g) cudaGraphDestroy(g);
+  if (cap) cudaStreamDestroy(cap);
+  cudaFree(st_hist);
+  cudaFree(it_hist);
+  cudaFree(rs_hist);
+  if (rc != NMPC_OK) {
+    cudaGetLastError();
+    fprintf(stderr, "nmpc: closed-loop graph failed\n");
+    return rc;
+  }
+  h->has_state = true;
+  int rc_all = NMPC_OK;
+  for (int t = 0; t < steps; ++t) {
+    for (int b = 0; b < n; ++b) {
+      const size_t o = (size_t)t * n + b;
+      if (iters_hist) iters_hist[o] = ith[o];
+      if (res_hist) res_hist[o] = rsh[o];
+      if (rc_all == NMPC_OK) {
+        if (sth[o] == nmpc_dev::ST_DIVERGED) rc_all = NMPC_ERR_DIVERGED;
+        else if (sth[o] != nmpc_dev::ST_CONVERGED) rc_all = NMPC_ERR_NOT_CONVERGED;
+      }
+    }
+    // launch accounting from the iterations each step ran
+    int kmax = 0;
+    for (int b = 0; b < n; ++b) kmax = std::max(kmax, ith[(size_t)t * n + b] + 2);
+    const long long runs = (kmax + chunk - 1) / chunk;
+    h->launches += 8 + n_sub + runs * (chunk + 2);
+    h->iter_launches += runs * chunk;
+  }
+  h->launches += 1;
+  return rc_all;
+}
+
+}  // namespace
+
 extern "C" {
 
 void nmpc_default_opts(nmpc_opts* o) {
@@ -1066,6 +1232,10 @@ int nmpc_closed_loop(nmpc_handle* h, double* w, const double* ref, int steps, in
                      double* u_hist, int* iters_hist, double* res_hist, void* stream) {
   if (!h || !w || !ref || steps < 1 || n_sub < 1) return NMPC_ERR_BAD_ARG;
   cudaStream_t st = (cudaStream_t)stream;
+  if (h->opts.use_graph && !h->persistent) {
+    CK(cudaMemcpyAsync(h->ref_d, ref, h->n_g * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    return closed_loop_graph(h, w, steps, n_sub, u_hist, iters_hist, res_hist, st);
+  }
   const int n = h->n_inst;
   std::vector<nmpc_stats> stats(n);
   int rc_all = NMPC_OK;

@@ -1438,10 +1438,13 @@ __global__ void k_advance(int* iter_k, int n) {
 // shifted by one stage with the last stage repeated (mode 2; receding
 // horizon, the paper's closed loop).  first_full: iteration 0 evaluates the
 // float64 residual (warm starts that may already be converged).
+// step: null, or the closed loop's device step counter (after the first step
+// the start is always the shift, mode 2).
 __global__ void k_init_control(IterArgs A, int mode, int first_full, const double* xc,
-                               const double* uc, const double* lc) {
+                               const double* uc, const double* lc, const int* step = nullptr) {
   const int b = blockIdx.y;
   if (b >= A.n_inst) return;
+  if (step && *step != 0) mode = 2;
   const InstDev I = A.inst[b];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     for (int q = 0; q < RES_SLOTS; ++q) {
@@ -1501,11 +1504,15 @@ __global__ void k_init_control(IterArgs A, int mode, int first_full, const doubl
 //   w_out = w_in + (dt / n_sub) (Lap Phi(w_in) + b0 B u_1),
 // u_1 the first-stage controls of the current solution (u_cur).  Optionally
 // records u_1 into u_rec (packed [sum n_u]).
+// rec_step: null, or a device step counter t; u_rec then points at row t of
+// a [steps][sum n_u] history (rec_stride = sum n_u).
 __global__ void k_plant_substep(const InstDev* inst, int n_inst, const int* act,
                                 const double* w_in, double* w_out, const double* u_cur,
-                                double* u_rec, double dt_all, int n_sub) {
+                                double* u_rec, double dt_all, int n_sub,
+                                const int* rec_step = nullptr, long long rec_stride = 0) {
   const int b = blockIdx.y;
   if (b >= n_inst) return;
+  if (u_rec && rec_step) u_rec += (long long)*rec_step * rec_stride;
   const InstDev I = inst[b];
   // each instance's sampling period is its own stage length unless dt_all > 0
   const double dt = ((dt_all > 0.0) ? dt_all : I.h) / n_sub;
@@ -1584,6 +1591,40 @@ __global__ void k_gather_final(FinalArgs F) {
     F.uc[I.u_off + e] = v;
     if (F.u_out) F.u_out[I.u_off + e] = v;
   }
+}
+
+// Closed loop on the device (one graph): the step loop's WHILE condition,
+// the per-step record of each instance's status, iterations and residual,
+// and a plain copy (graph loop bodies hold kernels only).
+__global__ void k_cl_start(int* step, int steps, cudaGraphConditionalHandle outer) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    *step = 0;
+    cudaGraphSetConditional(outer, steps > 0 ? 1u : 0u);
+  }
+}
+
+__global__ void k_cl_next(int* step, int steps, cudaGraphConditionalHandle outer) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const int t = *step + 1;
+    *step = t;
+    cudaGraphSetConditional(outer, t < steps ? 1u : 0u);
+  }
+}
+
+__global__ void k_cl_record(const int* step, int n_inst, const int* status, const int* iters,
+                            const double* fin_inf, int* st_hist, int* it_hist, double* res_hist) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_inst) return;
+  const long long o = (long long)*step * n_inst + b;
+  st_hist[o] = status[b];
+  it_hist[o] = iters[b];
+  res_hist[o] = fin_inf[b];
+}
+
+__global__ void k_copy_f64(double* dst, const double* src, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    dst[e] = src[e];
 }
 
 // weights override: (q, r, qf) per instance from a device array

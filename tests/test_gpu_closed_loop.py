@@ -82,3 +82,29 @@ def test_plant_step_matches_oracle_at_full_size(G):
         o_w += ng
         o_u += N * nu
     s.close()
+
+
+@pytest.mark.parametrize("n_sub", [1, 2])
+def test_graph_closed_loop_equals_host_driven_loop(G, n_sub):
+    """The closed loop captured as one graph (nested WHILE nodes over steps and
+    over chunks of iterations) performs the same operations as the loop driven
+    from the host: identical controls, plant state, iterations and residuals."""
+    import torch
+    insts = [wl.heat2d(20, 18, 8, 2, 2, seed=61), wl.heat1d(40, 10, 3, 0.02, seed=62)]
+    steps = 4
+    out = []
+    for use_graph in (1, 0):
+        s = G.Solver(insts, tol=1e-8, precision=1, max_iter=5000, use_graph=use_graph)
+        w = _t(G.pack_fields(insts, "x0"))
+        nu_tot = sum(len(i.act) for i in insts)
+        u_hist = torch.zeros(steps * nu_tot, dtype=torch.float64, device="cuda")
+        rc, iters, res = G.nmpc_closed_loop(s.h, w, s.ref, steps, n_sub, len(insts), u_hist)
+        torch.cuda.synchronize()
+        out.append((rc, iters.copy(), res.copy(), u_hist.cpu().numpy(), w.cpu().numpy()))
+        s.close()
+    a, b = out
+    assert a[0] == b[0] == G.NMPC_OK
+    assert np.array_equal(a[1], b[1])
+    assert np.array_equal(a[2], b[2])
+    assert np.array_equal(a[3], b[3])
+    assert np.array_equal(a[4], b[4])
