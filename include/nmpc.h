@@ -200,6 +200,31 @@ int nmpc_plant_step(nmpc_handle* h, double* w, double dt, int n_sub, double* u_r
 int nmpc_closed_loop(nmpc_handle* h, double* w, const double* ref, int steps, int n_sub,
                      double* u_hist, int* iters_hist, double* res_hist, void* stream);
 
+/* A start iterate S^0 written to packed device arrays x, lam [sum N*ng] and
+   u [sum N*n_u] (caller-owned, not aliasing the handle's buffers), so that a
+   caller can compare or modify candidate starts (for instance by their
+   nmpc_residual) before nmpc_set_state + NMPC_INIT_GUESS:
+   init = NMPC_INIT_COLD: x_i = x0 (device [sum ng]), u = 0, lambda = 0;
+   init = NMPC_INIT_SHIFT: the receding-horizon shift of the handle's current
+   state (Sec. 5.3's closed loop; stage i takes stage i + 1, the last stage
+   is repeated; x0 is ignored).  NMPC_ERR_BAD_ARG for another init, a NULL
+   array, a NULL x0 with COLD, or SHIFT without a solved state. */
+int nmpc_start_state(nmpc_handle* h, int init, const double* x0, double* x, double* u,
+                     double* lam, void* stream);
+
+/* State and costate trajectories of a control trajectory u (device
+   [sum N*n_u]) from x0, ref (device [sum ng]): x_i = x_{i-1} + h (Lap Phi
+   (x_{i-1}) + b0 B u_i) forward (the model of eq. 6 stepped explicitly,
+   stable while h k(w) 2 (1/dx^2 + 1/dy^2) <= 1), then backward from
+   lambda_{N+1} = h qf (x_N - ref): lambda_i = lambda_{i+1} + h (q (x_i - ref)
+   + Phi'(x_i) Lap lambda_{i+1}) (the costate rows of eq. 9 with the coupling
+   taken at the later stage).  Written to device x, lam [sum N*ng]: a start
+   consistent with u to O(h^2) per stage for NMPC_INIT_GUESS (no counterpart
+   in the paper; it completes a control-only guess such as a learned one).
+   2 N launches; NMPC_ERR_BAD_ARG for a NULL array. */
+int nmpc_rollout(nmpc_handle* h, const double* x0, const double* ref, const double* u, double* x,
+                 double* lam, void* stream);
+
 /* Copy the handle's current state (after a solve: the returned iterates) to
    packed device arrays x, u, lam; any pointer may be NULL to skip it. */
 int nmpc_get_state(nmpc_handle* h, double* x, double* u, double* lam, void* stream);

@@ -53,6 +53,14 @@ int nmpc_transpose_bf16(const void* in, void* out, int rows, int cols, void* str
 int nmpc_cast_f32_f64(const float* in, double* out, int64_t n, void* stream);
 int nmpc_cast_f64_f32(const double* in, float* out, int64_t n, void* stream);
 
+/* Average pooling (no counterpart in the paper: the input reduction of the
+   learned warm start for large grids): src device float64 [n_img][my][mx]
+   row-major, dst device float32 [n_img][my/factor][mx/factor], each output
+   the mean of a factor x factor block (summed in float64).  mx and my must be
+   multiples of factor, else NMPC_MLP_ERR_BAD_ARG. */
+int nmpc_pool_avg(const double* src, float* dst, int n_img, int mx, int my, int factor,
+                  void* stream);
+
 /* Network with widths[0..n_layers] (each a multiple of 8), batches up to
    max_batch; weights U(-1/sqrt(in), 1/sqrt(in)) from SplitMix64(seed), biases
    0.  Synchronous. */

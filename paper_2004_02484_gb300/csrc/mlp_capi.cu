@@ -119,6 +119,19 @@ int nmpc_cast_f64_f32(const double* in, float* out, int64_t n, void* stream) {
   return NMPC_MLP_OK;
 }
 
+int nmpc_pool_avg(const double* src, float* dst, int n_img, int mx, int my, int factor,
+                  void* stream) {
+  if (!src || !dst || n_img < 0 || mx < 1 || my < 1 || factor < 1 || (mx % factor) != 0 ||
+      (my % factor) != 0)
+    return NMPC_MLP_ERR_BAD_ARG;
+  const long long n = (long long)n_img * (mx / factor) * (my / factor);
+  if (n == 0) return NMPC_MLP_OK;
+  mlp_dev::k_pool_avg<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(src, dst, n_img, mx, my,
+                                                                          factor);
+  MCK(cudaGetLastError());
+  return NMPC_MLP_OK;
+}
+
 int nmpc_mlp_create(int n_layers, const int* widths, int max_batch, uint64_t seed,
                     nmpc_mlp** out) {
   if (!out || !widths || n_layers < 1 || n_layers > 16 || max_batch < 1) return NMPC_MLP_ERR_BAD_ARG;

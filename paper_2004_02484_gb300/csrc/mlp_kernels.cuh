@@ -254,6 +254,25 @@ __global__ void k_cast_f64_f32(const double* in, float* out, long long n) {
     out[e] = (float)in[e];
 }
 
+// Average pooling of n_img row-major my x mx float64 fields by f x f blocks
+// into float32 [n_img][(my/f) (mx/f)] (sums in float64).
+__global__ void k_pool_avg(const double* src, float* dst, int n_img, int mx, int my, int f) {
+  const int ox = mx / f, oy = my / f;
+  const long long n = (long long)n_img * ox * oy;
+  const double inv = 1.0 / ((double)f * f);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long img = e / ((long long)ox * oy);
+    const int o = (int)(e - img * ox * oy);
+    const int oyi = o / ox, oxi = o - oyi * ox;
+    const double* s = src + img * (long long)mx * my + (long long)oyi * f * mx + (long long)oxi * f;
+    double acc = 0.0;
+    for (int a = 0; a < f; ++a)
+      for (int c = 0; c < f; ++c) acc += s[(long long)a * mx + c];
+    dst[e] = (float)(acc * inv);
+  }
+}
+
 // loss = mean((y - t)^2) over B*N; dy = 2 (y - t) / (B*N) written as bf16 (and fp32)
 __global__ void k_mse(const float* y, const float* t, long long n, float* dy32,
                       __nv_bfloat16* dy16, float* loss_acc) {

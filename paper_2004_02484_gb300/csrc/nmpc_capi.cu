@@ -1259,6 +1259,45 @@ int nmpc_closed_loop(nmpc_handle* h, double* w, const double* ref, int steps, in
   return rc_all;
 }
 
+int nmpc_start_state(nmpc_handle* h, int init, const double* x0, double* x, double* u,
+                     double* lam, void* stream) {
+  if (!h || !x || !u || !lam) return NMPC_ERR_BAD_ARG;
+  if (init == NMPC_INIT_COLD) {
+    if (!x0) return NMPC_ERR_BAD_ARG;
+  } else if (init == NMPC_INIT_SHIFT) {
+    if (!h->has_state) return NMPC_ERR_BAD_ARG;
+    x0 = nullptr;
+  } else {
+    return NMPC_ERR_BAD_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  nmpc_dev::k_shift_state<<<per_instance_grid(h), 256, 0, st>>>(
+      h->inst_d, h->n_inst, h->xb[2], h->ub[2], h->lb[2], x, u, lam, x0);
+  h->launches++;
+  CK(cudaGetLastError());
+  return NMPC_OK;
+}
+
+int nmpc_rollout(nmpc_handle* h, const double* x0, const double* ref, const double* u, double* x,
+                 double* lam, void* stream) {
+  if (!h || !x0 || !ref || !u || !x || !lam) return NMPC_ERR_BAD_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int nmax = 0;
+  for (const InstDev& I : h->inst_h) nmax = std::max(nmax, I.N);
+  for (int i = 0; i < nmax; ++i) {
+    nmpc_dev::k_rollout_state<<<per_instance_grid(h), 256, 0, st>>>(h->inst_d, h->n_inst, h->act_d,
+                                                                    x0, u, x, i);
+    h->launches++;
+  }
+  for (int i = 0; i < nmax; ++i) {
+    nmpc_dev::k_rollout_costate<<<per_instance_grid(h), 256, 0, st>>>(h->inst_d, h->n_inst, ref, x,
+                                                                      lam, i);
+    h->launches++;
+  }
+  CK(cudaGetLastError());
+  return NMPC_OK;
+}
+
 int nmpc_get_state(nmpc_handle* h, double* x, double* u, double* lam, void* stream) {
   if (!h) return NMPC_ERR_BAD_ARG;
   cudaStream_t st = (cudaStream_t)stream;

@@ -1593,6 +1593,91 @@ __global__ void k_gather_final(FinalArgs F) {
   }
 }
 
+// A start iterate written to (xo, uo, lo): with x0 == nullptr the
+// receding-horizon shift of (xc, uc, lc) (stage i takes stage i + 1, the last
+// stage is repeated); otherwise the cold start x_i = x0, u = 0, lambda = 0.
+__global__ void k_shift_state(const InstDev* inst, int n_inst, const double* xc, const double* uc,
+                              const double* lc, double* xo, double* uo, double* lo,
+                              const double* x0 = nullptr) {
+  const int b = blockIdx.y;
+  if (b >= n_inst) return;
+  const InstDev I = inst[b];
+  const long long n = (long long)I.N * I.ng;
+  if (x0) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+      xo[I.s_off + e] = x0[I.g_off + (e % I.ng)];
+      lo[I.s_off + e] = 0.0;
+    }
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)I.N * I.nu;
+         e += (long long)gridDim.x * blockDim.x)
+      uo[I.u_off + e] = 0.0;
+    return;
+  }
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / I.ng;
+    const long long src = (i + 1 < I.N) ? e + I.ng : e;
+    xo[I.s_off + e] = xc[I.s_off + src];
+    lo[I.s_off + e] = lc[I.s_off + src];
+  }
+  const long long nu_all = (long long)I.N * I.nu;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nu_all;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / I.nu;
+    uo[I.u_off + e] = uc[I.u_off + ((i + 1 < I.N) ? e + I.nu : e)];
+  }
+}
+
+// Trajectory of a control guess, one stage per launch for every instance
+// (instances with N <= i skip).  State, forward: x_i = x_{i-1} + h (Lap Phi
+// (x_{i-1}) + b0 B u_i), x_{-1} = x0 (the model of eq. 6 stepped explicitly).
+__global__ void k_rollout_state(const InstDev* inst, int n_inst, const int* act, const double* x0,
+                                const double* u, double* x, int i) {
+  const int b = blockIdx.y;
+  if (b >= n_inst) return;
+  const InstDev I = inst[b];
+  if (i >= I.N) return;
+  const double* src = (i == 0) ? x0 + I.g_off : x + I.s_off + (long long)(i - 1) * I.ng;
+  double* dst = x + I.s_off + (long long)i * I.ng;
+  const double* ui = u + I.u_off + (long long)i * I.nu;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < I.ng; c += gridDim.x * blockDim.x) {
+    const int ix = c % I.mx, iy = c / I.mx;
+    double srcu = 0.0;
+    for (int a = 0; a < I.nu; ++a)
+      if (act[I.act_off + a] == c) srcu += ui[a];
+    const double lphi = nbr_sum<double>(c, ix, iy, I.mx, I.my, I.cx, I.cy,
+                                        [&](int m) { return phi_d(src[m], I.k0, I.k1); }) -
+                        I.dcoef * phi_d(src[c], I.k0, I.k1);
+    dst[c] = src[c] + I.h * (lphi + I.b0 * srcu);
+  }
+}
+
+// Costate, backward from lambda_{N+1} = h qf (x_N - ref): the costate rows of
+// eq. 9 with the coupling term taken at the later stage,
+// lambda_i = lambda_{i+1} + h (q (x_i - ref) + Phi'(x_i) Lap lambda_{i+1}).
+__global__ void k_rollout_costate(const InstDev* inst, int n_inst, const double* ref,
+                                  const double* x, double* lam, int i_from_end) {
+  const int b = blockIdx.y;
+  if (b >= n_inst) return;
+  const InstDev I = inst[b];
+  const int i = I.N - 1 - i_from_end;
+  if (i < 0) return;
+  const double* xi = x + I.s_off + (long long)i * I.ng;
+  const double* r = ref + I.g_off;
+  const double* ln = lam + I.s_off + (long long)(i + 1) * I.ng;  // used for i < N - 1
+  double* li = lam + I.s_off + (long long)i * I.ng;
+  const bool last = (i == I.N - 1);
+  const double* xN = x + I.s_off + (long long)(I.N - 1) * I.ng;
+  auto next = [&](int m) { return last ? I.hqf * (xN[m] - r[m]) : ln[m]; };
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < I.ng; c += gridDim.x * blockDim.x) {
+    const int ix = c % I.mx, iy = c / I.mx;
+    const double lap = nbr_sum<double>(c, ix, iy, I.mx, I.my, I.cx, I.cy, next) - I.dcoef * next(c);
+    const double dphi = I.k0 * (1.0 + I.k1 * xi[c]);
+    li[c] = next(c) + I.h * (I.q * (xi[c] - r[c]) + dphi * lap);
+  }
+}
+
 // Closed loop on the device (one graph): the step loop's WHILE condition,
 // the per-step record of each instance's status, iterations and residual,
 // and a plain copy (graph loop bodies hold kernels only).

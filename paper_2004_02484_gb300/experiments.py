@@ -11,6 +11,13 @@ closedloop: the 2D 256x256, N = 100, 16-actuator batch in a receding-horizon
             reports solves/s (instances x steps / time), iterations per step,
             the iteration kernel's algorithmic HBM bandwidth and, with
             --check, the float64 residual of sampled returned states.
+closedloop_learned: the same loop with the learned start (controls from a
+            network on 4x4-pooled plant state and reference, trained on plain
+            closed loops of disjoint seeds; state and costate from the
+            controls' rollout or from the plain start) against the plain loop
+            on the same instances, for three rules (per-instance choice by
+            float64 residual, or always the learned start, rollout or not):
+            iterations per step and time.
 Prints one JSON line per experiment.
 """
 from __future__ import annotations
@@ -81,9 +88,53 @@ def closedloop(n: int, steps: int, grid: int, horizon: int, n_sub: int, check: i
     return out
 
 
+def closedloop_learned(n_train: int, train_steps: int, n_test: int, steps: int, grid: int,
+                       horizon: int, n_sub: int, fit_steps: int):
+    import torch
+    from . import warmstart as WS
+    t0 = time.perf_counter()
+    X, U = [], []
+    train = wl.heat2d_large_batch(n=n_train, base_seed=7000, m=grid, horizon=horizon)
+    for b0 in range(0, n_train, 8):
+        x, u = WS.closed_loop_data(train[b0:b0 + 8], train_steps, n_sub)
+        X.append(x)
+        U.append(u)
+    X, U = np.concatenate(X), np.concatenate(U)
+    t_gen = time.perf_counter() - t0
+    lcs = WS.LearnedControlStart(train[0])
+    losses = lcs.fit(X, U, steps=fit_steps)
+    test = wl.heat2d_large_batch(n=n_test, base_seed=5000, m=grid, horizon=horizon)
+    res = {"experiment": "closedloop_learned", "train_samples": int(X.shape[0]), "gen_s": t_gen,
+           "loss_first": losses[0], "loss_last": losses[-1], "instances": n_test, "steps": steps}
+    # plain loop (one graph) and learned loop on the same instances
+    s = G.Solver(test, tol=1e-6, precision=G.NMPC_MIXED, max_iter=4000)
+    w = s.x0.clone()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, iters, r = G.nmpc_closed_loop(s.h, w, s.ref, steps, n_sub, n_test)
+    torch.cuda.synchronize()
+    res.update({"plain_s": time.perf_counter() - t0, "plain_iters_per_step": iters.mean(axis=1).tolist(),
+                "plain_rc": rc})
+    s.close()
+    for rule, decode in (("residual", "rollout"), ("always", "rollout"), ("always", "controls")):
+        s = G.Solver(test, tol=1e-6, precision=G.NMPC_MIXED, max_iter=4000)
+        w = s.x0.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = WS.closed_loop_learned(s, lcs, w, steps, n_sub, rule=rule, decode=decode)
+        torch.cuda.synchronize()
+        res[rule + "_" + decode] = {"s": time.perf_counter() - t0,
+                     "iters_per_step": out["iters"].mean(axis=1).tolist(),
+                     "learned_used_per_step": out["learned"].mean(axis=1).tolist(),
+                     "res_plain_first_step": float(out["res_plain"][0].max()),
+                     "res_learned_first_step": float(out["res_learned"][0].max())}
+        s.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", choices=["batch1d", "closedloop"])
+    ap.add_argument("which", choices=["batch1d", "closedloop", "closedloop_learned"])
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--grid", type=int, default=256)
@@ -92,6 +143,9 @@ def main():
     ap.add_argument("--check", type=int, default=1)
     ap.add_argument("--cluster", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--n-train", type=int, default=64)
+    ap.add_argument("--train-steps", type=int, default=12)
+    ap.add_argument("--fit-steps", type=int, default=2000)
     a = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
@@ -99,6 +153,9 @@ def main():
     build.build()
     if a.which == "batch1d":
         print(json.dumps(batch1d(a.n or 1024)), flush=True)
+    elif a.which == "closedloop_learned":
+        print(json.dumps(closedloop_learned(a.n_train, a.train_steps, a.n or 8, a.steps, a.grid,
+                                            a.horizon, a.n_sub, a.fit_steps)), flush=True)
     else:
         res = closedloop(a.n or 64, a.steps, a.grid, a.horizon, a.n_sub, a.check,
                          cluster=a.cluster, threads=a.threads)

@@ -17,7 +17,7 @@ NMPC_MLP_ERR_BAD_ARG = -1
 NMPC_MLP_ERR_CUDA = -2
 
 EXPORTED = ["nmpc_gemm_bf16", "nmpc_cast_f32_bf16", "nmpc_cast_f32_f64", "nmpc_cast_f64_f32",
-            "nmpc_transpose_bf16",
+            "nmpc_transpose_bf16", "nmpc_pool_avg",
             "nmpc_mlp_create", "nmpc_mlp_num_params",
             "nmpc_mlp_set_params", "nmpc_mlp_get_params", "nmpc_mlp_forward",
             "nmpc_mlp_backward", "nmpc_mlp_get_grads", "nmpc_mlp_adam_step",
@@ -30,6 +30,7 @@ _SIG = {
     "nmpc_cast_f32_f64": (_I, [_P, _P, ctypes.c_int64, _P]),
     "nmpc_transpose_bf16": (_I, [_P, _P, _I, _I, _P]),
     "nmpc_cast_f64_f32": (_I, [_P, _P, ctypes.c_int64, _P]),
+    "nmpc_pool_avg": (_I, [_P, _P, _I, _I, _I, _I, _P]),
     "nmpc_mlp_create": (_I, [_I, ctypes.POINTER(_I), _I, ctypes.c_uint64, ctypes.POINTER(_P)]),
     "nmpc_mlp_num_params": (ctypes.c_int64, [_P]),
     "nmpc_mlp_set_params": (_I, [_P, _P]),
@@ -90,6 +91,15 @@ def nmpc_cast_f32_f64(x, out, stream=None):
     assert x.dtype == torch.float32 and out.dtype == torch.float64 and x.is_cuda and out.is_cuda
     _check(LIB.nmpc_cast_f32_f64(x.data_ptr(), out.data_ptr(), x.numel(), _stream(stream)),
            "nmpc_cast_f32_f64")
+
+
+def nmpc_pool_avg(src, out, n_img: int, mx: int, my: int, factor: int, stream=None):
+    """float64 fields [n_img, my, mx] -> float32 block means [n_img, my/f, mx/f]."""
+    import torch
+    assert src.dtype == torch.float64 and out.dtype == torch.float32 and src.is_cuda and out.is_cuda
+    assert src.numel() >= n_img * mx * my and out.numel() >= n_img * (mx // factor) * (my // factor)
+    _check(LIB.nmpc_pool_avg(src.data_ptr(), out.data_ptr(), n_img, mx, my, factor, _stream(stream)),
+           "nmpc_pool_avg")
 
 
 def nmpc_cast_f64_f32(x, out, stream=None):

@@ -60,7 +60,8 @@ class nmpc_stats(ctypes.Structure):
 
 EXPORTED = ["nmpc_default_opts", "nmpc_setup", "nmpc_solve", "nmpc_solve_host",
             "nmpc_residual", "nmpc_iterate", "nmpc_get_state", "nmpc_set_state",
-            "nmpc_sizes", "nmpc_launch_count", "nmpc_launch_plan", "nmpc_destroy", "nmpc_strerror",
+            "nmpc_sizes", "nmpc_launch_count", "nmpc_launch_plan", "nmpc_start_state", "nmpc_rollout", "nmpc_destroy",
+            "nmpc_strerror",
             "nmpc_solve_noalloc", "nmpc_plant_step", "nmpc_closed_loop"]
 
 
@@ -83,6 +84,8 @@ def _load() -> ctypes.CDLL:
         "nmpc_set_state": (I, [P, P, P, P, P]),
         "nmpc_sizes": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
         "nmpc_launch_plan": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
+        "nmpc_start_state": (I, [P, I, P, P, P, P, P]),
+        "nmpc_rollout": (I, [P, P, P, P, P, P, P]),
         "nmpc_launch_count": (ctypes.c_int64, [P]),
         "nmpc_destroy": (V, [P]),
         "nmpc_strerror": (ctypes.c_char_p, [I]),
@@ -239,6 +242,19 @@ def nmpc_closed_loop(h, w, ref, steps: int, n_sub: int, n_inst: int, u_hist=None
                               iters.ctypes.data, res.ctypes.data, _stream(stream))
     _check(rc, "nmpc_closed_loop", allow=(NMPC_ERR_NOT_CONVERGED, NMPC_ERR_DIVERGED))
     return rc, iters, res
+
+
+def nmpc_start_state(h, init: int, x0, x, u, lam, stream=None):
+    """Start iterate of `init` (NMPC_INIT_COLD from x0, or NMPC_INIT_SHIFT of the
+    current state) into device float64 arrays x, u, lam."""
+    _check(LIB.nmpc_start_state(h, init, _ptr(x0), _ptr(x), _ptr(u), _ptr(lam), _stream(stream)),
+           "nmpc_start_state")
+
+
+def nmpc_rollout(h, x0, ref, u, x, lam, stream=None):
+    """State (forward) and costate (backward) trajectories of the controls u."""
+    _check(LIB.nmpc_rollout(h, _ptr(x0), _ptr(ref), _ptr(u), _ptr(x), _ptr(lam), _stream(stream)),
+           "nmpc_rollout")
 
 
 def nmpc_launch_count(h) -> int:

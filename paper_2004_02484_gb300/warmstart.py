@@ -248,6 +248,160 @@ class LearnedWarmStart:
         return ws
 
 
+class LearnedControlStart:
+    """Learned start of the receding-horizon loop on large grids (Sec. 5.3's
+    closed loop): a network maps the plant state and the reference, each
+    reduced to f x f block means (library pooling kernel), to the control
+    trajectory; the candidate start takes its state and costate from the
+    plain start (the shifted previous solution, or the cold start at the first
+    step).  The loop keeps, per instance, whichever candidate has the smaller
+    float64 KKT residual, so the plain method stays the fallback."""
+
+    def __init__(self, template, pool: int = 4, hidden: Sequence[int] = (512, 512, 512),
+                 max_batch: int = 256, seed: int = 0):
+        if template.mx % pool or template.my % pool:
+            raise ValueError("grid not divisible by the pooling factor")
+        self.mx, self.my, self.pool = template.mx, template.my, pool
+        self.ngp = (template.mx // pool) * (template.my // pool)
+        self.N, self.nu = template.horizon, len(template.act)
+        self.n_out = self.N * self.nu
+        self.widths = [2 * self.ngp] + list(hidden) + [self.n_out]
+        self.net = GM.MLP(self.widths, max_batch, seed)
+        self.mean = self.std = None
+
+    def features(self, w, ref, B: int):
+        """Pooled [w; ref] rows, float32 device [B, 2 ngp]."""
+        torch = _torch()
+        f = torch.empty((B, 2, self.ngp), dtype=torch.float32, device=w.device)
+        wp = torch.empty((B, self.ngp), dtype=torch.float32, device=w.device)
+        rp = torch.empty((B, self.ngp), dtype=torch.float32, device=w.device)
+        GM.nmpc_pool_avg(w, wp, B, self.mx, self.my, self.pool)
+        GM.nmpc_pool_avg(ref, rp, B, self.mx, self.my, self.pool)
+        f[:, 0].copy_(wp)
+        f[:, 1].copy_(rp)
+        return f.view(B, 2 * self.ngp)
+
+    def fit(self, X: np.ndarray, U: np.ndarray, steps: int = 2000, batch: int = 128,
+            lr: float = 1e-3, seed: int = 0) -> List[float]:
+        """Train on pooled inputs X [n, 2 ngp] and control trajectories U [n, N nu]."""
+        torch = _torch()
+        n = X.shape[0]
+        T = U.astype(np.float64)
+        self.mean = T.mean(axis=0)
+        self.std = T.std(axis=0) + 1e-12 * max(np.abs(T).max(), 1.0)
+        Td = torch.from_numpy(((T - self.mean) / self.std).astype(np.float32)).cuda()
+        Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).cuda()
+        rng = np.random.default_rng(seed)
+        batch = min(batch, self.net.max_batch, n - n % 8)
+        losses = []
+        for it in range(steps):
+            idx = torch.from_numpy(rng.choice(n, size=batch, replace=False)).cuda()
+            lr_t = lr * 0.5 * (1.0 + np.cos(np.pi * it / steps))
+            want = (it % 50 == 0) or it == steps - 1
+            loss = self.net.train_step(Xd[idx].contiguous(), Td[idx].contiguous(), lr_t,
+                                       want_loss=want)
+            if want:
+                losses.append(loss)
+        LearnedWarmStart._fold_standardisation(self)
+        return losses
+
+    def predict_u(self, w, ref, B: int):
+        """Control trajectory guesses, float64 device [B N nu]."""
+        torch = _torch()
+        y = torch.empty((B, self.n_out), dtype=torch.float32, device=w.device)
+        self.net.forward(self.features(w, ref, B), y)
+        u = torch.empty(B * self.n_out, dtype=torch.float64, device=w.device)
+        GM.nmpc_cast_f32_f64(y.view(-1), u)
+        return u
+
+
+def closed_loop_data(instances, steps: int, n_sub: int, pool: int = 4, tol: float = 1e-6,
+                     precision: int = G.NMPC_MIXED):
+    """Plain closed loops of `instances` (cold first step, shifted starts): per
+    step the pooled [plant state; reference] rows and the solved control
+    trajectories.  Returns X float32 [steps B, 2 ngp], U float32 [steps B, N nu]."""
+    torch = _torch()
+    B = len(instances)
+    lcs = LearnedControlStart(instances[0], pool=pool, max_batch=8)
+    s = G.Solver(instances, tol=tol, precision=precision, max_iter=6000)
+    w = s.x0.clone()
+    X, U = [], []
+    for t in range(steps):
+        rc, st = G.nmpc_solve(s.h, w, s.ref, s.u, B,
+                              init=G.NMPC_INIT_COLD if t == 0 else G.NMPC_INIT_SHIFT)
+        if rc != G.NMPC_OK:
+            raise RuntimeError(f"training solve failed: {rc}")
+        X.append(lcs.features(w, s.ref, B).cpu().numpy())
+        U.append(s.u.view(B, -1).float().cpu().numpy())
+        G.nmpc_plant_step(s.h, w, 0.0, n_sub)
+    s.close()
+    return np.concatenate(X), np.concatenate(U)
+
+
+def closed_loop_learned(solver: "G.Solver", lcs: LearnedControlStart, w, steps: int,
+                        n_sub: int, rule: str = "always",
+                        decode: str = "rollout") -> Dict[str, object]:
+    """Receding-horizon loop with the learned start: per step the plain
+    candidate (cold at the first step, then the shifted previous solution)
+    and the learned one: the predicted controls with, for decode "rollout",
+    the state and costate trajectories they generate (nmpc_rollout), or, for
+    decode "controls", the plain candidate's state and costate.  rule
+    "residual": per instance the candidate with the smaller float64 residual
+    starts the solve (NMPC_INIT_GUESS); rule "always": the learned candidate
+    starts it, and a solve that does not converge is repeated from the plain
+    one.  Then the plant moves one stage length.  w (device float64 plant
+    state) is updated in place.  The initial residual predicts the iteration
+    count poorly: the rollout start has the larger residual on the 256x256,
+    N = 100 loop yet converges in fewer iterations, hence rule "always"."""
+    torch = _torch()
+    B = solver.n
+    dev = w.device
+    x = torch.empty(solver.n_s, dtype=torch.float64, device=dev)
+    lam = torch.empty_like(x)
+    x_l = torch.empty_like(x)
+    lam_l = torch.empty_like(x)
+    u_p = torch.empty(solver.n_u, dtype=torch.float64, device=dev)
+    iters, chosen, r_plain, r_learn = [], [], [], []
+    u_offs = np.cumsum([0] + [i.horizon * len(i.act) for i in solver.instances])
+    s_offs = np.cumsum([0] + [i.horizon * i.mx * i.my for i in solver.instances])
+    first = True
+    for t in range(steps):
+        init = G.NMPC_INIT_COLD if first else G.NMPC_INIT_SHIFT
+        G.nmpc_start_state(solver.h, init, w, x, u_p, lam)
+        u_l = lcs.predict_u(w, solver.ref, B)
+        if decode == "rollout":
+            G.nmpc_rollout(solver.h, w, solver.ref, u_l, x_l, lam_l)
+        else:
+            x_l.copy_(x)
+            lam_l.copy_(lam)
+        rp = G.nmpc_residual(solver.h, w, solver.ref, x, u_p, lam, B)[:, 0]
+        rl = G.nmpc_residual(solver.h, w, solver.ref, x_l, u_l, lam_l, B)[:, 0]
+        pick = (rl < rp) if rule == "residual" else np.ones(B, dtype=bool)
+        xs, us, ls = x.clone(), u_p.clone(), lam.clone()
+        for b in range(B):
+            if pick[b]:
+                us[u_offs[b]:u_offs[b + 1]].copy_(u_l[u_offs[b]:u_offs[b + 1]])
+                xs[s_offs[b]:s_offs[b + 1]].copy_(x_l[s_offs[b]:s_offs[b + 1]])
+                ls[s_offs[b]:s_offs[b + 1]].copy_(lam_l[s_offs[b]:s_offs[b + 1]])
+        G.nmpc_set_state(solver.h, xs, us, ls)
+        rc, st = G.nmpc_solve(solver.h, w, solver.ref, solver.u, B, init=G.NMPC_INIT_GUESS)
+        if rc != G.NMPC_OK and pick.any():
+            # the plain method is the fallback
+            G.nmpc_set_state(solver.h, x, u_p, lam)
+            rc, st = G.nmpc_solve(solver.h, w, solver.ref, solver.u, B, init=G.NMPC_INIT_GUESS)
+            pick[:] = False
+        if rc != G.NMPC_OK:
+            raise RuntimeError(f"closed-loop solve failed: {rc}")
+        iters.append([st[b].iters for b in range(B)])
+        chosen.append(pick.astype(int).tolist())
+        r_plain.append(rp.tolist())
+        r_learn.append(rl.tolist())
+        G.nmpc_plant_step(solver.h, w, 0.0, n_sub)
+        first = False
+    return {"iters": np.array(iters), "learned": np.array(chosen),
+            "res_plain": np.array(r_plain), "res_learned": np.array(r_learn)}
+
+
 def evaluate(ws: LearnedWarmStart, seeds: Sequence[int], tol: float = 1e-6,
              precision: int = G.NMPC_MIXED) -> Dict[str, float]:
     """Iterations and wall time to ||K||_inf <= tol from the cold start and

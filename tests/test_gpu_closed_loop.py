@@ -108,3 +108,94 @@ def test_graph_closed_loop_equals_host_driven_loop(G, n_sub):
     assert np.array_equal(a[2], b[2])
     assert np.array_equal(a[3], b[3])
     assert np.array_equal(a[4], b[4])
+
+
+def test_pool_and_start_state_match_their_definitions(G):
+    """nmpc_pool_avg is the f x f block mean; nmpc_start_state writes the cold
+    start (x_i = x0, u = 0, lambda = 0) and the receding-horizon shift (stage i
+    takes stage i + 1, the last repeated) of the handle's state."""
+    import torch
+    from paper_2004_02484_gb300 import mlp as GM
+    insts = [wl.heat2d(32, 24, 5, 2, 2, seed=71), wl.heat2d(32, 24, 5, 2, 2, seed=72)]
+    s = G.Solver(insts, tol=1e-6, precision=1, max_iter=2000)
+    B, ng = 2, 32 * 24
+    f = torch.empty((B, (32 // 4) * (24 // 4)), dtype=torch.float32, device="cuda")
+    GM.nmpc_pool_avg(s.x0, f, B, 32, 24, 4)
+    x0 = s.x0.cpu().numpy().reshape(B, 24, 32)
+    want = x0.reshape(B, 6, 4, 8, 4).mean(axis=(2, 4)).reshape(B, -1)
+    assert np.abs(f.cpu().numpy() - want).max() <= 1e-6 * np.abs(want).max()
+    x = torch.empty(s.n_s, dtype=torch.float64, device="cuda")
+    lam = torch.empty_like(x)
+    u = torch.empty(s.n_u, dtype=torch.float64, device="cuda")
+    G.nmpc_start_state(s.h, G.NMPC_INIT_COLD, s.x0, x, u, lam)
+    assert np.array_equal(x.cpu().numpy().reshape(B, 5, ng), np.repeat(x0.reshape(B, 1, ng), 5, 1))
+    assert not u.cpu().numpy().any() and not lam.cpu().numpy().any()
+    s.solve()
+    xs, us, ls = s.state()
+    G.nmpc_start_state(s.h, G.NMPC_INIT_SHIFT, None, x, u, lam)
+    X, L, U = (a.cpu().numpy() for a in (xs, ls, us))
+    for arr, got, per in ((X, x, ng), (L, lam, ng), (U, u, 4)):
+        a = arr.reshape(B, 5, per)
+        want = np.concatenate([a[:, 1:], a[:, -1:]], axis=1)
+        assert np.array_equal(got.cpu().numpy().reshape(B, 5, per), want)
+    s.close()
+
+
+def test_learned_closed_loop_keeps_the_better_start_and_converges(G):
+    """The learned closed loop (network on pooled inputs, per-instance choice
+    of the start with the smaller float64 residual) solves every step to the
+    tolerance, and every chosen start's residual is the smaller one."""
+    import torch
+    from paper_2004_02484_gb300 import warmstart as WS
+    train = wl.heat2d_large_batch(n=4, base_seed=7000, m=32, horizon=10)
+    X, U = WS.closed_loop_data(train, 4, 2)
+    lcs = WS.LearnedControlStart(train[0], pool=4, max_batch=16)
+    losses = lcs.fit(X, U, steps=200, batch=16)
+    assert losses[-1] < losses[0]
+    test = wl.heat2d_large_batch(n=2, base_seed=5000, m=32, horizon=10)
+    s = G.Solver(test, tol=1e-6, precision=1, max_iter=4000)
+    w = s.x0.clone()
+    out = WS.closed_loop_learned(s, lcs, w, 3, 2, rule="residual", decode="rollout")
+    x, u, lam = s.state()
+    r = G.nmpc_residual(s.h, w, s.ref, x, u, lam, 2)  # the last step's solution, plant moved on
+    chosen = out["learned"].astype(bool)
+    best = np.where(chosen, out["res_learned"], out["res_plain"])
+    assert np.all(best <= np.minimum(out["res_learned"], out["res_plain"]))
+    assert out["iters"].shape == (3, 2) and np.all(out["iters"] > 0)
+    s.close()
+
+
+def test_rollout_matches_its_definition(G):
+    """nmpc_rollout: explicit-Euler state trajectory of u from x0 and the
+    costate recursion lambda_i = lambda_{i+1} + h (q (x_i - ref) + Phi'(x_i)
+    Lap lambda_{i+1}) from lambda_{N+1} = h qf (x_N - ref), written out here
+    with the oracle's model terms, on a ragged 2D + 1D batch."""
+    import torch
+    insts = [wl.heat2d(20, 18, 7, 3, 3, seed=81), wl.heat1d(40, 11, 2, 0.02, seed=82)]
+    s = G.Solver(insts, tol=1e-6, precision=1, max_iter=2000)
+    rng = np.random.default_rng(83)
+    u = _t(rng.normal(0.0, 0.3, s.n_u))
+    x = torch.empty(s.n_s, dtype=torch.float64, device="cuda")
+    lam = torch.empty_like(x)
+    G.nmpc_rollout(s.h, s.x0, s.ref, u, x, lam)
+    torch.cuda.synchronize()
+    Us = G.split_stages(insts, u.cpu().numpy(), "nu")
+    Xs = G.split_stages(insts, x.cpu().numpy(), "ng")
+    Ls = G.split_stages(insts, lam.cpu().numpy(), "ng")
+    for inst, Ub, Xb, Lb in zip(insts, Us, Xs, Ls):
+        p = O.Problem(inst)
+        X = np.empty((p.N,) + p.shape)
+        prev = p.x0
+        for i in range(p.N):
+            X[i] = prev + p.h * p.f(prev, Ub[i])
+            prev = X[i]
+        L = np.empty_like(X)
+        nxt = p.h * p.qf * (X[-1] - p.ref)
+        for i in range(p.N - 1, -1, -1):
+            L[i] = nxt + p.h * (p.q * (X[i] - p.ref) + p.dphi(X[i]) * p.lap(nxt))
+            nxt = L[i]
+        sx = np.abs(X).max()
+        sl = np.abs(L).max()
+        assert np.abs(Xb.reshape(X.shape) - X).max() <= 1e-12 * sx
+        assert np.abs(Lb.reshape(L.shape) - L).max() <= 1e-12 * sl
+    s.close()
