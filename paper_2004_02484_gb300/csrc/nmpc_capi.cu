@@ -6,8 +6,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/nmpc.h"
@@ -89,8 +91,18 @@ struct nmpc_handle {
   // the whole iteration loop as one graph: a WHILE node over chunks
   cudaGraphExec_t loop_exec = nullptr;
   int loop_chunk = 0;
+  // tile path (k_tile)
+  int4* tiles_d = nullptr;
+  int n_tiles = 0;
+  int tile_x = 0, tile_y = 0, tile_threads = 0, tile_region = 0;
+  int n_tile_inst = 0;
+  size_t tile_smem = 0;
+  int4* patches_d = nullptr;  // k_patch work items
+  int n_patches = 0;
+  size_t patch_smem = 0;
+  double* v3_d = nullptr;  // v3 per control, written by k_patch
   long long launches = 0;
-  long long iter_launches = 0;  // of the iteration kernel
+  long long iter_launches = 0;  // iteration steps (each one or two kernel launches)
   bool has_state = false;
 };
 
@@ -125,7 +137,8 @@ void free_all(nmpc_handle* h) {
                   h->xb[0], h->xb[1], h->xb[2], h->ub[0], h->ub[1], h->ub[2],
                   h->lb[0], h->lb[1], h->lb[2], h->ictl, h->res_inf, h->res_err, h->res_sq,
                   h->res_first, h->status, h->iters, h->final_buf, h->fin_inf,
-                  h->fin_2, h->full_from, h->full0, h->scratch};
+                  h->fin_2, h->full_from, h->full0, h->scratch, h->tiles_d, h->patches_d,
+                  h->v3_d};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   void* hp[] = {h->h_active, h->h_status, h->h_iters, h->h_fin, h->h_res, h->h_resinf};
@@ -180,6 +193,13 @@ IterArgs make_args(nmpc_handle* h) {
   A.box_r = h->box_r;
   A.scratch = h->smem_mode ? nullptr : h->scratch;
   A.scratch_stride = h->scratch_stride;
+  A.tiles = h->tiles_d;
+  A.n_tiles = h->n_tiles;
+  A.tile_x = h->tile_x;
+  A.tile_y = h->tile_y;
+  A.patches = h->patches_d;
+  A.n_patches = h->n_patches;
+  A.v3g = h->v3_d;
   return A;
 }
 
@@ -465,12 +485,85 @@ LaunchPlan plan_of(const nmpc_handle* h) {
   return P;
 }
 
+// Strip kernel variants, one per n_lo = 1 .. 4.
+using TileKernel = void (*)(IterArgs, int, int);
+
+template <typename T>
+TileKernel tile_kernel(int n_lo) {
+  switch (n_lo) {
+    case 1: return nmpc_dev::k_strip<T, 1>;
+    case 2: return nmpc_dev::k_strip<T, 2>;
+    case 3: return nmpc_dev::k_strip<T, 3>;
+    default: return nmpc_dev::k_strip<T, 4>;
+  }
+}
+
+template <typename T>
+TileKernel patch_kernel(int n_lo) {
+  switch (n_lo) {
+    case 1: return nmpc_dev::k_patch<T, 1>;
+    case 2: return nmpc_dev::k_patch<T, 2>;
+    case 3: return nmpc_dev::k_patch<T, 3>;
+    default: return nmpc_dev::k_patch<T, 4>;
+  }
+}
+
+constexpr int PATCH_WARPS = 4;  // warps per k_patch block
+
+
+template <typename T>
+cudaError_t launch_patch(const nmpc_handle* h, const IterArgs& A, cudaStream_t st, int mode, int j) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((h->n_patches + PATCH_WARPS - 1) / PATCH_WARPS));
+  cfg.blockDim = dim3(32 * PATCH_WARPS);
+  cfg.dynamicSmemBytes = h->patch_smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = (mode == nmpc_dev::MODE_SOLVE) ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, patch_kernel<T>(h->opts.n_lo), A, mode, j);
+}
+
+template <typename T>
+cudaError_t launch_tile(const nmpc_handle* h, const IterArgs& A, cudaStream_t st, int mode, int j) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((h->n_tiles + nmpc_dev::STRIP_WARPS - 1) / nmpc_dev::STRIP_WARPS));
+  cfg.blockDim = dim3((unsigned)h->tile_threads);
+  cfg.dynamicSmemBytes = h->tile_smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = (mode == nmpc_dev::MODE_SOLVE) ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, tile_kernel<T>(h->opts.n_lo), A, mode, j);
+}
+
+// One iteration (or one-shot pass): the cluster kernel over the cluster
+// path's work items and the tile kernel over the tiles, whichever exist.
 template <int MODE>
 cudaError_t launch_iterate(nmpc_handle* h, const IterArgs& A, cudaStream_t st, int j = 0) {
-  h->launches++;
   h->iter_launches++;
-  const LaunchPlan P = plan_of(h);
-  return h->mixed ? launch_k<float>(P, A, st, MODE, j) : launch_k<double>(P, A, st, MODE, j);
+  cudaError_t e = cudaSuccess;
+  if (h->n_work > 0) {
+    h->launches++;
+    const LaunchPlan P = plan_of(h);
+    e = h->mixed ? launch_k<float>(P, A, st, MODE, j) : launch_k<double>(P, A, st, MODE, j);
+    if (e != cudaSuccess) return e;
+  }
+  if (h->n_tiles > 0) {
+    // the actuators' v3 first (not needed by a residual-only pass)
+    if (!(MODE == nmpc_dev::MODE_ONESHOT && A.resid_only)) {
+      h->launches++;
+      e = h->mixed ? launch_patch<float>(h, A, st, MODE, j) : launch_patch<double>(h, A, st, MODE, j);
+      if (e != cudaSuccess) return e;
+    }
+    h->launches++;
+    e = h->mixed ? launch_tile<float>(h, A, st, MODE, j) : launch_tile<double>(h, A, st, MODE, j);
+  }
+  return e;
 }
 
 // One chunk of solve iterations on stream st: launches j = 0 .. chunk - 1
@@ -504,7 +597,47 @@ cudaError_t configure_kernels(size_t smem) {
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
   }
+  for (int n_lo = 1; n_lo <= 4; ++n_lo) {
+    cudaError_t e = cudaFuncSetAttribute(tile_kernel<T>(n_lo),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(patch_kernel<T>(n_lo), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   return cudaSuccess;
+}
+
+// Whether instance I may run on the tile path: 2D, n_lo <= 4, and for
+// n_u_it > 1 actuators on distinct cells more than 2 (n_lo - 1) cells apart
+// (Manhattan), so that each actuator's u-iteration sees only its own
+// response.
+bool tile_eligible(const InstDev& I, const int* act, const nmpc_opts& o) {
+  if (I.dim != 2 || o.n_lo > 4) return false;
+  if (o.n_u_it > 1) {
+    const int reach = 2 * (o.n_lo - 1);
+    for (int a = 0; a < I.nu; ++a)
+      for (int b = a + 1; b < I.nu; ++b) {
+        const int dx = std::abs(act[a] % I.mx - act[b] % I.mx);
+        const int dy = std::abs(act[a] / I.mx - act[b] / I.mx);
+        if (dx + dy <= reach) return false;
+      }
+  }
+  return true;
+}
+
+// Whether a stage of instance I fits a cluster of at most 8 CTAs with its
+// float64 inputs staged in shared memory (the slab path's fast shape).
+bool fits_cluster_staged(const InstDev& I, const nmpc_opts& o, bool mixed, int max_optin) {
+  const size_t elem = mixed ? sizeof(float) : sizeof(double);
+  const size_t small = mixed ? small_shared_bytes_t<float>() : small_shared_bytes_t<double>();
+  for (int C = 1; C <= 8; ++C) {
+    const size_t bytes = small + (size_t)slab_stride(I, C) * (nmpc_dev::NUM_FIELDS * elem +
+                                                              nmpc_dev::NUM_SFIELDS * sizeof(double));
+    int t, c;
+    if (bytes <= (size_t)max_optin && thread_shape(slab_cells(I, C), o, &t, &c)) return true;
+  }
+  return false;
 }
 
 bool opts_ok(const nmpc_opts& o) {
@@ -513,7 +646,8 @@ bool opts_ok(const nmpc_opts& o) {
          (o.precision == NMPC_FP64 || o.precision == NMPC_MIXED) && o.threads >= 0 &&
          o.threads <= 512 && (o.threads % 32) == 0 && o.cluster >= 0 && o.cluster <= 16 &&
          (o.cluster <= 8 || o.cluster == 16) && (o.split_min >= 0) &&
-         (o.cells >= 0 && o.cells <= 8);
+         (o.cells >= 0 && o.cells <= 8) && (o.tiled >= 0 && o.tiled <= 2) &&
+         (o.tile_rows >= 0 && o.tile_rows <= 65535);
 }
 
 int validate(const nmpc_desc* d) {
@@ -953,6 +1087,8 @@ void nmpc_default_opts(nmpc_opts* o) {
   o->u_local = 0;
   o->cells = 0;
   o->persistent = 0;
+  o->tiled = 0;
+  o->tile_rows = 0;
 }
 
 int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
@@ -979,7 +1115,6 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
   cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
 
   std::vector<int> act_all;
-  std::vector<int2> work;
   for (int b = 0; b < n_instances; ++b) {
     const nmpc_desc& d = descs[b];
     InstDev I{};
@@ -1007,7 +1142,6 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
     nmpc_dev::derive(I);
     for (int a = 0; a < d.n_u; ++a) act_all.push_back(d.act_cell[a]);
     h->nu_tot += d.n_u;
-    for (int s = 0; s < d.horizon; ++s) work.push_back(make_int2(b, s));
     h->n_s += (long long)I.N * I.ng;
     h->n_u += (long long)I.N * I.nu;
     h->n_g += I.ng;
@@ -1016,7 +1150,6 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
     h->n_max_horizon = std::max(h->n_max_horizon, I.N);
     h->inst_h.push_back(I);
   }
-  h->n_work = (int)work.size();
 
   // launch configuration
   int max_optin = 0;
@@ -1028,9 +1161,75 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
     delete h;
     return NMPC_ERR_CUDA;
   }
-  LaunchPlan P = plan_launch(h->inst_h.data(), n_instances, h->n_work, o, h->mixed,
-                             std::max(1, h->num_sms), max_optin);
-  if (!P.smem_mode) {
+  // instances on the strip path, and the strip shape (shared by all of
+  // them): 32 - 2E own columns (one warp lane per region column) and ty own
+  // rows, by default enough strips for about four waves of warps
+  std::vector<char> on_tiles(n_instances, 0);
+  const int E = 2 * o.n_lo - 1;
+  const int tx = 32 - 2 * E;
+  int ty = 0;
+  if (o.tiled != 2) {
+    int my_max = 0;
+    long long whole = 0;  // strips with whole columns
+    for (int b = 0; b < n_instances; ++b) {
+      const InstDev& I = h->inst_h[b];
+      if (!tile_eligible(I, act_all.data() + I.act_off, o)) continue;
+      if (o.tiled == 0 && fits_cluster_staged(I, o, h->mixed, max_optin)) continue;
+      on_tiles[b] = 1;
+      my_max = std::max(my_max, I.my);
+      whole += (long long)I.N * ((I.mx + tx - 1) / tx);
+    }
+    if (my_max > 0) {
+      if (o.tile_rows) {
+        ty = std::min(o.tile_rows, my_max);
+      } else {
+        const long long target = 4LL * std::max(1, h->num_sms) * 32;
+        const long long segs = std::max(1LL, (target + whole - 1) / whole);
+        ty = (int)std::min<long long>(my_max, std::max(16LL, (my_max + segs - 1) / segs));
+      }
+    }
+  }
+  std::vector<int2> work;
+  std::vector<int4> tiles, patches;
+  std::vector<InstDev> cl_inst;
+  for (int b = 0; b < n_instances; ++b) {
+    const InstDev& I = h->inst_h[b];
+    if (on_tiles[b]) {
+      h->n_tile_inst++;
+      for (int s = 0; s < I.N; ++s) {
+        for (int y0 = 0; y0 < I.my; y0 += ty)
+          for (int x0 = 0; x0 < I.mx; x0 += tx) tiles.push_back(make_int4(b, s, x0, y0));
+        for (int a = 0; a < I.nu; ++a) patches.push_back(make_int4(b, s, a, 0));
+      }
+    } else {
+      cl_inst.push_back(I);
+      for (int s = 0; s < I.N; ++s) work.push_back(make_int2(b, s));
+    }
+  }
+  h->n_work = (int)work.size();
+  h->n_tiles = (int)tiles.size();
+  h->n_patches = (int)patches.size();
+  if (h->n_tiles > 0) {
+    h->tile_x = tx;
+    h->tile_y = ty;
+    h->tile_threads = 32 * nmpc_dev::STRIP_WARPS;
+    h->tile_region = 32 * (ty + 2 * E);
+    h->tile_smem = nmpc_dev::STRIP_WARPS * ((sizeof(nmpc_dev::StripShared) + 15) & ~size_t(15));
+    const size_t P2 = (size_t)(2 * E + 1) * (2 * E + 1);
+    h->patch_smem = PATCH_WARPS * (((sizeof(nmpc_dev::PatchShared) + 15) & ~size_t(15)) +
+                                   8 * P2 * sizeof(double));
+    if (h->tile_smem > (size_t)max_optin || h->patch_smem > (size_t)max_optin) {
+      fprintf(stderr, "nmpc: tile shape needs %zu bytes of shared memory\n", h->tile_smem);
+      delete h;
+      return NMPC_ERR_UNSUPPORTED;
+    }
+  }
+  LaunchPlan P;
+  if (h->n_work > 0)
+    P = plan_launch(cl_inst.data(), (int)cl_inst.size(), h->n_work, o, h->mixed,
+                    std::max(1, h->num_sms), max_optin);
+  P.persistent = P.persistent && h->n_tiles == 0;
+  if (h->n_work > 0 && !P.smem_mode) {
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &per_sm, iter_kernel_of(h->mixed, GLOBAL_NC, false), P.threads, P.smem);
@@ -1056,6 +1255,9 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
   auto A = [&](cudaError_t e) { ok = ok && (e == cudaSuccess); };
   A(dev_alloc(&h->inst_d, n_instances));
   A(dev_alloc(&h->work_d, h->n_work));
+  A(dev_alloc(&h->tiles_d, h->n_tiles));
+  A(dev_alloc(&h->patches_d, h->n_patches));
+  A(dev_alloc(&h->v3_d, h->n_tiles > 0 ? h->n_u : 0));
   A(dev_alloc(&h->act_d, act_all.size()));
   A(dev_alloc(&h->x0_d, h->n_g));
   A(dev_alloc(&h->ref_d, h->n_g));
@@ -1078,7 +1280,7 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
   A(dev_alloc(&h->final_buf, n_instances));
   A(dev_alloc(&h->fin_inf, n_instances));
   A(dev_alloc(&h->fin_2, n_instances));
-  if (!h->smem_mode) {
+  if (h->n_work > 0 && !h->smem_mode) {
     h->scratch_stride = (long long)((work_bytes + 255) & ~size_t(255));
     A(cudaMalloc((void**)&h->scratch, (size_t)h->scratch_stride * h->grid));
   }
@@ -1090,7 +1292,13 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
   A(cudaMallocHost((void**)&h->h_resinf, n_instances * sizeof(unsigned long long)));
   if (ok) {
     A(cudaMemcpy(h->inst_d, h->inst_h.data(), n_instances * sizeof(InstDev), cudaMemcpyHostToDevice));
-    A(cudaMemcpy(h->work_d, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    if (!work.empty())
+      A(cudaMemcpy(h->work_d, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    if (!tiles.empty())
+      A(cudaMemcpy(h->tiles_d, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    if (!patches.empty())
+      A(cudaMemcpy(h->patches_d, patches.data(), patches.size() * sizeof(int4),
+                   cudaMemcpyHostToDevice));
     A(cudaMemcpy(h->act_d, act_all.data(), act_all.size() * sizeof(int), cudaMemcpyHostToDevice));
     A(cudaMemset(h->ictl, 0, 8 * sizeof(int)));
     A(cudaDeviceSynchronize());
@@ -1327,6 +1535,20 @@ int nmpc_sizes(const nmpc_handle* h, int64_t* out) {
 }
 
 int64_t nmpc_launch_count(const nmpc_handle* h) { return h ? h->launches : 0; }
+
+int nmpc_tile_plan(const nmpc_handle* h, int64_t* out) {
+  if (!h || !out) return NMPC_ERR_BAD_ARG;
+  const bool on = h->n_tiles > 0;
+  out[0] = h->n_tiles;
+  out[1] = on ? h->tile_x : 0;
+  out[2] = on ? h->tile_y : 0;
+  out[3] = on ? h->tile_threads : 0;
+  out[4] = on ? (int64_t)h->tile_smem : 0;
+  out[5] = on ? h->n_patches : 0;
+  out[6] = h->n_tile_inst;
+  out[7] = on ? h->tile_region : 0;
+  return NMPC_OK;
+}
 
 int nmpc_launch_plan(const nmpc_handle* h, int64_t* out) {
   if (!h || !out) return NMPC_ERR_BAD_ARG;

@@ -24,6 +24,7 @@
 #pragma once
 
 #include <cooperative_groups.h>
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <math_constants.h>
 #include <stdint.h>
@@ -116,6 +117,14 @@ struct IterArgs {
   // slab of scratch_stride bytes per CTA
   char* scratch;
   long long scratch_stride;
+  // tile path (k_tile): (instance, stage, first column, first row) per tile
+  const int4* tiles;
+  int n_tiles;
+  int tile_x, tile_y;  // own cells per tile
+  // k_patch: (instance, stage, actuator) per warp; v3 per control (float64)
+  const int4* patches;
+  int n_patches;
+  double* v3g;
 };
 
 struct Cl {
@@ -496,67 +505,101 @@ __device__ __forceinline__ void cp_async8(void* dst_smem, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
 }
 
-// Iteration k's decision for work item (b, s), taken by one thread from the
-// instance's residual history (iteration k - 1): skip (instance finished, or
-// k past max_iter) and whether the residual is evaluated in float64.  The CTA
-// of stage 0, cluster rank 0 records a finished instance (status, returned
-// iterate k - 1) and clears the residual slot of iteration k + 1.  Control
-// words are read around L1 (other CTAs write them within a persistent
-// launch).
-__device__ __noinline__ void control_decision(const IterArgs& A, int b, int s, int k, const Cl& cl,
-                                              int& skip_out, int& full_out) {
-  int skip = 0, fl = 1;
-  // every control word this decision reads, loaded at once
-  const int pslot = (k > 0) ? ((k - 1) % RES_SLOTS) * A.n_inst + b : 0;
+// Iteration k's decision for instance b, from its residual history
+// (iteration k - 1), with no side effects: skip (finished before, or k past
+// max_iter: `before`; or finished now: st != ST_RUNNING) and whether the
+// residual is evaluated in float64.  Control words are read around L1 (other
+// CTAs write them within a persistent launch).
+struct Decision {
+  int skip, full, before, st, pslot, ffrom;
+  double r;
+};
+
+__device__ __forceinline__ Decision decide(const IterArgs& A, int b, int k) {
+  Decision d{0, 1, 0, ST_RUNNING, (k > 0) ? ((k - 1) % RES_SLOTS) * A.n_inst + b : 0, 0, 0.0};
+  // every control word the decision reads, loaded at once
   const int status_b = __ldcg(A.status + b);
-  const int ffrom = __ldcg(A.full_from + b);
+  d.ffrom = __ldcg(A.full_from + b);
   const int f0 = __ldcg(A.full0 + b);
-  const unsigned long long r_bits = __ldcg(A.res_inf + pslot);
+  const unsigned long long r_bits = __ldcg(A.res_inf + d.pslot);
   const unsigned long long r0_bits = __ldcg(A.res_first + b);
-  const unsigned long long e_bits = __ldcg(A.res_err + pslot);
+  const unsigned long long e_bits = __ldcg(A.res_err + d.pslot);
   if (k > A.max_iter || status_b != ST_RUNNING) {
-    skip = 1;
-  } else {
-    int st = ST_RUNNING;
-    bool switch_now = false;
-    double r = 0.0;
-    if (k > 0) {
-      r = __longlong_as_double((long long)r_bits);
-      const double r0 = __longlong_as_double((long long)r0_bits);
-      const bool prev_full = (k - 1 >= ffrom) || (k == 1 && f0);
-      if (!(r <= 1.79e308) || r > A.div_limit * fmax(r0, 1e-300)) st = ST_DIVERGED;
-      else if (prev_full && r <= A.tol) st = ST_CONVERGED;
-      else if (!prev_full) {
-        // leave the split residual once it can no longer show that the
-        // float64 residual is above the threshold: r minus its rounding
-        // bound at or below max(tol, split_min)
-        const double e = __longlong_as_double((long long)e_bits);
-        if (r - e <= fmax(A.tol, A.split_min)) switch_now = true;
-      }
-    }
-    if (st != ST_RUNNING) {
-      skip = 1;
-      if (s == 0 && cl.rank == 0) {
-        A.status[b] = st;
-        A.iters[b] = k - 1;
-        A.final_buf[b] = (k - 1) & 1;
-        A.fin_inf[b] = r;
-        A.fin_2[b] = sqrt(__ldcg(A.res_sq + pslot));
-        atomicSub(A.n_active, 1);
-      }
-    } else {
-      fl = (A.full_all || k >= ffrom || switch_now || k == A.max_iter || (k == 0 && f0)) ? 1 : 0;
-      if (s == 0 && cl.rank == 0) {
-        if (fl && ffrom > k) A.full_from[b] = k;
-        const int nslot = ((k + 1) % RES_SLOTS) * A.n_inst + b;
-        A.res_inf[nslot] = 0ull;
-        A.res_err[nslot] = 0ull;
-        A.res_sq[nslot] = 0.0;
-      }
+    d.skip = 1;
+    d.before = 1;
+    return d;
+  }
+  bool switch_now = false;
+  if (k > 0) {
+    d.r = __longlong_as_double((long long)r_bits);
+    const double r0 = __longlong_as_double((long long)r0_bits);
+    const bool prev_full = (k - 1 >= d.ffrom) || (k == 1 && f0);
+    if (!(d.r <= 1.79e308) || d.r > A.div_limit * fmax(r0, 1e-300)) d.st = ST_DIVERGED;
+    else if (prev_full && d.r <= A.tol) d.st = ST_CONVERGED;
+    else if (!prev_full) {
+      // leave the split residual once it can no longer show that the float64
+      // residual is above the threshold: r minus its rounding bound at or
+      // below max(tol, split_min)
+      const double e = __longlong_as_double((long long)e_bits);
+      if (d.r - e <= fmax(A.tol, A.split_min)) switch_now = true;
     }
   }
-  skip_out = skip;
-  full_out = fl;
+  if (d.st != ST_RUNNING) {
+    d.skip = 1;
+  } else {
+    d.full = (A.full_all || k >= d.ffrom || switch_now || k == A.max_iter || (k == 0 && f0)) ? 1 : 0;
+  }
+  return d;
+}
+
+// decide() for work item (b, s), taken by one thread; the CTA of stage 0,
+// cluster rank 0 keeps the books: it records a finished instance (status,
+// returned iterate k - 1), the first float64-residual iteration, and clears
+// the residual slot of iteration k + 1.
+__device__ __noinline__ void control_decision(const IterArgs& A, int b, int s, int k, const Cl& cl,
+                                              int& skip_out, int& full_out) {
+  const Decision d = decide(A, b, k);
+  if (!d.before && s == 0 && cl.rank == 0) {
+    if (d.st != ST_RUNNING) {
+      A.status[b] = d.st;
+      A.iters[b] = k - 1;
+      A.final_buf[b] = (k - 1) & 1;
+      A.fin_inf[b] = d.r;
+      A.fin_2[b] = sqrt(__ldcg(A.res_sq + d.pslot));
+      atomicSub(A.n_active, 1);
+    } else {
+      if (d.full && d.ffrom > k) A.full_from[b] = k;
+      const int nslot = ((k + 1) % RES_SLOTS) * A.n_inst + b;
+      A.res_inf[nslot] = 0ull;
+      A.res_err[nslot] = 0ull;
+      A.res_sq[nslot] = 0.0;
+    }
+  }
+  skip_out = d.skip;
+  full_out = d.full;
+}
+
+// Rounding bound of the split residual over a set of cells (unit roundoff
+// u = 2^-24).  x and lambda are truncated to float32 (2u), Phi, Phi' and the
+// five-point sums are evaluated in float32 (a few u each): with X, Lm the
+// maxima of |x|, |lambda| over the cells and their stencil neighbours, every
+// O(h) term is off by at most 16 u h S, S = 4 (cx + cy) (Phi_max + Phi'_max
+// Lm) + b0 sum|u| + (q + qf [last stage]) (X + max|ref|); the float64
+// differences and the stage-gradient rows are truncated once (2u) and summed
+// (u).  Every cell's |K_split - K| is below the bound.  It is evaluated in
+// float32 (its own rounding, a few u relative, is far inside the factor 16)
+// and rounded up by 1%.  mags: X, Lm, max |float64 difference or K2|, max
+// |ref|; usum: sum over the stage's controls of |u| (float32).
+__device__ __forceinline__ double split_bound(const InstDev& I, bool last, const float* mags,
+                                              float usum) {
+  const float u32 = 5.9604645e-08f;
+  const float Xm = mags[0], Lm = mags[1], Dm = mags[2], Rm = mags[3];
+  const float ak0 = fabsf(I.fk0), ak1 = fabsf(I.fk1);
+  const float pmax = ak0 * (Xm + 0.5f * ak1 * Xm * Xm);
+  const float dpmax = ak0 * (1.0f + ak1 * Xm);
+  const float S = 2.0f * I.fdc * (pmax + dpmax * Lm) + fabsf(I.fb0) * usum +
+                  (I.fq + (last ? I.fhqf / I.fh : 0.0f)) * (Xm + Rm);
+  return f2d(1.01f * u32 * (3.0f * Dm + 16.0f * I.fh * S));
 }
 
 // Residual norms of a work item (max, sum of squares) and, for the split
@@ -948,26 +991,9 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
     const int slot = (k % RES_SLOTS) * A.n_inst + b;
     double e = 0.0;
     if (!full) {
-      // Rounding bound of the split residual on this slab (unit roundoff
-      // u = 2^-24).  x and lambda are truncated to float32 (2u), Phi, Phi' and
-      // the five-point sums are evaluated in float32 (a few u each): with
-      // X, Lm the maxima of |x|, |lambda| over the padded slab, every O(h) term
-      // is off by at most 16 u h S, S = 4 (cx + cy) (Phi_max + Phi'_max Lm) +
-      // b0 sum|u| + (q + qf [last stage]) (X + max|ref|); the float64
-      // differences and the stage-gradient rows are truncated once (2u) and
-      // summed (u).  Every cell's |K_split - K| is below the bound.  It is
-      // evaluated in float32 (its own rounding, a few u relative, is far
-      // inside the factor 16) and rounded up by 1%.
-      const float u32 = 5.9604645e-08f;
-      const float Xm = mags[0], Lm = mags[1], Dm = mags[2], Rm = mags[3];
       float usum = 0.0f;
       for (int a = 0; a < nu; ++a) usum += fabsf(d2f(sm.u[a]));
-      const float ak0 = fabsf(I.fk0), ak1 = fabsf(I.fk1);
-      const float pmax = ak0 * (Xm + 0.5f * ak1 * Xm * Xm);
-      const float dpmax = ak0 * (1.0f + ak1 * Xm);
-      const float S = 2.0f * I.fdc * (pmax + dpmax * Lm) + fabsf(I.fb0) * usum +
-                      (I.fq + (last ? I.fhqf / I.fh : 0.0f)) * (Xm + Rm);
-      e = f2d(1.01f * u32 * (3.0f * Dm + 16.0f * I.fh * S));
+      e = split_bound(I, last, mags, usum);
     }
     // each CTA's own atomics, issued before the barrier (they do not block)
     publish_residual(A, slot, b, k, sm.red_out[0], sm.red_out[1], e, full);
@@ -1721,5 +1747,7 @@ __global__ void k_set_weights(InstDev* inst, int n_inst, const double* w) {
   inst[b].qf = w[3 * b + 2];
   derive(inst[b]);
 }
+
+#include "nmpc_tile.cuh"
 
 }  // namespace nmpc_dev

@@ -1,0 +1,404 @@
+// Strip path of the upper-layer iteration for large 2D stages (included from
+// nmpc_kernels.cuh inside namespace nmpc_dev, after nmpc_tile.cuh).
+//
+// One warp of k_strip computes one strip of one (instance, stage) work item
+// of iteration k: 32 - 2E own columns (lane = region column, E = 2 n_lo - 1
+// on each side) and a run of own rows, from a region extended by E rows above
+// and below.  The warp walks down the region's rows; at step j, pass m works
+// on row j - m:
+//   pass 0       the stencil inputs Phi(x), lambda of row j;
+//   pass 1       K_i (eq. 9), Phi'(x), A_xx, 1/diag F_x and the first F_x
+//                sweep of row j - 1;
+//   pass 2..n_lo the F_x sweeps of P^{-1} (eq. 24), the last one also the
+//                first F_x^T sweep;
+//   pass n_lo+1..E the F_x^T sweeps; pass E updates the own cells of row
+//                j - E (S <- S + alpha Y, eq. 15, float64).
+// A pass reads its stencil neighbours from the previous pass: the rows above
+// and below from a three-row register window, the columns left and right by
+// warp shuffles.  Cells at level < m of pass m (lanes or rows near the
+// region's border) hold values no own cell depends on.  Cells outside the
+// grid carry 1/diag F_x = 0, so every sweep is zero there (the Dirichlet
+// ring).  Inputs arrive by asynchronous copies into a four-row ring in
+// shared memory, two rows ahead.  No block barrier and no shared-memory
+// stencil traffic.  The actuators' v3 come from k_patch (same iteration).
+
+constexpr int STRIP_WARPS = 4;  // warps (strips) per CTA
+constexpr int STRIP_RING = 4;   // rows in a warp's input ring
+constexpr int STRIP_AHEAD = 2;  // rows copied ahead
+
+// An actuator inside a strip's region: region row, lane, control index.
+struct StripAct {
+  int row, lane, a, pad;
+};
+
+// Shared memory of one strip warp: the input ring (STRIP_RING rows x SREC
+// fields x 32 lanes, float64) and the actuators in reach sorted by row.
+struct StripShared {
+  double ring[STRIP_RING * SREC * 32];
+  StripAct act[MAX_NU];
+  int n_act;
+};
+
+// A three-row window of a stencil field: w0 = row above, w1 = centre,
+// w2 = row below the consumer's row.
+template <typename V>
+struct Win {
+  V w0, w1, w2;
+  __device__ __forceinline__ void push(V v) {
+    w0 = w1;
+    w1 = w2;
+    w2 = v;
+  }
+  // centre's horizontal neighbours plus the vertical ones, weighted
+  __device__ __forceinline__ V nsum(V cx, V cy) const {
+    const V l = __shfl_up_sync(0xffffffffu, w1, 1), r = __shfl_down_sync(0xffffffffu, w1, 1);
+    return cx * (l + r) + cy * (w0 + w2);
+  }
+};
+
+// Shift register of per-row values: at step j, d[k] holds the value pass 1
+// formed k + 1 steps earlier (row j - 2 - k).
+template <typename V, int D>
+struct Shift {
+  V d[D > 0 ? D : 1];
+  __device__ __forceinline__ void push(V v) {
+    if constexpr (D > 0) {
+#pragma unroll
+      for (int k = D - 1; k > 0; --k) d[k] = d[k - 1];
+      d[0] = v;
+    }
+  }
+};
+
+template <typename T, int n_lo>
+__global__ void __launch_bounds__(STRIP_WARPS * 32) k_strip(IterArgs A, int MODE, int j_launch) {
+  constexpr int E = 2 * n_lo - 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  StripShared& ws = *reinterpret_cast<StripShared*>(
+      smem_raw + warp * ((sizeof(StripShared) + 15) & ~size_t(15)));
+  pdl_trigger();
+  const int k = (MODE == MODE_SOLVE) ? *(volatile int*)A.iter_k + j_launch : 0;
+  const int rd = (MODE == MODE_SOLVE) ? (k & 1) : 0;
+  pdl_wait();  // the previous iteration's state, residuals and control words; this one's v3
+  const int item = blockIdx.x * STRIP_WARPS + warp;
+  if (item >= A.n_tiles) return;  // warp-uniform; no block barriers in this kernel
+  const int4 it = A.tiles[item];
+  const int b = it.x, s = it.y, x0 = it.z, y0 = it.w;
+  const InstDev& I = A.inst[b];
+  const int nu = I.nu;
+  const bool last = (s == I.N - 1);
+  const long long so = I.s_off + (long long)s * I.ng;
+
+  bool resid_only, full;
+  if (MODE == MODE_ONESHOT) {
+    resid_only = (A.resid_only != 0);
+    full = resid_only || (A.full_all != 0);
+  } else {
+    int skip = 0, fl = 1;
+    if (lane == 0) {
+      Cl cl;
+      cl.C = 1;
+      cl.rank = (x0 == 0 && y0 == 0) ? 0 : 1;  // the stage's first strip keeps the books
+      control_decision(A, b, s, k, cl, skip, fl);
+    }
+    skip = __shfl_sync(0xffffffffu, skip, 0);
+    fl = __shfl_sync(0xffffffffu, fl, 0);
+    if (skip) return;
+    full = fl != 0;
+    resid_only = (k == A.max_iter);
+  }
+
+  // region: columns x0 - E + lane, rows y0 - E .. y0 + own_rows + E - 1
+  const int own_rows = min(A.tile_y, I.my - y0);
+  const int RH = own_rows + 2 * E;
+  const int gx = x0 - E + lane;
+  const bool gx_ok = gx >= 0 && gx < I.mx;
+  const bool own_lane = lane >= E && lane < 32 - E && gx_ok;
+  const int gy0 = y0 - E;
+
+  // actuators in reach, sorted by (row, lane, index): lane 0 builds the list
+  if (lane == 0) {
+    int n = 0;
+    for (int a = 0; a < nu; ++a) {
+      const int c = A.act[I.act_off + a];
+      const int rl = c % I.mx - (x0 - E), rr = c / I.mx - gy0;
+      if (rl >= 0 && rl < 32 && rr >= 0 && rr < RH) {
+        int p = n++;
+        while (p > 0 && (ws.act[p - 1].row > rr || (ws.act[p - 1].row == rr && ws.act[p - 1].lane > rl))) {
+          ws.act[p] = ws.act[p - 1];
+          --p;
+        }
+        ws.act[p] = StripAct{rr, rl, a, 0};
+      }
+    }
+    ws.n_act = n;
+  }
+  __syncwarp();
+  const int n_act = ws.n_act;
+  int na = 0;  // next actuator entry (rows increase along the strip)
+
+  // asynchronous copies of region row rj into its ring slot (zero outside the grid)
+  const double* Xg = A.xin[rd] + so;
+  const double* Lg = A.lin[rd] + so;
+  const double* XPg = (s == 0) ? A.x0 + I.g_off : A.xin[rd] + so - I.ng;
+  const double* LNg = A.lin[rd] + so + I.ng;
+  const double* RFg = A.ref + I.g_off;
+  auto slot = [&](int rj, int f) -> double* {
+    return &ws.ring[((rj & (STRIP_RING - 1)) * SREC + f) * 32 + lane];
+  };
+  auto fetch = [&](int rj) {
+    if (rj < RH) {
+      const int gy = gy0 + rj;
+      if (gx_ok && gy >= 0 && gy < I.my) {
+        const int c = gy * I.mx + gx;
+        cp_async8(slot(rj, R_X), Xg + c);
+        cp_async8(slot(rj, R_L), Lg + c);
+        cp_async8(slot(rj, R_XP), XPg + c);
+        if (!last) cp_async8(slot(rj, R_LN), LNg + c);
+        cp_async8(slot(rj, R_RF), RFg + c);
+      } else {
+        *slot(rj, R_X) = 0.0;
+        *slot(rj, R_L) = 0.0;
+        *slot(rj, R_XP) = 0.0;
+        *slot(rj, R_LN) = 0.0;
+        *slot(rj, R_RF) = 0.0;
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+  };
+#pragma unroll
+  for (int q = 0; q < STRIP_AHEAD; ++q) fetch(q);
+
+  const T th = pick<T>(I.h, I.fh), tdc = pick<T>(I.dcoef, I.fdc), tb0 = pick<T>(I.b0, I.fb0);
+  const T tcx = pick<T>(I.cx, I.fcx), tcy = pick<T>(I.cy, I.fcy);
+  const double alpha = A.alpha;
+  double* Xo = A.xout[rd ^ 1] + so;
+  double* Lo = A.lout[rd ^ 1] + so;
+  const double* Xin = Xg;
+  const double* Lin = Lg;
+
+  Norms nm{0.0f, 0.0f, make_float4(0.f, 0.f, 0.f, 0.f), 0.0, 0.0};
+  // pass 0 windows (float64 in the full residual, float32 in the split one)
+  Win<double> phd{0.0, 0.0, 0.0}, lad{0.0, 0.0, 0.0};
+  Win<float> phf{0.f, 0.f, 0.f}, laf{0.f, 0.f, 0.f}, xvf{0.f, 0.f, 0.f};
+  // sweep fields: pw[m] is the window of pass m + 1's output (m = 0 .. E - 2)
+  Win<T> pw[E > 1 ? E - 1 : 1];
+#pragma unroll
+  for (int m = 0; m < (E > 1 ? E - 1 : 1); ++m) pw[m] = Win<T>{T(0), T(0), T(0)};
+  // per-row values of pass 1 for the later passes
+  Shift<T, E - 1> sdp, srg;        // Phi', 1/diag F_x  (passes 2 .. E)
+  Shift<T, n_lo - 1> sk3, sax, sv1;  // K3, A_xx, v1     (passes 2 .. n_lo)
+  Shift<T, n_lo - 1> sv5, sw1;     // v5, w1 of pass n_lo (passes n_lo + 1 .. E)
+
+  const int steps = RH + E;
+  for (int j = 0; j < steps; ++j) {
+    fetch(j + STRIP_AHEAD);
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(STRIP_AHEAD));
+    // ---- pass 0: row j ----
+    {
+      const double x = *slot(j, R_X), l = *slot(j, R_L);
+      if (full) {
+        phd.push(I.k0 * (x + 0.5 * I.k1 * x * x));
+        lad.push(l);
+      } else {
+        const float xv = d2f(x), lf = d2f(l);
+        phf.push(I.fk0 * (xv + I.fk1h * xv * xv));
+        laf.push(lf);
+        xvf.push(xv);
+        if (j < RH) {
+          nm.mg.x = fmaxf(nm.mg.x, fabsf(xv));
+          nm.mg.y = fmaxf(nm.mg.y, fabsf(lf));
+        }
+      }
+    }
+    // ---- pass 1: row j - 1 ----
+    T K3 = T(0), ax = T(0), rg = T(0), dp = T(0), v1 = T(0);
+    {
+      const int rj = j - 1;
+      const int gy = gy0 + rj;
+      const bool in_grid = gx_ok && gy >= 0 && gy < I.my;
+      const bool own = own_lane && rj >= E && rj < RH - E && gy < I.my;
+      // sources of the cell: sum of u (b0 B u in K1) and of v3 (F_u v3)
+      double srcd = 0.0;
+      float srcf = 0.0f;
+      T inj = T(0);
+      while (na < n_act && ws.act[na].row < rj) ++na;  // entries of rows before the strip's start
+      while (na < n_act && ws.act[na].row == rj) {
+        const StripAct e = ws.act[na];
+        if (e.lane == lane) {
+          const double ua = A.uin[rd][I.u_off + (long long)s * nu + e.a];
+          srcd += ua;
+          srcf += d2f(ua);
+          inj += (T)A.v3g[I.u_off + (long long)s * nu + e.a];
+        }
+        ++na;
+      }
+      const double* rs = slot(rj, 0);
+      const double x = rs[R_X * 32], lam = rs[R_L * 32], xp = rs[R_XP * 32], rc = rs[R_RF * 32];
+      T K1;
+      if (full) {
+        const double ln = last ? I.hqf * (x - rc) : rs[R_LN * 32];
+        const double lphi = phd.nsum(I.cx, I.cy) - I.dcoef * phd.w1;
+        const double mu = lad.nsum(I.cx, I.cy) - I.dcoef * lad.w1;
+        const double dphi = I.k0 * (1.0 + I.k1 * x);
+        const double K1d = xp - x + I.h * (lphi + I.b0 * srcd);
+        const double K3d = ln - lam + I.h * (I.q * (x - rc) + dphi * mu);
+        if (own) {
+          nm.vmax = fmax(nm.vmax, fmax(abs_or_inf(K1d), abs_or_inf(K3d)));
+          nm.vsq += K1d * K1d + K3d * K3d;
+        }
+        K1 = to_T<T>(K1d);
+        K3 = to_T<T>(K3d);
+        dp = to_T<T>(dphi);
+        ax = to_T<T>(I.h * (I.q + I.k0 * I.k1 * mu) + (last ? I.hqf : 0.0));
+      } else {
+        const float hqff = last ? I.fhqf : 0.0f;
+        const float lphi = phf.nsum(I.fcx, I.fcy) - I.fdc * phf.w1;
+        const float mu = laf.nsum(I.fcx, I.fcy) - I.fdc * laf.w1;
+        const float xv = xvf.w1, rv = d2f(rc);
+        const float dphi = I.fk0 * (1.0f + I.fk1 * xv);
+        const float t1 = I.fh * (lphi + I.fb0 * srcf);
+        const float t3 = I.fh * (I.fq * (xv - rv) + dphi * mu);
+        const double d3 = last ? -lam : rs[R_LN * 32] - lam;
+        const float dx = d2f(xp - x), dl = d2f(d3);
+        const float K1f = dx + t1;
+        const float K3f = dl + t3 + hqff * (xv - rv);
+        const float K1v = own ? K1f : 0.0f, K3v = own ? K3f : 0.0f;
+        nm.mg.z = fmaxf(nm.mg.z, own ? fmaxf(fabsf(dx), fabsf(dl)) : 0.0f);
+        nm.mg.w = fmaxf(nm.mg.w, own ? fabsf(rv) : 0.0f);
+        nm.fmax = fmax_nan(nm.fmax, fmax_nan(fabsf(K1v), fabsf(K3v)));
+        nm.fsq += K1v * K1v + K3v * K3v;
+        K1 = (T)K1f;
+        K3 = (T)K3f;
+        dp = (T)dphi;
+        ax = (T)(I.fh * (I.fq + I.fk01 * mu) + hqff);
+      }
+      // 1/diag F_x, zero outside the grid (every sweep there stays zero)
+      rg = in_grid ? rcp_T(-T(1) - th * tdc * dp) : T(0);
+      v1 = (th * tb0 * inj - K1) * rg;  // first F_x sweep of F_x v5 = F_u v3 - K1
+    }
+    if (!resid_only) {
+      if constexpr (n_lo == 1) {
+        // pass 1 is the last pass: v5 = v1, v4 = w1
+        const int rj = j - 1;
+        const int gy = gy0 + rj;
+        if (own_lane && rj >= E && rj < RH - E && gy < I.my) {
+          const int c = gy * I.mx + gx;
+          const T w = (-K3 - ax * v1) * rg;
+          Xo[c] = fma(alpha, to_double(v1), Xin[c]);
+          Lo[c] = fma(alpha, to_double(w), Lin[c]);
+        }
+      } else {
+        // ---- pass 1's output: the first F_x sweep's field (or w1 for n_lo = 1) ----
+        pw[0].push(dp * v1);
+        // ---- passes 2 .. n_lo: F_x sweeps of row j - m ----
+        T v5n = T(0), w1n = T(0);
+#pragma unroll
+        for (int m = 2; m <= n_lo; ++m) {
+          // row j - m: pass 1 values of m - 1 steps ago
+          const T dpm = sdp.d[m - 2], rgm = srg.d[m - 2], v1m = sv1.d[m - 2];
+          const T off = th * pw[m - 2].nsum(tcx, tcy);
+          const T v = v1m - rgm * off;
+          if (m < n_lo) {
+            pw[m - 1].push(dpm * v);
+          } else {
+            const T w = (-sk3.d[m - 2] - sax.d[m - 2] * v) * rgm;
+            v5n = v;
+            w1n = w;
+            pw[m - 1].push(w);
+          }
+        }
+        // ---- passes n_lo + 1 .. E: F_x^T sweeps of row j - m ----
+#pragma unroll
+        for (int m = n_lo + 1; m <= E; ++m) {
+          const T dpm = sdp.d[m - 2], rgm = srg.d[m - 2];
+          const T w1m = sw1.d[m - n_lo - 1];
+          const T off = th * dpm * pw[m - 2].nsum(tcx, tcy);
+          const T v4 = w1m - rgm * off;
+          if (m < E) {
+            pw[m - 1].push(v4);
+          } else {
+            // ---- update of the own cells of row j - E ----
+            const int rj = j - E;
+            const int gy = gy0 + rj;
+            if (own_lane && rj >= E && rj < RH - E && gy < I.my) {
+              const int c = gy * I.mx + gx;
+              const T v5m = sv5.d[E - n_lo - 1];
+              Xo[c] = fma(alpha, to_double(v5m), Xin[c]);
+              Lo[c] = fma(alpha, to_double(v4), Lin[c]);
+            }
+          }
+        }
+        sv5.push(v5n);
+        sw1.push(w1n);
+      }
+    }
+    sdp.push(dp);
+    srg.push(rg);
+    sk3.push(K3);
+    sax.push(ax);
+    sv1.push(v1);
+  }
+  asm volatile("cp.async.wait_all;\n" ::);
+
+  // u rows (K2) and updates of the actuators whose cell is an own cell
+  for (int e = 0; e < n_act; ++e) {
+    const StripAct a = ws.act[e];
+    const int gy = gy0 + a.row;
+    if (a.lane != lane || !own_lane || a.row < E || a.row >= RH - E || gy >= I.my) continue;
+    const double ua = A.uin[rd][I.u_off + (long long)s * nu + a.a];
+    const double K2 = I.h * (I.r * ua + I.b0 * Lin[gy * I.mx + gx]);
+    if (full) {
+      nm.vmax = fmax(nm.vmax, abs_or_inf(K2));
+      nm.vsq += K2 * K2;
+    } else {
+      const float K2f = d2f(K2);
+      nm.fmax = fmax_nan(nm.fmax, fabsf(K2f));
+      nm.fsq += K2f * K2f;
+      nm.mg.z = fmaxf(nm.mg.z, fabsf(K2f));
+    }
+    if (!resid_only)
+      A.uout[rd ^ 1][I.u_off + (long long)s * nu + a.a] =
+          ua - alpha * (double)(T)A.v3g[I.u_off + (long long)s * nu + a.a];
+  }
+  // warp reduction of the norms, then one publication per strip
+  double rmax, rsq;
+  float mags[4];
+  if (full) {
+    double vm = nm.vmax, vs = nm.vsq;
+    for (int o = 16; o > 0; o >>= 1) {
+      vm = dmax_nan(vm, __shfl_xor_sync(0xffffffffu, vm, o));
+      vs += __shfl_xor_sync(0xffffffffu, vs, o);
+    }
+    rmax = vm;
+    rsq = vs;
+  } else {
+    float fm = nm.fmax, fs = nm.fsq;
+    float4 mg = nm.mg;
+    for (int o = 16; o > 0; o >>= 1) {
+      fm = fmax_nan(fm, __shfl_xor_sync(0xffffffffu, fm, o));
+      fs += __shfl_xor_sync(0xffffffffu, fs, o);
+      mg.x = fmaxf(mg.x, __shfl_xor_sync(0xffffffffu, mg.x, o));
+      mg.y = fmaxf(mg.y, __shfl_xor_sync(0xffffffffu, mg.y, o));
+      mg.z = fmaxf(mg.z, __shfl_xor_sync(0xffffffffu, mg.z, o));
+      mg.w = fmaxf(mg.w, __shfl_xor_sync(0xffffffffu, mg.w, o));
+    }
+    rmax = f2d(fm);
+    rsq = f2d(fs);
+    mags[0] = mg.x;
+    mags[1] = mg.y;
+    mags[2] = mg.z;
+    mags[3] = mg.w;
+  }
+  if (lane == 0) {
+    const int slot_k = (k % RES_SLOTS) * A.n_inst + b;
+    double e = 0.0;
+    if (!full) {
+      float usum = 0.0f;
+      for (int a = 0; a < nu; ++a) usum += fabsf(d2f(A.uin[rd][I.u_off + (long long)s * nu + a]));
+      e = split_bound(I, last, mags, usum);
+    }
+    publish_residual(A, slot_k, b, k, rmax, rsq, e, full);
+  }
+}

@@ -60,6 +60,7 @@ def closedloop(n: int, steps: int, grid: int, horizon: int, n_sub: int, check: i
     import torch
     insts = wl.heat2d_large_batch(n=n, m=grid, horizon=horizon)
     s = G.Solver(insts, tol=1e-6, precision=G.NMPC_MIXED, max_iter=4000, **opts)
+    tile_plan = G.nmpc_tile_plan(s.h)
     w = s.x0.clone()
     nu_tot = sum(len(i.act) for i in insts)
     u_hist = torch.zeros(steps * nu_tot, dtype=torch.float64, device="cuda")
@@ -77,7 +78,8 @@ def closedloop(n: int, steps: int, grid: int, horizon: int, n_sub: int, check: i
            "iters_first_step_mean": float(iters[0].mean()),
            "iters_later_mean": float(iters[1:].mean()) if steps > 1 else None,
            "res_max": float(res.max()), "launches": launches,
-           "hbm_gbs_algorithmic": BYTES_PER_CELL_STAGE * cells * iter_launches / dt / 1e9}
+           "hbm_gbs_algorithmic": BYTES_PER_CELL_STAGE * cells * iter_launches / dt / 1e9,
+           "tile_plan": tile_plan}
     if check:
         # one more solve from the final plant state, then its float64 residual
         rc2, st = G.nmpc_solve(s.h, w, s.ref, s.u, n, init=G.NMPC_INIT_SHIFT)
@@ -143,6 +145,8 @@ def main():
     ap.add_argument("--check", type=int, default=1)
     ap.add_argument("--cluster", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--tiled", type=int, default=0)
+    ap.add_argument("--tile-rows", type=int, default=0)
     ap.add_argument("--n-train", type=int, default=64)
     ap.add_argument("--train-steps", type=int, default=12)
     ap.add_argument("--fit-steps", type=int, default=2000)
@@ -158,7 +162,8 @@ def main():
                                             a.horizon, a.n_sub, a.fit_steps)), flush=True)
     else:
         res = closedloop(a.n or 64, a.steps, a.grid, a.horizon, a.n_sub, a.check,
-                         cluster=a.cluster, threads=a.threads)
+                         cluster=a.cluster, threads=a.threads, tiled=a.tiled,
+                         tile_rows=a.tile_rows)
         res.update({"cluster": a.cluster, "threads": a.threads})
         print(json.dumps(res), flush=True)
 

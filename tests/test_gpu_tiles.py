@@ -1,0 +1,217 @@
+"""Strip path (k_patch + k_strip) against the FP64 oracle.
+
+The strip kernel computes each strip of 32 - 2E own columns from a region
+extended by E = 2 n_lo - 1 cells (one warp walking down the rows with every
+pass pipelined), and k_patch the actuators' controls v3 from patches around
+them, so the path evaluates the same formulas as the oracle in a different
+order: FP64 iterates agree to a few ulps of the largest term (relative
+1e-10), the mixed path's update Delta s to float32 accuracy (relative 1e-4 of
+|Delta s|).  The cases put actuators on strip corners and edges, use ragged
+strips (grids that are not multiples of the strip), and mix strip-path
+instances with a 1D instance on the cluster path in one handle.
+"""
+import numpy as np
+import pytest
+
+from oracle import nmpc as O
+from paper_2004_02484_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2004_02484_gb300 import build as b
+    b.build()
+    from paper_2004_02484_gb300 import nmpc as G
+    import torch
+    torch.cuda.set_device(0)
+    return G
+
+
+def _t(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def _with_act(inst, rows_cols):
+    """Actuators at explicit (row, column) cells."""
+    inst.act = np.asarray([r * inst.mx + c for r, c in rows_cols], dtype=np.int64)
+    return inst
+
+
+def _batch(far=True):
+    """70x20 (strips of 26 columns for n_lo = 2: 26, 26, 18; rows of 8, 8, 4
+    with tile_rows 8), 30x26 (a full and a ragged strip), and a 1D instance
+    (cluster path).  With `far` the 2D actuators are more than 4 cells apart
+    (Manhattan)."""
+    a = wl.heat2d(70, 20, 4, 3, 2, seed=91)
+    cells = [(7, 63), (10, 66), (0, 0), (19, 69), (12, 30), (8, 5)] if far else \
+        [(7, 63), (8, 64), (0, 0), (19, 69), (12, 30), (12, 31)]
+    a = _with_act(a, cells)
+    b = _with_act(wl.heat2d(30, 26, 3, 2, 2, seed=92), [(8, 8), (8, 21), (17, 0), (25, 29)])
+    c = wl.heat1d(40, 5, 2, 0.02, seed=93)
+    return [a, b, c]
+
+
+def _rand_state(insts, seed, sx=0.05, su=0.5, sl=1e-4):
+    rng = np.random.default_rng(seed)
+    Xs, Us, Ls = [], [], []
+    for inst in insts:
+        X, U, L = O.Problem(inst).cold_start()
+        Xs.append(X + sx * rng.standard_normal(X.shape))
+        Us.append(U + su * rng.standard_normal(U.shape))
+        Ls.append(L + sl * rng.standard_normal(L.shape))
+    pk = lambda A: np.concatenate([a.reshape(-1) for a in A])
+    return (pk(Xs), pk(Us), pk(Ls)), (Xs, Us, Ls)
+
+
+def _iterate(G, insts, state, n_iter, **opts):
+    import torch
+    h = G.nmpc_setup(insts, **opts)
+    plan = G.nmpc_tile_plan(h)
+    x0 = _t(G.pack_fields(insts, "x0"))
+    ref = _t(G.pack_fields(insts, "ref"))
+    xi, ui, li = (_t(a) for a in state)
+    xo, uo, lo = torch.empty_like(xi), torch.empty_like(ui), torch.empty_like(li)
+    res = G.nmpc_iterate(h, x0, ref, xi, ui, li, xo, uo, lo, n_iter, len(insts))
+    torch.cuda.synchronize()
+    G.nmpc_destroy(h)
+    return (xo.cpu().numpy(), uo.cpu().numpy(), lo.cpu().numpy()), res, plan
+
+
+def _oracle(insts, lists, n_iter, **kw):
+    out, norms = [], []
+    for b, inst in enumerate(insts):
+        p = O.Problem(inst)
+        X, U, L = lists[0][b], lists[1][b], lists[2][b]
+        nm = None
+        for _ in range(n_iter):
+            X, U, L, nm = O.jacobi_iteration(p, X, U, L, **kw)
+        out.append((X.reshape(p.N, -1), U, L.reshape(p.N, -1)))
+        norms.append(nm)
+    return out, norms
+
+
+def _split(G, insts, x, u, lam):
+    return (G.split_stages(insts, x, "ng"), G.split_stages(insts, u, "nu"),
+            G.split_stages(insts, lam, "ng"))
+
+
+@pytest.mark.parametrize("n_lo,n_u_it", [(1, 1), (2, 1), (2, 2), (3, 1), (3, 3), (4, 1), (1, 3)])
+def test_tile_iterates_fp64_match_oracle(G, n_lo, n_u_it):
+    insts = _batch(far=True)
+    state, lists = _rand_state(insts, 94)
+    gpu, res, plan = _iterate(G, insts, state, 2, precision=G.NMPC_FP64, tiled=1, tile_rows=8,
+                              n_lo=n_lo, n_u_it=n_u_it)
+    tx = 32 - 2 * (2 * n_lo - 1)
+    assert plan["instances"] == 2 and plan["tile_x"] == tx and plan["tile_y"] == 8
+    assert plan["tiles"] == 4 * -(-70 // tx) * 3 + 3 * -(-30 // tx) * 4
+    ora, norms = _oracle(insts, lists, 2, n_lo=n_lo, n_u_it=n_u_it)
+    gx, gu, gl = _split(G, insts, *gpu)
+    for b in range(len(insts)):
+        for g, o in zip((gx[b], gu[b], gl[b]), ora[b]):
+            err = np.abs(g - o).max() / max(np.abs(o).max(), 1e-300)
+            assert err <= 1e-10, (b, err)
+        assert abs(res[b, 0] - norms[b][0]) <= 1e-11 * norms[b][0]
+        assert abs(res[b, 1] - norms[b][1]) <= 1e-9 * norms[b][1]
+
+
+def test_tile_actuators_close_together_with_one_u_iteration(G):
+    """Neighbouring and adjacent actuators are fine for n_u_it = 1 (each
+    control starts from zero); with n_u_it = 2 the instance goes to the
+    cluster path and still matches."""
+    insts = _batch(far=False)
+    state, lists = _rand_state(insts, 95)
+    for n_u_it, on_tiles in ((1, 2), (2, 1)):
+        gpu, _, plan = _iterate(G, insts, state, 2, precision=G.NMPC_FP64, tiled=1, tile_rows=8,
+                                n_u_it=n_u_it)
+        assert plan["instances"] == on_tiles
+        ora, _ = _oracle(insts, lists, 2, n_u_it=n_u_it)
+        gx, gu, gl = _split(G, insts, *gpu)
+        for b in range(len(insts)):
+            for g, o in zip((gx[b], gu[b], gl[b]), ora[b]):
+                err = np.abs(g - o).max() / max(np.abs(o).max(), 1e-300)
+                assert err <= 1e-10, (n_u_it, b, err)
+
+
+@pytest.mark.parametrize("tile_rows", [3, 8, 16])
+def test_tile_iterate_mixed_matches_oracle(G, tile_rows):
+    """Float32 lower layer with the split residual: the update Delta s agrees
+    with the oracle's to 1e-4 of its size, the split residual norm to 1e-5."""
+    insts = _batch(far=True)
+    state, lists = _rand_state(insts, 96)
+    gpu, res, plan = _iterate(G, insts, state, 1, precision=G.NMPC_MIXED, tiled=1,
+                              tile_rows=tile_rows)
+    assert plan["instances"] == 2
+    ora, norms = _oracle(insts, lists, 1)
+    gx, gu, gl = _split(G, insts, *gpu)
+    for b in range(len(insts)):
+        X, U, L = ora[b]
+        for g, o, i in ((gx[b], X, lists[0][b]), (gl[b], L, lists[2][b]), (gu[b], U, lists[1][b])):
+            i = i.reshape(o.shape)
+            d_or = o - i
+            err = np.abs((g - i) - d_or).max() / max(np.abs(d_or).max(), 1e-300)
+            assert err <= 1e-4, (b, err)
+        assert abs(res[b, 0] - norms[b][0]) <= 1e-5 * norms[b][0]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_tile_solve_equals_cluster_solve(G, precision):
+    """Solves to a tolerance on the tile path and on the cluster path: same
+    iteration counts in FP64 and the same root (controls to 1e-9 relative);
+    in mixed precision both stop on a float64 residual <= tol."""
+    import torch
+    insts = _batch(far=True)
+    tol = 1e-8 if precision == 0 else 1e-6
+    out = {}
+    for tiled in (1, 2):
+        s = G.Solver(insts, tol=tol, precision=precision, max_iter=8000, tiled=tiled, tile_rows=8)
+        rc, st = s.solve()
+        torch.cuda.synchronize()
+        assert rc == G.NMPC_OK
+        x, u, lam = s.state()
+        r = G.nmpc_residual(s.h, s.x0, s.ref, x, u, lam, len(insts))
+        out[tiled] = ([st[b].iters for b in range(3)], u.cpu().numpy(), r[:, 0])
+        s.close()
+    it_t, u_t, r_t = out[1]
+    it_c, u_c, r_c = out[2]
+    assert np.all(r_t <= tol) and np.all(r_c <= tol)
+    if precision == 0:
+        assert it_t == it_c
+        assert np.abs(u_t - u_c).max() <= 1e-9 * np.abs(u_c).max()
+    else:
+        assert np.abs(u_t - u_c).max() <= 1e-3 * np.abs(u_c).max()
+
+
+def test_tile_residual_entry_point_matches_oracle(G):
+    import torch
+    insts = _batch(far=True)
+    state, lists = _rand_state(insts, 97)
+    h = G.nmpc_setup(insts, precision=G.NMPC_MIXED, tiled=1, tile_rows=8)
+    x0 = _t(G.pack_fields(insts, "x0"))
+    ref = _t(G.pack_fields(insts, "ref"))
+    r = G.nmpc_residual(h, x0, ref, *(_t(a) for a in state), len(insts))
+    torch.cuda.synchronize()
+    G.nmpc_destroy(h)
+    for b, inst in enumerate(insts):
+        p = O.Problem(inst)
+        K = O.kkt(p, lists[0][b].reshape((p.N,) + p.shape), lists[1][b],
+                  lists[2][b].reshape((p.N,) + p.shape))
+        inf, two = O.kkt_norms(*K)
+        assert abs(r[b, 0] - inf) <= 1e-12 * inf
+        assert abs(r[b, 1] - two) <= 1e-10 * two
+
+
+def test_auto_routes_large_stages_to_tiles(G):
+    """tiled = 0: a 256x256 stage goes to the tile path, a 64x64 stage and a
+    1D instance stay on the cluster path."""
+    insts = [wl.heat2d(256, 256, 2, 4, 4, seed=98), wl.heat2d(64, 64, 2, 4, 2, seed=99),
+             wl.heat1d(50, 3, 1, 0.01, seed=100)]
+    h = G.nmpc_setup(insts, precision=G.NMPC_MIXED)
+    plan, lp = G.nmpc_tile_plan(h), G.nmpc_launch_plan(h)
+    G.nmpc_destroy(h)
+    ty = plan["tile_y"]
+    assert plan["instances"] == 1 and plan["tile_x"] == 26 and 16 <= ty <= 256
+    assert plan["tiles"] == 2 * -(-256 // 26) * -(-256 // ty)
+    assert lp["work_items"] == 2 + 3
