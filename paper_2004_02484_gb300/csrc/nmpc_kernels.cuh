@@ -505,6 +505,14 @@ __device__ __forceinline__ void cp_async8(void* dst_smem, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
 }
 
+// cp_async8 that writes zeros instead when `valid` is false (source size 0:
+// nothing is read; src must still be a valid address)
+__device__ __forceinline__ void cp_async8_zfill(void* dst_smem, const void* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src),
+               "r"(valid ? 8 : 0));
+}
+
 // Iteration k's decision for instance b, from its residual history
 // (iteration k - 1), with no side effects: skip (finished before, or k past
 // max_iter: `before`; or finished now: st != ST_RUNNING) and whether the

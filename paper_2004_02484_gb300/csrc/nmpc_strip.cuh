@@ -70,45 +70,18 @@ struct Shift {
   }
 };
 
-template <typename T, int n_lo>
-__global__ void __launch_bounds__(STRIP_WARPS * 32) k_strip(IterArgs A, int MODE, int j_launch) {
+// The strip of work item (b, s, x0, y0) for one residual form (FULL: the
+// float64 residual; else the split one): a separate instantiation per form,
+// so neither form's arithmetic is issued in the other's iterations.
+template <typename T, int n_lo, bool FULL>
+__device__ __forceinline__ void strip_body(const IterArgs& A, StripShared& ws, int lane, int b,
+                                           int s, int k, int rd, int x0, int y0, bool resid_only) {
   constexpr int E = 2 * n_lo - 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  StripShared& ws = *reinterpret_cast<StripShared*>(
-      smem_raw + warp * ((sizeof(StripShared) + 15) & ~size_t(15)));
-  pdl_trigger();
-  const int k = (MODE == MODE_SOLVE) ? *(volatile int*)A.iter_k + j_launch : 0;
-  const int rd = (MODE == MODE_SOLVE) ? (k & 1) : 0;
-  pdl_wait();  // the previous iteration's state, residuals and control words; this one's v3
-  const int item = blockIdx.x * STRIP_WARPS + warp;
-  if (item >= A.n_tiles) return;  // warp-uniform; no block barriers in this kernel
-  const int4 it = A.tiles[item];
-  const int b = it.x, s = it.y, x0 = it.z, y0 = it.w;
+  constexpr bool full = FULL;
   const InstDev& I = A.inst[b];
   const int nu = I.nu;
   const bool last = (s == I.N - 1);
   const long long so = I.s_off + (long long)s * I.ng;
-
-  bool resid_only, full;
-  if (MODE == MODE_ONESHOT) {
-    resid_only = (A.resid_only != 0);
-    full = resid_only || (A.full_all != 0);
-  } else {
-    int skip = 0, fl = 1;
-    if (lane == 0) {
-      Cl cl;
-      cl.C = 1;
-      cl.rank = (x0 == 0 && y0 == 0) ? 0 : 1;  // the stage's first strip keeps the books
-      control_decision(A, b, s, k, cl, skip, fl);
-    }
-    skip = __shfl_sync(0xffffffffu, skip, 0);
-    fl = __shfl_sync(0xffffffffu, fl, 0);
-    if (skip) return;
-    full = fl != 0;
-    resid_only = (k == A.max_iter);
-  }
-
   // region: columns x0 - E + lane, rows y0 - E .. y0 + own_rows + E - 1
   const int own_rows = min(A.tile_y, I.my - y0);
   const int RH = own_rows + 2 * E;
@@ -144,27 +117,25 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) k_strip(IterArgs A, int MODE
   const double* XPg = (s == 0) ? A.x0 + I.g_off : A.xin[rd] + so - I.ng;
   const double* LNg = A.lin[rd] + so + I.ng;
   const double* RFg = A.ref + I.g_off;
+  double* ring = ws.ring + lane;
   auto slot = [&](int rj, int f) -> double* {
-    return &ws.ring[((rj & (STRIP_RING - 1)) * SREC + f) * 32 + lane];
+    return ring + ((rj & (STRIP_RING - 1)) * SREC + f) * 32;
   };
+  // row rj's five inputs; cells outside the grid and rows past the region
+  // are zero-filled by the copies themselves (source size 0, from a clamped
+  // address inside the grid)
+  const int gxc = min(max(gx, 0), I.mx - 1);
+  const int mx = I.mx, my = I.my;
   auto fetch = [&](int rj) {
-    if (rj < RH) {
-      const int gy = gy0 + rj;
-      if (gx_ok && gy >= 0 && gy < I.my) {
-        const int c = gy * I.mx + gx;
-        cp_async8(slot(rj, R_X), Xg + c);
-        cp_async8(slot(rj, R_L), Lg + c);
-        cp_async8(slot(rj, R_XP), XPg + c);
-        if (!last) cp_async8(slot(rj, R_LN), LNg + c);
-        cp_async8(slot(rj, R_RF), RFg + c);
-      } else {
-        *slot(rj, R_X) = 0.0;
-        *slot(rj, R_L) = 0.0;
-        *slot(rj, R_XP) = 0.0;
-        *slot(rj, R_LN) = 0.0;
-        *slot(rj, R_RF) = 0.0;
-      }
-    }
+    const int gy = gy0 + rj;
+    const bool ok = gx_ok && gy >= 0 && gy < my && rj < RH;
+    const int c = min(max(gy, 0), my - 1) * mx + gxc;
+    double* d = slot(rj, 0);
+    cp_async8_zfill(d + R_X * 32, Xg + c, ok);
+    cp_async8_zfill(d + R_L * 32, Lg + c, ok);
+    cp_async8_zfill(d + R_XP * 32, XPg + c, ok);
+    cp_async8_zfill(d + R_LN * 32, (last ? Lg : LNg) + c, ok && !last);
+    cp_async8_zfill(d + R_RF * 32, RFg + c, ok);
     asm volatile("cp.async.commit_group;\n" ::);
   };
 #pragma unroll
@@ -173,10 +144,19 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) k_strip(IterArgs A, int MODE
   const T th = pick<T>(I.h, I.fh), tdc = pick<T>(I.dcoef, I.fdc), tb0 = pick<T>(I.b0, I.fb0);
   const T tcx = pick<T>(I.cx, I.fcx), tcy = pick<T>(I.cy, I.fcy);
   const double alpha = A.alpha;
-  double* Xo = A.xout[rd ^ 1] + so;
-  double* Lo = A.lout[rd ^ 1] + so;
+  double* __restrict__ Xo = A.xout[rd ^ 1] + so;
+  double* __restrict__ Lo = A.lout[rd ^ 1] + so;
   const double* Xin = Xg;
   const double* Lin = Lg;
+  // the instance's constants in registers (the loop's stores could alias the
+  // descriptor table as far as the compiler knows)
+  const double cxd = I.cx, cyd = I.cy, dcd = I.dcoef, hd = I.h, k0d = I.k0, k1d = I.k1;
+  const double qd = I.q, b0d = I.b0, hqfd = I.hqf;
+  const float fcx = I.fcx, fcy = I.fcy, fdc = I.fdc, fh = I.fh, fk0 = I.fk0, fk1 = I.fk1;
+  const float fk1h = I.fk1h, fq = I.fq, fb0 = I.fb0, fk01 = I.fk01;
+  const float hqff = last ? I.fhqf : 0.0f;
+  const double* uin_s = A.uin[rd] + I.u_off + (long long)s * nu;
+  const double* v3_s = A.v3g + I.u_off + (long long)s * nu;
 
   Norms nm{0.0f, 0.0f, make_float4(0.f, 0.f, 0.f, 0.f), 0.0, 0.0};
   // pass 0 windows (float64 in the full residual, float32 in the split one)
@@ -198,12 +178,12 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) k_strip(IterArgs A, int MODE
     // ---- pass 0: row j ----
     {
       const double x = *slot(j, R_X), l = *slot(j, R_L);
-      if (full) {
-        phd.push(I.k0 * (x + 0.5 * I.k1 * x * x));
+      if constexpr (full) {
+        phd.push(k0d * (x + 0.5 * k1d * x * x));
         lad.push(l);
       } else {
         const float xv = d2f(x), lf = d2f(l);
-        phf.push(I.fk0 * (xv + I.fk1h * xv * xv));
+        phf.push(fk0 * (xv + fk1h * xv * xv));
         laf.push(lf);
         xvf.push(xv);
         if (j < RH) {
@@ -217,8 +197,8 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) k_strip(IterArgs A, int MODE
     {
       const int rj = j - 1;
       const int gy = gy0 + rj;
-      const bool in_grid = gx_ok && gy >= 0 && gy < I.my;
-      const bool own = own_lane && rj >= E && rj < RH - E && gy < I.my;
+      const bool in_grid = gx_ok && gy >= 0 && gy < my;
+      const bool own = own_lane && rj >= E && rj < RH - E && gy < my;
       // sources of the cell: sum of u (b0 B u in K1) and of v3 (F_u v3)
       double srcd = 0.0;
       float srcf = 0.0f;
@@ -227,23 +207,23 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) k_strip(IterArgs A, int MODE
       while (na < n_act && ws.act[na].row == rj) {
         const StripAct e = ws.act[na];
         if (e.lane == lane) {
-          const double ua = A.uin[rd][I.u_off + (long long)s * nu + e.a];
-          srcd += ua;
-          srcf += d2f(ua);
-          inj += (T)A.v3g[I.u_off + (long long)s * nu + e.a];
+          const double ua = uin_s[e.a];
+          if constexpr (full) srcd += ua;
+          else srcf += d2f(ua);
+          inj += (T)v3_s[e.a];
         }
         ++na;
       }
       const double* rs = slot(rj, 0);
       const double x = rs[R_X * 32], lam = rs[R_L * 32], xp = rs[R_XP * 32], rc = rs[R_RF * 32];
       T K1;
-      if (full) {
-        const double ln = last ? I.hqf * (x - rc) : rs[R_LN * 32];
-        const double lphi = phd.nsum(I.cx, I.cy) - I.dcoef * phd.w1;
-        const double mu = lad.nsum(I.cx, I.cy) - I.dcoef * lad.w1;
-        const double dphi = I.k0 * (1.0 + I.k1 * x);
-        const double K1d = xp - x + I.h * (lphi + I.b0 * srcd);
-        const double K3d = ln - lam + I.h * (I.q * (x - rc) + dphi * mu);
+      if constexpr (full) {
+        const double ln = last ? hqfd * (x - rc) : rs[R_LN * 32];
+        const double lphi = phd.nsum(cxd, cyd) - dcd * phd.w1;
+        const double mu = lad.nsum(cxd, cyd) - dcd * lad.w1;
+        const double dphi = k0d * (1.0 + k1d * x);
+        const double K1d = xp - x + hd * (lphi + b0d * srcd);
+        const double K3d = ln - lam + hd * (qd * (x - rc) + dphi * mu);
         if (own) {
           nm.vmax = fmax(nm.vmax, fmax(abs_or_inf(K1d), abs_or_inf(K3d)));
           nm.vsq += K1d * K1d + K3d * K3d;
@@ -251,15 +231,14 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) k_strip(IterArgs A, int MODE
         K1 = to_T<T>(K1d);
         K3 = to_T<T>(K3d);
         dp = to_T<T>(dphi);
-        ax = to_T<T>(I.h * (I.q + I.k0 * I.k1 * mu) + (last ? I.hqf : 0.0));
+        ax = to_T<T>(hd * (qd + k0d * k1d * mu) + (last ? hqfd : 0.0));
       } else {
-        const float hqff = last ? I.fhqf : 0.0f;
-        const float lphi = phf.nsum(I.fcx, I.fcy) - I.fdc * phf.w1;
-        const float mu = laf.nsum(I.fcx, I.fcy) - I.fdc * laf.w1;
+        const float lphi = phf.nsum(fcx, fcy) - fdc * phf.w1;
+        const float mu = laf.nsum(fcx, fcy) - fdc * laf.w1;
         const float xv = xvf.w1, rv = d2f(rc);
-        const float dphi = I.fk0 * (1.0f + I.fk1 * xv);
-        const float t1 = I.fh * (lphi + I.fb0 * srcf);
-        const float t3 = I.fh * (I.fq * (xv - rv) + dphi * mu);
+        const float dphi = fk0 * (1.0f + fk1 * xv);
+        const float t1 = fh * (lphi + fb0 * srcf);
+        const float t3 = fh * (fq * (xv - rv) + dphi * mu);
         const double d3 = last ? -lam : rs[R_LN * 32] - lam;
         const float dx = d2f(xp - x), dl = d2f(d3);
         const float K1f = dx + t1;
@@ -272,7 +251,7 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) k_strip(IterArgs A, int MODE
         K1 = (T)K1f;
         K3 = (T)K3f;
         dp = (T)dphi;
-        ax = (T)(I.fh * (I.fq + I.fk01 * mu) + hqff);
+        ax = (T)(fh * (fq + fk01 * mu) + hqff);
       }
       // 1/diag F_x, zero outside the grid (every sweep there stays zero)
       rg = in_grid ? rcp_T(-T(1) - th * tdc * dp) : T(0);
@@ -283,8 +262,8 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) k_strip(IterArgs A, int MODE
         // pass 1 is the last pass: v5 = v1, v4 = w1
         const int rj = j - 1;
         const int gy = gy0 + rj;
-        if (own_lane && rj >= E && rj < RH - E && gy < I.my) {
-          const int c = gy * I.mx + gx;
+        if (own_lane && rj >= E && rj < RH - E && gy < my) {
+          const int c = gy * mx + gx;
           const T w = (-K3 - ax * v1) * rg;
           Xo[c] = fma(alpha, to_double(v1), Xin[c]);
           Lo[c] = fma(alpha, to_double(w), Lin[c]);
@@ -322,8 +301,8 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) k_strip(IterArgs A, int MODE
             // ---- update of the own cells of row j - E ----
             const int rj = j - E;
             const int gy = gy0 + rj;
-            if (own_lane && rj >= E && rj < RH - E && gy < I.my) {
-              const int c = gy * I.mx + gx;
+            if (own_lane && rj >= E && rj < RH - E && gy < my) {
+              const int c = gy * mx + gx;
               const T v5m = sv5.d[E - n_lo - 1];
               Xo[c] = fma(alpha, to_double(v5m), Xin[c]);
               Lo[c] = fma(alpha, to_double(v4), Lin[c]);
@@ -349,7 +328,7 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) k_strip(IterArgs A, int MODE
     if (a.lane != lane || !own_lane || a.row < E || a.row >= RH - E || gy >= I.my) continue;
     const double ua = A.uin[rd][I.u_off + (long long)s * nu + a.a];
     const double K2 = I.h * (I.r * ua + I.b0 * Lin[gy * I.mx + gx]);
-    if (full) {
+    if constexpr (full) {
       nm.vmax = fmax(nm.vmax, abs_or_inf(K2));
       nm.vsq += K2 * K2;
     } else {
@@ -365,7 +344,7 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) k_strip(IterArgs A, int MODE
   // warp reduction of the norms, then one publication per strip
   double rmax, rsq;
   float mags[4];
-  if (full) {
+  if constexpr (full) {
     double vm = nm.vmax, vs = nm.vsq;
     for (int o = 16; o > 0; o >>= 1) {
       vm = dmax_nan(vm, __shfl_xor_sync(0xffffffffu, vm, o));
@@ -394,11 +373,53 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32) k_strip(IterArgs A, int MODE
   if (lane == 0) {
     const int slot_k = (k % RES_SLOTS) * A.n_inst + b;
     double e = 0.0;
-    if (!full) {
+    if constexpr (!full) {
       float usum = 0.0f;
       for (int a = 0; a < nu; ++a) usum += fabsf(d2f(A.uin[rd][I.u_off + (long long)s * nu + a]));
       e = split_bound(I, last, mags, usum);
     }
     publish_residual(A, slot_k, b, k, rmax, rsq, e, full);
   }
+}
+
+// One upper-layer iteration over the strip work list (MODE_SOLVE: iteration
+// *iter_k + j with the convergence bookkeeping; MODE_ONESHOT: one residual or
+// iteration from the given buffers), after k_patch of the same iteration.
+template <typename T, int n_lo>
+__global__ void __launch_bounds__(STRIP_WARPS * 32) k_strip(IterArgs A, int MODE, int j_launch) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  StripShared& ws = *reinterpret_cast<StripShared*>(
+      smem_raw + warp * ((sizeof(StripShared) + 15) & ~size_t(15)));
+  pdl_trigger();
+  const int k = (MODE == MODE_SOLVE) ? *(volatile int*)A.iter_k + j_launch : 0;
+  const int rd = (MODE == MODE_SOLVE) ? (k & 1) : 0;
+  pdl_wait();  // the previous iteration's state, residuals and control words; this one's v3
+  const int item = blockIdx.x * STRIP_WARPS + warp;
+  if (item >= A.n_tiles) return;  // warp-uniform; no block barriers in this kernel
+  const int4 it = A.tiles[item];
+  const int b = it.x, s = it.y, x0 = it.z, y0 = it.w;
+
+  bool resid_only, full;
+  if (MODE == MODE_ONESHOT) {
+    resid_only = (A.resid_only != 0);
+    full = resid_only || (A.full_all != 0);
+  } else {
+    int skip = 0, fl = 1;
+    if (lane == 0) {
+      Cl cl;
+      cl.C = 1;
+      cl.rank = (x0 == 0 && y0 == 0) ? 0 : 1;  // the stage's first strip keeps the books
+      control_decision(A, b, s, k, cl, skip, fl);
+    }
+    skip = __shfl_sync(0xffffffffu, skip, 0);
+    fl = __shfl_sync(0xffffffffu, fl, 0);
+    if (skip) return;
+    full = fl != 0;
+    resid_only = (k == A.max_iter);
+  }
+  if (full || std::is_same<T, double>::value)
+    strip_body<T, n_lo, true>(A, ws, lane, b, s, k, rd, x0, y0, resid_only);
+  else
+    strip_body<T, n_lo, false>(A, ws, lane, b, s, k, rd, x0, y0, resid_only);
 }
