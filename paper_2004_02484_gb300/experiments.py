@@ -2,6 +2,7 @@
 
     python -m paper_2004_02484_gb300.experiments batch1d   [--n 1024]
     python -m paper_2004_02484_gb300.experiments closedloop [--n 64 --steps 200 --grid 256]
+    python -m paper_2004_02484_gb300.experiments solve      [--n 8 --grid 256 --graph 1]
 
 batch1d:    the ragged 1D batch (M ~ U{32..256}, N ~ U{10..60}, n_u ~ U{1..4},
             R = 10^U[-3,-1]) solved in one handle, mixed precision, to
@@ -18,6 +19,11 @@ closedloop_learned: the same loop with the learned start (controls from a
             on the same instances, for three rules (per-instance choice by
             float64 residual, or always the learned start, rollout or not):
             iterations per step and time.
+solve:      cold-start solves of the 2D 256x256, N = 100 batch (mixed, to
+            ||K||_inf <= 1e-6), one warm-up and --reps timed; with --graph 0
+            the iteration loop is launched from the host in chunks instead of
+            one graph (a profiler can then capture single iteration kernels);
+            reports iterations, ms per iteration and the launch plans.
 Prints one JSON line per experiment.
 """
 from __future__ import annotations
@@ -90,6 +96,28 @@ def closedloop(n: int, steps: int, grid: int, horizon: int, n_sub: int, check: i
     return out
 
 
+def solve(n: int, grid: int, horizon: int, reps: int, use_graph: int, **opts):
+    import torch
+    insts = wl.heat2d_large_batch(n=n, m=grid, horizon=horizon)
+    s = G.Solver(insts, tol=1e-6, precision=G.NMPC_MIXED, max_iter=4000, use_graph=use_graph,
+                 **opts)
+    rc, st = s.solve()
+    assert rc == G.NMPC_OK, rc
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        rc, st = s.solve()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / reps
+    its = np.array([st[b].iters for b in range(n)])
+    out = {"experiment": "solve", "instances": n, "grid": grid, "horizon": horizon,
+           "use_graph": use_graph, "rc": rc, "s_per_solve": dt, "iters_mean": float(its.mean()),
+           "ms_per_iteration": 1e3 * dt / (int(its.max()) + 1),
+           "tile_plan": G.nmpc_tile_plan(s.h), "launch_plan": G.nmpc_launch_plan(s.h)}
+    s.close()
+    return out
+
+
 def closedloop_learned(n_train: int, train_steps: int, n_test: int, steps: int, grid: int,
                        horizon: int, n_sub: int, fit_steps: int):
     import torch
@@ -136,7 +164,7 @@ def closedloop_learned(n_train: int, train_steps: int, n_test: int, steps: int, 
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", choices=["batch1d", "closedloop", "closedloop_learned"])
+    ap.add_argument("which", choices=["batch1d", "closedloop", "closedloop_learned", "solve"])
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--grid", type=int, default=256)
@@ -150,6 +178,8 @@ def main():
     ap.add_argument("--n-train", type=int, default=64)
     ap.add_argument("--train-steps", type=int, default=12)
     ap.add_argument("--fit-steps", type=int, default=2000)
+    ap.add_argument("--graph", type=int, default=1)
+    ap.add_argument("--reps", type=int, default=2)
     a = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
@@ -157,6 +187,9 @@ def main():
     build.build()
     if a.which == "batch1d":
         print(json.dumps(batch1d(a.n or 1024)), flush=True)
+    elif a.which == "solve":
+        print(json.dumps(solve(a.n or 8, a.grid, a.horizon, a.reps, a.graph, tiled=a.tiled,
+                               tile_rows=a.tile_rows)), flush=True)
     elif a.which == "closedloop_learned":
         print(json.dumps(closedloop_learned(a.n_train, a.train_steps, a.n or 8, a.steps, a.grid,
                                             a.horizon, a.n_sub, a.fit_steps)), flush=True)
