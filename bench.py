@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--ref-iters", type=int, default=8, help="oracle iterations per reference step")
+    ap.add_argument("--graph", type=int, default=1,
+                    help="1: the solve loop is one CUDA graph; 0: chunks of iteration launches "
+                         "from the host (the same kernels; a profiler can capture them)")
     return ap.parse_args()
 
 
@@ -202,7 +205,8 @@ def main():
     # solves of this workload, outside the timed region)
     from paper_2004_02484_gb300 import autotune as AT
     tuned = AT.tune([insts[0]], prec, tol=TOL, cache_path=AT.DEFAULT_CACHE + f".rank{rank}")
-    solver = G.Solver([insts[0]], tol=TOL, precision=prec, max_iter=5000, **AT.solver_opts(tuned))
+    solver = G.Solver([insts[0]], tol=TOL, precision=prec, max_iter=5000, use_graph=args.graph,
+                      **AT.solver_opts(tuned))
     dev = solver.u.device
     x0s = [torch.from_numpy(G.pack_fields([i], "x0")).to(dev) for i in insts]
     refs = [torch.from_numpy(G.pack_fields([i], "ref")).to(dev) for i in insts]
@@ -298,6 +302,7 @@ def main():
                "dtype": "f32+f64" if prec == G.NMPC_MIXED else "f64", "data": "synthetic",
                "config": {"workload": WORKLOAD, "precision": args.precision, "tol": TOL,
                           "instances_per_rank": 1, "tuned": AT.solver_opts(tuned),
+                          "solve_loop": "one CUDA graph" if args.graph else "host-launched chunks",
                           "l2": "flushed between steps (256 MiB write) outside the per-step events",
                           "iterations_per_solve": {"min": min(iters), "max": max(iters),
                                                    "mean": sum(iters) / len(iters)}},

@@ -215,3 +215,50 @@ def test_auto_routes_large_stages_to_tiles(G):
     assert plan["instances"] == 1 and plan["tile_x"] == 26 and 16 <= ty <= 256
     assert plan["tiles"] == 2 * -(-256 // 26) * -(-256 // ty)
     assert lp["work_items"] == 2 + 3
+
+
+@pytest.mark.parametrize("precision,rtol", [(0, 1e-5), (1, 1e-3)])
+def test_full_size_grid_strip_solve_matches_oracle_solve(G, precision, rtol):
+    """A 256x256 instance of the large closed-loop batch (16 actuators) on the
+    strip path, horizon shortened to N = 10 so that the oracle's own Jacobi
+    solve finishes in seconds: controls agree to 1e-5 (FP64) / 1e-3 (mixed)
+    relative at ||K||_inf <= 1e-6, and the oracle's float64 residual of the
+    GPU's returned state is <= 1e-6."""
+    import torch
+    inst = wl.heat2d_large_batch(n=1, base_seed=5000, m=256, horizon=10)[0]
+    s = G.Solver([inst], tol=1e-6, precision=precision, max_iter=4000)
+    assert G.nmpc_tile_plan(s.h)["instances"] == 1
+    rc, st = s.solve()
+    torch.cuda.synchronize()
+    assert rc == G.NMPC_OK
+    x, u, lam = (t.cpu().numpy() for t in s.state())
+    s.close()
+    p = O.Problem(inst)
+    K = O.kkt(p, x.reshape((p.N,) + p.shape), u.reshape(p.N, p.nu), lam.reshape((p.N,) + p.shape))
+    assert O.kkt_norms(*K)[0] <= 1e-6
+    (X, U, L), info = O.solve_jacobi(p, tol=1e-6)
+    assert info["converged"]
+    err = np.abs(u.reshape(U.shape) - U).max() / np.abs(U).max()
+    assert err <= rtol, err
+
+
+def test_large_batch_horizon_100_state_passes_the_oracle_residual(G):
+    """Two instances of the large closed-loop batch at full size (256x256,
+    N = 100, mixed precision, strip path): the oracle's float64 KKT residual
+    of each returned state is <= 1e-6."""
+    import torch
+    insts = wl.heat2d_large_batch(n=2, base_seed=5000, m=256, horizon=100)
+    s = G.Solver(insts, tol=1e-6, precision=G.NMPC_MIXED, max_iter=4000)
+    rc, st = s.solve()
+    torch.cuda.synchronize()
+    assert rc == G.NMPC_OK
+    x, u, lam = (t.cpu().numpy() for t in s.state())
+    s.close()
+    xs, us, ls = G.split_stages(insts, x, "ng"), G.split_stages(insts, u, "nu"), \
+        G.split_stages(insts, lam, "ng")
+    for b, inst in enumerate(insts):
+        p = O.Problem(inst)
+        K = O.kkt(p, xs[b].reshape((p.N,) + p.shape), us[b], ls[b].reshape((p.N,) + p.shape))
+        r = O.kkt_norms(*K)[0]
+        assert r <= 1e-6, (b, r)
+        assert abs(r - st[b].res_inf) <= 1e-9 * r
