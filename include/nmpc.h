@@ -240,6 +240,27 @@ int nmpc_start_state(nmpc_handle* h, int init, const double* x0, double* x, doub
 int nmpc_rollout(nmpc_handle* h, const double* x0, const double* ref, const double* u, double* x,
                  double* lam, void* stream);
 
+/* Step start of nmpc_closed_loop_learned, supplied by the caller: enqueue on
+   `stream` the work that writes a control trajectory guess (device float64,
+   [sum N n_u], the packing of u) into the caller's u_guess buffer, reading
+   the plant state in the caller's w buffer.  Kernel launches only (no
+   synchronisation, allocation or host copies): with the graph loop the calls
+   are captured, once, and replayed every step. */
+typedef void (*nmpc_start_fn)(void* ctx, void* stream);
+
+/* nmpc_closed_loop with a learned start (no counterpart in the paper; the
+   controls come from a network, e.g. on pooled plant state and reference):
+   each step copies w into x0, runs start(ctx, stream), completes the guess
+   u_guess with its state and costate trajectories (nmpc_rollout) and solves
+   from that start (NMPC_INIT_GUESS); then the plant moves as in
+   nmpc_closed_loop.  With opts.use_graph (and no persistent launch) the whole
+   loop, the start's kernels included, is one CUDA graph.  Histories and
+   return codes as nmpc_closed_loop; NMPC_ERR_BAD_ARG for a NULL h, w, ref,
+   start or u_guess, steps < 1 or n_sub < 1. */
+int nmpc_closed_loop_learned(nmpc_handle* h, double* w, const double* ref, int steps, int n_sub,
+                             nmpc_start_fn start, void* ctx, const double* u_guess,
+                             double* u_hist, int* iters_hist, double* res_hist, void* stream);
+
 /* Copy the handle's current state (after a solve: the returned iterates) to
    packed device arrays x, u, lam; any pointer may be NULL to skip it. */
 int nmpc_get_state(nmpc_handle* h, double* x, double* u, double* lam, void* stream);

@@ -57,9 +57,12 @@ int nmpc_cast_f64_f32(const double* in, float* out, int64_t n, void* stream);
    learned warm start for large grids): src device float64 [n_img][my][mx]
    row-major, dst device float32 [n_img][my/factor][mx/factor], each output
    the mean of a factor x factor block (summed in float64).  mx and my must be
-   multiples of factor, else NMPC_MLP_ERR_BAD_ARG. */
+   multiples of factor, else NMPC_MLP_ERR_BAD_ARG.  Image i's pooled cells
+   start at dst + i * dst_stride (dst_stride >= (mx / factor) (my / factor);
+   0 means exactly that), so pooled fields can land interleaved in feature
+   rows. */
 int nmpc_pool_avg(const double* src, float* dst, int n_img, int mx, int my, int factor,
-                  void* stream);
+                  int64_t dst_stride, void* stream);
 
 /* Network with widths[0..n_layers] (each a multiple of 8), batches up to
    max_batch; weights U(-1/sqrt(in), 1/sqrt(in)) from SplitMix64(seed), biases

@@ -120,14 +120,17 @@ int nmpc_cast_f64_f32(const double* in, float* out, int64_t n, void* stream) {
 }
 
 int nmpc_pool_avg(const double* src, float* dst, int n_img, int mx, int my, int factor,
-                  void* stream) {
+                  int64_t dst_stride, void* stream) {
   if (!src || !dst || n_img < 0 || mx < 1 || my < 1 || factor < 1 || (mx % factor) != 0 ||
       (my % factor) != 0)
     return NMPC_MLP_ERR_BAD_ARG;
-  const long long n = (long long)n_img * (mx / factor) * (my / factor);
+  const long long per = (long long)(mx / factor) * (my / factor);
+  if (dst_stride == 0) dst_stride = per;
+  if (dst_stride < per) return NMPC_MLP_ERR_BAD_ARG;
+  const long long n = (long long)n_img * per;
   if (n == 0) return NMPC_MLP_OK;
   mlp_dev::k_pool_avg<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(src, dst, n_img, mx, my,
-                                                                          factor);
+                                                                          factor, dst_stride);
   MCK(cudaGetLastError());
   return NMPC_MLP_OK;
 }
@@ -272,7 +275,12 @@ static int forward_impl(nmpc_mlp* m, const float* x, int B, float* y, cudaStream
     }
   }
   const int nout = m->w[m->L];
-  MCK(cudaMemcpyAsync(y, m->z[m->L - 1], (size_t)B * nout * 4, cudaMemcpyDeviceToDevice, st));
+  if (y != m->z[m->L - 1]) {
+    const long long ny = (long long)B * nout;
+    mlp_dev::k_copy_f32<<<grid_for(ny, 256), 256, 0, st>>>(m->z[m->L - 1], y, ny);
+    MCK(cudaGetLastError());
+    m->launches++;
+  }
   return NMPC_MLP_OK;
 }
 

@@ -236,6 +236,14 @@ __global__ void k_transpose_bf16(const __nv_bfloat16* in, __nv_bfloat16* out, in
   }
 }
 
+// out = in (a kernel rather than a copy node, so that the forward pass can be
+// captured into any graph, conditional bodies included)
+__global__ void k_copy_f32(const float* in, float* out, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    out[e] = in[e];
+}
+
 __global__ void k_cast_bf16(const float* in, __nv_bfloat16* out, long long n) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x)
@@ -256,7 +264,8 @@ __global__ void k_cast_f64_f32(const double* in, float* out, long long n) {
 
 // Average pooling of n_img row-major my x mx float64 fields by f x f blocks
 // into float32 [n_img][(my/f) (mx/f)] (sums in float64).
-__global__ void k_pool_avg(const double* src, float* dst, int n_img, int mx, int my, int f) {
+__global__ void k_pool_avg(const double* src, float* dst, int n_img, int mx, int my, int f,
+                           long long dst_stride) {
   const int ox = mx / f, oy = my / f;
   const long long n = (long long)n_img * ox * oy;
   const double inv = 1.0 / ((double)f * f);
@@ -269,7 +278,7 @@ __global__ void k_pool_avg(const double* src, float* dst, int n_img, int mx, int
     double acc = 0.0;
     for (int a = 0; a < f; ++a)
       for (int c = 0; c < f; ++c) acc += s[(long long)a * mx + c];
-    dst[e] = (float)(acc * inv);
+    dst[img * dst_stride + o] = (float)(acc * inv);
   }
 }
 

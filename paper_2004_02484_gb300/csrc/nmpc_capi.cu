@@ -944,8 +944,29 @@ cudaError_t add_while(cudaGraph_t g, cudaGraphNode_t dep, cudaGraphConditionalHa
 // at step 0, shifted afterwards), runs the solve loop (a nested WHILE node
 // over chunks of iteration launches), settles the instances, records the
 // step's status / iterations / residual, and moves the plant.
+// State (forward) and costate (backward) trajectories of controls u from x0
+// into x, lam: 2 N_max launches on st.
+cudaError_t enqueue_rollout(nmpc_handle* h, const double* x0, const double* ref, const double* u,
+                            double* x, double* lam, cudaStream_t st) {
+  int nmax = 0;
+  for (const InstDev& I : h->inst_h) nmax = std::max(nmax, I.N);
+  for (int i = 0; i < nmax; ++i) {
+    nmpc_dev::k_rollout_state<<<per_instance_grid(h), 256, 0, st>>>(h->inst_d, h->n_inst, h->act_d,
+                                                                    x0, u, x, i);
+    h->launches++;
+  }
+  for (int i = 0; i < nmax; ++i) {
+    nmpc_dev::k_rollout_costate<<<per_instance_grid(h), 256, 0, st>>>(h->inst_d, h->n_inst, ref, x,
+                                                                      lam, i);
+    h->launches++;
+  }
+  return cudaGetLastError();
+}
+
 int closed_loop_graph(nmpc_handle* h, double* w, int steps, int n_sub, double* u_hist,
-                      int* iters_hist, double* res_hist, cudaStream_t st) {
+                      int* iters_hist, double* res_hist, cudaStream_t st,
+                      nmpc_start_fn start = nullptr, void* ctx = nullptr,
+                      const double* u_guess = nullptr) {
   const int n = h->n_inst;
   const int chunk = std::max(1, h->opts.check_every);
   IterArgs A = make_args(h);
@@ -980,11 +1001,21 @@ int closed_loop_graph(nmpc_handle* h, double* w, int steps, int n_sub, double* u
     if (cudaGraphConditionalHandleCreate(&inner, body_o, 0, cudaGraphCondAssignDefault) !=
         cudaSuccess)
       break;
-    // step: x0 <- w, start, first loop decision
+    // step: x0 <- w, start (cold / shifted, or the caller's guess completed
+    // by its state and costate trajectories), first loop decision
     if (capture_after(body_o, nullptr, 0, cap, [&]() {
           nmpc_dev::k_copy_f64<<<256, 256, 0, cap>>>(h->x0_d, w, h->n_g);
-          nmpc_dev::k_init_control<<<per_instance_grid(h), 256, 0, cap>>>(
-              A, first_mode, 0, h->xb[2], h->ub[2], h->lb[2], step);
+          if (start) {
+            start(ctx, (void*)cap);
+            nmpc_dev::k_copy_f64<<<256, 256, 0, cap>>>(h->ub[0], u_guess, h->n_u);
+            cudaError_t e = enqueue_rollout(h, h->x0_d, h->ref_d, h->ub[0], h->xb[0], h->lb[0], cap);
+            if (e != cudaSuccess) return e;
+            nmpc_dev::k_init_control<<<per_instance_grid(h), 256, 0, cap>>>(
+                A, 1, 0, h->xb[2], h->ub[2], h->lb[2], nullptr);
+          } else {
+            nmpc_dev::k_init_control<<<per_instance_grid(h), 256, 0, cap>>>(
+                A, first_mode, 0, h->xb[2], h->ub[2], h->lb[2], step);
+          }
           nmpc_dev::k_loop_cond<<<1, 32, 0, cap>>>(inner, A.n_active, A.iter_k, h->opts.max_iter);
           return cudaGetLastError();
         }, &n1) != cudaSuccess)
@@ -1060,6 +1091,7 @@ int closed_loop_graph(nmpc_handle* h, double* w, int steps, int n_sub, double* u
     for (int b = 0; b < n; ++b) kmax = std::max(kmax, ith[(size_t)t * n + b] + 2);
     const long long runs = (kmax + chunk - 1) / chunk;
     h->launches += 8 + n_sub + runs * (chunk + 2);
+    if (start) h->launches += 1 + 2 * (long long)h->n_max_horizon;  // guess copy, rollout
     h->iter_launches += runs * chunk;
   }
   h->launches += 1;
@@ -1489,21 +1521,40 @@ int nmpc_start_state(nmpc_handle* h, int init, const double* x0, double* x, doub
 int nmpc_rollout(nmpc_handle* h, const double* x0, const double* ref, const double* u, double* x,
                  double* lam, void* stream) {
   if (!h || !x0 || !ref || !u || !x || !lam) return NMPC_ERR_BAD_ARG;
-  cudaStream_t st = (cudaStream_t)stream;
-  int nmax = 0;
-  for (const InstDev& I : h->inst_h) nmax = std::max(nmax, I.N);
-  for (int i = 0; i < nmax; ++i) {
-    nmpc_dev::k_rollout_state<<<per_instance_grid(h), 256, 0, st>>>(h->inst_d, h->n_inst, h->act_d,
-                                                                    x0, u, x, i);
-    h->launches++;
-  }
-  for (int i = 0; i < nmax; ++i) {
-    nmpc_dev::k_rollout_costate<<<per_instance_grid(h), 256, 0, st>>>(h->inst_d, h->n_inst, ref, x,
-                                                                      lam, i);
-    h->launches++;
-  }
-  CK(cudaGetLastError());
+  CK(enqueue_rollout(h, x0, ref, u, x, lam, (cudaStream_t)stream));
   return NMPC_OK;
+}
+
+int nmpc_closed_loop_learned(nmpc_handle* h, double* w, const double* ref, int steps, int n_sub,
+                             nmpc_start_fn start, void* ctx, const double* u_guess,
+                             double* u_hist, int* iters_hist, double* res_hist, void* stream) {
+  if (!h || !w || !ref || !start || !u_guess || steps < 1 || n_sub < 1) return NMPC_ERR_BAD_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(h->ref_d, ref, h->n_g * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (h->opts.use_graph && !h->persistent)
+    return closed_loop_graph(h, w, steps, n_sub, u_hist, iters_hist, res_hist, st, start, ctx,
+                             u_guess);
+  const int n = h->n_inst;
+  std::vector<nmpc_stats> stats(n);
+  int rc_all = NMPC_OK;
+  for (int t = 0; t < steps; ++t) {
+    CK(cudaMemcpyAsync(h->x0_d, w, h->n_g * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    start(ctx, stream);
+    CK(cudaMemcpyAsync(h->ub[2], u_guess, h->n_u * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(enqueue_rollout(h, h->x0_d, h->ref_d, h->ub[2], h->xb[2], h->lb[2], st));
+    h->has_state = true;  // the guess is the handle's current state
+    int rc = solve_core(h, 0, nullptr, NMPC_INIT_GUESS, nullptr, stats.data(), st);
+    if (rc == NMPC_ERR_BAD_ARG || rc == NMPC_ERR_CUDA) return rc;
+    if (rc != NMPC_OK && rc_all == NMPC_OK) rc_all = rc;
+    for (int b = 0; b < n; ++b) {
+      if (iters_hist) iters_hist[(size_t)t * n + b] = stats[b].iters;
+      if (res_hist) res_hist[(size_t)t * n + b] = stats[b].res_inf;
+    }
+    int prc = nmpc_plant_step(h, w, 0.0, n_sub,
+                              u_hist ? u_hist + (size_t)t * h->nu_tot : nullptr, stream);
+    if (prc != NMPC_OK) return prc;
+  }
+  return rc_all;
 }
 
 int nmpc_get_state(nmpc_handle* h, double* x, double* u, double* lam, void* stream) {

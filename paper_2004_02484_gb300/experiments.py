@@ -15,10 +15,10 @@ closedloop: the 2D 256x256, N = 100, 16-actuator batch in a receding-horizon
 closedloop_learned: the same loop with the learned start (controls from a
             network on 4x4-pooled plant state and reference, trained on plain
             closed loops of disjoint seeds; state and costate from the
-            controls' rollout or from the plain start) against the plain loop
-            on the same instances, for three rules (per-instance choice by
-            float64 residual, or always the learned start, rollout or not):
-            iterations per step and time.
+            controls' rollout) against the plain loop on the same instances,
+            both as one CUDA graph: iterations per step and solves/s; with
+            --rules 1 also the host-driven variants (per-instance choice by
+            float64 residual, or always the learned start, rollout or not).
 solve:      cold-start solves of the 2D 256x256, N = 100 batch (mixed, to
             ||K||_inf <= 1e-6), one warm-up and --reps timed; with --graph 0
             the iteration loop is launched from the host in chunks instead of
@@ -119,7 +119,7 @@ def solve(n: int, grid: int, horizon: int, reps: int, use_graph: int, **opts):
 
 
 def closedloop_learned(n_train: int, train_steps: int, n_test: int, steps: int, grid: int,
-                       horizon: int, n_sub: int, fit_steps: int):
+                       horizon: int, n_sub: int, fit_steps: int, rules: int = 1):
     import torch
     from . import warmstart as WS
     t0 = time.perf_counter()
@@ -146,7 +146,23 @@ def closedloop_learned(n_train: int, train_steps: int, n_test: int, steps: int, 
     res.update({"plain_s": time.perf_counter() - t0, "plain_iters_per_step": iters.mean(axis=1).tolist(),
                 "plain_rc": rc})
     s.close()
-    for rule, decode in (("residual", "rollout"), ("always", "rollout"), ("always", "controls")):
+    # the learned loop as one graph (network kernels captured into each step)
+    s = G.Solver(test, tol=1e-6, precision=G.NMPC_MIXED, max_iter=4000)
+    w = s.x0.clone()
+    WS.closed_loop_learned_graph(s, lcs, w, 1, n_sub)  # warm-up (buffers, module load)
+    w = s.x0.clone()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, iters, r = WS.closed_loop_learned_graph(s, lcs, w, steps, n_sub)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    res.update({"learned_graph_s": dt, "learned_graph_rc": rc,
+                "learned_graph_iters_per_step": iters.mean(axis=1).tolist(),
+                "learned_graph_solves_per_s": n_test * steps / dt,
+                "plain_solves_per_s": n_test * steps / res["plain_s"]})
+    s.close()
+    for rule, decode in ((("residual", "rollout"), ("always", "rollout"), ("always", "controls"))
+                         if rules else ()):
         s = G.Solver(test, tol=1e-6, precision=G.NMPC_MIXED, max_iter=4000)
         w = s.x0.clone()
         torch.cuda.synchronize()
@@ -180,6 +196,7 @@ def main():
     ap.add_argument("--fit-steps", type=int, default=2000)
     ap.add_argument("--graph", type=int, default=1)
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--rules", type=int, default=1)
     a = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
@@ -192,7 +209,7 @@ def main():
                                tile_rows=a.tile_rows)), flush=True)
     elif a.which == "closedloop_learned":
         print(json.dumps(closedloop_learned(a.n_train, a.train_steps, a.n or 8, a.steps, a.grid,
-                                            a.horizon, a.n_sub, a.fit_steps)), flush=True)
+                                            a.horizon, a.n_sub, a.fit_steps, a.rules)), flush=True)
     else:
         res = closedloop(a.n or 64, a.steps, a.grid, a.horizon, a.n_sub, a.check,
                          cluster=a.cluster, threads=a.threads, tiled=a.tiled,

@@ -30,7 +30,7 @@ _SIG = {
     "nmpc_cast_f32_f64": (_I, [_P, _P, ctypes.c_int64, _P]),
     "nmpc_transpose_bf16": (_I, [_P, _P, _I, _I, _P]),
     "nmpc_cast_f64_f32": (_I, [_P, _P, ctypes.c_int64, _P]),
-    "nmpc_pool_avg": (_I, [_P, _P, _I, _I, _I, _I, _P]),
+    "nmpc_pool_avg": (_I, [_P, _P, _I, _I, _I, _I, ctypes.c_int64, _P]),
     "nmpc_mlp_create": (_I, [_I, ctypes.POINTER(_I), _I, ctypes.c_uint64, ctypes.POINTER(_P)]),
     "nmpc_mlp_num_params": (ctypes.c_int64, [_P]),
     "nmpc_mlp_set_params": (_I, [_P, _P]),
@@ -93,13 +93,19 @@ def nmpc_cast_f32_f64(x, out, stream=None):
            "nmpc_cast_f32_f64")
 
 
-def nmpc_pool_avg(src, out, n_img: int, mx: int, my: int, factor: int, stream=None):
-    """float64 fields [n_img, my, mx] -> float32 block means [n_img, my/f, mx/f]."""
+def nmpc_pool_avg(src, out, n_img: int, mx: int, my: int, factor: int, dst_stride: int = 0,
+                  stream=None):
+    """float64 fields [n_img, my, mx] -> float32 block means [n_img, my/f, mx/f]
+    (image i's at out + i dst_stride; 0 = packed)."""
     import torch
     assert src.dtype == torch.float64 and out.dtype == torch.float32 and src.is_cuda and out.is_cuda
-    assert src.numel() >= n_img * mx * my and out.numel() >= n_img * (mx // factor) * (my // factor)
-    _check(LIB.nmpc_pool_avg(src.data_ptr(), out.data_ptr(), n_img, mx, my, factor, _stream(stream)),
-           "nmpc_pool_avg")
+    per = (mx // factor) * (my // factor)
+    stride = dst_stride or per
+    assert src.numel() >= n_img * mx * my
+    room = out.untyped_storage().nbytes() // 4 - out.storage_offset()
+    assert n_img == 0 or room >= (n_img - 1) * stride + per
+    _check(LIB.nmpc_pool_avg(src.data_ptr(), out.data_ptr(), n_img, mx, my, factor, dst_stride,
+                             _stream(stream)), "nmpc_pool_avg")
 
 
 def nmpc_cast_f64_f32(x, out, stream=None):

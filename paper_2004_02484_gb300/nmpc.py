@@ -63,7 +63,12 @@ EXPORTED = ["nmpc_default_opts", "nmpc_setup", "nmpc_solve", "nmpc_solve_host",
             "nmpc_residual", "nmpc_iterate", "nmpc_get_state", "nmpc_set_state",
             "nmpc_sizes", "nmpc_launch_count", "nmpc_launch_plan", "nmpc_tile_plan", "nmpc_start_state", "nmpc_rollout", "nmpc_destroy",
             "nmpc_strerror",
-            "nmpc_solve_noalloc", "nmpc_plant_step", "nmpc_closed_loop"]
+            "nmpc_solve_noalloc", "nmpc_plant_step", "nmpc_closed_loop",
+            "nmpc_closed_loop_learned"]
+
+
+# step start of nmpc_closed_loop_learned: void (*)(void* ctx, void* stream)
+START_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 
 def _load() -> ctypes.CDLL:
@@ -95,6 +100,7 @@ def _load() -> ctypes.CDLL:
                                    P, ctypes.POINTER(nmpc_stats), P]),
         "nmpc_plant_step": (I, [P, P, D, I, P, P]),
         "nmpc_closed_loop": (I, [P, P, P, I, I, P, P, P, P]),
+        "nmpc_closed_loop_learned": (I, [P, P, P, I, I, START_FN, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -128,7 +134,10 @@ def _ptr(t) -> Optional[int]:
 
 
 def _stream(stream):
+    """A torch stream, a raw cudaStream_t (int) or None (torch's current stream)."""
     import torch
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
 
@@ -253,6 +262,32 @@ def nmpc_closed_loop(h, w, ref, steps: int, n_sub: int, n_inst: int, u_hist=None
     rc = LIB.nmpc_closed_loop(h, _ptr(w), _ptr(ref), steps, n_sub, _ptr(u_hist),
                               iters.ctypes.data, res.ctypes.data, _stream(stream))
     _check(rc, "nmpc_closed_loop", allow=(NMPC_ERR_NOT_CONVERGED, NMPC_ERR_DIVERGED))
+    return rc, iters, res
+
+
+def nmpc_closed_loop_learned(h, w, ref, steps: int, n_sub: int, n_inst: int, start, u_guess,
+                             u_hist=None, stream=None):
+    """Closed loop with a learned start.  start(stream_ptr: int) enqueues, on
+    the given raw stream, kernels that write the control guess into u_guess
+    from the plant state w (kernel launches only: they are captured into the
+    loop's graph).  Returns (rc, iters [steps, n], res [steps, n])."""
+    iters = np.zeros((steps, n_inst), dtype=np.int32)
+    res = np.zeros((steps, n_inst), dtype=np.float64)
+    errors = []
+
+    def _cb(ctx, st):
+        try:
+            start(int(st or 0))
+        except BaseException as e:  # reported after the call: the C side cannot see it
+            errors.append(e)
+
+    cb = START_FN(_cb)
+    rc = LIB.nmpc_closed_loop_learned(h, _ptr(w), _ptr(ref), steps, n_sub, cb, None, _ptr(u_guess),
+                                      _ptr(u_hist), iters.ctypes.data, res.ctypes.data,
+                                      _stream(stream))
+    if errors:
+        raise errors[0]
+    _check(rc, "nmpc_closed_loop_learned", allow=(NMPC_ERR_NOT_CONVERGED, NMPC_ERR_DIVERGED))
     return rc, iters, res
 
 

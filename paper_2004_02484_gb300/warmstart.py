@@ -269,17 +269,15 @@ class LearnedControlStart:
         self.net = GM.MLP(self.widths, max_batch, seed)
         self.mean = self.std = None
 
-    def features(self, w, ref, B: int):
-        """Pooled [w; ref] rows, float32 device [B, 2 ngp]."""
+    def features(self, w, ref, B: int, out=None, stream=None):
+        """Pooled [w; ref] rows, float32 device [B, 2 ngp] (into `out` if given;
+        kernels only, so the call can be captured into a graph)."""
         torch = _torch()
-        f = torch.empty((B, 2, self.ngp), dtype=torch.float32, device=w.device)
-        wp = torch.empty((B, self.ngp), dtype=torch.float32, device=w.device)
-        rp = torch.empty((B, self.ngp), dtype=torch.float32, device=w.device)
-        GM.nmpc_pool_avg(w, wp, B, self.mx, self.my, self.pool)
-        GM.nmpc_pool_avg(ref, rp, B, self.mx, self.my, self.pool)
-        f[:, 0].copy_(wp)
-        f[:, 1].copy_(rp)
-        return f.view(B, 2 * self.ngp)
+        f = out if out is not None else torch.empty((B, 2 * self.ngp), dtype=torch.float32,
+                                                    device=w.device)
+        GM.nmpc_pool_avg(w, f, B, self.mx, self.my, self.pool, 2 * self.ngp, stream)
+        GM.nmpc_pool_avg(ref, f[:, self.ngp:], B, self.mx, self.my, self.pool, 2 * self.ngp, stream)
+        return f
 
     def fit(self, X: np.ndarray, U: np.ndarray, steps: int = 2000, batch: int = 128,
             lr: float = 1e-3, seed: int = 0) -> List[float]:
@@ -308,11 +306,21 @@ class LearnedControlStart:
     def predict_u(self, w, ref, B: int):
         """Control trajectory guesses, float64 device [B N nu]."""
         torch = _torch()
-        y = torch.empty((B, self.n_out), dtype=torch.float32, device=w.device)
-        self.net.forward(self.features(w, ref, B), y)
         u = torch.empty(B * self.n_out, dtype=torch.float64, device=w.device)
-        GM.nmpc_cast_f32_f64(y.view(-1), u)
+        self.predict_u_into(w, ref, B, u)
         return u
+
+    def predict_u_into(self, w, ref, B: int, u, stream=None):
+        """predict_u into the float64 device array u [B N nu] with buffers kept
+        for the batch size: only kernel launches on `stream`, so the call can
+        be captured into a CUDA graph (after one call outside the capture)."""
+        torch = _torch()
+        if getattr(self, "_buf_b", None) != B:
+            self._f = torch.empty((B, 2 * self.ngp), dtype=torch.float32, device=w.device)
+            self._y = torch.empty((B, self.n_out), dtype=torch.float32, device=w.device)
+            self._buf_b = B
+        self.net.forward(self.features(w, ref, B, self._f, stream), self._y, stream)
+        GM.nmpc_cast_f32_f64(self._y.view(-1), u, stream)
 
 
 def closed_loop_data(instances, steps: int, n_sub: int, pool: int = 4, tol: float = 1e-6,
@@ -400,6 +408,23 @@ def closed_loop_learned(solver: "G.Solver", lcs: LearnedControlStart, w, steps: 
         first = False
     return {"iters": np.array(iters), "learned": np.array(chosen),
             "res_plain": np.array(r_plain), "res_learned": np.array(r_learn)}
+
+
+def closed_loop_learned_graph(solver: "G.Solver", lcs: LearnedControlStart, w, steps: int,
+                              n_sub: int, u_hist=None):
+    """The closed loop with the learned start in one CUDA graph (with the
+    handle's graph option): every step the network's controls (pooled plant
+    state and reference -> controls), completed by their state and costate
+    trajectories, start the solve.  w (device float64 plant state) is updated
+    in place.  Returns (rc, iters [steps, n], res [steps, n])."""
+    torch = _torch()
+    B = solver.n
+    u_guess = torch.empty(solver.n_u, dtype=torch.float64, device=w.device)
+    lcs.predict_u_into(w, solver.ref, B, u_guess)  # buffers for this batch, outside any capture
+    torch.cuda.synchronize()
+    return G.nmpc_closed_loop_learned(
+        solver.h, w, solver.ref, steps, n_sub, B,
+        lambda st: lcs.predict_u_into(w, solver.ref, B, u_guess, st), u_guess, u_hist)
 
 
 def evaluate(ws: LearnedWarmStart, seeds: Sequence[int], tol: float = 1e-6,

@@ -199,3 +199,36 @@ def test_rollout_matches_its_definition(G):
         assert np.abs(Xb.reshape(X.shape) - X).max() <= 1e-12 * sx
         assert np.abs(Lb.reshape(L.shape) - L).max() <= 1e-12 * sl
     s.close()
+
+
+@pytest.mark.parametrize("tiled", [2, 1])
+def test_learned_closed_loop_graph_equals_host_driven_loops(G, tiled):
+    """The learned closed loop as one CUDA graph (network kernels captured into
+    the step body, rollout, solve, plant) gives the host-driven C loop's and
+    the Python-driven loop's iterations and plant states, on the cluster path
+    (tiled 2) and on the strip path (tiled 1)."""
+    import torch
+    from paper_2004_02484_gb300 import warmstart as WS
+    train = wl.heat2d_large_batch(n=4, base_seed=7000, m=32, horizon=10)
+    X, U = WS.closed_loop_data(train, 4, 2)
+    lcs = WS.LearnedControlStart(train[0], pool=4, max_batch=16)
+    lcs.fit(X, U, steps=100, batch=16)
+    test = wl.heat2d_large_batch(n=2, base_seed=5000, m=32, horizon=10)
+    out = []
+    for use_graph in (1, 0):
+        s = G.Solver(test, tol=1e-6, precision=1, max_iter=4000, use_graph=use_graph, tiled=tiled)
+        w = s.x0.clone()
+        rc, iters, res = WS.closed_loop_learned_graph(s, lcs, w, 3, 2)
+        torch.cuda.synchronize()
+        assert rc == G.NMPC_OK and np.all(res <= 1e-6)
+        out.append((iters, w.cpu().numpy()))
+        s.close()
+    s = G.Solver(test, tol=1e-6, precision=1, max_iter=4000, tiled=tiled)
+    w = s.x0.clone()
+    py = WS.closed_loop_learned(s, lcs, w, 3, 2, rule="always", decode="rollout")
+    torch.cuda.synchronize()
+    out.append((py["iters"], w.cpu().numpy()))
+    s.close()
+    for it, wf in out[1:]:
+        assert np.array_equal(it, out[0][0])
+        assert np.array_equal(wf, out[0][1])
