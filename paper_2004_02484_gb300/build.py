@@ -7,6 +7,7 @@ source is newer than the library.
 """
 from __future__ import annotations
 
+import glob
 import os
 import subprocess
 import sys
@@ -16,10 +17,9 @@ ROOT = os.path.dirname(HERE)
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libnmpc_gb300.so")
 SOURCES = [os.path.join(HERE, "csrc", "nmpc_capi.cu"), os.path.join(HERE, "csrc", "mlp_capi.cu")]
-DEPS = SOURCES + [os.path.join(HERE, "csrc", "nmpc_kernels.cuh"),
-                  os.path.join(HERE, "csrc", "mlp_kernels.cuh"),
-                  os.path.join(ROOT, "include", "nmpc.h"),
-                  os.path.join(ROOT, "include", "nmpc_mlp.h")]
+# every source and header the library is built from
+DEPS = SOURCES + sorted(glob.glob(os.path.join(HERE, "csrc", "*.cuh")) +
+                        glob.glob(os.path.join(ROOT, "include", "*.h")))
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

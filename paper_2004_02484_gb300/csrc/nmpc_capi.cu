@@ -1246,7 +1246,12 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
     h->tile_y = ty;
     h->tile_threads = 32 * nmpc_dev::STRIP_WARPS;
     h->tile_region = 32 * (ty + 2 * E);
-    h->tile_smem = nmpc_dev::STRIP_WARPS * ((sizeof(nmpc_dev::StripShared) + 15) & ~size_t(15));
+    const size_t ws_bytes =
+        o.n_lo <= 1   ? sizeof(nmpc_dev::StripShared<nmpc_dev::strip_ring_rows(1)>)
+        : o.n_lo == 2 ? sizeof(nmpc_dev::StripShared<nmpc_dev::strip_ring_rows(2)>)
+        : o.n_lo == 3 ? sizeof(nmpc_dev::StripShared<nmpc_dev::strip_ring_rows(3)>)
+                      : sizeof(nmpc_dev::StripShared<nmpc_dev::strip_ring_rows(4)>);
+    h->tile_smem = nmpc_dev::STRIP_WARPS * ((ws_bytes + 15) & ~size_t(15));
     const size_t P2 = (size_t)(2 * E + 1) * (2 * E + 1);
     h->patch_smem = PATCH_WARPS * (((sizeof(nmpc_dev::PatchShared) + 15) & ~size_t(15)) +
                                    8 * P2 * sizeof(double));

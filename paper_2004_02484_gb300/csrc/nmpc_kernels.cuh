@@ -594,12 +594,15 @@ __device__ __noinline__ void control_decision(const IterArgs& A, int b, int s, i
 // O(h) term is off by at most 16 u h S, S = 4 (cx + cy) (Phi_max + Phi'_max
 // Lm) + b0 sum|u| + (q + qf [last stage]) (X + max|ref|); the float64
 // differences and the stage-gradient rows are truncated once (2u) and summed
-// (u).  Every cell's |K_split - K| is below the bound.  It is evaluated in
-// float32 (its own rounding, a few u relative, is far inside the factor 16)
-// and rounded up by 1%.  mags: X, Lm, max |float64 difference or K2|, max
-// |ref|; usum: sum over the stage's controls of |u| (float32).
+// (u).  With diff32 the differences are instead taken in float32 from the
+// truncated values (2u each, then rounded: u), which adds 4u max(X, Lm) with
+// X, Lm covering the neighbouring stages' values as well.  Every cell's
+// |K_split - K| is below the bound.  It is evaluated in float32 (its own
+// rounding, a few u relative, is far inside the factor 16) and rounded up by
+// 1%.  mags: X, Lm, max |difference or K2|, max |ref|; usum: sum over the
+// stage's controls of |u| (float32).
 __device__ __forceinline__ double split_bound(const InstDev& I, bool last, const float* mags,
-                                              float usum) {
+                                              float usum, bool diff32 = false) {
   const float u32 = 5.9604645e-08f;
   const float Xm = mags[0], Lm = mags[1], Dm = mags[2], Rm = mags[3];
   const float ak0 = fabsf(I.fk0), ak1 = fabsf(I.fk1);
@@ -607,7 +610,8 @@ __device__ __forceinline__ double split_bound(const InstDev& I, bool last, const
   const float dpmax = ak0 * (1.0f + ak1 * Xm);
   const float S = 2.0f * I.fdc * (pmax + dpmax * Lm) + fabsf(I.fb0) * usum +
                   (I.fq + (last ? I.fhqf / I.fh : 0.0f)) * (Xm + Rm);
-  return f2d(1.01f * u32 * (3.0f * Dm + 16.0f * I.fh * S));
+  const float Dterm = 3.0f * Dm + (diff32 ? 4.0f * fmaxf(Xm, Lm) : 0.0f);
+  return f2d(1.01f * u32 * (Dterm + 16.0f * I.fh * S));
 }
 
 // Residual norms of a work item (max, sum of squares) and, for the split

@@ -23,18 +23,29 @@
 // stencil traffic.  The actuators' v3 come from k_patch (same iteration).
 
 constexpr int STRIP_WARPS = 4;  // warps (strips) per CTA
-constexpr int STRIP_RING = 4;   // rows in a warp's input ring
 constexpr int STRIP_AHEAD = 2;  // rows copied ahead
+// CTAs per SM the register allocation must allow (4 warps each)
+#ifndef STRIP_MIN_BLOCKS
+#define STRIP_MIN_BLOCKS 5
+#endif
 
 // An actuator inside a strip's region: region row, lane, control index.
 struct StripAct {
   int row, lane, a, pad;
 };
 
-// Shared memory of one strip warp: the input ring (STRIP_RING rows x SREC
-// fields x 32 lanes, float64) and the actuators in reach sorted by row.
+// Rows of a warp's input ring: from the row pass E updates (j - E) to the
+// row being copied (j + STRIP_AHEAD), so the update reads x, lambda from
+// shared memory.
+__host__ __device__ constexpr int strip_ring_rows(int n_lo) {
+  return 2 * n_lo - 1 + STRIP_AHEAD + 1;
+}
+
+// Shared memory of one strip warp: the input ring (RING rows x SREC fields x
+// 32 lanes, float64) and the actuators in reach sorted by row.
+template <int RING>
 struct StripShared {
-  double ring[STRIP_RING * SREC * 32];
+  double ring[RING * SREC * 32];
   StripAct act[MAX_NU];
   int n_act;
 };
@@ -74,9 +85,12 @@ struct Shift {
 // float64 residual; else the split one): a separate instantiation per form,
 // so neither form's arithmetic is issued in the other's iterations.
 template <typename T, int n_lo, bool FULL>
-__device__ __forceinline__ void strip_body(const IterArgs& A, StripShared& ws, int lane, int b,
-                                           int s, int k, int rd, int x0, int y0, bool resid_only) {
+__device__ __forceinline__ void strip_body(const IterArgs& A,
+                                           StripShared<strip_ring_rows(n_lo)>& ws, int lane,
+                                           int b, int s, int k, int rd, int x0, int y0,
+                                           bool resid_only) {
   constexpr int E = 2 * n_lo - 1;
+  constexpr int RING = strip_ring_rows(n_lo);
   constexpr bool full = FULL;
   const InstDev& I = A.inst[b];
   const int nu = I.nu;
@@ -109,7 +123,8 @@ __device__ __forceinline__ void strip_body(const IterArgs& A, StripShared& ws, i
   }
   __syncwarp();
   const int n_act = ws.n_act;
-  int na = 0;  // next actuator entry (rows increase along the strip)
+  int na = 0;  // next actuator entry (rows increase along the strip; all rows >= 0)
+  int next_row = n_act > 0 ? ws.act[0].row : 0x7fffffff;
 
   // asynchronous copies of region row rj into its ring slot (zero outside the grid)
   const double* Xg = A.xin[rd] + so;
@@ -119,7 +134,7 @@ __device__ __forceinline__ void strip_body(const IterArgs& A, StripShared& ws, i
   const double* RFg = A.ref + I.g_off;
   double* ring = ws.ring + lane;
   auto slot = [&](int rj, int f) -> double* {
-    return ring + ((rj & (STRIP_RING - 1)) * SREC + f) * 32;
+    return ring + (((rj + RING) % RING) * SREC + f) * 32;  // rj >= -1
   };
   // row rj's five inputs; cells outside the grid and rows past the region
   // are zero-filled by the copies themselves (source size 0, from a clamped
@@ -146,7 +161,6 @@ __device__ __forceinline__ void strip_body(const IterArgs& A, StripShared& ws, i
   const double alpha = A.alpha;
   double* __restrict__ Xo = A.xout[rd ^ 1] + so;
   double* __restrict__ Lo = A.lout[rd ^ 1] + so;
-  const double* Xin = Xg;
   const double* Lin = Lg;
   // the instance's constants in registers (the loop's stores could alias the
   // descriptor table as far as the compiler knows)
@@ -203,16 +217,18 @@ __device__ __forceinline__ void strip_body(const IterArgs& A, StripShared& ws, i
       double srcd = 0.0;
       float srcf = 0.0f;
       T inj = T(0);
-      while (na < n_act && ws.act[na].row < rj) ++na;  // entries of rows before the strip's start
-      while (na < n_act && ws.act[na].row == rj) {
-        const StripAct e = ws.act[na];
-        if (e.lane == lane) {
-          const double ua = uin_s[e.a];
-          if constexpr (full) srcd += ua;
-          else srcf += d2f(ua);
-          inj += (T)v3_s[e.a];
+      if (rj == next_row) {  // warp-uniform
+        while (na < n_act && ws.act[na].row == rj) {
+          const StripAct e = ws.act[na];
+          if (e.lane == lane) {
+            const double ua = uin_s[e.a];
+            if constexpr (full) srcd += ua;
+            else srcf += d2f(ua);
+            inj += (T)v3_s[e.a];
+          }
+          ++na;
         }
-        ++na;
+        next_row = na < n_act ? ws.act[na].row : 0x7fffffff;
       }
       const double* rs = slot(rj, 0);
       const double x = rs[R_X * 32], lam = rs[R_L * 32], xp = rs[R_XP * 32], rc = rs[R_RF * 32];
@@ -239,11 +255,17 @@ __device__ __forceinline__ void strip_body(const IterArgs& A, StripShared& ws, i
         const float dphi = fk0 * (1.0f + fk1 * xv);
         const float t1 = fh * (lphi + fb0 * srcf);
         const float t3 = fh * (fq * (xv - rv) + dphi * mu);
-        const double d3 = last ? -lam : rs[R_LN * 32] - lam;
-        const float dx = d2f(xp - x), dl = d2f(d3);
+        // the O(1) differences in float32 from the truncated values (the
+        // float64 pipe issues 2 lanes per clock per SM; their rounding enters
+        // the bound, and the float64 residual certifies convergence); at the
+        // last stage lambda_{N+1} = h qf (x_N - ref) is an O(h) term
+        const float xpf = d2f(xp), lnf = last ? 0.0f : d2f(rs[R_LN * 32]);
+        const float dx = xpf - xv, dl = lnf - laf.w1;
         const float K1f = dx + t1;
         const float K3f = dl + t3 + hqff * (xv - rv);
         const float K1v = own ? K1f : 0.0f, K3v = own ? K3f : 0.0f;
+        nm.mg.x = fmaxf(nm.mg.x, own ? fabsf(xpf) : 0.0f);
+        nm.mg.y = fmaxf(nm.mg.y, own ? fabsf(lnf) : 0.0f);
         nm.mg.z = fmaxf(nm.mg.z, own ? fmaxf(fabsf(dx), fabsf(dl)) : 0.0f);
         nm.mg.w = fmaxf(nm.mg.w, own ? fabsf(rv) : 0.0f);
         nm.fmax = fmax_nan(nm.fmax, fmax_nan(fabsf(K1v), fabsf(K3v)));
@@ -265,8 +287,9 @@ __device__ __forceinline__ void strip_body(const IterArgs& A, StripShared& ws, i
         if (own_lane && rj >= E && rj < RH - E && gy < my) {
           const int c = gy * mx + gx;
           const T w = (-K3 - ax * v1) * rg;
-          Xo[c] = fma(alpha, to_double(v1), Xin[c]);
-          Lo[c] = fma(alpha, to_double(w), Lin[c]);
+          const double* rs = slot(rj, 0);
+          Xo[c] = fma(alpha, to_double(v1), rs[R_X * 32]);
+          Lo[c] = fma(alpha, to_double(w), rs[R_L * 32]);
         }
       } else {
         // ---- pass 1's output: the first F_x sweep's field (or w1 for n_lo = 1) ----
@@ -304,8 +327,9 @@ __device__ __forceinline__ void strip_body(const IterArgs& A, StripShared& ws, i
             if (own_lane && rj >= E && rj < RH - E && gy < my) {
               const int c = gy * mx + gx;
               const T v5m = sv5.d[E - n_lo - 1];
-              Xo[c] = fma(alpha, to_double(v5m), Xin[c]);
-              Lo[c] = fma(alpha, to_double(v4), Lin[c]);
+              const double* rs = slot(rj, 0);  // still in the ring
+              Xo[c] = fma(alpha, to_double(v5m), rs[R_X * 32]);
+              Lo[c] = fma(alpha, to_double(v4), rs[R_L * 32]);
             }
           }
         }
@@ -376,7 +400,7 @@ __device__ __forceinline__ void strip_body(const IterArgs& A, StripShared& ws, i
     if constexpr (!full) {
       float usum = 0.0f;
       for (int a = 0; a < nu; ++a) usum += fabsf(d2f(A.uin[rd][I.u_off + (long long)s * nu + a]));
-      e = split_bound(I, last, mags, usum);
+      e = split_bound(I, last, mags, usum, true);
     }
     publish_residual(A, slot_k, b, k, rmax, rsq, e, full);
   }
@@ -386,11 +410,11 @@ __device__ __forceinline__ void strip_body(const IterArgs& A, StripShared& ws, i
 // *iter_k + j with the convergence bookkeeping; MODE_ONESHOT: one residual or
 // iteration from the given buffers), after k_patch of the same iteration.
 template <typename T, int n_lo>
-__global__ void __launch_bounds__(STRIP_WARPS * 32) k_strip(IterArgs A, int MODE, int j_launch) {
+__global__ void __launch_bounds__(STRIP_WARPS * 32, STRIP_MIN_BLOCKS) k_strip(IterArgs A, int MODE, int j_launch) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  StripShared& ws = *reinterpret_cast<StripShared*>(
-      smem_raw + warp * ((sizeof(StripShared) + 15) & ~size_t(15)));
+  using WS = StripShared<strip_ring_rows(n_lo)>;
+  WS& ws = *reinterpret_cast<WS*>(smem_raw + warp * ((sizeof(WS) + 15) & ~size_t(15)));
   pdl_trigger();
   const int k = (MODE == MODE_SOLVE) ? *(volatile int*)A.iter_k + j_launch : 0;
   const int rd = (MODE == MODE_SOLVE) ? (k & 1) : 0;
