@@ -601,14 +601,21 @@ __device__ __noinline__ void control_decision(const IterArgs& A, int b, int s, i
 // rounding, a few u relative, is far inside the factor 16) and rounded up by
 // 1%.  mags: X, Lm, max |difference or K2|, max |ref|; usum: sum over the
 // stage's controls of |u| (float32).
+// With Gm >= 0 the Laplacian of Phi is instead summed in difference form,
+// sum_n c_n k0 (x_n - x_c)(1 + k1/2 (x_n + x_c)), from the truncated values:
+// each term is off by k0 (1 + |k1| X)(4u X + 7u Gm), Gm the largest
+// neighbour difference, so that part of S is dcoef k0 (1 + |k1| X)(4 X + 7
+// Gm) / 8 (no cancellation of the O(dcoef Phi) terms).
 __device__ __forceinline__ double split_bound(const InstDev& I, bool last, const float* mags,
-                                              float usum, bool diff32 = false) {
+                                              float usum, bool diff32 = false, float Gm = -1.0f) {
   const float u32 = 5.9604645e-08f;
   const float Xm = mags[0], Lm = mags[1], Dm = mags[2], Rm = mags[3];
   const float ak0 = fabsf(I.fk0), ak1 = fabsf(I.fk1);
   const float pmax = ak0 * (Xm + 0.5f * ak1 * Xm * Xm);
   const float dpmax = ak0 * (1.0f + ak1 * Xm);
-  const float S = 2.0f * I.fdc * (pmax + dpmax * Lm) + fabsf(I.fb0) * usum +
+  const float phi_part = (Gm >= 0.0f) ? I.fdc * dpmax * (4.0f * Xm + 7.0f * Gm) * 0.125f
+                                      : 2.0f * I.fdc * pmax;
+  const float S = phi_part + 2.0f * I.fdc * dpmax * Lm + fabsf(I.fb0) * usum +
                   (I.fq + (last ? I.fhqf / I.fh : 0.0f)) * (Xm + Rm);
   const float Dterm = 3.0f * Dm + (diff32 ? 4.0f * fmaxf(Xm, Lm) : 0.0f);
   return f2d(1.01f * u32 * (Dterm + 16.0f * I.fh * S));

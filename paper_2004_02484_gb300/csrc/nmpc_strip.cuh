@@ -104,22 +104,41 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
   const bool own_lane = lane >= E && lane < 32 - E && gx_ok;
   const int gy0 = y0 - E;
 
-  // actuators in reach, sorted by (row, lane, index): lane 0 builds the list
-  if (lane == 0) {
-    int n = 0;
-    for (int a = 0; a < nu; ++a) {
-      const int c = A.act[I.act_off + a];
-      const int rl = c % I.mx - (x0 - E), rr = c / I.mx - gy0;
-      if (rl >= 0 && rl < 32 && rr >= 0 && rr < RH) {
-        int p = n++;
-        while (p > 0 && (ws.act[p - 1].row > rr || (ws.act[p - 1].row == rr && ws.act[p - 1].lane > rl))) {
-          ws.act[p] = ws.act[p - 1];
-          --p;
-        }
-        ws.act[p] = StripAct{rr, rl, a, 0};
+  // actuators in reach, sorted by (row, lane, index): lane l looks at
+  // actuators l and l + 32 (n_u <= 64), each candidate's rank is the number
+  // of smaller keys across the warp
+  {
+    const float inv_mx = 1.0f / (float)I.mx;
+    long long key[2];
+    int rr[2], rl[2];
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+      const int a = lane + 32 * h2;
+      key[h2] = 0x7fffffffffffffffLL;
+      rr[h2] = rl[h2] = 0;
+      if (a < nu) {
+        const int c = A.act[I.act_off + a];
+        const int cy = fdiv(c, I.mx, inv_mx), cx = c - cy * I.mx;
+        rl[h2] = cx - (x0 - E);
+        rr[h2] = cy - gy0;
+        if (rl[h2] >= 0 && rl[h2] < 32 && rr[h2] >= 0 && rr[h2] < RH)
+          key[h2] = ((long long)rr[h2] * 32 + rl[h2]) * MAX_NU + a;
       }
     }
-    ws.n_act = n;
+    int rank[2] = {0, 0};
+    for (int l = 0; l < 32; ++l) {
+      const long long k0 = __shfl_sync(0xffffffffu, key[0], l);
+      const long long k1 = __shfl_sync(0xffffffffu, key[1], l);
+#pragma unroll
+      for (int h2 = 0; h2 < 2; ++h2) rank[h2] += (k0 < key[h2]) + (k1 < key[h2]);
+    }
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2)
+      if (key[h2] != 0x7fffffffffffffffLL)
+        ws.act[rank[h2]] = StripAct{rr[h2], rl[h2], lane + 32 * h2, 0};
+    const int n = __popc(__ballot_sync(0xffffffffu, key[0] != 0x7fffffffffffffffLL)) +
+                  __popc(__ballot_sync(0xffffffffu, key[1] != 0x7fffffffffffffffLL));
+    if (lane == 0) ws.n_act = n;
   }
   __syncwarp();
   const int n_act = ws.n_act;
@@ -133,19 +152,24 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
   const double* LNg = A.lin[rd] + so + I.ng;
   const double* RFg = A.ref + I.g_off;
   double* ring = ws.ring + lane;
-  auto slot = [&](int rj, int f) -> double* {
-    return ring + (((rj + RING) % RING) * SREC + f) * 32;  // rj >= -1
+  // ring row of j + d for the current step j (sj = j mod RING), -RING < d < RING
+  int sj = 0;
+  auto slot_at = [&](int d, int f) -> double* {
+    int q = sj + d;
+    q = q < 0 ? q + RING : (q >= RING ? q - RING : q);
+    return ring + (q * SREC + f) * 32;
   };
   // row rj's five inputs; cells outside the grid and rows past the region
   // are zero-filled by the copies themselves (source size 0, from a clamped
   // address inside the grid)
   const int gxc = min(max(gx, 0), I.mx - 1);
   const int mx = I.mx, my = I.my;
-  auto fetch = [&](int rj) {
+  // row rj = j + dj of the current step j
+  auto fetch = [&](int rj, int dj) {
     const int gy = gy0 + rj;
     const bool ok = gx_ok && gy >= 0 && gy < my && rj < RH;
     const int c = min(max(gy, 0), my - 1) * mx + gxc;
-    double* d = slot(rj, 0);
+    double* d = slot_at(dj, 0);
     cp_async8_zfill(d + R_X * 32, Xg + c, ok);
     cp_async8_zfill(d + R_L * 32, Lg + c, ok);
     cp_async8_zfill(d + R_XP * 32, XPg + c, ok);
@@ -154,7 +178,7 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
     asm volatile("cp.async.commit_group;\n" ::);
   };
 #pragma unroll
-  for (int q = 0; q < STRIP_AHEAD; ++q) fetch(q);
+  for (int q = 0; q < STRIP_AHEAD; ++q) fetch(q, q);  // before step 0 (sj = 0)
 
   const T th = pick<T>(I.h, I.fh), tdc = pick<T>(I.dcoef, I.fdc), tb0 = pick<T>(I.b0, I.fb0);
   const T tcx = pick<T>(I.cx, I.fcx), tcy = pick<T>(I.cy, I.fcy);
@@ -172,10 +196,10 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
   const double* uin_s = A.uin[rd] + I.u_off + (long long)s * nu;
   const double* v3_s = A.v3g + I.u_off + (long long)s * nu;
 
-  Norms nm{0.0f, 0.0f, make_float4(0.f, 0.f, 0.f, 0.f), 0.0, 0.0};
+  Norms nm{0.0f, 0.0f, make_float4(0.f, 0.f, 0.f, 0.f), 0.0, 0.0, 0.0f};
   // pass 0 windows (float64 in the full residual, float32 in the split one)
   Win<double> phd{0.0, 0.0, 0.0}, lad{0.0, 0.0, 0.0};
-  Win<float> phf{0.f, 0.f, 0.f}, laf{0.f, 0.f, 0.f}, xvf{0.f, 0.f, 0.f};
+  Win<float> laf{0.f, 0.f, 0.f}, xvf{0.f, 0.f, 0.f};
   // sweep fields: pw[m] is the window of pass m + 1's output (m = 0 .. E - 2)
   Win<T> pw[E > 1 ? E - 1 : 1];
 #pragma unroll
@@ -187,17 +211,16 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
 
   const int steps = RH + E;
   for (int j = 0; j < steps; ++j) {
-    fetch(j + STRIP_AHEAD);
+    fetch(j + STRIP_AHEAD, STRIP_AHEAD);
     asm volatile("cp.async.wait_group %0;\n" ::"n"(STRIP_AHEAD));
     // ---- pass 0: row j ----
     {
-      const double x = *slot(j, R_X), l = *slot(j, R_L);
+      const double x = *slot_at(0, R_X), l = *slot_at(0, R_L);
       if constexpr (full) {
         phd.push(k0d * (x + 0.5 * k1d * x * x));
         lad.push(l);
       } else {
         const float xv = d2f(x), lf = d2f(l);
-        phf.push(fk0 * (xv + fk1h * xv * xv));
         laf.push(lf);
         xvf.push(xv);
         if (j < RH) {
@@ -230,7 +253,7 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
         }
         next_row = na < n_act ? ws.act[na].row : 0x7fffffff;
       }
-      const double* rs = slot(rj, 0);
+      const double* rs = slot_at(-1, 0);
       const double x = rs[R_X * 32], lam = rs[R_L * 32], xp = rs[R_XP * 32], rc = rs[R_RF * 32];
       T K1;
       if constexpr (full) {
@@ -249,9 +272,16 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
         dp = to_T<T>(dphi);
         ax = to_T<T>(hd * (qd + k0d * k1d * mu) + (last ? hqfd : 0.0));
       } else {
-        const float lphi = phf.nsum(fcx, fcy) - fdc * phf.w1;
-        const float mu = laf.nsum(fcx, fcy) - fdc * laf.w1;
+        // Lap Phi(x) in difference form, sum_n c_n k0 (x_n - x_c)(1 + k1/2
+        // (x_n + x_c)): no cancellation of the O(dcoef Phi) terms, so its
+        // rounding bound scales with the neighbour differences
         const float xv = xvf.w1, rv = d2f(rc);
+        const float xl = __shfl_up_sync(0xffffffffu, xv, 1), xr = __shfl_down_sync(0xffffffffu, xv, 1);
+        const float dlx = xl - xv, drx = xr - xv, dux = xvf.w0 - xv, ddx = xvf.w2 - xv;
+        const float lphi =
+            fk0 * (fcx * (dlx * (1.0f + fk1h * (xl + xv)) + drx * (1.0f + fk1h * (xr + xv))) +
+                   fcy * (dux * (1.0f + fk1h * (xvf.w0 + xv)) + ddx * (1.0f + fk1h * (xvf.w2 + xv))));
+        const float mu = laf.nsum(fcx, fcy) - fdc * laf.w1;
         const float dphi = fk0 * (1.0f + fk1 * xv);
         const float t1 = fh * (lphi + fb0 * srcf);
         const float t3 = fh * (fq * (xv - rv) + dphi * mu);
@@ -264,6 +294,8 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
         const float K1f = dx + t1;
         const float K3f = dl + t3 + hqff * (xv - rv);
         const float K1v = own ? K1f : 0.0f, K3v = own ? K3f : 0.0f;
+        nm.gm = fmaxf(nm.gm, own ? fmaxf(fmaxf(fabsf(dlx), fabsf(drx)), fmaxf(fabsf(dux), fabsf(ddx)))
+                                 : 0.0f);
         nm.mg.x = fmaxf(nm.mg.x, own ? fabsf(xpf) : 0.0f);
         nm.mg.y = fmaxf(nm.mg.y, own ? fabsf(lnf) : 0.0f);
         nm.mg.z = fmaxf(nm.mg.z, own ? fmaxf(fabsf(dx), fabsf(dl)) : 0.0f);
@@ -287,7 +319,7 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
         if (own_lane && rj >= E && rj < RH - E && gy < my) {
           const int c = gy * mx + gx;
           const T w = (-K3 - ax * v1) * rg;
-          const double* rs = slot(rj, 0);
+          const double* rs = slot_at(-1, 0);
           Xo[c] = fma(alpha, to_double(v1), rs[R_X * 32]);
           Lo[c] = fma(alpha, to_double(w), rs[R_L * 32]);
         }
@@ -327,7 +359,7 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
             if (own_lane && rj >= E && rj < RH - E && gy < my) {
               const int c = gy * mx + gx;
               const T v5m = sv5.d[E - n_lo - 1];
-              const double* rs = slot(rj, 0);  // still in the ring
+              const double* rs = slot_at(-E, 0);  // still in the ring
               Xo[c] = fma(alpha, to_double(v5m), rs[R_X * 32]);
               Lo[c] = fma(alpha, to_double(v4), rs[R_L * 32]);
             }
@@ -342,6 +374,7 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
     sk3.push(K3);
     sax.push(ax);
     sv1.push(v1);
+    sj = (sj + 1 == RING) ? 0 : sj + 1;
   }
   asm volatile("cp.async.wait_all;\n" ::);
 
@@ -377,9 +410,10 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
     rmax = vm;
     rsq = vs;
   } else {
-    float fm = nm.fmax, fs = nm.fsq;
+    float fm = nm.fmax, fs = nm.fsq, gm = nm.gm;
     float4 mg = nm.mg;
     for (int o = 16; o > 0; o >>= 1) {
+      gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, o));
       fm = fmax_nan(fm, __shfl_xor_sync(0xffffffffu, fm, o));
       fs += __shfl_xor_sync(0xffffffffu, fs, o);
       mg.x = fmaxf(mg.x, __shfl_xor_sync(0xffffffffu, mg.x, o));
@@ -393,6 +427,7 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
     mags[1] = mg.y;
     mags[2] = mg.z;
     mags[3] = mg.w;
+    nm.gm = gm;
   }
   if (lane == 0) {
     const int slot_k = (k % RES_SLOTS) * A.n_inst + b;
@@ -400,7 +435,7 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
     if constexpr (!full) {
       float usum = 0.0f;
       for (int a = 0; a < nu; ++a) usum += fabsf(d2f(A.uin[rd][I.u_off + (long long)s * nu + a]));
-      e = split_bound(I, last, mags, usum, true);
+      e = split_bound(I, last, mags, usum, true, nm.gm);
     }
     publish_residual(A, slot_k, b, k, rmax, rsq, e, full);
   }

@@ -33,6 +33,7 @@ struct Norms {
   float fmax, fsq;
   float4 mg;
   double vmax, vsq;
+  float gm;  // largest neighbour difference of x (difference-form Laplacian)
 };
 
 template <int NT>
