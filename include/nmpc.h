@@ -120,7 +120,7 @@ typedef struct {
                       waits; a wait that runs out restarts the solve with
                       one launch per iteration); the iterates are identical
                       to those of 0: one launch per iteration (default)     */
-  int tiled;       /* 2D instances on the strip path: each warp computes a
+  int strips;       /* 2D instances on the strip path: each warp computes a
                       strip of 32 - 2E own columns (E = 2 n_lo - 1) from a
                       region extended by E cells, walking down its rows with
                       every lower-layer pass pipelined in registers
@@ -131,7 +131,7 @@ typedef struct {
                       instance, 2 = never.  Eligible: n_lo <= 4, and for
                       n_u_it > 1 no two actuators on one cell or within
                       2 (n_lo - 1) cells (Manhattan) of each other          */
-  int tile_rows;   /* own rows per strip (0..65535); 0 = auto (whole columns
+  int strip_rows;   /* own rows per strip (0..65535); 0 = auto (whole columns
                       when the batch gives enough strips, else shorter
                       strips, at least 16 rows)                             */
 } nmpc_opts;
@@ -147,8 +147,8 @@ typedef struct nmpc_handle nmpc_handle;
 
 /* Fill *o with defaults: tol 1e-6, max_iter 2000, n_lo 2, n_u_it 2, FP64,
    check_every 16, alpha 1, div_limit 1e8, threads auto, graph on, cluster
-   auto, split_min 1e-7, u_local 0, cells auto, persistent 0, tiled auto,
-   tile_rows auto. */
+   auto, split_min 1e-7, u_local 0, cells auto, persistent 0, strips auto,
+   strip_rows auto. */
 void nmpc_default_opts(nmpc_opts* o);
 
 /* Validate the descriptors, build the device instance table and allocate the
@@ -285,19 +285,19 @@ int64_t nmpc_launch_count(const nmpc_handle* h);
    launch, out[7] 1 if the u-iteration uses local responses, out[8] clusters
    of this shape the device keeps resident at once for the persistent
    launch, out[9] work items (instance stages) on the cluster path (the
-   tile path's are in nmpc_tile_plan), out[10] iteration steps launched
+   strip path's are in nmpc_strip_plan), out[10] iteration steps launched
    (one per iteration, whichever kernels it takes; one per solve when
    persistent) since setup.  Returns NMPC_ERR_BAD_ARG for a null handle or array. */
 int nmpc_launch_plan(const nmpc_handle* h, int64_t* out);
 
-/* Strip path of the handle (opts.tiled): out[0] strips per iteration (work
+/* Strip path of the handle (opts.strips): out[0] strips per iteration (work
    items of k_strip, one warp each), out[1] own columns and out[2] own rows
    per strip, out[3] threads per CTA, out[4] dynamic shared memory per CTA
    (bytes), out[5] actuator patches per iteration (k_patch work items, one
    warp each), out[6] instances on the strip path, out[7] cells of a
    strip's extended region.  All zero when no instance
-   is on the tile path.  NMPC_ERR_BAD_ARG for NULL arguments. */
-int nmpc_tile_plan(const nmpc_handle* h, int64_t* out);
+   is on the strip path.  NMPC_ERR_BAD_ARG for NULL arguments. */
+int nmpc_strip_plan(const nmpc_handle* h, int64_t* out);
 
 /* Allocation-free solve of ONE instance (no counterpart in the paper; it
    exists for callers that may not allocate device memory when they solve:

@@ -91,12 +91,12 @@ struct nmpc_handle {
   // the whole iteration loop as one graph: a WHILE node over chunks
   cudaGraphExec_t loop_exec = nullptr;
   int loop_chunk = 0;
-  // tile path (k_tile)
-  int4* tiles_d = nullptr;
-  int n_tiles = 0;
-  int tile_x = 0, tile_y = 0, tile_threads = 0, tile_region = 0;
-  int n_tile_inst = 0;
-  size_t tile_smem = 0;
+  // strip path (k_patch + k_strip)
+  int4* strips_d = nullptr;
+  int n_strips = 0;
+  int strip_x = 0, strip_y = 0, strip_threads = 0, strip_region = 0;
+  int n_strip_inst = 0;
+  size_t strip_smem = 0;
   int4* patches_d = nullptr;  // k_patch work items
   int n_patches = 0;
   size_t patch_smem = 0;
@@ -137,7 +137,7 @@ void free_all(nmpc_handle* h) {
                   h->xb[0], h->xb[1], h->xb[2], h->ub[0], h->ub[1], h->ub[2],
                   h->lb[0], h->lb[1], h->lb[2], h->ictl, h->res_inf, h->res_err, h->res_sq,
                   h->res_first, h->status, h->iters, h->final_buf, h->fin_inf,
-                  h->fin_2, h->full_from, h->full0, h->scratch, h->tiles_d, h->patches_d,
+                  h->fin_2, h->full_from, h->full0, h->scratch, h->strips_d, h->patches_d,
                   h->v3_d};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -193,10 +193,10 @@ IterArgs make_args(nmpc_handle* h) {
   A.box_r = h->box_r;
   A.scratch = h->smem_mode ? nullptr : h->scratch;
   A.scratch_stride = h->scratch_stride;
-  A.tiles = h->tiles_d;
-  A.n_tiles = h->n_tiles;
-  A.tile_x = h->tile_x;
-  A.tile_y = h->tile_y;
+  A.strips = h->strips_d;
+  A.n_strips = h->n_strips;
+  A.strip_x = h->strip_x;
+  A.strip_y = h->strip_y;
   A.patches = h->patches_d;
   A.n_patches = h->n_patches;
   A.v3g = h->v3_d;
@@ -489,7 +489,7 @@ LaunchPlan plan_of(const nmpc_handle* h) {
 using TileKernel = void (*)(IterArgs, int, int);
 
 template <typename T>
-TileKernel tile_kernel(int n_lo) {
+TileKernel strip_kernel(int n_lo) {
   switch (n_lo) {
     case 1: return nmpc_dev::k_strip<T, 1>;
     case 2: return nmpc_dev::k_strip<T, 2>;
@@ -527,22 +527,22 @@ cudaError_t launch_patch(const nmpc_handle* h, const IterArgs& A, cudaStream_t s
 }
 
 template <typename T>
-cudaError_t launch_tile(const nmpc_handle* h, const IterArgs& A, cudaStream_t st, int mode, int j) {
+cudaError_t launch_strip(const nmpc_handle* h, const IterArgs& A, cudaStream_t st, int mode, int j) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)((h->n_tiles + nmpc_dev::STRIP_WARPS - 1) / nmpc_dev::STRIP_WARPS));
-  cfg.blockDim = dim3((unsigned)h->tile_threads);
-  cfg.dynamicSmemBytes = h->tile_smem;
+  cfg.gridDim = dim3((unsigned)((h->n_strips + nmpc_dev::STRIP_WARPS - 1) / nmpc_dev::STRIP_WARPS));
+  cfg.blockDim = dim3((unsigned)h->strip_threads);
+  cfg.dynamicSmemBytes = h->strip_smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = (mode == nmpc_dev::MODE_SOLVE) ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, tile_kernel<T>(h->opts.n_lo), A, mode, j);
+  return cudaLaunchKernelEx(&cfg, strip_kernel<T>(h->opts.n_lo), A, mode, j);
 }
 
 // One iteration (or one-shot pass): the cluster kernel over the cluster
-// path's work items and the tile kernel over the tiles, whichever exist.
+// path's work items and the strip kernels over the strips, whichever exist.
 template <int MODE>
 cudaError_t launch_iterate(nmpc_handle* h, const IterArgs& A, cudaStream_t st, int j = 0) {
   h->iter_launches++;
@@ -553,7 +553,7 @@ cudaError_t launch_iterate(nmpc_handle* h, const IterArgs& A, cudaStream_t st, i
     e = h->mixed ? launch_k<float>(P, A, st, MODE, j) : launch_k<double>(P, A, st, MODE, j);
     if (e != cudaSuccess) return e;
   }
-  if (h->n_tiles > 0) {
+  if (h->n_strips > 0) {
     // the actuators' v3 first (not needed by a residual-only pass)
     if (!(MODE == nmpc_dev::MODE_ONESHOT && A.resid_only)) {
       h->launches++;
@@ -561,7 +561,7 @@ cudaError_t launch_iterate(nmpc_handle* h, const IterArgs& A, cudaStream_t st, i
       if (e != cudaSuccess) return e;
     }
     h->launches++;
-    e = h->mixed ? launch_tile<float>(h, A, st, MODE, j) : launch_tile<double>(h, A, st, MODE, j);
+    e = h->mixed ? launch_strip<float>(h, A, st, MODE, j) : launch_strip<double>(h, A, st, MODE, j);
   }
   return e;
 }
@@ -598,7 +598,7 @@ cudaError_t configure_kernels(size_t smem) {
     if (e != cudaSuccess) return e;
   }
   for (int n_lo = 1; n_lo <= 4; ++n_lo) {
-    cudaError_t e = cudaFuncSetAttribute(tile_kernel<T>(n_lo),
+    cudaError_t e = cudaFuncSetAttribute(strip_kernel<T>(n_lo),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(patch_kernel<T>(n_lo), cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -608,11 +608,11 @@ cudaError_t configure_kernels(size_t smem) {
   return cudaSuccess;
 }
 
-// Whether instance I may run on the tile path: 2D, n_lo <= 4, and for
+// Whether instance I may run on the strip path: 2D, n_lo <= 4, and for
 // n_u_it > 1 actuators on distinct cells more than 2 (n_lo - 1) cells apart
 // (Manhattan), so that each actuator's u-iteration sees only its own
 // response.
-bool tile_eligible(const InstDev& I, const int* act, const nmpc_opts& o) {
+bool strip_eligible(const InstDev& I, const int* act, const nmpc_opts& o) {
   if (I.dim != 2 || o.n_lo > 4) return false;
   if (o.n_u_it > 1) {
     const int reach = 2 * (o.n_lo - 1);
@@ -646,8 +646,8 @@ bool opts_ok(const nmpc_opts& o) {
          (o.precision == NMPC_FP64 || o.precision == NMPC_MIXED) && o.threads >= 0 &&
          o.threads <= 512 && (o.threads % 32) == 0 && o.cluster >= 0 && o.cluster <= 16 &&
          (o.cluster <= 8 || o.cluster == 16) && (o.split_min >= 0) &&
-         (o.cells >= 0 && o.cells <= 8) && (o.tiled >= 0 && o.tiled <= 2) &&
-         (o.tile_rows >= 0 && o.tile_rows <= 65535);
+         (o.cells >= 0 && o.cells <= 8) && (o.strips >= 0 && o.strips <= 2) &&
+         (o.strip_rows >= 0 && o.strip_rows <= 65535);
 }
 
 int validate(const nmpc_desc* d) {
@@ -1119,8 +1119,8 @@ void nmpc_default_opts(nmpc_opts* o) {
   o->u_local = 0;
   o->cells = 0;
   o->persistent = 0;
-  o->tiled = 0;
-  o->tile_rows = 0;
+  o->strips = 0;
+  o->strip_rows = 0;
 }
 
 int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
@@ -1196,24 +1196,24 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
   // instances on the strip path, and the strip shape (shared by all of
   // them): 32 - 2E own columns (one warp lane per region column) and ty own
   // rows, by default enough strips for about four waves of warps
-  std::vector<char> on_tiles(n_instances, 0);
+  std::vector<char> on_strips(n_instances, 0);
   const int E = 2 * o.n_lo - 1;
   const int tx = 32 - 2 * E;
   int ty = 0;
-  if (o.tiled != 2) {
+  if (o.strips != 2) {
     int my_max = 0;
     long long whole = 0;  // strips with whole columns
     for (int b = 0; b < n_instances; ++b) {
       const InstDev& I = h->inst_h[b];
-      if (!tile_eligible(I, act_all.data() + I.act_off, o)) continue;
-      if (o.tiled == 0 && fits_cluster_staged(I, o, h->mixed, max_optin)) continue;
-      on_tiles[b] = 1;
+      if (!strip_eligible(I, act_all.data() + I.act_off, o)) continue;
+      if (o.strips == 0 && fits_cluster_staged(I, o, h->mixed, max_optin)) continue;
+      on_strips[b] = 1;
       my_max = std::max(my_max, I.my);
       whole += (long long)I.N * ((I.mx + tx - 1) / tx);
     }
     if (my_max > 0) {
-      if (o.tile_rows) {
-        ty = std::min(o.tile_rows, my_max);
+      if (o.strip_rows) {
+        ty = std::min(o.strip_rows, my_max);
       } else {
         const long long target = 4LL * std::max(1, h->num_sms) * 32;
         const long long segs = std::max(1LL, (target + whole - 1) / whole);
@@ -1222,15 +1222,15 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
     }
   }
   std::vector<int2> work;
-  std::vector<int4> tiles, patches;
+  std::vector<int4> strips, patches;
   std::vector<InstDev> cl_inst;
   for (int b = 0; b < n_instances; ++b) {
     const InstDev& I = h->inst_h[b];
-    if (on_tiles[b]) {
-      h->n_tile_inst++;
+    if (on_strips[b]) {
+      h->n_strip_inst++;
       for (int s = 0; s < I.N; ++s) {
         for (int y0 = 0; y0 < I.my; y0 += ty)
-          for (int x0 = 0; x0 < I.mx; x0 += tx) tiles.push_back(make_int4(b, s, x0, y0));
+          for (int x0 = 0; x0 < I.mx; x0 += tx) strips.push_back(make_int4(b, s, x0, y0));
         for (int a = 0; a < I.nu; ++a) patches.push_back(make_int4(b, s, a, 0));
       }
     } else {
@@ -1239,24 +1239,24 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
     }
   }
   h->n_work = (int)work.size();
-  h->n_tiles = (int)tiles.size();
+  h->n_strips = (int)strips.size();
   h->n_patches = (int)patches.size();
-  if (h->n_tiles > 0) {
-    h->tile_x = tx;
-    h->tile_y = ty;
-    h->tile_threads = 32 * nmpc_dev::STRIP_WARPS;
-    h->tile_region = 32 * (ty + 2 * E);
+  if (h->n_strips > 0) {
+    h->strip_x = tx;
+    h->strip_y = ty;
+    h->strip_threads = 32 * nmpc_dev::STRIP_WARPS;
+    h->strip_region = 32 * (ty + 2 * E);
     const size_t ws_bytes =
         o.n_lo <= 1   ? sizeof(nmpc_dev::StripShared<nmpc_dev::strip_ring_rows(1)>)
         : o.n_lo == 2 ? sizeof(nmpc_dev::StripShared<nmpc_dev::strip_ring_rows(2)>)
         : o.n_lo == 3 ? sizeof(nmpc_dev::StripShared<nmpc_dev::strip_ring_rows(3)>)
                       : sizeof(nmpc_dev::StripShared<nmpc_dev::strip_ring_rows(4)>);
-    h->tile_smem = nmpc_dev::STRIP_WARPS * ((ws_bytes + 15) & ~size_t(15));
+    h->strip_smem = nmpc_dev::STRIP_WARPS * ((ws_bytes + 15) & ~size_t(15));
     const size_t P2 = (size_t)(2 * E + 1) * (2 * E + 1);
     h->patch_smem = PATCH_WARPS * (((sizeof(nmpc_dev::PatchShared) + 15) & ~size_t(15)) +
                                    8 * P2 * sizeof(double));
-    if (h->tile_smem > (size_t)max_optin || h->patch_smem > (size_t)max_optin) {
-      fprintf(stderr, "nmpc: tile shape needs %zu bytes of shared memory\n", h->tile_smem);
+    if (h->strip_smem > (size_t)max_optin || h->patch_smem > (size_t)max_optin) {
+      fprintf(stderr, "nmpc: strip shape needs %zu bytes of shared memory\n", h->strip_smem);
       delete h;
       return NMPC_ERR_UNSUPPORTED;
     }
@@ -1265,7 +1265,7 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
   if (h->n_work > 0)
     P = plan_launch(cl_inst.data(), (int)cl_inst.size(), h->n_work, o, h->mixed,
                     std::max(1, h->num_sms), max_optin);
-  P.persistent = P.persistent && h->n_tiles == 0;
+  P.persistent = P.persistent && h->n_strips == 0;
   if (h->n_work > 0 && !P.smem_mode) {
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(
@@ -1292,9 +1292,9 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
   auto A = [&](cudaError_t e) { ok = ok && (e == cudaSuccess); };
   A(dev_alloc(&h->inst_d, n_instances));
   A(dev_alloc(&h->work_d, h->n_work));
-  A(dev_alloc(&h->tiles_d, h->n_tiles));
+  A(dev_alloc(&h->strips_d, h->n_strips));
   A(dev_alloc(&h->patches_d, h->n_patches));
-  A(dev_alloc(&h->v3_d, h->n_tiles > 0 ? h->n_u : 0));
+  A(dev_alloc(&h->v3_d, h->n_strips > 0 ? h->n_u : 0));
   A(dev_alloc(&h->act_d, act_all.size()));
   A(dev_alloc(&h->x0_d, h->n_g));
   A(dev_alloc(&h->ref_d, h->n_g));
@@ -1331,8 +1331,8 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
     A(cudaMemcpy(h->inst_d, h->inst_h.data(), n_instances * sizeof(InstDev), cudaMemcpyHostToDevice));
     if (!work.empty())
       A(cudaMemcpy(h->work_d, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice));
-    if (!tiles.empty())
-      A(cudaMemcpy(h->tiles_d, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    if (!strips.empty())
+      A(cudaMemcpy(h->strips_d, strips.data(), strips.size() * sizeof(int4), cudaMemcpyHostToDevice));
     if (!patches.empty())
       A(cudaMemcpy(h->patches_d, patches.data(), patches.size() * sizeof(int4),
                    cudaMemcpyHostToDevice));
@@ -1592,17 +1592,17 @@ int nmpc_sizes(const nmpc_handle* h, int64_t* out) {
 
 int64_t nmpc_launch_count(const nmpc_handle* h) { return h ? h->launches : 0; }
 
-int nmpc_tile_plan(const nmpc_handle* h, int64_t* out) {
+int nmpc_strip_plan(const nmpc_handle* h, int64_t* out) {
   if (!h || !out) return NMPC_ERR_BAD_ARG;
-  const bool on = h->n_tiles > 0;
-  out[0] = h->n_tiles;
-  out[1] = on ? h->tile_x : 0;
-  out[2] = on ? h->tile_y : 0;
-  out[3] = on ? h->tile_threads : 0;
-  out[4] = on ? (int64_t)h->tile_smem : 0;
+  const bool on = h->n_strips > 0;
+  out[0] = h->n_strips;
+  out[1] = on ? h->strip_x : 0;
+  out[2] = on ? h->strip_y : 0;
+  out[3] = on ? h->strip_threads : 0;
+  out[4] = on ? (int64_t)h->strip_smem : 0;
   out[5] = on ? h->n_patches : 0;
-  out[6] = h->n_tile_inst;
-  out[7] = on ? h->tile_region : 0;
+  out[6] = h->n_strip_inst;
+  out[7] = on ? h->strip_region : 0;
   return NMPC_OK;
 }
 

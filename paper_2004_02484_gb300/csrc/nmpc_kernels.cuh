@@ -117,10 +117,11 @@ struct IterArgs {
   // slab of scratch_stride bytes per CTA
   char* scratch;
   long long scratch_stride;
-  // tile path (k_tile): (instance, stage, first column, first row) per tile
-  const int4* tiles;
-  int n_tiles;
-  int tile_x, tile_y;  // own cells per tile
+  // strip path (k_strip): (instance, stage, first own column, first own row)
+  // per strip
+  const int4* strips;
+  int n_strips;
+  int strip_x, strip_y;  // own columns and rows per strip
   // k_patch: (instance, stage, actuator) per warp; v3 per control (float64)
   const int4* patches;
   int n_patches;
@@ -1767,6 +1768,6 @@ __global__ void k_set_weights(InstDev* inst, int n_inst, const double* w) {
   derive(inst[b]);
 }
 
-#include "nmpc_tile.cuh"
+#include "nmpc_patch.cuh"
 
 }  // namespace nmpc_dev

@@ -1,5 +1,5 @@
 // Strip path of the upper-layer iteration for large 2D stages (included from
-// nmpc_kernels.cuh inside namespace nmpc_dev, after nmpc_tile.cuh).
+// nmpc_kernels.cuh inside namespace nmpc_dev, after nmpc_patch.cuh).
 //
 // One warp of k_strip computes one strip of one (instance, stage) work item
 // of iteration k: 32 - 2E own columns (lane = region column, E = 2 n_lo - 1
@@ -97,7 +97,7 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
   const bool last = (s == I.N - 1);
   const long long so = I.s_off + (long long)s * I.ng;
   // region: columns x0 - E + lane, rows y0 - E .. y0 + own_rows + E - 1
-  const int own_rows = min(A.tile_y, I.my - y0);
+  const int own_rows = min(A.strip_y, I.my - y0);
   const int RH = own_rows + 2 * E;
   const int gx = x0 - E + lane;
   const bool gx_ok = gx >= 0 && gx < I.mx;
@@ -455,8 +455,8 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32, STRIP_MIN_BLOCKS) k_strip(It
   const int rd = (MODE == MODE_SOLVE) ? (k & 1) : 0;
   pdl_wait();  // the previous iteration's state, residuals and control words; this one's v3
   const int item = blockIdx.x * STRIP_WARPS + warp;
-  if (item >= A.n_tiles) return;  // warp-uniform; no block barriers in this kernel
-  const int4 it = A.tiles[item];
+  if (item >= A.n_strips) return;  // warp-uniform; no block barriers in this kernel
+  const int4 it = A.strips[item];
   const int b = it.x, s = it.y, x0 = it.z, y0 = it.w;
 
   bool resid_only, full;

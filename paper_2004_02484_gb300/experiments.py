@@ -66,7 +66,7 @@ def closedloop(n: int, steps: int, grid: int, horizon: int, n_sub: int, check: i
     import torch
     insts = wl.heat2d_large_batch(n=n, m=grid, horizon=horizon)
     s = G.Solver(insts, tol=1e-6, precision=G.NMPC_MIXED, max_iter=4000, **opts)
-    tile_plan = G.nmpc_tile_plan(s.h)
+    strip_plan = G.nmpc_strip_plan(s.h)
     w = s.x0.clone()
     nu_tot = sum(len(i.act) for i in insts)
     u_hist = torch.zeros(steps * nu_tot, dtype=torch.float64, device="cuda")
@@ -85,7 +85,7 @@ def closedloop(n: int, steps: int, grid: int, horizon: int, n_sub: int, check: i
            "iters_later_mean": float(iters[1:].mean()) if steps > 1 else None,
            "res_max": float(res.max()), "launches": launches,
            "hbm_gbs_algorithmic": BYTES_PER_CELL_STAGE * cells * iter_launches / dt / 1e9,
-           "tile_plan": tile_plan}
+           "strip_plan": strip_plan}
     if check:
         # one more solve from the final plant state, then its float64 residual
         rc2, st = G.nmpc_solve(s.h, w, s.ref, s.u, n, init=G.NMPC_INIT_SHIFT)
@@ -113,7 +113,7 @@ def solve(n: int, grid: int, horizon: int, reps: int, use_graph: int, **opts):
     out = {"experiment": "solve", "instances": n, "grid": grid, "horizon": horizon,
            "use_graph": use_graph, "rc": rc, "s_per_solve": dt, "iters_mean": float(its.mean()),
            "ms_per_iteration": 1e3 * dt / (int(its.max()) + 1),
-           "tile_plan": G.nmpc_tile_plan(s.h), "launch_plan": G.nmpc_launch_plan(s.h)}
+           "strip_plan": G.nmpc_strip_plan(s.h), "launch_plan": G.nmpc_launch_plan(s.h)}
     s.close()
     return out
 
@@ -189,8 +189,8 @@ def main():
     ap.add_argument("--check", type=int, default=1)
     ap.add_argument("--cluster", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
-    ap.add_argument("--tiled", type=int, default=0)
-    ap.add_argument("--tile-rows", type=int, default=0)
+    ap.add_argument("--strips", type=int, default=0)
+    ap.add_argument("--strip-rows", type=int, default=0)
     ap.add_argument("--n-train", type=int, default=64)
     ap.add_argument("--train-steps", type=int, default=12)
     ap.add_argument("--fit-steps", type=int, default=2000)
@@ -205,15 +205,15 @@ def main():
     if a.which == "batch1d":
         print(json.dumps(batch1d(a.n or 1024)), flush=True)
     elif a.which == "solve":
-        print(json.dumps(solve(a.n or 8, a.grid, a.horizon, a.reps, a.graph, tiled=a.tiled,
-                               tile_rows=a.tile_rows)), flush=True)
+        print(json.dumps(solve(a.n or 8, a.grid, a.horizon, a.reps, a.graph, strips=a.strips,
+                               strip_rows=a.strip_rows)), flush=True)
     elif a.which == "closedloop_learned":
         print(json.dumps(closedloop_learned(a.n_train, a.train_steps, a.n or 8, a.steps, a.grid,
                                             a.horizon, a.n_sub, a.fit_steps, a.rules)), flush=True)
     else:
         res = closedloop(a.n or 64, a.steps, a.grid, a.horizon, a.n_sub, a.check,
-                         cluster=a.cluster, threads=a.threads, tiled=a.tiled,
-                         tile_rows=a.tile_rows)
+                         cluster=a.cluster, threads=a.threads, strips=a.strips,
+                         strip_rows=a.strip_rows)
         res.update({"cluster": a.cluster, "threads": a.threads})
         print(json.dumps(res), flush=True)
 

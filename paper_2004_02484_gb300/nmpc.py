@@ -51,7 +51,7 @@ class nmpc_opts(ctypes.Structure):
                 ("use_graph", ctypes.c_int), ("cluster", ctypes.c_int),
                 ("split_min", ctypes.c_double), ("u_local", ctypes.c_int),
                 ("cells", ctypes.c_int), ("persistent", ctypes.c_int),
-                ("tiled", ctypes.c_int), ("tile_rows", ctypes.c_int)]
+                ("strips", ctypes.c_int), ("strip_rows", ctypes.c_int)]
 
 
 class nmpc_stats(ctypes.Structure):
@@ -61,7 +61,7 @@ class nmpc_stats(ctypes.Structure):
 
 EXPORTED = ["nmpc_default_opts", "nmpc_setup", "nmpc_solve", "nmpc_solve_host",
             "nmpc_residual", "nmpc_iterate", "nmpc_get_state", "nmpc_set_state",
-            "nmpc_sizes", "nmpc_launch_count", "nmpc_launch_plan", "nmpc_tile_plan", "nmpc_start_state", "nmpc_rollout", "nmpc_destroy",
+            "nmpc_sizes", "nmpc_launch_count", "nmpc_launch_plan", "nmpc_strip_plan", "nmpc_start_state", "nmpc_rollout", "nmpc_destroy",
             "nmpc_strerror",
             "nmpc_solve_noalloc", "nmpc_plant_step", "nmpc_closed_loop",
             "nmpc_closed_loop_learned"]
@@ -90,7 +90,7 @@ def _load() -> ctypes.CDLL:
         "nmpc_set_state": (I, [P, P, P, P, P]),
         "nmpc_sizes": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
         "nmpc_launch_plan": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
-        "nmpc_tile_plan": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
+        "nmpc_strip_plan": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
         "nmpc_start_state": (I, [P, I, P, P, P, P, P]),
         "nmpc_rollout": (I, [P, P, P, P, P, P, P]),
         "nmpc_launch_count": (ctypes.c_int64, [P]),
@@ -176,13 +176,13 @@ def nmpc_setup(instances: Sequence, **opts) -> ctypes.c_void_p:
     return h
 
 
-def nmpc_tile_plan(h) -> dict:
-    """The handle's tile path (tiles per iteration, tile shape, threads, shared
+def nmpc_strip_plan(h) -> dict:
+    """The handle's strip path (strips per iteration, strip shape, threads, shared
     memory, actuator patches per iteration, instances on the path, region
     cells)."""
     out = (ctypes.c_int64 * 8)()
-    _check(LIB.nmpc_tile_plan(h, out), "nmpc_tile_plan")
-    keys = ("tiles", "tile_x", "tile_y", "threads", "smem", "patches", "instances", "region")
+    _check(LIB.nmpc_strip_plan(h, out), "nmpc_strip_plan")
+    keys = ("strips", "strip_x", "strip_y", "threads", "smem", "patches", "instances", "region")
     return {k: int(v) for k, v in zip(keys, out)}
 
 

@@ -201,12 +201,12 @@ def test_rollout_matches_its_definition(G):
     s.close()
 
 
-@pytest.mark.parametrize("tiled", [2, 1])
-def test_learned_closed_loop_graph_equals_host_driven_loops(G, tiled):
+@pytest.mark.parametrize("strips", [2, 1])
+def test_learned_closed_loop_graph_equals_host_driven_loops(G, strips):
     """The learned closed loop as one CUDA graph (network kernels captured into
     the step body, rollout, solve, plant) gives the host-driven C loop's and
     the Python-driven loop's iterations and plant states, on the cluster path
-    (tiled 2) and on the strip path (tiled 1)."""
+    (strips 2) and on the strip path (strips 1)."""
     import torch
     from paper_2004_02484_gb300 import warmstart as WS
     train = wl.heat2d_large_batch(n=4, base_seed=7000, m=32, horizon=10)
@@ -216,14 +216,14 @@ def test_learned_closed_loop_graph_equals_host_driven_loops(G, tiled):
     test = wl.heat2d_large_batch(n=2, base_seed=5000, m=32, horizon=10)
     out = []
     for use_graph in (1, 0):
-        s = G.Solver(test, tol=1e-6, precision=1, max_iter=4000, use_graph=use_graph, tiled=tiled)
+        s = G.Solver(test, tol=1e-6, precision=1, max_iter=4000, use_graph=use_graph, strips=strips)
         w = s.x0.clone()
         rc, iters, res = WS.closed_loop_learned_graph(s, lcs, w, 3, 2)
         torch.cuda.synchronize()
         assert rc == G.NMPC_OK and np.all(res <= 1e-6)
         out.append((iters, w.cpu().numpy()))
         s.close()
-    s = G.Solver(test, tol=1e-6, precision=1, max_iter=4000, tiled=tiled)
+    s = G.Solver(test, tol=1e-6, precision=1, max_iter=4000, strips=strips)
     w = s.x0.clone()
     py = WS.closed_loop_learned(s, lcs, w, 3, 2, rule="always", decode="rollout")
     torch.cuda.synchronize()

@@ -42,7 +42,7 @@ def _with_act(inst, rows_cols):
 
 def _batch(far=True):
     """70x20 (strips of 26 columns for n_lo = 2: 26, 26, 18; rows of 8, 8, 4
-    with tile_rows 8), 30x26 (a full and a ragged strip), and a 1D instance
+    with strip_rows 8), 30x26 (a full and a ragged strip), and a 1D instance
     (cluster path).  With `far` the 2D actuators are more than 4 cells apart
     (Manhattan)."""
     a = wl.heat2d(70, 20, 4, 3, 2, seed=91)
@@ -69,7 +69,7 @@ def _rand_state(insts, seed, sx=0.05, su=0.5, sl=1e-4):
 def _iterate(G, insts, state, n_iter, **opts):
     import torch
     h = G.nmpc_setup(insts, **opts)
-    plan = G.nmpc_tile_plan(h)
+    plan = G.nmpc_strip_plan(h)
     x0 = _t(G.pack_fields(insts, "x0"))
     ref = _t(G.pack_fields(insts, "ref"))
     xi, ui, li = (_t(a) for a in state)
@@ -99,14 +99,14 @@ def _split(G, insts, x, u, lam):
 
 
 @pytest.mark.parametrize("n_lo,n_u_it", [(1, 1), (2, 1), (2, 2), (3, 1), (3, 3), (4, 1), (1, 3)])
-def test_tile_iterates_fp64_match_oracle(G, n_lo, n_u_it):
+def test_strip_iterates_fp64_match_oracle(G, n_lo, n_u_it):
     insts = _batch(far=True)
     state, lists = _rand_state(insts, 94)
-    gpu, res, plan = _iterate(G, insts, state, 2, precision=G.NMPC_FP64, tiled=1, tile_rows=8,
+    gpu, res, plan = _iterate(G, insts, state, 2, precision=G.NMPC_FP64, strips=1, strip_rows=8,
                               n_lo=n_lo, n_u_it=n_u_it)
     tx = 32 - 2 * (2 * n_lo - 1)
-    assert plan["instances"] == 2 and plan["tile_x"] == tx and plan["tile_y"] == 8
-    assert plan["tiles"] == 4 * -(-70 // tx) * 3 + 3 * -(-30 // tx) * 4
+    assert plan["instances"] == 2 and plan["strip_x"] == tx and plan["strip_y"] == 8
+    assert plan["strips"] == 4 * -(-70 // tx) * 3 + 3 * -(-30 // tx) * 4
     ora, norms = _oracle(insts, lists, 2, n_lo=n_lo, n_u_it=n_u_it)
     gx, gu, gl = _split(G, insts, *gpu)
     for b in range(len(insts)):
@@ -117,16 +117,16 @@ def test_tile_iterates_fp64_match_oracle(G, n_lo, n_u_it):
         assert abs(res[b, 1] - norms[b][1]) <= 1e-9 * norms[b][1]
 
 
-def test_tile_actuators_close_together_with_one_u_iteration(G):
+def test_strip_actuators_close_together_with_one_u_iteration(G):
     """Neighbouring and adjacent actuators are fine for n_u_it = 1 (each
     control starts from zero); with n_u_it = 2 the instance goes to the
     cluster path and still matches."""
     insts = _batch(far=False)
     state, lists = _rand_state(insts, 95)
-    for n_u_it, on_tiles in ((1, 2), (2, 1)):
-        gpu, _, plan = _iterate(G, insts, state, 2, precision=G.NMPC_FP64, tiled=1, tile_rows=8,
+    for n_u_it, on_strips in ((1, 2), (2, 1)):
+        gpu, _, plan = _iterate(G, insts, state, 2, precision=G.NMPC_FP64, strips=1, strip_rows=8,
                                 n_u_it=n_u_it)
-        assert plan["instances"] == on_tiles
+        assert plan["instances"] == on_strips
         ora, _ = _oracle(insts, lists, 2, n_u_it=n_u_it)
         gx, gu, gl = _split(G, insts, *gpu)
         for b in range(len(insts)):
@@ -135,14 +135,14 @@ def test_tile_actuators_close_together_with_one_u_iteration(G):
                 assert err <= 1e-10, (n_u_it, b, err)
 
 
-@pytest.mark.parametrize("tile_rows", [3, 8, 16])
-def test_tile_iterate_mixed_matches_oracle(G, tile_rows):
+@pytest.mark.parametrize("strip_rows", [3, 8, 16])
+def test_strip_iterate_mixed_matches_oracle(G, strip_rows):
     """Float32 lower layer with the split residual: the update Delta s agrees
     with the oracle's to 1e-4 of its size, the split residual norm to 1e-5."""
     insts = _batch(far=True)
     state, lists = _rand_state(insts, 96)
-    gpu, res, plan = _iterate(G, insts, state, 1, precision=G.NMPC_MIXED, tiled=1,
-                              tile_rows=tile_rows)
+    gpu, res, plan = _iterate(G, insts, state, 1, precision=G.NMPC_MIXED, strips=1,
+                              strip_rows=strip_rows)
     assert plan["instances"] == 2
     ora, norms = _oracle(insts, lists, 1)
     gx, gu, gl = _split(G, insts, *gpu)
@@ -157,22 +157,22 @@ def test_tile_iterate_mixed_matches_oracle(G, tile_rows):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_tile_solve_equals_cluster_solve(G, precision):
-    """Solves to a tolerance on the tile path and on the cluster path: same
+def test_strip_solve_equals_cluster_solve(G, precision):
+    """Solves to a tolerance on the strip path and on the cluster path: same
     iteration counts in FP64 and the same root (controls to 1e-9 relative);
     in mixed precision both stop on a float64 residual <= tol."""
     import torch
     insts = _batch(far=True)
     tol = 1e-8 if precision == 0 else 1e-6
     out = {}
-    for tiled in (1, 2):
-        s = G.Solver(insts, tol=tol, precision=precision, max_iter=8000, tiled=tiled, tile_rows=8)
+    for strips in (1, 2):
+        s = G.Solver(insts, tol=tol, precision=precision, max_iter=8000, strips=strips, strip_rows=8)
         rc, st = s.solve()
         torch.cuda.synchronize()
         assert rc == G.NMPC_OK
         x, u, lam = s.state()
         r = G.nmpc_residual(s.h, s.x0, s.ref, x, u, lam, len(insts))
-        out[tiled] = ([st[b].iters for b in range(3)], u.cpu().numpy(), r[:, 0])
+        out[strips] = ([st[b].iters for b in range(3)], u.cpu().numpy(), r[:, 0])
         s.close()
     it_t, u_t, r_t = out[1]
     it_c, u_c, r_c = out[2]
@@ -184,11 +184,11 @@ def test_tile_solve_equals_cluster_solve(G, precision):
         assert np.abs(u_t - u_c).max() <= 1e-3 * np.abs(u_c).max()
 
 
-def test_tile_residual_entry_point_matches_oracle(G):
+def test_strip_residual_entry_point_matches_oracle(G):
     import torch
     insts = _batch(far=True)
     state, lists = _rand_state(insts, 97)
-    h = G.nmpc_setup(insts, precision=G.NMPC_MIXED, tiled=1, tile_rows=8)
+    h = G.nmpc_setup(insts, precision=G.NMPC_MIXED, strips=1, strip_rows=8)
     x0 = _t(G.pack_fields(insts, "x0"))
     ref = _t(G.pack_fields(insts, "ref"))
     r = G.nmpc_residual(h, x0, ref, *(_t(a) for a in state), len(insts))
@@ -203,17 +203,17 @@ def test_tile_residual_entry_point_matches_oracle(G):
         assert abs(r[b, 1] - two) <= 1e-10 * two
 
 
-def test_auto_routes_large_stages_to_tiles(G):
-    """tiled = 0: a 256x256 stage goes to the tile path, a 64x64 stage and a
+def test_auto_routes_large_stages_to_strips(G):
+    """strips = 0: a 256x256 stage goes to the strip path, a 64x64 stage and a
     1D instance stay on the cluster path."""
     insts = [wl.heat2d(256, 256, 2, 4, 4, seed=98), wl.heat2d(64, 64, 2, 4, 2, seed=99),
              wl.heat1d(50, 3, 1, 0.01, seed=100)]
     h = G.nmpc_setup(insts, precision=G.NMPC_MIXED)
-    plan, lp = G.nmpc_tile_plan(h), G.nmpc_launch_plan(h)
+    plan, lp = G.nmpc_strip_plan(h), G.nmpc_launch_plan(h)
     G.nmpc_destroy(h)
-    ty = plan["tile_y"]
-    assert plan["instances"] == 1 and plan["tile_x"] == 26 and 16 <= ty <= 256
-    assert plan["tiles"] == 2 * -(-256 // 26) * -(-256 // ty)
+    ty = plan["strip_y"]
+    assert plan["instances"] == 1 and plan["strip_x"] == 26 and 16 <= ty <= 256
+    assert plan["strips"] == 2 * -(-256 // 26) * -(-256 // ty)
     assert lp["work_items"] == 2 + 3
 
 
@@ -227,7 +227,7 @@ def test_full_size_grid_strip_solve_matches_oracle_solve(G, precision, rtol):
     import torch
     inst = wl.heat2d_large_batch(n=1, base_seed=5000, m=256, horizon=10)[0]
     s = G.Solver([inst], tol=1e-6, precision=precision, max_iter=4000)
-    assert G.nmpc_tile_plan(s.h)["instances"] == 1
+    assert G.nmpc_strip_plan(s.h)["instances"] == 1
     rc, st = s.solve()
     torch.cuda.synchronize()
     assert rc == G.NMPC_OK
