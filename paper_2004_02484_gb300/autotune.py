@@ -8,7 +8,9 @@ u-iterations n_u_it.  The KKT root does not depend on these (the lower layer
 is a fixed linear approximation of D_i^{-1} and the iteration's fixed point
 is K(S) = 0), only the iteration count and the time per iteration do.  The
 u-iteration's form (through the actuators' local responses or full-field
-sweeps) is a candidate as well.
+sweeps) is a candidate as well.  Batches of large 2D stages (the strip path:
+one warp per strip of the stage grid) are tuned over the strip's own rows
+and the inner counts instead.
 
 Results are cached in a JSON file keyed by a bucketed signature of the batch
 (dimension, grid size, horizon, actuators, batch size, precision).
@@ -41,8 +43,18 @@ def signature(instances: Sequence, precision: int) -> str:
     }, sort_keys=True)
 
 
+# stages from this many cells up are on the strip path (the auto rule of the
+# library: larger than a cluster of 8 CTAs with staged inputs holds)
+STRIP_CELLS = 16384
+
+
 def candidates(instances: Sequence, quick: bool = True) -> List[Dict]:
     ngmax = max(i.mx * i.my for i in instances)
+    if all(i.dim == 2 and i.mx * i.my >= STRIP_CELLS for i in instances):
+        rows = (0, 64) if quick else (0, 32, 64, 128)
+        inner = [(2, 1), (2, 2)] if quick else [(2, 1), (2, 2), (1, 2), (3, 1)]
+        return [{"strips": 1, "strip_rows": r, "n_lo": nlo, "n_u_it": nut, "check_every": 16}
+                for r in rows for nlo, nut in inner]
     clusters = [0, 1] if ngmax < 1024 else [0, 2, 4, 8]
     threads = [0, 256] if quick else [0, 64, 128, 256, 512]
     inner = [(2, 2), (2, 1), (2, 3), (1, 2), (3, 2)] if not quick else [(2, 2), (2, 1)]
@@ -117,4 +129,5 @@ def tune(instances: Sequence, precision: int, tol: float = 1e-6, cache_path: str
 def solver_opts(result: Dict) -> Dict:
     """The nmpc_opts fields of a tuning result."""
     return {k: v for k, v in result.items() if k in ("cluster", "threads", "n_lo", "n_u_it",
-                                                     "u_local", "cells", "check_every")}
+                                                     "u_local", "cells", "check_every",
+                                                     "strips", "strip_rows")}

@@ -36,3 +36,21 @@ def test_tune_caches_and_keeps_the_root(tmp_path):
     assert np.abs(u1 - u2).max() <= 1e-3 * np.abs(u1).max()
     s1.close()
     s2.close()
+
+
+def test_tune_large_2d_batch_over_strip_shapes(tmp_path):
+    from paper_2004_02484_gb300 import build as b
+    b.build()
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2004_02484_gb300 import autotune as AT
+    from paper_2004_02484_gb300 import nmpc as G
+    insts = wl.heat2d_large_batch(n=2, m=256, horizon=8)
+    res = AT.tune(insts, G.NMPC_MIXED, tol=1e-6, cache_path=str(tmp_path / "t.json"))
+    opts = AT.solver_opts(res)
+    assert opts["strips"] == 1 and opts["strip_rows"] in (0, 64)
+    s = G.Solver(insts, tol=1e-6, precision=G.NMPC_MIXED, **opts)
+    assert G.nmpc_strip_plan(s.h)["instances"] == 2
+    rc, st = s.solve()
+    assert rc == G.NMPC_OK and all(st[b].res_inf <= 1e-6 for b in range(2))
+    s.close()
