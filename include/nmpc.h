@@ -240,6 +240,14 @@ int nmpc_start_state(nmpc_handle* h, int init, const double* x0, double* x, doub
 int nmpc_rollout(nmpc_handle* h, const double* x0, const double* ref, const double* u, double* x,
                  double* lam, void* stream);
 
+/* nmpc_rollout in one launch with float32 arithmetic (stores float64): one
+   CTA per instance walks the stages with a block barrier between them.  For
+   start guesses, where the launch count of the per-stage form dominates (a
+   few hundred microseconds of launches against tens of microseconds of
+   work on small grids).  Same arguments and errors as nmpc_rollout. */
+int nmpc_rollout_fused(nmpc_handle* h, const double* x0, const double* ref, const double* u,
+                       double* x, double* lam, void* stream);
+
 /* Step start of nmpc_closed_loop_learned, supplied by the caller: enqueue on
    `stream` the work that writes a control trajectory guess (device float64,
    [sum N n_u], the packing of u) into the caller's u_guess buffer, reading

@@ -1530,6 +1530,16 @@ int nmpc_rollout(nmpc_handle* h, const double* x0, const double* ref, const doub
   return NMPC_OK;
 }
 
+int nmpc_rollout_fused(nmpc_handle* h, const double* x0, const double* ref, const double* u,
+                       double* x, double* lam, void* stream) {
+  if (!h || !x0 || !ref || !u || !x || !lam) return NMPC_ERR_BAD_ARG;
+  nmpc_dev::k_rollout_fused<<<h->n_inst, 1024, 0, (cudaStream_t)stream>>>(
+      h->inst_d, h->n_inst, h->act_d, x0, ref, u, x, lam);
+  h->launches++;
+  CK(cudaGetLastError());
+  return NMPC_OK;
+}
+
 int nmpc_closed_loop_learned(nmpc_handle* h, double* w, const double* ref, int steps, int n_sub,
                              nmpc_start_fn start, void* ctx, const double* u_guess,
                              double* u_hist, int* iters_hist, double* res_hist, void* stream) {

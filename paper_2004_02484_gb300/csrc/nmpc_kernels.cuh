@@ -1724,6 +1724,62 @@ __global__ void k_rollout_costate(const InstDev* inst, int n_inst, const double*
   }
 }
 
+// The same two recursions in one launch, in float32 arithmetic (a start
+// guess needs no more): one CTA per instance walks the stages, a block
+// barrier between stages (each stage reads the previous one's values, just
+// written by this CTA, from global memory).  Stores float64.
+__global__ void __launch_bounds__(1024) k_rollout_fused(const InstDev* inst, int n_inst,
+                                                         const int* act, const double* x0,
+                                                         const double* ref, const double* u,
+                                                         double* x, double* lam) {
+  const int b = blockIdx.x;
+  if (b >= n_inst) return;
+  const InstDev& I = inst[b];
+  const int ng = I.ng, mx = I.mx, my = I.my, nu = I.nu;
+  const float h = I.fh, cx = I.fcx, cy = I.fcy, dc = I.fdc, k0 = I.fk0, k1 = I.fk1, k1h = I.fk1h;
+  const float b0 = I.fb0, q = I.fq, hqf = I.fhqf;
+  const double* r = ref + I.g_off;
+  // Phi(v) of float64 storage, as float32
+  auto phi = [&](double v) {
+    const float f = d2f(v);
+    return k0 * (f + k1h * f * f);
+  };
+  for (int i = 0; i < I.N; ++i) {
+    const double* src = (i == 0) ? x0 + I.g_off : x + I.s_off + (long long)(i - 1) * ng;
+    double* dst = x + I.s_off + (long long)i * ng;
+    const double* ui = u + I.u_off + (long long)i * nu;
+    for (int c = threadIdx.x; c < ng; c += blockDim.x) {
+      const int iy = c / mx, ix = c - iy * mx;
+      float srcu = 0.0f;
+      for (int a = 0; a < nu; ++a)
+        if (act[I.act_off + a] == c) srcu += d2f(ui[a]);
+      const float pc = phi(src[c]);
+      const float lphi = cx * ((ix > 0 ? phi(src[c - 1]) : 0.0f) + (ix + 1 < mx ? phi(src[c + 1]) : 0.0f)) +
+                         cy * ((iy > 0 ? phi(src[c - mx]) : 0.0f) + (iy + 1 < my ? phi(src[c + mx]) : 0.0f)) -
+                         dc * pc;
+      dst[c] = f2d(d2f(src[c]) + h * (lphi + b0 * srcu));
+    }
+    __syncthreads();
+  }
+  const double* xN = x + I.s_off + (long long)(I.N - 1) * ng;
+  for (int i = I.N - 1; i >= 0; --i) {
+    const bool lst = (i == I.N - 1);
+    const double* xi = x + I.s_off + (long long)i * ng;
+    const double* ln = lam + I.s_off + (long long)(i + 1) * ng;  // read for i < N - 1
+    double* li = lam + I.s_off + (long long)i * ng;
+    auto next = [&](int m) { return lst ? hqf * (d2f(xN[m]) - d2f(r[m])) : d2f(ln[m]); };
+    for (int c = threadIdx.x; c < ng; c += blockDim.x) {
+      const int iy = c / mx, ix = c - iy * mx;
+      const float lap = cx * ((ix > 0 ? next(c - 1) : 0.0f) + (ix + 1 < mx ? next(c + 1) : 0.0f)) +
+                        cy * ((iy > 0 ? next(c - mx) : 0.0f) + (iy + 1 < my ? next(c + mx) : 0.0f)) -
+                        dc * next(c);
+      const float xv = d2f(xi[c]);
+      li[c] = f2d(next(c) + h * (q * (xv - d2f(r[c])) + k0 * (1.0f + k1 * xv) * lap));
+    }
+    __syncthreads();
+  }
+}
+
 // Closed loop on the device (one graph): the step loop's WHILE condition,
 // the per-step record of each instance's status, iterations and residual,
 // and a plain copy (graph loop bodies hold kernels only).

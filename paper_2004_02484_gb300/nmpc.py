@@ -61,7 +61,7 @@ class nmpc_stats(ctypes.Structure):
 
 EXPORTED = ["nmpc_default_opts", "nmpc_setup", "nmpc_solve", "nmpc_solve_host",
             "nmpc_residual", "nmpc_iterate", "nmpc_get_state", "nmpc_set_state",
-            "nmpc_sizes", "nmpc_launch_count", "nmpc_launch_plan", "nmpc_strip_plan", "nmpc_start_state", "nmpc_rollout", "nmpc_destroy",
+            "nmpc_sizes", "nmpc_launch_count", "nmpc_launch_plan", "nmpc_strip_plan", "nmpc_start_state", "nmpc_rollout", "nmpc_rollout_fused", "nmpc_destroy",
             "nmpc_strerror",
             "nmpc_solve_noalloc", "nmpc_plant_step", "nmpc_closed_loop",
             "nmpc_closed_loop_learned"]
@@ -93,6 +93,7 @@ def _load() -> ctypes.CDLL:
         "nmpc_strip_plan": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
         "nmpc_start_state": (I, [P, I, P, P, P, P, P]),
         "nmpc_rollout": (I, [P, P, P, P, P, P, P]),
+        "nmpc_rollout_fused": (I, [P, P, P, P, P, P, P]),
         "nmpc_launch_count": (ctypes.c_int64, [P]),
         "nmpc_destroy": (V, [P]),
         "nmpc_strerror": (ctypes.c_char_p, [I]),
@@ -302,6 +303,12 @@ def nmpc_rollout(h, x0, ref, u, x, lam, stream=None):
     """State (forward) and costate (backward) trajectories of the controls u."""
     _check(LIB.nmpc_rollout(h, _ptr(x0), _ptr(ref), _ptr(u), _ptr(x), _ptr(lam), _stream(stream)),
            "nmpc_rollout")
+
+
+def nmpc_rollout_fused(h, x0, ref, u, x, lam, stream=None):
+    """nmpc_rollout in one launch, float32 arithmetic (a start guess)."""
+    _check(LIB.nmpc_rollout_fused(h, _ptr(x0), _ptr(ref), _ptr(u), _ptr(x), _ptr(lam),
+                                  _stream(stream)), "nmpc_rollout_fused")
 
 
 def nmpc_launch_count(h) -> int:

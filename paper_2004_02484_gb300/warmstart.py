@@ -165,13 +165,12 @@ class LearnedWarmStart:
         self.net.set_params(p.astype(np.float32))
 
     # ---- inference ----
-    def predict_state(self, x0, ref):
-        """Float64 device guesses (x [B*N*ng], u [B*N*nu], lam [B*N*ng]) for
-        device float64 x0, ref [B*ng] (all on the GPU, all in library kernels)."""
+    def _forward(self, x0, ref):
+        """Network output [B, n_out] (float32) and x0 as float32 [B, ng]."""
         torch = _torch()
         dev = x0.device
         B = x0.numel() // self.ng
-        ng, N, R, Nu = self.ng, self.N, self.rank, self.N * self.nu
+        ng = self.ng
         x0v, rv = x0.view(B, ng), ref.view(B, ng)
         inp = torch.empty((B, 2 * ng), dtype=torch.float32, device=dev)
         x0f = torch.empty((B, ng), dtype=torch.float32, device=dev)
@@ -181,6 +180,27 @@ class LearnedWarmStart:
             GM.nmpc_cast_f64_f32(rv[b], inp[b, ng:])
         y = torch.empty((B, self.n_out), dtype=torch.float32, device=dev)
         self.net.forward(inp, y)
+        return y, x0f
+
+    def predict_controls(self, x0, ref):
+        """Float64 device control guesses u [B*N*nu] only (the POD part of the
+        output unused)."""
+        torch = _torch()
+        y, _ = self._forward(x0, ref)
+        B, Nu = y.shape[0], self.N * self.nu
+        u = torch.empty(B * Nu, dtype=torch.float64, device=x0.device)
+        for b in range(B):
+            GM.nmpc_cast_f32_f64(y[b, :Nu], u[b * Nu:(b + 1) * Nu])
+        return u
+
+    def predict_state(self, x0, ref):
+        """Float64 device guesses (x [B*N*ng], u [B*N*nu], lam [B*N*ng]) for
+        device float64 x0, ref [B*ng] (all on the GPU, all in library kernels)."""
+        torch = _torch()
+        dev = x0.device
+        B = x0.numel() // self.ng
+        ng, N, R, Nu = self.ng, self.N, self.rank, self.N * self.nu
+        y, x0f = self._forward(x0, ref)
         yb = torch.empty((B, self.n_out), dtype=torch.bfloat16, device=dev)
         GM.nmpc_cast_f32_bf16(y, yb)
         Vx, Vl = self._vb(self.Vx), self._vb(self.Vl)
@@ -211,13 +231,23 @@ class LearnedWarmStart:
             self._vcache = cache
         return cache[key]
 
-    def solve(self, solver: "G.Solver", check_residual: bool = False):
-        """Solve `solver`'s instances from the predicted state.  The plain
-        method stays the fallback: if the guessed start does not converge
-        (diverged or max_iter) the instances are re-solved from the cold
-        start.  Returns (rc, stats, used) with used "learned" or "cold"; with
-        check_residual, stats gain the guess's float64 residual norms."""
-        x, u, lam = self.predict_state(solver.x0, solver.ref)
+    def solve(self, solver: "G.Solver", check_residual: bool = False, decode: str = "pod"):
+        """Solve `solver`'s instances from the predicted state.  decode "pod":
+        state and costate from the predicted POD coefficients; "rollout": from
+        the predicted controls' state and costate trajectories
+        (nmpc_rollout).  The plain method stays the fallback: if the guessed
+        start does not converge (diverged or max_iter) the instances are
+        re-solved from the cold start.  Returns (rc, stats, used) with used
+        "learned" or "cold"; with check_residual, stats gain the guess's
+        float64 residual norms."""
+        if decode == "rollout":
+            torch = _torch()
+            u = self.predict_controls(solver.x0, solver.ref)
+            x = torch.empty(solver.n_s, dtype=torch.float64, device=u.device)
+            lam = torch.empty_like(x)
+            G.nmpc_rollout_fused(solver.h, solver.x0, solver.ref, u, x, lam)
+        else:
+            x, u, lam = self.predict_state(solver.x0, solver.ref)
         r_guess = None
         if check_residual:
             r_guess = G.nmpc_residual(solver.h, solver.x0, solver.ref, x, u, lam, solver.n)
@@ -249,13 +279,12 @@ class LearnedWarmStart:
 
 
 class LearnedControlStart:
-    """Learned start of the receding-horizon loop on large grids (Sec. 5.3's
-    closed loop): a network maps the plant state and the reference, each
-    reduced to f x f block means (library pooling kernel), to the control
-    trajectory; the candidate start takes its state and costate from the
-    plain start (the shifted previous solution, or the cold start at the first
-    step).  The loop keeps, per instance, whichever candidate has the smaller
-    float64 KKT residual, so the plain method stays the fallback."""
+    """Learned start of the receding-horizon loop on large grids: a network
+    maps the plant state and the reference, each reduced to f x f block means
+    (library pooling kernel), to the control trajectory; the loops complete it
+    with the state and costate trajectories the controls generate
+    (nmpc_rollout) and start the solve there (closed_loop_learned_graph, or
+    the host-driven closed_loop_learned with its other rules)."""
 
     def __init__(self, template, pool: int = 4, hidden: Sequence[int] = (512, 512, 512),
                  max_batch: int = 256, seed: int = 0):
@@ -428,10 +457,11 @@ def closed_loop_learned_graph(solver: "G.Solver", lcs: LearnedControlStart, w, s
 
 
 def evaluate(ws: LearnedWarmStart, seeds: Sequence[int], tol: float = 1e-6,
-             precision: int = G.NMPC_MIXED) -> Dict[str, float]:
+             precision: int = G.NMPC_MIXED, decode: str = "pod") -> Dict[str, float]:
     """Iterations and wall time to ||K||_inf <= tol from the cold start and
-    from the learned start (fallback to cold when its residual is worse),
-    one instance at a time."""
+    from the learned start (decode as in LearnedWarmStart.solve; the cold
+    start is the fallback when the learned one does not converge), one
+    instance at a time."""
     torch = _torch()
     it_c, it_l, t_c, t_l, used = [], [], [], [], []
     for s in seeds:
@@ -445,7 +475,7 @@ def evaluate(ws: LearnedWarmStart, seeds: Sequence[int], tol: float = 1e-6,
         t_c.append(time.perf_counter() - t0)
         it_c.append(st[0].iters)
         t0 = time.perf_counter()
-        rc2, st2, u2 = ws.solve(sol)
+        rc2, st2, u2 = ws.solve(sol, decode=decode)
         torch.cuda.synchronize()
         t_l.append(time.perf_counter() - t0)
         it_l.append(st2[0].iters)
@@ -454,7 +484,8 @@ def evaluate(ws: LearnedWarmStart, seeds: Sequence[int], tol: float = 1e-6,
         sol.close()
     return {"iters_cold": float(np.mean(it_c)), "iters_learned": float(np.mean(it_l)),
             "ms_cold": 1e3 * float(np.mean(t_c)), "ms_learned": 1e3 * float(np.mean(t_l)),
-            "learned_used": used.count("learned") / len(used), "n": len(seeds)}
+            "learned_used": used.count("learned") / len(used), "n": len(seeds),
+            "decode": decode}
 
 
 def main():
@@ -481,6 +512,7 @@ def main():
     if a.out:
         ws.save(a.out)
     res = evaluate(ws, list(range(2_000_000, 2_000_000 + a.test)))
+    res["rollout"] = evaluate(ws, list(range(2_000_000, 2_000_000 + a.test)), decode="rollout")
     res.update({"train": a.train, "gen_s": t_gen, "fit_s": t_fit, "loss_first": losses[0],
                 "loss_last": losses[-1], "mean_train_iters": float(data["iters"].mean())})
     print(json.dumps(res), flush=True)

@@ -232,3 +232,26 @@ def test_learned_closed_loop_graph_equals_host_driven_loops(G, strips):
     for it, wf in out[1:]:
         assert np.array_equal(it, out[0][0])
         assert np.array_equal(wf, out[0][1])
+
+
+def test_fused_rollout_matches_the_float64_rollout(G):
+    """nmpc_rollout_fused (one launch, float32 arithmetic) gives the float64
+    rollout's trajectories to float32 accuracy (relative 1e-5 of each field's
+    scale), on a ragged 2D + 1D batch."""
+    import torch
+    insts = [wl.heat2d(20, 18, 7, 3, 3, seed=81), wl.heat1d(40, 11, 2, 0.02, seed=82),
+             wl.heat2d(64, 64, 12, 4, 2, seed=84)]
+    s = G.Solver(insts, tol=1e-6, precision=1, max_iter=2000)
+    rng = np.random.default_rng(85)
+    u = _t(rng.normal(0.0, 0.3, s.n_u))
+    x, lam = (torch.empty(s.n_s, dtype=torch.float64, device="cuda") for _ in range(2))
+    xf, lf = torch.empty_like(x), torch.empty_like(x)
+    G.nmpc_rollout(s.h, s.x0, s.ref, u, x, lam)
+    G.nmpc_rollout_fused(s.h, s.x0, s.ref, u, xf, lf)
+    torch.cuda.synchronize()
+    s.close()
+    for a, b_, per in ((x, xf, "ng"), (lam, lf, "ng")):
+        A = G.split_stages(insts, a.cpu().numpy(), per)
+        Bf = G.split_stages(insts, b_.cpu().numpy(), per)
+        for ai, bi in zip(A, Bf):
+            assert np.abs(ai - bi).max() <= 1e-5 * np.abs(ai).max()
