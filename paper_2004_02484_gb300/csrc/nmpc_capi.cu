@@ -1533,8 +1533,14 @@ int nmpc_rollout(nmpc_handle* h, const double* x0, const double* ref, const doub
 int nmpc_rollout_fused(nmpc_handle* h, const double* x0, const double* ref, const double* u,
                        double* x, double* lam, void* stream) {
   if (!h || !x0 || !ref || !u || !x || !lam) return NMPC_ERR_BAD_ARG;
-  nmpc_dev::k_rollout_fused<<<h->n_inst, 1024, 0, (cudaStream_t)stream>>>(
-      h->inst_d, h->n_inst, h->act_d, x0, ref, u, x, lam);
+  // two stages of float32 recursion variable in shared memory when they fit
+  const int cells = h->ng_max <= 12288 ? h->ng_max : 0;
+  const size_t smem = 2 * (size_t)cells * sizeof(float);
+  if (smem > 48 * 1024)
+    CK(cudaFuncSetAttribute(nmpc_dev::k_rollout_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)smem));
+  nmpc_dev::k_rollout_fused<<<h->n_inst, 1024, smem, (cudaStream_t)stream>>>(
+      h->inst_d, h->n_inst, h->act_d, x0, ref, u, x, lam, cells);
   h->launches++;
   CK(cudaGetLastError());
   return NMPC_OK;

@@ -1726,26 +1726,33 @@ __global__ void k_rollout_costate(const InstDev* inst, int n_inst, const double*
 
 // The same two recursions in one launch, in float32 arithmetic (a start
 // guess needs no more): one CTA per instance walks the stages, a block
-// barrier between stages (each stage reads the previous one's values, just
-// written by this CTA, from global memory).  Stores float64.
+// barrier between stages.  The recursion variable (the previous stage's x,
+// or the next stage's lambda) is kept in shared memory as float32 when two
+// stages fit (smem_cells >= ng; else it is read back from the float64
+// output).  Stores float64.
 __global__ void __launch_bounds__(1024) k_rollout_fused(const InstDev* inst, int n_inst,
                                                          const int* act, const double* x0,
                                                          const double* ref, const double* u,
-                                                         double* x, double* lam) {
+                                                         double* x, double* lam,
+                                                         int smem_cells) {
+  extern __shared__ float rbuf[];  // [2][smem_cells]
   const int b = blockIdx.x;
   if (b >= n_inst) return;
   const InstDev& I = inst[b];
   const int ng = I.ng, mx = I.mx, my = I.my, nu = I.nu;
+  const bool on_chip = ng <= smem_cells;
   const float h = I.fh, cx = I.fcx, cy = I.fcy, dc = I.fdc, k0 = I.fk0, k1 = I.fk1, k1h = I.fk1h;
   const float b0 = I.fb0, q = I.fq, hqf = I.fhqf;
   const double* r = ref + I.g_off;
-  // Phi(v) of float64 storage, as float32
-  auto phi = [&](double v) {
-    const float f = d2f(v);
-    return k0 * (f + k1h * f * f);
-  };
+  const double* x0b = x0 + I.g_off;
+  auto phi = [&](float f) { return k0 * (f + k1h * f * f); };
+  int cur = 0;
+  // forward: x_i = x_{i-1} + h (Lap Phi(x_{i-1}) + b0 B u_i)
   for (int i = 0; i < I.N; ++i) {
-    const double* src = (i == 0) ? x0 + I.g_off : x + I.s_off + (long long)(i - 1) * ng;
+    const double* srcg = (i == 0) ? x0b : x + I.s_off + (long long)(i - 1) * ng;
+    const float* srcs = rbuf + (cur ^ 1) * smem_cells;
+    float* dsts = rbuf + cur * smem_cells;
+    auto src = [&](int m) { return (on_chip && i > 0) ? srcs[m] : d2f(srcg[m]); };
     double* dst = x + I.s_off + (long long)i * ng;
     const double* ui = u + I.u_off + (long long)i * nu;
     for (int c = threadIdx.x; c < ng; c += blockDim.x) {
@@ -1753,30 +1760,42 @@ __global__ void __launch_bounds__(1024) k_rollout_fused(const InstDev* inst, int
       float srcu = 0.0f;
       for (int a = 0; a < nu; ++a)
         if (act[I.act_off + a] == c) srcu += d2f(ui[a]);
-      const float pc = phi(src[c]);
-      const float lphi = cx * ((ix > 0 ? phi(src[c - 1]) : 0.0f) + (ix + 1 < mx ? phi(src[c + 1]) : 0.0f)) +
-                         cy * ((iy > 0 ? phi(src[c - mx]) : 0.0f) + (iy + 1 < my ? phi(src[c + mx]) : 0.0f)) -
-                         dc * pc;
-      dst[c] = f2d(d2f(src[c]) + h * (lphi + b0 * srcu));
+      const float sc = src(c);
+      const float lphi = cx * ((ix > 0 ? phi(src(c - 1)) : 0.0f) + (ix + 1 < mx ? phi(src(c + 1)) : 0.0f)) +
+                         cy * ((iy > 0 ? phi(src(c - mx)) : 0.0f) + (iy + 1 < my ? phi(src(c + mx)) : 0.0f)) -
+                         dc * phi(sc);
+      const float v = sc + h * (lphi + b0 * srcu);
+      if (on_chip) dsts[c] = v;
+      dst[c] = f2d(v);
     }
     __syncthreads();
+    cur ^= 1;
   }
+  // backward: lambda_{N+1} = h qf (x_N - ref), lambda_i = lambda_{i+1} +
+  // h (q (x_i - ref) + Phi'(x_i) Lap lambda_{i+1})
   const double* xN = x + I.s_off + (long long)(I.N - 1) * ng;
   for (int i = I.N - 1; i >= 0; --i) {
     const bool lst = (i == I.N - 1);
     const double* xi = x + I.s_off + (long long)i * ng;
-    const double* ln = lam + I.s_off + (long long)(i + 1) * ng;  // read for i < N - 1
+    const double* lng = lam + I.s_off + (long long)(i + 1) * ng;  // read for i < N - 1
+    const float* lns = rbuf + (cur ^ 1) * smem_cells;
+    float* lds = rbuf + cur * smem_cells;
     double* li = lam + I.s_off + (long long)i * ng;
-    auto next = [&](int m) { return lst ? hqf * (d2f(xN[m]) - d2f(r[m])) : d2f(ln[m]); };
+    auto next = [&](int m) {
+      return lst ? hqf * (d2f(xN[m]) - d2f(r[m])) : (on_chip ? lns[m] : d2f(lng[m]));
+    };
     for (int c = threadIdx.x; c < ng; c += blockDim.x) {
       const int iy = c / mx, ix = c - iy * mx;
       const float lap = cx * ((ix > 0 ? next(c - 1) : 0.0f) + (ix + 1 < mx ? next(c + 1) : 0.0f)) +
                         cy * ((iy > 0 ? next(c - mx) : 0.0f) + (iy + 1 < my ? next(c + mx) : 0.0f)) -
                         dc * next(c);
       const float xv = d2f(xi[c]);
-      li[c] = f2d(next(c) + h * (q * (xv - d2f(r[c])) + k0 * (1.0f + k1 * xv) * lap));
+      const float v = next(c) + h * (q * (xv - d2f(r[c])) + k0 * (1.0f + k1 * xv) * lap);
+      if (on_chip) lds[c] = v;
+      li[c] = f2d(v);
     }
     __syncthreads();
+    cur ^= 1;
   }
 }
 
