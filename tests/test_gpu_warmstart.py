@@ -43,7 +43,11 @@ def test_training_loss_falls(trained):
     assert losses[-1] < 0.1 * losses[0]
 
 
-def test_learned_start_cuts_iterations_at_equal_residual(WS, trained):
+@pytest.mark.parametrize("decode,gain", [("pod", 0.85), ("rollout", 0.6)])
+def test_learned_start_cuts_iterations_at_equal_residual(WS, trained, decode, gain):
+    """The trained network's start, decoded from its POD coefficients or
+    completed by its controls' rollout, reaches the cold start's root at
+    equal residual in fewer iterations (<= 85% / 60% of the cold start's)."""
     import torch
     from paper_2004_02484_gb300 import nmpc as G
     from paper_2004_02484_gb300 import workloads as wl
@@ -54,12 +58,9 @@ def test_learned_start_cuts_iterations_at_equal_residual(WS, trained):
         sol = G.Solver([inst], tol=1e-6, precision=G.NMPC_MIXED)
         rc, st = sol.solve(init=G.NMPC_INIT_COLD)
         uc = sol.u.cpu().numpy().copy()
-        rc2, st2, used = ws.solve(sol, check_residual=True)
-        ul = sol.u.cpu().numpy()
+        rc2, st2, used = ws.solve(sol, check_residual=True, decode=decode)
         assert rc == G.NMPC_OK and rc2 == G.NMPC_OK
         assert st[0].res_inf <= 1e-6 and st2[0].res_inf <= 1e-6 and used == "learned"
-        # both are roots to the same tolerance: controls agree at the FP32-path bar
-        assert np.abs(ul - uc).max() <= 1e-3 * np.abs(uc).max()
         # the float64 residual of the returned state, recomputed by the oracle
         if s == 2_000_000:
             x, u, lam = sol.state()
@@ -71,4 +72,16 @@ def test_learned_start_cuts_iterations_at_equal_residual(WS, trained):
         its_c.append(st[0].iters)
         its_l.append(st2[0].iters)
         sol.close()
-    assert np.mean(its_l) <= 0.85 * np.mean(its_c), (its_c, its_l)
+    assert np.mean(its_l) <= gain * np.mean(its_c), (its_c, its_l)
+    # The same root: the u rows of K carry h r (2e-7 here), so ||K||_inf <=
+    # 1e-6 leaves the controls loose; driven to 1e-10 from either start they
+    # agree to 1e-5 relative (the FP32 path's bar at that tolerance).
+    inst = wl.heat2d_learning_instance(2_000_001)
+    sol = G.Solver([inst], tol=1e-10, precision=G.NMPC_MIXED, max_iter=20000)
+    rc, st = sol.solve(init=G.NMPC_INIT_COLD)
+    uc = sol.u.cpu().numpy().copy()
+    rc2, st2, used = ws.solve(sol, decode=decode)
+    ul = sol.u.cpu().numpy()
+    sol.close()
+    assert rc == rc2 == G.NMPC_OK and used == "learned"
+    assert np.abs(ul - uc).max() <= 1e-5 * np.abs(uc).max()
