@@ -37,10 +37,13 @@ TOL = 1e-6
 # algorithmic bytes per cell-stage per iteration: read x_i, lambda_i and write
 # them back in float64 (the neighbour-stage reads are the same arrays)
 BYTES_PER_POINT_STAGE = 32
-# algorithmic float32 flops per cell-stage per iteration of the mixed path with
-# two P^-1 applications (n_u_it = 1): split residual ~30, two applications of
-# 2 x 2 sweeps x ~10 flops + 2, coefficients ~10
-FP32_FLOPS_PER_POINT_STAGE = 124
+
+def fp32_flops_per_point_stage(n_lo: int, n_u_it: int) -> int:
+    """Algorithmic float32 flops per cell-stage per iteration of the mixed
+    path: split residual ~30 and coefficients ~10, then n_u_it + 1
+    applications of P^-1 (eq. 24), each 2 n_lo sweeps of ~10 flops plus ~2."""
+    return 30 + 10 + (n_u_it + 1) * (2 * n_lo * 10 + 2)
+
 # float32 FMA peak: 128 lanes x 2 flops x 152 SMs x 2.07 GHz (unit counts and
 # maximum SM clock of the part)
 FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.07e9 / 1e12
@@ -281,10 +284,11 @@ def main():
                      if k in ("threads", "cluster", "cells", "staged", "persistent")}}
     # the same launches against the float32 ALU ceiling (the 64x64 stage slabs
     # live in shared memory; the kernel is latency-bound)
-    ach_alu = FP32_FLOPS_PER_POINT_STAGE * cells / (avg_launch_ms / 1e3) / 1e12
+    flops_cs = fp32_flops_per_point_stage(tuned.get("n_lo", 2), tuned.get("n_u_it", 2))
+    ach_alu = flops_cs * cells / (avg_launch_ms / 1e3) / 1e12
     roof_alu = {"bound": "alu", "achieved": ach_alu, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach_alu / FP32_PEAK_TFLOPS, "peak_source": "derived (unit counts x clock)",
-                "flops_per_cell_stage": FP32_FLOPS_PER_POINT_STAGE}
+                "flops_per_cell_stage": flops_cs}
     cpu = None
     if rank == 0:
         os.environ.setdefault("OMP_NUM_THREADS", "1")

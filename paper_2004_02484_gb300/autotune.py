@@ -52,12 +52,13 @@ def candidates(instances: Sequence, quick: bool = True) -> List[Dict]:
     ngmax = max(i.mx * i.my for i in instances)
     if all(i.dim == 2 and i.mx * i.my >= STRIP_CELLS for i in instances):
         rows = (0, 64) if quick else (0, 32, 64, 128)
-        inner = [(2, 1), (2, 2)] if quick else [(2, 1), (2, 2), (1, 2), (3, 1)]
+        inner = [(2, 1), (2, 2), (1, 1)] if quick else [(2, 1), (2, 2), (1, 1), (1, 2), (3, 1)]
         return [{"strips": 1, "strip_rows": r, "n_lo": nlo, "n_u_it": nut, "check_every": 16}
                 for r in rows for nlo, nut in inner]
     clusters = [0, 1] if ngmax < 1024 else [0, 2, 4, 8]
     threads = [0, 256] if quick else [0, 64, 128, 256, 512]
-    inner = [(2, 2), (2, 1), (2, 3), (1, 2), (3, 2)] if not quick else [(2, 2), (2, 1)]
+    inner = ([(2, 2), (2, 1), (2, 3), (1, 1), (1, 2), (3, 2)] if not quick
+             else [(2, 2), (2, 1), (1, 1)])
     out = []
     cells = (0,) if quick else (0, 4)
     for c, t, (nlo, nut), ul, ce in itertools.product(clusters, threads, inner, (1, 0), cells):
