@@ -134,6 +134,13 @@ typedef struct {
   int strip_rows;   /* own rows per strip (0..65535); 0 = auto (whole columns
                       when the batch gives enough strips, else shorter
                       strips, at least 16 rows)                             */
+  int lines;        /* NMPC_MIXED 1D instances of at most 256 cells on the
+                      line path: one warp per stage, the stage's cells in
+                      registers (8 per lane at most), every pass of the
+                      iteration without a block barrier; full-field
+                      u-iteration (u_local does not apply there).
+                      0 = auto (every such instance), 1 = the same,
+                      2 = never (cluster path)                              */
 } nmpc_opts;
 
 typedef struct {
@@ -306,6 +313,13 @@ int nmpc_launch_plan(const nmpc_handle* h, int64_t* out);
    strip's extended region.  All zero when no instance
    is on the strip path.  NMPC_ERR_BAD_ARG for NULL arguments. */
 int nmpc_strip_plan(const nmpc_handle* h, int64_t* out);
+
+/* Line path of the handle (opts.lines): out[0] line work items per
+   iteration (one warp each: an (instance, stage) of a 1D instance), out[1]
+   instances on the line path, out[2] threads per CTA, out[3] dynamic shared
+   memory per CTA (bytes).  All zero when no instance is on the line path.
+   NMPC_ERR_BAD_ARG for NULL arguments. */
+int nmpc_line_plan(const nmpc_handle* h, int64_t* out);
 
 /* Allocation-free solve of ONE instance (no counterpart in the paper; it
    exists for callers that may not allocate device memory when they solve:

@@ -101,6 +101,11 @@ struct nmpc_handle {
   int n_patches = 0;
   size_t patch_smem = 0;
   double* v3_d = nullptr;  // v3 per control, written by k_patch
+  // line path (k_line): one warp per 1D stage
+  int4* lines_d = nullptr;
+  int n_lines = 0;
+  int n_line_inst = 0;
+  size_t line_smem = 0;
   long long launches = 0;
   long long iter_launches = 0;  // iteration steps (each one or two kernel launches)
   bool has_state = false;
@@ -137,7 +142,7 @@ void free_all(nmpc_handle* h) {
                   h->xb[0], h->xb[1], h->xb[2], h->ub[0], h->ub[1], h->ub[2],
                   h->lb[0], h->lb[1], h->lb[2], h->ictl, h->res_inf, h->res_err, h->res_sq,
                   h->res_first, h->status, h->iters, h->final_buf, h->fin_inf,
-                  h->fin_2, h->full_from, h->full0, h->scratch, h->strips_d, h->patches_d,
+                  h->fin_2, h->full_from, h->full0, h->scratch, h->strips_d, h->patches_d, h->lines_d,
                   h->v3_d};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -200,6 +205,8 @@ IterArgs make_args(nmpc_handle* h) {
   A.patches = h->patches_d;
   A.n_patches = h->n_patches;
   A.v3g = h->v3_d;
+  A.lines = h->lines_d;
+  A.n_lines = h->n_lines;
   return A;
 }
 
@@ -541,8 +548,23 @@ cudaError_t launch_strip(const nmpc_handle* h, const IterArgs& A, cudaStream_t s
   return cudaLaunchKernelEx(&cfg, strip_kernel<T>(h->opts.n_lo), A, mode, j);
 }
 
+cudaError_t launch_line(const nmpc_handle* h, const IterArgs& A, cudaStream_t st, int mode, int j) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((h->n_lines + nmpc_dev::LINE_WARPS - 1) / nmpc_dev::LINE_WARPS));
+  cfg.blockDim = dim3(32 * nmpc_dev::LINE_WARPS);
+  cfg.dynamicSmemBytes = h->line_smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = (mode == nmpc_dev::MODE_SOLVE) ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, nmpc_dev::k_line, A, mode, j);
+}
+
 // One iteration (or one-shot pass): the cluster kernel over the cluster
-// path's work items and the strip kernels over the strips, whichever exist.
+// path's work items, the strip kernels over the strips and the line kernel
+// over the 1D stages, whichever exist.
 template <int MODE>
 cudaError_t launch_iterate(nmpc_handle* h, const IterArgs& A, cudaStream_t st, int j = 0) {
   h->iter_launches++;
@@ -562,6 +584,11 @@ cudaError_t launch_iterate(nmpc_handle* h, const IterArgs& A, cudaStream_t st, i
     }
     h->launches++;
     e = h->mixed ? launch_strip<float>(h, A, st, MODE, j) : launch_strip<double>(h, A, st, MODE, j);
+    if (e != cudaSuccess) return e;
+  }
+  if (h->n_lines > 0) {
+    h->launches++;
+    e = launch_line(h, A, st, MODE, j);
   }
   return e;
 }
@@ -605,7 +632,8 @@ cudaError_t configure_kernels(size_t smem) {
                              (int)smem);
     if (e != cudaSuccess) return e;
   }
-  return cudaSuccess;
+  return cudaFuncSetAttribute(nmpc_dev::k_line, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem);
 }
 
 // Whether instance I may run on the strip path: 2D, n_lo <= 4, and for
@@ -624,6 +652,20 @@ bool strip_eligible(const InstDev& I, const int* act, const nmpc_opts& o) {
       }
   }
   return true;
+}
+
+// Whether instance I runs on the line path: 1D, at most 32 x LINE_MAX_CPL
+// cells, float32 lower layer.
+bool line_eligible(const InstDev& I, bool mixed) {
+  return mixed && I.dim == 1 && I.mx >= 1 && I.mx <= 32 * nmpc_dev::LINE_MAX_CPL &&
+         I.nu <= nmpc_dev::MAX_NU;
+}
+
+// Cells per lane of a line of mx cells: the smallest of 1, 2, 4, 8 that covers it.
+int line_cells_per_lane(int mx) {
+  int c = 1;
+  while (32 * c < mx) c *= 2;
+  return c;
 }
 
 // Whether a stage of instance I fits a cluster of at most 8 CTAs with its
@@ -646,7 +688,7 @@ bool opts_ok(const nmpc_opts& o) {
          (o.precision == NMPC_FP64 || o.precision == NMPC_MIXED) && o.threads >= 0 &&
          o.threads <= 512 && (o.threads % 32) == 0 && o.cluster >= 0 && o.cluster <= 16 &&
          (o.cluster <= 8 || o.cluster == 16) && (o.split_min >= 0) &&
-         (o.cells >= 0 && o.cells <= 8) && (o.strips >= 0 && o.strips <= 2) &&
+         (o.cells >= 0 && o.cells <= 8) && (o.strips >= 0 && o.strips <= 2) && (o.lines >= 0 && o.lines <= 2) &&
          (o.strip_rows >= 0 && o.strip_rows <= 65535);
 }
 
@@ -1121,6 +1163,7 @@ void nmpc_default_opts(nmpc_opts* o) {
   o->persistent = 0;
   o->strips = 0;
   o->strip_rows = 0;
+  o->lines = 0;
 }
 
 int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
@@ -1222,11 +1265,15 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
     }
   }
   std::vector<int2> work;
-  std::vector<int4> strips, patches;
+  std::vector<int4> strips, patches, lines;
   std::vector<InstDev> cl_inst;
   for (int b = 0; b < n_instances; ++b) {
     const InstDev& I = h->inst_h[b];
-    if (on_strips[b]) {
+    if (o.lines != 2 && line_eligible(I, h->mixed)) {
+      h->n_line_inst++;
+      const int cpl = line_cells_per_lane(I.mx);
+      for (int s = 0; s < I.N; ++s) lines.push_back(make_int4(b, s, cpl, 0));
+    } else if (on_strips[b]) {
       h->n_strip_inst++;
       for (int s = 0; s < I.N; ++s) {
         for (int y0 = 0; y0 < I.my; y0 += ty)
@@ -1238,9 +1285,20 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
       for (int s = 0; s < I.N; ++s) work.push_back(make_int2(b, s));
     }
   }
+  // line items grouped by cells per lane (neighbouring CTAs then run the same
+  // specialisation of the kernel body: instruction-cache locality)
+  std::stable_sort(lines.begin(), lines.end(),
+                   [](const int4& a, const int4& b) { return a.z < b.z; });
   h->n_work = (int)work.size();
   h->n_strips = (int)strips.size();
   h->n_patches = (int)patches.size();
+  h->n_lines = (int)lines.size();
+  h->line_smem = nmpc_dev::LINE_WARPS * ((sizeof(nmpc_dev::LineShared) + 15) & ~size_t(15));
+  if (h->n_lines > 0 && h->line_smem > (size_t)max_optin) {
+    fprintf(stderr, "nmpc: line path needs %zu bytes of shared memory\n", h->line_smem);
+    delete h;
+    return NMPC_ERR_UNSUPPORTED;
+  }
   if (h->n_strips > 0) {
     h->strip_x = tx;
     h->strip_y = ty;
@@ -1265,7 +1323,7 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
   if (h->n_work > 0)
     P = plan_launch(cl_inst.data(), (int)cl_inst.size(), h->n_work, o, h->mixed,
                     std::max(1, h->num_sms), max_optin);
-  P.persistent = P.persistent && h->n_strips == 0;
+  P.persistent = P.persistent && h->n_strips == 0 && h->n_lines == 0;
   if (h->n_work > 0 && !P.smem_mode) {
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(
@@ -1294,6 +1352,7 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
   A(dev_alloc(&h->work_d, h->n_work));
   A(dev_alloc(&h->strips_d, h->n_strips));
   A(dev_alloc(&h->patches_d, h->n_patches));
+  A(dev_alloc(&h->lines_d, h->n_lines));
   A(dev_alloc(&h->v3_d, h->n_strips > 0 ? h->n_u : 0));
   A(dev_alloc(&h->act_d, act_all.size()));
   A(dev_alloc(&h->x0_d, h->n_g));
@@ -1336,6 +1395,8 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
     if (!patches.empty())
       A(cudaMemcpy(h->patches_d, patches.data(), patches.size() * sizeof(int4),
                    cudaMemcpyHostToDevice));
+    if (!lines.empty())
+      A(cudaMemcpy(h->lines_d, lines.data(), lines.size() * sizeof(int4), cudaMemcpyHostToDevice));
     A(cudaMemcpy(h->act_d, act_all.data(), act_all.size() * sizeof(int), cudaMemcpyHostToDevice));
     A(cudaMemset(h->ictl, 0, 8 * sizeof(int)));
     A(cudaDeviceSynchronize());
@@ -1635,6 +1696,16 @@ int nmpc_launch_plan(const nmpc_handle* h, int64_t* out) {
   out[8] = h->resident_clusters;
   out[9] = h->n_work;
   out[10] = h->iter_launches;
+  return NMPC_OK;
+}
+
+int nmpc_line_plan(const nmpc_handle* h, int64_t* out) {
+  if (!h || !out) return NMPC_ERR_BAD_ARG;
+  const bool on = h->n_lines > 0;
+  out[0] = h->n_lines;
+  out[1] = h->n_line_inst;
+  out[2] = on ? 32 * nmpc_dev::LINE_WARPS : 0;
+  out[3] = on ? (int64_t)h->line_smem : 0;
   return NMPC_OK;
 }
 

@@ -126,6 +126,9 @@ struct IterArgs {
   const int4* patches;
   int n_patches;
   double* v3g;
+  // line path (k_line): (instance, stage, cells per lane, 0) per 1D stage
+  const int4* lines;
+  int n_lines;
 };
 
 struct Cl {
@@ -1844,5 +1847,6 @@ __global__ void k_set_weights(InstDev* inst, int n_inst, const double* w) {
 }
 
 #include "nmpc_patch.cuh"
+#include "nmpc_line.cuh"
 
 }  // namespace nmpc_dev

@@ -6,7 +6,11 @@
 
 batch1d:    the ragged 1D batch (M ~ U{32..256}, N ~ U{10..60}, n_u ~ U{1..4},
             R = 10^U[-3,-1]) solved in one handle, mixed precision, to
-            ||K||_inf <= 1e-6; reports solves/s and iterations.
+            ||K||_inf <= 1e-6, launch shape and inner counts from the
+            autotuner (--tune 0: the library defaults; --lines 2 keeps the
+            1D stages off the line path); reports solves/s and iterations;
+            --graph 0 launches the iterations from the host (a profiler can
+            then capture single iteration kernels).
 closedloop: the 2D 256x256, N = 100, 16-actuator batch in a receding-horizon
             loop (shifted warm starts, explicit-Euler plant), mixed precision;
             reports solves/s (instances x steps / time), iterations per step,
@@ -40,10 +44,16 @@ from . import workloads as wl
 BYTES_PER_CELL_STAGE = 32  # read x, lambda; write x, lambda (float64)
 
 
-def batch1d(n: int, tol: float = 1e-6, reps: int = 3):
+def batch1d(n: int, tol: float = 1e-6, reps: int = 3, tune: int = 1, use_graph: int = 1,
+            lines: int = 0):
     import torch
     insts = wl.heat1d_ragged_batch(n)
-    s = G.Solver(insts, tol=tol, precision=G.NMPC_MIXED, max_iter=20000)
+    opts = {}
+    if tune:
+        from . import autotune as AT
+        opts = AT.solver_opts(AT.tune(insts, G.NMPC_MIXED, tol=tol))
+    s = G.Solver(insts, tol=tol, precision=G.NMPC_MIXED, max_iter=20000, use_graph=use_graph,
+                 lines=lines, **opts)
     rc, st = s.solve()
     assert rc == G.NMPC_OK, rc
     torch.cuda.synchronize()
@@ -56,7 +66,8 @@ def batch1d(n: int, tol: float = 1e-6, reps: int = 3):
     cells = sum(i.mx * i.horizon for i in insts)
     out = {"experiment": "batch1d", "instances": n, "s_per_batch": dt, "solves_per_s": n / dt,
            "iters_mean": float(its.mean()), "iters_max": int(its.max()),
-           "cell_stages": cells, "launches": G.nmpc_launch_count(s.h)}
+           "cell_stages": cells, "launches": G.nmpc_launch_count(s.h), "opts": opts,
+           "line_plan": G.nmpc_line_plan(s.h)}
     s.close()
     return out
 
@@ -197,13 +208,16 @@ def main():
     ap.add_argument("--graph", type=int, default=1)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--rules", type=int, default=1)
+    ap.add_argument("--tune", type=int, default=1)
+    ap.add_argument("--lines", type=int, default=0)
     a = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
     from . import build
     build.build()
     if a.which == "batch1d":
-        print(json.dumps(batch1d(a.n or 1024)), flush=True)
+        print(json.dumps(batch1d(a.n or 1024, reps=a.reps, tune=a.tune, use_graph=a.graph,
+                                 lines=a.lines)), flush=True)
     elif a.which == "solve":
         print(json.dumps(solve(a.n or 8, a.grid, a.horizon, a.reps, a.graph, strips=a.strips,
                                strip_rows=a.strip_rows)), flush=True)

@@ -51,7 +51,8 @@ class nmpc_opts(ctypes.Structure):
                 ("use_graph", ctypes.c_int), ("cluster", ctypes.c_int),
                 ("split_min", ctypes.c_double), ("u_local", ctypes.c_int),
                 ("cells", ctypes.c_int), ("persistent", ctypes.c_int),
-                ("strips", ctypes.c_int), ("strip_rows", ctypes.c_int)]
+                ("strips", ctypes.c_int), ("strip_rows", ctypes.c_int),
+                ("lines", ctypes.c_int)]
 
 
 class nmpc_stats(ctypes.Structure):
@@ -61,7 +62,7 @@ class nmpc_stats(ctypes.Structure):
 
 EXPORTED = ["nmpc_default_opts", "nmpc_setup", "nmpc_solve", "nmpc_solve_host",
             "nmpc_residual", "nmpc_iterate", "nmpc_get_state", "nmpc_set_state",
-            "nmpc_sizes", "nmpc_launch_count", "nmpc_launch_plan", "nmpc_strip_plan", "nmpc_start_state", "nmpc_rollout", "nmpc_rollout_fused", "nmpc_destroy",
+            "nmpc_sizes", "nmpc_launch_count", "nmpc_launch_plan", "nmpc_strip_plan", "nmpc_line_plan", "nmpc_start_state", "nmpc_rollout", "nmpc_rollout_fused", "nmpc_destroy",
             "nmpc_strerror",
             "nmpc_solve_noalloc", "nmpc_plant_step", "nmpc_closed_loop",
             "nmpc_closed_loop_learned"]
@@ -91,6 +92,7 @@ def _load() -> ctypes.CDLL:
         "nmpc_sizes": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
         "nmpc_launch_plan": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
         "nmpc_strip_plan": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
+        "nmpc_line_plan": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
         "nmpc_start_state": (I, [P, I, P, P, P, P, P]),
         "nmpc_rollout": (I, [P, P, P, P, P, P, P]),
         "nmpc_rollout_fused": (I, [P, P, P, P, P, P, P]),
@@ -185,6 +187,14 @@ def nmpc_strip_plan(h) -> dict:
     _check(LIB.nmpc_strip_plan(h, out), "nmpc_strip_plan")
     keys = ("strips", "strip_x", "strip_y", "threads", "smem", "patches", "instances", "region")
     return {k: int(v) for k, v in zip(keys, out)}
+
+
+def nmpc_line_plan(h) -> dict:
+    """The line path of a handle: line work items per iteration (one warp
+    each), instances on it, threads and dynamic shared memory per CTA."""
+    out = (ctypes.c_int64 * 4)()
+    _check(LIB.nmpc_line_plan(h, out), "nmpc_line_plan")
+    return {k: int(v) for k, v in zip(("lines", "instances", "threads", "smem"), out)}
 
 
 def nmpc_launch_plan(h) -> dict:

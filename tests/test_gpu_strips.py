@@ -8,7 +8,8 @@ order: FP64 iterates agree to a few ulps of the largest term (relative
 1e-10), the mixed path's update Delta s to float32 accuracy (relative 1e-4 of
 |Delta s|).  The cases put actuators on strip corners and edges, use ragged
 strips (grids that are not multiples of the strip), and mix strip-path
-instances with a 1D instance on the cluster path in one handle.
+instances with a 1D instance (line path in mixed precision, cluster path in
+FP64) in one handle.
 """
 import numpy as np
 import pytest
@@ -204,17 +205,17 @@ def test_strip_residual_entry_point_matches_oracle(G):
 
 
 def test_auto_routes_large_stages_to_strips(G):
-    """strips = 0: a 256x256 stage goes to the strip path, a 64x64 stage and a
-    1D instance stay on the cluster path."""
+    """strips = 0: a 256x256 stage goes to the strip path, a 64x64 stage stays
+    on the cluster path and the 1D instance goes to the line path."""
     insts = [wl.heat2d(256, 256, 2, 4, 4, seed=98), wl.heat2d(64, 64, 2, 4, 2, seed=99),
              wl.heat1d(50, 3, 1, 0.01, seed=100)]
     h = G.nmpc_setup(insts, precision=G.NMPC_MIXED)
-    plan, lp = G.nmpc_strip_plan(h), G.nmpc_launch_plan(h)
+    plan, lp, ln = G.nmpc_strip_plan(h), G.nmpc_launch_plan(h), G.nmpc_line_plan(h)
     G.nmpc_destroy(h)
     ty = plan["strip_y"]
     assert plan["instances"] == 1 and plan["strip_x"] == 26 and 16 <= ty <= 256
     assert plan["strips"] == 2 * -(-256 // 26) * -(-256 // ty)
-    assert lp["work_items"] == 2 + 3
+    assert lp["work_items"] == 2 and ln["instances"] == 1 and ln["lines"] == 3
 
 
 @pytest.mark.parametrize("precision,rtol", [(0, 1e-5), (1, 1e-3)])
