@@ -103,7 +103,9 @@ typedef struct {
                       previous split residual r has r - e > max(tol,
                       split_min); from then on every iteration uses the
                       float64 residual (convergence is only ever declared on
-                      a float64 residual)                                     */
+                      a float64 residual).  Handles with strip-path instances
+                      use max(split_min, 1e-6): their split residual takes
+                      the stage differences from float32 values        */
   int u_local;     /* 1: the u-iteration uses the actuators' local responses
                       (P^{-1} is a fixed linear map, so Y(v3) = Y(0) + sum_b
                       v3_b Z(e_b) with Z(e_b) zero outside 2(n_lo-1) cells of

@@ -113,6 +113,10 @@ struct nmpc_handle {
 
 namespace {
 
+// Lower limit of the residual level at which handles with strip-path
+// instances switch to the float64 residual (see make_args).
+constexpr double STRIP_SPLIT_FLOOR = 1e-6;
+
 template <typename T>
 size_t small_shared_bytes() {
   return (sizeof(nmpc_dev::SmallShared<T>) + 15) & ~size_t(15);
@@ -183,7 +187,12 @@ IterArgs make_args(nmpc_handle* h) {
   A.tol = h->opts.tol;
   A.div_limit = h->opts.div_limit;
   A.alpha = h->opts.alpha;
-  A.split_min = h->opts.split_min;
+  // the strip path's split residual takes the O(1) stage differences from
+  // float32-truncated values: they move in steps of 2^-23 |x|, so its
+  // iteration cannot settle far below ~1e-6; such handles switch to the
+  // float64 residual by then at the latest
+  A.split_min = (h->n_strips > 0) ? std::max(h->opts.split_min, STRIP_SPLIT_FLOOR)
+                                  : h->opts.split_min;
   A.max_iter = h->opts.max_iter;
   A.n_lo = h->opts.n_lo;
   A.n_u_it = h->opts.n_u_it;

@@ -198,8 +198,10 @@ __device__ __forceinline__ void line_body(const IterArgs& A, LineShared& ws, int
       const float dphi = I.fk0 * (1.0f + I.fk1 * xv[t]);
       const float t1 = I.fh * (lphi[t] + I.fb0 * srcf[t]);
       const float t3 = I.fh * (I.fq * (xv[t] - rv) + dphi * mu);
-      // the O(1) differences in float64; at the last stage lambda_{N+1} is
-      // h qf (x_N - ref), an O(h) term
+      // the O(1) differences in float64 (taken in float32 from truncated
+      // values they would move in steps of 2^-23 |x|, and the split
+      // iteration would stall at that scale above tight tolerances); at the
+      // last stage lambda_{N+1} is h qf (x_N - ref), an O(h) term
       const double d3 = last ? -lam : ws.f[L_LN][pb0 + t] - lam;
       const float dx = d2f(xp - x), dl = d2f(d3);
       const float K1f = dx + t1;
@@ -324,11 +326,15 @@ __device__ __forceinline__ void line_body(const IterArgs& A, LineShared& ws, int
   double* Lo = A.lout[rd ^ 1] + so;
 #pragma unroll
   for (int t = 0; t < CPL; ++t) {
+    // every position q < 32 CPL exists (zeros past M): only the stores are
+    // predicated
     const int q = t * 32 + lane;
+    const int p = lpad<CPL>(q);
+    const double xn = fma(alpha, f2d(Y5[p]), ws.f[L_X][p]);
+    const double ln = fma(alpha, f2d(Y4[p]), ws.f[L_L][p]);
     if (q < M) {
-      const int p = lpad<CPL>(q);
-      Xo[q] = fma(alpha, f2d(Y5[p]), ws.f[L_X][p]);
-      Lo[q] = fma(alpha, f2d(Y4[p]), ws.f[L_L][p]);
+      Xo[q] = xn;
+      Lo[q] = ln;
     }
   }
   double* Uo = A.uout[rd ^ 1] + I.u_off + (long long)s * nu;

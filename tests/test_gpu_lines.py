@@ -209,3 +209,24 @@ def test_fp64_handles_keep_1d_on_the_cluster_path(G):
     h = G.nmpc_setup(_lines_batch()[:3], precision=G.NMPC_FP64)
     assert G.nmpc_line_plan(h)["instances"] == 0
     G.nmpc_destroy(h)
+
+
+def test_line_mixed_solve_reaches_a_tight_tolerance(G):
+    """Mixed precision at tol = 1e-9 on the line path (float32 lower layer,
+    float64 residual once the split residual's bound can no longer show the
+    level): every instance converges and the oracle's float64 residual of the
+    returned state is <= 1e-9."""
+    import torch
+    insts = _lines_batch()
+    s = G.Solver(insts, tol=1e-9, precision=G.NMPC_MIXED, max_iter=8000)
+    rc, st = s.solve()
+    torch.cuda.synchronize()
+    assert rc == G.NMPC_OK
+    x, u, lam = (t.cpu().numpy() for t in s.state())
+    s.close()
+    xs, us, ls = _split(G, insts, x, u, lam)
+    for b, inst in enumerate(insts):
+        p = O.Problem(inst)
+        K = O.kkt(p, xs[b].reshape((p.N,) + p.shape), us[b].reshape(p.N, p.nu),
+                  ls[b].reshape((p.N,) + p.shape))
+        assert O.kkt_norms(*K)[0] <= 1.0001e-9, b

@@ -263,3 +263,24 @@ def test_large_batch_horizon_100_state_passes_the_oracle_residual(G):
         r = O.kkt_norms(*K)[0]
         assert r <= 1e-6, (b, r)
         assert abs(r - st[b].res_inf) <= 1e-9 * r
+
+
+def test_strip_mixed_solve_reaches_a_tight_tolerance(G):
+    """Mixed precision at tol = 1e-8 on the strip path: the split residual's
+    float32 stage differences cannot resolve levels that low, so the handle
+    switches to the float64 residual by 1e-6 at the latest and converges on
+    it; the oracle's float64 residual of the returned state is <= 1e-8."""
+    import torch
+    insts = _batch(far=True)[:2]
+    s = G.Solver(insts, tol=1e-8, precision=G.NMPC_MIXED, max_iter=8000, strips=1, strip_rows=8)
+    rc, st = s.solve()
+    torch.cuda.synchronize()
+    assert rc == G.NMPC_OK
+    x, u, lam = (t.cpu().numpy() for t in s.state())
+    s.close()
+    xs, us, ls = _split(G, insts, x, u, lam)
+    for b, inst in enumerate(insts):
+        p = O.Problem(inst)
+        K = O.kkt(p, xs[b].reshape((p.N,) + p.shape), us[b].reshape(p.N, p.nu),
+                  ls[b].reshape((p.N,) + p.shape))
+        assert O.kkt_norms(*K)[0] <= 1.0001e-8, b
