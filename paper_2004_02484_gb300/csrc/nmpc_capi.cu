@@ -49,7 +49,7 @@ struct nmpc_handle {
   double* ub[3] = {nullptr, nullptr, nullptr};
   double* lb[3] = {nullptr, nullptr, nullptr};
   // control
-  int* ictl = nullptr;  // iter_k, (unused), n_active, (unused), grid barrier words [4]
+  int* ictl = nullptr;  // iter_k, closed-loop step, n_active, running line items, grid barrier words [4]
   unsigned long long* res_inf = nullptr;
   unsigned long long* res_err = nullptr;
   double* res_sq = nullptr;
@@ -103,7 +103,9 @@ struct nmpc_handle {
   double* v3_d = nullptr;  // v3 per control, written by k_patch
   // line path (k_line): one warp per 1D stage
   int4* lines_d = nullptr;
+  int4* lines_act_d = nullptr;  // items of running instances (solve mode)
   int n_lines = 0;
+  int line_grid = 0;  // CTAs of a k_line launch
   int n_line_inst = 0;
   size_t line_smem = 0;
   long long launches = 0;
@@ -146,7 +148,7 @@ void free_all(nmpc_handle* h) {
                   h->xb[0], h->xb[1], h->xb[2], h->ub[0], h->ub[1], h->ub[2],
                   h->lb[0], h->lb[1], h->lb[2], h->ictl, h->res_inf, h->res_err, h->res_sq,
                   h->res_first, h->status, h->iters, h->final_buf, h->fin_inf,
-                  h->fin_2, h->full_from, h->full0, h->scratch, h->strips_d, h->patches_d, h->lines_d,
+                  h->fin_2, h->full_from, h->full0, h->scratch, h->strips_d, h->patches_d, h->lines_d, h->lines_act_d,
                   h->v3_d};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -216,6 +218,8 @@ IterArgs make_args(nmpc_handle* h) {
   A.v3g = h->v3_d;
   A.lines = h->lines_d;
   A.n_lines = h->n_lines;
+  A.lines_act = h->lines_act_d;
+  A.n_lines_act = h->ictl + 3;
   return A;
 }
 
@@ -559,7 +563,7 @@ cudaError_t launch_strip(const nmpc_handle* h, const IterArgs& A, cudaStream_t s
 
 cudaError_t launch_line(const nmpc_handle* h, const IterArgs& A, cudaStream_t st, int mode, int j) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)((h->n_lines + nmpc_dev::LINE_WARPS - 1) / nmpc_dev::LINE_WARPS));
+  cfg.gridDim = dim3((unsigned)h->line_grid);
   cfg.blockDim = dim3(32 * nmpc_dev::LINE_WARPS);
   cfg.dynamicSmemBytes = h->line_smem;
   cfg.stream = st;
@@ -605,6 +609,11 @@ cudaError_t launch_iterate(nmpc_handle* h, const IterArgs& A, cudaStream_t st, i
 // One chunk of solve iterations on stream st: launches j = 0 .. chunk - 1
 // (iterations *iter_k + j), then the counter advance.
 cudaError_t enqueue_chunk(nmpc_handle* h, const IterArgs& A, cudaStream_t st, int chunk) {
+  if (h->n_lines > 0) {
+    // the line items of the instances still running
+    nmpc_dev::k_compact_lines<<<1, nmpc_dev::COMPACT_THREADS, 0, st>>>(A);
+    h->launches++;
+  }
   for (int i = 0; i < chunk; ++i) {
     cudaError_t e = launch_iterate<nmpc_dev::MODE_SOLVE>(h, A, st, i);
     if (e != cudaSuccess) return e;
@@ -1308,6 +1317,9 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
     delete h;
     return NMPC_ERR_UNSUPPORTED;
   }
+  // one warp per item of the whole list (solve-mode launches past the running
+  // items' count return at once)
+  h->line_grid = (h->n_lines + nmpc_dev::LINE_WARPS - 1) / nmpc_dev::LINE_WARPS;
   if (h->n_strips > 0) {
     h->strip_x = tx;
     h->strip_y = ty;
@@ -1362,6 +1374,7 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
   A(dev_alloc(&h->strips_d, h->n_strips));
   A(dev_alloc(&h->patches_d, h->n_patches));
   A(dev_alloc(&h->lines_d, h->n_lines));
+  A(dev_alloc(&h->lines_act_d, h->n_lines));
   A(dev_alloc(&h->v3_d, h->n_strips > 0 ? h->n_u : 0));
   A(dev_alloc(&h->act_d, act_all.size()));
   A(dev_alloc(&h->x0_d, h->n_g));

@@ -126,9 +126,12 @@ struct IterArgs {
   const int4* patches;
   int n_patches;
   double* v3g;
-  // line path (k_line): (instance, stage, cells per lane, 0) per 1D stage
+  // line path (k_line): (instance, stage, cells per lane, 0) per 1D stage;
+  // solve mode walks the items of running instances (k_compact_lines)
   const int4* lines;
   int n_lines;
+  int4* lines_act;
+  int* n_lines_act;
 };
 
 struct Cl {

@@ -342,8 +342,11 @@ __device__ __forceinline__ void line_body(const IterArgs& A, LineShared& ws, int
 }
 
 // One upper-layer iteration over the line work list (MODE_SOLVE: iteration
-// *iter_k + j with the convergence bookkeeping; MODE_ONESHOT: one residual or
-// iteration from the given buffers).  Item (b, s, CPL).
+// *iter_k + j with the convergence bookkeeping, over the items of the
+// instances running at the start of the chunk, compacted to the front of the
+// list and followed by empty items; MODE_ONESHOT: one residual or iteration
+// from the given buffers, over every item).  Item (b, s, CPL); one item per
+// warp, warps on an empty item return at once.
 __global__ void __launch_bounds__(LINE_WARPS * 32, 4) k_line(IterArgs A, int MODE, int j_launch) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -355,7 +358,9 @@ __global__ void __launch_bounds__(LINE_WARPS * 32, 4) k_line(IterArgs A, int MOD
   pdl_wait();  // the previous iteration's state, residuals and control words
   const int item = blockIdx.x * LINE_WARPS + warp;
   if (item >= A.n_lines) return;  // warp-uniform; no block barriers in this kernel
-  const int4 it = A.lines[item];
+  const int4* list = (MODE == MODE_SOLVE) ? A.lines_act : A.lines;
+  const int4 it = list[item];
+  if (it.x < 0) return;  // past the running items (solve mode)
   const int b = it.x, s = it.y, cpl = it.z;
 
   bool resid_only, full;
@@ -391,4 +396,47 @@ __global__ void __launch_bounds__(LINE_WARPS * 32, 4) k_line(IterArgs A, int MOD
       default: line_body<8, false>(A, ws, lane, b, s, k, rd, resid_only); break;
     }
   }
+}
+
+// The items of the line list whose instance is running, in list order (one
+// CTA: per round of blockDim items, ballots and a prefix over the warps'
+// counts), then empty items (instance -1) up to the list's length, and the
+// running items' number.  Runs at the start of every chunk of solve
+// iterations, so an instance that finishes inside a chunk keeps its items
+// (its stage-0 warp records the finish) until the next chunk.
+constexpr int COMPACT_THREADS = 1024;
+__global__ void __launch_bounds__(COMPACT_THREADS) k_compact_lines(IterArgs A) {
+  __shared__ int wofs[32];
+  __shared__ int total;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int base = 0;  // every thread keeps the same running count
+  for (int i0 = 0; i0 < A.n_lines; i0 += blockDim.x) {
+    const int i = i0 + threadIdx.x;
+    int4 it = make_int4(0, 0, 0, 0);
+    bool keep = false;
+    if (i < A.n_lines) {
+      it = A.lines[i];
+      keep = __ldcg(A.status + it.x) == ST_RUNNING;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) wofs[w] = __popc(m);
+    __syncthreads();
+    if (w == 0) {
+      const int c = (lane < nw) ? wofs[lane] : 0;
+      int incl = c;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      if (lane < nw) wofs[lane] = incl - c;
+      if (lane == 31) total = incl;
+    }
+    __syncthreads();
+    if (keep) A.lines_act[base + wofs[w] + __popc(m & ((1u << lane) - 1u))] = it;
+    base += total;
+    __syncthreads();  // wofs and total are rewritten by the next round
+  }
+  for (int i = base + threadIdx.x; i < A.n_lines; i += blockDim.x)
+    A.lines_act[i] = make_int4(-1, 0, 0, 0);
+  if (threadIdx.x == 0) *A.n_lines_act = base;
 }
