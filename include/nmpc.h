@@ -302,7 +302,8 @@ int64_t nmpc_launch_count(const nmpc_handle* h);
    launch, out[7] 1 if the u-iteration uses local responses, out[8] clusters
    of this shape the device keeps resident at once for the persistent
    launch, out[9] work items (instance stages) on the cluster path (the
-   strip path's are in nmpc_strip_plan), out[10] iteration steps launched
+   strip path's are in nmpc_strip_plan, the line path's in nmpc_line_plan),
+   out[10] iteration steps launched
    (one per iteration, whichever kernels it takes; one per solve when
    persistent) since setup.  Returns NMPC_ERR_BAD_ARG for a null handle or array. */
 int nmpc_launch_plan(const nmpc_handle* h, int64_t* out);

@@ -10,7 +10,9 @@ is K(S) = 0), only the iteration count and the time per iteration do.  The
 u-iteration's form (through the actuators' local responses or full-field
 sweeps) is a candidate as well.  Batches of large 2D stages (the strip path:
 one warp per strip of the stage grid) are tuned over the strip's own rows
-and the inner counts instead.
+and the inner counts instead, and mixed-precision batches of 1D stages (the
+line path: one warp per stage) over the inner counts, with the cluster path
+as one more candidate.
 
 Results are cached in a JSON file keyed by a bucketed signature of the batch
 (dimension, grid size, horizon, actuators, batch size, precision).
@@ -48,8 +50,21 @@ def signature(instances: Sequence, precision: int) -> str:
 STRIP_CELLS = 16384
 
 
-def candidates(instances: Sequence, quick: bool = True) -> List[Dict]:
+# 1D stages of at most this many cells run on the line path (mixed precision)
+LINE_MAX_CELLS = 256
+MIXED = 1  # NMPC_MIXED
+
+
+def candidates(instances: Sequence, quick: bool = True, precision: int = -1) -> List[Dict]:
+    """Option sets to time.  With ``precision`` = NMPC_MIXED, batches of 1D
+    instances that all run on the line path (one warp per stage; no launch
+    shape to choose) are tuned over the inner counts, plus the cluster path
+    with its automatic shape as a fallback candidate."""
     ngmax = max(i.mx * i.my for i in instances)
+    if precision == MIXED and all(i.dim == 1 and i.mx <= LINE_MAX_CELLS for i in instances):
+        inner = [(2, 1), (2, 2), (1, 1)] if quick else [(2, 1), (2, 2), (1, 1), (1, 2), (3, 1)]
+        out = [{"lines": 0, "n_lo": nlo, "n_u_it": nut, "check_every": 16} for nlo, nut in inner]
+        return out + [{"lines": 2, "n_lo": 2, "n_u_it": 1, "check_every": 16}]
     if all(i.dim == 2 and i.mx * i.my >= STRIP_CELLS for i in instances):
         rows = (0, 64) if quick else (0, 32, 64, 128)
         inner = [(2, 1), (2, 2), (1, 1)] if quick else [(2, 1), (2, 2), (1, 1), (1, 2), (3, 1)]
@@ -108,7 +123,7 @@ def tune(instances: Sequence, precision: int, tol: float = 1e-6, cache_path: str
     if key in cache and not force:
         return cache[key]
     best, best_t, reasons = None, float("inf"), []
-    for cfg in candidates(instances, quick):
+    for cfg in candidates(instances, quick, precision):
         t, why = _time_config(G, instances, precision, tol, cfg)
         if verbose:
             print(json.dumps({"cfg": cfg, "s_per_solve": t, "error": why}), flush=True)
@@ -131,4 +146,4 @@ def solver_opts(result: Dict) -> Dict:
     """The nmpc_opts fields of a tuning result."""
     return {k: v for k, v in result.items() if k in ("cluster", "threads", "n_lo", "n_u_it",
                                                      "u_local", "cells", "check_every",
-                                                     "strips", "strip_rows")}
+                                                     "strips", "strip_rows", "lines")}

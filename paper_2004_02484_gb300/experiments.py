@@ -52,8 +52,11 @@ def batch1d(n: int, tol: float = 1e-6, reps: int = 3, tune: int = 1, use_graph: 
     if tune:
         from . import autotune as AT
         opts = AT.solver_opts(AT.tune(insts, G.NMPC_MIXED, tol=tol))
+    kw = dict(opts)
+    if lines or "lines" not in kw:
+        kw["lines"] = lines  # an explicit choice overrides the tuned one
     s = G.Solver(insts, tol=tol, precision=G.NMPC_MIXED, max_iter=20000, use_graph=use_graph,
-                 lines=lines, **opts)
+                 **kw)
     rc, st = s.solve()
     assert rc == G.NMPC_OK, rc
     torch.cuda.synchronize()

@@ -21,6 +21,19 @@ def test_small_batches_are_tuned_over_cluster_shapes():
     assert {x["cluster"] for x in AT.candidates(oned)} == {0, 1}
 
 
+def test_mixed_1d_batches_are_tuned_over_line_inner_counts():
+    oned = wl.heat1d_ragged_batch(8)
+    c = AT.candidates(oned, quick=True, precision=1)
+    assert [x["lines"] for x in c] == [0, 0, 0, 2]
+    assert {(x["n_lo"], x["n_u_it"]) for x in c[:3]} == {(2, 1), (2, 2), (1, 1)}
+    assert all(set(AT.solver_opts(dict(x, s_per_solve=1.0))) == set(x) for x in c)
+    # FP64 batches, and batches with a stage beyond the line path, keep the
+    # cluster candidates
+    assert all("lines" not in x for x in AT.candidates(oned, quick=True, precision=0))
+    wide = oned + [wl.heat1d(300, 5, 2, 0.01, seed=5)]
+    assert all("lines" not in x for x in AT.candidates(wide, quick=True, precision=1))
+
+
 def test_signature_buckets_sizes_and_separates_precisions():
     a = wl.heat1d_ragged_batch(16)
     b = wl.heat1d_ragged_batch(17)
