@@ -74,11 +74,33 @@ def dist_env():
     return rank, world, local
 
 
+def step_seed(step: int, rank: int) -> int:
+    """Seed of the initial field of a rank's step: step 0 of rank 0 is the
+    canonical seed-1 field, every other (rank, step) a fresh field of its own
+    (ranks solve disjoint instances: replicas, no data-path collective)."""
+    return 1 if (step == 0 and rank == 0) else 100_000 + 1000 * rank + step
+
+
 def step_instance(step: int, rank: int):
     from paper_2004_02484_gb300 import workloads as wl
-    # step 0 is the canonical seed-1 field; later steps draw fresh seeded fields
-    seed = 1 if (step == 0 and rank == 0) else 100_000 + 1000 * rank + step
-    return wl.heat2d_single(seed=seed)
+    return wl.heat2d_single(seed=step_seed(step, rank))
+
+
+def max_over_ranks(x: float, device) -> float:
+    """The largest x over the ranks of the process group (x itself when
+    there is none): the job's time is its slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, steps: int, seconds: float) -> float:
+    """Whole-job solves/s: every rank's steps over the slowest rank's time."""
+    return world * steps / seconds
 
 
 class ClockSampler:
@@ -241,13 +263,10 @@ def main():
         torch.cuda.synchronize()
     launches = G.nmpc_launch_count(solver.h) - launches0
     it_launches = G.nmpc_launch_plan(solver.h)["iteration_launches"] - it_launches0
-    t_ms = sum(a.elapsed_time(b_) for a, b_ in ev)
+    t_ms = max_over_ranks(sum(a.elapsed_time(b_) for a, b_ in ev), dev)
     if world > 1:
-        tt = torch.tensor([t_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(tt.item())
         torch.distributed.barrier()
-    value = world * args.steps / (t_ms / 1e3)
+    value = job_rate(world, args.steps, t_ms / 1e3)
 
     # end to end through the host-pointer entry point (pinned host buffers)
     x0h = [torch.from_numpy(G.pack_fields([i], "x0")).pin_memory().numpy() for i in insts]
@@ -258,11 +277,7 @@ def main():
     for k in range(args.steps):
         rc, st = G.nmpc_solve_host(solver.h, x0h[args.warmup + k], refh[args.warmup + k], uh, 1)
         assert rc == G.NMPC_OK
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
 
     # roofline of the dominant kernel (the fused iteration kernel, one launch
     # per iteration): the timed region divided by its launches (the region
@@ -310,7 +325,7 @@ def main():
                           "l2": "flushed between steps (256 MiB write) outside the per-step events",
                           "iterations_per_solve": {"min": min(iters), "max": max(iters),
                                                    "mean": sum(iters) / len(iters)}},
-               "e2e": {"value": world * args.steps / e2e_s, "unit": "solves/s",
+               "e2e": {"value": job_rate(world, args.steps, e2e_s), "unit": "solves/s",
                        "h2d_bytes_per_step": 2 * 8 * ins.mx * ins.my,
                        "d2h_bytes_per_step": 8 * ins.horizon * len(ins.act)},
                "gpu_launches": launches,

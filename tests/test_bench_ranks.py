@@ -1,0 +1,66 @@
+"""The bench's multi-rank path on CPU (gloo, world size 2).
+
+Instances are independent, so `bench.py --gpus N` runs replicas: each rank
+solves its own seeded instances and the only collectives are the barrier and
+the max over ranks of the timed region.  These tests run that host logic in
+two processes on the gloo backend: disjoint instance seeds per rank, the max
+over ranks seen identically by both, and the whole-job rate (every rank's
+steps over the slowest rank's time)."""
+import os
+import socket
+
+import pytest
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank: int, world: int, port: int, out):
+    import torch
+    import torch.distributed as dist
+    import bench
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port),
+                       "RANK": str(rank), "WORLD_SIZE": str(world), "LOCAL_RANK": str(rank)})
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    r, w, lr = bench.dist_env()
+    seeds = [bench.step_seed(s, r) for s in range(16)]
+    gathered = [None] * w
+    dist.all_gather_object(gathered, seeds)
+    # rank r's timed region took 1.5 + r seconds
+    t = bench.max_over_ranks(1.5 + r, torch.device("cpu"))
+    dist.barrier()
+    out.put((r, w, lr, gathered, t, bench.job_rate(w, 10, t)))
+    dist.destroy_process_group()
+
+
+def test_two_ranks_solve_disjoint_instances_and_agree_on_the_slowest_time():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    res.sort()
+    for r, (rank, world, local, gathered, t, rate) in enumerate(res):
+        assert (rank, world, local) == (r, 2, r)
+        assert t == 2.5                      # the slower rank's time, on both
+        assert rate == pytest.approx(2 * 10 / 2.5)
+        s0, s1 = gathered
+        assert len(set(s0)) == 16 and len(set(s1)) == 16
+        assert not set(s0) & set(s1)         # disjoint instances
+        assert s0[0] == 1                    # rank 0 starts from the canonical field
+
+
+def test_single_process_needs_no_group():
+    import torch
+    import bench
+    assert bench.max_over_ranks(3.25, torch.device("cpu")) == 3.25
+    assert bench.job_rate(1, 4, 2.0) == 2.0
