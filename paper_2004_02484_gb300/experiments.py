@@ -38,8 +38,9 @@ import time
 
 import numpy as np
 
-from . import nmpc as G
 from . import workloads as wl
+
+G = None  # the library binding, imported by main() once the library is built
 
 BYTES_PER_CELL_STAGE = 32  # read x, lambda; write x, lambda (float64)
 
@@ -217,7 +218,9 @@ def main():
     import torch
     torch.cuda.set_device(0)
     from . import build
-    build.build()
+    build.build()  # before the binding loads the library (a rebuilt one, if sources changed)
+    global G
+    from . import nmpc as G
     if a.which == "batch1d":
         print(json.dumps(batch1d(a.n or 1024, reps=a.reps, tune=a.tune, use_graph=a.graph,
                                  lines=a.lines)), flush=True)
