@@ -73,3 +73,19 @@ def test_setup_rejects_bad_descriptors_before_touching_the_device(lib_path):
     descs, keep = G.make_descs([wl.heat1d_single()])
     h = ctypes.c_void_p()
     assert G.LIB.nmpc_setup(descs, 1, ctypes.byref(o), ctypes.byref(h)) == G.NMPC_ERR_BAD_ARG
+
+
+def test_path_options_default_to_auto_and_are_validated_on_the_host(lib_path):
+    """strips / strip_rows / lines (the last fields of nmpc_opts: a layout
+    mismatch between the binding and the header would show here) default to
+    0 = automatic, and out-of-range values are rejected before any CUDA call."""
+    from paper_2004_02484_gb300 import nmpc as G
+    from paper_2004_02484_gb300 import workloads as wl
+    o = G.nmpc_default_opts()
+    assert (o.strips, o.strip_rows, o.lines) == (0, 0, 0)
+    for field, value in (("lines", 3), ("lines", -1), ("strips", 3)):
+        o = G.nmpc_default_opts()
+        setattr(o, field, value)
+        descs, keep = G.make_descs([wl.heat1d_single()])
+        h = ctypes.c_void_p()
+        assert G.LIB.nmpc_setup(descs, 1, ctypes.byref(o), ctypes.byref(h)) == G.NMPC_ERR_BAD_ARG
