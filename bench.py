@@ -56,11 +56,14 @@ TRAFFIC_BYTES_PER_LAUNCH = 3.48e6
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--ref-iters", type=int, default=8, help="oracle iterations per reference step")
+    ap.add_argument("--ref-iters", type=int, default=300,
+                    help="oracle iterations timed on the host in all: the cpu_baseline sample, "
+                         "and the reference arm's (spread over its steps, at least one per "
+                         "step); ~30 ms each on the GPU box's Grace cores")
     ap.add_argument("--graph", type=int, default=1,
                     help="1: the solve loop is one CUDA graph; 0: chunks of iteration launches "
                          "from the host (the same kernels; a profiler can capture them)")
@@ -104,7 +107,9 @@ def job_rate(world: int, steps: int, seconds: float) -> float:
 
 
 class ClockSampler:
-    """nvidia-smi samples every 200 ms during the timed region."""
+    """nvidia-smi samples every 100 ms during the timed region: entering
+    waits (up to 3 s) for the sampler's first line, and the summary covers
+    the lines read from then on."""
 
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -114,15 +119,20 @@ class ClockSampler:
         self.index = index
         self.rows = []
         self.proc = None
+        self.start = 0
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t_end = time.time() + 3.0
+            while not self.rows and time.time() < t_end and self.proc.poll() is None:
+                time.sleep(0.01)
+            self.start = len(self.rows)  # samples from here on fall in the timed region
         except Exception:
             self.proc = None
         return self
@@ -142,7 +152,10 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
+        # the timed region's samples (the last one before it when it was too
+        # short to hold one)
+        rows = self.rows[self.start:] or self.rows[-1:]
+        for r in rows:
             try:
                 sm.append(float(r[0]))
                 mx = float(r[1])
@@ -183,6 +196,12 @@ def oracle_iters_to_tol():
     return info["iters"]
 
 
+def ref_iters_per_step(total: int, steps: int) -> int:
+    """Oracle iterations per reference step: about `total` over the run (a
+    bounded sample whatever the step count), at least one per step."""
+    return max(1, round(total / max(1, steps)))
+
+
 def reference_arm(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -191,13 +210,14 @@ def reference_arm(args):
     n_it = oracle_iters_to_tol()  # part of warm-up: the oracle's own iteration count
     for _ in range(args.warmup):
         run_oracle_sample(1)
+    per_step = ref_iters_per_step(args.ref_iters, args.steps)
     t = 0.0
     for _ in range(args.steps):
-        t += run_oracle_sample(args.ref_iters)
-    sec_per_iter = t / (args.steps * args.ref_iters)
+        t += run_oracle_sample(per_step)
+    sec_per_iter = t / (args.steps * per_step)
     value = 1.0 / (sec_per_iter * n_it)
     cb = {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-          "sample": f"{args.ref_iters} FP64 numpy oracle iterations per step x {args.steps} steps; "
+          "sample": f"{per_step} FP64 numpy oracle iterations per step x {args.steps} steps; "
                     f"solves/s = 1 / (s per iteration x {n_it} oracle iterations to 1e-6)"}
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
                       "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,

@@ -1,4 +1,5 @@
-"""The bench's multi-rank path on CPU (gloo, world size 2).
+"""The bench's host logic on CPU: its multi-rank path (gloo, world size 2),
+the size of its host-side oracle sample, and its clock record.
 
 Instances are independent, so `bench.py --gpus N` runs replicas: each rank
 solves its own seeded instances and the only collectives are the barrier and
@@ -64,3 +65,27 @@ def test_single_process_needs_no_group():
     import bench
     assert bench.max_over_ranks(3.25, torch.device("cpu")) == 3.25
     assert bench.job_rate(1, 4, 2.0) == 2.0
+
+
+def test_reference_sample_is_bounded_whatever_the_step_count():
+    import bench
+    assert bench.ref_iters_per_step(300, 100) == 3
+    assert bench.ref_iters_per_step(300, 10) == 30
+    assert bench.ref_iters_per_step(300, 1000) == 1   # at least one per step
+    assert bench.ref_iters_per_step(300, 0) == 300
+
+
+def test_clock_summary_reads_the_timed_region_and_flags_throttling():
+    import bench
+    c = bench.ClockSampler(0)
+    idle = ["345", "2070", "90.1", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"]
+    busy = ["2070", "2070", "1100.0", "0x4", "Not Active", "Not Active", "Not Active", "Active"]
+    hot = ["1800", "2070", "1300.0", "0x40", "Not Active", "Active", "Not Active", "Not Active"]
+    c.rows = [idle, busy, busy, hot, ["garbage"]]
+    c.start = 1  # the idle sample came before the timed region
+    s = c.summary()
+    assert s["samples"] == 3 and s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+    # a region too short for a sample of its own: the last one before it
+    c.rows, c.start = [idle, busy], 2
+    assert c.summary()["samples"] == 1 and c.summary()["sm_mhz"] == 2070.0
