@@ -115,8 +115,8 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
-        self.index = index
+    def __init__(self, index):
+        self.index = index  # nvidia-smi -i selector: a GPU UUID or a physical index
         self.rows = []
         self.proc = None
         self.start = 0
@@ -166,6 +166,26 @@ class ClockSampler:
                 pass
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def smi_selector(dev: int) -> str:
+    """The nvidia-smi -i selector of CUDA device `dev` of this process.
+
+    nvidia-smi numbers physical GPUs and ignores CUDA_VISIBLE_DEVICES, so the
+    device's UUID is used (torch reports it without the "GPU-" prefix); failing
+    that, the dev-th entry of a numeric CUDA_VISIBLE_DEVICES, else dev."""
+    try:
+        import torch
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        if u and u.lower() != "none":
+            return u if u.startswith(("GPU-", "MIG-")) else "GPU-" + u
+    except Exception:
+        pass
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [v.strip() for v in vis.split(",") if v.strip()]
+    if dev < len(ids):
+        return ids[dev]
+    return str(dev)
 
 
 def measured_peaks():
@@ -272,7 +292,7 @@ def main():
     iters, launches0 = [], G.nmpc_launch_count(solver.h)
     it_launches0 = G.nmpc_launch_plan(solver.h)["iteration_launches"]
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
+    with ClockSampler(smi_selector(local)) as clk:
         for k in range(args.steps):
             flush.zero_()
             ev[k][0].record(stream)

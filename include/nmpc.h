@@ -161,7 +161,11 @@ typedef struct nmpc_handle nmpc_handle;
 void nmpc_default_opts(nmpc_opts* o);
 
 /* Validate the descriptors, build the device instance table and allocate the
-   workspace on the current CUDA device.  On success *out owns everything;
+   workspace on the current CUDA device.  An instance is the discretized
+   problem of Sec. 2 (eq. 4, a first-order model: a = 0 in eq. 1) posed as
+   the N-stage NLP of eq. 6; the workspace holds the primal-dual iterates
+   S = (s_1, ..., s_N), s_i = (x_i, u_i, lambda_i) of Sec. 3.2, twice (the
+   iterates k and k + 1 of eq. 15) plus the handle's current state.  On success *out owns everything;
    release it with nmpc_destroy.  Errors: BAD_ARG (a descriptor field out of
    range, NULL pointers), UNSUPPORTED (n_u > NMPC_MAX_NU, ng > NMPC_MAX_NG),
    NO_DEVICE, CUDA.  Synchronous. */
@@ -169,7 +173,11 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
                nmpc_handle** out);
 
 /* Solve every instance from x0 (packed [sum ng], device) tracking ref
-   (packed [sum ng], device).  horizon: 0 = each instance's own N; only 0 or a
+   (packed [sum ng], device): the KKT system K(S) = 0 of eq. 9 by the
+   upper-layer iteration of eq. 15 (every stage's Delta s_i from iterate k,
+   each by the lower-layer solve of Sec. 4.3, eqs. 21-24, with the
+   u-iteration of Sec. 5.2), stopped by the rule of Table 2 with the
+   threshold opts.tol: ||K(S^k)||_inf <= tol, evaluated in float64.  horizon: 0 = each instance's own N; only 0 or a
    value equal to every instance's N is accepted (BAD_ARG otherwise).
    weights: NULL, or device [n_instances][3] = (q, r, qf) overriding the
    descriptors for this and later solves.  init: NMPC_INIT_COLD / _WARM / _GUESS.
@@ -278,8 +286,10 @@ int nmpc_closed_loop_learned(nmpc_handle* h, double* w, const double* ref, int s
                              nmpc_start_fn start, void* ctx, const double* u_guess,
                              double* u_hist, int* iters_hist, double* res_hist, void* stream);
 
-/* Copy the handle's current state (after a solve: the returned iterates) to
-   packed device arrays x, u, lam; any pointer may be NULL to skip it. */
+/* Copy the handle's current state (after a solve: the returned iterates
+   S^k = (x_i, u_i, lambda_i), i = 1..N, the primal-dual variables of
+   Sec. 3.2) to packed device arrays x, u, lam; any pointer may be NULL to
+   skip it. */
 int nmpc_get_state(nmpc_handle* h, double* x, double* u, double* lam, void* stream);
 
 /* Replace the handle's current state (the NMPC_INIT_WARM start). */
@@ -335,7 +345,13 @@ int nmpc_line_plan(const nmpc_handle* h, int64_t* out);
    on a device looks up that array's device address (make that first call
    before any stream capture).  desc: the instance (act_cell is read during
    the call); opts: NULL for defaults; x0, ref: device [mx*my]; u_out: device
-   [horizon*n_u]; stats: host, one entry.  Returns UNSUPPORTED (and prints the
+   [horizon*n_u]; stats: host, one entry.  It always runs the cluster path
+   (one thread-block cluster per stage, or one CTA per stage over a slab in
+   the static array when a stage does not fit a cluster), never the strip or
+   line path: opts.strips and opts.lines must be 0 or 2 (1, forcing one of
+   those paths, returns UNSUPPORTED); opts.strip_rows, opts.persistent and
+   opts.use_graph are ignored (the iterations are launched from the host in
+   chunks of check_every).  Returns UNSUPPORTED (and prints the
    needed size) when the instance's workspace exceeds the static array,
    otherwise as nmpc_solve.  Every call reuses the same array, and the call
    resets whatever must start from zero; calls whose GPU work overlaps (other

@@ -1830,8 +1830,17 @@ extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
   nmpc_default_opts(&o);
   if (opts) o = *opts;
   if (!opts_ok(o)) return NMPC_ERR_BAD_ARG;
+  // this entry point runs the cluster (or global-slab) path only: a forced
+  // strip or line path cannot be honoured
+  if (o.strips == 1 || o.lines == 1) return NMPC_ERR_UNSUPPORTED;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return NMPC_ERR_NO_DEVICE;
+  // per-device set-up first (the workspace address and the kernels'
+  // shared-memory and cluster limits), so that the launch plan below sees
+  // configured kernels on the first call in a process as on every later one
+  void* base_v = nullptr;
+  rc = noalloc_workspace(&base_v);
+  if (rc != NMPC_OK) return rc;
 
   const nmpc_desc& d = *desc;
   const bool mixed = (o.precision == NMPC_MIXED);
@@ -1896,9 +1905,6 @@ extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
             off, (unsigned)NMPC_NOALLOC_SCRATCH_BYTES);
     return NMPC_ERR_UNSUPPORTED;
   }
-  void* base_v = nullptr;
-  rc = noalloc_workspace(&base_v);
-  if (rc != NMPC_OK) return rc;
   char* base = static_cast<char*>(base_v);
   cudaStream_t st = (cudaStream_t)stream;
 
