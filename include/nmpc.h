@@ -327,6 +327,24 @@ int nmpc_launch_plan(const nmpc_handle* h, int64_t* out);
    is on the strip path.  NMPC_ERR_BAD_ARG for NULL arguments. */
 int nmpc_strip_plan(const nmpc_handle* h, int64_t* out);
 
+/* Per-kernel device timing (no counterpart in the paper; for measurement):
+   with enable != 0, every later launch of the iteration kernels that is not
+   being captured into a CUDA graph is bracketed by a CUDA event pair on its
+   stream (which also stops consecutive launches from overlapping their
+   start and end, so each pair times its kernel alone); enable = 0 stops
+   recording.  Either call clears the totals.  Solves with opts.use_graph
+   run their iterations inside a graph and are not timed: use use_graph = 0
+   for timed runs.  Synchronizes on the recorded events.  BAD_ARG for a NULL
+   handle. */
+int nmpc_kernel_timing(nmpc_handle* h, int enable);
+
+/* Totals since the last nmpc_kernel_timing call, per kernel kind k = 0
+   cluster-path iteration kernel (k_iterate), 1 actuator patches (k_patch),
+   2 strips (k_strip), 3 lines (k_line): launches[k] timed launches and
+   ms[k] their summed device time in milliseconds.  Waits for the recorded
+   events.  BAD_ARG for NULL arguments. */
+int nmpc_kernel_times(nmpc_handle* h, int64_t* launches, double* ms);
+
 /* Line path of the handle (opts.lines): out[0] line work items per
    iteration (one warp each: an (instance, stage) of a 1D instance), out[1]
    instances on the line path, out[2] threads per CTA, out[3] dynamic shared

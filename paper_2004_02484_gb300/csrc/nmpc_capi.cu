@@ -109,6 +109,17 @@ struct nmpc_handle {
   int n_line_inst = 0;
   size_t line_smem = 0;
   long long launches = 0;
+  // per-kernel CUDA-event timing (nmpc_kernel_timing): event pairs around
+  // launches that are not being captured, summed per kernel kind
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_free;
+  struct TimedLaunch {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<TimedLaunch> ev_pending;
+  double kt_ms[4] = {0, 0, 0, 0};
+  long long kt_n[4] = {0, 0, 0, 0};
   long long iter_launches = 0;  // iteration steps (each one or two kernel launches)
   bool has_state = false;
 };
@@ -575,6 +586,58 @@ cudaError_t launch_line(const nmpc_handle* h, const IterArgs& A, cudaStream_t st
   return cudaLaunchKernelEx(&cfg, nmpc_dev::k_line, A, mode, j);
 }
 
+// Kernel kinds of nmpc_kernel_times.
+enum { KT_CLUSTER = 0, KT_PATCH = 1, KT_STRIP = 2, KT_LINE = 3 };
+
+// Sum the elapsed times of the recorded launches into the per-kind totals and
+// recycle their events (waits for the last one).
+cudaError_t harvest_timing(nmpc_handle* h) {
+  if (h->ev_pending.empty()) return cudaSuccess;
+  cudaError_t e = cudaEventSynchronize(h->ev_pending.back().b);
+  for (auto& t : h->ev_pending) {
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t.a, t.b);
+    h->kt_ms[t.kind] += ms;
+    h->kt_n[t.kind] += 1;
+    h->ev_free.push_back(t.a);
+    h->ev_free.push_back(t.b);
+  }
+  h->ev_pending.clear();
+  return e;
+}
+
+cudaError_t take_event(nmpc_handle* h, cudaEvent_t* ev) {
+  if (h->ev_free.empty()) return cudaEventCreate(ev);
+  *ev = h->ev_free.back();
+  h->ev_free.pop_back();
+  return cudaSuccess;
+}
+
+// launch() bracketed by a CUDA event pair on st when the handle times kernels
+// and st is not capturing a graph (events in a capture would become graph
+// dependencies, not timestamps).
+template <typename F>
+cudaError_t timed(nmpc_handle* h, int kind, cudaStream_t st, F launch) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (!h->timing || cudaStreamIsCapturing(st, &cs) != cudaSuccess ||
+      cs != cudaStreamCaptureStatusNone)
+    return launch();
+  if (h->ev_pending.size() >= 4096) {
+    cudaError_t e = harvest_timing(h);
+    if (e != cudaSuccess) return e;
+  }
+  cudaEvent_t a, b;
+  cudaError_t e = take_event(h, &a);
+  if (e == cudaSuccess) e = take_event(h, &b);
+  if (e == cudaSuccess) e = cudaEventRecord(a, st);
+  if (e != cudaSuccess) return e;
+  e = launch();
+  if (e != cudaSuccess) return e;
+  e = cudaEventRecord(b, st);
+  if (e == cudaSuccess) h->ev_pending.push_back({kind, a, b});
+  return e;
+}
+
 // One iteration (or one-shot pass): the cluster kernel over the cluster
 // path's work items, the strip kernels over the strips and the line kernel
 // over the 1D stages, whichever exist.
@@ -585,23 +648,31 @@ cudaError_t launch_iterate(nmpc_handle* h, const IterArgs& A, cudaStream_t st, i
   if (h->n_work > 0) {
     h->launches++;
     const LaunchPlan P = plan_of(h);
-    e = h->mixed ? launch_k<float>(P, A, st, MODE, j) : launch_k<double>(P, A, st, MODE, j);
+    e = timed(h, KT_CLUSTER, st, [&]() {
+      return h->mixed ? launch_k<float>(P, A, st, MODE, j) : launch_k<double>(P, A, st, MODE, j);
+    });
     if (e != cudaSuccess) return e;
   }
   if (h->n_strips > 0) {
     // the actuators' v3 first (not needed by a residual-only pass)
     if (!(MODE == nmpc_dev::MODE_ONESHOT && A.resid_only)) {
       h->launches++;
-      e = h->mixed ? launch_patch<float>(h, A, st, MODE, j) : launch_patch<double>(h, A, st, MODE, j);
+      e = timed(h, KT_PATCH, st, [&]() {
+        return h->mixed ? launch_patch<float>(h, A, st, MODE, j)
+                        : launch_patch<double>(h, A, st, MODE, j);
+      });
       if (e != cudaSuccess) return e;
     }
     h->launches++;
-    e = h->mixed ? launch_strip<float>(h, A, st, MODE, j) : launch_strip<double>(h, A, st, MODE, j);
+    e = timed(h, KT_STRIP, st, [&]() {
+      return h->mixed ? launch_strip<float>(h, A, st, MODE, j)
+                      : launch_strip<double>(h, A, st, MODE, j);
+    });
     if (e != cudaSuccess) return e;
   }
   if (h->n_lines > 0) {
     h->launches++;
-    e = launch_line(h, A, st, MODE, j);
+    e = timed(h, KT_LINE, st, [&]() { return launch_line(h, A, st, MODE, j); });
   }
   return e;
 }
@@ -1734,8 +1805,34 @@ int nmpc_line_plan(const nmpc_handle* h, int64_t* out) {
 void nmpc_destroy(nmpc_handle* h) {
   if (!h) return;
   cudaDeviceSynchronize();
+  for (auto& t : h->ev_pending) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  for (auto ev : h->ev_free) cudaEventDestroy(ev);
   free_all(h);
   delete h;
+}
+
+int nmpc_kernel_timing(nmpc_handle* h, int enable) {
+  if (!h) return NMPC_ERR_BAD_ARG;
+  CK(harvest_timing(h));
+  for (int q = 0; q < 4; ++q) {
+    h->kt_ms[q] = 0.0;
+    h->kt_n[q] = 0;
+  }
+  h->timing = (enable != 0);
+  return NMPC_OK;
+}
+
+int nmpc_kernel_times(nmpc_handle* h, int64_t* launches, double* ms) {
+  if (!h || !launches || !ms) return NMPC_ERR_BAD_ARG;
+  CK(harvest_timing(h));
+  for (int q = 0; q < 4; ++q) {
+    launches[q] = h->kt_n[q];
+    ms[q] = h->kt_ms[q];
+  }
+  return NMPC_OK;
 }
 
 const char* nmpc_strerror(int code) {

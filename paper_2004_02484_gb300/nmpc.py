@@ -65,7 +65,7 @@ EXPORTED = ["nmpc_default_opts", "nmpc_setup", "nmpc_solve", "nmpc_solve_host",
             "nmpc_sizes", "nmpc_launch_count", "nmpc_launch_plan", "nmpc_strip_plan", "nmpc_line_plan", "nmpc_start_state", "nmpc_rollout", "nmpc_rollout_fused", "nmpc_destroy",
             "nmpc_strerror",
             "nmpc_solve_noalloc", "nmpc_plant_step", "nmpc_closed_loop",
-            "nmpc_closed_loop_learned"]
+            "nmpc_closed_loop_learned", "nmpc_kernel_timing", "nmpc_kernel_times"]
 
 
 # step start of nmpc_closed_loop_learned: void (*)(void* ctx, void* stream)
@@ -104,6 +104,9 @@ def _load() -> ctypes.CDLL:
         "nmpc_plant_step": (I, [P, P, D, I, P, P]),
         "nmpc_closed_loop": (I, [P, P, P, I, I, P, P, P, P]),
         "nmpc_closed_loop_learned": (I, [P, P, P, I, I, START_FN, P, P, P, P, P, P]),
+        "nmpc_kernel_timing": (I, [P, I]),
+        "nmpc_kernel_times": (I, [P, ctypes.POINTER(ctypes.c_int64),
+                                  ctypes.POINTER(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -195,6 +198,24 @@ def nmpc_line_plan(h) -> dict:
     out = (ctypes.c_int64 * 4)()
     _check(LIB.nmpc_line_plan(h, out), "nmpc_line_plan")
     return {k: int(v) for k, v in zip(("lines", "instances", "threads", "smem"), out)}
+
+
+KERNEL_KINDS = ("k_iterate", "k_patch", "k_strip", "k_line")
+
+
+def nmpc_kernel_timing(h, enable: bool = True) -> None:
+    """Start (or stop) CUDA-event timing of the iteration kernels' launches
+    outside graphs; clears the totals."""
+    _check(LIB.nmpc_kernel_timing(h, 1 if enable else 0), "nmpc_kernel_timing")
+
+
+def nmpc_kernel_times(h) -> dict:
+    """{kernel: (timed launches, summed device ms)} since the last
+    nmpc_kernel_timing call (waits for the recorded events)."""
+    n = (ctypes.c_int64 * 4)()
+    ms = (ctypes.c_double * 4)()
+    _check(LIB.nmpc_kernel_times(h, n, ms), "nmpc_kernel_times")
+    return {k: (int(n[i]), float(ms[i])) for i, k in enumerate(KERNEL_KINDS)}
 
 
 def nmpc_launch_plan(h) -> dict:

@@ -69,10 +69,21 @@ def test_single_process_needs_no_group():
 
 def test_reference_sample_is_bounded_whatever_the_step_count():
     import bench
-    assert bench.ref_iters_per_step(300, 100) == 3
-    assert bench.ref_iters_per_step(300, 10) == 30
-    assert bench.ref_iters_per_step(300, 1000) == 1   # at least one per step
-    assert bench.ref_iters_per_step(300, 0) == 300
+    assert bench.ref_chunk(20) == 15
+    assert bench.ref_chunk(100) == 3
+    assert bench.ref_chunk(1000) == 1                  # at least one per step
+    assert bench.ref_chunk(0) == 300
+    for k in (1, 7, 20, 64, 299):                      # about 300 iterations in all
+        assert 300 <= k * bench.ref_chunk(k) < 300 + k
+
+
+def test_batches_of_ranks_and_of_training_are_disjoint():
+    import bench
+    starts = {bench.batch_seed(r, t) for r in range(8) for t in (False, True)}
+    assert len(starts) == 16
+    # 64 consecutive seeds per batch never overlap another batch's
+    ranges = sorted(starts)
+    assert all(b - a >= 64 for a, b in zip(ranges, ranges[1:]))
 
 
 def test_clock_summary_reads_the_timed_region_and_flags_throttling():
