@@ -302,8 +302,9 @@ def secondary(args, rank, world, dev):
     from paper_2004_02484_gb300 import workloads as wl
     n_steps, n_warm = 50, 3
     insts = [wl.heat2d_single(seed=step_seed(s, rank)) for s in range(n_warm + n_steps)]
-    # the settings the autotuner picks for this workload (n_lo = 1, n_u_it = 1)
-    o = dict(tol=TOL, precision=G.NMPC_MIXED, max_iter=5000, n_lo=1, n_u_it=1)
+    # the settings the autotuner picks for this workload (n_lo = 1, n_u_it = 1,
+    # clusters of 8 CTAs per stage)
+    o = dict(tol=TOL, precision=G.NMPC_MIXED, max_iter=5000, n_lo=1, n_u_it=1, cluster=8)
     if args.variant == "redblack":
         o["variant"] = G.NMPC_VARIANT_REDBLACK
     s = G.Solver([insts[0]], **o)

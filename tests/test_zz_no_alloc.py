@@ -104,10 +104,10 @@ def test_noalloc_mixed_1d_instance_against_the_line_path(G):
 
 
 def test_noalloc_global_slab_stage_against_the_strip_path(G):
-    # a 384x384 stage fits no cluster of shared-memory slabs, so this entry
+    # a 320x320 stage fits no cluster of shared-memory slabs, so this entry
     # point runs one CTA per stage over a slab in the static array (about
-    # 20 MB of its 32 MiB); the handle puts the instance on the strip path
-    inst = wl.heat2d(384, 384, 3, 2, 2, seed=43)
+    # 23 MB of its 32 MiB); the handle puts the instance on the strip path
+    inst = wl.heat2d(320, 320, 3, 2, 2, seed=43)
     opts = dict(tol=1e-6, precision=1)
     ref = _handle_solve(G, inst, **opts)
     got = _noalloc_solve(G, inst, **opts)
