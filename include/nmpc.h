@@ -50,6 +50,18 @@ extern "C" {
 #define NMPC_MIXED 1 /* lower layer (Sec. 4.3) in float32; KKT residual, norms,
                         convergence test and the update of S in float64       */
 
+#define NMPC_VARIANT_JACOBI 0   /* upper layer: Jacobi, eq. 15 (all stages from
+                                   iterate k)                                  */
+#define NMPC_VARIANT_REDBLACK 1 /* upper layer: block Gauss-Seidel (the form of
+                                   eq. 18, (D + L)^{-1} K) in the red-black stage
+                                   order: even 0-based stages from iterate k,
+                                   then odd stages with their neighbours'
+                                   updated x_{i-1}, lambda_{i+1}.  The KKT
+                                   matrix is block tridiagonal, so this order is
+                                   consistent and the factor is the Jacobi one
+                                   squared (Theorem 3); both halves are
+                                   stage-parallel launches                     */
+
 #define NMPC_INIT_COLD 0 /* S^0: x_i = x0, u_i = 0, lambda_i = 0              */
 #define NMPC_INIT_WARM 1 /* S^0 = the handle's current state (last solution or
                             a state set by nmpc_set_state); in NMPC_MIXED the
@@ -143,6 +155,12 @@ typedef struct {
                       u-iteration (u_local does not apply there).
                       0 = auto (every such instance), 1 = the same,
                       2 = never (cluster path)                              */
+  int variant;      /* NMPC_VARIANT_JACOBI (default) or NMPC_VARIANT_REDBLACK:
+                      two stage-parallel launches per iteration (half 0: even
+                      stages, half 1: odd stages); the convergence test still
+                      uses ||K(S^k)||_inf of whole iterates.  Requires
+                      alpha = 1 (BAD_ARG otherwise) and never runs the
+                      persistent launch                                     */
 } nmpc_opts;
 
 typedef struct {
@@ -157,7 +175,7 @@ typedef struct nmpc_handle nmpc_handle;
 /* Fill *o with defaults: tol 1e-6, max_iter 2000, n_lo 2, n_u_it 2, FP64,
    check_every 16, alpha 1, div_limit 1e8, threads auto, graph on, cluster
    auto, split_min 1e-7, u_local 0, cells auto, persistent 0, strips auto,
-   strip_rows auto. */
+   strip_rows auto, lines auto, variant Jacobi. */
 void nmpc_default_opts(nmpc_opts* o);
 
 /* Validate the descriptors, build the device instance table and allocate the
@@ -369,7 +387,8 @@ int nmpc_line_plan(const nmpc_handle* h, int64_t* out);
    line path: opts.strips and opts.lines must be 0 or 2 (1, forcing one of
    those paths, returns UNSUPPORTED); opts.strip_rows, opts.persistent and
    opts.use_graph are ignored (the iterations are launched from the host in
-   chunks of check_every).  Returns UNSUPPORTED (and prints the
+   chunks of check_every).  opts.variant must be NMPC_VARIANT_JACOBI
+   (UNSUPPORTED otherwise).  Returns UNSUPPORTED (and prints the
    needed size) when the instance's workspace exceeds the static array,
    otherwise as nmpc_solve.  Every call reuses the same array, and the call
    resets whatever must start from zero; calls whose GPU work overlaps (other

@@ -27,6 +27,9 @@ What is computed, in the paper's notation:
   D^_i = D_i - M_U D^_{i+1}^{-1} M_L; dense LU of the whole matrix (tiny).
 * Upper-layer Jacobi (Sec. 4.2, eq. 15): S <- S - alpha D^{-1} K, all stages
   at once from x_{i-1} and lambda_{i+1} of iterate k.
+* Jacobi-type variants (Sec. 4.2, eqs. 18-20): block Gauss-Seidel (D + L)^{-1}
+  in forward (FGS), backward (BGS) or red-black stage order, and the
+  symmetric sweep (SGS) of eq. 20, each with D^k, K^k of iterate k.
 * Lower layer (Sec. 4.3, eqs. 21-24, and the u-iteration of Sec. 5.2):
   reordered block [[0, F_x, F_u], [F_x^T, A_xx, A_xu], [F_u^T, A_ux, A_uu]];
   v3 by ``n_u_it`` steps A_uu v3+ = b3 + [F_u^T A_ux] P^{-1}([F_u; A_xu] v3
@@ -403,6 +406,126 @@ def solve_jacobi(p: Problem, S0=None, tol=1e-6, max_iter=10000, n_lo=2, n_u_it=2
                                    converged=bool(r_inf <= tol),
                                    diverged=not np.isfinite(r_inf), hist=hist)
         X, U, L, _ = jacobi_iteration(p, X, U, L, n_lo, n_u_it, alpha, exact_inner, u_tilde)
+
+
+# ---------------------------------------------------------------------------
+# Jacobi-type variants, Sec. 4.2 (eqs. 18-20)
+# ---------------------------------------------------------------------------
+def _stage_view(c: StageCoeffs, i: int) -> StageCoeffs:
+    """The coefficients of stage i alone (arrays keep a leading axis of 1)."""
+    v = object.__new__(StageCoeffs)
+    v.p = c.p
+    v.dphi = c.dphi[i:i + 1]
+    v.diag = c.diag[i:i + 1]
+    v.axx = c.axx[i:i + 1]
+    v.auu = c.auu
+    return v
+
+
+def stage_solver(p: Problem, X, U, Lam, n_lo=2, n_u_it=2, exact_inner=False):
+    """solve(i, b1, b2, b3) -> (dx, du, dlam): the approximate (D_i^k)^{-1}
+    of the lower layer (or, with ``exact_inner``, a dense solve of D_i^k)
+    applied to state rows b1, costate rows b2 and u rows b3 of stage i."""
+    if exact_inner:
+        D = dense_stage_blocks(p, X, U, Lam)
+        ng, nu = p.ng, p.nu
+
+        def solve(i, b1, b2, b3):
+            d = np.linalg.solve(D[i], np.concatenate([b1.ravel(), b3, b2.ravel()]))
+            return (d[:ng].reshape(p.shape), d[ng:ng + nu], d[ng + nu:].reshape(p.shape))
+        return solve
+    c = StageCoeffs(p, X, U, Lam)
+
+    def solve(i, b1, b2, b3):
+        v1, v2, v3 = lower_layer(_stage_view(c, i), b1[None], b2[None], b3[None], n_lo, n_u_it)
+        return v2[0], v3[0], v1[0]
+    return solve
+
+
+def gs_order(N: int, kind: str):
+    """Stage visiting order (0-based) of a block Gauss-Seidel sweep: forward
+    (FGS, eq. 18), backward (BGS) or red-black (even stages, then odd)."""
+    if kind == "forward":
+        return list(range(N))
+    if kind == "backward":
+        return list(range(N - 1, -1, -1))
+    if kind == "redblack":
+        return list(range(0, N, 2)) + list(range(1, N, 2))
+    raise ValueError(kind)
+
+
+def gauss_seidel_iteration(p: Problem, X, U, Lam, order, n_lo=2, n_u_it=2, alpha=1.0,
+                           exact_inner=False, u_tilde=None):
+    """S^{k+1} = S^k - alpha (D^k + L_o)^{-1} K^k: block Gauss-Seidel on the
+    KKT system of eq. 10 with the stages visited in ``order``; L_o holds the
+    coupling blocks to stages visited earlier.  Forward order is FGS (eq. 18,
+    L_o = L), backward order BGS (D^k + U).  Visiting stage i solves D_i^k
+    Delta s_i = K_i^k - (M_L Delta s_{i-1} if i-1 was visited) - (M_U
+    Delta s_{i+1} if i+1 was visited): M_L takes Delta x_{i-1} into the state
+    rows, M_U Delta lambda_{i+1} into the costate rows.  D^k and K^k are those
+    of iterate k throughout.  Returns (X, U, Lam) and the norms of K^k."""
+    K1, K2, K3 = kkt(p, X, U, Lam)
+    if u_tilde is not None:
+        K2 = K2 + p.gamma * (U - u_tilde)
+    norms = kkt_norms(*kkt(p, X, U, Lam))
+    solve = stage_solver(p, X, U, Lam, n_lo, n_u_it, exact_inner)
+    dX, dU, dL = np.zeros_like(X), np.zeros_like(U), np.zeros_like(Lam)
+    seen = np.zeros(p.N, dtype=bool)
+    for i in order:
+        b1, b2 = K1[i].copy(), K3[i].copy()
+        if i > 0 and seen[i - 1]:
+            b1 = b1 - dX[i - 1]
+        if i < p.N - 1 and seen[i + 1]:
+            b2 = b2 - dL[i + 1]
+        dX[i], dU[i], dL[i] = solve(i, b1, b2, K2[i])
+        seen[i] = True
+    return X - alpha * dX, U - alpha * dU, Lam - alpha * dL, norms
+
+
+def sgs_iteration(p: Problem, X, U, Lam, n_lo=2, n_u_it=2, alpha=1.0, exact_inner=False,
+                  u_tilde=None):
+    """Symmetric Gauss-Seidel, eq. 20: S^{k+1} = S^k - alpha (D^k + L)^{-1}
+    (K^k - U (D^k + U)^{-1} K^k): a backward sweep z = (D^k + U)^{-1} K^k,
+    then a forward sweep on K^k - U z, whose costate rows of stage i lose
+    z_lambda of stage i+1."""
+    K1, K2, K3 = kkt(p, X, U, Lam)
+    if u_tilde is not None:
+        K2 = K2 + p.gamma * (U - u_tilde)
+    norms = kkt_norms(*kkt(p, X, U, Lam))
+    solve = stage_solver(p, X, U, Lam, n_lo, n_u_it, exact_inner)
+    N = p.N
+    zL = np.zeros_like(Lam)
+    for i in range(N - 1, -1, -1):
+        b2 = K3[i] - zL[i + 1] if i < N - 1 else K3[i]
+        _, _, zL[i] = solve(i, K1[i], b2, K2[i])
+    dX, dU, dL = np.zeros_like(X), np.zeros_like(U), np.zeros_like(Lam)
+    for i in range(N):
+        b1 = K1[i] - dX[i - 1] if i > 0 else K1[i]
+        b2 = K3[i] - zL[i + 1] if i < N - 1 else K3[i]
+        dX[i], dU[i], dL[i] = solve(i, b1, b2, K2[i])
+    return X - alpha * dX, U - alpha * dU, Lam - alpha * dL, norms
+
+
+def variant_iteration(p: Problem, X, U, Lam, variant="jacobi", **kw):
+    """One iteration of an upper-layer variant: jacobi (eq. 15), fgs (eq. 18),
+    bgs, sgs (eq. 20) or redblack."""
+    if variant == "jacobi":
+        return jacobi_iteration(p, X, U, Lam, **kw)
+    if variant == "sgs":
+        return sgs_iteration(p, X, U, Lam, **kw)
+    kind = {"fgs": "forward", "bgs": "backward", "redblack": "redblack"}[variant]
+    return gauss_seidel_iteration(p, X, U, Lam, gs_order(p.N, kind), **kw)
+
+
+def solve_variant(p: Problem, variant="jacobi", S0=None, tol=1e-6, max_iter=10000, **kw):
+    """Iterate a variant until ||K^k||_inf <= tol (as solve_jacobi)."""
+    X, U, L = p.cold_start() if S0 is None else (a.copy() for a in S0)
+    for k in range(max_iter + 1):
+        r_inf, r_2 = kkt_norms(*kkt(p, X, U, L))
+        if (not np.isfinite(r_inf)) or r_inf <= tol or k == max_iter:
+            return (X, U, L), dict(iters=k, res_inf=r_inf, res_2=r_2,
+                                   converged=bool(r_inf <= tol), diverged=not np.isfinite(r_inf))
+        X, U, L, _ = variant_iteration(p, X, U, L, variant, **kw)
 
 
 # ---------------------------------------------------------------------------

@@ -85,6 +85,8 @@ struct nmpc_handle {
   int box_r = 0;
   size_t box_bytes = 0;
   bool mixed = false;
+  bool rb = false;  // red-black upper layer (two half-sweep launches per iteration)
+  size_t strip_smem_rb = 0;  // k_strip's shared memory in red-black half 1
   // graph of one chunk of iterations
   cudaGraphExec_t graph_exec = nullptr;
   int graph_chunk = 0;
@@ -209,6 +211,7 @@ IterArgs make_args(nmpc_handle* h) {
   A.max_iter = h->opts.max_iter;
   A.n_lo = h->opts.n_lo;
   A.n_u_it = h->opts.n_u_it;
+  A.rb = h->rb ? 1 : 0;
   A.resid_only = 0;
   A.full_from = h->full_from;
   A.full0 = h->full0;
@@ -444,7 +447,8 @@ LaunchPlan plan_launch(const InstDev* insts, int n_inst, int n_work, const nmpc_
   // one cluster per work item for the whole solve, if all fit at once
   P.resident_clusters =
       P.smem_mode ? clusters_resident(C, P.threads, P.cpt, P.smem, mixed, true) : 0;
-  P.persistent = o.persistent && P.smem_mode && P.stage && P.resident_clusters >= n_work;
+  P.persistent = o.persistent && o.variant == 0 && P.smem_mode && P.stage &&
+                 P.resident_clusters >= n_work;
   return P;
 }
 
@@ -520,14 +524,25 @@ LaunchPlan plan_of(const nmpc_handle* h) {
 using TileKernel = void (*)(IterArgs, int, int);
 
 template <typename T>
-TileKernel strip_kernel(int n_lo) {
+TileKernel strip_kernel(int n_lo, bool rbn = false) {
+  if (rbn) {
+    switch (n_lo) {
+      case 1: return nmpc_dev::k_strip<T, 1, true>;
+      case 2: return nmpc_dev::k_strip<T, 2, true>;
+      case 3: return nmpc_dev::k_strip<T, 3, true>;
+      default: return nmpc_dev::k_strip<T, 4, true>;
+    }
+  }
   switch (n_lo) {
-    case 1: return nmpc_dev::k_strip<T, 1>;
-    case 2: return nmpc_dev::k_strip<T, 2>;
-    case 3: return nmpc_dev::k_strip<T, 3>;
-    default: return nmpc_dev::k_strip<T, 4>;
+    case 1: return nmpc_dev::k_strip<T, 1, false>;
+    case 2: return nmpc_dev::k_strip<T, 2, false>;
+    case 3: return nmpc_dev::k_strip<T, 3, false>;
+    default: return nmpc_dev::k_strip<T, 4, false>;
   }
 }
+
+// Whether launch j of an iteration is red-black half 1.
+inline bool rb_half1(const IterArgs& A, int j) { return A.rb && (j & 1); }
 
 template <typename T>
 TileKernel patch_kernel(int n_lo) {
@@ -562,14 +577,14 @@ cudaError_t launch_strip(const nmpc_handle* h, const IterArgs& A, cudaStream_t s
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)((h->n_strips + nmpc_dev::STRIP_WARPS - 1) / nmpc_dev::STRIP_WARPS));
   cfg.blockDim = dim3((unsigned)h->strip_threads);
-  cfg.dynamicSmemBytes = h->strip_smem;
+  cfg.dynamicSmemBytes = rb_half1(A, j) ? h->strip_smem_rb : h->strip_smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = (mode == nmpc_dev::MODE_SOLVE) ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, strip_kernel<T>(h->opts.n_lo), A, mode, j);
+  return cudaLaunchKernelEx(&cfg, strip_kernel<T>(h->opts.n_lo, rb_half1(A, j)), A, mode, j);
 }
 
 cudaError_t launch_line(const nmpc_handle* h, const IterArgs& A, cudaStream_t st, int mode, int j) {
@@ -583,7 +598,8 @@ cudaError_t launch_line(const nmpc_handle* h, const IterArgs& A, cudaStream_t st
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = (mode == nmpc_dev::MODE_SOLVE) ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, nmpc_dev::k_line, A, mode, j);
+  return cudaLaunchKernelEx(&cfg, rb_half1(A, j) ? nmpc_dev::k_line<true> : nmpc_dev::k_line<false>,
+                            A, mode, j);
 }
 
 // Kernel kinds of nmpc_kernel_times.
@@ -643,7 +659,7 @@ cudaError_t timed(nmpc_handle* h, int kind, cudaStream_t st, F launch) {
 // over the 1D stages, whichever exist.
 template <int MODE>
 cudaError_t launch_iterate(nmpc_handle* h, const IterArgs& A, cudaStream_t st, int j = 0) {
-  h->iter_launches++;
+  if (!rb_half1(A, j)) h->iter_launches++;  // one iteration step per Jacobi launch or half pair
   cudaError_t e = cudaSuccess;
   if (h->n_work > 0) {
     h->launches++;
@@ -685,7 +701,9 @@ cudaError_t enqueue_chunk(nmpc_handle* h, const IterArgs& A, cudaStream_t st, in
     nmpc_dev::k_compact_lines<<<1, nmpc_dev::COMPACT_THREADS, 0, st>>>(A);
     h->launches++;
   }
-  for (int i = 0; i < chunk; ++i) {
+  // red-black: launches j = 2 i (half 0) and 2 i + 1 (half 1) of iteration i
+  const int per = A.rb ? 2 : 1;
+  for (int i = 0; i < chunk * per; ++i) {
     cudaError_t e = launch_iterate<nmpc_dev::MODE_SOLVE>(h, A, st, i);
     if (e != cudaSuccess) return e;
   }
@@ -717,11 +735,17 @@ cudaError_t configure_kernels(size_t smem) {
     cudaError_t e = cudaFuncSetAttribute(strip_kernel<T>(n_lo),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(strip_kernel<T>(n_lo, true),
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(patch_kernel<T>(n_lo), cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
   }
-  return cudaFuncSetAttribute(nmpc_dev::k_line, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(nmpc_dev::k_line<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(nmpc_dev::k_line<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem);
 }
 
@@ -778,7 +802,8 @@ bool opts_ok(const nmpc_opts& o) {
          o.threads <= 512 && (o.threads % 32) == 0 && o.cluster >= 0 && o.cluster <= 16 &&
          (o.cluster <= 8 || o.cluster == 16) && (o.split_min >= 0) &&
          (o.cells >= 0 && o.cells <= 8) && (o.strips >= 0 && o.strips <= 2) && (o.lines >= 0 && o.lines <= 2) &&
-         (o.strip_rows >= 0 && o.strip_rows <= 65535);
+         (o.strip_rows >= 0 && o.strip_rows <= 65535) &&
+         (o.variant == NMPC_VARIANT_JACOBI || (o.variant == NMPC_VARIANT_REDBLACK && o.alpha == 1.0));
 }
 
 int validate(const nmpc_desc* d) {
@@ -796,6 +821,15 @@ int validate(const nmpc_desc* d) {
   if (!(d->k0 > 0) || !std::isfinite(d->k1) || !std::isfinite(d->act_gain))
     return NMPC_ERR_BAD_ARG;
   return NMPC_OK;
+}
+
+// Kernel launches of one chunk of `chunk` iterations (enqueue_chunk): the
+// line-list compaction, every path's iteration kernels (twice per iteration
+// for red-black), the counter advance.
+long long chunk_launches(const nmpc_handle* h, int chunk) {
+  const long long per_iter = (h->n_work > 0 ? 1 : 0) + (h->n_strips > 0 ? 2 : 0) +
+                             (h->n_lines > 0 ? 1 : 0);
+  return (h->n_lines > 0 ? 1 : 0) + (long long)chunk * per_iter * (h->rb ? 2 : 1) + 1;
 }
 
 int run_chunk(nmpc_handle* h, const IterArgs& A, cudaStream_t st, int chunk) {
@@ -825,7 +859,7 @@ int run_chunk(nmpc_handle* h, const IterArgs& A, cudaStream_t st, int chunk) {
       h->graph_chunk = chunk;
     }
     CK(cudaGraphLaunch(h->graph_exec, st));
-    h->launches += chunk + 1;
+    h->launches += chunk_launches(h, chunk);
     h->iter_launches += chunk;
   } else {
     CK(enqueue_chunk(h, A, st, chunk));
@@ -1012,7 +1046,7 @@ int solve_core(nmpc_handle* h, int horizon, const double* weights, int init, dou
   if (loop_graph) {
     // launch accounting: the loop ran iter_k / chunk chunks
     const long long runs = (h->h_active[0] + chunk - 1) / chunk;
-    h->launches += 1 + runs * (chunk + 2);
+    h->launches += 1 + runs * (chunk_launches(h, chunk) + 1);  // + the condition kernels
     h->iter_launches += runs * chunk;
   }
   int rc = NMPC_OK;
@@ -1221,7 +1255,7 @@ int closed_loop_graph(nmpc_handle* h, double* w, int steps, int n_sub, double* u
     int kmax = 0;
     for (int b = 0; b < n; ++b) kmax = std::max(kmax, ith[(size_t)t * n + b] + 2);
     const long long runs = (kmax + chunk - 1) / chunk;
-    h->launches += 8 + n_sub + runs * (chunk + 2);
+    h->launches += 8 + n_sub + runs * (chunk_launches(h, chunk) + 1);
     if (start) h->launches += 1 + 2 * (long long)h->n_max_horizon;  // guess copy, rollout
     h->iter_launches += runs * chunk;
   }
@@ -1250,6 +1284,7 @@ void nmpc_default_opts(nmpc_opts* o) {
   o->u_local = 0;
   o->cells = 0;
   o->persistent = 0;
+  o->variant = NMPC_VARIANT_JACOBI;
   o->strips = 0;
   o->strip_rows = 0;
   o->lines = 0;
@@ -1275,6 +1310,7 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
   h->n_inst = n_instances;
   h->opts = o;
   h->mixed = (o.precision == NMPC_MIXED);
+  h->rb = (o.variant == NMPC_VARIANT_REDBLACK);
   cudaGetDevice(&h->device);
   cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
 
@@ -1402,10 +1438,18 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
         : o.n_lo == 3 ? sizeof(nmpc_dev::StripShared<nmpc_dev::strip_ring_rows(3)>)
                       : sizeof(nmpc_dev::StripShared<nmpc_dev::strip_ring_rows(4)>);
     h->strip_smem = nmpc_dev::STRIP_WARPS * ((ws_bytes + 15) & ~size_t(15));
+    constexpr int NF1 = nmpc_dev::strip_fields(true);  // red-black half 1's ring
+    const size_t ws_rb =
+        o.n_lo <= 1   ? sizeof(nmpc_dev::StripShared<nmpc_dev::strip_ring_rows(1), NF1>)
+        : o.n_lo == 2 ? sizeof(nmpc_dev::StripShared<nmpc_dev::strip_ring_rows(2), NF1>)
+        : o.n_lo == 3 ? sizeof(nmpc_dev::StripShared<nmpc_dev::strip_ring_rows(3), NF1>)
+                      : sizeof(nmpc_dev::StripShared<nmpc_dev::strip_ring_rows(4), NF1>);
+    h->strip_smem_rb = nmpc_dev::STRIP_WARPS * ((ws_rb + 15) & ~size_t(15));
     const size_t P2 = (size_t)(2 * E + 1) * (2 * E + 1);
     h->patch_smem = PATCH_WARPS * (((sizeof(nmpc_dev::PatchShared) + 15) & ~size_t(15)) +
                                    8 * P2 * sizeof(double));
-    if (h->strip_smem > (size_t)max_optin || h->patch_smem > (size_t)max_optin) {
+    if (h->strip_smem > (size_t)max_optin || h->patch_smem > (size_t)max_optin ||
+        (h->rb && h->strip_smem_rb > (size_t)max_optin)) {
       fprintf(stderr, "nmpc: strip shape needs %zu bytes of shared memory\n", h->strip_smem);
       delete h;
       return NMPC_ERR_UNSUPPORTED;
@@ -1551,7 +1595,10 @@ static int oneshot(nmpc_handle* h, const double* xi, const double* ui, const dou
     CK(cudaMemsetAsync(h->res_inf, 0, h->n_inst * sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(h->res_sq, 0, h->n_inst * sizeof(double), st));
   }
-  CK(launch_iterate<nmpc_dev::MODE_ONESHOT>(h, A, st));
+  // residual-only passes evaluate every stage at once
+  if (resid_only) A.rb = 0;
+  CK(launch_iterate<nmpc_dev::MODE_ONESHOT>(h, A, st, 0));
+  if (A.rb) CK(launch_iterate<nmpc_dev::MODE_ONESHOT>(h, A, st, 1));
   if (out_res) {
     CK(cudaMemcpyAsync(h->h_resinf, h->res_inf, h->n_inst * sizeof(unsigned long long),
                        cudaMemcpyDeviceToHost, st));
@@ -1929,7 +1976,8 @@ extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
   if (!opts_ok(o)) return NMPC_ERR_BAD_ARG;
   // this entry point runs the cluster (or global-slab) path only: a forced
   // strip or line path cannot be honoured
-  if (o.strips == 1 || o.lines == 1) return NMPC_ERR_UNSUPPORTED;
+  if (o.strips == 1 || o.lines == 1 || o.variant != NMPC_VARIANT_JACOBI)
+    return NMPC_ERR_UNSUPPORTED;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return NMPC_ERR_NO_DEVICE;
   // per-device set-up first (the workspace address and the kernels'

@@ -106,6 +106,12 @@ struct IterArgs {
   double tol, div_limit, alpha;
   double split_min;  // below max(tol, split_min) iterations use the float64 residual
   int max_iter, n_lo, n_u_it;
+  // upper-layer variant: 0 Jacobi (eq. 15, every stage from iterate k);
+  // 1 red-black Gauss-Seidel (the stage-block form of eq. 18 in the order
+  // even stages, then odd stages): an iteration is two launches, half 0
+  // updating the even 0-based stages from iterate k, half 1 the odd ones
+  // with x_{i-1}, lambda_{i+1} already updated (launch index j = 2 i + half)
+  int rb;
   int resid_only;  // one-shot: residual norms only (float64)
   int full_all;    // every residual in float64 (FP64 precision)
   int csize;       // CTAs per work item (cluster size)
@@ -520,6 +526,14 @@ __device__ __forceinline__ void cp_async8_zfill(void* dst_smem, const void* src,
                "r"(valid ? 8 : 0));
 }
 
+// Iteration index (relative to *iter_k) and half-sweep of launch j.
+__device__ __forceinline__ int launch_iter(const IterArgs& A, int j) { return A.rb ? (j >> 1) : j; }
+__device__ __forceinline__ int launch_half(const IterArgs& A, int j) { return A.rb ? (j & 1) : 0; }
+// Whether stage s is updated by half-sweep `half` (every stage under Jacobi).
+__device__ __forceinline__ bool stage_in_half(const IterArgs& A, int s, int half) {
+  return !A.rb || ((s & 1) == half);
+}
+
 // Iteration k's decision for instance b, from its residual history
 // (iteration k - 1), with no side effects: skip (finished before, or k past
 // max_iter: `before`; or finished now: st != ST_RUNNING) and whether the
@@ -650,7 +664,8 @@ __device__ __forceinline__ void publish_residual(const IterArgs& A, int slot, in
 template <typename T, int NC, bool SMEM>
 __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, bool full,
                              bool resid_only, SmallShared<T>& sm, char* B, int wk_off, int st_off,
-                             bool staged, const Cl& cl, bool resident = false, bool keep = false) {
+                             bool staged, const Cl& cl, bool resident = false, bool keep = false,
+                             bool rbn = false) {
   constexpr int TS = (int)sizeof(T);
   constexpr int RB = NUM_FIELDS * TS;  // bytes per work record
   constexpr int SB = NUM_SFIELDS * 8;  // bytes per staged record
@@ -819,6 +834,16 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
     return staged ? SV(spos(sl.p), S_LN) : (sl.v ? L[so + ng + g.lo + sl.q] : 0.0);
   };
   auto ORF = [&](const Slot& sl) { return staged ? SV(spos(sl.p), S_RF) : (sl.v ? ref[g.lo + sl.q] : 0.0); };
+  // red-black half 1 (rbn): x_{i-1} and lambda_{i+1} as updated by half 0 of
+  // this iteration (the buffer being written); K_i with them is the
+  // right-hand side of the Gauss-Seidel stage solve, K_i with the values of
+  // iterate k (above) gives the norms of K(S^k)
+  const double* __restrict__ XNw = A.xout[rd ^ 1];
+  const double* __restrict__ LNw = A.lout[rd ^ 1];
+  auto OXPN = [&](const Slot& sl) {
+    return sl.v ? ((s == 0) ? x0[g.lo + sl.q] : XNw[so - ng + g.lo + sl.q]) : 0.0;
+  };
+  auto OLNN = [&](const Slot& sl) { return sl.v ? LNw[so + ng + g.lo + sl.q] : 0.0; };
 
   // ---- P1: residual inputs on the padded slab, halo rows included ----
   const float k0f = I.fk0, k1h = I.fk1h;
@@ -936,14 +961,23 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
                  dcoef * lam;
           }
           const double dphi = k0 * (1.0 + k1 * x);
-          const double K1 = xp - x + h * (lphi + srcd);
-          const double K3 = ln - lam + h * (I.q * (x - rc_) + dphi * mu);
+          // explicit fused multiply-adds: the same rounding in every
+          // instantiation (with and without the red-black branch)
+          const double s1 = lphi + srcd;
+          const double s3 = I.q * (x - rc_) + dphi * mu;
+          const double K1 = __fma_rn(h, s1, xp - x);
+          const double K3 = __fma_rn(h, s3, ln - lam);
           if (valid) {
             vmax = fmax(vmax, fmax(abs_or_inf(K1), abs_or_inf(K3)));
             vsq += K1 * K1 + K3 * K3;
           }
-          o.K1 = to_T<T>(K1);
-          o.K3 = to_T<T>(K3);
+          double K1r = K1, K3r = K3;
+          if (rbn) {
+            K1r = __fma_rn(h, s1, OXPN(sl) - x);
+            if (!last) K3r = __fma_rn(h, s3, OLNN(sl) - lam);
+          }
+          o.K1 = to_T<T>(K1r);
+          o.K3 = to_T<T>(K3r);
           o.dp = to_T<T>(dphi);
           o.ax = to_T<T>(h * (I.q + k0 * k1 * mu) + (last ? I.hqf : 0.0));
           return o;
@@ -973,22 +1007,28 @@ __device__ void process_item(const IterArgs& A, int b, int s, int k, int rd, boo
               if (sm.act[a] == c) srcf += d2f(sm.u[a]);
           }
           const float dphi = k0f_ * (1.0f + k1f_ * xv);
-          const float t1 = hf * (lphi + b0f * srcf);
-          const float t3 = hf * (qf_ * (xv - rv) + dphi * mu);
+          const float s1 = lphi + b0f * srcf;
+          const float s3 = qf_ * (xv - rv) + dphi * mu;
           // the O(1) differences in float64; at the last stage lambda_{N+1} is
-          // h qf (x_N - ref), an O(h) term
+          // h qf (x_N - ref), an O(h) term (explicit fused multiply-adds, as
+          // in the float64 form)
           const double d3 = last ? -lam : OLN(sl) - lam;
           const float dx = d2f(xp - x), dl = d2f(d3);
-          const float K1 = dx + t1;
-          const float K3 = dl + t3 + (last ? hqff * (xv - rv) : 0.0f);
+          const float K1 = __fmaf_rn(hf, s1, dx);
+          const float K3 = __fmaf_rn(hf, s3, dl) + (last ? hqff * (xv - rv) : 0.0f);
           // slots past the slab contribute nothing (selects, no branch)
           const float K1v = valid ? K1 : 0.0f, K3v = valid ? K3 : 0.0f;
           mg.z = fmaxf(mg.z, valid ? fmaxf(fabsf(dx), fabsf(dl)) : 0.0f);
           mg.w = fmaxf(mg.w, valid ? fabsf(rv) : 0.0f);
           fmax_ = fmax_nan(fmax_, fmax_nan(fabsf(K1v), fabsf(K3v)));
           fsq += K1v * K1v + K3v * K3v;
-          o.K1 = (T)K1;
-          o.K3 = (T)K3;
+          float K1r = K1, K3r = K3;
+          if (rbn) {
+            K1r = __fmaf_rn(hf, s1, d2f(OXPN(sl) - x));
+            if (!last) K3r = __fmaf_rn(hf, s3, d2f(OLNN(sl) - lam));
+          }
+          o.K1 = (T)K1r;
+          o.K3 = (T)K3r;
           o.dp = (T)dphi;
           o.ax = (T)(hf * (qf_ + k01f * mu) + hqff);
           return o;
@@ -1348,13 +1388,15 @@ __global__ void __launch_bounds__(512) k_iterate(IterArgs A, int MODE, int j) {
   pdl_trigger();
   // *iter_k only changes between chunks of launches (k_advance), never while
   // an iteration launch of the chunk is in flight
-  const int k = (MODE == MODE_SOLVE) ? *(volatile int*)A.iter_k + j : 0;
+  const int k = (MODE == MODE_SOLVE) ? *(volatile int*)A.iter_k + launch_iter(A, j) : 0;
+  const int half = launch_half(A, j);
   const int n_clusters = gridDim.x / A.csize;
   pdl_wait();  // the previous iteration's state, residuals and control words
 
   for (int w = blockIdx.x / A.csize; w < A.n_work; w += n_clusters) {
     const int2 item = A.work[w];
     const int b = item.x, s = item.y;
+    if (!stage_in_half(A, s, half)) continue;  // uniform across the cluster
     bool resid_only = false;
     bool full = true;
     if (MODE == MODE_ONESHOT) {
@@ -1370,7 +1412,7 @@ __global__ void __launch_bounds__(512) k_iterate(IterArgs A, int MODE, int j) {
       resid_only = (k == A.max_iter);
     }
     process_item<T, NC, SMEM>(A, b, s, k, (MODE == MODE_SOLVE) ? (k & 1) : 0, full, resid_only, sm,
-                              B, wk_off, st_off, staged, cl);
+                              B, wk_off, st_off, staged, cl, false, false, A.rb && half == 1);
   }
 
 }

@@ -64,7 +64,10 @@ __device__ __forceinline__ V line_at(const V (&v)[CPL], int c) {
 }
 
 // The stage of work item (b, s) for one residual form (FULL: float64).
-template <int CPL, bool FULL>
+// RBN: red-black half 1 (the right-hand side takes x_{i-1}, lambda_{i+1} as
+// updated by half 0, read from the buffer being written; the norms stay
+// those of K(S^k)).
+template <int CPL, bool FULL, bool RBN>
 __device__ __forceinline__ void line_body(const IterArgs& A, LineShared& ws, int lane, int b,
                                           int s, int k, int rd, bool resid_only) {
   using T = float;
@@ -79,6 +82,8 @@ __device__ __forceinline__ void line_body(const IterArgs& A, LineShared& ws, int
   const double* XPg = (s == 0) ? A.x0 + I.g_off : A.xin[rd] + so - I.ng;
   const double* LNg = last ? Lg : A.lin[rd] + so + I.ng;
   const double* RFg = A.ref + I.g_off;
+  const double* XPNg = (s == 0) ? A.x0 + I.g_off : A.xout[rd ^ 1] + so - I.ng;
+  const double* LNNg = A.lout[rd ^ 1] + so + I.ng;
   // coalesced copies: lane l copies cells t 32 + l (zeros past M)
 #pragma unroll
   for (int t = 0; t < CPL; ++t) {
@@ -105,6 +110,16 @@ __device__ __forceinline__ void line_body(const IterArgs& A, LineShared& ws, int
 
   // blocked registers: lane l's cells l CPL + t
   const int q0 = lane * CPL;
+  // red-black half 1: the lane's cells of the updated x_{i-1}, lambda_{i+1}
+  double xpn[RBN ? CPL : 1], lnn[RBN ? CPL : 1];
+  if constexpr (RBN) {
+#pragma unroll
+    for (int t = 0; t < CPL; ++t) {
+      const bool ok = q0 + t < M;
+      xpn[t] = ok ? XPNg[q0 + t] : 0.0;
+      lnn[t] = (ok && !last) ? LNNg[q0 + t] : 0.0;
+    }
+  }
   const int pb0 = lpad<CPL>(q0);  // positions pb0 + t (one lane's cells are contiguous)
   const T th = I.fh, tdc = I.fdc, tcx = I.fcx, tb0 = I.fb0;
   T K1[CPL], K3[CPL], dp[CPL], ax[CPL], rg[CPL];
@@ -134,14 +149,21 @@ __device__ __forceinline__ void line_body(const IterArgs& A, LineShared& ws, int
       double srcd = 0.0;  // controls on this cell
       for (int a = 0; a < nu; ++a)
         if (ws.act[a] == q0 + t) srcd += ws.u[a];
-      const double K1d = xp - x + I.h * (lphi[t] + srcd * I.b0);
-      const double K3d = ln - lam + I.h * (I.q * (x - rc) + dphi * mu);
+      const double t1 = I.h * (lphi[t] + srcd * I.b0);
+      const double t3 = I.h * (I.q * (x - rc) + dphi * mu);
+      const double K1d = xp - x + t1;
+      const double K3d = ln - lam + t3;
       if (valid) {
         vmax = fmax(vmax, fmax(abs_or_inf(K1d), abs_or_inf(K3d)));
         vsq += K1d * K1d + K3d * K3d;
       }
-      K1[t] = to_T<T>(K1d);
-      K3[t] = to_T<T>(K3d);
+      if constexpr (RBN) {
+        K1[t] = to_T<T>(xpn[t] - x + t1);
+        K3[t] = to_T<T>(last ? K3d : lnn[t] - lam + t3);
+      } else {
+        K1[t] = to_T<T>(K1d);
+        K3[t] = to_T<T>(K3d);
+      }
       dp[t] = to_T<T>(dphi);
       ax[t] = to_T<T>(I.h * (I.q + I.k0 * I.k1 * mu) + (last ? I.hqf : 0.0));
       rg[t] = valid ? rcp_T(-T(1) - th * tdc * dp[t]) : T(0);
@@ -211,8 +233,13 @@ __device__ __forceinline__ void line_body(const IterArgs& A, LineShared& ws, int
       mg.w = fmaxf(mg.w, valid ? fabsf(rv) : 0.0f);
       fm = fmax_nan(fm, fmax_nan(fabsf(K1v), fabsf(K3v)));
       fs += K1v * K1v + K3v * K3v;
-      K1[t] = K1f;
-      K3[t] = K3f;
+      if constexpr (RBN) {
+        K1[t] = d2f(xpn[t] - x) + t1;
+        K3[t] = last ? K3f : d2f(lnn[t] - lam) + t3;
+      } else {
+        K1[t] = K1f;
+        K3[t] = K3f;
+      }
       dp[t] = dphi;
       ax[t] = I.fh * (I.fq + I.fk01 * mu) + hqff;
       rg[t] = valid ? rcp_T(-T(1) - th * tdc * dp[t]) : T(0);
@@ -347,13 +374,15 @@ __device__ __forceinline__ void line_body(const IterArgs& A, LineShared& ws, int
 // list and followed by empty items; MODE_ONESHOT: one residual or iteration
 // from the given buffers, over every item).  Item (b, s, CPL); one item per
 // warp, warps on an empty item return at once.
+template <bool RBN>
 __global__ void __launch_bounds__(LINE_WARPS * 32, 4) k_line(IterArgs A, int MODE, int j_launch) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   LineShared& ws = *reinterpret_cast<LineShared*>(
       smem_raw + warp * ((sizeof(LineShared) + 15) & ~size_t(15)));
   pdl_trigger();
-  const int k = (MODE == MODE_SOLVE) ? *(volatile int*)A.iter_k + j_launch : 0;
+  const int k = (MODE == MODE_SOLVE) ? *(volatile int*)A.iter_k + launch_iter(A, j_launch) : 0;
+  const int half = launch_half(A, j_launch);
   const int rd = (MODE == MODE_SOLVE) ? (k & 1) : 0;
   pdl_wait();  // the previous iteration's state, residuals and control words
   const int item = blockIdx.x * LINE_WARPS + warp;
@@ -362,6 +391,7 @@ __global__ void __launch_bounds__(LINE_WARPS * 32, 4) k_line(IterArgs A, int MOD
   const int4 it = list[item];
   if (it.x < 0) return;  // past the running items (solve mode)
   const int b = it.x, s = it.y, cpl = it.z;
+  if (!stage_in_half(A, s, half)) return;
 
   bool resid_only, full;
   if (MODE == MODE_ONESHOT) {
@@ -383,17 +413,17 @@ __global__ void __launch_bounds__(LINE_WARPS * 32, 4) k_line(IterArgs A, int MOD
   }
   if (full) {
     switch (cpl) {
-      case 1: line_body<1, true>(A, ws, lane, b, s, k, rd, resid_only); break;
-      case 2: line_body<2, true>(A, ws, lane, b, s, k, rd, resid_only); break;
-      case 4: line_body<4, true>(A, ws, lane, b, s, k, rd, resid_only); break;
-      default: line_body<8, true>(A, ws, lane, b, s, k, rd, resid_only); break;
+      case 1: line_body<1, true, RBN>(A, ws, lane, b, s, k, rd, resid_only); break;
+      case 2: line_body<2, true, RBN>(A, ws, lane, b, s, k, rd, resid_only); break;
+      case 4: line_body<4, true, RBN>(A, ws, lane, b, s, k, rd, resid_only); break;
+      default: line_body<8, true, RBN>(A, ws, lane, b, s, k, rd, resid_only); break;
     }
   } else {
     switch (cpl) {
-      case 1: line_body<1, false>(A, ws, lane, b, s, k, rd, resid_only); break;
-      case 2: line_body<2, false>(A, ws, lane, b, s, k, rd, resid_only); break;
-      case 4: line_body<4, false>(A, ws, lane, b, s, k, rd, resid_only); break;
-      default: line_body<8, false>(A, ws, lane, b, s, k, rd, resid_only); break;
+      case 1: line_body<1, false, RBN>(A, ws, lane, b, s, k, rd, resid_only); break;
+      case 2: line_body<2, false, RBN>(A, ws, lane, b, s, k, rd, resid_only); break;
+      case 4: line_body<4, false, RBN>(A, ws, lane, b, s, k, rd, resid_only); break;
+      default: line_body<8, false, RBN>(A, ws, lane, b, s, k, rd, resid_only); break;
     }
   }
 }

@@ -344,13 +344,15 @@ __global__ void __launch_bounds__(128) k_patch(IterArgs A, int MODE, int j) {
   double* W1 = W0 + nP;
   double* W2 = W1 + nP;
   pdl_trigger();
-  const int k = (MODE == MODE_SOLVE) ? *(volatile int*)A.iter_k + j : 0;
+  const int k = (MODE == MODE_SOLVE) ? *(volatile int*)A.iter_k + launch_iter(A, j) : 0;
+  const int half = launch_half(A, j);
   const int rd = (MODE == MODE_SOLVE) ? (k & 1) : 0;
   pdl_wait();
   const int item = blockIdx.x * WPB + warp;
   if (item >= A.n_patches) return;  // warp-uniform; no block barriers follow
   const int4 it = A.patches[item];
   const int b = it.x, s = it.y, a = it.z;
+  if (!stage_in_half(A, s, half)) return;
   bool full;
   if (MODE == MODE_SOLVE) {
     int skip = 0, fl = 1;
@@ -379,8 +381,12 @@ __global__ void __launch_bounds__(128) k_patch(IterArgs A, int MODE, int j) {
   const long long so = I.s_off + (long long)s * I.ng;
   const double* Xg = A.xin[rd] + so;
   const double* Lg = A.lin[rd] + so;
-  const double* XPg = (s == 0) ? A.x0 + I.g_off : A.xin[rd] + so - I.ng;
-  const double* LNg = A.lin[rd] + so + I.ng;
+  // v3 enters the right-hand side only: in red-black half 1 it is formed
+  // with x_{i-1}, lambda_{i+1} as updated by half 0 (the buffer being written)
+  const bool rbn = A.rb && half == 1;
+  const double* XPg = (s == 0) ? A.x0 + I.g_off
+                               : (rbn ? A.xout[rd ^ 1] : A.xin[rd]) + so - I.ng;
+  const double* LNg = (rbn ? A.lout[rd ^ 1] : A.lin[rd]) + so + I.ng;
   const double* RFg = A.ref + I.g_off;
   for (int r = lane; r < nP; r += 32) {
     const int rj = r / P, ri = r - rj * P;

@@ -41,11 +41,15 @@ __host__ __device__ constexpr int strip_ring_rows(int n_lo) {
   return 2 * n_lo - 1 + STRIP_AHEAD + 1;
 }
 
-// Shared memory of one strip warp: the input ring (RING rows x SREC fields x
-// 32 lanes, float64) and the actuators in reach sorted by row.
-template <int RING>
+// Shared memory of one strip warp: the input ring (RING rows x NF fields x
+// 32 lanes, float64) and the actuators in reach sorted by row.  NF = SREC,
+// or SREC + 2 for red-black half 1, whose ring also holds x_{i-1} and
+// lambda_{i+1} as updated by half 0 (fields R_XPN, R_LNN).
+enum { R_XPN = SREC, R_LNN = SREC + 1 };
+__host__ __device__ constexpr int strip_fields(bool rbn) { return rbn ? SREC + 2 : SREC; }
+template <int RING, int NF = SREC>
 struct StripShared {
-  double ring[RING * SREC * 32];
+  double ring[RING * NF * 32];
   StripAct act[MAX_NU];
   int n_act;
 };
@@ -83,14 +87,17 @@ struct Shift {
 
 // The strip of work item (b, s, x0, y0) for one residual form (FULL: the
 // float64 residual; else the split one): a separate instantiation per form,
-// so neither form's arithmetic is issued in the other's iterations.
-template <typename T, int n_lo, bool FULL>
+// so neither form's arithmetic is issued in the other's iterations.  RBN:
+// red-black half 1 (the right-hand side takes x_{i-1}, lambda_{i+1} as
+// updated by half 0; the norms stay those of K(S^k)).
+template <typename T, int n_lo, bool FULL, bool RBN>
 __device__ __forceinline__ void strip_body(const IterArgs& A,
-                                           StripShared<strip_ring_rows(n_lo)>& ws, int lane,
-                                           int b, int s, int k, int rd, int x0, int y0,
+                                           StripShared<strip_ring_rows(n_lo), strip_fields(RBN)>& ws,
+                                           int lane, int b, int s, int k, int rd, int x0, int y0,
                                            bool resid_only) {
   constexpr int E = 2 * n_lo - 1;
   constexpr int RING = strip_ring_rows(n_lo);
+  constexpr int NF = strip_fields(RBN);
   constexpr bool full = FULL;
   const InstDev& I = A.inst[b];
   const int nu = I.nu;
@@ -151,13 +158,15 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
   const double* XPg = (s == 0) ? A.x0 + I.g_off : A.xin[rd] + so - I.ng;
   const double* LNg = A.lin[rd] + so + I.ng;
   const double* RFg = A.ref + I.g_off;
+  const double* XPNg = (s == 0) ? A.x0 + I.g_off : A.xout[rd ^ 1] + so - I.ng;
+  const double* LNNg = A.lout[rd ^ 1] + so + I.ng;
   double* ring = ws.ring + lane;
   // ring row of j + d for the current step j (sj = j mod RING), -RING < d < RING
   int sj = 0;
   auto slot_at = [&](int d, int f) -> double* {
     int q = sj + d;
     q = q < 0 ? q + RING : (q >= RING ? q - RING : q);
-    return ring + (q * SREC + f) * 32;
+    return ring + (q * NF + f) * 32;
   };
   // row rj's five inputs; cells outside the grid and rows past the region
   // are zero-filled by the copies themselves (source size 0, from a clamped
@@ -175,6 +184,10 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
     cp_async8_zfill(d + R_XP * 32, XPg + c, ok);
     cp_async8_zfill(d + R_LN * 32, (last ? Lg : LNg) + c, ok && !last);
     cp_async8_zfill(d + R_RF * 32, RFg + c, ok);
+    if constexpr (RBN) {
+      cp_async8_zfill(d + R_XPN * 32, XPNg + c, ok);
+      cp_async8_zfill(d + R_LNN * 32, (last ? Lg : LNNg) + c, ok && !last);
+    }
     asm volatile("cp.async.commit_group;\n" ::);
   };
 #pragma unroll
@@ -261,14 +274,21 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
         const double lphi = phd.nsum(cxd, cyd) - dcd * phd.w1;
         const double mu = lad.nsum(cxd, cyd) - dcd * lad.w1;
         const double dphi = k0d * (1.0 + k1d * x);
-        const double K1d = xp - x + hd * (lphi + b0d * srcd);
-        const double K3d = ln - lam + hd * (qd * (x - rc) + dphi * mu);
+        const double t1 = hd * (lphi + b0d * srcd);
+        const double t3 = hd * (qd * (x - rc) + dphi * mu);
+        const double K1d = xp - x + t1;
+        const double K3d = ln - lam + t3;
         if (own) {
           nm.vmax = fmax(nm.vmax, fmax(abs_or_inf(K1d), abs_or_inf(K3d)));
           nm.vsq += K1d * K1d + K3d * K3d;
         }
-        K1 = to_T<T>(K1d);
-        K3 = to_T<T>(K3d);
+        if constexpr (RBN) {
+          K1 = to_T<T>(rs[R_XPN * 32] - x + t1);
+          K3 = to_T<T>(last ? K3d : rs[R_LNN * 32] - lam + t3);
+        } else {
+          K1 = to_T<T>(K1d);
+          K3 = to_T<T>(K3d);
+        }
         dp = to_T<T>(dphi);
         ax = to_T<T>(hd * (qd + k0d * k1d * mu) + (last ? hqfd : 0.0));
       } else {
@@ -302,8 +322,13 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
         nm.mg.w = fmaxf(nm.mg.w, own ? fabsf(rv) : 0.0f);
         nm.fmax = fmax_nan(nm.fmax, fmax_nan(fabsf(K1v), fabsf(K3v)));
         nm.fsq += K1v * K1v + K3v * K3v;
-        K1 = (T)K1f;
-        K3 = (T)K3f;
+        if constexpr (RBN) {
+          K1 = (T)((d2f(rs[R_XPN * 32]) - xv) + t1);
+          K3 = last ? (T)K3f : (T)((d2f(rs[R_LNN * 32]) - laf.w1) + t3);
+        } else {
+          K1 = (T)K1f;
+          K3 = (T)K3f;
+        }
         dp = (T)dphi;
         ax = (T)(fh * (fq + fk01 * mu) + hqff);
       }
@@ -444,20 +469,22 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
 // One upper-layer iteration over the strip work list (MODE_SOLVE: iteration
 // *iter_k + j with the convergence bookkeeping; MODE_ONESHOT: one residual or
 // iteration from the given buffers), after k_patch of the same iteration.
-template <typename T, int n_lo>
+template <typename T, int n_lo, bool RBN>
 __global__ void __launch_bounds__(STRIP_WARPS * 32, STRIP_MIN_BLOCKS) k_strip(IterArgs A, int MODE, int j_launch) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  using WS = StripShared<strip_ring_rows(n_lo)>;
+  using WS = StripShared<strip_ring_rows(n_lo), strip_fields(RBN)>;
   WS& ws = *reinterpret_cast<WS*>(smem_raw + warp * ((sizeof(WS) + 15) & ~size_t(15)));
   pdl_trigger();
-  const int k = (MODE == MODE_SOLVE) ? *(volatile int*)A.iter_k + j_launch : 0;
+  const int k = (MODE == MODE_SOLVE) ? *(volatile int*)A.iter_k + launch_iter(A, j_launch) : 0;
+  const int half = launch_half(A, j_launch);
   const int rd = (MODE == MODE_SOLVE) ? (k & 1) : 0;
   pdl_wait();  // the previous iteration's state, residuals and control words; this one's v3
   const int item = blockIdx.x * STRIP_WARPS + warp;
   if (item >= A.n_strips) return;  // warp-uniform; no block barriers in this kernel
   const int4 it = A.strips[item];
   const int b = it.x, s = it.y, x0 = it.z, y0 = it.w;
+  if (!stage_in_half(A, s, half)) return;
 
   bool resid_only, full;
   if (MODE == MODE_ONESHOT) {
@@ -478,7 +505,7 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32, STRIP_MIN_BLOCKS) k_strip(It
     resid_only = (k == A.max_iter);
   }
   if (full || std::is_same<T, double>::value)
-    strip_body<T, n_lo, true>(A, ws, lane, b, s, k, rd, x0, y0, resid_only);
+    strip_body<T, n_lo, true, RBN>(A, ws, lane, b, s, k, rd, x0, y0, resid_only);
   else
-    strip_body<T, n_lo, false>(A, ws, lane, b, s, k, rd, x0, y0, resid_only);
+    strip_body<T, n_lo, false, RBN>(A, ws, lane, b, s, k, rd, x0, y0, resid_only);
 }

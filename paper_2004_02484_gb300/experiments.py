@@ -214,6 +214,8 @@ def main():
     ap.add_argument("--rules", type=int, default=1)
     ap.add_argument("--tune", type=int, default=1)
     ap.add_argument("--lines", type=int, default=0)
+    ap.add_argument("--variant", type=int, default=0,
+                    help="upper layer: 0 Jacobi (eq. 15), 1 red-black Gauss-Seidel")
     a = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
@@ -226,7 +228,7 @@ def main():
                                  lines=a.lines)), flush=True)
     elif a.which == "solve":
         print(json.dumps(solve(a.n or 8, a.grid, a.horizon, a.reps, a.graph, strips=a.strips,
-                               strip_rows=a.strip_rows)), flush=True)
+                               strip_rows=a.strip_rows, variant=a.variant)), flush=True)
     elif a.which == "closedloop_learned":
         print(json.dumps(closedloop_learned(a.n_train, a.train_steps, a.n or 8, a.steps, a.grid,
                                             a.horizon, a.n_sub, a.fit_steps, a.rules)), flush=True)

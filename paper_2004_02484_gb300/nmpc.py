@@ -25,6 +25,8 @@ NMPC_ERR_NO_DEVICE = -5
 NMPC_ERR_UNSUPPORTED = -6
 NMPC_FP64 = 0
 NMPC_MIXED = 1
+NMPC_VARIANT_JACOBI = 0
+NMPC_VARIANT_REDBLACK = 1
 NMPC_INIT_COLD = 0
 NMPC_INIT_WARM = 1
 NMPC_INIT_GUESS = 2
@@ -52,7 +54,7 @@ class nmpc_opts(ctypes.Structure):
                 ("split_min", ctypes.c_double), ("u_local", ctypes.c_int),
                 ("cells", ctypes.c_int), ("persistent", ctypes.c_int),
                 ("strips", ctypes.c_int), ("strip_rows", ctypes.c_int),
-                ("lines", ctypes.c_int)]
+                ("lines", ctypes.c_int), ("variant", ctypes.c_int)]
 
 
 class nmpc_stats(ctypes.Structure):
