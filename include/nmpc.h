@@ -161,6 +161,13 @@ typedef struct {
                       uses ||K(S^k)||_inf of whole iterates.  Requires
                       alpha = 1 (BAD_ARG otherwise) and never runs the
                       persistent launch                                     */
+  int64_t barrier_wait_cycles; /* persistent launch: spin budget of one grid-
+                      barrier wait in SM clock cycles (0 = 4e9, about two
+                      seconds).  A wait that runs out ends the launch with an
+                      error word; the host then discards that launch's state
+                      and solves from S^0 with one launch per iteration (the
+                      handle keeps that mode).  A tiny budget exercises this
+                      path                                                  */
 } nmpc_opts;
 
 typedef struct {
@@ -175,7 +182,7 @@ typedef struct nmpc_handle nmpc_handle;
 /* Fill *o with defaults: tol 1e-6, max_iter 2000, n_lo 2, n_u_it 2, FP64,
    check_every 16, alpha 1, div_limit 1e8, threads auto, graph on, cluster
    auto, split_min 1e-7, u_local 0, cells auto, persistent 0, strips auto,
-   strip_rows auto, lines auto, variant Jacobi. */
+   strip_rows auto, lines auto, variant Jacobi, barrier_wait_cycles 0. */
 void nmpc_default_opts(nmpc_opts* o);
 
 /* Validate the descriptors, build the device instance table and allocate the

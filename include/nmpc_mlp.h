@@ -81,6 +81,10 @@ int nmpc_mlp_forward(nmpc_mlp* m, const float* x, int B, float* y, void* stream)
 int nmpc_mlp_backward(nmpc_mlp* m, const float* x, const float* target, int B,
                       float* loss_host, void* stream);
 int nmpc_mlp_get_grads(nmpc_mlp* m, float* host);
+/* Replace the handle's gradients by a host copy in the parameter packing (no
+   counterpart in the paper: for a loss computed elsewhere, and for testing
+   Adam on given gradients).  Synchronous. */
+int nmpc_mlp_set_grads(nmpc_mlp* m, const float* host);
 /* One Adam update with the current gradients, learning rate lr. */
 int nmpc_mlp_adam_step(nmpc_mlp* m, float lr, void* stream);
 /* backward + adam_step. */

@@ -255,6 +255,20 @@ int nmpc_mlp_get_grads(nmpc_mlp* m, float* host) {
   return copy_out(m, host, true);
 }
 
+int nmpc_mlp_set_grads(nmpc_mlp* m, const float* host) {
+  if (!m || !host) return NMPC_MLP_ERR_BAD_ARG;
+  MCK(cudaDeviceSynchronize());
+  size_t o = 0;
+  for (int l = 0; l < m->L; ++l) {
+    const size_t nin = m->w[l], nout = m->w[l + 1];
+    MCK(cudaMemcpy(m->gW[l], host + o, nin * nout * 4, cudaMemcpyHostToDevice));
+    o += nin * nout;
+    MCK(cudaMemcpy(m->gb[l], host + o, nout * 4, cudaMemcpyHostToDevice));
+    o += nout;
+  }
+  return NMPC_MLP_OK;
+}
+
 static int forward_impl(nmpc_mlp* m, const float* x, int B, float* y, cudaStream_t st) {
   const int n_in = m->w[0];
   mlp_dev::k_cast_bf16<<<grid_for((long long)B * n_in, 256), 256, 0, st>>>(x, m->a[0],

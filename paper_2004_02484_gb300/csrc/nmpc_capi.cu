@@ -212,6 +212,8 @@ IterArgs make_args(nmpc_handle* h) {
   A.n_lo = h->opts.n_lo;
   A.n_u_it = h->opts.n_u_it;
   A.rb = h->rb ? 1 : 0;
+  A.grid_wait = h->opts.barrier_wait_cycles > 0 ? (long long)h->opts.barrier_wait_cycles
+                                                : nmpc_dev::GRID_WAIT_CYCLES;
   A.resid_only = 0;
   A.full_from = h->full_from;
   A.full0 = h->full0;
@@ -803,7 +805,8 @@ bool opts_ok(const nmpc_opts& o) {
          (o.cluster <= 8 || o.cluster == 16) && (o.split_min >= 0) &&
          (o.cells >= 0 && o.cells <= 8) && (o.strips >= 0 && o.strips <= 2) && (o.lines >= 0 && o.lines <= 2) &&
          (o.strip_rows >= 0 && o.strip_rows <= 65535) &&
-         (o.variant == NMPC_VARIANT_JACOBI || (o.variant == NMPC_VARIANT_REDBLACK && o.alpha == 1.0));
+         (o.variant == NMPC_VARIANT_JACOBI || (o.variant == NMPC_VARIANT_REDBLACK && o.alpha == 1.0)) &&
+         o.barrier_wait_cycles >= 0;
 }
 
 int validate(const nmpc_desc* d) {
@@ -1285,6 +1288,7 @@ void nmpc_default_opts(nmpc_opts* o) {
   o->cells = 0;
   o->persistent = 0;
   o->variant = NMPC_VARIANT_JACOBI;
+  o->barrier_wait_cycles = 0;
   o->strips = 0;
   o->strip_rows = 0;
   o->lines = 0;

@@ -112,6 +112,7 @@ struct IterArgs {
   // updating the even 0-based stages from iterate k, half 1 the odd ones
   // with x_{i-1}, lambda_{i+1} already updated (launch index j = 2 i + half)
   int rb;
+  long long grid_wait;  // spin budget of one grid-barrier wait (SM clock cycles)
   int resid_only;  // one-shot: residual norms only (float64)
   int full_all;    // every residual in float64 (FP64 precision)
   int csize;       // CTAs per work item (cluster size)
@@ -1417,7 +1418,8 @@ __global__ void __launch_bounds__(512) k_iterate(IterArgs A, int MODE, int j) {
 
 }
 
-// Spin budget of one grid-barrier wait (SM clock cycles, about two seconds).
+// Default spin budget of one grid-barrier wait (SM clock cycles, about two
+// seconds); IterArgs.grid_wait holds the handle's budget.
 constexpr long long GRID_WAIT_CYCLES = 4000000000LL;
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
@@ -1430,7 +1432,7 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 // cluster's CTAs meet (after publishing their global writes), rank 0 arrives
 // on the counter, the last arrival decides whether to stop (no instance
 // running) and opens the next generation; the others wait for it, for at most
-// GRID_WAIT_CYCLES, and on timeout raise the error word.  Returns
+// A.grid_wait cycles, and on timeout raise the error word.  Returns
 // stop | error << 1 to every thread of the cluster.
 template <typename T>
 __device__ int grid_barrier(const IterArgs& A, int n_clusters, unsigned& gen, const Cl& cl,
@@ -1450,7 +1452,7 @@ __device__ int grid_barrier(const IterArgs& A, int n_clusters, unsigned& gen, co
       const long long t0 = clock64();
       while (ld_acquire_u32(&gs[1]) != target) {
         if (ld_acquire_u32(&gs[3]) != 0u) break;
-        if (clock64() - t0 > GRID_WAIT_CYCLES) {
+        if (clock64() - t0 > A.grid_wait) {
           atomicExch(&gs[3], 1u);
           break;
         }

@@ -20,7 +20,7 @@ EXPORTED = ["nmpc_gemm_bf16", "nmpc_cast_f32_bf16", "nmpc_cast_f32_f64", "nmpc_c
             "nmpc_transpose_bf16", "nmpc_pool_avg",
             "nmpc_mlp_create", "nmpc_mlp_num_params",
             "nmpc_mlp_set_params", "nmpc_mlp_get_params", "nmpc_mlp_forward",
-            "nmpc_mlp_backward", "nmpc_mlp_get_grads", "nmpc_mlp_adam_step",
+            "nmpc_mlp_backward", "nmpc_mlp_get_grads", "nmpc_mlp_set_grads", "nmpc_mlp_adam_step",
             "nmpc_mlp_train_step", "nmpc_mlp_launch_count", "nmpc_mlp_destroy"]
 
 _P, _I, _F = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
@@ -38,6 +38,7 @@ _SIG = {
     "nmpc_mlp_forward": (_I, [_P, _P, _I, _P, _P]),
     "nmpc_mlp_backward": (_I, [_P, _P, _P, _I, ctypes.POINTER(_F), _P]),
     "nmpc_mlp_get_grads": (_I, [_P, _P]),
+    "nmpc_mlp_set_grads": (_I, [_P, _P]),
     "nmpc_mlp_adam_step": (_I, [_P, _F, _P]),
     "nmpc_mlp_train_step": (_I, [_P, _P, _P, _I, _F, ctypes.POINTER(_F), _P]),
     "nmpc_mlp_launch_count": (ctypes.c_int64, [_P]),
@@ -142,6 +143,11 @@ class MLP:
         out = np.zeros(self.n_params, dtype=np.float32)
         _check(LIB.nmpc_mlp_get_grads(self.h, out.ctypes.data), "nmpc_mlp_get_grads")
         return out
+
+    def set_grads(self, g: np.ndarray):
+        g = np.ascontiguousarray(g, dtype=np.float32)
+        assert g.size == self.n_params
+        _check(LIB.nmpc_mlp_set_grads(self.h, g.ctypes.data), "nmpc_mlp_set_grads")
 
     def forward(self, x, y, stream=None):
         _check(LIB.nmpc_mlp_forward(self.h, _dptr(x, "f32"), x.shape[0], _dptr(y, "f32"),

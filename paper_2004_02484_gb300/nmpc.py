@@ -54,7 +54,8 @@ class nmpc_opts(ctypes.Structure):
                 ("split_min", ctypes.c_double), ("u_local", ctypes.c_int),
                 ("cells", ctypes.c_int), ("persistent", ctypes.c_int),
                 ("strips", ctypes.c_int), ("strip_rows", ctypes.c_int),
-                ("lines", ctypes.c_int), ("variant", ctypes.c_int)]
+                ("lines", ctypes.c_int), ("variant", ctypes.c_int),
+                ("barrier_wait_cycles", ctypes.c_int64)]
 
 
 class nmpc_stats(ctypes.Structure):

@@ -392,3 +392,35 @@ def test_persistent_solve_is_bit_identical_to_per_iteration_launches(G, precisio
     assert a[1] == b[1]
     for i in (2, 3, 4):
         assert np.array_equal(a[i], b[i])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_grid_barrier_timeout_falls_back_to_per_iteration_launches(G, precision):
+    """A persistent launch whose grid-barrier waits may spin for only 100 SM
+    cycles: the first cluster that has to wait gives up, raises the error word
+    and every cluster leaves the launch (bounded waits: no hang, no fault);
+    the host discards that launch's state and solves from S^0 with one launch
+    per iteration, so the result is the one of a handle that never tried the
+    persistent launch, and the handle stays in per-iteration mode."""
+    import torch
+    insts, kw = [wl.heat1d(40, 9, 3, 0.02, seed=11)], dict(cluster=3)
+    out = []
+    for persistent, wait in ((1, 100), (0, 0)):
+        s = G.Solver(insts, tol=1e-6, precision=precision, max_iter=4000, persistent=persistent,
+                     barrier_wait_cycles=wait, **kw)
+        assert G.nmpc_launch_plan(s.h)["persistent"] == persistent
+        rc, st = s.solve()
+        x, u, lam = s.state()
+        torch.cuda.synchronize()
+        out.append((rc, st[0].iters, st[0].res_inf, x.cpu().numpy(), u.cpu().numpy(),
+                    lam.cpu().numpy()))
+        if persistent:
+            assert G.nmpc_launch_plan(s.h)["persistent"] == 0  # fell back, and stays so
+            rc2, st2 = s.solve()
+            assert rc2 == G.NMPC_OK and st2[0].iters == st[0].iters
+        s.close()
+    a, b = out
+    assert a[0] == b[0] == G.NMPC_OK
+    assert a[1] == b[1] and a[2] == b[2]
+    for i in (3, 4, 5):
+        assert np.array_equal(a[i], b[i])
