@@ -43,6 +43,22 @@ typedef struct nmpc_mlp nmpc_mlp;
 int nmpc_gemm_bf16(const void* A, const void* B, const float* bias, float* C, void* Cb, int M,
                    int N, int K, int lda, int ldb, int ldc, int gelu, void* stream);
 
+/* GEMM implementation (no counterpart in the paper): path 0 (default) runs
+   the tcgen05 tensor-core kernel (operand tiles by TMA with the 128-byte
+   swizzle, FP32 accumulator in tensor memory, split-K inside the network's
+   passes) whenever both operands meet the tensor-map rules (16-byte aligned
+   base, leading dimension a multiple of 8 elements), else the mma.sync
+   kernel; path 1 always the mma.sync kernel (for comparisons).  GEMMs of at
+   most 8 rows take a GEMV kernel either way.  Process-wide setting.
+   NMPC_MLP_ERR_BAD_ARG for another value. */
+int nmpc_gemm_set_path(int path);
+
+/* 1 if a tensor-core GEMM on the current device gave up on one of its
+   bounded waits since the last clear (its outputs are then invalid), else 0;
+   clear != 0 resets the word.  Synchronizes the device.  Negative on a CUDA
+   error. */
+int nmpc_gemm_error(int clear);
+
 /* out[i] = bf16(in[i]), round to nearest even. */
 int nmpc_cast_f32_bf16(const float* in, void* out, int64_t n, void* stream);
 

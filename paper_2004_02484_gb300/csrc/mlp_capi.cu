@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -31,17 +32,136 @@ int grid_for(long long n, int threads) {
   return (int)std::min<long long>(std::max<long long>(b, 1), 4096);
 }
 
+// ---------------------------------------------------------------------------
+// GEMM dispatch: GEMV for M <= 8; the tcgen05 kernel (TMA operand tiles) when
+// both operands meet the tensor-map rules (16-byte aligned base, rows a
+// multiple of 16 bytes apart); the mma.sync kernel otherwise (or when forced).
+// ---------------------------------------------------------------------------
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                 const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                 const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn() {
+  static EncodeTiled fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+int g_gemm_path = 0;  // 0 automatic, 1 the mma.sync kernel only
+
+// error word of the tcgen05 kernel's bounded waits (one per device and process)
+__device__ int g_tc_error;
+
+int* tc_error_ptr() {
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_tc_error) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return static_cast<int*>(p);
+}
+
+// Tensor map of a row-major BF16 matrix [rows][ld] read in boxes of
+// 128 rows x 64 elements with the 128-byte swizzle (zero fill past the end).
+bool make_map(CUtensorMap* m, const __nv_bfloat16* ptr, int rows, int K, int ld) {
+  EncodeTiled enc = encode_fn();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)mlp_dev::TC_BK, (cuuint32_t)mlp_dev::TC_BM};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(ptr), dims, strides,
+             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool tma_ok(const void* p, int ld, int K) {
+  return ((uintptr_t)p % 16 == 0) && (ld % 8 == 0) && (K % 8 == 0) && K >= 8;
+}
+
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n < 1) n = 1;
+  }
+  return n;
+}
+
+// ws: FP32 workspace of ws_elems for split-K partial products (null: no split).
 cudaError_t gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bias, float* C,
                  __nv_bfloat16* Cb, int M, int N, int K, int lda, int ldb, int ldc, int epi,
-                 cudaStream_t st) {
+                 cudaStream_t st, float* ws = nullptr, size_t ws_elems = 0) {
   mlp_dev::GemmArgs g{A, B, bias, C, Cb, M, N, K, lda, ldb, ldc, epi};
   if (M <= mlp_dev::GEMV_MAX_M) {
     mlp_dev::k_gemv_bf16<<<(N + 7) / 8, 256, 0, st>>>(g);
     return cudaGetLastError();
   }
+  CUtensorMap ta, tb;
+  if (g_gemm_path == 0 && tma_ok(A, lda, K) && tma_ok(B, ldb, K) && make_map(&ta, A, M, K, lda) &&
+      make_map(&tb, B, N, K, ldb)) {
+    static bool configured = false;
+    if (!configured) {
+      cudaError_t e = cudaFuncSetAttribute(mlp_dev::k_gemm_tc,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           mlp_dev::TC_SMEM);
+      if (e != cudaSuccess) return e;
+      configured = true;
+    }
+    const int tiles_m = (M + mlp_dev::TC_BM - 1) / mlp_dev::TC_BM;
+    const int tiles_n = (N + mlp_dev::TC_BN - 1) / mlp_dev::TC_BN;
+    const int tiles = tiles_m * tiles_n;
+    const int n_kb = (K + mlp_dev::TC_BK - 1) / mlp_dev::TC_BK;
+    // split K over more CTAs while the tiles alone leave most SMs idle (at
+    // least two K blocks per slice; the partials must fit the workspace)
+    int split = 1;
+    if (ws && tiles * 2 < num_sms() && n_kb >= 4) {
+      split = std::min((num_sms() + tiles - 1) / tiles, n_kb / 2);
+      const size_t per = (size_t)M * N;
+      split = (int)std::min<size_t>((size_t)split, ws_elems / std::max<size_t>(per, 1));
+      split = std::max(split, 1);
+    }
+    const int kb_per = (n_kb + split - 1) / split;
+    split = (n_kb + kb_per - 1) / kb_per;  // no empty slice
+    mlp_dev::TcArgs t{M, N, K, kb_per, n_kb, bias, C, Cb, ldc, epi,
+                      split > 1 ? ws : nullptr, tc_error_ptr()};
+    dim3 grid(tiles_n, tiles_m, split);
+    mlp_dev::k_gemm_tc<<<grid, mlp_dev::TC_THREADS, mlp_dev::TC_SMEM, st>>>(ta, tb, t);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || split == 1) return e;
+    const long long total = (long long)M * N;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
+    mlp_dev::k_splitk_epilogue<<<blocks, 256, 0, st>>>(ws, split, M, N, bias, epi, C, Cb, ldc);
+    return cudaGetLastError();
+  }
   dim3 grid((N + mlp_dev::BN - 1) / mlp_dev::BN, (M + mlp_dev::BM - 1) / mlp_dev::BM);
   mlp_dev::k_gemm_bf16<<<grid, mlp_dev::GEMM_THREADS, 0, st>>>(g);
   return cudaGetLastError();
+}
+
+// Launches gemm() issues for these operands (for launch accounting).
+int gemm_launches(const void* A, const void* B, int M, int N, int K, int lda, int ldb,
+                  bool has_ws) {
+  if (M <= mlp_dev::GEMV_MAX_M || g_gemm_path != 0 || !tma_ok(A, lda, K) || !tma_ok(B, ldb, K) ||
+      !encode_fn())
+    return 1;
+  const int tiles = ((M + 127) / 128) * ((N + 127) / 128);
+  const int n_kb = (K + 63) / 64;
+  return (has_ws && tiles * 2 < num_sms() && n_kb >= 4) ? 2 : 1;
 }
 
 cudaError_t transpose(const __nv_bfloat16* in, __nv_bfloat16* out, int rows, int cols,
@@ -71,11 +191,29 @@ struct nmpc_mlp {
   float* y = nullptr;             // [B, out]
   float* loss = nullptr;
   float* h_loss = nullptr;
+  float* ws = nullptr;  // split-K partial products of the tensor-core GEMM
+  size_t ws_elems = 0;
   int step = 0;
   long long launches = 0;
 };
 
 extern "C" {
+
+int nmpc_gemm_set_path(int path) {
+  if (path != 0 && path != 1) return NMPC_MLP_ERR_BAD_ARG;
+  g_gemm_path = path;
+  return NMPC_MLP_OK;
+}
+
+int nmpc_gemm_error(int clear) {
+  int* p = tc_error_ptr();
+  if (!p) return NMPC_MLP_ERR_CUDA;
+  int v = 0;
+  MCK(cudaDeviceSynchronize());
+  MCK(cudaMemcpy(&v, p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (clear) MCK(cudaMemset(p, 0, sizeof(int)));
+  return v;
+}
 
 int nmpc_gemm_bf16(const void* A, const void* B, const float* bias, float* C, void* Cb, int M,
                    int N, int K, int lda, int ldb, int ldc, int gelu, void* stream) {
@@ -176,6 +314,9 @@ int nmpc_mlp_create(int n_layers, const int* widths, int max_batch, uint64_t see
   bal(&m->dzT, (size_t)B * wmax);
   fal(&m->y, (size_t)B * m->w[n_layers]);
   fal(&m->loss, 1);
+  // split-K partial products: up to 8 Mi floats (32 MiB)
+  m->ws_elems = std::min<size_t>(size_t(8) << 20, (size_t)B * wmax * 16);
+  fal(&m->ws, m->ws_elems);
   A(cudaMallocHost((void**)&m->h_loss, sizeof(float)));
   if (!ok) {
     nmpc_mlp_destroy(m);
@@ -278,15 +419,11 @@ static int forward_impl(nmpc_mlp* m, const float* x, int B, float* y, cudaStream
   for (int l = 0; l < m->L; ++l) {
     const int nin = m->w[l], nout = m->w[l + 1];
     const bool last = (l == m->L - 1);
-    // z = a W^T + b (fp32 kept for the backward pass); hidden layers store GELU(z) as bf16
-    MCK(gemm(m->a[l], m->Wb[l], m->b[l], m->z[l], nullptr, B, nout, nin, nin, nin, nout,
-             mlp_dev::EPI_NONE, st));
-    m->launches++;
-    if (!last) {
-      MCK(gemm(m->a[l], m->Wb[l], m->b[l], nullptr, m->a[l + 1], B, nout, nin, nin, nin, nout,
-               mlp_dev::EPI_GELU, st));
-      m->launches++;
-    }
+    // z = a W^T + b (fp32 kept for the backward pass) and, for a hidden
+    // layer, GELU(z) as bf16: both from one product
+    MCK(gemm(m->a[l], m->Wb[l], m->b[l], m->z[l], last ? nullptr : m->a[l + 1], B, nout, nin, nin,
+             nin, nout, last ? mlp_dev::EPI_NONE : mlp_dev::EPI_Z_GELU, st, m->ws, m->ws_elems));
+    m->launches += gemm_launches(m->a[l], m->Wb[l], B, nout, nin, nin, nin, m->ws != nullptr);
   }
   const int nout = m->w[m->L];
   if (y != m->z[m->L - 1]) {
@@ -324,17 +461,18 @@ int nmpc_mlp_backward(nmpc_mlp* m, const float* x, const float* target, int B, f
     MCK(transpose(m->dz16, m->dzT, B, nout, st));
     MCK(transpose(m->a[l], m->aT[l], B, nin, st));
     MCK(gemm(m->dzT, m->aT[l], nullptr, m->gW[l], nullptr, nout, nin, B, B, B, nin,
-             mlp_dev::EPI_NONE, st));
-    m->launches += 4;
+             mlp_dev::EPI_NONE, st, m->ws, m->ws_elems));
+    m->launches += 3 + gemm_launches(m->dzT, m->aT[l], nout, nin, B, B, B, m->ws != nullptr);
     if (l > 0) {
       // da[b, i] = sum_o dz[b, o] W[o, i]: A = dz [B, nout], B-operand = W^T [nin, nout]
       MCK(gemm(m->dz16, m->WTb[l], nullptr, m->da, nullptr, B, nin, nout, nout, nout, nin,
-               mlp_dev::EPI_NONE, st));
+               mlp_dev::EPI_NONE, st, m->ws, m->ws_elems));
       const long long n = (long long)B * nin;
       mlp_dev::k_gelu_backward<<<grid_for(n, 256), 256, 0, st>>>(m->da, m->z[l - 1], m->dz,
                                                                 m->dz16, n);
       MCK(cudaGetLastError());
-      m->launches += 2;
+      m->launches += 1 + gemm_launches(m->dz16, m->WTb[l], B, nin, nout, nout, nout,
+                                       m->ws != nullptr);
     }
   }
   if (loss_host) {
@@ -382,7 +520,7 @@ void nmpc_mlp_destroy(nmpc_mlp* m) {
     F(m->mb[l]); F(m->vb[l]); F(m->Wb[l]); F(m->WTb[l]); F(m->z[l]);
   }
   for (size_t l = 0; l < m->a.size(); ++l) { F(m->a[l]); F(m->aT[l]); }
-  F(m->da); F(m->dz); F(m->dz16); F(m->dzT); F(m->y); F(m->loss);
+  F(m->da); F(m->dz); F(m->dz16); F(m->dzT); F(m->y); F(m->loss); F(m->ws);
   if (m->h_loss) cudaFreeHost(m->h_loss);
   delete m;
 }

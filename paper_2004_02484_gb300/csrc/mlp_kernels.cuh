@@ -12,6 +12,7 @@
 // needs to be a multiple of 8 (16-byte chunks).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math_constants.h>
@@ -21,7 +22,7 @@ namespace mlp_dev {
 
 constexpr int BM = 128, BN = 128, BK = 32, PAD = 8, LDS = BK + PAD;  // bf16 elements
 constexpr int GEMM_THREADS = 256;
-enum { EPI_NONE = 0, EPI_GELU = 1 };
+enum { EPI_NONE = 0, EPI_GELU = 1, EPI_Z_GELU = 2 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -62,6 +63,24 @@ __device__ __forceinline__ float gelu_grad(float z) {
   const float cdf = 0.5f * (1.0f + erff(z * 0.70710678118654752f));
   const float pdf = 0.39894228040143268f * expf(-0.5f * z * z);
   return cdf + z * pdf;
+}
+
+// Output (m, n) of an accumulated product x: + bias; EPI_NONE / EPI_GELU store
+// the (activated) value to C and/or Cb; EPI_Z_GELU stores the pre-activation
+// to C and BF16 GELU of it to Cb (a hidden layer's z and activation from one
+// product).
+__device__ __forceinline__ void epilogue_store(float x, int m, int n, const float* bias, int epi,
+                                               float* C, __nv_bfloat16* Cb, int ldc) {
+  if (bias) x += bias[n];
+  const long long o = (long long)m * ldc + n;
+  if (epi == EPI_Z_GELU) {
+    if (C) C[o] = x;
+    if (Cb) Cb[o] = __float2bfloat16_rn(gelu(x));
+    return;
+  }
+  if (epi == EPI_GELU) x = gelu(x);
+  if (C) C[o] = x;
+  if (Cb) Cb[o] = __float2bfloat16_rn(x);
 }
 
 struct GemmArgs {
@@ -161,11 +180,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_gemm_bf16(GemmArgs g) {
         const int m = m0 + wm + i * 16 + (lane >> 2) + ((q >> 1) ? 8 : 0);
         const int n = n0 + wn + j * 8 + (lane & 3) * 2 + (q & 1);
         if (m < g.M && n < g.N) {
-          float v = acc[i][j][q];
-          if (g.bias) v += g.bias[n];
-          if (g.epi == EPI_GELU) v = gelu(v);
-          if (g.C) g.C[(long long)m * g.ldc + n] = v;
-          if (g.Cb) g.Cb[(long long)m * g.ldc + n] = __float2bfloat16_rn(v);
+          epilogue_store(acc[i][j][q], m, n, g.bias, g.epi, g.C, g.Cb, g.ldc);
         }
       }
 }
@@ -211,12 +226,7 @@ __global__ void __launch_bounds__(256) k_gemv_bf16(GemmArgs g) {
   for (int m = 0; m < GEMV_MAX_M; ++m) {
     float v = acc[m];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0 && m < g.M) {
-      if (g.bias) v += g.bias[n];
-      if (g.epi == EPI_GELU) v = gelu(v);
-      if (g.C) g.C[(long long)m * g.ldc + n] = v;
-      if (g.Cb) g.Cb[(long long)m * g.ldc + n] = __float2bfloat16_rn(v);
-    }
+    if (lane == 0 && m < g.M) epilogue_store(v, m, n, g.bias, g.epi, g.C, g.Cb, g.ldc);
   }
 }
 
@@ -335,5 +345,7 @@ __global__ void k_adam(float* w, const float* g, float* m, float* v, __nv_bfloat
     if (wb) wb[e] = __float2bfloat16_rn(nw);
   }
 }
+
+#include "mlp_tc.cuh"
 
 }  // namespace mlp_dev

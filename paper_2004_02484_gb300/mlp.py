@@ -16,7 +16,7 @@ NMPC_MLP_OK = 0
 NMPC_MLP_ERR_BAD_ARG = -1
 NMPC_MLP_ERR_CUDA = -2
 
-EXPORTED = ["nmpc_gemm_bf16", "nmpc_cast_f32_bf16", "nmpc_cast_f32_f64", "nmpc_cast_f64_f32",
+EXPORTED = ["nmpc_gemm_bf16", "nmpc_gemm_set_path", "nmpc_gemm_error", "nmpc_cast_f32_bf16", "nmpc_cast_f32_f64", "nmpc_cast_f64_f32",
             "nmpc_transpose_bf16", "nmpc_pool_avg",
             "nmpc_mlp_create", "nmpc_mlp_num_params",
             "nmpc_mlp_set_params", "nmpc_mlp_get_params", "nmpc_mlp_forward",
@@ -26,6 +26,8 @@ EXPORTED = ["nmpc_gemm_bf16", "nmpc_cast_f32_bf16", "nmpc_cast_f32_f64", "nmpc_c
 _P, _I, _F = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
 _SIG = {
     "nmpc_gemm_bf16": (_I, [_P, _P, _P, _P, _P, _I, _I, _I, _I, _I, _I, _I, _P]),
+    "nmpc_gemm_set_path": (_I, [_I]),
+    "nmpc_gemm_error": (_I, [_I]),
     "nmpc_cast_f32_bf16": (_I, [_P, _P, ctypes.c_int64, _P]),
     "nmpc_cast_f32_f64": (_I, [_P, _P, ctypes.c_int64, _P]),
     "nmpc_transpose_bf16": (_I, [_P, _P, _I, _I, _P]),
@@ -74,6 +76,20 @@ def nmpc_gemm_bf16(A, B, C=None, Cb=None, bias=None, gelu=False, stream=None):
                             None if Cb is None else _dptr(Cb, "bf16"),
                             M, N, K, A.stride(0), B.stride(0), ldc, int(gelu), _stream(stream))
     _check(rc, "nmpc_gemm_bf16")
+
+
+def nmpc_gemm_set_path(path: int) -> None:
+    """0: tcgen05 tensor-core GEMM where the operands allow it (default);
+    1: the mma.sync GEMM everywhere (comparisons)."""
+    _check(LIB.nmpc_gemm_set_path(int(path)), "nmpc_gemm_set_path")
+
+
+def nmpc_gemm_error(clear: bool = True) -> int:
+    """1 if a tensor-core GEMM gave up on a bounded wait since the last clear."""
+    rc = LIB.nmpc_gemm_error(1 if clear else 0)
+    if rc < 0:
+        raise RuntimeError(f"nmpc_gemm_error failed ({rc})")
+    return rc
 
 
 def nmpc_cast_f32_bf16(x, out, stream=None):

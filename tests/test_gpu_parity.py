@@ -403,7 +403,9 @@ def test_grid_barrier_timeout_falls_back_to_per_iteration_launches(G, precision)
     per iteration, so the result is the one of a handle that never tried the
     persistent launch, and the handle stays in per-iteration mode."""
     import torch
-    insts, kw = [wl.heat1d(40, 9, 3, 0.02, seed=11)], dict(cluster=3)
+    # lines=2 keeps the mixed-precision 1D instance on the cluster path (the
+    # line path has no persistent launch)
+    insts, kw = [wl.heat1d(40, 9, 3, 0.02, seed=11)], dict(cluster=3, lines=2)
     out = []
     for persistent, wait in ((1, 100), (0, 0)):
         s = G.Solver(insts, tol=1e-6, precision=precision, max_iter=4000, persistent=persistent,
