@@ -193,9 +193,69 @@ def closedloop_learned(n_train: int, train_steps: int, n_test: int, steps: int, 
     return res
 
 
+def gemm_bench(shapes, reps: int, path_list=(0, 1)):
+    """CUDA-event time of nmpc_gemm_bf16 (C = A B^T, BF16 in, FP32 out) per
+    shape and GEMM path (0: tcgen05 where the operands allow, 1: mma.sync),
+    and of the network passes of the learned start (split-K inside)."""
+    import torch
+    from . import mlp as GM
+    out = []
+    for (M, N, K) in shapes:
+        A = torch.randn(M, K, device="cuda").to(torch.bfloat16)
+        B = torch.randn(N, K, device="cuda").to(torch.bfloat16)
+        C = torch.empty(M, N, device="cuda")
+        for path in path_list:
+            GM.nmpc_gemm_set_path(path)
+            for _ in range(3):
+                GM.nmpc_gemm_bf16(A, B, C=C)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                GM.nmpc_gemm_bf16(A, B, C=C)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            out.append({"M": M, "N": N, "K": K, "path": "tcgen05" if path == 0 else "mma.sync",
+                        "us": 1e3 * ms, "tflops": 2.0 * M * N * K / (ms / 1e3) / 1e12})
+    GM.nmpc_gemm_set_path(0)
+    for widths, batch in (([8192, 512, 512, 512, 1600], 64), ([8192, 512, 512, 512, 6800], 256)):
+        for path in path_list:
+            GM.nmpc_gemm_set_path(path)
+            net = GM.MLP(widths, batch, 0)
+            x = torch.randn(batch, widths[0], device="cuda")
+            t = torch.randn(batch, widths[-1], device="cuda")
+            y = torch.empty(batch, widths[-1], device="cuda")
+            for _ in range(3):
+                net.forward(x, y)
+                net.train_step(x, t, 1e-4, want_loss=False)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record()
+            for _ in range(reps):
+                net.forward(x, y)
+            e[1].record()
+            for _ in range(reps):
+                net.train_step(x, t, 1e-4, want_loss=False)
+            e[2].record()
+            torch.cuda.synchronize()
+            fl = sum(2.0 * batch * widths[l] * widths[l + 1] for l in range(len(widths) - 1))
+            fwd = e[0].elapsed_time(e[1]) / reps
+            trn = e[1].elapsed_time(e[2]) / reps
+            out.append({"net": widths, "batch": batch,
+                        "path": "tcgen05" if path == 0 else "mma.sync",
+                        "forward_us": 1e3 * fwd, "forward_tflops": fl / (fwd / 1e3) / 1e12,
+                        "train_step_us": 1e3 * trn, "train_tflops": 3 * fl / (trn / 1e3) / 1e12})
+            net.close()
+    GM.nmpc_gemm_set_path(0)
+    return {"experiment": "gemm", "results": out, "tc_error": GM.nmpc_gemm_error(True)}
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", choices=["batch1d", "closedloop", "closedloop_learned", "solve"])
+    ap.add_argument("which", choices=["batch1d", "closedloop", "closedloop_learned", "solve",
+                                      "gemm"])
+    ap.add_argument("--shapes", default="4096x4096x4096,256x512x8192,256x6800x512,64x512x8192",
+                    help="gemm: MxNxK list")
+    ap.add_argument("--paths", default="0,1", help="gemm: 0 tcgen05, 1 mma.sync")
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--grid", type=int, default=256)
@@ -223,7 +283,11 @@ def main():
     build.build()  # before the binding loads the library (a rebuilt one, if sources changed)
     global G
     from . import nmpc as G
-    if a.which == "batch1d":
+    if a.which == "gemm":
+        shapes = [tuple(int(v) for v in sh.split("x")) for sh in a.shapes.split(",") if sh]
+        paths = tuple(int(v) for v in a.paths.split(","))
+        print(json.dumps(gemm_bench(shapes, a.reps, paths)), flush=True)
+    elif a.which == "batch1d":
         print(json.dumps(batch1d(a.n or 1024, reps=a.reps, tune=a.tune, use_graph=a.graph,
                                  lines=a.lines)), flush=True)
     elif a.which == "solve":
