@@ -137,7 +137,8 @@ cudaError_t gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, const float* bi
     }
     const int kb_per = (n_kb + split - 1) / split;
     split = (n_kb + kb_per - 1) / kb_per;  // no empty slice
-    mlp_dev::TcArgs t{M, N, K, kb_per, n_kb, bias, C, Cb, ldc, epi,
+    const int vec_ok = (ldc % 8 == 0) && ((uintptr_t)C % 16 == 0) && ((uintptr_t)Cb % 16 == 0);
+    mlp_dev::TcArgs t{M, N, K, kb_per, n_kb, bias, C, Cb, ldc, epi, vec_ok,
                       split > 1 ? ws : nullptr, tc_error_ptr()};
     dim3 grid(tiles_n, tiles_m, split);
     mlp_dev::k_gemm_tc<<<grid, mlp_dev::TC_THREADS, mlp_dev::TC_SMEM, st>>>(ta, tb, t);

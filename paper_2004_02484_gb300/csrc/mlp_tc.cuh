@@ -27,7 +27,9 @@
 // frees its TMEM and returns.
 #pragma once
 
-constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 4;
+// three stages (96 KB) so that two CTAs fit per SM: one CTA's epilogue then
+// overlaps the other's main loop (TMEM: 2 x 128 of 512 columns)
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 3;
 constexpr int TC_THREADS = 128;
 constexpr int TC_TILE_A = TC_BM * TC_BK * 2;  // bytes of one A stage (16 KB)
 constexpr int TC_TILE_B = TC_BN * TC_BK * 2;  // bytes of one B stage (16 KB)
@@ -42,6 +44,7 @@ struct TcArgs {
   float* C;             // [M, ldc] or null
   __nv_bfloat16* Cb;    // [M, ldc] or null
   int ldc, epi;
+  int vec_ok;           // C / Cb rows 16-byte aligned (ldc % 8 == 0, aligned bases)
   float* ws;            // split-K partials [split][M][N] (split > 1) or null
   int* err;             // raised when a bounded wait ran out
 };
@@ -132,7 +135,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(TC_THREADS, 2)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               TcArgs g) {
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
@@ -230,11 +233,56 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       tmem_ld32(lane_base + (uint32_t)c0, v);
       const int n = n0 + c0;
       if (row < g.M && n < g.N) {
+        const bool whole = (n + 32 <= g.N);
         if (g.ws) {
           float* dst = g.ws + ((long long)blockIdx.z * g.M + row) * g.N + n;
+          if (whole && ((g.N & 3) == 0)) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (n + j < g.N) dst[j] = v[j];
+            for (int j = 0; j < 32; j += 4)
+              *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (n + j < g.N) dst[j] = v[j];
+          }
+        } else if (whole && g.vec_ok) {
+          // 32 whole columns with 16-byte aligned rows: vector stores
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            float x = v[j];
+            if (g.bias) x += g.bias[n + j];
+            v[j] = x;
+          }
+          const long long o = (long long)row * g.ldc + n;
+          if (g.C) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+              float4 q;
+              q.x = (g.epi == EPI_GELU) ? gelu(v[j]) : v[j];
+              q.y = (g.epi == EPI_GELU) ? gelu(v[j + 1]) : v[j + 1];
+              q.z = (g.epi == EPI_GELU) ? gelu(v[j + 2]) : v[j + 2];
+              q.w = (g.epi == EPI_GELU) ? gelu(v[j + 3]) : v[j + 3];
+              *reinterpret_cast<float4*>(g.C + o + j) = q;
+            }
+          }
+          if (g.Cb) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 8) {
+              uint4 q;
+              uint32_t* w = reinterpret_cast<uint32_t*>(&q);
+#pragma unroll
+              for (int t = 0; t < 4; ++t) {
+                float a = v[j + 2 * t], b = v[j + 2 * t + 1];
+                if (g.epi != EPI_NONE) {
+                  a = gelu(a);
+                  b = gelu(b);
+                }
+                const __nv_bfloat162 h2 = __floats2bfloat162_rn(a, b);
+                w[t] = *reinterpret_cast<const uint32_t*>(&h2);
+              }
+              *reinterpret_cast<uint4*>(g.Cb + o + j) = q;
+            }
+          }
         } else {
 #pragma unroll
           for (int j = 0; j < 32; ++j)
