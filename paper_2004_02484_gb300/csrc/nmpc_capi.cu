@@ -86,6 +86,7 @@ struct nmpc_handle {
   size_t box_bytes = 0;
   bool mixed = false;
   bool rb = false;  // red-black upper layer (two half-sweep launches per iteration)
+  int n_work_even = 0, n_strips_even = 0, n_patches_even = 0;  // red-black: even-stage items first
   size_t strip_smem_rb = 0;  // k_strip's shared memory in red-black half 1
   // graph of one chunk of iterations
   cudaGraphExec_t graph_exec = nullptr;
@@ -212,6 +213,9 @@ IterArgs make_args(nmpc_handle* h) {
   A.n_lo = h->opts.n_lo;
   A.n_u_it = h->opts.n_u_it;
   A.rb = h->rb ? 1 : 0;
+  A.n_work_even = h->n_work_even;
+  A.n_strips_even = h->n_strips_even;
+  A.n_patches_even = h->n_patches_even;
   A.grid_wait = h->opts.barrier_wait_cycles > 0 ? (long long)h->opts.barrier_wait_cycles
                                                 : nmpc_dev::GRID_WAIT_CYCLES;
   A.resid_only = 0;
@@ -546,6 +550,13 @@ TileKernel strip_kernel(int n_lo, bool rbn = false) {
 // Whether launch j of an iteration is red-black half 1.
 inline bool rb_half1(const IterArgs& A, int j) { return A.rb && (j & 1); }
 
+// Items of a list of n (n_even of them at even stages, first) that launch j
+// covers: all of them, or one half-sweep's share.
+inline int half_count(const IterArgs& A, int j, int n, int n_even) {
+  if (!A.rb) return n;
+  return (j & 1) ? n - n_even : n_even;
+}
+
 template <typename T>
 TileKernel patch_kernel(int n_lo) {
   switch (n_lo) {
@@ -561,8 +572,10 @@ constexpr int PATCH_WARPS = 4;  // warps per k_patch block
 
 template <typename T>
 cudaError_t launch_patch(const nmpc_handle* h, const IterArgs& A, cudaStream_t st, int mode, int j) {
+  const int count = half_count(A, j, h->n_patches, h->n_patches_even);
+  if (count == 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)((h->n_patches + PATCH_WARPS - 1) / PATCH_WARPS));
+  cfg.gridDim = dim3((unsigned)((count + PATCH_WARPS - 1) / PATCH_WARPS));
   cfg.blockDim = dim3(32 * PATCH_WARPS);
   cfg.dynamicSmemBytes = h->patch_smem;
   cfg.stream = st;
@@ -576,8 +589,10 @@ cudaError_t launch_patch(const nmpc_handle* h, const IterArgs& A, cudaStream_t s
 
 template <typename T>
 cudaError_t launch_strip(const nmpc_handle* h, const IterArgs& A, cudaStream_t st, int mode, int j) {
+  const int count = half_count(A, j, h->n_strips, h->n_strips_even);
+  if (count == 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)((h->n_strips + nmpc_dev::STRIP_WARPS - 1) / nmpc_dev::STRIP_WARPS));
+  cfg.gridDim = dim3((unsigned)((count + nmpc_dev::STRIP_WARPS - 1) / nmpc_dev::STRIP_WARPS));
   cfg.blockDim = dim3((unsigned)h->strip_threads);
   cfg.dynamicSmemBytes = rb_half1(A, j) ? h->strip_smem_rb : h->strip_smem;
   cfg.stream = st;
@@ -663,9 +678,13 @@ template <int MODE>
 cudaError_t launch_iterate(nmpc_handle* h, const IterArgs& A, cudaStream_t st, int j = 0) {
   if (!rb_half1(A, j)) h->iter_launches++;  // one iteration step per Jacobi launch or half pair
   cudaError_t e = cudaSuccess;
-  if (h->n_work > 0) {
+  const int n_cl = half_count(A, j, h->n_work, h->n_work_even);
+  if (n_cl > 0) {
     h->launches++;
-    const LaunchPlan P = plan_of(h);
+    LaunchPlan P = plan_of(h);
+    // a red-black half launches the clusters of its own items only (a
+    // global-slab launch keeps at most the CTAs it has slabs for)
+    if (A.rb) P.grid = P.smem_mode ? n_cl * P.csize : std::min(P.grid, n_cl);
     e = timed(h, KT_CLUSTER, st, [&]() {
       return h->mixed ? launch_k<float>(P, A, st, MODE, j) : launch_k<double>(P, A, st, MODE, j);
     });
@@ -1418,6 +1437,17 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
   // specialisation of the kernel body: instruction-cache locality)
   std::stable_sort(lines.begin(), lines.end(),
                    [](const int4& a, const int4& b) { return a.z < b.z; });
+  if (h->rb) {
+    // red-black: each list's even-stage items first, so that a half-sweep
+    // launch covers exactly its own items
+    auto even2 = [](const int2& w) { return (w.y & 1) == 0; };
+    auto even4 = [](const int4& w) { return (w.y & 1) == 0; };
+    h->n_work_even = (int)(std::stable_partition(work.begin(), work.end(), even2) - work.begin());
+    h->n_strips_even =
+        (int)(std::stable_partition(strips.begin(), strips.end(), even4) - strips.begin());
+    h->n_patches_even =
+        (int)(std::stable_partition(patches.begin(), patches.end(), even4) - patches.begin());
+  }
   h->n_work = (int)work.size();
   h->n_strips = (int)strips.size();
   h->n_patches = (int)patches.size();

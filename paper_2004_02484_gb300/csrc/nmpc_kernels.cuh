@@ -27,6 +27,7 @@
 #include <type_traits>
 #include <cuda_runtime.h>
 #include <math_constants.h>
+#include <stddef.h>
 #include <stdint.h>
 
 namespace nmpc_dev {
@@ -112,6 +113,10 @@ struct IterArgs {
   // updating the even 0-based stages from iterate k, half 1 the odd ones
   // with x_{i-1}, lambda_{i+1} already updated (launch index j = 2 i + half)
   int rb;
+  // red-black: the cluster, strip and patch lists hold the items of even
+  // stages first (this many), then those of odd stages; a half-sweep
+  // launch covers its own range only
+  int n_work_even, n_strips_even, n_patches_even;
   long long grid_wait;  // spin budget of one grid-barrier wait (SM clock cycles)
   int resid_only;  // one-shot: residual norms only (float64)
   int full_all;    // every residual in float64 (FP64 precision)
@@ -1394,7 +1399,9 @@ __global__ void __launch_bounds__(512) k_iterate(IterArgs A, int MODE, int j) {
   const int n_clusters = gridDim.x / A.csize;
   pdl_wait();  // the previous iteration's state, residuals and control words
 
-  for (int w = blockIdx.x / A.csize; w < A.n_work; w += n_clusters) {
+  const int w_begin = (A.rb && half) ? A.n_work_even : 0;
+  const int w_end = A.rb ? (half ? A.n_work : A.n_work_even) : A.n_work;
+  for (int w = w_begin + blockIdx.x / A.csize; w < w_end; w += n_clusters) {
     const int2 item = A.work[w];
     const int b = item.x, s = item.y;
     if (!stage_in_half(A, s, half)) continue;  // uniform across the cluster

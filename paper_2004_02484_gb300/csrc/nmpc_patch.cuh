@@ -348,8 +348,9 @@ __global__ void __launch_bounds__(128) k_patch(IterArgs A, int MODE, int j) {
   const int half = launch_half(A, j);
   const int rd = (MODE == MODE_SOLVE) ? (k & 1) : 0;
   pdl_wait();
-  const int item = blockIdx.x * WPB + warp;
-  if (item >= A.n_patches) return;  // warp-uniform; no block barriers follow
+  const int item = ((A.rb && half) ? A.n_patches_even : 0) + blockIdx.x * WPB + warp;
+  const int item_end = A.rb ? (half ? A.n_patches : A.n_patches_even) : A.n_patches;
+  if (item >= item_end) return;  // warp-uniform; no block barriers follow
   const int4 it = A.patches[item];
   const int b = it.x, s = it.y, a = it.z;
   if (!stage_in_half(A, s, half)) return;

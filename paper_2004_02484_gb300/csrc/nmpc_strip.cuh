@@ -41,15 +41,21 @@ __host__ __device__ constexpr int strip_ring_rows(int n_lo) {
   return 2 * n_lo - 1 + STRIP_AHEAD + 1;
 }
 
-// Shared memory of one strip warp: the input ring (RING rows x NF fields x
-// 32 lanes, float64) and the actuators in reach sorted by row.  NF = SREC,
-// or SREC + 2 for red-black half 1, whose ring also holds x_{i-1} and
-// lambda_{i+1} as updated by half 0 (fields R_XPN, R_LNN).
-enum { R_XPN = SREC, R_LNN = SREC + 1 };
-__host__ __device__ constexpr int strip_fields(bool rbn) { return rbn ? SREC + 2 : SREC; }
-template <int RING, int NF = SREC>
+// Shared memory of one strip warp: the input rings (float64, 32 lanes) and
+// the actuators in reach sorted by row.  x_i and lambda_i stay RING rows
+// (the update of row j - E reads them); the fields only pass 1 reads
+// (x_{i-1}, lambda_{i+1}, ref, and for red-black half 1 x_{i-1}, lambda_{i+1}
+// as updated by half 0) need rows j - 1 .. j + 2 only: a ring of
+// STRIP_AHEAD + 2 rows with NF = 3 or 5 fields.
+enum { RB_X = 0, RB_L = 1 };                                      // RING rows
+enum { RS_XP = 0, RS_LN = 1, RS_RF = 2, RS_XPN = 3, RS_LNN = 4 };  // short ring
+constexpr int STRIP_SHORT = STRIP_AHEAD + 2;
+static_assert((STRIP_SHORT & (STRIP_SHORT - 1)) == 0, "the short ring is indexed by j & (rows - 1)");
+__host__ __device__ constexpr int strip_fields(bool rbn) { return rbn ? 5 : 3; }
+template <int RING, int NF = 3>
 struct StripShared {
-  double ring[RING * NF * 32];
+  double ring[RING * 2 * 32];
+  double sring[STRIP_SHORT * NF * 32];
   StripAct act[MAX_NU];
   int n_act;
 };
@@ -161,12 +167,21 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
   const double* XPNg = (s == 0) ? A.x0 + I.g_off : A.xout[rd ^ 1] + so - I.ng;
   const double* LNNg = A.lout[rd ^ 1] + so + I.ng;
   double* ring = ws.ring + lane;
+  // the short ring follows the long one in the same structure: addressed
+  // from the same base (no second pointer register)
+  using SS = StripShared<RING, NF>;
+  static_assert(offsetof(SS, sring) == offsetof(SS, ring) + sizeof(double) * RING * 2 * 32,
+                "short ring right after the long one");
   // ring row of j + d for the current step j (sj = j mod RING), -RING < d < RING
   int sj = 0;
   auto slot_at = [&](int d, int f) -> double* {
     int q = sj + d;
     q = q < 0 ? q + RING : (q >= RING ? q - RING : q);
-    return ring + (q * NF + f) * 32;
+    return ring + (q * 2 + f) * 32;
+  };
+  // short-ring row of region row r (any r >= -1: rows j - 1 .. j + 2 of step j)
+  auto sslot_row = [&](int r, int f) -> double* {
+    return ring + RING * 2 * 32 + (((r + STRIP_SHORT) & (STRIP_SHORT - 1)) * NF + f) * 32;
   };
   // row rj's five inputs; cells outside the grid and rows past the region
   // are zero-filled by the copies themselves (source size 0, from a clamped
@@ -179,14 +194,15 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
     const bool ok = gx_ok && gy >= 0 && gy < my && rj < RH;
     const int c = min(max(gy, 0), my - 1) * mx + gxc;
     double* d = slot_at(dj, 0);
-    cp_async8_zfill(d + R_X * 32, Xg + c, ok);
-    cp_async8_zfill(d + R_L * 32, Lg + c, ok);
-    cp_async8_zfill(d + R_XP * 32, XPg + c, ok);
-    cp_async8_zfill(d + R_LN * 32, (last ? Lg : LNg) + c, ok && !last);
-    cp_async8_zfill(d + R_RF * 32, RFg + c, ok);
+    double* e = sslot_row(rj, 0);
+    cp_async8_zfill(d + RB_X * 32, Xg + c, ok);
+    cp_async8_zfill(d + RB_L * 32, Lg + c, ok);
+    cp_async8_zfill(e + RS_XP * 32, XPg + c, ok);
+    cp_async8_zfill(e + RS_LN * 32, (last ? Lg : LNg) + c, ok && !last);
+    cp_async8_zfill(e + RS_RF * 32, RFg + c, ok);
     if constexpr (RBN) {
-      cp_async8_zfill(d + R_XPN * 32, XPNg + c, ok);
-      cp_async8_zfill(d + R_LNN * 32, (last ? Lg : LNNg) + c, ok && !last);
+      cp_async8_zfill(e + RS_XPN * 32, XPNg + c, ok);
+      cp_async8_zfill(e + RS_LNN * 32, (last ? Lg : LNNg) + c, ok && !last);
     }
     asm volatile("cp.async.commit_group;\n" ::);
   };
@@ -228,7 +244,7 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
     asm volatile("cp.async.wait_group %0;\n" ::"n"(STRIP_AHEAD));
     // ---- pass 0: row j ----
     {
-      const double x = *slot_at(0, R_X), l = *slot_at(0, R_L);
+      const double x = *slot_at(0, RB_X), l = *slot_at(0, RB_L);
       if constexpr (full) {
         phd.push(k0d * (x + 0.5 * k1d * x * x));
         lad.push(l);
@@ -267,10 +283,11 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
         next_row = na < n_act ? ws.act[na].row : 0x7fffffff;
       }
       const double* rs = slot_at(-1, 0);
-      const double x = rs[R_X * 32], lam = rs[R_L * 32], xp = rs[R_XP * 32], rc = rs[R_RF * 32];
+      const double* qs = sslot_row(j - 1, 0);
+      const double x = rs[RB_X * 32], lam = rs[RB_L * 32], xp = qs[RS_XP * 32], rc = qs[RS_RF * 32];
       T K1;
       if constexpr (full) {
-        const double ln = last ? hqfd * (x - rc) : rs[R_LN * 32];
+        const double ln = last ? hqfd * (x - rc) : qs[RS_LN * 32];
         const double lphi = phd.nsum(cxd, cyd) - dcd * phd.w1;
         const double mu = lad.nsum(cxd, cyd) - dcd * lad.w1;
         const double dphi = k0d * (1.0 + k1d * x);
@@ -283,8 +300,8 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
           nm.vsq += K1d * K1d + K3d * K3d;
         }
         if constexpr (RBN) {
-          K1 = to_T<T>(rs[R_XPN * 32] - x + t1);
-          K3 = to_T<T>(last ? K3d : rs[R_LNN * 32] - lam + t3);
+          K1 = to_T<T>(qs[RS_XPN * 32] - x + t1);
+          K3 = to_T<T>(last ? K3d : qs[RS_LNN * 32] - lam + t3);
         } else {
           K1 = to_T<T>(K1d);
           K3 = to_T<T>(K3d);
@@ -309,7 +326,7 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
         // float64 pipe issues 2 lanes per clock per SM; their rounding enters
         // the bound, and the float64 residual certifies convergence); at the
         // last stage lambda_{N+1} = h qf (x_N - ref) is an O(h) term
-        const float xpf = d2f(xp), lnf = last ? 0.0f : d2f(rs[R_LN * 32]);
+        const float xpf = d2f(xp), lnf = last ? 0.0f : d2f(qs[RS_LN * 32]);
         const float dx = xpf - xv, dl = lnf - laf.w1;
         const float K1f = dx + t1;
         const float K3f = dl + t3 + hqff * (xv - rv);
@@ -323,8 +340,8 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
         nm.fmax = fmax_nan(nm.fmax, fmax_nan(fabsf(K1v), fabsf(K3v)));
         nm.fsq += K1v * K1v + K3v * K3v;
         if constexpr (RBN) {
-          K1 = (T)((d2f(rs[R_XPN * 32]) - xv) + t1);
-          K3 = last ? (T)K3f : (T)((d2f(rs[R_LNN * 32]) - laf.w1) + t3);
+          K1 = (T)((d2f(qs[RS_XPN * 32]) - xv) + t1);
+          K3 = last ? (T)K3f : (T)((d2f(qs[RS_LNN * 32]) - laf.w1) + t3);
         } else {
           K1 = (T)K1f;
           K3 = (T)K3f;
@@ -345,8 +362,8 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
           const int c = gy * mx + gx;
           const T w = (-K3 - ax * v1) * rg;
           const double* rs = slot_at(-1, 0);
-          Xo[c] = fma(alpha, to_double(v1), rs[R_X * 32]);
-          Lo[c] = fma(alpha, to_double(w), rs[R_L * 32]);
+          Xo[c] = fma(alpha, to_double(v1), rs[RB_X * 32]);
+          Lo[c] = fma(alpha, to_double(w), rs[RB_L * 32]);
         }
       } else {
         // ---- pass 1's output: the first F_x sweep's field (or w1 for n_lo = 1) ----
@@ -385,8 +402,8 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
               const int c = gy * mx + gx;
               const T v5m = sv5.d[E - n_lo - 1];
               const double* rs = slot_at(-E, 0);  // still in the ring
-              Xo[c] = fma(alpha, to_double(v5m), rs[R_X * 32]);
-              Lo[c] = fma(alpha, to_double(v4), rs[R_L * 32]);
+              Xo[c] = fma(alpha, to_double(v5m), rs[RB_X * 32]);
+              Lo[c] = fma(alpha, to_double(v4), rs[RB_L * 32]);
             }
           }
         }
@@ -480,8 +497,9 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32, STRIP_MIN_BLOCKS) k_strip(It
   const int half = launch_half(A, j_launch);
   const int rd = (MODE == MODE_SOLVE) ? (k & 1) : 0;
   pdl_wait();  // the previous iteration's state, residuals and control words; this one's v3
-  const int item = blockIdx.x * STRIP_WARPS + warp;
-  if (item >= A.n_strips) return;  // warp-uniform; no block barriers in this kernel
+  const int item = ((A.rb && half) ? A.n_strips_even : 0) + blockIdx.x * STRIP_WARPS + warp;
+  const int item_end = A.rb ? (half ? A.n_strips : A.n_strips_even) : A.n_strips;
+  if (item >= item_end) return;  // warp-uniform; no block barriers in this kernel
   const int4 it = A.strips[item];
   const int b = it.x, s = it.y, x0 = it.z, y0 = it.w;
   if (!stage_in_half(A, s, half)) return;
