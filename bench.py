@@ -6,7 +6,11 @@ horizon closed loop, FP32 lower layer with float64 residual, norms and
 update, every solve to ||K||_inf <= 1e-6.  A step is one step of the loop:
 one solve of each of the 64 instances (64 solves) plus the plant's advance.
 The loop runs as one CUDA graph; K steps are timed from the loop's start
-(first solve from the cold or learned start, later ones warm).
+(first solve from the cold or learned start, later ones warm).  The upper
+layer is the red-black ordering of the block Gauss-Seidel variant (two
+stage-parallel half-sweeps per iteration; Theorem 3: the Jacobi factor
+squared); ``--variant jacobi`` times the stage-parallel Jacobi iteration of
+eq. 15, and the line also carries the plain loop of the other variant.
 
 Two arms in one run, on the same instances:
   plain    the plain method: cold first step, then the shifted previous
@@ -63,6 +67,13 @@ FIT_STEPS = 1500   # Adam steps of the learned start
 # algorithmic bytes per cell-stage per iteration: read x_i, lambda_i and write
 # them back in float64 (the neighbour-stage reads are the same arrays)
 BYTES_PER_POINT_STAGE = 32
+# DRAM bytes over algorithmic bytes of the strip kernel, from ncu captures of
+# the current kernels on 8 instances (dram__bytes_read.sum + write.sum per
+# launch over 32 B x the launch's cell-stages): Jacobi 1.704 GB / 1.678 GB;
+# red-black half 0 1.283 GB and half 1 1.721 GB over 0.839 GB each (the
+# neighbouring stages' x_{i-1}, lambda_{i+1} are not processed in the same
+# launch, so they come from DRAM rather than L2)
+TRAFFIC_RATIO = {"jacobi": 1.704 / 1.678, "redblack": (1.283 + 1.721) / (2 * 0.839)}
 
 
 def parse():
@@ -78,9 +89,12 @@ def parse():
                     help="1: time the C oracle on the host (rank 0) and compare controls")
     ap.add_argument("--secondary", type=int, default=1,
                     help="1: also time the 64x64 single-instance workload")
-    ap.add_argument("--variant", default="jacobi", choices=["jacobi", "redblack"],
-                    help="upper-layer iteration: stage-parallel Jacobi (eq. 15) or the red-black "
-                         "ordering of the Gauss-Seidel variants")
+    ap.add_argument("--variant", default="redblack", choices=["jacobi", "redblack"],
+                    help="upper-layer iteration: the red-black ordering of the block Gauss-Seidel "
+                         "variant (default; Theorem 3: the Jacobi factor squared) or the "
+                         "stage-parallel Jacobi iteration of eq. 15")
+    ap.add_argument("--compare", type=int, default=1,
+                    help="1: also time the plain loop with the other upper-layer variant")
     return ap.parse_args()
 
 
@@ -435,6 +449,26 @@ def main():
     assert rc_l == G.NMPC_OK and float(res_l.max()) <= TOL, (rc_l, float(res_l.max()))
     s.close()
 
+    # ---- the plain loop with the other upper-layer variant (context) ----
+    other = None
+    if args.compare:
+        from paper_2004_02484_gb300 import nmpc as G2
+        o2 = dict(opts)
+        o2["variant"] = (G2.NMPC_VARIANT_JACOBI if args.variant == "redblack"
+                         else G2.NMPC_VARIANT_REDBLACK)
+        s = G.Solver(test, **o2)
+        w = s.x0.clone()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        rc_o, it_o, res_o = G.nmpc_closed_loop(s.h, w, s.ref, K, N_SUB, B)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_o = max_over_ranks(e0.elapsed_time(e1) / 1e3, dev)
+        s.close()
+        other = {"variant": "jacobi" if args.variant == "redblack" else "redblack",
+                 "plain_value": job_rate(world, B * K, t_o), "unit": "solves/s",
+                 "iterations_per_solve_mean": float(np.mean(it_o)), "rc": rc_o}
+
     # ---- end to end through host buffers: every step the measured plant
     # state goes host -> device, one loop step runs, the applied controls and
     # the plant's next state come back ----
@@ -479,8 +513,11 @@ def main():
     alg_bytes = BYTES_PER_POINT_STAGE * cell_stage_iters
     peaks, which = measured_peaks()
     achieved = alg_bytes / (ms_s / 1e3) / 1e9 if ms_s > 0 else None
+    traffic = TRAFFIC_RATIO[args.variant] * alg_bytes / max(1, n_s)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"] if achieved else None, "traffic": None,
+            "frac": achieved / peaks["hbm_gbs"] if achieved else None, "traffic": traffic,
+            "traffic_source": "ncu dram__bytes_read.sum + write.sum of the same kernels on 8 "
+                              "instances, scaled by the cell-stages per launch",
             "peak_source": which, "kernel": "k_strip<float,2> (strip path: residual, lower "
             "layer and update of 26-column strips of 256x256 stages)",
             "algorithmic_bytes_per_launch": alg_bytes / max(1, n_s),
@@ -556,6 +593,7 @@ def main():
                "learned": {"iterations_per_solve_mean": float(np.mean(it_l)),
                            "iterations_first_step_mean": float(np.mean(it_l[0]))},
                "gain_learned_vs_plain": value / plain,
+               "other_variant": other,
                "e2e": {"value": job_rate(world, B * K, e2e_s), "unit": "solves/s",
                        "h2d_bytes_per_step": 8 * B * ng,
                        "d2h_bytes_per_step": 8 * B * ng + 8 * B * nu},
