@@ -318,9 +318,10 @@ def secondary(args, rank, world, dev):
     insts = [wl.heat2d_single(seed=step_seed(s, rank)) for s in range(n_warm + n_steps)]
     # the settings the autotuner picks for this workload (n_lo = 1, n_u_it = 1,
     # clusters of 8 CTAs per stage)
+    # (the Jacobi upper layer: on this latency-bound workload, ~20 us per
+    # launch, red-black's two launches per iteration cost more than its
+    # halved iteration count saves: 2.72 against 2.3 ms per solve)
     o = dict(tol=TOL, precision=G.NMPC_MIXED, max_iter=5000, n_lo=1, n_u_it=1, cluster=8)
-    if args.variant == "redblack":
-        o["variant"] = G.NMPC_VARIANT_REDBLACK
     s = G.Solver([insts[0]], **o)
     x0s = [torch.from_numpy(G.pack_fields([i], "x0")).to(dev) for i in insts]
     refs = [torch.from_numpy(G.pack_fields([i], "ref")).to(dev) for i in insts]

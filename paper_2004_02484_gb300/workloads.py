@@ -241,3 +241,124 @@ def heat2d_learning_instance(seed: int) -> Instance:
     d = uniform01(seed + 77_777_777, 3)
     return heat2d(64, 64, 50, 4, 2, seed=seed, ref_center=(0.3 + 0.4 * d[0], 0.3 + 0.4 * d[1]),
                   ref_amp=0.5 + d[2], name=f"heat2d_learn_{seed}")
+
+
+# ---------------------------------------------------------------------------
+# Pinned-actuator problems: the copper plate of the paper's experiment
+# ---------------------------------------------------------------------------
+@dataclasses.dataclass
+class PlateInstance:
+    """A pinned-actuator instance: the temperatures of the grid points in
+    ``act`` are the inputs (they are not states).  ``x0`` and ``x_ref`` hold
+    the state points (grid order, actuator points left out), ``u_ref`` the
+    actuator points.  Model w_t = Lap(k0 (w + k1 w^2 / 2)) - beta (w - t_amb)
+    - gamma_r (w^4 - t_amb^4); bounds u_lo <= u <= u_hi with barrier weight
+    tau (0: no bounds)."""
+
+    dim: int
+    m: int
+    bc: str
+    horizon: int
+    h: float
+    act: np.ndarray
+    k0: float
+    k1: float
+    beta: float
+    t_amb: float
+    gamma_r: float
+    q: float
+    r: float
+    qf: float
+    gamma: float
+    tau: float
+    u_lo: float
+    u_hi: float
+    x0: np.ndarray
+    x_ref: np.ndarray
+    u_ref: np.ndarray
+    name: str = ""
+
+    @property
+    def ng(self) -> int:
+        return self.m ** self.dim
+
+    @property
+    def ns(self) -> int:
+        return self.ng - len(self.act)
+
+
+# Table 1 of the paper (copper plate) and Table 2 (NMPC settings)
+PLATE_RHO, PLATE_CP, PLATE_TZ, PLATE_K = 8960.0, 386.0, 0.01, 400.0
+PLATE_HC, PLATE_TA, PLATE_EPS, PLATE_SIGMA = 1.0, 300.0, 0.5, 5.67e-8
+
+
+def plate_reference(m: int, shape: str, t_amb: float = PLATE_TA) -> np.ndarray:
+    """Stand-ins for the paper's reference fields (its figure is not
+    available): "slope", t_amb + 50 + 300 x, and "V", t_amb + 50 + 300 |2x - 1|,
+    over the m x m grid points of [0, 1]^2 (x the horizontal axis)."""
+    xs = np.linspace(0.0, 1.0, m)
+    prof = xs if shape == "slope" else np.abs(2.0 * xs - 1.0)
+    field = np.tile(t_amb + 50.0 + 300.0 * prof, (m, 1))
+    return field.reshape(-1)
+
+
+def plate_instance(m: int = 13, horizon: int = 20, T: float = 100.0, shape: str = "slope",
+                   x0_field: Optional[np.ndarray] = None, act_idx=(1, 4, 8, 11),
+                   tau: float = 100.0, gamma: float = 0.5, name: str = "") -> PlateInstance:
+    """The paper's plate: m x m points with zero-Neumann boundaries, actuators
+    at the grid points act_idx x act_idx (16 for the default 13 x 13 grid:
+    169 - 16 = 153 states), inputs in [t_amb, t_amb + 400] K, T = 100 s,
+    N = 20 (h = 5 s), Q = I, R = 0.1 I, tau = 100, gamma = 0.5; the state
+    starts at the ambient temperature unless x0_field (m x m) is given."""
+    rc = PLATE_RHO * PLATE_CP
+    if not all(0 <= a < m for a in act_idx):
+        raise ValueError("actuator indices outside the grid")
+    act = np.asarray([iy * m + ix for iy in act_idx for ix in act_idx], dtype=np.int32)
+    is_act = np.zeros(m * m, dtype=bool)
+    is_act[act] = True
+    full_ref = plate_reference(m, shape)
+    full_x0 = np.full(m * m, PLATE_TA) if x0_field is None else np.asarray(x0_field, float)
+    return PlateInstance(dim=2, m=m, bc="neumann", horizon=horizon, h=T / horizon, act=act,
+                         k0=PLATE_K / rc, k1=0.0, beta=2.0 * PLATE_HC / (rc * PLATE_TZ),
+                         t_amb=PLATE_TA, gamma_r=2.0 * PLATE_EPS * PLATE_SIGMA / (rc * PLATE_TZ),
+                         q=1.0, r=0.1, qf=0.0, gamma=gamma, tau=tau, u_lo=PLATE_TA,
+                         u_hi=PLATE_TA + 400.0, x0=full_x0[~is_act].copy(),
+                         x_ref=full_ref[~is_act].copy(), u_ref=full_ref[is_act].copy(),
+                         name=name or f"plate_{m}x{m}_N{horizon}_{shape}")
+
+
+def plate_batch(n: int, base_seed: int = 9000, m: int = 13, horizon: int = 20) -> List[PlateInstance]:
+    """n plates whose initial temperature fields are t_amb plus a seeded smooth
+    perturbation (16 cosine modes, amplitudes N(0, 10^2) K) and whose
+    reference is the slope or the V field (alternating)."""
+    out = []
+    xs = np.linspace(0.0, 1.0, m)
+    for b in range(n):
+        a = normal(base_seed + b, 16).reshape(4, 4) * 10.0
+        f = np.full((m, m), PLATE_TA)
+        for p_ in range(4):
+            for q_ in range(4):
+                f += a[p_, q_] * np.outer(np.cos(q_ * np.pi * xs), np.cos(p_ * np.pi * xs))
+        out.append(plate_instance(m, horizon, shape="slope" if b % 2 == 0 else "V",
+                                  x0_field=f.reshape(-1), name=f"plate_b{b}"))
+    return out
+
+
+def pinned_heat1d(m: int = 32, horizon: int = 20, h: float = 1e-4, seed: int = 0,
+                  act_pos=(0.25, 0.75), r: float = 0.01,
+                  gamma: Optional[float] = None) -> PlateInstance:
+    """The 1D heat workload (M = 32 interior cells, Dirichlet ring, k(w) =
+    0.1 (1 + 0.5 w), N = 20, h = 1e-4, reference 0.8 sin(pi x), R = 0.01,
+    terminal weight 10) with the other reading of its actuators: the cells
+    nearest x = 0.25 and 0.75 pinned to the inputs (no bounds)."""
+    act = np.asarray([nearest_cell(p_, m) for p_ in act_pos], dtype=np.int32)
+    is_act = np.zeros(m, dtype=bool)
+    is_act[act] = True
+    x0 = uniform01(seed, m)
+    ref = 0.8 * np.sin(np.pi * _coords_1d(m))
+    return PlateInstance(dim=1, m=m, bc="dirichlet", horizon=horizon, h=h, act=act, k0=0.1,
+                         k1=0.5, beta=0.0, t_amb=0.0, gamma_r=0.0, q=1.0, r=r, qf=10.0,
+                         gamma=default_gamma(h, r) if gamma is None else gamma, tau=0.0,
+                         u_lo=-np.inf, u_hi=np.inf, x0=x0[~is_act].copy(),
+                         x_ref=ref[~is_act].copy(), u_ref=np.zeros(len(act)),
+                         name="pinned_heat1d_M32_N20")
