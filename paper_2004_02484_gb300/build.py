@@ -1,8 +1,8 @@
 """Build the sm_103a shared library ``_lib/libnmpc_gb300.so`` with nvcc.
 
-Two translation units (the solver's C ABI with its kernels, and the learned
-warm start's network), compiled in parallel in-tree and linked into one
-library; the outputs are git-ignored.  ``build()`` rebuilds only when a
+Three translation units (the solver's C ABI with its kernels, the learned
+warm start's network, and the pinned-actuator solver of the paper's plate),
+compiled in parallel in-tree and linked into one library; the outputs are git-ignored.  ``build()`` rebuilds only when a
 source is newer than the library.
 """
 from __future__ import annotations
@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libnmpc_gb300.so")
-SOURCES = [os.path.join(HERE, "csrc", "nmpc_capi.cu"), os.path.join(HERE, "csrc", "mlp_capi.cu")]
+SOURCES = [os.path.join(HERE, "csrc", "nmpc_capi.cu"), os.path.join(HERE, "csrc", "mlp_capi.cu"),
+           os.path.join(HERE, "csrc", "plate_capi.cu")]
 # every source and header the library is built from
 DEPS = SOURCES + sorted(glob.glob(os.path.join(HERE, "csrc", "*.cuh")) +
                         glob.glob(os.path.join(ROOT, "include", "*.h")))

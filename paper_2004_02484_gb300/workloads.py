@@ -327,7 +327,8 @@ def plate_instance(m: int = 13, horizon: int = 20, T: float = 100.0, shape: str 
                          name=name or f"plate_{m}x{m}_N{horizon}_{shape}")
 
 
-def plate_batch(n: int, base_seed: int = 9000, m: int = 13, horizon: int = 20) -> List[PlateInstance]:
+def plate_batch(n: int, base_seed: int = 9000, m: int = 13, horizon: int = 20,
+                act_idx=(1, 4, 8, 11)) -> List[PlateInstance]:
     """n plates whose initial temperature fields are t_amb plus a seeded smooth
     perturbation (16 cosine modes, amplitudes N(0, 10^2) K) and whose
     reference is the slope or the V field (alternating)."""
@@ -340,7 +341,7 @@ def plate_batch(n: int, base_seed: int = 9000, m: int = 13, horizon: int = 20) -
             for q_ in range(4):
                 f += a[p_, q_] * np.outer(np.cos(q_ * np.pi * xs), np.cos(p_ * np.pi * xs))
         out.append(plate_instance(m, horizon, shape="slope" if b % 2 == 0 else "V",
-                                  x0_field=f.reshape(-1), name=f"plate_b{b}"))
+                                  x0_field=f.reshape(-1), act_idx=act_idx, name=f"plate_b{b}"))
     return out
 
 

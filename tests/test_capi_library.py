@@ -42,8 +42,10 @@ def test_library_exports_every_declared_symbol(lib_path):
 def test_binding_covers_the_headers(lib_path):
     from paper_2004_02484_gb300 import nmpc as G
     from paper_2004_02484_gb300 import mlp as GM
+    from paper_2004_02484_gb300 import plate as GP
     assert sorted(G.EXPORTED) == _declared("nmpc.h")
     assert sorted(GM.EXPORTED) == _declared("nmpc_mlp.h")
+    assert sorted(GP.EXPORTED) == _declared("nmpc_plate.h")
 
 
 def test_strerror_and_defaults(lib_path):
@@ -89,3 +91,30 @@ def test_path_options_default_to_auto_and_are_validated_on_the_host(lib_path):
         descs, keep = G.make_descs([wl.heat1d_single()])
         h = ctypes.c_void_p()
         assert G.LIB.nmpc_setup(descs, 1, ctypes.byref(o), ctypes.byref(h)) == G.NMPC_ERR_BAD_ARG
+
+
+def test_plate_setup_rejects_bad_descriptors_before_touching_the_device(lib_path):
+    """Pinned-actuator descriptors are validated on the host before any CUDA
+    call: repeated or out-of-grid actuators, empty bounds, oversize grids."""
+    import numpy as np
+    from paper_2004_02484_gb300 import plate as GP
+    from paper_2004_02484_gb300 import workloads as wl
+    base = wl.plate_instance(m=7, horizon=3, T=15.0, act_idx=(1, 4))
+    bad = []
+    b1 = wl.plate_instance(m=7, horizon=3, T=15.0, act_idx=(1, 4))
+    b1.act = np.array([8, 8, 11, 29], dtype=np.int32)       # repeated actuator
+    bad.append((b1, -1))
+    b2 = wl.plate_instance(m=7, horizon=3, T=15.0, act_idx=(1, 4))
+    b2.act = np.array([8, 11, 29, 49], dtype=np.int32)      # outside the 7x7 grid
+    bad.append((b2, -1))
+    b3 = wl.plate_instance(m=7, horizon=3, T=15.0, act_idx=(1, 4))
+    b3.u_lo, b3.u_hi = 700.0, 300.0                          # empty bounds
+    bad.append((b3, -1))
+    b4 = wl.plate_instance(m=33, horizon=3, T=15.0, act_idx=(1, 4))  # 1089 points
+    bad.append((b4, -6))
+    for inst, code in bad:
+        descs, keep = GP.make_descs([inst])
+        h = ctypes.c_void_p()
+        o = GP.default_opts()
+        assert GP.LIB.nmpc_plate_setup(descs, 1, ctypes.byref(o), ctypes.byref(h)) == code
+    assert base.ns == 45
