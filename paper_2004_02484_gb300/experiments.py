@@ -28,6 +28,17 @@ solve:      cold-start solves of the 2D 256x256, N = 100 batch (mixed, to
             the iteration loop is launched from the host in chunks instead of
             one graph (a profiler can then capture single iteration kernels);
             reports iterations, ms per iteration and the launch plans.
+plate:      the paper's own closed loop (Sec. 5.3, Table 2): one 13x13
+            copper plate from the ambient temperature, 200 periods of 5 s,
+            the slope reference up to 500 s and then moving linearly to the V
+            reference within 50 s; each period one solve from the shifted
+            previous solution, stopping at ||K||_inf < --plate-tol (Table 2:
+            1), then the plant one period with the first inputs.  Reports
+            iterations per period, time per iteration (min over --reps runs
+            of each period, the paper's protocol; and device time of 200
+            back-to-back iterations), the input range against the bounds and
+            the tracking error; then cold solves of --n plates to 1e-6
+            (solves/s, iterations).
 Prints one JSON line per experiment.
 """
 from __future__ import annotations
@@ -249,10 +260,88 @@ def gemm_bench(shapes, reps: int, path_list=(0, 1)):
     return {"experiment": "gemm", "results": out, "tc_error": GM.nmpc_gemm_error(True)}
 
 
+def plate(n_batch: int, steps: int, variant: int, tol_loop: float, reps: int, n_sub: int):
+    import torch
+    from . import plate as GP
+    inst = wl.plate_instance()
+    slope = wl.plate_reference(inst.m, "slope")
+    vee = wl.plate_reference(inst.m, "V")
+    is_act = np.zeros(inst.ng, dtype=bool)
+    is_act[inst.act] = True
+    dt = inst.h
+
+    def reference(t):
+        s = min(max((t - 500.0) / 50.0, 0.0), 1.0)
+        full = (1.0 - s) * slope + s * vee
+        return full[~is_act], full[is_act]
+
+    per_step = np.full(steps, np.inf)
+    iters = np.zeros(steps, dtype=np.int64)
+    u_hist = np.zeros((steps, len(inst.act)))
+    err = np.zeros(steps)
+    for rep in range(reps):
+        sol = GP.PlateSolver([inst], tol=tol_loop, variant=variant, max_iter=5000)
+        w = torch.from_numpy(np.asarray(inst.x0, dtype=np.float64)).cuda()
+        for k in range(steps):
+            xr, ur = reference(k * dt)
+            sol.x_ref.copy_(torch.from_numpy(xr))
+            sol.u_ref.copy_(torch.from_numpy(ur))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, st = sol.solve(G.NMPC_INIT_COLD if k == 0 else G.NMPC_INIT_SHIFT, x0=w)
+            t1 = time.perf_counter()
+            per_step[k] = min(per_step[k], t1 - t0)
+            iters[k] = st[0].iters
+            u_hist[k] = sol.u[:len(inst.act)].cpu().numpy()
+            sol.plant_step(w, dt, n_sub)
+            torch.cuda.synchronize()
+            err[k] = float(np.abs(w.cpu().numpy() - xr).max())
+        sol.close()
+    # device time of back-to-back iterations (no convergence polls)
+    sol = GP.PlateSolver([inst], variant=variant)
+    x = torch.from_numpy(np.tile(inst.x0, inst.horizon)).cuda()
+    u = torch.full((inst.horizon * len(inst.act),), 0.5 * (inst.u_lo + inst.u_hi),
+                   dtype=torch.float64, device="cuda")
+    lam = torch.zeros_like(x)
+    sol.iterate(x, u, lam, 20)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    sol.iterate(x, u, lam, 200)
+    e1.record()
+    torch.cuda.synchronize()
+    it_us = 1e3 * e0.elapsed_time(e1) / 200
+    sol.close()
+    out = {"experiment": "plate", "variant": "redblack" if variant else "jacobi",
+           "loop": {"steps": steps, "tol": tol_loop, "n_sub": n_sub,
+                    "iters_mean": float(iters.mean()), "iters_max": int(iters.max()),
+                    "iters_first": int(iters[0]),
+                    "ms_per_iter_min_of_reps": 1e3 * float(per_step.sum() / iters.sum()),
+                    "ms_per_step_mean": 1e3 * float(per_step.mean()),
+                    "u_min": float(u_hist.min()), "u_max": float(u_hist.max()),
+                    "track_err_t500": float(err[min(steps, 100) - 1]),
+                    "track_err_end": float(err[-1])},
+           "us_per_iter_device": it_us}
+    if n_batch:
+        insts = wl.plate_batch(n_batch)
+        sol = GP.PlateSolver(insts, tol=1e-6, variant=variant, max_iter=20000)
+        sol.solve()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, st = sol.solve()
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        its = np.array([s_.iters for s_ in st])
+        sol.close()
+        out["batch"] = {"n": n_batch, "rc": rc, "solves_per_s": n_batch / t, "ms": 1e3 * t,
+                        "iters_mean": float(its.mean()), "iters_max": int(its.max()),
+                        "us_per_iter": 1e6 * t / int(its.max())}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("which", choices=["batch1d", "closedloop", "closedloop_learned", "solve",
-                                      "gemm"])
+                                      "gemm", "plate"])
     ap.add_argument("--shapes", default="4096x4096x4096,256x512x8192,256x6800x512,64x512x8192",
                     help="gemm: MxNxK list")
     ap.add_argument("--paths", default="0,1", help="gemm: 0 tcgen05, 1 mma.sync")
@@ -274,6 +363,7 @@ def main():
     ap.add_argument("--rules", type=int, default=1)
     ap.add_argument("--tune", type=int, default=1)
     ap.add_argument("--lines", type=int, default=0)
+    ap.add_argument("--plate-tol", type=float, default=1.0)
     ap.add_argument("--variant", type=int, default=0,
                     help="upper layer: 0 Jacobi (eq. 15), 1 red-black Gauss-Seidel")
     a = ap.parse_args()
@@ -287,6 +377,9 @@ def main():
         shapes = [tuple(int(v) for v in sh.split("x")) for sh in a.shapes.split(",") if sh]
         paths = tuple(int(v) for v in a.paths.split(","))
         print(json.dumps(gemm_bench(shapes, a.reps, paths)), flush=True)
+    elif a.which == "plate":
+        print(json.dumps(plate(1024 if a.n is None else a.n, a.steps, a.variant, a.plate_tol,
+                               max(a.reps, 1), 10 if a.n_sub == 2 else a.n_sub)), flush=True)
     elif a.which == "batch1d":
         print(json.dumps(batch1d(a.n or 1024, reps=a.reps, tune=a.tune, use_graph=a.graph,
                                  lines=a.lines)), flush=True)

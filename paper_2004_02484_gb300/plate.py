@@ -138,6 +138,10 @@ class PlateSolver:
                "nmpc_plate_get_state")
         return x, u, lam
 
+    def plant_step(self, w, dt: float, n_sub: int, stream=None):
+        _check(LIB.nmpc_plate_plant_step(self.h, _ptr(w), float(dt), int(n_sub), _stream(stream)),
+               "nmpc_plate_plant_step")
+
     def closed_loop(self, w, steps: int, n_sub: int, u_hist=None, stream=None):
         iters = np.zeros((steps, self.n), dtype=np.int32)
         res = np.zeros((steps, self.n), dtype=np.float64)
