@@ -363,3 +363,82 @@ def pinned_heat1d(m: int = 32, horizon: int = 20, h: float = 1e-4, seed: int = 0
                          u_lo=-np.inf, u_hi=np.inf, x0=x0[~is_act].copy(),
                          x_ref=ref[~is_act].copy(), u_ref=np.zeros(len(act)),
                          name="pinned_heat1d_M32_N20")
+
+
+@dataclasses.dataclass
+class WaveInstance:
+    """A second-order-in-time instance: a w_tt + b w_t = c Lap w - kappa w^3
+    + sum_a gain u_a delta_a on a grid of m (dim 1) or m x m (dim 2) points,
+    point forces at the cells ``act``.  ``x0`` holds the initial (W, V) with
+    V = dW/dt (all W first), ``w_ref`` the displacement reference, ``u_ref``
+    the input reference."""
+
+    dim: int
+    m: int
+    bc: str
+    horizon: int
+    h: float
+    act: np.ndarray
+    a: float
+    b: float
+    c: float
+    kappa: float
+    gain: float
+    q: float
+    qv: float
+    r: float
+    qf: float
+    gamma: float
+    x0: np.ndarray
+    w_ref: np.ndarray
+    u_ref: np.ndarray
+    name: str = ""
+
+    @property
+    def ng(self) -> int:
+        return self.m ** self.dim
+
+
+def wave_instance(dim: int = 1, m: int = 64, horizon: int = 20, T: float = 0.06, seed: int = 0,
+                  n_act: int = 2, a: float = 1.0, b: float = 1.0, c: float = 1.0,
+                  kappa: float = 10.0, gain: float = 10.0, r: float = 1e-2, qv: float = 0.1, qf: float = 10.0,
+                  gamma: Optional[float] = None, bc: str = "dirichlet",
+                  name: str = "") -> WaveInstance:
+    """A damped string (dim 1) or membrane (dim 2) with a cubic stiffening
+    term, interior grid, zero Dirichlet ring (``bc="neumann"``: free edges,
+    boundary points included).  Actuators: n_act (1D) or n_act x n_act (2D)
+    point forces at the cells nearest the centres (k + 1/2) / n_act, force
+    ``gain`` per unit input on the cell.  gamma defaults to h r (the ratio of
+    the paper's experiment).  Initial displacement a
+    smooth random field (4 sine modes per axis, std 0.1) at rest; reference a
+    Gaussian bump of height 0.2 and width 0.15 in the middle."""
+    coords = _coords_1d(m) if bc == "dirichlet" else np.linspace(0.0, 1.0, m)
+    near = lambda p_: int(np.argmin(np.abs(coords - p_)))
+    cents = [(k + 0.5) / n_act for k in range(n_act)]
+    if dim == 1:
+        act = np.asarray([near(p_) for p_ in cents], dtype=np.int32)
+        W0 = np.zeros(m)
+        a_ = normal(seed, 4) * 0.1
+        for k in range(4):
+            W0 += a_[k] * np.sin((k + 1) * np.pi * coords)
+        ref = 0.2 * np.exp(-(coords - 0.5) ** 2 / (2 * 0.15 ** 2))
+    else:
+        act = np.asarray([near(py) * m + near(px) for py in cents for px in cents], dtype=np.int32)
+        a_ = normal(seed, 16).reshape(4, 4) * 0.1
+        W0 = np.zeros((m, m))
+        for p_ in range(4):
+            for q_ in range(4):
+                W0 += a_[p_, q_] * np.outer(np.sin((q_ + 1) * np.pi * coords),
+                                            np.sin((p_ + 1) * np.pi * coords))
+        W0 = W0.reshape(-1)
+        d2 = (coords[None, :] - 0.5) ** 2 + (coords[:, None] - 0.5) ** 2
+        ref = (0.2 * np.exp(-d2 / (2 * 0.15 ** 2))).reshape(-1)
+    if len(set(act.tolist())) != len(act):
+        raise ValueError("two actuators on one cell")
+    h = T / horizon
+    return WaveInstance(dim=dim, m=m, bc=bc, horizon=horizon, h=h, act=act, a=a, b=b, c=c,
+                        kappa=kappa, gain=gain, q=1.0, qv=qv, r=r, qf=qf,
+                        gamma=default_gamma(h, r) if gamma is None else gamma,
+                        x0=np.concatenate([W0, np.zeros_like(W0)]), w_ref=ref,
+                        u_ref=np.zeros(len(act)),
+                        name=name or f"wave{dim}d_m{m}_N{horizon}_s{seed}")
