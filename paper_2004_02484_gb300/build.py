@@ -1,8 +1,9 @@
 """Build the sm_103a shared library ``_lib/libnmpc_gb300.so`` with nvcc.
 
-Three translation units (the solver's C ABI with its kernels, the learned
-warm start's network, and the pinned-actuator solver of the paper's plate),
-compiled in parallel in-tree and linked into one library; the outputs are git-ignored.  ``build()`` rebuilds only when a
+Four translation units (the solver's C ABI with its kernels, the learned
+warm start's network, the pinned-actuator solver of the paper's plate and
+the second-order-in-time solver), compiled in parallel in-tree and linked
+into one library; the outputs are git-ignored.  ``build()`` rebuilds only when a
 source is newer than the library.
 """
 from __future__ import annotations
@@ -17,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libnmpc_gb300.so")
 SOURCES = [os.path.join(HERE, "csrc", "nmpc_capi.cu"), os.path.join(HERE, "csrc", "mlp_capi.cu"),
-           os.path.join(HERE, "csrc", "plate_capi.cu")]
+           os.path.join(HERE, "csrc", "plate_capi.cu"), os.path.join(HERE, "csrc", "wave_capi.cu")]
 # every source and header the library is built from
 DEPS = SOURCES + sorted(glob.glob(os.path.join(HERE, "csrc", "*.cuh")) +
                         glob.glob(os.path.join(ROOT, "include", "*.h")))

@@ -43,9 +43,11 @@ def test_binding_covers_the_headers(lib_path):
     from paper_2004_02484_gb300 import nmpc as G
     from paper_2004_02484_gb300 import mlp as GM
     from paper_2004_02484_gb300 import plate as GP
+    from paper_2004_02484_gb300 import wave as GW
     assert sorted(G.EXPORTED) == _declared("nmpc.h")
     assert sorted(GM.EXPORTED) == _declared("nmpc_mlp.h")
     assert sorted(GP.EXPORTED) == _declared("nmpc_plate.h")
+    assert sorted(GW.EXPORTED) == _declared("nmpc_wave.h")
 
 
 def test_strerror_and_defaults(lib_path):
@@ -118,3 +120,32 @@ def test_plate_setup_rejects_bad_descriptors_before_touching_the_device(lib_path
         o = GP.default_opts()
         assert GP.LIB.nmpc_plate_setup(descs, 1, ctypes.byref(o), ctypes.byref(h)) == code
     assert base.ns == 45
+
+
+def test_wave_setup_rejects_bad_descriptors_before_touching_the_device(lib_path):
+    """Second-order descriptors are validated on the host before any CUDA
+    call: a <= 0, repeated or out-of-grid actuators, r <= 0, oversize grids."""
+    import numpy as np
+    from paper_2004_02484_gb300 import wave as GW
+    from paper_2004_02484_gb300 import workloads as wl
+    mk = lambda **kw: wl.wave_instance(dim=1, m=16, horizon=3, **kw)
+    bad = []
+    b = mk()
+    b.a = 0.0
+    bad.append((b, -1))
+    b = mk()
+    b.act = np.array([3, 3], dtype=np.int32)
+    bad.append((b, -1))
+    b = mk()
+    b.act = np.array([3, 16], dtype=np.int32)
+    bad.append((b, -1))
+    bad.append((mk(r=0.0), -1))
+    bad.append((wl.wave_instance(dim=2, m=33, horizon=2), -6))
+    for inst, code in bad:
+        descs, keep = GW.make_descs([inst])
+        h = ctypes.c_void_p()
+        o = GW.default_opts()
+        assert GW.LIB.nmpc_wave_setup(descs, 1, ctypes.byref(o), ctypes.byref(h)) == code
+    o = GW.default_opts(variant=7)
+    descs, keep = GW.make_descs([mk()])
+    assert GW.LIB.nmpc_wave_setup(descs, 1, ctypes.byref(o), ctypes.byref(ctypes.c_void_p())) == -1
