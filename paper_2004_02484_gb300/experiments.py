@@ -39,6 +39,10 @@ plate:      the paper's own closed loop (Sec. 5.3, Table 2): one 13x13
             back-to-back iterations), the input range against the bounds and
             the tracking error; then cold solves of --n plates to 1e-6
             (solves/s, iterations).
+wave:       second-order-in-time batches (damped nonlinear string, 1D
+            m = 64, N = 20; membrane, 2D 32x32, N = 10), cold solves to
+            ||K||_inf <= 1e-6 of --n instances each with seeded initial
+            fields: solves/s, iterations, time per batch iteration.
 Prints one JSON line per experiment.
 """
 from __future__ import annotations
@@ -338,10 +342,37 @@ def plate(n_batch: int, steps: int, variant: int, tol_loop: float, reps: int, n_
     return out
 
 
+def wave(n: int, variant: int, reps: int, dims=(1, 2), single: bool = True):
+    import torch
+    from . import wave as GW
+    out = {"experiment": "wave", "variant": "redblack" if variant else "jacobi", "results": []}
+    cases = {1: dict(dim=1, m=64, horizon=20), 2: dict(dim=2, m=32, horizon=10, n_act=3)}
+    for kw in (cases[d] for d in dims):
+        for nb in ((1, n) if single and n > 1 else (n,)):
+            insts = [wl.wave_instance(seed=s_, **kw) for s_ in range(nb)]
+            sol = GW.WaveSolver(insts, tol=1e-6, variant=variant, max_iter=20000)
+            sol.solve()
+            torch.cuda.synchronize()
+            best = float("inf")
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                rc, st = sol.solve()
+                torch.cuda.synchronize()
+                best = min(best, time.perf_counter() - t0)
+            its = np.array([s_.iters for s_ in st])
+            sol.close()
+            out["results"].append({"workload": f"wave{kw['dim']}d_m{kw['m']}_N{kw['horizon']}",
+                                   "n": nb, "rc": rc, "solves_per_s": nb / best,
+                                   "ms": 1e3 * best, "iters_mean": float(its.mean()),
+                                   "iters_max": int(its.max()),
+                                   "us_per_iter": 1e6 * best / int(its.max())})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("which", choices=["batch1d", "closedloop", "closedloop_learned", "solve",
-                                      "gemm", "plate"])
+                                      "gemm", "plate", "wave"])
     ap.add_argument("--shapes", default="4096x4096x4096,256x512x8192,256x6800x512,64x512x8192",
                     help="gemm: MxNxK list")
     ap.add_argument("--paths", default="0,1", help="gemm: 0 tcgen05, 1 mma.sync")
@@ -364,6 +395,8 @@ def main():
     ap.add_argument("--tune", type=int, default=1)
     ap.add_argument("--lines", type=int, default=0)
     ap.add_argument("--plate-tol", type=float, default=1.0)
+    ap.add_argument("--wave-dims", default="1,2", help="wave: 1 string, 2 membrane")
+    ap.add_argument("--wave-single", type=int, default=1, help="wave: also time one instance")
     ap.add_argument("--variant", type=int, default=0,
                     help="upper layer: 0 Jacobi (eq. 15), 1 red-black Gauss-Seidel")
     a = ap.parse_args()
@@ -377,6 +410,10 @@ def main():
         shapes = [tuple(int(v) for v in sh.split("x")) for sh in a.shapes.split(",") if sh]
         paths = tuple(int(v) for v in a.paths.split(","))
         print(json.dumps(gemm_bench(shapes, a.reps, paths)), flush=True)
+    elif a.which == "wave":
+        print(json.dumps(wave(256 if a.n is None else a.n, a.variant, max(a.reps, 1),
+                              tuple(int(v) for v in a.wave_dims.split(",")), a.wave_single != 0)),
+              flush=True)
     elif a.which == "plate":
         print(json.dumps(plate(1024 if a.n is None else a.n, a.steps, a.variant, a.plate_tol,
                                max(a.reps, 1), 10 if a.n_sub == 2 else a.n_sub)), flush=True)
