@@ -368,17 +368,18 @@ __device__ __forceinline__ double dmax_nan(double a, double b) {
 
 // float64 <-> float32 by IEEE-754 bit manipulation on the integer ALUs (the
 // float64 pipe issues 2 lanes per clock per SM on this part).  d2f truncates
-// toward zero (relative error < 2^-23); zero/subnormal doubles become +-0 and
-// out-of-range or NaN doubles become +-Inf.  f2d is exact for normal floats;
-// subnormal floats become +-0.
+// toward zero (relative error < 2^-23) for magnitudes in [2^-126, 2^128);
+// the magnitude's high word is clamped to that range first (two min/max
+// instructions instead of two compare/select pairs), so +-0 stays +-0,
+// smaller magnitudes become floats below 2^-146 (of the right sign), and
+// 2^128 and beyond, Inf and NaN become Inf or NaN (never a finite value).
+// f2d is exact for normal floats; subnormal floats become +-0.
 __device__ __forceinline__ float d2f(double d) {
   const unsigned hi = (unsigned)__double2hiint(d);
   const unsigned lo = (unsigned)__double2loint(d);
-  const unsigned a = hi & 0x7fffffffu;
+  const unsigned a = min(hi & 0x7fffffffu, 0x47f00000u);
   // exponent rebiased (1023 -> 127) and the top 23 mantissa bits, in one funnel shift
-  unsigned bits = __funnelshift_l(lo, a - 0x38000000u, 3);
-  bits = (a < 0x38100000u) ? 0u : bits;           // below the float32 normal range
-  bits = (a >= 0x47f00000u) ? 0x7f800000u : bits;  // beyond it, Inf or NaN
+  const unsigned bits = __funnelshift_l(lo, max(a, 0x38000000u) - 0x38000000u, 3);
   return __uint_as_float(bits | (hi & 0x80000000u));
 }
 
