@@ -168,6 +168,11 @@ typedef struct {
                       and solves from S^0 with one launch per iteration (the
                       handle keeps that mode).  A tiny budget exercises this
                       path                                                  */
+  int strip_cols;   /* grid columns per lane on the strip path: 0 = auto (two
+                      where NMPC_MIXED, n_lo <= 2 and every strip instance
+                      has an even grid width and even array offsets: 64-column
+                      regions with 64 - 4 n_lo own columns, packed float32
+                      pairs; else one), 1 = one (32-column regions)         */
 } nmpc_opts;
 
 typedef struct {
@@ -182,7 +187,8 @@ typedef struct nmpc_handle nmpc_handle;
 /* Fill *o with defaults: tol 1e-6, max_iter 2000, n_lo 2, n_u_it 2, FP64,
    check_every 16, alpha 1, div_limit 1e8, threads auto, graph on, cluster
    auto, split_min 1e-7, u_local 0, cells auto, persistent 0, strips auto,
-   strip_rows auto, lines auto, variant Jacobi, barrier_wait_cycles 0. */
+   strip_rows auto, lines auto, variant Jacobi, barrier_wait_cycles 0,
+   strip_cols auto. */
 void nmpc_default_opts(nmpc_opts* o);
 
 /* Validate the descriptors, build the device instance table and allocate the
@@ -222,7 +228,10 @@ int nmpc_solve_host(nmpc_handle* h, const double* x0, const double* ref, int hor
 
 /* Float64 KKT residual (eq. 9, u~ = u) of the state (x, u, lam) (packed,
    device) for initial states x0 and references ref (device).  out: host
-   [n_instances][2] = (||K_b||_inf, ||K_b||_2).  Synchronizes on stream. */
+   [n_instances][2] = (||K_b||_inf, ||K_b||_2).  Synchronizes on stream.
+   When the handle runs its strip path with two columns per lane
+   (nmpc_opts.strip_cols), x and lam must be 16-byte aligned (BAD_ARG
+   otherwise); the same holds for nmpc_iterate's x and lam arrays. */
 int nmpc_residual(nmpc_handle* h, const double* x0, const double* ref, const double* x,
                   const double* u, const double* lam, double* out, void* stream);
 

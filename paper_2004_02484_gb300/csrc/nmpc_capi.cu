@@ -10,6 +10,7 @@
 #include <cstring>
 #include <new>
 #include <type_traits>
+#include <cstdint>
 #include <vector>
 
 #include "../../include/nmpc.h"
@@ -99,6 +100,7 @@ struct nmpc_handle {
   int n_strips = 0;
   int strip_x = 0, strip_y = 0, strip_threads = 0, strip_region = 0;
   int n_strip_inst = 0;
+  bool strip2 = false;  // two grid columns per lane (k_strip2)
   size_t strip_smem = 0;
   int4* patches_d = nullptr;  // k_patch work items
   int n_patches = 0;
@@ -530,7 +532,11 @@ LaunchPlan plan_of(const nmpc_handle* h) {
 using TileKernel = void (*)(IterArgs, int, int);
 
 template <typename T>
-TileKernel strip_kernel(int n_lo, bool rbn = false) {
+TileKernel strip_kernel(int n_lo, bool rbn = false, bool two = false) {
+  if (two) {  // float32 lower layer, n_lo <= 2 (checked at setup)
+    if (n_lo <= 1) return rbn ? nmpc_dev::k_strip2<1, true> : nmpc_dev::k_strip2<1, false>;
+    return rbn ? nmpc_dev::k_strip2<2, true> : nmpc_dev::k_strip2<2, false>;
+  }
   if (rbn) {
     switch (n_lo) {
       case 1: return nmpc_dev::k_strip<T, 1, true>;
@@ -592,7 +598,8 @@ cudaError_t launch_strip(const nmpc_handle* h, const IterArgs& A, cudaStream_t s
   const int count = half_count(A, j, h->n_strips, h->n_strips_even);
   if (count == 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)((count + nmpc_dev::STRIP_WARPS - 1) / nmpc_dev::STRIP_WARPS));
+  const int warps = h->strip2 ? nmpc_dev::STRIP2_WARPS : nmpc_dev::STRIP_WARPS;
+  cfg.gridDim = dim3((unsigned)((count + warps - 1) / warps));
   cfg.blockDim = dim3((unsigned)h->strip_threads);
   cfg.dynamicSmemBytes = rb_half1(A, j) ? h->strip_smem_rb : h->strip_smem;
   cfg.stream = st;
@@ -601,7 +608,8 @@ cudaError_t launch_strip(const nmpc_handle* h, const IterArgs& A, cudaStream_t s
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = (mode == nmpc_dev::MODE_SOLVE) ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, strip_kernel<T>(h->opts.n_lo, rb_half1(A, j)), A, mode, j);
+  return cudaLaunchKernelEx(&cfg, strip_kernel<T>(h->opts.n_lo, rb_half1(A, j), h->strip2), A,
+                            mode, j);
 }
 
 cudaError_t launch_line(const nmpc_handle* h, const IterArgs& A, cudaStream_t st, int mode, int j) {
@@ -762,6 +770,13 @@ cudaError_t configure_kernels(size_t smem) {
     e = cudaFuncSetAttribute(patch_kernel<T>(n_lo), cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
+    if (std::is_same<T, float>::value && n_lo <= 2) {
+      for (int rbn = 0; rbn < 2; ++rbn) {
+        e = cudaFuncSetAttribute(strip_kernel<T>(n_lo, rbn != 0, true),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+      }
+    }
   }
   cudaError_t e = cudaFuncSetAttribute(nmpc_dev::k_line<false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -825,7 +840,7 @@ bool opts_ok(const nmpc_opts& o) {
          (o.cells >= 0 && o.cells <= 8) && (o.strips >= 0 && o.strips <= 2) && (o.lines >= 0 && o.lines <= 2) &&
          (o.strip_rows >= 0 && o.strip_rows <= 65535) &&
          (o.variant == NMPC_VARIANT_JACOBI || (o.variant == NMPC_VARIANT_REDBLACK && o.alpha == 1.0)) &&
-         o.barrier_wait_cycles >= 0;
+         o.barrier_wait_cycles >= 0 && (o.strip_cols == 0 || o.strip_cols == 1);
 }
 
 int validate(const nmpc_desc* d) {
@@ -1311,6 +1326,7 @@ void nmpc_default_opts(nmpc_opts* o) {
   o->strips = 0;
   o->strip_rows = 0;
   o->lines = 0;
+  o->strip_cols = 0;
 }
 
 int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
@@ -1385,31 +1401,38 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
     return NMPC_ERR_CUDA;
   }
   // instances on the strip path, and the strip shape (shared by all of
-  // them): 32 - 2E own columns (one warp lane per region column) and ty own
-  // rows, by default enough strips for about four waves of warps
+  // them): 32 - 2E own columns (one warp lane per region column), or with
+  // two columns per lane 64 - 2P (P = 2 n_lo, k_strip2), and ty own rows, by
+  // default enough strips for about four waves of warps
   std::vector<char> on_strips(n_instances, 0);
   const int E = 2 * o.n_lo - 1;
-  const int tx = 32 - 2 * E;
-  int ty = 0;
+  int ty = 0, my_max = 0;
+  bool two = h->mixed && o.n_lo <= 2 && o.strip_cols == 0;
   if (o.strips != 2) {
-    int my_max = 0;
-    long long whole = 0;  // strips with whole columns
     for (int b = 0; b < n_instances; ++b) {
       const InstDev& I = h->inst_h[b];
       if (!strip_eligible(I, act_all.data() + I.act_off, o)) continue;
       if (o.strips == 0 && fits_cluster_staged(I, o, h->mixed, max_optin)) continue;
       on_strips[b] = 1;
       my_max = std::max(my_max, I.my);
-      whole += (long long)I.N * ((I.mx + tx - 1) / tx);
+      // column pairs are 16-byte aligned: even width and even array offsets
+      if ((I.mx & 1) || (I.s_off & 1) || (I.g_off & 1)) two = false;
     }
-    if (my_max > 0) {
-      if (o.strip_rows) {
-        ty = std::min(o.strip_rows, my_max);
-      } else {
-        const long long target = 4LL * std::max(1, h->num_sms) * 32;
-        const long long segs = std::max(1LL, (target + whole - 1) / whole);
-        ty = (int)std::min<long long>(my_max, std::max(16LL, (my_max + segs - 1) / segs));
+  }
+  const int tx = two ? 64 - 2 * nmpc_dev::strip2_pad(o.n_lo) : 32 - 2 * E;
+  if (my_max > 0) {
+    long long whole = 0;  // strips with whole columns
+    for (int b = 0; b < n_instances; ++b)
+      if (on_strips[b]) {
+        const InstDev& I = h->inst_h[b];
+        whole += (long long)I.N * ((I.mx + tx - 1) / tx);
       }
+    if (o.strip_rows) {
+      ty = std::min(o.strip_rows, my_max);
+    } else {
+      const long long target = 4LL * std::max(1, h->num_sms) * 32;
+      const long long segs = std::max(1LL, (target + whole - 1) / whole);
+      ty = (int)std::min<long long>(my_max, std::max(16LL, (my_max + segs - 1) / segs));
     }
   }
   std::vector<int2> work;
@@ -1461,7 +1484,22 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
   // one warp per item of the whole list (solve-mode launches past the running
   // items' count return at once)
   h->line_grid = (h->n_lines + nmpc_dev::LINE_WARPS - 1) / nmpc_dev::LINE_WARPS;
-  if (h->n_strips > 0) {
+  if (h->n_strips > 0 && two) {
+    h->strip2 = true;
+    h->strip_x = tx;
+    h->strip_y = ty;
+    h->strip_threads = 32 * nmpc_dev::STRIP2_WARPS;
+    h->strip_region = 64 * (ty + 2 * E);
+    constexpr int NF1 = nmpc_dev::strip_fields(true);
+    const size_t ws_bytes =
+        o.n_lo <= 1 ? sizeof(nmpc_dev::StripShared2<nmpc_dev::strip_ring_rows(1)>)
+                    : sizeof(nmpc_dev::StripShared2<nmpc_dev::strip_ring_rows(2)>);
+    const size_t ws_rb =
+        o.n_lo <= 1 ? sizeof(nmpc_dev::StripShared2<nmpc_dev::strip_ring_rows(1), NF1>)
+                    : sizeof(nmpc_dev::StripShared2<nmpc_dev::strip_ring_rows(2), NF1>);
+    h->strip_smem = nmpc_dev::STRIP2_WARPS * ((ws_bytes + 15) & ~size_t(15));
+    h->strip_smem_rb = nmpc_dev::STRIP2_WARPS * ((ws_rb + 15) & ~size_t(15));
+  } else if (h->n_strips > 0) {
     h->strip_x = tx;
     h->strip_y = ty;
     h->strip_threads = 32 * nmpc_dev::STRIP_WARPS;
@@ -1479,6 +1517,9 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
         : o.n_lo == 3 ? sizeof(nmpc_dev::StripShared<nmpc_dev::strip_ring_rows(3), NF1>)
                       : sizeof(nmpc_dev::StripShared<nmpc_dev::strip_ring_rows(4), NF1>);
     h->strip_smem_rb = nmpc_dev::STRIP_WARPS * ((ws_rb + 15) & ~size_t(15));
+  }
+  if (h->n_strips > 0) {
+    // k_patch (both strip kernels): one region of radius E per warp
     const size_t P2 = (size_t)(2 * E + 1) * (2 * E + 1);
     h->patch_smem = PATCH_WARPS * (((sizeof(nmpc_dev::PatchShared) + 15) & ~size_t(15)) +
                                    8 * P2 * sizeof(double));
@@ -1616,6 +1657,12 @@ int nmpc_solve_host(nmpc_handle* h, const double* x0, const double* ref, int hor
 static int oneshot(nmpc_handle* h, const double* xi, const double* ui, const double* li,
                    double* xo, double* uo, double* lo, int resid_only, double* out_res,
                    cudaStream_t st) {
+  if (h->strip2) {
+    // k_strip2 moves x, lambda as 16-byte column pairs
+    auto misaligned = [](const void* p) { return ((uintptr_t)p & 15u) != 0; };
+    if (misaligned(xi) || misaligned(li) || misaligned(xo) || misaligned(lo))
+      return NMPC_ERR_BAD_ARG;
+  }
   IterArgs A = make_args(h);
   A.xin[0] = xi;
   A.uin[0] = ui;

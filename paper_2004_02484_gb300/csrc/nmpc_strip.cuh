@@ -527,3 +527,4 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32, STRIP_MIN_BLOCKS) k_strip(It
   else
     strip_body<T, n_lo, false, RBN>(A, ws, lane, b, s, k, rd, x0, y0, resid_only);
 }
+#include "nmpc_strip2.cuh"

@@ -386,6 +386,8 @@ def main():
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--strips", type=int, default=0)
     ap.add_argument("--strip-rows", type=int, default=0)
+    ap.add_argument("--strip-cols", type=int, default=0,
+                    help="strip path: 0 auto (two columns per lane where eligible), 1 one")
     ap.add_argument("--n-train", type=int, default=64)
     ap.add_argument("--train-steps", type=int, default=12)
     ap.add_argument("--fit-steps", type=int, default=2000)
@@ -422,7 +424,8 @@ def main():
                                  lines=a.lines)), flush=True)
     elif a.which == "solve":
         print(json.dumps(solve(a.n or 8, a.grid, a.horizon, a.reps, a.graph, strips=a.strips,
-                               strip_rows=a.strip_rows, variant=a.variant)), flush=True)
+                               strip_rows=a.strip_rows, variant=a.variant,
+                               strip_cols=a.strip_cols)), flush=True)
     elif a.which == "closedloop_learned":
         print(json.dumps(closedloop_learned(a.n_train, a.train_steps, a.n or 8, a.steps, a.grid,
                                             a.horizon, a.n_sub, a.fit_steps, a.rules)), flush=True)

@@ -55,7 +55,7 @@ class nmpc_opts(ctypes.Structure):
                 ("cells", ctypes.c_int), ("persistent", ctypes.c_int),
                 ("strips", ctypes.c_int), ("strip_rows", ctypes.c_int),
                 ("lines", ctypes.c_int), ("variant", ctypes.c_int),
-                ("barrier_wait_cycles", ctypes.c_int64)]
+                ("barrier_wait_cycles", ctypes.c_int64), ("strip_cols", ctypes.c_int)]
 
 
 class nmpc_stats(ctypes.Structure):

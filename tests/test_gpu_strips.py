@@ -2,7 +2,9 @@
 
 The strip kernel computes each strip of 32 - 2E own columns from a region
 extended by E = 2 n_lo - 1 cells (one warp walking down the rows with every
-pass pipelined), and k_patch the actuators' controls v3 from patches around
+pass pipelined; in mixed precision with n_lo <= 2 and even grid widths two
+columns per lane: 64 - 4 n_lo own columns of a 64-column region, packed
+float32 pairs), and k_patch the actuators' controls v3 from patches around
 them, so the path evaluates the same formulas as the oracle in a different
 order: FP64 iterates agree to a few ulps of the largest term (relative
 1e-10), the mixed path's update Delta s to float32 accuracy (relative 1e-4 of
@@ -136,16 +138,8 @@ def test_strip_actuators_close_together_with_one_u_iteration(G):
                 assert err <= 1e-10, (n_u_it, b, err)
 
 
-@pytest.mark.parametrize("strip_rows", [3, 8, 16])
-def test_strip_iterate_mixed_matches_oracle(G, strip_rows):
-    """Float32 lower layer with the split residual: the update Delta s agrees
-    with the oracle's to 1e-4 of its size, the split residual norm to 1e-5."""
-    insts = _batch(far=True)
-    state, lists = _rand_state(insts, 96)
-    gpu, res, plan = _iterate(G, insts, state, 1, precision=G.NMPC_MIXED, strips=1,
-                              strip_rows=strip_rows)
-    assert plan["instances"] == 2
-    ora, norms = _oracle(insts, lists, 1)
+def _check_mixed_update(G, insts, state, lists, gpu, res, n_lo=2):
+    ora, norms = _oracle(insts, lists, 1, n_lo=n_lo)
     gx, gu, gl = _split(G, insts, *gpu)
     for b in range(len(insts)):
         X, U, L = ora[b]
@@ -155,6 +149,74 @@ def test_strip_iterate_mixed_matches_oracle(G, strip_rows):
             err = np.abs((g - i) - d_or).max() / max(np.abs(d_or).max(), 1e-300)
             assert err <= 1e-4, (b, err)
         assert abs(res[b, 0] - norms[b][0]) <= 1e-5 * norms[b][0]
+
+
+@pytest.mark.parametrize("strip_cols,strip_x", [(0, 56), (1, 26)])
+@pytest.mark.parametrize("strip_rows", [3, 8, 16])
+def test_strip_iterate_mixed_matches_oracle(G, strip_rows, strip_cols, strip_x):
+    """Float32 lower layer with the split residual, two columns per lane
+    (strips of 56 own columns) or one (26): the update Delta s agrees with
+    the oracle's to 1e-4 of its size, the split residual norm to 1e-5."""
+    insts = _batch(far=True)
+    state, lists = _rand_state(insts, 96)
+    gpu, res, plan = _iterate(G, insts, state, 1, precision=G.NMPC_MIXED, strips=1,
+                              strip_rows=strip_rows, strip_cols=strip_cols)
+    assert plan["instances"] == 2 and plan["strip_x"] == strip_x
+    _check_mixed_update(G, insts, state, lists, gpu, res)
+
+
+@pytest.mark.parametrize("n_lo,strip_x", [(1, 60), (2, 56)])
+def test_two_column_strips_over_several_iterations_and_inner_counts(G, n_lo, strip_x):
+    """Two columns per lane for n_lo = 1 and 2, actuators on even and odd
+    columns of a lane, three iterations against the oracle (mixed: 1e-4 of
+    the iterate's change)."""
+    insts = _batch(far=True)
+    state, lists = _rand_state(insts, 98)
+    gpu, res, plan = _iterate(G, insts, state, 3, precision=G.NMPC_MIXED, strips=1,
+                              strip_rows=8, n_lo=n_lo, n_u_it=1)
+    assert plan["strip_x"] == strip_x
+    ora, norms = _oracle(insts, lists, 3, n_lo=n_lo, n_u_it=1)
+    gx, gu, gl = _split(G, insts, *gpu)
+    for b in range(len(insts)):
+        X, U, L = ora[b]
+        for g, o, i in ((gx[b], X, lists[0][b]), (gl[b], L, lists[2][b]), (gu[b], U, lists[1][b])):
+            i = i.reshape(o.shape)
+            d_or = o - i
+            assert np.abs((g - i) - d_or).max() <= 1e-4 * np.abs(d_or).max(), b
+
+
+def test_odd_grid_width_keeps_one_column_per_lane(G):
+    """A strip instance of odd width (or odd array offsets) cannot move 16-byte
+    column pairs: the handle falls back to one column per lane, with the same
+    parity."""
+    insts = _batch(far=True)
+    odd = _with_act(wl.heat2d(31, 18, 3, 2, 2, seed=95), [(4, 4), (9, 30), (17, 15), (0, 17)])
+    insts = [insts[0], odd, insts[2]]
+    state, lists = _rand_state(insts, 99)
+    gpu, res, plan = _iterate(G, insts, state, 1, precision=G.NMPC_MIXED, strips=1, strip_rows=8)
+    assert plan["strip_x"] == 26
+    _check_mixed_update(G, insts, state, lists, gpu, res)
+
+
+def test_two_column_strips_reject_misaligned_state_pointers(G):
+    """x and lam must be 16-byte aligned for the two-column strips: a pointer
+    one double into a buffer is rejected on the host (nothing launched)."""
+    import ctypes
+    import torch
+    insts = _batch(far=True)
+    h = G.nmpc_setup(insts, precision=G.NMPC_MIXED, strips=1, strip_rows=8)
+    assert G.nmpc_strip_plan(h)["strip_x"] == 56
+    x0 = _t(G.pack_fields(insts, "x0"))
+    ref = _t(G.pack_fields(insts, "ref"))
+    (xs, us, ls), _ = _rand_state(insts, 100)
+    xb = _t(np.concatenate([[0.0], xs]))
+    u, lam = _t(us), _t(ls)
+    out = np.zeros((len(insts), 2))
+    rc = G.LIB.nmpc_residual(h, x0.data_ptr(), ref.data_ptr(), xb.data_ptr() + 8, u.data_ptr(),
+                             lam.data_ptr(), out.ctypes.data, ctypes.c_void_p(0))
+    torch.cuda.synchronize()
+    G.nmpc_destroy(h)
+    assert rc == G.NMPC_ERR_BAD_ARG
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -205,16 +267,17 @@ def test_strip_residual_entry_point_matches_oracle(G):
 
 
 def test_auto_routes_large_stages_to_strips(G):
-    """strips = 0: a 256x256 stage goes to the strip path, a 64x64 stage stays
-    on the cluster path and the 1D instance goes to the line path."""
+    """strips = 0: a 256x256 stage goes to the strip path (two columns per
+    lane: 56 own columns), a 64x64 stage stays on the cluster path and the 1D
+    instance goes to the line path."""
     insts = [wl.heat2d(256, 256, 2, 4, 4, seed=98), wl.heat2d(64, 64, 2, 4, 2, seed=99),
              wl.heat1d(50, 3, 1, 0.01, seed=100)]
     h = G.nmpc_setup(insts, precision=G.NMPC_MIXED)
     plan, lp, ln = G.nmpc_strip_plan(h), G.nmpc_launch_plan(h), G.nmpc_line_plan(h)
     G.nmpc_destroy(h)
     ty = plan["strip_y"]
-    assert plan["instances"] == 1 and plan["strip_x"] == 26 and 16 <= ty <= 256
-    assert plan["strips"] == 2 * -(-256 // 26) * -(-256 // ty)
+    assert plan["instances"] == 1 and plan["strip_x"] == 56 and 16 <= ty <= 256
+    assert plan["strips"] == 2 * -(-256 // 56) * -(-256 // ty)
     assert lp["work_items"] == 2 and ln["instances"] == 1 and ln["lines"] == 3
 
 
