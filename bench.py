@@ -67,13 +67,13 @@ FIT_STEPS = 1500   # Adam steps of the learned start
 # algorithmic bytes per cell-stage per iteration: read x_i, lambda_i and write
 # them back in float64 (the neighbour-stage reads are the same arrays)
 BYTES_PER_POINT_STAGE = 32
-# DRAM bytes over algorithmic bytes of the strip kernel, from ncu captures of
-# the current kernels on 8 instances (dram__bytes_read.sum + write.sum per
-# launch over 32 B x the launch's cell-stages): Jacobi 1.704 GB / 1.678 GB;
-# red-black half 0 1.283 GB and half 1 1.721 GB over 0.839 GB each (the
+# DRAM bytes over algorithmic bytes of the strip kernel (two columns per
+# lane), from ncu captures on 8 instances (dram__bytes_read.sum + write.sum
+# per launch over 32 B x the launch's cell-stages): Jacobi 1.741 GB / 1.678
+# GB; red-black half 0 1.321 GB and half 1 1.776 GB over 0.839 GB each (the
 # neighbouring stages' x_{i-1}, lambda_{i+1} are not processed in the same
 # launch, so they come from DRAM rather than L2)
-TRAFFIC_RATIO = {"jacobi": 1.704 / 1.678, "redblack": (1.283 + 1.721) / (2 * 0.839)}
+TRAFFIC_RATIO = {"jacobi": 1.741 / 1.678, "redblack": (1.321 + 1.776) / (2 * 0.839)}
 
 
 def parse():
@@ -519,8 +519,12 @@ def main():
             "frac": achieved / peaks["hbm_gbs"] if achieved else None, "traffic": traffic,
             "traffic_source": "ncu dram__bytes_read.sum + write.sum of the same kernels on 8 "
                               "instances, scaled by the cell-stages per launch",
-            "peak_source": which, "kernel": "k_strip<float,2> (strip path: residual, lower "
-            "layer and update of 26-column strips of 256x256 stages)",
+            "peak_source": which,
+            "kernel": (f"k_strip2<2> (strip path, two columns per lane: residual, lower layer "
+                       f"and update of {plan['strip_x']}-column strips of 256x256 stages)"
+                       if plan["strip_x"] > 32 else
+                       f"k_strip<float,2> (strip path: residual, lower layer and update of "
+                       f"{plan['strip_x']}-column strips of 256x256 stages)"),
             "algorithmic_bytes_per_launch": alg_bytes / max(1, n_s),
             "avg_launch_ms": ms_s / max(1, n_s), "timed_launches": n_s,
             "kernel_share_of_step": {k: v[1] / (1e3 * t_kt) for k, v in kt.items() if v[0]},
