@@ -29,9 +29,9 @@
  * Arrays, packed per instance in setup order, float64, device pointers:
  *   x0 [sum 2 n_g] (W0 then V0); w_ref [sum n_g]; u_ref [sum n_u];
  *   x, lam [sum N 2 n_g] stage-major, (W, V) per stage; u [sum N n_u].
- * All arithmetic is float64.  The caller owns its buffers; the handle owns
- * its workspace (allocated in setup, freed in destroy); solves allocate
- * nothing.  Return codes are the NMPC_* codes of nmpc.h.
+ * Arithmetic: float64, or with NMPC_MIXED a float32 lower layer.  The
+ * caller owns its buffers; the handle owns its workspace (allocated in
+ * setup, freed in destroy); solves allocate nothing.  Return codes are the NMPC_* codes of nmpc.h.
  */
 #ifndef NMPC_GB300_WAVE_H
 #define NMPC_GB300_WAVE_H
@@ -68,11 +68,16 @@ typedef struct {
   int n_u_it;       /* u fixed-point iterations (Sec. 5.2: 2)                */
   int variant;      /* NMPC_VARIANT_JACOBI or NMPC_VARIANT_REDBLACK           */
   int check_every;  /* iterations between host polls of the running count    */
+  int precision;    /* NMPC_FP64 (default), or NMPC_MIXED: the lower layer's
+                       sweeps and u-iteration in float32 against the float64
+                       residual, coefficients and update (the root is the
+                       float64 root)                                         */
 } nmpc_wave_opts;
 
 typedef struct nmpc_wave nmpc_wave;
 
-/* Defaults: tol 1e-6, max_iter 5000, n_lo 2, n_u_it 2, Jacobi, check_every 16. */
+/* Defaults: tol 1e-6, max_iter 5000, n_lo 2, n_u_it 2, Jacobi, check_every 16,
+   NMPC_FP64. */
 void nmpc_wave_default_opts(nmpc_wave_opts* o);
 
 /* Validate the descriptors (BAD_ARG: dims, a <= 0, negative weights, r <= 0,

@@ -55,11 +55,22 @@ struct PArgs {
   const int* Ltc;       // the same for L^T
   const double* Ltv;
   const double* Ld;     // [sum ng] L[p][p]
+  const float* Lvf;     // float32 copies of Lv, Ltv, Ld (mixed precision)
+  const float* Ltvf;
+  const float* Ldf;
   const double* x0;
   const double* xref;
   const double* uref;
   int n_lo, n_u_it, rb, half;
 };
+
+// The stencil tables in the lower layer's type T.
+template <typename T>
+__device__ __forceinline__ const T* tab(const double* d, const float* f);
+template <>
+__device__ __forceinline__ const double* tab<double>(const double* d, const float*) { return d; }
+template <>
+__device__ __forceinline__ const float* tab<float>(const double*, const float* f) { return f; }
 
 __device__ __forceinline__ double phi(const PInst& I, double w) {
   return I.k0 * (w + 0.5 * I.k1 * w * w);
@@ -72,40 +83,48 @@ __device__ __forceinline__ double dphi(const PInst& I, double w) {
 // F_x v5 = b4, then F_x^T v4 = b5 - A_xx v5, n_lo pointwise Jacobi sweeps
 // each from zero (Lemma 1).  F_x = h (L diag(Phi'(w)) - diag(beta + 4 gr x^3))
 // - I on the state points; its off-diagonal part sums L[p][q] Phi'(w_q) v_q
-// over the state neighbours q (v is zero at the actuator points).
+// over the state neighbours q (v is zero at the actuator points).  The
+// lower layer runs in T (float64, or float32 in mixed precision: the
+// residual, the coefficients and the update stay float64, so the fixed
+// point is the float64 root); the grid values and costates stay float64.
+template <typename T>
 struct Fields {
-  double *W, *LB, *PH, *DP, *LTL, *DG, *AX, *V, *V2, *B4, *B5, *K1, *K3, *Y4, *Y5, *Z;
+  double *W, *LB, *PH, *LTL;
+  T *DP, *DG, *AX, *V, *V2, *B4, *B5, *K1, *K3, *Y4, *Y5, *Z;
 };
+constexpr int F64_FIELDS = 4, T_FIELDS = 12;  // shared memory: n_g values each
 
-__device__ void p_inv(const PArgs& A, const PInst& I, const Fields& f, const int* pts) {
+template <typename T>
+__device__ void p_inv(const PArgs& A, const PInst& I, const Fields<T>& f, const int* pts) {
   const int ng = I.ng;
   const int* Lc = A.Lc + I.t_off * ELL;
-  const double* Lv = A.Lv + I.t_off * ELL;
+  const T* Lv = tab<T>(A.Lv, A.Lvf) + I.t_off * ELL;
   const int* Ltc = A.Ltc + I.t_off * ELL;
-  const double* Ltv = A.Ltv + I.t_off * ELL;
-  const double* Ld = A.Ld + I.t_off;
+  const T* Ltv = tab<T>(A.Ltv, A.Ltvf) + I.t_off * ELL;
+  const T* Ld = tab<T>(A.Ld, A.Ldf) + I.t_off;
+  const T h = (T)I.h;
   // F_x v5 = b4
-  double* cur = f.V;
-  double* nxt = f.V2;
-  for (int p = threadIdx.x; p < ng; p += THREADS) cur[p] = (pts[p] >= 0) ? f.B4[p] / f.DG[p] : 0.0;
+  T* cur = f.V;
+  T* nxt = f.V2;
+  for (int p = threadIdx.x; p < ng; p += THREADS) cur[p] = (pts[p] >= 0) ? f.B4[p] / f.DG[p] : T(0);
   __syncthreads();
   for (int sw = 1; sw < A.n_lo; ++sw) {
     for (int p = threadIdx.x; p < ng; p += THREADS) {
-      double v = 0.0;
+      T v = T(0);
       if (pts[p] >= 0) {
-        double off = 0.0;
+        T off = T(0);
 #pragma unroll
         for (int e = 0; e < ELL; ++e) {
           const int c = Lc[p * ELL + e];
           off += Lv[p * ELL + e] * f.DP[c] * cur[c];
         }
         off -= Ld[p] * f.DP[p] * cur[p];
-        v = (f.B4[p] - I.h * off) / f.DG[p];
+        v = (f.B4[p] - h * off) / f.DG[p];
       }
       nxt[p] = v;
     }
     __syncthreads();
-    double* t = cur;
+    T* t = cur;
     cur = nxt;
     nxt = t;
   }
@@ -113,22 +132,22 @@ __device__ void p_inv(const PArgs& A, const PInst& I, const Fields& f, const int
   __syncthreads();
   // F_x^T v4 = b5 - A_xx v5; off-diagonal part h Phi'(x_p) sum_q L[q][p] v_q
   for (int p = threadIdx.x; p < ng; p += THREADS)
-    cur[p] = (pts[p] >= 0) ? (f.B5[p] - f.AX[p] * f.Y5[p]) / f.DG[p] : 0.0;
+    cur[p] = (pts[p] >= 0) ? (f.B5[p] - f.AX[p] * f.Y5[p]) / f.DG[p] : T(0);
   __syncthreads();
   for (int sw = 1; sw < A.n_lo; ++sw) {
     for (int p = threadIdx.x; p < ng; p += THREADS) {
-      double v = 0.0;
+      T v = T(0);
       if (pts[p] >= 0) {
-        double off = 0.0;
+        T off = T(0);
 #pragma unroll
         for (int e = 0; e < ELL; ++e) off += Ltv[p * ELL + e] * cur[Ltc[p * ELL + e]];
         off -= Ld[p] * cur[p];
-        v = (f.B5[p] - f.AX[p] * f.Y5[p] - I.h * f.DP[p] * off) / f.DG[p];
+        v = (f.B5[p] - f.AX[p] * f.Y5[p] - h * f.DP[p] * off) / f.DG[p];
       }
       nxt[p] = v;
     }
     __syncthreads();
-    double* t = cur;
+    T* t = cur;
     cur = nxt;
     nxt = t;
   }
@@ -136,6 +155,7 @@ __device__ void p_inv(const PArgs& A, const PInst& I, const Fields& f, const int
   __syncthreads();
 }
 
+template <typename T>
 __global__ void __launch_bounds__(THREADS) k_plate_dir(PArgs A, Ctl C, Iter S) {
   const int2 it = C.work[blockIdx.x];
   const int b = it.x, s = it.y;
@@ -146,25 +166,27 @@ __global__ void __launch_bounds__(THREADS) k_plate_dir(PArgs A, Ctl C, Iter S) {
   const int ng = I.ng, ns = I.ns, nu = I.nu, N = I.N;
   const bool last = (s == N - 1);
   extern __shared__ double smem[];
-  Fields f;
+  Fields<T> f;
   double* q = smem;
   f.W = q; q += ng;
   f.LB = q; q += ng;
   f.PH = q; q += ng;
-  f.DP = q; q += ng;
   f.LTL = q; q += ng;
-  f.DG = q; q += ng;
-  f.AX = q; q += ng;
-  f.V = q; q += ng;
-  f.V2 = q; q += ng;
-  f.B4 = q; q += ng;
-  f.B5 = q; q += ng;
-  f.K1 = q; q += ng;
-  f.K3 = q; q += ng;
-  f.Y4 = q; q += ng;
-  f.Y5 = q; q += ng;
-  f.Z = q; q += ng;
-  __shared__ double sK2[MAX_NU], sAUU[MAX_NU], sV3[MAX_NU], red[64];
+  T* qt = reinterpret_cast<T*>(q);
+  f.DP = qt; qt += ng;
+  f.DG = qt; qt += ng;
+  f.AX = qt; qt += ng;
+  f.V = qt; qt += ng;
+  f.V2 = qt; qt += ng;
+  f.B4 = qt; qt += ng;
+  f.B5 = qt; qt += ng;
+  f.K1 = qt; qt += ng;
+  f.K3 = qt; qt += ng;
+  f.Y4 = qt; qt += ng;
+  f.Y5 = qt; qt += ng;
+  f.Z = qt; qt += ng;
+  __shared__ double red[64];
+  __shared__ T sK2[MAX_NU], sAUU[MAX_NU], sV3[MAX_NU];
   const int* pts = A.pt_state + I.t_off;
   const int* apt = A.act_pt + I.a_off;
   const int* Lc = A.Lc + I.t_off * ELL;
@@ -172,6 +194,8 @@ __global__ void __launch_bounds__(THREADS) k_plate_dir(PArgs A, Ctl C, Iter S) {
   const int* Ltc = A.Ltc + I.t_off * ELL;
   const double* Ltv = A.Ltv + I.t_off * ELL;
   const double* Ld = A.Ld + I.t_off;
+  const T* LvT = tab<T>(A.Lv, A.Lvf) + I.t_off * ELL;
+  const T* LtvT = tab<T>(A.Ltv, A.Ltvf) + I.t_off * ELL;
   const long long so = Ly.s_off + (long long)s * ns;
   const long long uo = Ly.u_off + (long long)s * nu;
   const double h = I.h;
@@ -190,7 +214,7 @@ __global__ void __launch_bounds__(THREADS) k_plate_dir(PArgs A, Ctl C, Iter S) {
     f.W[p] = w;
     f.LB[p] = lb;
     f.PH[p] = phi(I, w);
-    f.DP[p] = dphi(I, w);
+    f.DP[p] = (T)dphi(I, w);
   }
   __syncthreads();
   for (int p = threadIdx.x; p < ng; p += THREADS) {
@@ -207,9 +231,9 @@ __global__ void __launch_bounds__(THREADS) k_plate_dir(PArgs A, Ctl C, Iter S) {
   for (int p = threadIdx.x; p < ng; p += THREADS) {
     const int t = pts[p];
     if (t < 0) {
-      f.K1[p] = f.K3[p] = 0.0;
-      f.DG[p] = 1.0;
-      f.AX[p] = 0.0;
+      f.K1[p] = f.K3[p] = T(0);
+      f.DG[p] = T(1);
+      f.AX[p] = T(0);
       continue;
     }
     const double x = f.W[p], lam = f.LB[p], xr = A.xref[Ly.g_off + t];
@@ -221,7 +245,8 @@ __global__ void __launch_bounds__(THREADS) k_plate_dir(PArgs A, Ctl C, Iter S) {
     const double x3 = x * x * x;
     const double fp = lph - I.beta * (x - I.ta) - I.gr * (x3 * x - I.ta * I.ta * I.ta * I.ta);
     const double K1 = xprev - x + h * fp;
-    const double gxT = f.DP[p] * f.LTL[p] - (I.beta + 4.0 * I.gr * x3) * lam;
+    const double dpx = dphi(I, x);
+    const double gxT = dpx * f.LTL[p] - (I.beta + 4.0 * I.gr * x3) * lam;
     const double K3 = lnext - lam + h * (I.q * (x - xr) + gxT);
     mx = stage_drv::nan_max(mx, stage_drv::nan_max(fabs(K1), fabs(K3)));
     sq += K1 * K1 + K3 * K3;
@@ -233,10 +258,10 @@ __global__ void __launch_bounds__(THREADS) k_plate_dir(PArgs A, Ctl C, Iter S) {
       if (s > 0) K1r -= S.dx[so - ns + t];
       if (!last) K3r -= S.dl[so + ns + t];
     }
-    f.K1[p] = K1r;
-    f.K3[p] = K3r;
-    f.DG[p] = h * (Ld[p] * f.DP[p] - I.beta - 4.0 * I.gr * x3) - 1.0;
-    f.AX[p] = h * (I.q + d2p * f.LTL[p] - 12.0 * I.gr * x * x * lam) + (last ? h * I.qf : 0.0);
+    f.K1[p] = (T)K1r;
+    f.K3[p] = (T)K3r;
+    f.DG[p] = (T)(h * (Ld[p] * dpx - I.beta - 4.0 * I.gr * x3) - 1.0);
+    f.AX[p] = (T)(h * (I.q + d2p * f.LTL[p] - 12.0 * I.gr * x * x * lam) + (last ? h * I.qf : 0.0));
   }
   for (int a = threadIdx.x; a < nu; a += THREADS) {
     const int pa = apt[a];
@@ -246,12 +271,12 @@ __global__ void __launch_bounds__(THREADS) k_plate_dir(PArgs A, Ctl C, Iter S) {
       db = -I.tau / (u - I.ulo) + I.tau / (I.uhi - u);
       d2b = I.tau / ((u - I.ulo) * (u - I.ulo)) + I.tau / ((I.uhi - u) * (I.uhi - u));
     }
-    const double K2 = h * (I.r * (u - A.uref[I.a_off + a]) + db + f.DP[pa] * f.LTL[pa]);
+    const double K2 = h * (I.r * (u - A.uref[I.a_off + a]) + db + dphi(I, u) * f.LTL[pa]);
     mx = stage_drv::nan_max(mx, fabs(K2));
     sq += K2 * K2;
-    sK2[a] = K2;
-    sAUU[a] = h * (I.r + d2b + d2p * f.LTL[pa]) + I.gamma;
-    sV3[a] = 0.0;
+    sK2[a] = (T)K2;
+    sAUU[a] = (T)(h * (I.r + d2b + d2p * f.LTL[pa]) + I.gamma);
+    sV3[a] = T(0);
   }
   __syncthreads();
   stage_drv::block_max_sum(mx, sq, red, THREADS);
@@ -259,34 +284,35 @@ __global__ void __launch_bounds__(THREADS) k_plate_dir(PArgs A, Ctl C, Iter S) {
 
   // u fixed-point iteration (Sec. 5.2): y = P^{-1}(F_u v3 - b1, -b2),
   // v3 = (b3 + F_u^T y_lambda) / A_uu, from v3 = 0
+  const T hT = (T)h;
   for (int itu = 0; itu <= A.n_u_it; ++itu) {
     const bool final_pass = (itu == A.n_u_it);
     // Z = Phi'(u) v3 at the actuator points, zero elsewhere
-    for (int p = threadIdx.x; p < ng; p += THREADS) f.Z[p] = 0.0;
+    for (int p = threadIdx.x; p < ng; p += THREADS) f.Z[p] = T(0);
     __syncthreads();
     for (int a = threadIdx.x; a < nu; a += THREADS) f.Z[apt[a]] = f.DP[apt[a]] * sV3[a];
     __syncthreads();
     for (int p = threadIdx.x; p < ng; p += THREADS) {
-      double fu = 0.0;  // (F_u v3)(p) = h sum_a L[p][a] Phi'(u_a) v3_a
+      T fu = T(0);  // (F_u v3)(p) = h sum_a L[p][a] Phi'(u_a) v3_a
 #pragma unroll
-      for (int e = 0; e < ELL; ++e) fu += Lv[p * ELL + e] * f.Z[Lc[p * ELL + e]];
-      fu *= h;
+      for (int e = 0; e < ELL; ++e) fu += LvT[p * ELL + e] * f.Z[Lc[p * ELL + e]];
+      fu *= hT;
       if (pts[p] >= 0) {
         f.B4[p] = final_pass ? f.K1[p] - fu : fu - f.K1[p];
         f.B5[p] = final_pass ? f.K3[p] : -f.K3[p];
       } else {
-        f.B4[p] = f.B5[p] = 0.0;
+        f.B4[p] = f.B5[p] = T(0);
       }
     }
     __syncthreads();
-    p_inv(A, I, f, pts);
+    p_inv<T>(A, I, f, pts);
     if (final_pass) break;
     for (int a = threadIdx.x; a < nu; a += THREADS) {
       const int pa = apt[a];
-      double acc = 0.0;  // (L^T y_lambda)(a) over the state points
+      T acc = T(0);  // (L^T y_lambda)(a) over the state points
 #pragma unroll
-      for (int e = 0; e < ELL; ++e) acc += Ltv[pa * ELL + e] * f.Y4[Ltc[pa * ELL + e]];
-      sV3[a] = (sK2[a] + h * f.DP[pa] * acc) / sAUU[a];
+      for (int e = 0; e < ELL; ++e) acc += LtvT[pa * ELL + e] * f.Y4[Ltc[pa * ELL + e]];
+      sV3[a] = (sK2[a] + hT * f.DP[pa] * acc) / sAUU[a];
     }
     __syncthreads();
   }
@@ -294,13 +320,13 @@ __global__ void __launch_bounds__(THREADS) k_plate_dir(PArgs A, Ctl C, Iter S) {
   for (int p = threadIdx.x; p < ng; p += THREADS) {
     const int t = pts[p];
     if (t >= 0) {
-      S.dx[so + t] = f.Y5[p];
-      S.dl[so + t] = f.Y4[p];
+      S.dx[so + t] = (double)f.Y5[p];
+      S.dl[so + t] = (double)f.Y4[p];
     }
   }
   double amin = 1.0;
   for (int a = threadIdx.x; a < nu; a += THREADS) {
-    const double d = sV3[a], u = f.W[apt[a]];
+    const double d = (double)sV3[a], u = f.W[apt[a]];
     S.du[uo + a] = d;
     if (I.tau > 0.0) {
       if (d > 0.0) amin = fmin(amin, 0.995 * (u - I.ulo) / d);
@@ -371,6 +397,7 @@ struct nmpc_plate {
   PInst* inst_d = nullptr;
   int *pt_state = nullptr, *act_pt = nullptr, *Lc = nullptr, *Ltc = nullptr;
   double *Lv = nullptr, *Ltv = nullptr, *Ld = nullptr;
+  float *Lvf = nullptr, *Ltvf = nullptr, *Ldf = nullptr;
   double *xref = nullptr, *uref = nullptr;
   size_t smem = 0;
 };
@@ -379,8 +406,8 @@ namespace {
 
 void free_plate(nmpc_plate* h) {
   stage_drv::driver_free(h->drv);
-  void* ptrs[] = {h->inst_d, h->pt_state, h->act_pt, h->Lc, h->Ltc, h->Lv, h->Ltv, h->Ld, h->xref,
-                  h->uref};
+  void* ptrs[] = {h->inst_d, h->pt_state, h->act_pt, h->Lc, h->Ltc, h->Lv, h->Ltv, h->Ld, h->Lvf,
+                  h->Ltvf, h->Ldf, h->xref, h->uref};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -415,6 +442,9 @@ PArgs make_args(const nmpc_plate* h) {
   A.Ltc = h->Ltc;
   A.Ltv = h->Ltv;
   A.Ld = h->Ld;
+  A.Lvf = h->Lvf;
+  A.Ltvf = h->Ltvf;
+  A.Ldf = h->Ldf;
   A.x0 = h->drv.x0;
   A.xref = h->xref;
   A.uref = h->uref;
@@ -433,7 +463,10 @@ struct PlateDir {
     PArgs A = make_args(h);
     for (int half = 0; half < (A.rb ? 2 : 1); ++half) {
       A.half = half;
-      plate_dev::k_plate_dir<<<h->drv.n_work, plate_dev::THREADS, h->smem, st>>>(A, C, S);
+      if (h->opts.precision == NMPC_MIXED)
+        plate_dev::k_plate_dir<float><<<h->drv.n_work, plate_dev::THREADS, h->smem, st>>>(A, C, S);
+      else
+        plate_dev::k_plate_dir<double><<<h->drv.n_work, plate_dev::THREADS, h->smem, st>>>(A, C, S);
       const cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
@@ -469,6 +502,7 @@ void nmpc_plate_default_opts(nmpc_plate_opts* o) {
   o->n_u_it = 2;
   o->variant = NMPC_VARIANT_JACOBI;
   o->check_every = 16;
+  o->precision = NMPC_FP64;
 }
 
 int nmpc_plate_setup(const nmpc_plate_desc* descs, int n, const nmpc_plate_opts* opts,
@@ -479,7 +513,8 @@ int nmpc_plate_setup(const nmpc_plate_desc* descs, int n, const nmpc_plate_opts*
   nmpc_plate_default_opts(&o);
   if (opts) o = *opts;
   if (!(o.tol >= 0) || o.max_iter < 0 || o.n_lo < 1 || o.n_u_it < 0 || o.check_every < 1 ||
-      (o.variant != NMPC_VARIANT_JACOBI && o.variant != NMPC_VARIANT_REDBLACK))
+      (o.variant != NMPC_VARIANT_JACOBI && o.variant != NMPC_VARIANT_REDBLACK) ||
+      (o.precision != NMPC_FP64 && o.precision != NMPC_MIXED))
     return NMPC_ERR_BAD_ARG;
   for (int b = 0; b < n; ++b) {
     const int rc = validate(descs[b]);
@@ -541,7 +576,8 @@ int nmpc_plate_setup(const nmpc_plate_desc* descs, int n, const nmpc_plate_opts*
     h->ng_max = std::max(h->ng_max, I.ng);
     h->inst_h.push_back(I);
   }
-  h->smem = (size_t)16 * h->ng_max * sizeof(double);
+  const size_t tsz = o.precision == NMPC_MIXED ? sizeof(float) : sizeof(double);
+  h->smem = (size_t)h->ng_max * (plate_dev::F64_FIELDS * sizeof(double) + plate_dev::T_FIELDS * tsz);
   cudaError_t e = stage_drv::driver_alloc(h->drv);
   auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
   A(stage_drv::dalloc(&h->inst_d, n));
@@ -562,9 +598,22 @@ int nmpc_plate_setup(const nmpc_plate_desc* descs, int n, const nmpc_plate_opts*
   A(stage_drv::upload(h->Lv, Lv));
   A(stage_drv::upload(h->Ltv, Ltv));
   A(stage_drv::upload(h->Ld, Ld));
-  if (h->smem > 48 * 1024)
-    A(cudaFuncSetAttribute(plate_dev::k_plate_dir, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)h->smem));
+  {
+    const std::vector<float> Lvf(Lv.begin(), Lv.end()), Ltvf(Ltv.begin(), Ltv.end()),
+        Ldf(Ld.begin(), Ld.end());
+    A(stage_drv::dalloc(&h->Lvf, Lvf.size()));
+    A(stage_drv::dalloc(&h->Ltvf, Ltvf.size()));
+    A(stage_drv::dalloc(&h->Ldf, Ldf.size()));
+    A(stage_drv::upload(h->Lvf, Lvf));
+    A(stage_drv::upload(h->Ltvf, Ltvf));
+    A(stage_drv::upload(h->Ldf, Ldf));
+  }
+  if (h->smem > 48 * 1024) {
+    A(cudaFuncSetAttribute(plate_dev::k_plate_dir<double>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem));
+    A(cudaFuncSetAttribute(plate_dev::k_plate_dir<float>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem));
+  }
   if (e != cudaSuccess) {
     fprintf(stderr, "nmpc_plate_setup: %s\n", cudaGetErrorString(e));
     free_plate(h);

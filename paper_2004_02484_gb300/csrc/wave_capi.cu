@@ -31,7 +31,9 @@ using stage_drv::Iter;
 using stage_drv::Layout;
 constexpr int THREADS = 256;
 constexpr int MAX_NU = 64;
-constexpr int FIELDS = 21;  // shared-memory fields of n_g doubles in k_wave_dir
+// shared-memory fields of n_g values in k_wave_dir: float64 grid values and
+// costates, the lower layer's fields in its type T
+constexpr int F64_FIELDS = 4, T_FIELDS = 18;
 
 struct WInst {
   int dim, m, ng, nu, N;
@@ -50,51 +52,69 @@ struct WArgs {
   const int* Ltc;     // the same for L^T
   const double* Ltv;
   const double* Ld;   // [sum ng] L[p][p]
+  const float* Lvf;   // float32 copies of Lv, Ltv, Ld (mixed precision)
+  const float* Ltvf;
+  const float* Ldf;
   const double* x0;
   const double* wref;
   const double* uref;
   int n_lo, n_u_it, rb, half;
 };
 
+// The lower layer runs in T: float64, or float32 in mixed precision (the
+// residual, the coefficients and the update stay float64, so the fixed point
+// is the float64 root); WT holds W in T for the lower layer's products.
+template <typename T>
 struct Fields {
-  double *W, *V, *LW, *LV, *ED, *AXW, *K1W, *K1V, *K3W, *K3V;
-  double *B6, *B7, *B8, *B9, *T, *C0, *C1, *Y6, *Y7, *Y8, *Y9;
+  double *W, *V, *LW, *LV;
+  T *WT, *ED, *AXW, *K1W, *K1V, *K3W, *K3V;
+  T *B6, *B7, *B8, *B9, *T_, *C0, *C1, *Y6, *Y7, *Y8, *Y9;
 };
 
+template <typename V>
 struct Stencil {
   const int *Lc, *Ltc;
-  const double *Lv, *Ltv, *Ld;
-  __device__ double lap(const double* v, int p) const {  // (L v)(p)
-    double acc = 0.0;
+  const V *Lv, *Ltv, *Ld;
+  __device__ V lap(const V* v, int p) const {  // (L v)(p)
+    V acc = V(0);
 #pragma unroll
     for (int e = 0; e < ELL; ++e) acc += Lv[p * ELL + e] * v[Lc[p * ELL + e]];
     return acc;
   }
-  __device__ double lapT(const double* v, int p) const {  // (L^T v)(p)
-    double acc = 0.0;
+  __device__ V lapT(const V* v, int p) const {  // (L^T v)(p)
+    V acc = V(0);
 #pragma unroll
     for (int e = 0; e < ELL; ++e) acc += Ltv[p * ELL + e] * v[Ltc[p * ELL + e]];
     return acc;
   }
 };
 
+// The stencil tables in type V.
+template <typename V>
+__device__ __forceinline__ const V* tab(const double* d, const float* f);
+template <>
+__device__ __forceinline__ const double* tab<double>(const double* d, const float*) { return d; }
+template <>
+__device__ __forceinline__ const float* tab<float>(const double*, const float* f) { return f; }
+
 // n_lo Jacobi sweeps from zero on E v = T (transposed: E^T), result in the
 // returned buffer (C0 or C1).  E = diag ED + (h^2 c / a)(L - diag L).
-__device__ double* jacobi_E(const WArgs& A, const WInst& I, const Stencil& L, const Fields& f,
-                            bool transposed) {
+template <typename T>
+__device__ T* jacobi_E(const WArgs& A, const WInst& I, const Stencil<T>& L, const Fields<T>& f,
+                       bool transposed) {
   const int ng = I.ng;
-  const double s = I.h * I.h * I.c / I.a;
-  double* cur = f.C0;
-  double* nxt = f.C1;
-  for (int p = threadIdx.x; p < ng; p += THREADS) cur[p] = f.T[p] / f.ED[p];
+  const T s = (T)(I.h * I.h * I.c / I.a);
+  T* cur = f.C0;
+  T* nxt = f.C1;
+  for (int p = threadIdx.x; p < ng; p += THREADS) cur[p] = f.T_[p] / f.ED[p];
   __syncthreads();
   for (int sw = 1; sw < A.n_lo; ++sw) {
     for (int p = threadIdx.x; p < ng; p += THREADS) {
-      const double lv = transposed ? L.lapT(cur, p) : L.lap(cur, p);
-      nxt[p] = (f.T[p] - s * (lv - L.Ld[p] * cur[p])) / f.ED[p];
+      const T lv = transposed ? L.lapT(cur, p) : L.lap(cur, p);
+      nxt[p] = (f.T_[p] - s * (lv - L.Ld[p] * cur[p])) / f.ED[p];
     }
     __syncthreads();
-    double* t = cur;
+    T* t = cur;
     cur = nxt;
     nxt = t;
   }
@@ -103,16 +123,18 @@ __device__ double* jacobi_E(const WArgs& A, const WInst& I, const Stencil& L, co
 
 // P^{-1} (eq. 24): F_x (Y6, Y7) = (B6, B7), then F_x^T (Y8, Y9) = (B8, B9) -
 // A_xx (Y6, Y7), both by the v6 elimination (eq. 25).  B8 is overwritten.
-__device__ void p_inv(const WArgs& A, const WInst& I, const Stencil& L, const Fields& f) {
+template <typename T>
+__device__ void p_inv(const WArgs& A, const WInst& I, const Stencil<T>& L, const Fields<T>& f) {
   const int ng = I.ng;
-  const double h = I.h, ia = 1.0 / I.a, axv = h * I.qv;
+  const T h = (T)I.h, ia = (T)(1.0 / I.a), axv = (T)(I.h * I.qv), c = (T)I.c;
+  const T k3 = (T)(3.0 * I.kappa);
   // E v7 = b7 + h grad_W g b6
   for (int p = threadIdx.x; p < ng; p += THREADS) {
-    const double gw = (I.c * L.lap(f.B6, p) - 3.0 * I.kappa * f.W[p] * f.W[p] * f.B6[p]) * ia;
-    f.T[p] = f.B7[p] + h * gw;
+    const T gw = (c * L.lap(f.B6, p) - k3 * f.WT[p] * f.WT[p] * f.B6[p]) * ia;
+    f.T_[p] = f.B7[p] + h * gw;
   }
   __syncthreads();
-  const double* v7 = jacobi_E(A, I, L, f, false);
+  const T* v7 = jacobi_E<T>(A, I, L, f, false);
   for (int p = threadIdx.x; p < ng; p += THREADS) {
     f.Y7[p] = v7[p];
     f.Y6[p] = h * v7[p] - f.B6[p];
@@ -120,22 +142,23 @@ __device__ void p_inv(const WArgs& A, const WInst& I, const Stencil& L, const Fi
   __syncthreads();
   // (b8, b9) = (B8, B9) - A_xx (Y6, Y7); E^T v9 = b9 + h b8
   for (int p = threadIdx.x; p < ng; p += THREADS) {
-    const double b8 = f.B8[p] - f.AXW[p] * f.Y6[p];
+    const T b8 = f.B8[p] - f.AXW[p] * f.Y6[p];
     f.B8[p] = b8;
-    f.T[p] = (f.B9[p] - axv * f.Y7[p]) + h * b8;
+    f.T_[p] = (f.B9[p] - axv * f.Y7[p]) + h * b8;
   }
   __syncthreads();
-  const double* v9 = jacobi_E(A, I, L, f, true);
+  const T* v9 = jacobi_E<T>(A, I, L, f, true);
   for (int p = threadIdx.x; p < ng; p += THREADS) f.Y9[p] = v9[p];
   __syncthreads();
   // v8 = h grad_W g^T v9 - b8
   for (int p = threadIdx.x; p < ng; p += THREADS) {
-    const double gwt = (I.c * L.lapT(f.Y9, p) - 3.0 * I.kappa * f.W[p] * f.W[p] * f.Y9[p]) * ia;
+    const T gwt = (c * L.lapT(f.Y9, p) - k3 * f.WT[p] * f.WT[p] * f.Y9[p]) * ia;
     f.Y8[p] = h * gwt - f.B8[p];
   }
   __syncthreads();
 }
 
+template <typename T>
 __global__ void __launch_bounds__(THREADS) k_wave_dir(WArgs A, Ctl C, Iter S) {
   const int2 it = C.work[blockIdx.x];
   const int b = it.x, s = it.y;
@@ -146,16 +169,23 @@ __global__ void __launch_bounds__(THREADS) k_wave_dir(WArgs A, Ctl C, Iter S) {
   const int ng = I.ng, nu = I.nu, nx = 2 * ng;
   const bool last = (s == I.N - 1);
   extern __shared__ double smem[];
-  Fields f;
+  Fields<T> f;
   {
-    double** fp[FIELDS] = {&f.W,   &f.V,   &f.LW, &f.LV, &f.ED, &f.AXW, &f.K1W,
-                           &f.K1V, &f.K3W, &f.K3V, &f.B6, &f.B7, &f.B8,  &f.B9,
-                           &f.T,   &f.C0,  &f.C1, &f.Y6, &f.Y7, &f.Y8,  &f.Y9};
-    for (int q = 0; q < FIELDS; ++q) *fp[q] = smem + (size_t)q * ng;
+    double** fd[F64_FIELDS] = {&f.W, &f.V, &f.LW, &f.LV};
+    for (int q = 0; q < F64_FIELDS; ++q) *fd[q] = smem + (size_t)q * ng;
+    T* base = reinterpret_cast<T*>(smem + (size_t)F64_FIELDS * ng);
+    T** ft[T_FIELDS] = {&f.WT, &f.ED, &f.AXW, &f.K1W, &f.K1V, &f.K3W, &f.K3V, &f.B6, &f.B7,
+                        &f.B8, &f.B9, &f.T_,  &f.C0,  &f.C1,  &f.Y6,  &f.Y7,  &f.Y8, &f.Y9};
+    for (int q = 0; q < T_FIELDS; ++q) *ft[q] = base + (size_t)q * ng;
   }
-  __shared__ double sK2[MAX_NU], sV3[MAX_NU], sU[MAX_NU], red[64];
-  Stencil L{A.Lc + I.t_off * ELL, A.Ltc + I.t_off * ELL, A.Lv + I.t_off * ELL,
-            A.Ltv + I.t_off * ELL, A.Ld + I.t_off};
+  __shared__ double sU[MAX_NU], red[64];
+  __shared__ T sK2[MAX_NU], sV3[MAX_NU];
+  // the residual's stencil (float64) and the lower layer's (T)
+  Stencil<double> L{A.Lc + I.t_off * ELL, A.Ltc + I.t_off * ELL, A.Lv + I.t_off * ELL,
+                    A.Ltv + I.t_off * ELL, A.Ld + I.t_off};
+  Stencil<T> LT{A.Lc + I.t_off * ELL, A.Ltc + I.t_off * ELL,
+                tab<T>(A.Lv, A.Lvf) + I.t_off * ELL, tab<T>(A.Ltv, A.Ltvf) + I.t_off * ELL,
+                tab<T>(A.Ld, A.Ldf) + I.t_off};
   const int* act_of = A.act_of + I.t_off;
   const int* apt = A.act_pt + I.a_off;
   const long long so = Ly.s_off + (long long)s * nx;
@@ -205,21 +235,22 @@ __global__ void __launch_bounds__(THREADS) k_wave_dir(WArgs A, Ctl C, Iter S) {
         k3v -= S.dl[so + nx + ng + p];
       }
     }
-    f.K1W[p] = k1w;
-    f.K1V[p] = k1v;
-    f.K3W[p] = k3w;
-    f.K3V[p] = k3v;
+    f.K1W[p] = (T)k1w;
+    f.K1V[p] = (T)k1v;
+    f.K3W[p] = (T)k3w;
+    f.K3V[p] = (T)k3v;
+    f.WT[p] = (T)w;
     // E's diagonal: h grad_V g - 1 + h^2 grad_W g at (p, p)
-    f.ED[p] = -(1.0 + h * I.b * ia) + h * h * (I.c * L.Ld[p] - 3.0 * I.kappa * w * w) * ia;
-    f.AXW[p] = h * (I.q - 6.0 * I.kappa * w * lv * ia) + (last ? h * I.qf : 0.0);
+    f.ED[p] = (T)(-(1.0 + h * I.b * ia) + h * h * (I.c * L.Ld[p] - 3.0 * I.kappa * w * w) * ia);
+    f.AXW[p] = (T)(h * (I.q - 6.0 * I.kappa * w * lv * ia) + (last ? h * I.qf : 0.0));
   }
   __syncthreads();
   for (int a = threadIdx.x; a < nu; a += THREADS) {
     const double K2 = h * (I.r * (sU[a] - A.uref[I.a_off + a]) + I.gain * ia * f.LV[apt[a]]);
     mx = stage_drv::nan_max(mx, fabs(K2));
     sq += K2 * K2;
-    sK2[a] = K2;
-    sV3[a] = 0.0;
+    sK2[a] = (T)K2;
+    sV3[a] = T(0);
   }
   __syncthreads();
   stage_drv::block_max_sum(mx, sq, red, THREADS);
@@ -228,31 +259,31 @@ __global__ void __launch_bounds__(THREADS) k_wave_dir(WArgs A, Ctl C, Iter S) {
   // u fixed-point iteration (Sec. 5.2): y = P^{-1}(F_u v3 - b1, -b2),
   // v3 = (b3 + F_u^T y_lambda) / A_uu from v3 = 0, then the final
   // P^{-1}(b1 - F_u v3, b2).  F_u = [0; h B / a]; A_uu = h r + gamma.
-  const double fu = h * I.gain * ia, auu = h * I.r + I.gamma;
+  const T fu = (T)(h * I.gain * ia), auu = (T)(h * I.r + I.gamma);
   for (int itu = 0; itu <= A.n_u_it; ++itu) {
     const bool final_pass = (itu == A.n_u_it);
     for (int p = threadIdx.x; p < ng; p += THREADS) {
       const int ap = act_of[p];
-      const double fuv = ap >= 0 ? fu * sV3[ap] : 0.0;
+      const T fuv = ap >= 0 ? fu * sV3[ap] : T(0);
       f.B6[p] = final_pass ? f.K1W[p] : -f.K1W[p];
       f.B7[p] = final_pass ? f.K1V[p] - fuv : fuv - f.K1V[p];
       f.B8[p] = final_pass ? f.K3W[p] : -f.K3W[p];
       f.B9[p] = final_pass ? f.K3V[p] : -f.K3V[p];
     }
     __syncthreads();
-    p_inv(A, I, L, f);
+    p_inv<T>(A, I, LT, f);
     if (final_pass) break;
     for (int a = threadIdx.x; a < nu; a += THREADS) sV3[a] = (sK2[a] + fu * f.Y9[apt[a]]) / auu;
     __syncthreads();
   }
   // direction (Delta x, Delta u, Delta lambda) = (v5, v3, v4)
   for (int p = threadIdx.x; p < ng; p += THREADS) {
-    S.dx[so + p] = f.Y6[p];
-    S.dx[so + ng + p] = f.Y7[p];
-    S.dl[so + p] = f.Y8[p];
-    S.dl[so + ng + p] = f.Y9[p];
+    S.dx[so + p] = (double)f.Y6[p];
+    S.dx[so + ng + p] = (double)f.Y7[p];
+    S.dl[so + p] = (double)f.Y8[p];
+    S.dl[so + ng + p] = (double)f.Y9[p];
   }
-  for (int a = threadIdx.x; a < nu; a += THREADS) S.du[uo + a] = sV3[a];
+  for (int a = threadIdx.x; a < nu; a += THREADS) S.du[uo + a] = (double)sV3[a];
 }
 
 }  // namespace wave_dev
@@ -269,6 +300,7 @@ struct nmpc_wave {
   WInst* inst_d = nullptr;
   int *act_of = nullptr, *act_pt = nullptr, *Lc = nullptr, *Ltc = nullptr;
   double *Lv = nullptr, *Ltv = nullptr, *Ld = nullptr;
+  float *Lvf = nullptr, *Ltvf = nullptr, *Ldf = nullptr;
   double *wref = nullptr, *uref = nullptr;
   size_t smem = 0;
 };
@@ -277,8 +309,8 @@ namespace {
 
 void free_wave(nmpc_wave* h) {
   stage_drv::driver_free(h->drv);
-  void* ptrs[] = {h->inst_d, h->act_of, h->act_pt, h->Lc, h->Ltc, h->Lv, h->Ltv, h->Ld, h->wref,
-                  h->uref};
+  void* ptrs[] = {h->inst_d, h->act_of, h->act_pt, h->Lc, h->Ltc, h->Lv, h->Ltv, h->Ld, h->Lvf,
+                  h->Ltvf, h->Ldf, h->wref, h->uref};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -311,6 +343,9 @@ WArgs make_args(const nmpc_wave* h) {
   A.Ltc = h->Ltc;
   A.Ltv = h->Ltv;
   A.Ld = h->Ld;
+  A.Lvf = h->Lvf;
+  A.Ltvf = h->Ltvf;
+  A.Ldf = h->Ldf;
   A.x0 = h->drv.x0;
   A.wref = h->wref;
   A.uref = h->uref;
@@ -327,7 +362,10 @@ struct WaveDir {
     WArgs A = make_args(h);
     for (int half = 0; half < (A.rb ? 2 : 1); ++half) {
       A.half = half;
-      wave_dev::k_wave_dir<<<h->drv.n_work, wave_dev::THREADS, h->smem, st>>>(A, C, S);
+      if (h->opts.precision == NMPC_MIXED)
+        wave_dev::k_wave_dir<float><<<h->drv.n_work, wave_dev::THREADS, h->smem, st>>>(A, C, S);
+      else
+        wave_dev::k_wave_dir<double><<<h->drv.n_work, wave_dev::THREADS, h->smem, st>>>(A, C, S);
       const cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
     }
@@ -355,6 +393,7 @@ void nmpc_wave_default_opts(nmpc_wave_opts* o) {
   o->n_u_it = 2;
   o->variant = NMPC_VARIANT_JACOBI;
   o->check_every = 16;
+  o->precision = NMPC_FP64;
 }
 
 int nmpc_wave_setup(const nmpc_wave_desc* descs, int n, const nmpc_wave_opts* opts, nmpc_wave** out) {
@@ -364,7 +403,8 @@ int nmpc_wave_setup(const nmpc_wave_desc* descs, int n, const nmpc_wave_opts* op
   nmpc_wave_default_opts(&o);
   if (opts) o = *opts;
   if (!(o.tol >= 0) || o.max_iter < 0 || o.n_lo < 1 || o.n_u_it < 0 || o.check_every < 1 ||
-      (o.variant != NMPC_VARIANT_JACOBI && o.variant != NMPC_VARIANT_REDBLACK))
+      (o.variant != NMPC_VARIANT_JACOBI && o.variant != NMPC_VARIANT_REDBLACK) ||
+      (o.precision != NMPC_FP64 && o.precision != NMPC_MIXED))
     return NMPC_ERR_BAD_ARG;
   for (int b = 0; b < n; ++b) {
     const int rc = validate(descs[b]);
@@ -417,7 +457,8 @@ int nmpc_wave_setup(const nmpc_wave_desc* descs, int n, const nmpc_wave_opts* op
     h->ng_max = std::max(h->ng_max, I.ng);
     h->inst_h.push_back(I);
   }
-  h->smem = (size_t)wave_dev::FIELDS * h->ng_max * sizeof(double);
+  const size_t tsz = o.precision == NMPC_MIXED ? sizeof(float) : sizeof(double);
+  h->smem = (size_t)h->ng_max * (wave_dev::F64_FIELDS * sizeof(double) + wave_dev::T_FIELDS * tsz);
   cudaError_t e = stage_drv::driver_alloc(h->drv);
   auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
   A(stage_drv::dalloc(&h->inst_d, n));
@@ -438,9 +479,22 @@ int nmpc_wave_setup(const nmpc_wave_desc* descs, int n, const nmpc_wave_opts* op
   A(stage_drv::upload(h->Lv, Lv));
   A(stage_drv::upload(h->Ltv, Ltv));
   A(stage_drv::upload(h->Ld, Ld));
-  if (h->smem > 48 * 1024)
-    A(cudaFuncSetAttribute(wave_dev::k_wave_dir, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)h->smem));
+  {
+    const std::vector<float> Lvf(Lv.begin(), Lv.end()), Ltvf(Ltv.begin(), Ltv.end()),
+        Ldf(Ld.begin(), Ld.end());
+    A(stage_drv::dalloc(&h->Lvf, Lvf.size()));
+    A(stage_drv::dalloc(&h->Ltvf, Ltvf.size()));
+    A(stage_drv::dalloc(&h->Ldf, Ldf.size()));
+    A(stage_drv::upload(h->Lvf, Lvf));
+    A(stage_drv::upload(h->Ltvf, Ltvf));
+    A(stage_drv::upload(h->Ldf, Ldf));
+  }
+  if (h->smem > 48 * 1024) {
+    A(cudaFuncSetAttribute(wave_dev::k_wave_dir<double>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem));
+    A(cudaFuncSetAttribute(wave_dev::k_wave_dir<float>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem));
+  }
   if (e != cudaSuccess) {
     fprintf(stderr, "nmpc_wave_setup: %s\n", cudaGetErrorString(e));
     free_wave(h);

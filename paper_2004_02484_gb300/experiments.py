@@ -264,7 +264,8 @@ def gemm_bench(shapes, reps: int, path_list=(0, 1)):
     return {"experiment": "gemm", "results": out, "tc_error": GM.nmpc_gemm_error(True)}
 
 
-def plate(n_batch: int, steps: int, variant: int, tol_loop: float, reps: int, n_sub: int):
+def plate(n_batch: int, steps: int, variant: int, tol_loop: float, reps: int, n_sub: int,
+          precision: int = 0):
     import torch
     from . import plate as GP
     inst = wl.plate_instance()
@@ -284,7 +285,8 @@ def plate(n_batch: int, steps: int, variant: int, tol_loop: float, reps: int, n_
     u_hist = np.zeros((steps, len(inst.act)))
     err = np.zeros(steps)
     for rep in range(reps):
-        sol = GP.PlateSolver([inst], tol=tol_loop, variant=variant, max_iter=5000)
+        sol = GP.PlateSolver([inst], tol=tol_loop, variant=variant, max_iter=5000,
+                             precision=precision)
         w = torch.from_numpy(np.asarray(inst.x0, dtype=np.float64)).cuda()
         for k in range(steps):
             xr, ur = reference(k * dt)
@@ -302,7 +304,7 @@ def plate(n_batch: int, steps: int, variant: int, tol_loop: float, reps: int, n_
             err[k] = float(np.abs(w.cpu().numpy() - xr).max())
         sol.close()
     # device time of back-to-back iterations (no convergence polls)
-    sol = GP.PlateSolver([inst], variant=variant)
+    sol = GP.PlateSolver([inst], variant=variant, precision=precision)
     x = torch.from_numpy(np.tile(inst.x0, inst.horizon)).cuda()
     u = torch.full((inst.horizon * len(inst.act),), 0.5 * (inst.u_lo + inst.u_hi),
                    dtype=torch.float64, device="cuda")
@@ -316,6 +318,7 @@ def plate(n_batch: int, steps: int, variant: int, tol_loop: float, reps: int, n_
     it_us = 1e3 * e0.elapsed_time(e1) / 200
     sol.close()
     out = {"experiment": "plate", "variant": "redblack" if variant else "jacobi",
+           "precision": "mixed" if precision else "fp64",
            "loop": {"steps": steps, "tol": tol_loop, "n_sub": n_sub,
                     "iters_mean": float(iters.mean()), "iters_max": int(iters.max()),
                     "iters_first": int(iters[0]),
@@ -327,7 +330,8 @@ def plate(n_batch: int, steps: int, variant: int, tol_loop: float, reps: int, n_
            "us_per_iter_device": it_us}
     if n_batch:
         insts = wl.plate_batch(n_batch)
-        sol = GP.PlateSolver(insts, tol=1e-6, variant=variant, max_iter=20000)
+        sol = GP.PlateSolver(insts, tol=1e-6, variant=variant, max_iter=20000,
+                             precision=precision)
         sol.solve()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -342,15 +346,17 @@ def plate(n_batch: int, steps: int, variant: int, tol_loop: float, reps: int, n_
     return out
 
 
-def wave(n: int, variant: int, reps: int, dims=(1, 2), single: bool = True):
+def wave(n: int, variant: int, reps: int, dims=(1, 2), single: bool = True, precision: int = 0):
     import torch
     from . import wave as GW
-    out = {"experiment": "wave", "variant": "redblack" if variant else "jacobi", "results": []}
+    out = {"experiment": "wave", "variant": "redblack" if variant else "jacobi",
+           "precision": "mixed" if precision else "fp64", "results": []}
     cases = {1: dict(dim=1, m=64, horizon=20), 2: dict(dim=2, m=32, horizon=10, n_act=3)}
     for kw in (cases[d] for d in dims):
         for nb in ((1, n) if single and n > 1 else (n,)):
             insts = [wl.wave_instance(seed=s_, **kw) for s_ in range(nb)]
-            sol = GW.WaveSolver(insts, tol=1e-6, variant=variant, max_iter=20000)
+            sol = GW.WaveSolver(insts, tol=1e-6, variant=variant, max_iter=20000,
+                                precision=precision)
             sol.solve()
             torch.cuda.synchronize()
             best = float("inf")
@@ -397,6 +403,8 @@ def main():
     ap.add_argument("--tune", type=int, default=1)
     ap.add_argument("--lines", type=int, default=0)
     ap.add_argument("--plate-tol", type=float, default=1.0)
+    ap.add_argument("--precision", type=int, default=0,
+                    help="plate, wave: 0 float64, 1 float32 lower layer (NMPC_MIXED)")
     ap.add_argument("--wave-dims", default="1,2", help="wave: 1 string, 2 membrane")
     ap.add_argument("--wave-single", type=int, default=1, help="wave: also time one instance")
     ap.add_argument("--variant", type=int, default=0,
@@ -414,11 +422,13 @@ def main():
         print(json.dumps(gemm_bench(shapes, a.reps, paths)), flush=True)
     elif a.which == "wave":
         print(json.dumps(wave(256 if a.n is None else a.n, a.variant, max(a.reps, 1),
-                              tuple(int(v) for v in a.wave_dims.split(",")), a.wave_single != 0)),
+                              tuple(int(v) for v in a.wave_dims.split(",")), a.wave_single != 0,
+                              a.precision)),
               flush=True)
     elif a.which == "plate":
         print(json.dumps(plate(1024 if a.n is None else a.n, a.steps, a.variant, a.plate_tol,
-                               max(a.reps, 1), 10 if a.n_sub == 2 else a.n_sub)), flush=True)
+                               max(a.reps, 1), 10 if a.n_sub == 2 else a.n_sub, a.precision)),
+              flush=True)
     elif a.which == "batch1d":
         print(json.dumps(batch1d(a.n or 1024, reps=a.reps, tune=a.tune, use_graph=a.graph,
                                  lines=a.lines)), flush=True)

@@ -33,7 +33,7 @@ class nmpc_wave_desc(ctypes.Structure):
 class nmpc_wave_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("n_lo", ctypes.c_int),
                 ("n_u_it", ctypes.c_int), ("variant", ctypes.c_int),
-                ("check_every", ctypes.c_int)]
+                ("check_every", ctypes.c_int), ("precision", ctypes.c_int)]
 
 
 _P, _I = ctypes.c_void_p, ctypes.c_int

@@ -190,3 +190,49 @@ def test_closed_loop_matches_the_oracle(GP):
         x = P.plant_step(p, x, U[0], p.h, 1)
         S = tuple(np.vstack([A[1:], A[-1:]]) for A in (X, U, L))
     assert np.abs(w.cpu().numpy() - x).max() <= 1e-7 * np.abs(x).max()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("variant,oracle_variant", [(0, "jacobi"), (1, "redblack")])
+def test_mixed_iteration_matches_the_oracle(GP, case, variant, oracle_variant):
+    """Float32 lower layer (NMPC_MIXED): one iteration's change agrees with the
+    oracle's float64 change to 1e-4 of its size; the norms come from the
+    float64 residual (1e-11)."""
+    insts = CASES[case]()
+    probs = [P.PinnedProblem(i) for i in insts]
+    states = [_start(p, 30 + b) for b, p in enumerate(probs)]
+    gpu, out = _gpu_iter(GP, insts, states, 1, variant=variant, precision=1)
+    for b, p in enumerate(probs):
+        X0, U0, L0 = states[b]
+        X, U, L, nm, a = P.iteration(p, X0, U0, L0, oracle_variant)
+        for g, o, i in zip(gpu[b], (X, U, L), (X0, U0, L0)):
+            assert np.abs((g - i) - (o - i)).max() <= 1e-4 * np.abs(o - i).max(), b
+        assert abs(out[b, 0] - nm[0]) <= 1e-11 * nm[0]
+        assert abs(out[b, 2] - a) <= 1e-4
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_mixed_solve_reaches_the_float64_root(GP, variant):
+    """NMPC_MIXED solves stop on the float64 residual and land on the float64
+    root: controls within 1e-7 (relative) of the oracle's solve, about the
+    same iteration count as the float64 GPU solve."""
+    import torch
+    insts = CASES["plate_batch_3"]() + CASES["plate_13x13_N20"]()
+    its, us = {}, {}
+    for prec in (0, 1):
+        s = GP.PlateSolver(insts, tol=1e-6, variant=variant, precision=prec, max_iter=3000)
+        rc, st = s.solve()
+        torch.cuda.synchronize()
+        assert rc == 0 and all(x.res_inf <= 1e-6 for x in st)
+        its[prec] = [x.iters for x in st]
+        us[prec] = s.u.cpu().numpy()
+        s.close()
+    ou = 0
+    for b, inst in enumerate(insts):
+        p = P.PinnedProblem(inst)
+        (X, U, L), info = P.solve(p, "redblack" if variant else "jacobi", tol=1e-6, max_iter=3000)
+        nu, N = len(inst.act), inst.horizon
+        ug = us[1][ou:ou + N * nu].reshape(N, nu)
+        assert np.abs(ug - U).max() <= 1e-7 * np.abs(U).max()
+        assert abs(its[1][b] - its[0][b]) <= max(2, 0.05 * its[0][b]), (its[0][b], its[1][b])
+        ou += N * nu

@@ -170,3 +170,48 @@ def test_warm_and_shifted_starts_use_the_returned_state(GW):
     X, U, L, nm = Wv.iteration(p, *S, "jacobi")
     assert np.abs(uo.cpu().numpy().reshape(U.shape) - U).max() <= 1e-11 * np.abs(U).max()
     assert out[0, 0] == pytest.approx(nm[0], rel=1e-11)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("variant,oracle_variant", [(0, "jacobi"), (1, "redblack")])
+def test_mixed_iteration_matches_the_oracle(GW, case, variant, oracle_variant):
+    """Float32 lower layer (NMPC_MIXED): one iteration's change agrees with the
+    oracle's float64 change to 1e-4 of its size; the norms come from the
+    float64 residual (1e-11)."""
+    insts = CASES[case]()
+    probs = [Wv.WaveProblem(i) for i in insts]
+    states = [_start(p, 60 + b) for b, p in enumerate(probs)]
+    gpu, out = _gpu_iter(GW, insts, states, 1, variant=variant, precision=1)
+    for b, p in enumerate(probs):
+        X0, U0, L0 = states[b]
+        X, U, L, nm = Wv.iteration(p, X0, U0, L0, oracle_variant)
+        for g, o, i in zip(gpu[b], (X, U, L), (X0, U0, L0)):
+            assert np.abs((g - i) - (o - i)).max() <= 1e-4 * np.abs(o - i).max(), b
+        assert abs(out[b, 0] - nm[0]) <= 1e-11 * nm[0]
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_mixed_solve_reaches_the_float64_root(GW, variant):
+    """NMPC_MIXED solves to 1e-9 stop on the float64 residual and land on the
+    float64 root: controls within 1e-6 (relative) of the oracle's solve to
+    the same tolerance, about the same iteration count as float64."""
+    import torch
+    insts = CASES["ragged_batch_4"]() + CASES["string_m64_N20"]()
+    its, us = {}, {}
+    for prec in (0, 1):
+        s = GW.WaveSolver(insts, tol=1e-9, variant=variant, precision=prec, max_iter=5000)
+        rc, st = s.solve()
+        torch.cuda.synchronize()
+        assert rc == 0 and all(x.res_inf <= 1e-9 for x in st)
+        its[prec] = [x.iters for x in st]
+        us[prec] = s.u.cpu().numpy()
+        s.close()
+    ou = 0
+    for b, inst in enumerate(insts):
+        p = Wv.WaveProblem(inst)
+        (X, U, L), info = Wv.solve(p, "redblack" if variant else "jacobi", tol=1e-9, max_iter=5000)
+        nu, N = len(inst.act), inst.horizon
+        ug = us[1][ou:ou + N * nu].reshape(N, nu)
+        assert np.abs(ug - U).max() <= 1e-6 * np.abs(U).max()
+        assert abs(its[1][b] - its[0][b]) <= max(2, 0.05 * its[0][b]), (its[0][b], its[1][b])
+        ou += N * nu
