@@ -392,6 +392,8 @@ def main():
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--strips", type=int, default=0)
     ap.add_argument("--strip-rows", type=int, default=0)
+    ap.add_argument("--n-lo", type=int, default=2, help="solve: Jacobi sweeps per P^-1 solve")
+    ap.add_argument("--n-u-it", type=int, default=2, help="solve: u fixed-point iterations")
     ap.add_argument("--strip-cols", type=int, default=0,
                     help="strip path: 0 auto (two columns per lane where eligible), 1 one")
     ap.add_argument("--n-train", type=int, default=64)
@@ -435,7 +437,8 @@ def main():
     elif a.which == "solve":
         print(json.dumps(solve(a.n or 8, a.grid, a.horizon, a.reps, a.graph, strips=a.strips,
                                strip_rows=a.strip_rows, variant=a.variant,
-                               strip_cols=a.strip_cols)), flush=True)
+                               strip_cols=a.strip_cols, n_lo=a.n_lo, n_u_it=a.n_u_it)),
+              flush=True)
     elif a.which == "closedloop_learned":
         print(json.dumps(closedloop_learned(a.n_train, a.train_steps, a.n or 8, a.steps, a.grid,
                                             a.horizon, a.n_sub, a.fit_steps, a.rules)), flush=True)
