@@ -16,6 +16,8 @@ plate (Sec. 5.1, Tables 1-2) and the 1D heat workload with pinned actuators.
 * The lower layer with many sweeps equals the dense stage solve.
 * The Gauss-Seidel sweeps with exact stage solves are their matrix
   definitions (eqs. 18, 20).
+* The SGS convergence factor (Sec. 5.4, Theorem 2) falls with gamma > 0 and
+  with a shorter horizon (dense iteration matrices at the root).
 * Evidence for the reading of the heat workloads' actuators as heat
   sources: with the actuator cells pinned instead (the plate's model), the
   linearised double-layer iteration at the root of the 1D heat workload has
@@ -259,3 +261,35 @@ def test_pinned_actuators_stall_the_1d_heat_workload_while_heat_sources_converge
     rh = float(np.abs(np.linalg.eigvals(np.eye(len(Ah)) - np.linalg.solve(Dh, Ah))).max())
     assert rh < 0.95
     assert O.solve_jacobi(hp, tol=1e-6)[1]["converged"]
+
+
+def _sgs_factor(p, X, U, L):
+    """rho((D + L)^{-1} U (D + U)^{-1} L) of the KKT matrix at (X, U, L) with
+    the regularization in D (the linearization of Theorem 1, u~ = u*)."""
+    A = P.kkt_matrix(p, X, U, L, with_gamma=True)
+    n = 2 * p.ns + p.nu
+    D = np.zeros_like(A)
+    for i in range(p.N):
+        D[i * n:(i + 1) * n, i * n:(i + 1) * n] = A[i * n:(i + 1) * n, i * n:(i + 1) * n]
+    R = A - D
+    Lo, Up = np.tril(R), np.triu(R)
+    M = np.linalg.solve(D + Lo, Up) @ np.linalg.solve(D + Up, Lo)
+    return float(np.abs(np.linalg.eigvals(M)).max())
+
+
+def test_sgs_factor_falls_with_regularization_and_a_short_horizon():
+    """Sec. 5.4 and Theorem 2: the SGS convergence factor at the root of the
+    plate problem (7 x 7 grid, N = 20, Table 2's tau) is smaller with gamma =
+    0.5 than without regularization, and smaller for T = 20 s than for
+    T = 100 s; with either remedy it is well below 1."""
+    rho = {}
+    for T in (20.0, 100.0):
+        for g in (0.0, 0.5):
+            inst = wl.plate_instance(m=7, horizon=20, T=T, act_idx=(1, 4), gamma=g)
+            p = P.PinnedProblem(inst)
+            (X, U, L), hist = P.newton_solve(p, tol=1e-9)
+            assert hist[-1] <= 1e-9
+            rho[T, g] = _sgs_factor(p, X, U, L)
+    assert rho[100.0, 0.5] < 0.8 * rho[100.0, 0.0]
+    assert rho[20.0, 0.0] < 0.5 * rho[100.0, 0.0] and rho[20.0, 0.5] < rho[100.0, 0.5]
+    assert max(rho[20.0, 0.0], rho[20.0, 0.5], rho[100.0, 0.5]) < 0.7
