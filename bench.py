@@ -526,6 +526,11 @@ def main():
                        f"k_strip<float,2> (strip path: residual, lower layer and update of "
                        f"{plan['strip_x']}-column strips of 256x256 stages)"),
             "algorithmic_bytes_per_launch": alg_bytes / max(1, n_s),
+            # the DRAM bytes a launch moves (traffic) over its live duration:
+            # the red-black halves read the other half's stages from DRAM
+            "dram_achieved": (traffic / (ms_s / max(1, n_s) / 1e3) / 1e9) if ms_s > 0 else None,
+            "dram_frac": (traffic / (ms_s / max(1, n_s) / 1e3) / 1e9 / peaks["hbm_gbs"])
+                         if ms_s > 0 else None,
             "avg_launch_ms": ms_s / max(1, n_s), "timed_launches": n_s,
             "kernel_share_of_step": {k: v[1] / (1e3 * t_kt) for k, v in kt.items() if v[0]},
             "strip_plan": plan,
