@@ -398,3 +398,43 @@ def reduced_cost(p: WaveProblem, U):
                     + 0.5 * p.r * np.sum((U[i] - p.u_ref) ** 2))
     W = p.split(X[-1])[0]
     return J + p.h * 0.5 * p.qf * np.sum((W - p.w_ref) ** 2)
+
+
+# ---------------------------------------------------------------------------
+# The plant of the closed loop (Sec. 5.3)
+# ---------------------------------------------------------------------------
+def plant_step(p: WaveProblem, x, u1, dt, n_sub):
+    """Advance the true system x = (W, V) by dt with the inputs held at u1:
+    n_sub semi-implicit (symplectic) Euler steps of the same model,
+    V <- V + tau g(W, V, u1), then W <- W + tau V with the new V (tau =
+    dt / n_sub).  (Explicit Euler would amplify every undamped mode.)"""
+    x = np.asarray(x, dtype=np.float64).copy()
+    u1 = np.asarray(u1, dtype=np.float64)
+    tau = dt / n_sub
+    for _ in range(n_sub):
+        W, V = x[:p.ng].copy(), x[p.ng:].copy()
+        V = V + tau * p.g(np.concatenate([W, V]), u1)
+        W = W + tau * V
+        x = np.concatenate([W, V])
+    return x
+
+
+def closed_loop(inst, steps, n_sub, tol=1e-9, max_iter=20000, variant="jacobi"):
+    """Receding horizon: each period solves from the plant's state (the first
+    from the cold start, later ones from the previous solution shifted by one
+    stage, the last repeated), applies u_1 for one stage length h and
+    advances the plant.  Returns the applied inputs, the iteration counts and
+    the final plant state."""
+    import copy
+    cur = copy.copy(inst)
+    x = np.asarray(inst.x0, dtype=np.float64).copy()
+    S, us, its = None, [], []
+    for _ in range(steps):
+        cur.x0 = x.copy()
+        p = WaveProblem(cur)
+        (X, U, L), info = solve(p, variant, S0=S, tol=tol, max_iter=max_iter)
+        us.append(U[0].copy())
+        its.append(info["iters"])
+        x = plant_step(p, x, U[0], p.h, n_sub)
+        S = tuple(np.vstack([A[1:], A[-1:]]) for A in (X, U, L))
+    return np.array(us), np.array(its), x

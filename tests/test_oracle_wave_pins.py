@@ -246,3 +246,45 @@ def test_iterations_reach_the_newton_root(wave_root, variant):
     # ||K||_inf <= 1e-11 bounds the distance to the root by ||A^-1|| 1e-11
     np.testing.assert_allclose(Uv, U, rtol=0, atol=1e-6 * np.abs(U).max())
     np.testing.assert_allclose(Xv, X, rtol=0, atol=1e-6 * np.abs(X).max())
+
+
+def test_plant_converges_to_the_standing_wave_at_first_order():
+    """With b = kappa = 0 and no input, a discrete eigenmode v of L (L v = mu
+    v) released at rest oscillates as cos(omega t) v, omega^2 = -c mu / a.
+    The plant's symplectic Euler steps converge to it at first order (the
+    error halves with twice the sub-steps) and never grow in amplitude."""
+    inst = small(dim=1, m=15, N=2, b=0.0, kappa=0.0)
+    p = Wv.WaveProblem(inst)
+    xs = np.arange(1, p.m + 1) / (p.m + 1)
+    v = np.sin(np.pi * xs)
+    mu = -(4 * (p.m + 1) ** 2) * np.sin(np.pi / (2 * (p.m + 1))) ** 2
+    omega = np.sqrt(-p.c * mu / p.a)
+    t = 1.3 * 2 * np.pi / omega          # 1.3 periods
+    x0 = np.concatenate([v, np.zeros(p.ng)])
+    exact = np.cos(omega * t) * v
+    errs = []
+    for n_sub in (200, 400, 800):
+        x = Wv.plant_step(p, x0, np.zeros(p.nu), t, n_sub)
+        errs.append(np.abs(x[:p.ng] - exact).max())
+        assert np.abs(x[:p.ng]).max() <= 1.01  # no growth
+    assert 1.8 < errs[0] / errs[1] < 2.2 and 1.8 < errs[1] / errs[2] < 2.2, errs
+
+
+def test_plant_damping_and_forces():
+    """Damping b > 0 makes the energy a/2 |V|^2 - c/2 W.L W fall step by step
+    (no input, kappa = 0); a constant force on an actuator cell accelerates
+    that cell first (its V grows by tau gain u / a in the first sub-step)."""
+    inst = small(dim=1, m=15, N=2, b=2.0, kappa=0.0)
+    p = Wv.WaveProblem(inst)
+    rng = np.random.default_rng(1)
+    x = np.concatenate([0.1 * rng.standard_normal(p.ng), np.zeros(p.ng)])
+    energy = lambda y: 0.5 * p.a * y[p.ng:] @ y[p.ng:] - 0.5 * p.c * y[:p.ng] @ (p.L @ y[:p.ng])
+    e = [energy(x)]
+    for _ in range(20):
+        x = Wv.plant_step(p, x, np.zeros(p.nu), 1e-3, 1)
+        e.append(energy(x))
+    assert all(e[k + 1] < e[k] for k in range(len(e) - 1))
+    x1 = Wv.plant_step(p, np.zeros(2 * p.ng), np.array([1.0] + [0.0] * (p.nu - 1)), 1e-4, 1)
+    V = x1[p.ng:]
+    assert V[p.act[0]] == pytest.approx(1e-4 * p.gain / p.a)
+    assert np.abs(np.delete(V, p.act[0])).max() == 0.0
