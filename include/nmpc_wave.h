@@ -111,6 +111,22 @@ int nmpc_wave_iterate(nmpc_wave* h, const double* x0, const double* w_ref, const
 /* The handle's current state (the returned iterates after a solve). */
 int nmpc_wave_get_state(nmpc_wave* h, double* x, double* u, double* lam, void* stream);
 
+/* The plant of the closed loop (Sec. 5.3): x = (W, V) (device [sum 2 n_g],
+   in place) advances by dt in n_sub semi-implicit (symplectic) Euler steps
+   of the model, V <- V + tau g(W, V, u1) then W <- W + tau V, with the
+   inputs at the first-stage values u1 of the current state.  BAD_ARG
+   without a solved state. */
+int nmpc_wave_plant_step(nmpc_wave* h, double* x, double dt, int n_sub, void* stream);
+
+/* Receding-horizon loop: each of `steps` periods solves from x0 = x (cold
+   at the first step unless the handle holds a state, then shifted), applies
+   u_1 for one stage length (each instance's own h; n_sub plant steps).
+   u_hist: NULL or device [steps][sum n_u]; iters_hist, res_hist: NULL or
+   host [steps][n].  Returns the first non-OK solve code met. */
+int nmpc_wave_closed_loop(nmpc_wave* h, double* x, const double* w_ref, const double* u_ref,
+                          int steps, int n_sub, double* u_hist, int* iters_hist,
+                          double* res_hist, void* stream);
+
 /* Free everything (NULL is a no-op).  Synchronizes. */
 void nmpc_wave_destroy(nmpc_wave* h);
 

@@ -34,6 +34,7 @@ constexpr int MAX_NU = 64;
 // shared-memory fields of n_g values in k_wave_dir: float64 grid values and
 // costates, the lower layer's fields in its type T
 constexpr int F64_FIELDS = 4, T_FIELDS = 18;
+constexpr int NG_PER_THREAD = (NMPC_WAVE_MAX_POINTS + THREADS - 1) / THREADS;  // the plant's points
 
 struct WInst {
   int dim, m, ng, nu, N;
@@ -284,6 +285,54 @@ __global__ void __launch_bounds__(THREADS) k_wave_dir(WArgs A, Ctl C, Iter S) {
     S.dl[so + ng + p] = (double)f.Y9[p];
   }
   for (int a = threadIdx.x; a < nu; a += THREADS) S.du[uo + a] = (double)sV3[a];
+}
+
+// The plant (Sec. 5.3): the true system x = (W, V) (device [sum 2 n_g], in
+// place) advances by n_sub symplectic Euler steps of tau = dt / n_sub (dt < 0:
+// each instance's own stage length h) with the inputs at the first-stage
+// values u1 of the current state: V <- V + tau g(W, V, u1), then W <- W + tau
+// V.  One CTA per instance; W, V and the forces in shared memory.
+__global__ void __launch_bounds__(THREADS) k_wave_plant(WArgs A, const Layout* lay, double* x,
+                                                        const double* uc, double dt, int n_sub) {
+  const int b = blockIdx.x;
+  const WInst I = A.inst[b];
+  const Layout Ly = lay[b];
+  const int ng = I.ng;
+  extern __shared__ double smem[];
+  double* W = smem;
+  double* V = W + ng;
+  double* F = V + ng;
+  Stencil<double> L{A.Lc + I.t_off * ELL, A.Ltc + I.t_off * ELL, A.Lv + I.t_off * ELL,
+                    A.Ltv + I.t_off * ELL, A.Ld + I.t_off};
+  const int* act_of = A.act_of + I.t_off;
+  for (int p = threadIdx.x; p < ng; p += THREADS) {
+    W[p] = x[Ly.g_off + p];
+    V[p] = x[Ly.g_off + ng + p];
+    const int ap = act_of[p];
+    F[p] = ap >= 0 ? I.gain * uc[Ly.u_off + ap] : 0.0;
+  }
+  __syncthreads();
+  const double tau = (dt < 0.0 ? I.h : dt) / n_sub, ia = 1.0 / I.a;
+  for (int k = 0; k < n_sub; ++k) {
+    double vn[NG_PER_THREAD];
+    int cnt = 0;
+    for (int p = threadIdx.x; p < ng; p += THREADS, ++cnt) {
+      const double w = W[p];
+      const double g = (I.c * L.lap(W, p) - I.b * V[p] - I.kappa * w * w * w + F[p]) * ia;
+      vn[cnt] = V[p] + tau * g;
+    }
+    __syncthreads();
+    cnt = 0;
+    for (int p = threadIdx.x; p < ng; p += THREADS, ++cnt) {
+      V[p] = vn[cnt];
+      W[p] += tau * vn[cnt];
+    }
+    __syncthreads();
+  }
+  for (int p = threadIdx.x; p < ng; p += THREADS) {
+    x[Ly.g_off + p] = W[p];
+    x[Ly.g_off + ng + p] = V[p];
+  }
 }
 
 }  // namespace wave_dev
@@ -545,6 +594,53 @@ int nmpc_wave_iterate(nmpc_wave* h, const double* x0, const double* w_ref, const
 int nmpc_wave_get_state(nmpc_wave* h, double* x, double* u, double* lam, void* stream) {
   if (!h) return NMPC_ERR_BAD_ARG;
   return stage_drv::get_state(h->drv, x, u, lam, (cudaStream_t)stream);
+}
+
+namespace {
+int plant(nmpc_wave* h, double* x, double dt, int n_sub, void* stream) {
+  wave_dev::k_wave_plant<<<h->drv.n, wave_dev::THREADS, 3 * h->ng_max * sizeof(double),
+                           (cudaStream_t)stream>>>(make_args(h), h->drv.lay, x, h->drv.ub[2], dt,
+                                                   n_sub);
+  SDRV_CHECK(cudaGetLastError());
+  return NMPC_OK;
+}
+}  // namespace
+
+int nmpc_wave_plant_step(nmpc_wave* h, double* x, double dt, int n_sub, void* stream) {
+  if (!h || !x || !(dt >= 0) || n_sub < 1 || !h->drv.has_state) return NMPC_ERR_BAD_ARG;
+  return plant(h, x, dt, n_sub, stream);
+}
+
+int nmpc_wave_closed_loop(nmpc_wave* h, double* x, const double* w_ref, const double* u_ref,
+                          int steps, int n_sub, double* u_hist, int* iters_hist, double* res_hist,
+                          void* stream) {
+  if (!h || !x || !w_ref || !u_ref || steps < 1 || n_sub < 1) return NMPC_ERR_BAD_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = h->drv.n;
+  std::vector<nmpc_stats> stats(n);
+  int rc_all = NMPC_OK;
+  for (int t = 0; t < steps; ++t) {
+    const int init = (t == 0 && !h->drv.has_state) ? NMPC_INIT_COLD : NMPC_INIT_SHIFT;
+    const int rc = nmpc_wave_solve(h, x, w_ref, u_ref, init, nullptr, stats.data(), stream);
+    if (rc == NMPC_ERR_BAD_ARG || rc == NMPC_ERR_CUDA) return rc;
+    if (rc != NMPC_OK && rc_all == NMPC_OK) rc_all = rc;
+    for (int b = 0; b < n; ++b) {
+      if (iters_hist) iters_hist[(size_t)t * n + b] = stats[b].iters;
+      if (res_hist) res_hist[(size_t)t * n + b] = stats[b].res_inf;
+    }
+    if (u_hist) {
+      // u_1 of every instance (stage 1 of the packed control trajectory)
+      for (int b = 0; b < n; ++b) {
+        const WInst& I = h->inst_h[b];
+        SDRV_CHECK(cudaMemcpyAsync(u_hist + (size_t)t * h->n_a + I.a_off,
+                                   h->drv.ub[2] + h->drv.lay_h[b].u_off, I.nu * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, st));
+      }
+    }
+    const int prc = plant(h, x, -1.0, n_sub, stream);  // each instance's own h
+    if (prc != NMPC_OK) return prc;
+  }
+  return rc_all;
 }
 
 void nmpc_wave_destroy(nmpc_wave* h) {

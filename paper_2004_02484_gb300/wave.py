@@ -17,7 +17,8 @@ nmpc_stats = _G.nmpc_stats
 _ptr, _stream, _check = _G._ptr, _G._stream, _G._check
 
 EXPORTED = ["nmpc_wave_default_opts", "nmpc_wave_setup", "nmpc_wave_sizes", "nmpc_wave_solve",
-            "nmpc_wave_iterate", "nmpc_wave_get_state", "nmpc_wave_destroy"]
+            "nmpc_wave_iterate", "nmpc_wave_get_state", "nmpc_wave_plant_step",
+            "nmpc_wave_closed_loop", "nmpc_wave_destroy"]
 
 
 class nmpc_wave_desc(ctypes.Structure):
@@ -45,6 +46,8 @@ _SIG = {
     "nmpc_wave_solve": (_I, [_P, _P, _P, _P, _I, _P, ctypes.POINTER(nmpc_stats), _P]),
     "nmpc_wave_iterate": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I, _P, _P]),
     "nmpc_wave_get_state": (_I, [_P, _P, _P, _P, _P]),
+    "nmpc_wave_plant_step": (_I, [_P, _P, ctypes.c_double, _I, _P]),
+    "nmpc_wave_closed_loop": (_I, [_P, _P, _P, _P, _I, _I, _P, _P, _P, _P]),
     "nmpc_wave_destroy": (None, [_P]),
 }
 for _name, (_res, _args) in _SIG.items():
@@ -131,6 +134,19 @@ class WaveSolver:
         _check(LIB.nmpc_wave_get_state(self.h, _ptr(x), _ptr(u), _ptr(lam), _stream(None)),
                "nmpc_wave_get_state")
         return x, u, lam
+
+    def plant_step(self, x, dt: float, n_sub: int, stream=None):
+        _check(LIB.nmpc_wave_plant_step(self.h, _ptr(x), float(dt), int(n_sub), _stream(stream)),
+               "nmpc_wave_plant_step")
+
+    def closed_loop(self, x, steps: int, n_sub: int, u_hist=None, stream=None):
+        iters = np.zeros((steps, self.n), dtype=np.int32)
+        res = np.zeros((steps, self.n), dtype=np.float64)
+        rc = LIB.nmpc_wave_closed_loop(self.h, _ptr(x), _ptr(self.w_ref), _ptr(self.u_ref), steps,
+                                       n_sub, _ptr(u_hist), iters.ctypes.data, res.ctypes.data,
+                                       _stream(stream))
+        _check(rc, "nmpc_wave_closed_loop", allow=(_G.NMPC_ERR_NOT_CONVERGED, _G.NMPC_ERR_DIVERGED))
+        return rc, iters, res
 
     def close(self):
         if self.h:

@@ -215,3 +215,44 @@ def test_mixed_solve_reaches_the_float64_root(GW, variant):
         assert np.abs(ug - U).max() <= 1e-6 * np.abs(U).max()
         assert abs(its[1][b] - its[0][b]) <= max(2, 0.05 * its[0][b]), (its[0][b], its[1][b])
         ou += N * nu
+
+
+def test_closed_loop_matches_the_oracle(GW):
+    """The receding-horizon use (Sec. 5.3) on a 24-point string, 4 periods,
+    each solve to 1e-9 from the previous solution shifted by one stage, the
+    plant 4 symplectic Euler steps per period: the GPU loop and the oracle's
+    apply the same first-stage inputs and their plants reach the same state."""
+    import torch
+    inst = wl.wave_instance(m=24, horizon=6, T=0.018)
+    steps, nu = 4, len(inst.act)
+    s = GW.WaveSolver([inst], tol=1e-9, max_iter=20000)
+    x = _t(inst.x0)
+    u_hist = torch.zeros(steps * nu, dtype=torch.float64, device="cuda")
+    rc, iters, res = s.closed_loop(x, steps, 4, u_hist)
+    torch.cuda.synchronize()
+    s.close()
+    assert rc == 0 and np.all(res <= 1e-9)
+    us, its, xf = Wv.closed_loop(inst, steps, 4, tol=1e-9)
+    for t in range(steps):
+        assert abs(int(iters[t, 0]) - int(its[t])) <= 1, (t, iters[t, 0], its[t])
+    uh = u_hist.cpu().numpy().reshape(steps, nu)
+    assert np.abs(uh - us).max() <= 1e-7 * np.abs(us).max()
+    assert np.abs(x.cpu().numpy() - xf).max() <= 1e-8 * np.abs(xf).max()
+
+
+def test_plant_step_matches_the_oracle(GW):
+    """One plant call on a membrane (Neumann edges, 3 x 3 point forces) from a
+    solved state: the same symplectic Euler sub-steps as the oracle's."""
+    import torch
+    inst = wl.wave_instance(dim=2, m=12, horizon=4, T=0.012, n_act=3, bc="neumann", seed=5)
+    p = Wv.WaveProblem(inst)
+    s = GW.WaveSolver([inst], tol=1e-8)
+    rc, st = s.solve()
+    assert rc == 0
+    u1 = s.u.cpu().numpy().reshape(inst.horizon, -1)[0]
+    x = _t(inst.x0)
+    s.plant_step(x, 0.01, 7)
+    torch.cuda.synchronize()
+    s.close()
+    xo = Wv.plant_step(p, inst.x0, u1, 0.01, 7)
+    assert np.abs(x.cpu().numpy() - xo).max() <= 1e-12 * max(1.0, np.abs(xo).max())
