@@ -128,12 +128,17 @@ typedef struct {
                       each thread carries its cells through every pass of a
                       work item as independent dependency chains; 0 = auto
                       (4)                                                     */
-  int persistent;  /* 1: when one cluster per stage fits on the device at
-                      once (staged slabs), one launch runs the whole solve
-                      with device-wide barriers between iterations (bounded
-                      waits; a wait that runs out restarts the solve with
-                      one launch per iteration); the iterates are identical
-                      to those of 0: one launch per iteration (default)     */
+  int persistent;  /* 1: one launch runs the whole solve with device-wide
+                      barriers between iterations (bounded waits; a wait
+                      that runs out restarts the solve with one launch per
+                      iteration): on the cluster path when one cluster per
+                      stage fits on the device at once (staged slabs), on
+                      the line path when every stage of the handle is on it
+                      (the resident warps walk the line list every
+                      iteration); Jacobi upper layer only.  The iterates
+                      are identical to those of 0 (one launch per
+                      iteration, the default) on the cluster path, equal to
+                      float32 rounding on the line path                    */
   int strips;       /* 2D instances on the strip path: each warp computes a
                       strip of 32 - 2E own columns (E = 2 n_lo - 1) from a
                       region extended by E cells, walking down its rows with

@@ -50,7 +50,8 @@ struct nmpc_handle {
   double* ub[3] = {nullptr, nullptr, nullptr};
   double* lb[3] = {nullptr, nullptr, nullptr};
   // control
-  int* ictl = nullptr;  // iter_k, closed-loop step, n_active, running line items, grid barrier words [4]
+  int* ictl = nullptr;  // iter_k, closed-loop step, n_active, running line items, grid barrier
+                        // words [4], the persistent line launch's item counters [2]
   unsigned long long* res_inf = nullptr;
   unsigned long long* res_err = nullptr;
   double* res_sq = nullptr;
@@ -111,6 +112,8 @@ struct nmpc_handle {
   int4* lines_act_d = nullptr;  // items of running instances (solve mode)
   int n_lines = 0;
   int line_grid = 0;  // CTAs of a k_line launch
+  bool line_persistent = false;  // one k_line_solve launch runs the whole solve
+  int line_solve_grid = 0;       // its CTAs (all resident at once)
   int n_line_inst = 0;
   size_t line_smem = 0;
   long long launches = 0;
@@ -781,8 +784,15 @@ cudaError_t configure_kernels(size_t smem) {
   cudaError_t e = cudaFuncSetAttribute(nmpc_dev::k_line<false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(nmpc_dev::k_line<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem);
+  e = cudaFuncSetAttribute(nmpc_dev::k_line<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+  if (e != cudaSuccess) return e;
+  // (k_line_solve also has static shared memory: the barrier's code word)
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, nmpc_dev::k_line_solve);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(nmpc_dev::k_line_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(smem - fa.sharedSizeBytes));
 }
 
 // Whether instance I may run on the strip path: 2D, n_lo <= 4, and for
@@ -1043,6 +1053,34 @@ int solve_core(nmpc_handle* h, int horizon, const double* weights, int init, dou
       // on this handle iterates with one launch per iteration
       fprintf(stderr, "nmpc: persistent launch not co-resident; using per-iteration launches\n");
       h->persistent = false;
+      rc0 = start();
+      if (rc0 != NMPC_OK) return rc0;
+    }
+  }
+  if (!done && h->line_persistent) {
+    // the whole solve in one cooperative launch over the line list
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)h->line_solve_grid);
+    cfg.blockDim = dim3(32 * nmpc_dev::LINE_WARPS);
+    cfg.dynamicSmemBytes = h->line_smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, nmpc_dev::k_line_solve, A));
+    h->launches++;
+    h->iter_launches++;
+    CK(cudaMemcpyAsync(h->h_active, h->ictl, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h->h_active[7] == 0) {
+      done = true;
+    } else {
+      // a barrier wait ran out: from now on this handle iterates with one
+      // launch per iteration
+      fprintf(stderr, "nmpc: persistent line launch timed out; using per-iteration launches\n");
+      h->line_persistent = false;
       rc0 = start();
       if (rc0 != NMPC_OK) return rc0;
     }
@@ -1484,6 +1522,21 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
   // one warp per item of the whole list (solve-mode launches past the running
   // items' count return at once)
   h->line_grid = (h->n_lines + nmpc_dev::LINE_WARPS - 1) / nmpc_dev::LINE_WARPS;
+  // persistent line solve (Jacobi, a handle whose stages are all on the line
+  // path): as many CTAs as are resident at once, at most one per four items
+  if (o.persistent && o.variant == NMPC_VARIANT_JACOBI && h->n_lines > 0 && h->n_work == 0 &&
+      h->n_strips == 0) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nmpc_dev::k_line_solve,
+                                                      32 * nmpc_dev::LINE_WARPS,
+                                                      h->line_smem) == cudaSuccess &&
+        per_sm > 0) {
+      h->line_solve_grid = std::min(per_sm * std::max(1, h->num_sms), h->line_grid);
+      h->line_persistent = true;
+    } else {
+      cudaGetLastError();
+    }
+  }
   if (h->n_strips > 0 && two) {
     h->strip2 = true;
     h->strip_x = tx;
@@ -1576,7 +1629,7 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
     A(dev_alloc(&h->lb[q], h->n_s));
     A(dev_alloc(&h->ub[q], h->n_u));
   }
-  A(dev_alloc(&h->ictl, 8));
+  A(dev_alloc(&h->ictl, 10));
   A(dev_alloc(&h->res_inf, (size_t)nmpc_dev::RES_SLOTS * n_instances));
   A(dev_alloc(&h->res_err, (size_t)nmpc_dev::RES_SLOTS * n_instances));
   A(dev_alloc(&h->res_sq, (size_t)nmpc_dev::RES_SLOTS * n_instances));
@@ -1610,7 +1663,7 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
     if (!lines.empty())
       A(cudaMemcpy(h->lines_d, lines.data(), lines.size() * sizeof(int4), cudaMemcpyHostToDevice));
     A(cudaMemcpy(h->act_d, act_all.data(), act_all.size() * sizeof(int), cudaMemcpyHostToDevice));
-    A(cudaMemset(h->ictl, 0, 8 * sizeof(int)));
+    A(cudaMemset(h->ictl, 0, 10 * sizeof(int)));
     A(cudaDeviceSynchronize());
   }
   if (!ok) {
@@ -1910,7 +1963,7 @@ int nmpc_launch_plan(const nmpc_handle* h, int64_t* out) {
   out[1] = h->csize;
   out[2] = h->cpt;
   out[3] = h->stage ? 1 : 0;
-  out[4] = h->persistent ? 1 : 0;
+  out[4] = (h->persistent || h->line_persistent) ? 1 : 0;
   out[5] = (int64_t)h->smem;
   out[6] = h->grid;
   out[7] = h->local_u ? 1 : 0;
@@ -2115,7 +2168,7 @@ extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
     o_l[q] = carve(&off, (size_t)n_s * sizeof(double));
     o_u[q] = carve(&off, (size_t)n_u * sizeof(double));
   }
-  const size_t o_ctl = carve(&off, 8 * sizeof(int));
+  const size_t o_ctl = carve(&off, 10 * sizeof(int));  // the handle's ictl layout
   const size_t o_rinf = carve(&off, nmpc_dev::RES_SLOTS * sizeof(unsigned long long));
   const size_t o_rerr = carve(&off, nmpc_dev::RES_SLOTS * sizeof(unsigned long long));
   const size_t o_rsq = carve(&off, nmpc_dev::RES_SLOTS * sizeof(double));

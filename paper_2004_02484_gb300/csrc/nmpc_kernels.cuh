@@ -1570,6 +1570,8 @@ __global__ void k_init_control(IterArgs A, int mode, int first_full, const doubl
       A.gsync[0] = 0u;  // the barrier generation (gsync[1]) carries on
       A.gsync[2] = 0u;
       A.gsync[3] = 0u;
+      A.gsync[4] = 0u;  // the persistent line launch's item counters
+      A.gsync[5] = 0u;
     }
   }
   if (mode == 1) return;

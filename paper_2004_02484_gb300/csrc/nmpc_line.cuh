@@ -470,3 +470,108 @@ __global__ void __launch_bounds__(COMPACT_THREADS) k_compact_lines(IterArgs A) {
     A.lines_act[i] = make_int4(-1, 0, 0, 0);
   if (threadIdx.x == 0) *A.n_lines_act = base;
 }
+
+// Persistent solve over the line list (Jacobi upper layer): in every
+// iteration k = *iter_k .. max_iter the resident CTAs' warps claim items of
+// the whole list from a per-iteration counter (an item of a finished
+// instance costs one control read), with a grid barrier between iterations
+// (one arrival per CTA; the last arrival clears the next iteration's counter
+// and ends the launch when no instance is running).  Its own inlined copy of
+// the stage body, so its float32 arithmetic may differ from k_line's by the
+// compiler's multiply-add contraction (rounding level).  A barrier wait longer than A.grid_wait cycles raises
+// the error word gsync[3] and ends the launch; the host then restarts the
+// solve with one launch per iteration.  Launched cooperatively with at most
+// the resident number of CTAs.
+constexpr int LINE_CLAIM = 1;  // items per claim of the persistent line launch (larger claims balance worse)
+
+__global__ void __launch_bounds__(LINE_WARPS * 32, 4) k_line_solve(IterArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int bar_code;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  LineShared& ws = *reinterpret_cast<LineShared*>(
+      smem_raw + warp * ((sizeof(LineShared) + 15) & ~size_t(15)));
+  unsigned* ctr = A.gsync + 4;  // item counters, one per iteration parity
+  unsigned gen = 0u;
+  if (threadIdx.x == 0) gen = ld_acquire_u32(&A.gsync[1]);
+  for (int k = *(volatile int*)A.iter_k; k <= A.max_iter; ++k) {
+    const int rd = k & 1;
+    for (;;) {
+      // claim LINE_CLAIM consecutive items; their lanes read the instances'
+      // status at once, and the warp runs the items of running instances
+      int base = 0;
+      if (lane == 0) base = (int)atomicAdd(&ctr[k & 1], (unsigned)LINE_CLAIM);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (base >= A.n_lines) break;
+      int4 mine = make_int4(-1, 0, 0, 0);
+      bool run = false;
+      if (lane < LINE_CLAIM && base + lane < A.n_lines) {
+        mine = A.lines[base + lane];
+        run = __ldcg(A.status + mine.x) == ST_RUNNING;
+      }
+      unsigned m = __ballot_sync(0xffffffffu, run);
+      while (m) {
+        const int l = __ffs(m) - 1;
+        m &= m - 1u;
+        const int b = __shfl_sync(0xffffffffu, mine.x, l);
+        const int s = __shfl_sync(0xffffffffu, mine.y, l);
+        const int cpl = __shfl_sync(0xffffffffu, mine.z, l);
+        int skip = 0, fl = 1;
+        if (lane == 0) {
+          Cl cl;
+          cl.C = 1;
+          cl.rank = 0;  // one warp per stage: stage 0's warp keeps the books
+          control_decision(A, b, s, k, cl, skip, fl);
+        }
+        skip = __shfl_sync(0xffffffffu, skip, 0);
+        fl = __shfl_sync(0xffffffffu, fl, 0);
+        if (skip) continue;
+        const bool resid_only = (k == A.max_iter);
+        if (fl) {
+          switch (cpl) {
+            case 1: line_body<1, true, false>(A, ws, lane, b, s, k, rd, resid_only); break;
+            case 2: line_body<2, true, false>(A, ws, lane, b, s, k, rd, resid_only); break;
+            case 4: line_body<4, true, false>(A, ws, lane, b, s, k, rd, resid_only); break;
+            default: line_body<8, true, false>(A, ws, lane, b, s, k, rd, resid_only); break;
+          }
+        } else {
+          switch (cpl) {
+            case 1: line_body<1, false, false>(A, ws, lane, b, s, k, rd, resid_only); break;
+            case 2: line_body<2, false, false>(A, ws, lane, b, s, k, rd, resid_only); break;
+            case 4: line_body<4, false, false>(A, ws, lane, b, s, k, rd, resid_only); break;
+            default: line_body<8, false, false>(A, ws, lane, b, s, k, rd, resid_only); break;
+          }
+        }
+      }
+    }
+    // grid barrier: the CTA's warps meet (after publishing their global
+    // writes), thread 0 arrives, the last arrival decides whether to stop
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      unsigned* gs = A.gsync;
+      const unsigned target = gen + 1u;
+      if (atomicAdd(&gs[0], 1u) == gridDim.x - 1u) {
+        gs[0] = 0u;
+        ctr[(k + 1) & 1] = 0u;  // every claim of iteration k - 1 is done
+        if (atomicOr(A.n_active, 0) == 0) gs[2] = 1u;
+        __threadfence();
+        atomicExch(&gs[1], target);
+      } else {
+        const long long t0 = clock64();
+        while (ld_acquire_u32(&gs[1]) != target) {
+          if (ld_acquire_u32(&gs[3]) != 0u) break;
+          if (clock64() - t0 > A.grid_wait) {
+            atomicExch(&gs[3], 1u);
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      __threadfence();
+      bar_code = (int)(ld_acquire_u32(&gs[2]) | (ld_acquire_u32(&gs[3]) << 1));
+      gen = target;
+    }
+    __syncthreads();
+    if (bar_code != 0) break;
+  }
+}

@@ -61,7 +61,7 @@ BYTES_PER_CELL_STAGE = 32  # read x, lambda; write x, lambda (float64)
 
 
 def batch1d(n: int, tol: float = 1e-6, reps: int = 3, tune: int = 1, use_graph: int = 1,
-            lines: int = 0):
+            lines: int = 0, persistent: int = 0):
     import torch
     insts = wl.heat1d_ragged_batch(n)
     opts = {}
@@ -71,6 +71,8 @@ def batch1d(n: int, tol: float = 1e-6, reps: int = 3, tune: int = 1, use_graph: 
     kw = dict(opts)
     if lines or "lines" not in kw:
         kw["lines"] = lines  # an explicit choice overrides the tuned one
+    if persistent:
+        kw["persistent"] = 1
     s = G.Solver(insts, tol=tol, precision=G.NMPC_MIXED, max_iter=20000, use_graph=use_graph,
                  **kw)
     rc, st = s.solve()
@@ -86,7 +88,8 @@ def batch1d(n: int, tol: float = 1e-6, reps: int = 3, tune: int = 1, use_graph: 
     out = {"experiment": "batch1d", "instances": n, "s_per_batch": dt, "solves_per_s": n / dt,
            "iters_mean": float(its.mean()), "iters_max": int(its.max()),
            "cell_stages": cells, "launches": G.nmpc_launch_count(s.h), "opts": opts,
-           "line_plan": G.nmpc_line_plan(s.h)}
+           "line_plan": G.nmpc_line_plan(s.h),
+           "persistent": G.nmpc_launch_plan(s.h)["persistent"]}
     s.close()
     return out
 
@@ -400,6 +403,8 @@ def main():
     ap.add_argument("--train-steps", type=int, default=12)
     ap.add_argument("--fit-steps", type=int, default=2000)
     ap.add_argument("--graph", type=int, default=1)
+    ap.add_argument("--persistent", type=int, default=0,
+                    help="batch1d: one launch for the whole solve (line path)")
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--rules", type=int, default=1)
     ap.add_argument("--tune", type=int, default=1)
@@ -433,7 +438,7 @@ def main():
               flush=True)
     elif a.which == "batch1d":
         print(json.dumps(batch1d(a.n or 1024, reps=a.reps, tune=a.tune, use_graph=a.graph,
-                                 lines=a.lines)), flush=True)
+                                 lines=a.lines, persistent=a.persistent)), flush=True)
     elif a.which == "solve":
         print(json.dumps(solve(a.n or 8, a.grid, a.horizon, a.reps, a.graph, strips=a.strips,
                                strip_rows=a.strip_rows, variant=a.variant,
