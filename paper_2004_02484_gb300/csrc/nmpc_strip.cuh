@@ -95,8 +95,13 @@ struct Shift {
 // float64 residual; else the split one): a separate instantiation per form,
 // so neither form's arithmetic is issued in the other's iterations.  RBN:
 // red-black half 1 (the right-hand side takes x_{i-1}, lambda_{i+1} as
-// updated by half 0; the norms stay those of K(S^k)).
-template <typename T, int n_lo, bool FULL, bool RBN>
+// updated by half 0; the norms stay those of K(S^k)).  GSN: red-black half 1
+// in the split form of a solve, where the norms are only the trigger of the
+// float64 residual: x_{i-1}, lambda_{i+1} as updated by half 0 serve both the
+// right-hand side and the norms (the Gauss-Seidel residual K_i of the
+// half-updated iterate), so the values of iterate k at the neighbours are
+// not read.
+template <typename T, int n_lo, bool FULL, bool RBN, bool GSN = false>
 __device__ __forceinline__ void strip_body(const IterArgs& A,
                                            StripShared<strip_ring_rows(n_lo), strip_fields(RBN)>& ws,
                                            int lane, int b, int s, int k, int rd, int x0, int y0,
@@ -161,8 +166,8 @@ __device__ __forceinline__ void strip_body(const IterArgs& A,
   // asynchronous copies of region row rj into its ring slot (zero outside the grid)
   const double* Xg = A.xin[rd] + so;
   const double* Lg = A.lin[rd] + so;
-  const double* XPg = (s == 0) ? A.x0 + I.g_off : A.xin[rd] + so - I.ng;
-  const double* LNg = A.lin[rd] + so + I.ng;
+  const double* XPg = (s == 0) ? A.x0 + I.g_off : (GSN ? A.xout[rd ^ 1] : A.xin[rd]) + so - I.ng;
+  const double* LNg = (GSN ? A.lout[rd ^ 1] : A.lin[rd]) + so + I.ng;
   const double* RFg = A.ref + I.g_off;
   const double* XPNg = (s == 0) ? A.x0 + I.g_off : A.xout[rd ^ 1] + so - I.ng;
   const double* LNNg = A.lout[rd ^ 1] + so + I.ng;
@@ -491,7 +496,9 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32, STRIP_MIN_BLOCKS) k_strip(It
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   using WS = StripShared<strip_ring_rows(n_lo), strip_fields(RBN)>;
-  WS& ws = *reinterpret_cast<WS*>(smem_raw + warp * ((sizeof(WS) + 15) & ~size_t(15)));
+  using WS3 = StripShared<strip_ring_rows(n_lo), strip_fields(false)>;  // fits in WS
+  unsigned char* wbase = smem_raw + warp * ((sizeof(WS) + 15) & ~size_t(15));
+  WS& ws = *reinterpret_cast<WS*>(wbase);
   pdl_trigger();
   const int k = (MODE == MODE_SOLVE) ? *(volatile int*)A.iter_k + launch_iter(A, j_launch) : 0;
   const int half = launch_half(A, j_launch);
@@ -524,6 +531,9 @@ __global__ void __launch_bounds__(STRIP_WARPS * 32, STRIP_MIN_BLOCKS) k_strip(It
   }
   if (full || std::is_same<T, double>::value)
     strip_body<T, n_lo, true, RBN>(A, ws, lane, b, s, k, rd, x0, y0, resid_only);
+  else if (RBN && MODE == MODE_SOLVE)
+    strip_body<T, n_lo, false, false, true>(A, *reinterpret_cast<WS3*>(wbase), lane, b, s, k, rd,
+                                            x0, y0, resid_only);
   else
     strip_body<T, n_lo, false, RBN>(A, ws, lane, b, s, k, rd, x0, y0, resid_only);
 }

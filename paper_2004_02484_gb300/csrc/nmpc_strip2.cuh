@@ -117,7 +117,7 @@ __device__ __forceinline__ void cp_async16_zfill(void* dst_smem, const void* src
                "r"(valid ? 16 : 0));
 }
 
-template <int n_lo, bool FULL, bool RBN>
+template <int n_lo, bool FULL, bool RBN, bool GSN = false>
 __device__ __forceinline__ void strip2_body(const IterArgs& A,
                                             StripShared2<strip_ring_rows(n_lo), strip_fields(RBN)>& ws,
                                             int lane, int b, int s, int k, int rd, int x0, int y0,
@@ -180,8 +180,8 @@ __device__ __forceinline__ void strip2_body(const IterArgs& A,
 
   const double* Xg = A.xin[rd] + so;
   const double* Lg = A.lin[rd] + so;
-  const double* XPg = (s == 0) ? A.x0 + I.g_off : A.xin[rd] + so - I.ng;
-  const double* LNg = A.lin[rd] + so + I.ng;
+  const double* XPg = (s == 0) ? A.x0 + I.g_off : (GSN ? A.xout[rd ^ 1] : A.xin[rd]) + so - I.ng;
+  const double* LNg = (GSN ? A.lout[rd ^ 1] : A.lin[rd]) + so + I.ng;
   const double* RFg = A.ref + I.g_off;
   const double* XPNg = (s == 0) ? A.x0 + I.g_off : A.xout[rd ^ 1] + so - I.ng;
   const double* LNNg = A.lout[rd ^ 1] + so + I.ng;
@@ -519,7 +519,9 @@ __global__ void __launch_bounds__(STRIP2_WARPS * 32, STRIP2_MIN_BLOCKS)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   using WS = StripShared2<strip_ring_rows(n_lo), strip_fields(RBN)>;
-  WS& ws = *reinterpret_cast<WS*>(smem_raw + warp * ((sizeof(WS) + 15) & ~size_t(15)));
+  using WS3 = StripShared2<strip_ring_rows(n_lo), strip_fields(false)>;  // fits in WS
+  unsigned char* wbase = smem_raw + warp * ((sizeof(WS) + 15) & ~size_t(15));
+  WS& ws = *reinterpret_cast<WS*>(wbase);
   pdl_trigger();
   const int k = (MODE == MODE_SOLVE) ? *(volatile int*)A.iter_k + launch_iter(A, j_launch) : 0;
   const int half = launch_half(A, j_launch);
@@ -552,6 +554,9 @@ __global__ void __launch_bounds__(STRIP2_WARPS * 32, STRIP2_MIN_BLOCKS)
   }
   if (full)
     strip2_body<n_lo, true, RBN>(A, ws, lane, b, s, k, rd, x0, y0, resid_only);
+  else if (RBN && MODE == MODE_SOLVE)
+    strip2_body<n_lo, false, false, true>(A, *reinterpret_cast<WS3*>(wbase), lane, b, s, k, rd,
+                                          x0, y0, resid_only);
   else
     strip2_body<n_lo, false, RBN>(A, ws, lane, b, s, k, rd, x0, y0, resid_only);
 }
