@@ -162,8 +162,13 @@ typedef struct {
                       2 = never (cluster path)                              */
   int variant;      /* NMPC_VARIANT_JACOBI (default) or NMPC_VARIANT_REDBLACK:
                       two stage-parallel launches per iteration (half 0: even
-                      stages, half 1: odd stages); the convergence test still
-                      uses ||K(S^k)||_inf of whole iterates.  Requires
+                      stages, half 1: odd stages); convergence is still
+                      declared on the float64 ||K(S^k)||_inf of whole
+                      iterates.  On the strip path the NMPC_MIXED split-form
+                      iterations before it (whose norms only trigger the
+                      float64 residual) take at odd stages the Gauss-Seidel
+                      residual, K_i with the neighbours updated by half 0;
+                      nmpc_iterate keeps the norms of K(S^k).  Requires
                       alpha = 1 (BAD_ARG otherwise) and never runs the
                       persistent launch                                     */
   int64_t barrier_wait_cycles; /* persistent launch: spin budget of one grid-
