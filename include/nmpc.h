@@ -111,11 +111,17 @@ typedef struct {
                       splits the stage grid); 0 = auto                        */
   double split_min;/* NMPC_MIXED: iterations evaluate K with float64
                       differences and float32 O(h) terms (the split residual,
-                      with a computed bound e on its rounding error) while the
-                      previous split residual r has r - e > max(tol,
-                      split_min); from then on every iteration uses the
-                      float64 residual (convergence is only ever declared on
-                      a float64 residual).  Handles with strip-path instances
+                      with a computed bound e on its rounding error); the
+                      float64 residual is evaluated in the iteration after
+                      one whose residual r (split or float64) was at or
+                      below T = max(tol, split_min), or after a split
+                      residual with r - e <= T that is no lower than 12
+                      iterations before (its rounding floor above T).  A
+                      float64 residual above T hands back to the split
+                      residual when the split residual had itself reached T
+                      or it was iteration 0's; otherwise the float64
+                      residual stays.  Convergence is only ever declared on
+                      a float64 residual.  Handles with strip-path instances
                       use max(split_min, 1e-6): their split residual takes
                       the stage differences from float32 values        */
   int u_local;     /* 1: the u-iteration uses the actuators' local responses
@@ -190,6 +196,8 @@ typedef struct {
   int status;     /* NMPC_STATUS_*                                            */
   double res_inf; /* ||K(S^k)||_inf (float64)                                 */
   double res_2;   /* ||K(S^k)||_2                                             */
+  int f64_iters;  /* iterations 0..k that evaluated the float64 residual (every
+                     one in NMPC_FP64; in NMPC_MIXED see split_min)         */
 } nmpc_stats;
 
 typedef struct nmpc_handle nmpc_handle;

@@ -61,7 +61,7 @@ struct nmpc_handle {
   int* final_buf = nullptr;
   double* fin_inf = nullptr;
   double* fin_2 = nullptr;
-  int* full_from = nullptr;
+  int* f64_count = nullptr;
   int* full0 = nullptr;
   char* scratch = nullptr;
   long long scratch_stride = 0;
@@ -69,6 +69,7 @@ struct nmpc_handle {
   int* h_active = nullptr;
   int* h_status = nullptr;
   int* h_iters = nullptr;
+  int* h_f64 = nullptr;     // float64-residual iterations per instance
   double* h_fin = nullptr;  // [2][n]
   double* h_res = nullptr;  // [2][n] for residual readback
   unsigned long long* h_resinf = nullptr;
@@ -167,11 +168,11 @@ void free_all(nmpc_handle* h) {
                   h->xb[0], h->xb[1], h->xb[2], h->ub[0], h->ub[1], h->ub[2],
                   h->lb[0], h->lb[1], h->lb[2], h->ictl, h->res_inf, h->res_err, h->res_sq,
                   h->res_first, h->status, h->iters, h->final_buf, h->fin_inf,
-                  h->fin_2, h->full_from, h->full0, h->scratch, h->strips_d, h->patches_d, h->lines_d, h->lines_act_d,
+                  h->fin_2, h->f64_count, h->full0, h->scratch, h->strips_d, h->patches_d, h->lines_d, h->lines_act_d,
                   h->v3_d};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  void* hp[] = {h->h_active, h->h_status, h->h_iters, h->h_fin, h->h_res, h->h_resinf};
+  void* hp[] = {h->h_active, h->h_status, h->h_iters, h->h_f64, h->h_fin, h->h_res, h->h_resinf};
   for (void* p : hp)
     if (p) cudaFreeHost(p);
 }
@@ -224,7 +225,7 @@ IterArgs make_args(nmpc_handle* h) {
   A.grid_wait = h->opts.barrier_wait_cycles > 0 ? (long long)h->opts.barrier_wait_cycles
                                                 : nmpc_dev::GRID_WAIT_CYCLES;
   A.resid_only = 0;
-  A.full_from = h->full_from;
+  A.f64_count = h->f64_count;
   A.full0 = h->full0;
   A.full_all = h->mixed ? 0 : 1;
   A.csize = h->csize;
@@ -1113,6 +1114,7 @@ int solve_core(nmpc_handle* h, int horizon, const double* weights, int init, dou
   const int n = h->n_inst;
   CK(cudaMemcpyAsync(h->h_status, h->status, n * sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(h->h_iters, h->iters, n * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h->h_f64, h->f64_count, n * sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(h->h_fin, h->fin_inf, n * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(h->h_fin + n, h->fin_2, n * sizeof(double), cudaMemcpyDeviceToHost, st));
   if (loop_graph)
@@ -1131,6 +1133,7 @@ int solve_core(nmpc_handle* h, int horizon, const double* weights, int init, dou
       stats[b].iters = h->h_iters[b];
       stats[b].res_inf = h->h_fin[b];
       stats[b].res_2 = h->h_fin[n + b];
+      stats[b].f64_iters = h->h_f64[b];
     }
     if (rc == NMPC_OK) {
       if (h->h_status[b] == nmpc_dev::ST_DIVERGED) rc = NMPC_ERR_DIVERGED;
@@ -1633,7 +1636,7 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
   A(dev_alloc(&h->res_inf, (size_t)nmpc_dev::RES_SLOTS * n_instances));
   A(dev_alloc(&h->res_err, (size_t)nmpc_dev::RES_SLOTS * n_instances));
   A(dev_alloc(&h->res_sq, (size_t)nmpc_dev::RES_SLOTS * n_instances));
-  A(dev_alloc(&h->full_from, n_instances));
+  A(dev_alloc(&h->f64_count, n_instances));
   A(dev_alloc(&h->full0, n_instances));
   A(dev_alloc(&h->res_first, n_instances));
   A(dev_alloc(&h->status, n_instances));
@@ -1648,6 +1651,7 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
   A(cudaMallocHost((void**)&h->h_active, 8 * sizeof(int)));
   A(cudaMallocHost((void**)&h->h_status, n_instances * sizeof(int)));
   A(cudaMallocHost((void**)&h->h_iters, n_instances * sizeof(int)));
+  A(cudaMallocHost((void**)&h->h_f64, n_instances * sizeof(int)));
   A(cudaMallocHost((void**)&h->h_fin, 2 * n_instances * sizeof(double)));
   A(cudaMallocHost((void**)&h->h_res, 2 * n_instances * sizeof(double)));
   A(cudaMallocHost((void**)&h->h_resinf, n_instances * sizeof(unsigned long long)));
@@ -2172,7 +2176,7 @@ extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
   const size_t o_rinf = carve(&off, nmpc_dev::RES_SLOTS * sizeof(unsigned long long));
   const size_t o_rerr = carve(&off, nmpc_dev::RES_SLOTS * sizeof(unsigned long long));
   const size_t o_rsq = carve(&off, nmpc_dev::RES_SLOTS * sizeof(double));
-  const size_t o_ffrom = carve(&off, 2 * sizeof(int));  // full_from, full0
+  const size_t o_f64 = carve(&off, 2 * sizeof(int));  // f64_count, full0
   const size_t o_rfirst = carve(&off, sizeof(unsigned long long));
   const size_t o_status = carve(&off, 3 * sizeof(int));  // status, iters, final_buf
   const size_t o_fin = carve(&off, 2 * sizeof(double));  // fin_inf, fin_2
@@ -2235,8 +2239,8 @@ extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
   A.n_lo = o.n_lo;
   A.n_u_it = o.n_u_it;
   A.resid_only = 0;
-  A.full_from = reinterpret_cast<int*>(base + o_ffrom);
-  A.full0 = A.full_from + 1;
+  A.f64_count = reinterpret_cast<int*>(base + o_f64);
+  A.full0 = A.f64_count + 1;
   A.full_all = mixed ? 0 : 1;
   A.csize = P.csize;
   A.slab_max = P.slab_max;
@@ -2290,8 +2294,10 @@ extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
   nmpc_dev::k_gather_final<<<dim3(64, 1), 256, 0, st>>>(F);
   CK(cudaGetLastError());
   int h_stat[3] = {0, 0, 0};
+  int h_f64 = 0;
   double h_fin[2] = {0.0, 0.0};
   CK(cudaMemcpyAsync(h_stat, stat, sizeof(h_stat), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&h_f64, A.f64_count, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(h_fin, fin, sizeof(h_fin), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (stats) {
@@ -2299,6 +2305,7 @@ extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
     stats->iters = h_stat[1];
     stats->res_inf = h_fin[0];
     stats->res_2 = h_fin[1];
+    stats->f64_iters = h_f64;
   }
   if (h_stat[0] == nmpc_dev::ST_DIVERGED) return NMPC_ERR_DIVERGED;
   if (h_stat[0] != nmpc_dev::ST_CONVERGED) return NMPC_ERR_NOT_CONVERGED;

@@ -35,6 +35,14 @@ namespace nmpc_dev {
 namespace cg = cooperative_groups;
 
 constexpr int RES_SLOTS = 16;    // rolling residual history per instance
+// iterations over which a split residual r with r - e <= threshold (e its
+// rounding bound) that has not decreased hands over to the float64 residual
+// although r itself stays above the threshold (its rounding floor)
+constexpr int SPLIT_PATIENCE = 12;
+static_assert(SPLIT_PATIENCE + 2 < RES_SLOTS, "history slots read by decide()");
+// res_err of an iteration that evaluated the float64 residual (above the bits
+// of every non-negative double or NaN, so atomicMax keeps it)
+constexpr unsigned long long RES_FULL_MARK = 0xfff0000000000000ull;
 constexpr int MAX_NU = 64;
 
 struct InstDev {
@@ -98,8 +106,8 @@ struct IterArgs {
   int* final_buf;
   double* fin_inf;
   double* fin_2;
-  int* full_from;  // [n_inst] first iteration evaluated with the float64 residual
-  int* full0;      // [n_inst] 1: iteration 0 also uses it (warm starts)
+  int* f64_count;  // [n_inst] iterations that evaluated the float64 residual
+  int* full0;      // [n_inst] 1: iteration 0 does (warm starts)
   int* n_active;
   // persistent launch: [0] barrier arrivals, [1] barrier generation, [2] stop
   // (no instance running), [3] a wait ran out of time
@@ -547,15 +555,14 @@ __device__ __forceinline__ bool stage_in_half(const IterArgs& A, int s, int half
 // residual is evaluated in float64.  Control words are read around L1 (other
 // CTAs write them within a persistent launch).
 struct Decision {
-  int skip, full, before, st, pslot, ffrom;
+  int skip, full, before, st, pslot;
   double r;
 };
 
 __device__ __forceinline__ Decision decide(const IterArgs& A, int b, int k) {
-  Decision d{0, 1, 0, ST_RUNNING, (k > 0) ? ((k - 1) % RES_SLOTS) * A.n_inst + b : 0, 0, 0.0};
+  Decision d{0, 1, 0, ST_RUNNING, (k > 0) ? ((k - 1) % RES_SLOTS) * A.n_inst + b : 0, 0.0};
   // every control word the decision reads, loaded at once
   const int status_b = __ldcg(A.status + b);
-  d.ffrom = __ldcg(A.full_from + b);
   const int f0 = __ldcg(A.full0 + b);
   const unsigned long long r_bits = __ldcg(A.res_inf + d.pslot);
   const unsigned long long r0_bits = __ldcg(A.res_first + b);
@@ -569,28 +576,52 @@ __device__ __forceinline__ Decision decide(const IterArgs& A, int b, int k) {
   if (k > 0) {
     d.r = __longlong_as_double((long long)r_bits);
     const double r0 = __longlong_as_double((long long)r0_bits);
-    const bool prev_full = (k - 1 >= d.ffrom) || (k == 1 && f0);
-    if (!(d.r <= 1.79e308) || d.r > A.div_limit * fmax(r0, 1e-300)) d.st = ST_DIVERGED;
-    else if (prev_full && d.r <= A.tol) d.st = ST_CONVERGED;
-    else if (!prev_full) {
-      // leave the split residual once it can no longer show that the float64
-      // residual is above the threshold: r minus its rounding bound at or
-      // below max(tol, split_min)
-      const double e = __longlong_as_double((long long)e_bits);
-      if (d.r - e <= fmax(A.tol, A.split_min)) switch_now = true;
+    const bool prev_full = e_bits == RES_FULL_MARK;
+    if (!(d.r <= 1.79e308) || d.r > A.div_limit * fmax(r0, 1e-300)) {
+      d.st = ST_DIVERGED;
+    } else if (prev_full && d.r <= A.tol) {
+      d.st = ST_CONVERGED;
+    } else {
+      // evaluate the float64 residual of S^k once r (split or float64) is at
+      // or below T = max(tol, split_min): it is then expected at or below T
+      // (or the split residual could not resolve it).  A float64 residual
+      // above T hands back to the split residual where the split residual
+      // itself had reached T (the iterates' residual rose again) or the
+      // float64 one was iteration 0's; a float64 phase that began on the
+      // split residual's rounding floor or has lasted longer stays.  The
+      // floor: a split residual with r - e <= T (it can no longer show that
+      // the float64 residual is above T) and no lower than SPLIT_PATIENCE
+      // iterations before.
+      const double T = fmax(A.tol, A.split_min);
+      if (d.r <= T) {
+        switch_now = true;
+      } else if (prev_full) {
+        if (k >= 2) {
+          const int sl = ((k - 2) % RES_SLOTS) * A.n_inst + b;
+          const unsigned long long e2 = __ldcg(A.res_err + sl);
+          const double r2 = __longlong_as_double((long long)__ldcg(A.res_inf + sl));
+          switch_now = e2 == RES_FULL_MARK || !(r2 <= T);
+        }
+      } else {
+        const double e = __longlong_as_double((long long)e_bits);
+        if (d.r - e <= T && k - 1 - SPLIT_PATIENCE >= 0) {
+          const int sl = ((k - 1 - SPLIT_PATIENCE) % RES_SLOTS) * A.n_inst + b;
+          switch_now = d.r >= __longlong_as_double((long long)__ldcg(A.res_inf + sl));
+        }
+      }
     }
   }
   if (d.st != ST_RUNNING) {
     d.skip = 1;
   } else {
-    d.full = (A.full_all || k >= d.ffrom || switch_now || k == A.max_iter || (k == 0 && f0)) ? 1 : 0;
+    d.full = (A.full_all || switch_now || k == A.max_iter || (k == 0 && f0)) ? 1 : 0;
   }
   return d;
 }
 
 // decide() for work item (b, s), taken by one thread; the CTA of stage 0,
 // cluster rank 0 keeps the books: it records a finished instance (status,
-// returned iterate k - 1), the first float64-residual iteration, and clears
+// returned iterate k - 1), counts the float64-residual iterations, and clears
 // the residual slot of iteration k + 1.
 __device__ __noinline__ void control_decision(const IterArgs& A, int b, int s, int k, const Cl& cl,
                                               int& skip_out, int& full_out) {
@@ -604,7 +635,7 @@ __device__ __noinline__ void control_decision(const IterArgs& A, int b, int s, i
       A.fin_2[b] = sqrt(__ldcg(A.res_sq + d.pslot));
       atomicSub(A.n_active, 1);
     } else {
-      if (d.full && d.ffrom > k) A.full_from[b] = k;
+      if (d.full) A.f64_count[b] += 1;
       const int nslot = ((k + 1) % RES_SLOTS) * A.n_inst + b;
       A.res_inf[nslot] = 0ull;
       A.res_err[nslot] = 0ull;
@@ -650,10 +681,11 @@ __device__ __forceinline__ double split_bound(const InstDev& I, bool last, const
 }
 
 // Residual norms of a work item (max, sum of squares) and, for the split
-// residual, its rounding bound, into iteration k's slot of instance b.
+// residual, its rounding bound (else RES_FULL_MARK), into iteration k's slot of
+// instance b.
 __device__ __forceinline__ void publish_residual(const IterArgs& A, int slot, int b, int k,
                                                  double rmax, double rsq, double e, bool full) {
-  if (!full) atomicMax(&A.res_err[slot], (unsigned long long)__double_as_longlong(e));
+  atomicMax(&A.res_err[slot], full ? RES_FULL_MARK : (unsigned long long)__double_as_longlong(e));
   atomicMax(&A.res_inf[slot], (unsigned long long)__double_as_longlong(rmax));
   atomicAdd(&A.res_sq[slot], rsq);
   if (k == 0 && A.res_first)
@@ -1562,7 +1594,7 @@ __global__ void k_init_control(IterArgs A, int mode, int first_full, const doubl
     A.final_buf[b] = 0;
     A.fin_inf[b] = 0.0;
     A.fin_2[b] = 0.0;
-    A.full_from[b] = A.full_all ? 0 : 0x7fffffff;
+    A.f64_count[b] = 0;
     A.full0[b] = first_full;
     if (b == 0) {
       *A.n_active = A.n_inst;

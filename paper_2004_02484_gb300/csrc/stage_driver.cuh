@@ -394,6 +394,7 @@ int solve(Driver& d, int init, int max_iter, double tol, int check_every, Dir& d
       stats[b].iters = iters[b];
       stats[b].res_inf = fin[b];
       stats[b].res_2 = fin[d.n + b];
+      stats[b].f64_iters = iters[b] + 1;  // every residual is evaluated in float64
     }
     if (rc == NMPC_OK) {
       if (status[b] == ST_DIVERGED) rc = NMPC_ERR_DIVERGED;

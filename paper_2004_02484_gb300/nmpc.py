@@ -60,7 +60,8 @@ class nmpc_opts(ctypes.Structure):
 
 class nmpc_stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int),
-                ("res_inf", ctypes.c_double), ("res_2", ctypes.c_double)]
+                ("res_inf", ctypes.c_double), ("res_2", ctypes.c_double),
+                ("f64_iters", ctypes.c_int)]
 
 
 EXPORTED = ["nmpc_default_opts", "nmpc_setup", "nmpc_solve", "nmpc_solve_host",

@@ -349,6 +349,40 @@ def test_mixed_solve_certifies_with_a_float64_residual(G, cluster):
     s.close()
 
 
+# (instances, options, most float64-residual iterations per solve): the
+# red-black iterates of the 32x32 instance and of one 1D instance first reach
+# ||K|| ~ 0.98e-6, then dwell at 1.0-1.2e-6 for several iterations, which the
+# split residual waits out
+SWITCH_CASES = {
+    "cluster_2d": (lambda: [wl.heat2d(32, 32, 20, 4, 2, seed=40)], {}, 3),
+    "line_1d": (lambda: wl.heat1d_ragged_batch(8), {}, 3),
+    "strip_2d": (lambda: [wl.heat2d(40, 30, 12, 2, 2, seed=3)], dict(strips=1, strip_rows=8), 3),
+}
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("case", list(SWITCH_CASES))
+def test_float64_residual_iterations_are_counted_and_few(G, case, variant):
+    """nmpc_stats.f64_iters counts the iterations that evaluated the float64
+    residual: all of them in FP64; in MIXED only those after a residual at or
+    below the threshold (a float64 residual above it hands back to the split
+    residual), so with tol above the split residual's rounding floor a solve
+    takes a few."""
+    mk, opts, most = SWITCH_CASES[case]
+    insts = mk()
+    s = G.Solver(insts, tol=1e-6, precision=G.NMPC_FP64, variant=variant, max_iter=4000, **opts)
+    rc, st = s.solve()
+    s.close()
+    assert rc == G.NMPC_OK and all(s_.f64_iters == s_.iters + 1 for s_ in st)
+    s = G.Solver(insts, tol=1e-6, precision=G.NMPC_MIXED, variant=variant, max_iter=4000, **opts)
+    rc, st = s.solve()
+    s.close()
+    assert rc == G.NMPC_OK
+    for s_ in st:
+        assert 1 <= s_.f64_iters <= most, (s_.iters, s_.f64_iters)
+        assert s_.res_inf <= 1e-6
+
+
 def test_mixed_reaches_tight_tolerance_above_the_split_floor(G):
     """1D M=256, h=1e-4: the split residual's float32 floor (~1e-7) is above
     tol = 1e-8; the solve must switch to the float64 residual and converge to
