@@ -62,7 +62,8 @@ WORKLOAD_2 = ("heat2d_64x64_N50: 64x64 grid, dt=2e-5, N=50, 8 actuators (2x4), s
 TOL = 1e-6
 N_INST = 64
 N_SUB = 2          # explicit-Euler plant sub-steps per sampling period
-TRAIN_STEPS = 12   # closed-loop steps of the training instances (768 samples)
+TRAIN_STEPS = 12   # closed-loop steps of the training instances
+TRAIN_BATCHES = 4  # batches of training instances (4 x 64 instances: 3072 samples)
 FIT_STEPS = 1500   # Adam steps of the learned start
 # algorithmic bytes per cell-stage per iteration: read x_i, lambda_i and write
 # them back in float64 (the neighbour-stage reads are the same arrays)
@@ -238,9 +239,12 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
-def batch(args, rank, train=False):
+def batch(args, rank, train=False, part=0):
+    """The rank's test batch, or part `part` of its training instances (seeds
+    following one another from the training base)."""
     from paper_2004_02484_gb300 import workloads as wl
-    return wl.heat2d_large_batch(n=args.instances, base_seed=batch_seed(rank, train),
+    return wl.heat2d_large_batch(n=args.instances,
+                                 base_seed=batch_seed(rank, train) + part * args.instances,
                                  m=args.grid, horizon=args.horizon)
 
 
@@ -385,15 +389,19 @@ def main():
     from paper_2004_02484_gb300 import warmstart as WS
     dev = torch.device("cuda", local)
     opts = solver_opts(args)
-    test, train = batch(args, rank), batch(args, rank, train=True)
+    test = batch(args, rank)
+    train = [batch(args, rank, train=True, part=q) for q in range(TRAIN_BATCHES)]
     K, W, B = args.steps, args.warmup, len(test)
     ng, N = test[0].mx * test[0].my, test[0].horizon
     nu = len(test[0].act)
 
     # ---- learned start: trained on plain closed loops of other instances ----
     t0 = time.perf_counter()
-    X, U = WS.closed_loop_data(train, TRAIN_STEPS, N_SUB)
-    lcs = WS.LearnedControlStart(train[0], max_batch=max(256, B))
+    # plain closed loops of the training instances, one batch at a time
+    data = [WS.closed_loop_data(tb, TRAIN_STEPS, N_SUB) for tb in train]
+    X, U = np.concatenate([d[0] for d in data]), np.concatenate([d[1] for d in data])
+    del data
+    lcs = WS.LearnedControlStart(train[0][0], max_batch=max(256, B))
     losses = lcs.fit(X, U, steps=FIT_STEPS)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
@@ -591,7 +599,7 @@ def main():
                           "variant": args.variant, "n_sub_plant": N_SUB,
                           "solves_per_step": B, "timed_from": "the loop's first step",
                           "l2": "state of 6.7 GB per iterate, far larger than L2 (no flush)",
-                          "learned_start": {"train_instances": len(train),
+                          "learned_start": {"train_instances": sum(len(tb) for tb in train),
                                             "train_samples": int(X.shape[0]),
                                             "fit_steps": FIT_STEPS, "train_s": t_train,
                                             "loss_first": losses[0], "loss_last": losses[-1],

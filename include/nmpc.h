@@ -305,7 +305,9 @@ int nmpc_start_state(nmpc_handle* h, int init, const double* x0, double* x, doub
    taken at the later stage).  Written to device x, lam [sum N*ng]: a start
    consistent with u to O(h^2) per stage for NMPC_INIT_GUESS (no counterpart
    in the paper; it completes a control-only guess such as a learned one).
-   2 N launches; NMPC_ERR_BAD_ARG for a NULL array. */
+   Float64 arithmetic on NMPC_FP64 handles; float32 arithmetic from the
+   float64 inputs truncated to float32 (stores float64) on NMPC_MIXED ones,
+   for start guesses.  2 N launches; NMPC_ERR_BAD_ARG for a NULL array. */
 int nmpc_rollout(nmpc_handle* h, const double* x0, const double* ref, const double* u, double* x,
                  double* lam, void* stream);
 

@@ -1193,14 +1193,16 @@ cudaError_t enqueue_rollout(nmpc_handle* h, const double* x0, const double* ref,
                             double* x, double* lam, cudaStream_t st) {
   int nmax = 0;
   for (const InstDev& I : h->inst_h) nmax = std::max(nmax, I.N);
+  // float32 arithmetic on NMPC_MIXED handles (a start guess), else float64
+  const auto ks = h->mixed ? nmpc_dev::k_rollout_state<float> : nmpc_dev::k_rollout_state<double>;
+  const auto kc =
+      h->mixed ? nmpc_dev::k_rollout_costate<float> : nmpc_dev::k_rollout_costate<double>;
   for (int i = 0; i < nmax; ++i) {
-    nmpc_dev::k_rollout_state<<<per_instance_grid(h), 256, 0, st>>>(h->inst_d, h->n_inst, h->act_d,
-                                                                    x0, u, x, i);
+    ks<<<per_instance_grid(h), 256, 0, st>>>(h->inst_d, h->n_inst, h->act_d, x0, u, x, i);
     h->launches++;
   }
   for (int i = 0; i < nmax; ++i) {
-    nmpc_dev::k_rollout_costate<<<per_instance_grid(h), 256, 0, st>>>(h->inst_d, h->n_inst, ref, x,
-                                                                      lam, i);
+    kc<<<per_instance_grid(h), 256, 0, st>>>(h->inst_d, h->n_inst, ref, x, lam, i);
     h->launches++;
   }
   return cudaGetLastError();

@@ -1767,38 +1767,66 @@ __global__ void k_shift_state(const InstDev* inst, int n_inst, const double* xc,
   }
 }
 
+// Arithmetic of the per-stage rollout: float64, or float32 from truncated
+// values (d2f) with exact widening of the result (f2d) for start guesses.
+__device__ __forceinline__ double ro_ld(double v, double) { return v; }
+__device__ __forceinline__ float ro_ld(double v, float) { return d2f(v); }
+__device__ __forceinline__ double ro_st(double v) { return v; }
+__device__ __forceinline__ double ro_st(float v) { return f2d(v); }
+
 // Trajectory of a control guess, one stage per launch for every instance
 // (instances with N <= i skip).  State, forward: x_i = x_{i-1} + h (Lap Phi
-// (x_{i-1}) + b0 B u_i), x_{-1} = x0 (the model of eq. 6 stepped explicitly).
+// (x_{i-1}) + b0 B u_i), x_{-1} = x0 (the model of eq. 6 stepped explicitly),
+// stage i in arithmetic T over cells c = t, t + stride, ... (t the thread's
+// index in the instance's grid).  Each thread looks up once which actuators
+// sit on its cells (a bit per actuator, n_u <= 64) instead of scanning them
+// per cell.
+template <typename T>
 __global__ void k_rollout_state(const InstDev* inst, int n_inst, const int* act, const double* x0,
                                 const double* u, double* x, int i) {
   const int b = blockIdx.y;
   if (b >= n_inst) return;
-  const InstDev I = inst[b];
+  const InstDev& I = inst[b];
   if (i >= I.N) return;
   const double* src = (i == 0) ? x0 + I.g_off : x + I.s_off + (long long)(i - 1) * I.ng;
   double* dst = x + I.s_off + (long long)i * I.ng;
   const double* ui = u + I.u_off + (long long)i * I.nu;
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < I.ng; c += gridDim.x * blockDim.x) {
-    const int ix = c % I.mx, iy = c / I.mx;
-    double srcu = 0.0;
-    for (int a = 0; a < I.nu; ++a)
-      if (act[I.act_off + a] == c) srcu += ui[a];
-    const double lphi = nbr_sum<double>(c, ix, iy, I.mx, I.my, I.cx, I.cy,
-                                        [&](int m) { return phi_d(src[m], I.k0, I.k1); }) -
-                        I.dcoef * phi_d(src[c], I.k0, I.k1);
-    dst[c] = src[c] + I.h * (lphi + I.b0 * srcu);
+  const int* ab = act + I.act_off;
+  const int stride = gridDim.x * blockDim.x, t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nu = I.nu, mx = I.mx, my = I.my, ng = I.ng;
+  unsigned long long own = 0ull;
+  for (int a = 0; a < nu; ++a)
+    if (ab[a] % stride == t) own |= 1ull << a;
+  const T z = T(0);
+  const T k0 = (T)I.k0, k1h = (T)(0.5 * I.k1), cx = (T)I.cx, cy = (T)I.cy, dc = (T)I.dcoef;
+  const T h = (T)I.h, b0 = (T)I.b0;
+  const float inv_mx = 1.0f / (float)mx;
+  auto phi = [&](int m) {
+    const T w = ro_ld(src[m], z);
+    return k0 * (w + k1h * w * w);
+  };
+  for (int c = t; c < ng; c += stride) {
+    const int iy = fdiv(c, mx, inv_mx), ix = c - iy * mx;
+    T srcu = z;
+    for (unsigned long long m = own; m; m &= m - 1) {
+      const int a = __ffsll((long long)m) - 1;
+      if (ab[a] == c) srcu += ro_ld(ui[a], z);
+    }
+    const T lphi = nbr_sum<T>(c, ix, iy, mx, my, cx, cy, phi) - dc * phi(c);
+    dst[c] = ro_st(ro_ld(src[c], z) + h * (lphi + b0 * srcu));
   }
 }
 
 // Costate, backward from lambda_{N+1} = h qf (x_N - ref): the costate rows of
 // eq. 9 with the coupling term taken at the later stage,
-// lambda_i = lambda_{i+1} + h (q (x_i - ref) + Phi'(x_i) Lap lambda_{i+1}).
+// lambda_i = lambda_{i+1} + h (q (x_i - ref) + Phi'(x_i) Lap lambda_{i+1}),
+// in arithmetic T.
+template <typename T>
 __global__ void k_rollout_costate(const InstDev* inst, int n_inst, const double* ref,
                                   const double* x, double* lam, int i_from_end) {
   const int b = blockIdx.y;
   if (b >= n_inst) return;
-  const InstDev I = inst[b];
+  const InstDev& I = inst[b];
   const int i = I.N - 1 - i_from_end;
   if (i < 0) return;
   const double* xi = x + I.s_off + (long long)i * I.ng;
@@ -1807,12 +1835,21 @@ __global__ void k_rollout_costate(const InstDev* inst, int n_inst, const double*
   double* li = lam + I.s_off + (long long)i * I.ng;
   const bool last = (i == I.N - 1);
   const double* xN = x + I.s_off + (long long)(I.N - 1) * I.ng;
-  auto next = [&](int m) { return last ? I.hqf * (xN[m] - r[m]) : ln[m]; };
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < I.ng; c += gridDim.x * blockDim.x) {
-    const int ix = c % I.mx, iy = c / I.mx;
-    const double lap = nbr_sum<double>(c, ix, iy, I.mx, I.my, I.cx, I.cy, next) - I.dcoef * next(c);
-    const double dphi = I.k0 * (1.0 + I.k1 * xi[c]);
-    li[c] = next(c) + I.h * (I.q * (xi[c] - r[c]) + dphi * lap);
+  const T z = T(0);
+  const T hqf = (T)I.hqf, k0 = (T)I.k0, k1 = (T)I.k1, cx = (T)I.cx, cy = (T)I.cy;
+  const T dc = (T)I.dcoef, h = (T)I.h, q = (T)I.q;
+  const int mx = I.mx, my = I.my, ng = I.ng;
+  const float inv_mx = 1.0f / (float)mx;
+  auto next = [&](int m) {
+    return last ? hqf * (ro_ld(xN[m], z) - ro_ld(r[m], z)) : ro_ld(ln[m], z);
+  };
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ng; c += gridDim.x * blockDim.x) {
+    const int iy = fdiv(c, mx, inv_mx), ix = c - iy * mx;
+    const T nc = next(c);
+    const T lap = nbr_sum<T>(c, ix, iy, mx, my, cx, cy, next) - dc * nc;
+    const T xc = ro_ld(xi[c], z);
+    const T dphi = k0 * (T(1) + k1 * xc);
+    li[c] = ro_st(nc + h * (q * (xc - ro_ld(r[c], z)) + dphi * lap));
   }
 }
 

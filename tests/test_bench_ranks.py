@@ -79,11 +79,12 @@ def test_reference_sample_is_bounded_whatever_the_step_count():
 
 def test_batches_of_ranks_and_of_training_are_disjoint():
     import bench
-    starts = {bench.batch_seed(r, t) for r in range(8) for t in (False, True)}
-    assert len(starts) == 16
-    # 64 consecutive seeds per batch never overlap another batch's
-    ranges = sorted(starts)
-    assert all(b - a >= 64 for a, b in zip(ranges, ranges[1:]))
+    # a rank's test batch: 64 consecutive seeds; its training instances:
+    # TRAIN_BATCHES x 64 consecutive seeds from the training base
+    spans = sorted((bench.batch_seed(r, t), 64 * (bench.TRAIN_BATCHES if t else 1))
+                   for r in range(8) for t in (False, True))
+    assert len({a for a, _ in spans}) == 16
+    assert all(a + n <= b for (a, n), (b, _) in zip(spans, spans[1:]))
 
 
 def test_clock_summary_reads_the_timed_region_and_flags_throttling():

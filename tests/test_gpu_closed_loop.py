@@ -165,14 +165,17 @@ def test_learned_closed_loop_keeps_the_better_start_and_converges(G):
     s.close()
 
 
-def test_rollout_matches_its_definition(G):
+@pytest.mark.parametrize("precision,rtol", [(0, 1e-12), (1, 2e-6)])
+def test_rollout_matches_its_definition(G, precision, rtol):
     """nmpc_rollout: explicit-Euler state trajectory of u from x0 and the
     costate recursion lambda_i = lambda_{i+1} + h (q (x_i - ref) + Phi'(x_i)
     Lap lambda_{i+1}) from lambda_{N+1} = h qf (x_N - ref), written out here
-    with the oracle's model terms, on a ragged 2D + 1D batch."""
+    with the oracle's model terms, on a ragged 2D + 1D batch: to float64
+    rounding on an FP64 handle, to float32 rounding accumulated over the
+    stages (relative 2e-6 of each field's scale) on a MIXED one."""
     import torch
     insts = [wl.heat2d(20, 18, 7, 3, 3, seed=81), wl.heat1d(40, 11, 2, 0.02, seed=82)]
-    s = G.Solver(insts, tol=1e-6, precision=1, max_iter=2000)
+    s = G.Solver(insts, tol=1e-6, precision=precision, max_iter=2000)
     rng = np.random.default_rng(83)
     u = _t(rng.normal(0.0, 0.3, s.n_u))
     x = torch.empty(s.n_s, dtype=torch.float64, device="cuda")
@@ -196,8 +199,8 @@ def test_rollout_matches_its_definition(G):
             nxt = L[i]
         sx = np.abs(X).max()
         sl = np.abs(L).max()
-        assert np.abs(Xb.reshape(X.shape) - X).max() <= 1e-12 * sx
-        assert np.abs(Lb.reshape(L.shape) - L).max() <= 1e-12 * sl
+        assert np.abs(Xb.reshape(X.shape) - X).max() <= rtol * sx
+        assert np.abs(Lb.reshape(L.shape) - L).max() <= rtol * sl
     s.close()
 
 
@@ -241,7 +244,7 @@ def test_fused_rollout_matches_the_float64_rollout(G):
     import torch
     insts = [wl.heat2d(20, 18, 7, 3, 3, seed=81), wl.heat1d(40, 11, 2, 0.02, seed=82),
              wl.heat2d(64, 64, 12, 4, 2, seed=84)]
-    s = G.Solver(insts, tol=1e-6, precision=1, max_iter=2000)
+    s = G.Solver(insts, tol=1e-6, precision=0, max_iter=2000)  # nmpc_rollout in float64
     rng = np.random.default_rng(85)
     u = _t(rng.normal(0.0, 0.3, s.n_u))
     x, lam = (torch.empty(s.n_s, dtype=torch.float64, device="cuda") for _ in range(2))
