@@ -64,6 +64,17 @@ __device__ __forceinline__ F2 bc2(float v) { return F2{v, v}; }
 __device__ __forceinline__ F2 sel2(bool p, F2 a, F2 b) { return p ? a : b; }
 __device__ __forceinline__ F2 d2f2(double2 v) { return F2{d2f(v.x), d2f(v.y)}; }
 
+// float -> double for the update's increments, in five integer operations:
+// exact for normal floats and +-0; a subnormal maps to within 2^-125 of its
+// value; Inf and NaN map to finite values of magnitude 2^128 and more, which
+// the next residual reads as infinite (divergence).
+__device__ __forceinline__ double f2d_upd(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned a = b & 0x7fffffffu;
+  const unsigned hi = (a == 0u) ? 0u : (a >> 3) + 0x38000000u;  // exponent rebiased
+  return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)(b << 29));
+}
+
 // A column pair of float64 values (the float64 residual's fields).
 struct D2 {
   double x, y;
@@ -390,9 +401,9 @@ __device__ __forceinline__ void strip2_body(const IterArgs& A,
           const double* rs = slot_at(-1, 0);
           const double2 xo = ld2(rs + RB_X * 64), lo = ld2(rs + RB_L * 64);
           *reinterpret_cast<double2*>(Xo + c) =
-              make_double2(fma(alpha, f2d(v1.x), xo.x), fma(alpha, f2d(v1.y), xo.y));
+              make_double2(fma(alpha, f2d_upd(v1.x), xo.x), fma(alpha, f2d_upd(v1.y), xo.y));
           *reinterpret_cast<double2*>(Lo + c) =
-              make_double2(fma(alpha, f2d(w.x), lo.x), fma(alpha, f2d(w.y), lo.y));
+              make_double2(fma(alpha, f2d_upd(w.x), lo.x), fma(alpha, f2d_upd(w.y), lo.y));
         }
       } else {
         pw[0].push(dp * v1);
@@ -429,9 +440,9 @@ __device__ __forceinline__ void strip2_body(const IterArgs& A,
               const double* rs = slot_at(-E, 0);  // still in the ring
               const double2 xo = ld2(rs + RB_X * 64), lo = ld2(rs + RB_L * 64);
               *reinterpret_cast<double2*>(Xo + c) =
-                  make_double2(fma(alpha, f2d(v5m.x), xo.x), fma(alpha, f2d(v5m.y), xo.y));
+                  make_double2(fma(alpha, f2d_upd(v5m.x), xo.x), fma(alpha, f2d_upd(v5m.y), xo.y));
               *reinterpret_cast<double2*>(Lo + c) =
-                  make_double2(fma(alpha, f2d(v4.x), lo.x), fma(alpha, f2d(v4.y), lo.y));
+                  make_double2(fma(alpha, f2d_upd(v4.x), lo.x), fma(alpha, f2d_upd(v4.y), lo.y));
             }
           }
         }
