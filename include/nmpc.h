@@ -189,6 +189,16 @@ typedef struct {
                       has an even grid width and even array offsets: 64-column
                       regions with 64 - 4 n_lo own columns, packed float32
                       pairs; else one), 1 = one (32-column regions)         */
+  int tail_rows;    /* two-column strip path, solves: own rows of a second,
+                      finer strip plan taken by the launches of a batch's
+                      tail, when at most tail_below instances still run
+                      (more warps per instance: a few running instances'
+                      strips no longer leave the GPU latency-bound).  0 =
+                      auto (64 where the main plan's rows are >= 256, else
+                      none), -1 = none, else 8..65535                      */
+  int tail_below;   /* running instances at or below which a launch takes the
+                      tail plan: 0 = auto (those whose main-plan strips fill
+                      fewer than six waves of resident warps), else >= 1   */
 } nmpc_opts;
 
 typedef struct {
@@ -206,7 +216,7 @@ typedef struct nmpc_handle nmpc_handle;
    check_every 16, alpha 1, div_limit 1e8, threads auto, graph on, cluster
    auto, split_min 1e-7, u_local 0, cells auto, persistent 0, strips auto,
    strip_rows auto, lines auto, variant Jacobi, barrier_wait_cycles 0,
-   strip_cols auto. */
+   strip_cols auto, tail_rows auto, tail_below auto. */
 void nmpc_default_opts(nmpc_opts* o);
 
 /* Validate the descriptors, build the device instance table and allocate the
@@ -377,8 +387,10 @@ int nmpc_launch_plan(const nmpc_handle* h, int64_t* out);
    per strip, out[3] threads per CTA, out[4] dynamic shared memory per CTA
    (bytes), out[5] actuator patches per iteration (k_patch work items, one
    warp each), out[6] instances on the strip path, out[7] cells of a
-   strip's extended region.  All zero when no instance
-   is on the strip path.  NMPC_ERR_BAD_ARG for NULL arguments. */
+   strip's extended region, out[8] own rows of the tail plan's strips (0:
+   none), out[9] running instances at or below which solve launches take
+   it.  All zero when no instance is on the strip path.  NMPC_ERR_BAD_ARG
+   for NULL arguments. */
 int nmpc_strip_plan(const nmpc_handle* h, int64_t* out);
 
 /* Per-kernel device timing (no counterpart in the paper; for measurement):

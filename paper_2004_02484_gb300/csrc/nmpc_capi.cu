@@ -51,6 +51,7 @@ struct nmpc_handle {
   double* lb[3] = {nullptr, nullptr, nullptr};
   // control
   int* ictl = nullptr;  // iter_k, closed-loop step, n_active, running line items, grid barrier
+                        // and item counters [4..9], running count for the strip plan [10]
                         // words [4], the persistent line launch's item counters [2]
   unsigned long long* res_inf = nullptr;
   unsigned long long* res_err = nullptr;
@@ -103,6 +104,10 @@ struct nmpc_handle {
   int strip_x = 0, strip_y = 0, strip_threads = 0, strip_region = 0;
   int n_strip_inst = 0;
   bool strip2 = false;  // two grid columns per lane (k_strip2)
+  // the tail plan of k_strip2: strips of tail_y own rows for the launches
+  // that run with at most tail_below instances still running
+  int4* tail_d = nullptr;
+  int n_tail = 0, n_tail_even = 0, tail_y = 0, tail_below = 0;
   size_t strip_smem = 0;
   int4* patches_d = nullptr;  // k_patch work items
   int n_patches = 0;
@@ -168,7 +173,7 @@ void free_all(nmpc_handle* h) {
                   h->xb[0], h->xb[1], h->xb[2], h->ub[0], h->ub[1], h->ub[2],
                   h->lb[0], h->lb[1], h->lb[2], h->ictl, h->res_inf, h->res_err, h->res_sq,
                   h->res_first, h->status, h->iters, h->final_buf, h->fin_inf,
-                  h->fin_2, h->f64_count, h->full0, h->scratch, h->strips_d, h->patches_d, h->lines_d, h->lines_act_d,
+                  h->fin_2, h->f64_count, h->full0, h->scratch, h->strips_d, h->tail_d, h->patches_d, h->lines_d, h->lines_act_d,
                   h->v3_d};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -239,6 +244,12 @@ IterArgs make_args(nmpc_handle* h) {
   A.n_strips = h->n_strips;
   A.strip_x = h->strip_x;
   A.strip_y = h->strip_y;
+  A.tail = h->tail_d;
+  A.n_tail = h->n_tail;
+  A.n_tail_even = h->n_tail_even;
+  A.tail_y = h->tail_y;
+  A.tail_below = h->tail_below;
+  A.strip_run = h->ictl + 10;
   A.patches = h->patches_d;
   A.n_patches = h->n_patches;
   A.v3g = h->v3_d;
@@ -582,7 +593,10 @@ constexpr int PATCH_WARPS = 4;  // warps per k_patch block
 
 template <typename T>
 cudaError_t launch_patch(const nmpc_handle* h, const IterArgs& A, cudaStream_t st, int mode, int j) {
-  const int count = half_count(A, j, h->n_patches, h->n_patches_even);
+  int count = half_count(A, j, h->n_patches, h->n_patches_even);
+  // with a tail plan every solve-mode strip launch follows a k_patch launch,
+  // which records the running-instance count for it
+  if (h->n_tail > 0 && mode == nmpc_dev::MODE_SOLVE) count = std::max(count, 1);
   if (count == 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)((count + PATCH_WARPS - 1) / PATCH_WARPS));
@@ -599,7 +613,10 @@ cudaError_t launch_patch(const nmpc_handle* h, const IterArgs& A, cudaStream_t s
 
 template <typename T>
 cudaError_t launch_strip(const nmpc_handle* h, const IterArgs& A, cudaStream_t st, int mode, int j) {
-  const int count = half_count(A, j, h->n_strips, h->n_strips_even);
+  int count = half_count(A, j, h->n_strips, h->n_strips_even);
+  // solve launches cover either plan (warps past the chosen plan's items return)
+  if (h->n_tail > 0 && mode == nmpc_dev::MODE_SOLVE)
+    count = std::max(count, half_count(A, j, h->n_tail, h->n_tail_even));
   if (count == 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
   const int warps = h->strip2 ? nmpc_dev::STRIP2_WARPS : nmpc_dev::STRIP_WARPS;
@@ -851,7 +868,9 @@ bool opts_ok(const nmpc_opts& o) {
          (o.cells >= 0 && o.cells <= 8) && (o.strips >= 0 && o.strips <= 2) && (o.lines >= 0 && o.lines <= 2) &&
          (o.strip_rows >= 0 && o.strip_rows <= 65535) &&
          (o.variant == NMPC_VARIANT_JACOBI || (o.variant == NMPC_VARIANT_REDBLACK && o.alpha == 1.0)) &&
-         o.barrier_wait_cycles >= 0 && (o.strip_cols == 0 || o.strip_cols == 1);
+         o.barrier_wait_cycles >= 0 && (o.strip_cols == 0 || o.strip_cols == 1) &&
+         (o.tail_rows == -1 || o.tail_rows == 0 || (o.tail_rows >= 8 && o.tail_rows <= 65535)) &&
+         o.tail_below >= 0;
 }
 
 int validate(const nmpc_desc* d) {
@@ -1370,6 +1389,8 @@ void nmpc_default_opts(nmpc_opts* o) {
   o->strip_rows = 0;
   o->lines = 0;
   o->strip_cols = 0;
+  o->tail_rows = 0;
+  o->tail_below = 0;
 }
 
 int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
@@ -1478,8 +1499,15 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
       ty = (int)std::min<long long>(my_max, std::max(16LL, (my_max + segs - 1) / segs));
     }
   }
+  // the tail plan (two columns per lane, solves): strips of ty_tail own rows
+  // where the main plan's are at least four times taller
+  int ty_tail = 0;
+  if (my_max > 0 && two && o.tail_rows >= 0) {
+    const int want = o.tail_rows > 0 ? o.tail_rows : 64;
+    if (o.tail_rows > 0 ? want < ty : ty >= 4 * want) ty_tail = want;
+  }
   std::vector<int2> work;
-  std::vector<int4> strips, patches, lines;
+  std::vector<int4> strips, patches, lines, tail;
   std::vector<InstDev> cl_inst;
   for (int b = 0; b < n_instances; ++b) {
     const InstDev& I = h->inst_h[b];
@@ -1492,6 +1520,9 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
       for (int s = 0; s < I.N; ++s) {
         for (int y0 = 0; y0 < I.my; y0 += ty)
           for (int x0 = 0; x0 < I.mx; x0 += tx) strips.push_back(make_int4(b, s, x0, y0));
+        if (ty_tail > 0)
+          for (int y0 = 0; y0 < I.my; y0 += ty_tail)
+            for (int x0 = 0; x0 < I.mx; x0 += tx) tail.push_back(make_int4(b, s, x0, y0));
         for (int a = 0; a < I.nu; ++a) patches.push_back(make_int4(b, s, a, 0));
       }
     } else {
@@ -1511,6 +1542,7 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
     h->n_work_even = (int)(std::stable_partition(work.begin(), work.end(), even2) - work.begin());
     h->n_strips_even =
         (int)(std::stable_partition(strips.begin(), strips.end(), even4) - strips.begin());
+    h->n_tail_even = (int)(std::stable_partition(tail.begin(), tail.end(), even4) - tail.begin());
     h->n_patches_even =
         (int)(std::stable_partition(patches.begin(), patches.end(), even4) - patches.begin());
   }
@@ -1546,6 +1578,20 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
     h->strip2 = true;
     h->strip_x = tx;
     h->strip_y = ty;
+    if (!tail.empty()) {
+      // the tail plan while the running instances' main-plan strips fill
+      // fewer than six waves of resident warps (3 CTAs of 4 warps per SM)
+      h->n_tail = (int)tail.size();
+      h->tail_y = ty_tail;
+      const long long per_launch = std::max(1, h->rb ? h->n_strips / 2 : h->n_strips);
+      const long long waves6 = 6LL * std::max(1, h->num_sms) * STRIP2_MIN_BLOCKS *
+                               nmpc_dev::STRIP2_WARPS;
+      h->tail_below = o.tail_below > 0
+                          ? o.tail_below
+                          : (int)std::max(1LL, waves6 * h->n_strip_inst / per_launch);
+    } else {
+      h->n_tail_even = 0;
+    }
     h->strip_threads = 32 * nmpc_dev::STRIP2_WARPS;
     h->strip_region = 64 * (ty + 2 * E);
     constexpr int NF1 = nmpc_dev::strip_fields(true);
@@ -1620,6 +1666,7 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
   A(dev_alloc(&h->inst_d, n_instances));
   A(dev_alloc(&h->work_d, h->n_work));
   A(dev_alloc(&h->strips_d, h->n_strips));
+  A(dev_alloc(&h->tail_d, h->n_tail));
   A(dev_alloc(&h->patches_d, h->n_patches));
   A(dev_alloc(&h->lines_d, h->n_lines));
   A(dev_alloc(&h->lines_act_d, h->n_lines));
@@ -1634,7 +1681,7 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
     A(dev_alloc(&h->lb[q], h->n_s));
     A(dev_alloc(&h->ub[q], h->n_u));
   }
-  A(dev_alloc(&h->ictl, 10));
+  A(dev_alloc(&h->ictl, 12));
   A(dev_alloc(&h->res_inf, (size_t)nmpc_dev::RES_SLOTS * n_instances));
   A(dev_alloc(&h->res_err, (size_t)nmpc_dev::RES_SLOTS * n_instances));
   A(dev_alloc(&h->res_sq, (size_t)nmpc_dev::RES_SLOTS * n_instances));
@@ -1663,13 +1710,15 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
       A(cudaMemcpy(h->work_d, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice));
     if (!strips.empty())
       A(cudaMemcpy(h->strips_d, strips.data(), strips.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    if (h->n_tail > 0)
+      A(cudaMemcpy(h->tail_d, tail.data(), tail.size() * sizeof(int4), cudaMemcpyHostToDevice));
     if (!patches.empty())
       A(cudaMemcpy(h->patches_d, patches.data(), patches.size() * sizeof(int4),
                    cudaMemcpyHostToDevice));
     if (!lines.empty())
       A(cudaMemcpy(h->lines_d, lines.data(), lines.size() * sizeof(int4), cudaMemcpyHostToDevice));
     A(cudaMemcpy(h->act_d, act_all.data(), act_all.size() * sizeof(int), cudaMemcpyHostToDevice));
-    A(cudaMemset(h->ictl, 0, 10 * sizeof(int)));
+    A(cudaMemset(h->ictl, 0, 12 * sizeof(int)));
     A(cudaDeviceSynchronize());
   }
   if (!ok) {
@@ -1960,6 +2009,8 @@ int nmpc_strip_plan(const nmpc_handle* h, int64_t* out) {
   out[5] = on ? h->n_patches : 0;
   out[6] = h->n_strip_inst;
   out[7] = on ? h->strip_region : 0;
+  out[8] = on ? h->tail_y : 0;
+  out[9] = on && h->tail_y > 0 ? h->tail_below : 0;
   return NMPC_OK;
 }
 
@@ -2174,7 +2225,7 @@ extern "C" int nmpc_solve_noalloc(const nmpc_desc* desc, const nmpc_opts* opts,
     o_l[q] = carve(&off, (size_t)n_s * sizeof(double));
     o_u[q] = carve(&off, (size_t)n_u * sizeof(double));
   }
-  const size_t o_ctl = carve(&off, 10 * sizeof(int));  // the handle's ictl layout
+  const size_t o_ctl = carve(&off, 12 * sizeof(int));  // the handle's ictl layout
   const size_t o_rinf = carve(&off, nmpc_dev::RES_SLOTS * sizeof(unsigned long long));
   const size_t o_rerr = carve(&off, nmpc_dev::RES_SLOTS * sizeof(unsigned long long));
   const size_t o_rsq = carve(&off, nmpc_dev::RES_SLOTS * sizeof(double));

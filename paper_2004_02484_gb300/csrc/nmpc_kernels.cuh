@@ -142,6 +142,12 @@ struct IterArgs {
   const int4* strips;
   int n_strips;
   int strip_x, strip_y;  // own columns and rows per strip
+  // the tail plan (k_strip2, solves): strips of tail_y own rows, taken by a
+  // launch when the running-instance count that k_patch recorded before it
+  // (*strip_run) is at most tail_below (n_tail = 0: no tail plan)
+  const int4* tail;
+  int n_tail, n_tail_even, tail_y, tail_below;
+  int* strip_run;
   // k_patch: (instance, stage, actuator) per warp; v3 per control (float64)
   const int4* patches;
   int n_patches;

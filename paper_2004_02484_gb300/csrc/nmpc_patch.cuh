@@ -348,6 +348,10 @@ __global__ void __launch_bounds__(128) k_patch(IterArgs A, int MODE, int j) {
   const int half = launch_half(A, j);
   const int rd = (MODE == MODE_SOLVE) ? (k & 1) : 0;
   pdl_wait();
+  // the running-instance count for the strip launch that follows (no
+  // instance finishes between the two: only the strip kernels keep the books)
+  if (MODE == MODE_SOLVE && A.n_tail > 0 && blockIdx.x == 0 && threadIdx.x == 0)
+    *A.strip_run = *(volatile int*)A.n_active;
   const int item = ((A.rb && half) ? A.n_patches_even : 0) + blockIdx.x * WPB + warp;
   const int item_end = A.rb ? (half ? A.n_patches : A.n_patches_even) : A.n_patches;
   if (item >= item_end) return;  // warp-uniform; no block barriers follow

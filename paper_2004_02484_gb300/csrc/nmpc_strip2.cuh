@@ -132,7 +132,7 @@ template <int n_lo, bool FULL, bool RBN, bool GSN = false>
 __device__ __forceinline__ void strip2_body(const IterArgs& A,
                                             StripShared2<strip_ring_rows(n_lo), strip_fields(RBN)>& ws,
                                             int lane, int b, int s, int k, int rd, int x0, int y0,
-                                            bool resid_only) {
+                                            int strip_y, bool resid_only) {
   constexpr int E = 2 * n_lo - 1;
   constexpr int P = strip2_pad(n_lo);
   constexpr int RING = strip_ring_rows(n_lo);
@@ -143,7 +143,7 @@ __device__ __forceinline__ void strip2_body(const IterArgs& A,
   const bool last = (s == I.N - 1);
   const long long so = I.s_off + (long long)s * I.ng;
   // region: columns x0 - P + 2 lane (+1), rows y0 - E .. y0 + own_rows + E - 1
-  const int own_rows = min(A.strip_y, I.my - y0);
+  const int own_rows = min(strip_y, I.my - y0);
   const int RH = own_rows + 2 * E;
   const int gx = x0 - P + 2 * lane;               // even; the pair is gx, gx + 1
   const bool gx_ok = gx >= 0 && gx < I.mx;        // both columns (even width)
@@ -538,10 +538,15 @@ __global__ void __launch_bounds__(STRIP2_WARPS * 32, STRIP2_MIN_BLOCKS)
   const int half = launch_half(A, j_launch);
   const int rd = (MODE == MODE_SOLVE) ? (k & 1) : 0;
   pdl_wait();
-  const int item = ((A.rb && half) ? A.n_strips_even : 0) + blockIdx.x * STRIP2_WARPS + warp;
-  const int item_end = A.rb ? (half ? A.n_strips : A.n_strips_even) : A.n_strips;
+  // the tail plan once few instances run (the count k_patch recorded before
+  // this launch: the same value for every warp)
+  const bool tail = MODE == MODE_SOLVE && A.n_tail > 0 && *A.strip_run <= A.tail_below;
+  const int n_all = tail ? A.n_tail : A.n_strips, n_even = tail ? A.n_tail_even : A.n_strips_even;
+  const int item = ((A.rb && half) ? n_even : 0) + blockIdx.x * STRIP2_WARPS + warp;
+  const int item_end = A.rb ? (half ? n_all : n_even) : n_all;
   if (item >= item_end) return;  // warp-uniform; no block barriers in this kernel
-  const int4 it = A.strips[item];
+  const int4 it = (tail ? A.tail : A.strips)[item];
+  const int sy = tail ? A.tail_y : A.strip_y;
   const int b = it.x, s = it.y, x0 = it.z, y0 = it.w;
   if (!stage_in_half(A, s, half)) return;
 
@@ -564,10 +569,10 @@ __global__ void __launch_bounds__(STRIP2_WARPS * 32, STRIP2_MIN_BLOCKS)
     resid_only = (k == A.max_iter);
   }
   if (full)
-    strip2_body<n_lo, true, RBN>(A, ws, lane, b, s, k, rd, x0, y0, resid_only);
+    strip2_body<n_lo, true, RBN>(A, ws, lane, b, s, k, rd, x0, y0, sy, resid_only);
   else if (RBN && MODE == MODE_SOLVE)
     strip2_body<n_lo, false, false, true>(A, *reinterpret_cast<WS3*>(wbase), lane, b, s, k, rd,
-                                          x0, y0, resid_only);
+                                          x0, y0, sy, resid_only);
   else
-    strip2_body<n_lo, false, RBN>(A, ws, lane, b, s, k, rd, x0, y0, resid_only);
+    strip2_body<n_lo, false, RBN>(A, ws, lane, b, s, k, rd, x0, y0, sy, resid_only);
 }

@@ -2,6 +2,7 @@
 
     python -m paper_2004_02484_gb300.experiments batch1d   [--n 1024]
     python -m paper_2004_02484_gb300.experiments closedloop [--n 64 --steps 200 --grid 256]
+        [--variant 1 --graph 0 --tail-rows -1 --tail-below 0]
     python -m paper_2004_02484_gb300.experiments solve      [--n 8 --grid 256 --graph 1]
 
 batch1d:    the ragged 1D batch (M ~ U{32..256}, N ~ U{10..60}, n_u ~ U{1..4},
@@ -117,6 +118,7 @@ def closedloop(n: int, steps: int, grid: int, horizon: int, n_sub: int, check: i
            "iters_first_step_mean": float(iters[0].mean()),
            "iters_later_mean": float(iters[1:].mean()) if steps > 1 else None,
            "res_max": float(res.max()), "launches": launches,
+           "iters": iters.tolist(),
            "hbm_gbs_algorithmic": BYTES_PER_CELL_STAGE * cells * iter_launches / dt / 1e9,
            "strip_plan": strip_plan}
     if check:
@@ -416,6 +418,10 @@ def main():
     ap.add_argument("--wave-single", type=int, default=1, help="wave: also time one instance")
     ap.add_argument("--variant", type=int, default=0,
                     help="upper layer: 0 Jacobi (eq. 15), 1 red-black Gauss-Seidel")
+    ap.add_argument("--tail-rows", type=int, default=0,
+                    help="closedloop: rows of the strip path's tail plan (0 auto, -1 none)")
+    ap.add_argument("--tail-below", type=int, default=0,
+                    help="closedloop: running instances that select the tail plan (0 auto)")
     a = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
@@ -450,7 +456,8 @@ def main():
     else:
         res = closedloop(a.n or 64, a.steps, a.grid, a.horizon, a.n_sub, a.check,
                          cluster=a.cluster, threads=a.threads, strips=a.strips,
-                         strip_rows=a.strip_rows)
+                         strip_rows=a.strip_rows, variant=a.variant, use_graph=a.graph,
+                         tail_rows=a.tail_rows, tail_below=a.tail_below)
         res.update({"cluster": a.cluster, "threads": a.threads})
         print(json.dumps(res), flush=True)
 

@@ -55,7 +55,8 @@ class nmpc_opts(ctypes.Structure):
                 ("cells", ctypes.c_int), ("persistent", ctypes.c_int),
                 ("strips", ctypes.c_int), ("strip_rows", ctypes.c_int),
                 ("lines", ctypes.c_int), ("variant", ctypes.c_int),
-                ("barrier_wait_cycles", ctypes.c_int64), ("strip_cols", ctypes.c_int)]
+                ("barrier_wait_cycles", ctypes.c_int64), ("strip_cols", ctypes.c_int),
+                ("tail_rows", ctypes.c_int), ("tail_below", ctypes.c_int)]
 
 
 class nmpc_stats(ctypes.Structure):
@@ -189,10 +190,11 @@ def nmpc_setup(instances: Sequence, **opts) -> ctypes.c_void_p:
 def nmpc_strip_plan(h) -> dict:
     """The handle's strip path (strips per iteration, strip shape, threads, shared
     memory, actuator patches per iteration, instances on the path, region
-    cells)."""
-    out = (ctypes.c_int64 * 8)()
+    cells, the tail plan's rows and the running count that selects it)."""
+    out = (ctypes.c_int64 * 10)()
     _check(LIB.nmpc_strip_plan(h, out), "nmpc_strip_plan")
-    keys = ("strips", "strip_x", "strip_y", "threads", "smem", "patches", "instances", "region")
+    keys = ("strips", "strip_x", "strip_y", "threads", "smem", "patches", "instances", "region",
+            "tail_rows", "tail_below")
     return {k: int(v) for k, v in zip(keys, out)}
 
 

@@ -87,7 +87,9 @@ def test_path_options_default_to_auto_and_are_validated_on_the_host(lib_path):
     from paper_2004_02484_gb300 import workloads as wl
     o = G.nmpc_default_opts()
     assert (o.strips, o.strip_rows, o.lines) == (0, 0, 0)
-    for field, value in (("lines", 3), ("lines", -1), ("strips", 3)):
+    assert (o.strip_cols, o.tail_rows, o.tail_below) == (0, 0, 0)
+    for field, value in (("lines", 3), ("lines", -1), ("strips", 3), ("tail_rows", -2),
+                         ("tail_rows", 7), ("tail_below", -1), ("strip_cols", 2)):
         o = G.nmpc_default_opts()
         setattr(o, field, value)
         descs, keep = G.make_descs([wl.heat1d_single()])

@@ -347,3 +347,39 @@ def test_strip_mixed_solve_reaches_a_tight_tolerance(G):
         K = O.kkt(p, xs[b].reshape((p.N,) + p.shape), us[b].reshape(p.N, p.nu),
                   ls[b].reshape((p.N,) + p.shape))
         assert O.kkt_norms(*K)[0] <= 1.0001e-8, b
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_tail_plan_solve_is_bit_identical_to_the_main_plan(G, variant):
+    """A solve whose launches all take the tail plan (strips of 8 own rows,
+    ragged against 30 grid rows, tail_below = every instance) gives the main
+    plan's (24-row strips, no tail plan) iterations, statuses and iterates bit
+    for bit: every own cell is computed from the same inputs by the same
+    code, whichever strip holds it.  The automatic plan keeps a tail plan of
+    64 rows for 256-row strips and none for short ones."""
+    import torch
+    insts = [wl.heat2d(40, 30, 12, 2, 2, seed=3), wl.heat2d(40, 30, 12, 2, 2, seed=5)]
+    out = []
+    for tail in (dict(tail_rows=-1), dict(tail_rows=8, tail_below=len(insts))):
+        s = G.Solver(insts, tol=1e-7, precision=G.NMPC_MIXED, variant=variant, strips=1,
+                     strip_rows=24, max_iter=4000, **tail)
+        plan = G.nmpc_strip_plan(s.h)
+        assert plan["strip_x"] == 56 and plan["strip_y"] == 24
+        assert plan["tail_rows"] == (8 if "tail_below" in tail else 0)
+        rc, st = s.solve()
+        torch.cuda.synchronize()
+        assert rc == G.NMPC_OK
+        out.append(([(x.iters, x.status, x.res_inf, x.f64_iters) for x in st],
+                    [t.cpu().numpy() for t in s.state()]))
+        s.close()
+    assert out[0][0] == out[1][0]
+    for a, b in zip(out[0][1], out[1][1]):
+        assert np.array_equal(a, b)
+    big = [wl.heat2d(256, 256, 4, 2, 2, seed=9)]
+    s = G.Solver(big, precision=G.NMPC_MIXED, strips=1, strip_rows=256)
+    plan = G.nmpc_strip_plan(s.h)
+    assert plan["tail_rows"] == 64 and plan["tail_below"] >= 1
+    s.close()
+    s = G.Solver(big, precision=G.NMPC_MIXED, strips=1, strip_rows=128)
+    assert G.nmpc_strip_plan(s.h)["tail_rows"] == 0
+    s.close()
