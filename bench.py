@@ -71,10 +71,10 @@ BYTES_PER_POINT_STAGE = 32
 # DRAM bytes over algorithmic bytes of the strip kernel (two columns per
 # lane), from ncu captures on 8 instances (dram__bytes_read.sum + write.sum
 # per launch over 32 B x the launch's cell-stages): Jacobi 1.741 GB / 1.678
-# GB; red-black half 0 1.321 GB and half 1 1.310 GB over 0.839 GB each (the
+# GB; red-black half 0 1.317 GB and half 1 1.307 GB over 0.839 GB each (the
 # neighbouring stages' x_{i-1}, lambda_{i+1} are not processed in the same
 # launch, so they come from DRAM rather than L2)
-TRAFFIC_RATIO = {"jacobi": 1.741 / 1.678, "redblack": (1.321 + 1.310) / (2 * 0.839)}
+TRAFFIC_RATIO = {"jacobi": 1.741 / 1.678, "redblack": (1.317 + 1.307) / (2 * 0.839)}
 
 
 def parse():

@@ -44,6 +44,7 @@ struct nmpc_handle {
   int* act_d = nullptr;
   double* x0_d = nullptr;
   double* ref_d = nullptr;
+  float* ref_f_d = nullptr;  // ref truncated to float32 (two-column strip path)
   double* uo_d = nullptr;  // staging for the host-pointer solve
   double* w_d = nullptr;   // staging for host weights
   double* xb[3] = {nullptr, nullptr, nullptr};  // A, B, current
@@ -165,11 +166,22 @@ cudaError_t dev_alloc(P** p, size_t count) {
   return cudaMalloc((void**)p, count * sizeof(P));
 }
 
+// ref into the handle's buffer, and its float32 copy where the two-column
+// strip path reads one.
+cudaError_t load_ref(nmpc_handle* h, const double* ref, cudaMemcpyKind kind, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(h->ref_d, ref, h->n_g * sizeof(double), kind, st);
+  if (e != cudaSuccess || !h->ref_f_d) return e;
+  nmpc_dev::k_f32_copy<<<(unsigned)std::min<long long>(1024, (h->n_g + 255) / 256), 256, 0, st>>>(
+      h->ref_d, h->ref_f_d, h->n_g);
+  h->launches++;
+  return cudaGetLastError();
+}
+
 void free_all(nmpc_handle* h) {
   if (!h) return;
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
   if (h->loop_exec) cudaGraphExecDestroy(h->loop_exec);
-  void* ptrs[] = {h->inst_d, h->work_d, h->act_d, h->x0_d, h->ref_d, h->uo_d, h->w_d,
+  void* ptrs[] = {h->inst_d, h->work_d, h->act_d, h->x0_d, h->ref_d, h->ref_f_d, h->uo_d, h->w_d,
                   h->xb[0], h->xb[1], h->xb[2], h->ub[0], h->ub[1], h->ub[2],
                   h->lb[0], h->lb[1], h->lb[2], h->ictl, h->res_inf, h->res_err, h->res_sq,
                   h->res_first, h->status, h->iters, h->final_buf, h->fin_inf,
@@ -191,6 +203,7 @@ IterArgs make_args(nmpc_handle* h) {
   A.act = h->act_d;
   A.x0 = h->x0_d;
   A.ref = h->ref_d;
+  A.ref_f = h->ref_f_d;
   for (int q = 0; q < 2; ++q) {
     A.xin[q] = h->xb[q];
     A.uin[q] = h->ub[q];
@@ -1674,6 +1687,7 @@ int nmpc_setup(const nmpc_desc* descs, int n_instances, const nmpc_opts* opts,
   A(dev_alloc(&h->act_d, act_all.size()));
   A(dev_alloc(&h->x0_d, h->n_g));
   A(dev_alloc(&h->ref_d, h->n_g));
+  if (h->strip2) A(dev_alloc(&h->ref_f_d, h->n_g));
   A(dev_alloc(&h->uo_d, h->n_u));
   A(dev_alloc(&h->w_d, 3 * (size_t)n_instances));
   for (int q = 0; q < 3; ++q) {
@@ -1737,7 +1751,7 @@ int nmpc_solve(nmpc_handle* h, const double* x0, const double* ref, int horizon,
   if (!h || !x0 || !ref) return NMPC_ERR_BAD_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   CK(cudaMemcpyAsync(h->x0_d, x0, h->n_g * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(h->ref_d, ref, h->n_g * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(load_ref(h, ref, cudaMemcpyDeviceToDevice, st));
   return solve_core(h, horizon, weights, init, u_out, stats, st);
 }
 
@@ -1747,7 +1761,7 @@ int nmpc_solve_host(nmpc_handle* h, const double* x0, const double* ref, int hor
   if (!h || !x0 || !ref) return NMPC_ERR_BAD_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   CK(cudaMemcpyAsync(h->x0_d, x0, h->n_g * sizeof(double), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(h->ref_d, ref, h->n_g * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(load_ref(h, ref, cudaMemcpyHostToDevice, st));
   const double* wd = nullptr;
   if (weights) {
     CK(cudaMemcpyAsync(h->w_d, weights, 3 * h->n_inst * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -1808,7 +1822,7 @@ int nmpc_residual(nmpc_handle* h, const double* x0, const double* ref, const dou
   if (!h || !x0 || !ref || !x || !u || !lam || !out) return NMPC_ERR_BAD_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   CK(cudaMemcpyAsync(h->x0_d, x0, h->n_g * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(h->ref_d, ref, h->n_g * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(load_ref(h, ref, cudaMemcpyDeviceToDevice, st));
   return oneshot(h, x, u, lam, nullptr, nullptr, nullptr, 1, out, st);
 }
 
@@ -1820,7 +1834,7 @@ int nmpc_iterate(nmpc_handle* h, const double* x0, const double* ref, const doub
     return NMPC_ERR_BAD_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   CK(cudaMemcpyAsync(h->x0_d, x0, h->n_g * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  CK(cudaMemcpyAsync(h->ref_d, ref, h->n_g * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(load_ref(h, ref, cudaMemcpyDeviceToDevice, st));
   // ping-pong through the handle's A/B buffers, then copy out (so in and out
   // may alias)
   const double* xi = x_in;
@@ -1868,7 +1882,7 @@ int nmpc_closed_loop(nmpc_handle* h, double* w, const double* ref, int steps, in
   if (!h || !w || !ref || steps < 1 || n_sub < 1) return NMPC_ERR_BAD_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   if (h->opts.use_graph && !h->persistent) {
-    CK(cudaMemcpyAsync(h->ref_d, ref, h->n_g * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(load_ref(h, ref, cudaMemcpyDeviceToDevice, st));
     return closed_loop_graph(h, w, steps, n_sub, u_hist, iters_hist, res_hist, st);
   }
   const int n = h->n_inst;
@@ -1877,7 +1891,7 @@ int nmpc_closed_loop(nmpc_handle* h, double* w, const double* ref, int steps, in
   for (int t = 0; t < steps; ++t) {
     // the measured plant state is the next problem's x0
     CK(cudaMemcpyAsync(h->x0_d, w, h->n_g * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(h->ref_d, ref, h->n_g * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(load_ref(h, ref, cudaMemcpyDeviceToDevice, st));
     int rc = solve_core(h, 0, nullptr, (t == 0 && !h->has_state) ? NMPC_INIT_COLD : NMPC_INIT_SHIFT,
                         nullptr, stats.data(), st);
     if (rc == NMPC_ERR_BAD_ARG || rc == NMPC_ERR_CUDA) return rc;
@@ -1941,7 +1955,7 @@ int nmpc_closed_loop_learned(nmpc_handle* h, double* w, const double* ref, int s
                              double* u_hist, int* iters_hist, double* res_hist, void* stream) {
   if (!h || !w || !ref || !start || !u_guess || steps < 1 || n_sub < 1) return NMPC_ERR_BAD_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  CK(cudaMemcpyAsync(h->ref_d, ref, h->n_g * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(load_ref(h, ref, cudaMemcpyDeviceToDevice, st));
   if (h->opts.use_graph && !h->persistent)
     return closed_loop_graph(h, w, steps, n_sub, u_hist, iters_hist, res_hist, st, start, ctx,
                              u_guess);

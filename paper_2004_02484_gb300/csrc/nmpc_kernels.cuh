@@ -142,6 +142,7 @@ struct IterArgs {
   const int4* strips;
   int n_strips;
   int strip_x, strip_y;  // own columns and rows per strip
+  const float* ref_f;    // ref truncated to float32 (d2f) for k_strip2's split residual
   // the tail plan (k_strip2, solves): strips of tail_y own rows, taken by a
   // launch when the running-instance count that k_patch recorded before it
   // (*strip_run) is at most tail_below (n_tail = 0: no tail plan)
@@ -406,6 +407,15 @@ __device__ __forceinline__ double f2d(float f) {
   lo = (a < 0x00800000u) ? 0u : lo;
   hi = (a >= 0x7f800000u) ? (0x7ff00000u | (a >> 3)) : hi;  // Inf, NaN
   return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)lo);
+}
+
+// dst = d2f(src): a float32 copy of a float64 field with the kernels' own
+// truncation (a copy read in place of truncating the field again every
+// iteration).
+__global__ void k_f32_copy(const double* src, float* dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = d2f(src[i]);
 }
 
 // Sum of the stencil neighbours' values, each weighted by its axis

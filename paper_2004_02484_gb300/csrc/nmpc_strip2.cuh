@@ -194,6 +194,7 @@ __device__ __forceinline__ void strip2_body(const IterArgs& A,
   const double* XPg = (s == 0) ? A.x0 + I.g_off : (GSN ? A.xout[rd ^ 1] : A.xin[rd]) + so - I.ng;
   const double* LNg = (GSN ? A.lout[rd ^ 1] : A.lin[rd]) + so + I.ng;
   const double* RFg = A.ref + I.g_off;
+  const float* RFf = A.ref_f + I.g_off;  // the split form reads ref as float32 pairs
   const double* XPNg = (s == 0) ? A.x0 + I.g_off : A.xout[rd ^ 1] + so - I.ng;
   const double* LNNg = A.lout[rd ^ 1] + so + I.ng;
   double* ring = ws.ring + 2 * lane;
@@ -222,7 +223,10 @@ __device__ __forceinline__ void strip2_body(const IterArgs& A,
     cp_async16_zfill(d + RB_L * 64, Lg + c, ok);
     cp_async16_zfill(e + RS_XP * 64, XPg + c, ok);
     cp_async16_zfill(e + RS_LN * 64, (last ? Lg : LNg) + c, ok && !last);
-    cp_async16_zfill(e + RS_RF * 64, RFg + c, ok);
+    if constexpr (full)
+      cp_async16_zfill(e + RS_RF * 64, RFg + c, ok);
+    else  // the first 8 bytes of the pair's slot
+      cp_async8_zfill(e + RS_RF * 64, RFf + c, ok);
     if constexpr (RBN) {
       cp_async16_zfill(e + RS_XPN * 64, XPNg + c, ok);
       cp_async16_zfill(e + RS_LNN * 64, (last ? Lg : LNNg) + c, ok && !last);
@@ -311,9 +315,10 @@ __device__ __forceinline__ void strip2_body(const IterArgs& A,
       const double* rs = slot_at(-1, 0);
       const double* qs = sslot_row(j - 1, 0);
       const double2 x = ld2(rs + RB_X * 64), lam = ld2(rs + RB_L * 64);
-      const double2 xp = ld2(qs + RS_XP * 64), rc = ld2(qs + RS_RF * 64);
+      const double2 xp = ld2(qs + RS_XP * 64);
       F2 K1;
       if constexpr (full) {
+        const double2 rc = ld2(qs + RS_RF * 64);
         const double2 lnv = last ? make_double2(hqfd * (x.x - rc.x), hqfd * (x.y - rc.y))
                                  : ld2(qs + RS_LN * 64);
         const D2 lphi = nsum2(phd, cxd, cyd) - dcd * phd.w1;
@@ -347,7 +352,7 @@ __device__ __forceinline__ void strip2_body(const IterArgs& A,
         ax = F2{d2f(hd * (qd + k0d * k1d * mu.x) + hq), d2f(hd * (qd + k0d * k1d * mu.y) + hq)};
       } else {
         // Lap Phi(x) in difference form (see k_strip)
-        const F2 xv = xvf.w1, rv = d2f2(rc);
+        const F2 xv = xvf.w1, rv = *reinterpret_cast<const F2*>(qs + RS_RF * 64);
         const F2 xl = xvf.left(), xr = xvf.right();
         const F2 dlx = xl - xv, drx = xr - xv, dux = xvf.w0 - xv, ddx = xvf.w2 - xv;
         const F2 sx = fma2(dlx, fma2(fk1h, xl + xv, one), drx * fma2(fk1h, xr + xv, one));
