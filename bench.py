@@ -63,7 +63,7 @@ TOL = 1e-6
 N_INST = 64
 N_SUB = 2          # explicit-Euler plant sub-steps per sampling period
 TRAIN_STEPS = 12   # closed-loop steps of the training instances
-TRAIN_BATCHES = 4  # batches of training instances (4 x 64 instances: 3072 samples)
+TRAIN_BATCHES = 8  # batches of training instances (8 x 64 instances: 6144 samples)
 FIT_STEPS = 1500   # Adam steps of the learned start
 # algorithmic bytes per cell-stage per iteration: read x_i, lambda_i and write
 # them back in float64 (the neighbour-stage reads are the same arrays)
