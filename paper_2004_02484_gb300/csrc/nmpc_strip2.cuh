@@ -64,10 +64,11 @@ __device__ __forceinline__ F2 bc2(float v) { return F2{v, v}; }
 __device__ __forceinline__ F2 sel2(bool p, F2 a, F2 b) { return p ? a : b; }
 __device__ __forceinline__ F2 d2f2(double2 v) { return F2{d2f(v.x), d2f(v.y)}; }
 
-// float -> double for the update's increments, in five integer operations:
-// exact for normal floats and +-0; a subnormal maps to within 2^-125 of its
-// value; Inf and NaN map to finite values of magnitude 2^128 and more, which
-// the next residual reads as infinite (divergence).
+// float -> double for the update's increments in a few integer operations (no
+// subnormal or Inf/NaN cases): exact for normal floats and +-0; a subnormal
+// maps to within 2^-125 of its value; Inf and NaN map to finite values of
+// magnitude 2^128 and more, which the next residual reads as infinite
+// (divergence).
 __device__ __forceinline__ double f2d_upd(float f) {
   const unsigned b = __float_as_uint(f);
   const unsigned a = b & 0x7fffffffu;
